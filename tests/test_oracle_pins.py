@@ -1,0 +1,317 @@
+"""Pins of the FP64 oracle's stress step against what the paper and the
+mathematics fix (no GPU).
+
+P2  zero flow: sigma(t) = sigma0 E_alpha(-t^alpha / Wi)  (Section 5.1 closed form)
+P3  (i) the mode recursion equals the full-history convolution with the exact
+    generating function of the BDF2 mode scheme; (ii) with an SOE accurate far
+    below dt the scheme equals BDF2 convolution quadrature of the exact symbol
+P4  alpha = 1: Oldroyd-B relaxation exp(-t/Wi) at second order; the steady
+    stress of the Lemma of Section 3.3 (Gaussian with C = I/2 - Wi D) for
+    symmetric trace-free D; the Lyapunov steady state for a general kappa
+P5  the full d x d tensor form stays symmetric and equals the packed form
+P6  uniform kappa and constant u give the same stress at every point
+P7  smooth start from rest: second order in dt for every alpha
+P8  one Fourier mode advected by a constant velocity follows
+    E_alpha(-(1/Wi + i k u) t^alpha) as dt and h go to zero
+P9  the stress is affine in (sigma0, G)
+adjoint: the reference adjoint agrees with FP64 central finite differences.
+
+Independent formulations used here (full-tensor Kronecker systems, generating
+functions, NumPy solves) share no code with the oracle's step.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.special
+
+from oracle import orc, soe, special
+from paper_2411_17294_gb300 import inputs
+
+PACK2 = [(0, 0), (0, 1), (1, 1)]
+PACK3 = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+
+
+def pack(S):
+    d = S.shape[0]
+    pairs = PACK2 if d == 2 else PACK3
+    return np.array([S[i, j] for i, j in pairs])
+
+
+def unpack(v, d):
+    pairs = PACK2 if d == 2 else PACK3
+    S = np.zeros((d, d))
+    for c, (i, j) in enumerate(pairs):
+        S[i, j] = S[j, i] = v[c]
+    return S
+
+
+def direct_history_solve(W, kap_of_n, S0, Wi, G, dt, alpha, steps):
+    """Full-history scheme  sum_{k=0}^{n+1} W_k (S^{n+1-k} - S0)
+         = dt [k* S + S k*^T - S/Wi + G (k* + k*^T) g(t_{n+1})]   (S^k = S0, k <= 0)
+    solved with full d x d unknowns (row-major vec, Kronecker products)."""
+    d = S0.shape[0]
+    I = np.eye(d)
+    hist = [S0.copy()]
+    for n in range(steps):
+        k = 2.0 * kap_of_n(n) - kap_of_n(n - 1 if n > 0 else 0)
+        g = 1.0 if alpha == 1.0 else ((n + 1) * dt) ** (alpha - 1) / math.gamma(alpha)
+        L = np.kron(k, I) + np.kron(I, k)
+        A = (W[0] + dt / Wi) * np.eye(d * d) - dt * L
+        rhs = W[0] * S0.ravel() + dt * G * g * (k + k.T).ravel()
+        for j in range(1, n + 2):
+            rhs -= W[j] * (hist[n + 1 - j] - S0).ravel()
+        hist.append(np.linalg.solve(A, rhs).reshape(d, d))
+    return hist
+
+
+def point_problem(dim, alpha, Wi, beta, dt, mu=None, w=None, **kw):
+    return orc.Problem(dim=dim, n=(1,) * dim, alpha=alpha, Wi=Wi, beta=beta, dt=dt,
+                       mu=np.zeros(0) if mu is None else mu, w=np.zeros(0) if w is None else w, **kw)
+
+
+# ------------------------------------------------------------------ P3 (i)
+@pytest.mark.parametrize("dim,alpha", [(2, 0.5), (3, 0.3), (3, 0.8), (2, 1.0)])
+def test_mode_recursion_equals_full_history(dim, alpha):
+    rng = np.random.default_rng(7)
+    dt, steps, Wi, beta = 2e-3, 80, 1.3, 0.4
+    if alpha < 1:
+        mu, w = soe.soe_nnls(alpha, dt, steps * dt, 8)
+        W = special.cq_weights_soe(mu, w, dt, steps)
+    else:
+        mu = w = None
+        W = np.zeros(steps + 1)
+        W[:3] = [1.5, -2.0, 0.5]
+    kseq = [rng.normal(scale=2.0, size=(dim, dim)) for _ in range(steps)]
+    S0 = unpack(rng.normal(size=3 if dim == 2 else 6), dim)
+    G = (1 - beta) / Wi
+    hist = direct_history_solve(W, lambda n: kseq[n], S0, Wi, G, dt, alpha, steps)
+    prob = point_problem(dim, alpha, Wi, beta, dt, mu, w)
+    o = orc.Oracle(prob, pack(S0)[:, None])
+    for n in range(steps):
+        o.step(kseq[n].reshape(-1, 1), kseq[n - 1 if n > 0 else 0].reshape(-1, 1))
+        ref = pack(hist[n + 1])
+        assert np.allclose(o.sig_n[:, 0], ref, rtol=1e-11, atol=1e-12 * np.max(np.abs(ref)))
+
+
+# ------------------------------------------------------------------ P3 (ii)
+def test_scheme_is_bdf2_convolution_quadrature_of_exact_symbol():
+    alpha, dt, steps = 0.5, 1e-2, 100
+    mu, w = soe.soe_expquad(alpha, dt * 1e-14, 10 * steps * dt, 700, tail=1e-14)
+    Wsoe = special.cq_weights_soe(mu, w, dt, steps)
+    Wex = special.cq_weights_power(alpha, dt, steps)
+    # the SOE resolves the kernel down to t_min = 1e-14 dt; the kernel mass it
+    # misses below t_min is (t_min/dt)^(1-alpha) = 1e-7 of the first weight
+    assert np.max(np.abs(Wsoe - Wex)) < 2e-7 * abs(Wex[0])
+    assert np.max(np.abs(Wsoe[3:] - Wex[3:])) < 1e-12 * abs(Wex[0])
+
+
+# ------------------------------------------------------------------ P2
+@pytest.mark.parametrize("alpha", [0.5, 0.8])
+def test_zero_flow_mittag_leffler(alpha):
+    Wi, T = 1.0, 1.0
+    sig0 = np.array([[1.0], [-0.4], [0.7]])
+
+    def closed(t):
+        if alpha == 0.5:
+            return scipy.special.erfcx(math.sqrt(t) / Wi)
+        return special.mittag_leffler(alpha, -t ** alpha / Wi)
+
+    errs = []
+    for steps in (100, 200, 400):
+        dt = T / steps
+        mu, w = soe.soe_expquad(alpha, dt * 1e-14, 10 * T, 700, tail=1e-14)
+        o = orc.Oracle(point_problem(2, alpha, Wi, 0.5, dt, mu, w), sig0)
+        sT = o.run(steps, np.zeros((4, 1)))
+        ratio = sT[:, 0] / sig0[:, 0]
+        assert np.allclose(ratio, ratio[0], rtol=1e-12)          # every component decays alike
+        errs.append(abs(ratio[0] - closed(T)))
+    # zero-past BDF2 with sigma0 != 0: first order at fixed t
+    assert errs[0] < 2e-3
+    for a, b in zip(errs, errs[1:]):
+        assert a / b > 1.8
+
+
+# ------------------------------------------------------------------ P4
+def test_alpha1_exponential_relaxation():
+    # Oldroyd-B relaxation exp(-t/Wi).  The scheme starts BDF2 with a zero past
+    # (sigma^{-1} = sigma^0): sigma - sigma0 is continued by zero for t <= 0,
+    # which has a kink at t = 0 when sigma0 != 0, so the error is first order
+    # here (second order from rest: P7 with alpha = 1).
+    Wi, T = 0.7, 1.0
+    sig0 = np.array([[1.0], [0.5], [-0.2], [0.1], [0.3], [-0.6]])
+    errs = []
+    for steps in (50, 100, 200):
+        o = orc.Oracle(point_problem(3, 1.0, Wi, 0.5, T / steps), sig0)
+        sT = o.run(steps, np.zeros((9, 1)))
+        errs.append(np.max(np.abs(sT[:, 0] - sig0[:, 0] * math.exp(-T / Wi))))
+    assert errs[0] < 5e-3
+    for a, b in zip(errs, errs[1:]):
+        assert 1.8 < a / b < 2.2
+
+
+def test_alpha1_lemma_gaussian_steady_state():
+    # symmetric trace-free D with I - 2 Wi D positive definite
+    D = np.array([[0.2, 0.1, 0.0], [0.1, -0.05, 0.08], [0.0, 0.08, -0.15]])
+    Wi, beta = 1.2, 0.3
+    G = (1 - beta) / Wi
+    ss = G * (np.linalg.inv(np.eye(3) - 2 * Wi * D) - np.eye(3))
+    o = orc.Oracle(point_problem(3, 1.0, Wi, beta, 0.05))
+    sT = o.run(4000, D.reshape(9, 1))
+    assert np.allclose(sT[:, 0], pack(ss), rtol=1e-9, atol=1e-12)
+
+
+def test_alpha1_lyapunov_steady_state_general_kappa():
+    k = np.array([[0.1, 0.4], [-0.3, -0.2]])
+    Wi, beta = 0.8, 0.6
+    G = (1 - beta) / Wi
+    I = np.eye(2)
+    L = np.kron(k, I) + np.kron(I, k) - np.eye(4) / Wi
+    ss = np.linalg.solve(L, -G * (k + k.T).ravel()).reshape(2, 2)
+    o = orc.Oracle(point_problem(2, 1.0, Wi, beta, 0.05))
+    sT = o.run(4000, k.reshape(4, 1))
+    assert np.allclose(sT[:, 0], pack(ss), rtol=1e-9, atol=1e-12)
+
+
+# ------------------------------------------------------------------ P5
+@pytest.mark.parametrize("dim", [2, 3])
+def test_full_tensor_symmetric_and_equal_to_packed(dim):
+    rng = np.random.default_rng(11)
+    n = (5, 4) if dim == 2 else (3, 4, 5)
+    alpha, dt, steps = 0.6, 1e-3, 12
+    mu, w = soe.soe_nnls(alpha, dt, steps * dt, 6)
+    N = int(np.prod(n))
+    kap = rng.normal(size=(dim * dim, N))
+    u = rng.normal(size=(dim, N)) * 0.5
+    sig0 = inputs.random_stress(dim, n, seed=3)
+    base = dict(dim=dim, n=n, alpha=alpha, Wi=1.1, beta=0.5, dt=dt, mu=mu, w=w, transport=True, eps=0.05)
+    packed = orc.forward(orc.Problem(**base), sig0, kap, u, steps)
+    full0 = np.stack([np.stack([unpack(sig0[:, p], dim) for p in range(N)])[:, i, j]
+                      for i in range(dim) for j in range(dim)])
+    full = orc.forward(orc.Problem(full=True, **base), full0, kap, u, steps)
+    F = full.reshape(dim, dim, N)
+    assert np.allclose(F, F.transpose(1, 0, 2), rtol=0, atol=1e-13 * np.max(np.abs(F)))
+    pairs = PACK2 if dim == 2 else PACK3
+    for c, (i, j) in enumerate(pairs):
+        assert np.allclose(packed[c], F[i, j], rtol=1e-12, atol=1e-13 * np.max(np.abs(F)))
+
+
+# ------------------------------------------------------------------ P6
+def test_homogeneous_fields_give_uniform_stress():
+    n = (6, 5, 4)
+    alpha, dt = 0.6, 2e-4
+    mu, w = soe.soe_nnls(alpha, dt, 0.01, 8)
+    km = np.array([[0.2, 1.0, 0.0], [0.3, -0.1, 0.4], [0.0, 0.2, -0.1]])
+    prob = orc.Problem(dim=3, n=n, alpha=alpha, Wi=2.0, beta=0.9, dt=dt, mu=mu, w=w, transport=True, eps=0.01)
+    s = orc.forward(prob, None, inputs.uniform_kappa(3, n, km), inputs.uniform_velocity(3, n, [0.3, -1.2, 0.5]), 20)
+    assert np.all(s == s[:, :1])
+    assert np.max(np.abs(s)) > 0
+
+
+# ------------------------------------------------------------------ P7
+@pytest.mark.parametrize("alpha", [0.3, 0.6, 1.0])
+def test_second_order_from_rest_every_alpha(alpha):
+    T = 1.0
+    if alpha < 1:
+        mu, w = soe.soe_expquad(alpha, 1e-9, 10 * T, 300, tail=1e-12)
+    else:
+        mu = w = None
+    k0 = np.array([[0.3, 1.0, 0.2], [-0.4, -0.1, 0.5], [0.1, 0.2, -0.2]])
+    res = {}
+    for steps in (50, 100, 200, 1600):
+        dt = T / steps
+        o = orc.Oracle(point_problem(3, alpha, 1.5, 0.5, dt, mu, w))
+        res[steps] = o.run(steps, lambda n, dt=dt: (inputs.ramp(n * dt) * k0).reshape(9, 1))
+    e = [np.max(np.abs(res[s] - res[1600])) for s in (50, 100, 200)]
+    for a, b in zip(e, e[1:]):
+        assert 3.6 < a / b < 4.6
+
+
+# ------------------------------------------------------------------ P8
+def test_single_fourier_mode_transport():
+    alpha, Wi, T, ux = 0.6, 1.0, 0.2, 0.8
+    n = (128, 1)
+    kx = 2
+    dt = 2.5e-4
+    steps = int(round(T / dt))
+    mu, w = soe.soe_expquad(alpha, dt * 1e-14, 10 * T, 700, tail=1e-14)
+    x = np.arange(n[0]) * (2 * np.pi / n[0])
+    sig0 = np.stack([np.cos(kx * x), 0.5 * np.cos(kx * x), -np.cos(kx * x)])
+    prob = orc.Problem(dim=2, n=n, alpha=alpha, Wi=Wi, beta=0.5, dt=dt, mu=mu, w=w, transport=True)
+    sT = orc.forward(prob, sig0, np.zeros((4, n[0])), inputs.uniform_velocity(2, n, [ux, 0.0]), steps)
+    y = special.mittag_leffler(alpha, -(1.0 / Wi + 1j * kx * ux) * T ** alpha)
+    exact = np.real(y * np.exp(1j * kx * x))
+    assert np.max(np.abs(sT[0] - exact)) < 3e-3
+    assert np.max(np.abs(sT[2] + exact)) < 3e-3
+    # the decay itself is large compared with the tolerance
+    assert np.max(np.abs(exact - np.cos(kx * x))) > 0.2
+
+
+# ------------------------------------------------------------------ P9
+def test_affine_in_sigma0_and_G():
+    rng = np.random.default_rng(5)
+    n = (6, 7)
+    alpha, dt, steps = 0.4, 1e-3, 15
+    mu, w = soe.soe_nnls(alpha, dt, steps * dt, 6)
+    N = 42
+    kap = rng.normal(size=(4, N))
+    u = rng.normal(size=(2, N)) * 0.3
+    base = dict(dim=2, n=n, alpha=alpha, Wi=1.0, dt=dt, mu=mu, w=w, transport=True)
+    s_a = inputs.random_stress(2, n, 1)
+    s_b = inputs.random_stress(2, n, 2)
+    f = lambda s0, beta: orc.forward(orc.Problem(beta=beta, **base), s0, kap, u, steps)
+    lhs = f(s_a + 2.0 * s_b, 0.5)
+    rhs = f(s_a, 0.5) + 2.0 * (f(s_b, 0.5) - f(None, 0.5))
+    assert np.allclose(lhs, rhs, rtol=1e-11, atol=1e-12)
+    # G = (1 - beta)/Wi enters linearly: beta = 0.2, 0.5, 0.8 are equally spaced in G
+    assert np.allclose(f(s_a, 0.2) - f(s_a, 0.5), f(s_a, 0.5) - f(s_a, 0.8), rtol=1e-10, atol=1e-12)
+
+
+# ------------------------------------------------------------------ adjoint
+@pytest.mark.parametrize("dim,transport,alpha", [(2, True, 0.5), (3, False, 0.7), (2, False, 1.0)])
+def test_reference_adjoint_matches_finite_differences(dim, transport, alpha):
+    rng = np.random.default_rng(21)
+    n = (5, 4) if dim == 2 else (3, 2, 2)
+    N = int(np.prod(n))
+    dt, steps = 2e-3, 12
+    if alpha < 1:
+        mu, w = soe.soe_nnls(alpha, dt, steps * dt, 6)
+    else:
+        mu, w = np.zeros(0), np.zeros(0)
+    kap = rng.normal(size=(dim * dim, N))
+    u = rng.normal(size=(dim, N)) * 0.5 if transport else None
+    sig0 = inputs.random_stress(dim, n, 9)
+    nc = sig0.shape[0]
+    target = rng.normal(size=(nc, N))
+
+    def J(Wi, beta, s0, k):
+        p = orc.Problem(dim=dim, n=n, alpha=alpha, Wi=Wi, beta=beta, dt=dt, mu=mu, w=w,
+                        transport=transport, eps=0.02 if transport else 0.0)
+        sT = orc.forward(p, s0, k, u, steps)
+        return float(np.sum((sT - target) ** 2))
+
+    Wi, beta = 1.3, 0.4
+    p = orc.Problem(dim=dim, n=n, alpha=alpha, Wi=Wi, beta=beta, dt=dt, mu=mu, w=w,
+                    transport=transport, eps=0.02 if transport else 0.0)
+    sT = orc.forward(p, sig0, kap, u, steps)
+    g = orc.gradients(p, sig0, kap, u, steps, 2.0 * (sT - target))
+    h = 1e-6
+
+    def fd(fun, x):
+        return (fun(x + h) - fun(x - h)) / (2 * h)
+
+    def close(a, b):
+        return abs(a - b) <= 1e-6 * max(abs(a), abs(b), 1e-3)
+
+    assert close(g["Wi"], fd(lambda x: J(x, beta, sig0, kap), Wi))
+    assert close(g["beta"], fd(lambda x: J(Wi, x, sig0, kap), beta))
+    for (c, q) in [(0, 0), (nc - 1, N - 1), (1, N // 2)]:
+        def fs(x, c=c, q=q):
+            s = sig0.copy(); s[c, q] = x
+            return J(Wi, beta, s, kap)
+        assert close(g["sigma0"][c, q], fd(fs, sig0[c, q]))
+    for (c, q) in [(0, 1), (dim * dim - 1, N - 2), (1, 3)]:
+        def fk(x, c=c, q=q):
+            k = kap.copy(); k[c, q] = x
+            return J(Wi, beta, sig0, k)
+        assert close(g["kappa"][c, q], fd(fk, kap[c, q]))

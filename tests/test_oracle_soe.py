@@ -1,0 +1,139 @@
+"""Pins of the oracle's SOE kernels and special functions (no GPU).
+
+P1: the sum of exponentials against the closed-form Caputo kernel
+t^-alpha / Gamma(1-alpha) on 400 log points of [dt, T]; two independent
+constructions agree within the sum of their errors.  The paper prints no SOE
+error, so the bounds below are the achieved accuracies (stated, not pinned by
+the paper).
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.special
+
+from oracle import soe, special
+
+# (alpha, dt, T, m, bound on max relative kernel error over [dt, T])
+WORKLOAD_SOES = [
+    (0.5, 1e-3, 1.0, 16, 1e-4),      # 2D 64^2 FP64 case, SOE on [1e-3, 1]
+    (0.3, 5e-4, 0.5, 32, 1e-8),      # 2D 1024^2 cases, 1000 steps
+    (0.5, 5e-4, 0.5, 32, 1e-8),
+    (0.8, 5e-4, 0.5, 32, 1e-8),
+    (0.6, 2e-4, 0.04, 32, 1e-8),     # 3D 256^3, 200 steps
+    (0.2, 2e-4, 0.1, 16, 1e-4),      # 3D 192^3 sweep, 500 steps
+    (0.5, 2e-4, 0.1, 48, 1e-11),
+    (0.9, 2e-4, 0.1, 48, 1e-11),
+]
+
+
+@pytest.mark.parametrize("alpha,dt,T,m,bound", WORKLOAD_SOES)
+def test_nnls_soe_matches_closed_form(alpha, dt, T, m, bound):
+    mu, w = soe.soe_nnls(alpha, dt, T, m)
+    assert len(mu) == m and len(w) == m
+    assert np.all(mu >= 0) and np.all(w > 0)            # completely monotone (Section 2.2)
+    assert soe.max_rel_error(alpha, mu, w, dt, T) <= bound
+
+
+def test_aaa_soe_paper_recipe_small_m():
+    # Section 2.2: AAA on s^alpha, divided by s -> no Dirac term, positive terms
+    alpha, dt, T, m = 0.5, 1e-3, 1.0, 16
+    mu, w = soe.soe_aaa(alpha, dt, T, m)
+    assert len(mu) == m
+    assert np.all(mu >= 0) and np.all(w >= 0)
+    e_aaa = soe.max_rel_error(alpha, mu, w, dt, T)
+    assert e_aaa < 5e-4
+    # independent construction: cross-check within the sum of the two errors
+    mu2, w2 = soe.soe_nnls(alpha, dt, T, m)
+    e_nnls = soe.max_rel_error(alpha, mu2, w2, dt, T)
+    t = np.logspace(math.log10(dt), math.log10(T), 400)
+    k = soe.kernel_exact(alpha, t)
+    diff = np.max(np.abs(soe.soe_eval(mu, w, t) - soe.soe_eval(mu2, w2, t)) / k)
+    assert diff <= (e_aaa + e_nnls) * (1 + 1e-9)
+
+
+def test_aaa_laplace_identity():
+    # the SOE's Laplace transform sum w/(s+mu) approximates s^(alpha-1)
+    alpha, dt, T, m = 0.5, 1e-3, 1.0, 16
+    mu, w = soe.soe_aaa(alpha, dt, T, m)
+    s = np.logspace(0, 3, 50)
+    K = (1.0 / (s[:, None] + mu[None, :])) @ w
+    assert np.max(np.abs(K / s ** (alpha - 1) - 1)) < 1e-4
+
+
+def test_trapezoid_soe_converges_and_agrees():
+    alpha, dt, T = 0.6, 2e-4, 0.04
+    mu, w = soe.soe_expquad(alpha, dt, T, 400, tail=1e-13)
+    e_tr = soe.max_rel_error(alpha, mu, w, dt, T)
+    assert e_tr < 1e-9
+    mu2, w2 = soe.soe_nnls(alpha, dt, T, 32)
+    e2 = soe.max_rel_error(alpha, mu2, w2, dt, T)
+    t = np.logspace(math.log10(dt), math.log10(T), 400)
+    k = soe.kernel_exact(alpha, t)
+    diff = np.max(np.abs(soe.soe_eval(mu, w, t) - soe.soe_eval(mu2, w2, t)) / k)
+    assert diff <= (e_tr + e2) * (1 + 1e-9)
+
+
+def test_kernel_exact_gamma_identity():
+    # t^-alpha/Gamma(1-alpha) integrates to t^(1-alpha)/Gamma(2-alpha); the
+    # algebraic end-point weight of QUADPACK carries the singularity
+    import scipy.integrate
+    alpha, t = 0.37, 0.8
+    g = scipy.special.gamma(1 - alpha)
+    val, _ = scipy.integrate.quad(lambda s: 1.0 / g, 0.0, t, weight="alg", wvar=(-alpha, 0.0))
+    ref = t ** (1 - alpha) / scipy.special.gamma(2 - alpha)
+    assert abs(val - ref) < 1e-12
+    # and the closed form itself at a point
+    assert abs(soe.kernel_exact(alpha, t) - t ** -alpha / g) < 1e-15
+
+
+# --------------------------- special functions ---------------------------
+
+def test_mittag_leffler_special_cases():
+    x = np.linspace(0.0, 2.0, 11)
+    # E_1(z) = exp(z)
+    assert np.allclose(special.mittag_leffler(1.0, -x), np.exp(-x), rtol=1e-13, atol=1e-15)
+    # E_{1/2}(-x) = exp(x^2) erfc(x)
+    assert np.allclose(special.mittag_leffler(0.5, -x), scipy.special.erfcx(x), rtol=1e-12, atol=1e-14)
+    # E_2(-x^2) = cos(x)
+    assert np.allclose(special.mittag_leffler(2.0, -x ** 2), np.cos(x), rtol=1e-12, atol=1e-12)
+    # complex argument: E_1(i y) = exp(i y)
+    y = np.linspace(-2, 2, 9)
+    assert np.allclose(special.mittag_leffler(1.0, 1j * y), np.exp(1j * y), rtol=1e-13, atol=1e-14)
+
+
+def test_mittag_leffler_against_mpmath():
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    # the series cancels badly when alpha is small and |z| large; the oracle
+    # only evaluates it where its largest term stays O(10)
+    for alpha, z in [(0.3, -0.2), (0.3, -1.0), (0.6, -0.2), (0.6, -1.0), (0.6, -2.5),
+                     (0.9, -0.2), (0.9, -1.0), (0.9, -2.5)]:
+        ref = mpmath.nsum(lambda k: mpmath.mpf(z) ** k / mpmath.gamma(alpha * k + 1), [0, mpmath.inf])
+        assert abs(special.mittag_leffler(alpha, z) - float(ref)) < 1e-13
+
+
+def test_cq_power_weights():
+    dt = 1e-2
+    # alpha = 1: the BDF2 coefficients themselves
+    W1 = special.cq_weights_power(1.0, dt, 6)
+    assert np.allclose(W1, [1.5, -2.0, 0.5, 0, 0, 0, 0], atol=1e-15)
+    # alpha = 1/2: the series squared equals dt * delta(zeta)
+    Wh = special.cq_weights_power(0.5, dt, 40)
+    sq = np.convolve(Wh, Wh)[:41]
+    ref = np.zeros(41)
+    ref[:3] = np.array([1.5, -2.0, 0.5]) * dt
+    assert np.allclose(sq, ref, atol=1e-15)
+
+
+def test_cq_soe_weights():
+    dt = 1e-2
+    # one term with mu = 0 and weight w: delta * w dt / delta = w dt
+    W = special.cq_weights_soe([0.0], [2.0], dt, 10)
+    assert np.allclose(W, np.r_[2.0 * dt, np.zeros(10)], atol=1e-16)
+    # mu > 0: delta(1) = 0 so the weights sum to zero (the derivative of a constant)
+    W = special.cq_weights_soe([3.0, 40.0], [1.0, 0.5], dt, 4000)
+    assert abs(W.sum()) < 1e-12
+    # first weight is eta = b0 sum_j w_j dt / (b0 + mu_j dt)
+    eta = sum(1.5 * w * dt / (1.5 + m * dt) for m, w in [(3.0, 1.0), (40.0, 0.5)])
+    assert abs(W[0] - eta) < 1e-16
