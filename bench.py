@@ -1,0 +1,328 @@
+"""Benchmark of the fractional polymer-stress step on GB300.
+
+Workload (one step = one tfs_step over the whole grid: extrapolated velocity
+gradient, upwind transport stencil, compensated mode history sum, FP64-accurate
+per-point 6x6 solve, push-forward of all modes):
+    3D periodic 256^3, 6 stress components, FP32 modes, alpha = 0.6, Wi = 2,
+    beta = 0.9, m = 32, dt = 2e-4, seeded divergence-free k^-5/3 velocity
+    |k| <= 24 at unit RMS, transport on.
+Metric: G point-mode updates/s = N * m * steps / time, plus the fraction of
+the HBM roofline of the step kernel.  The per-step working set (~41 GB) is far
+larger than L2, so no L2 flush is needed between steps.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs its own 256^3 problem (weak scaling,
+no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "G point-mode updates/s per fractional stress step and % of HBM peak; adjoint/forward ratio"
+UNIT = "G point-mode updates/s"
+
+WORKLOAD = dict(name="3D periodic 256^3 fractional stress step, m=32 SOE modes, FP32 modes + compensated sum",
+                dim=3, n=(256, 256, 256), alpha=0.6, Wi=2.0, beta=0.9, m=32, dt=2e-4, horizon_steps=200,
+                kmax=24, seed=3)
+
+
+def algorithmic_bytes_per_point(dim: int, m: int, elem: int, sigma0_nonzero: bool = False) -> int:
+    """3 words per (mode, component) + 3 nc stress words + (2 d^2 + d) input
+    words (+ nc for a nonzero initial stress)."""
+    nc = 3 if dim == 2 else 6
+    b = 3 * m * nc * elem + 3 * nc * elem + (2 * dim * dim + dim) * elem
+    if sigma0_nonzero:
+        b += nc * elem
+    return b
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id:
+                cmd.insert(1, f"--id={self.gpu_id}")
+            self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip() == "Active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(steps_hint: int = 3, budget_s: float = 15.0):
+    """The FP64 C oracle, as it stands, on a bounded sample of the workload:
+    a 64^3 periodic sub-problem with the same parameters and velocity recipe."""
+    import numpy as np
+
+    from oracle import orc
+    from oracle import soe as osoe
+    from paper_2411_17294_gb300 import inputs
+
+    W = WORKLOAD
+    n = (64, 64, 64)
+    dt = W["dt"]
+    mu, w = osoe.soe_build(W["alpha"], dt, W["horizon_steps"] * dt, W["m"])
+    u, kap = inputs.spectral_velocity(3, n, W["kmax"], W["seed"])
+    prob = orc.Problem(dim=3, n=n, alpha=W["alpha"], Wi=W["Wi"], beta=W["beta"], dt=dt, mu=mu, w=w,
+                       transport=True)
+    o = orc.Oracle(prob)
+    o.step(kap, kap, u)                       # warm-up
+    t0 = time.perf_counter()
+    o.step(kap, kap, u)
+    one = time.perf_counter() - t0
+    steps = max(steps_hint, int(budget_s / max(one, 1e-3)))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.step(kap, kap, u)
+    el = time.perf_counter() - t0
+    N = int(np.prod(n))
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": N * W["m"] * steps / el / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"64^3 sub-problem, same parameters and velocity recipe, {steps} steps after 1 warm-up, "
+                      f"FP64 C oracle with OpenMP", "seconds": el}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    res = cpu_baseline(steps_hint=max(args.steps, 1), budget_s=20.0)
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "sample": res["sample"]},
+            "cpu_baseline": {"value": res["value"], "unit": UNIT, "cores": res["cores"], "kind": "oracle",
+                             "sample": res["sample"]},
+            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32plain"])
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2411_17294_gb300 import build as tbuild
+    from paper_2411_17294_gb300 import inputs, soe, tfs
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        tbuild.build()
+    if dist is not None:
+        dist.barrier()
+
+    W = WORKLOAD
+    prec = {"fp32": tfs.TFS_FP32, "fp64": tfs.TFS_FP64, "fp32plain": tfs.TFS_FP32_PLAIN}[args.precision]
+    dt = W["dt"]
+    mu, w = soe.build(W["alpha"], dt, W["horizon_steps"] * dt, W["m"])
+    u64, kap64 = inputs.spectral_velocity(3, W["n"], W["kmax"], W["seed"] + rank, device=dev)
+    s = tfs.Solver(3, W["n"], W["alpha"], W["Wi"], W["beta"], dt, m=W["m"], precision=prec, mu=mu, w=w,
+                   transport=True, device=dev)
+    tdt = s.dtype
+    kap_n = torch.as_tensor(kap64, dtype=tdt, device=dev).contiguous()
+    kap_nm1 = kap_n.clone()          # frozen velocity, but a distinct buffer: both levels are read
+    u = torch.as_tensor(u64, dtype=tdt, device=dev).contiguous()
+    del u64, kap64
+    stream = torch.cuda.Stream(device=dev)
+    N = s.N
+    elem = 8 if prec == tfs.TFS_FP64 else 4
+    bytes_pp = algorithmic_bytes_per_point(3, W["m"], elem)
+    bytes_launch = bytes_pp * N
+
+    with torch.cuda.stream(stream):
+        s.set_state(None, stream=stream)
+        for _ in range(args.warmup):
+            s.step(kap_n, kap_nm1, u, stream=stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+
+    gpu_uuid = None
+    try:
+        gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(gpu_uuid)
+    sampler.start()
+    time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for k in range(args.steps):
+            s.step(kap_n, kap_nm1, u, stream=stream)
+            ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launch_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    flags = s.status()
+    t_max = total_ms
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    ms_per_step = t_max / args.steps
+    value = world * N * W["m"] * args.steps / (t_max * 1e-3) / 1e9
+    avg_launch_s = statistics.mean(launch_ms) * 1e-3
+    achieved = bytes_launch / avg_launch_s / 1e9
+    peak, peak_kind = read_peaks()
+
+    # ---- end to end through the C ABI with host buffers ----------------------
+    e2e = None
+    if args.e2e_steps > 0:
+        h_kn = torch.empty(kap_n.shape, dtype=tdt, pin_memory=True)
+        h_knm1 = torch.empty(kap_n.shape, dtype=tdt, pin_memory=True)
+        h_u = torch.empty(u.shape, dtype=tdt, pin_memory=True)
+        h_kn.copy_(kap_n.cpu()); h_knm1.copy_(kap_nm1.cpu()); h_u.copy_(u.cpu())
+        h_sig = torch.empty((s.nc, N), dtype=tdt, pin_memory=True)
+        d_kn = torch.empty_like(kap_n); d_knm1 = torch.empty_like(kap_n); d_u = torch.empty_like(u)
+        d_sig = torch.empty((s.nc, N), dtype=tdt, device=dev)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(args.e2e_steps):
+                d_kn.copy_(h_kn, non_blocking=True)
+                d_knm1.copy_(h_knm1, non_blocking=True)
+                d_u.copy_(h_u, non_blocking=True)
+                s.step(d_kn, d_knm1, d_u, stream=stream)
+                check = s.lib.tfs_get_stress(s.h, d_sig.data_ptr(), stream.cuda_stream)
+                if check != 0:
+                    raise RuntimeError("tfs_get_stress failed")
+                h_sig.copy_(d_sig, non_blocking=True)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        bi = (h_kn.numel() + h_knm1.numel() + h_u.numel()) * elem
+        bo = h_sig.numel() * elem
+        e2e = {"value": world * N * W["m"] * args.e2e_steps / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            cpu = cpu_baseline()
+            cpu.pop("seconds", None)
+        except Exception as exc:  # pragma: no cover - reported, not fatal
+            cpu = {"error": str(exc)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {tfs.TFS_FP64: "f64", tfs.TFS_FP32: "f32", tfs.TFS_FP32_PLAIN: "f32"}[prec],
+            "data": "synthetic",
+            "config": {"workload": W["name"], "grid": list(W["n"]), "m": W["m"], "alpha": W["alpha"],
+                       "Wi": W["Wi"], "beta": W["beta"], "dt": W["dt"], "transport": True,
+                       "precision": args.precision, "l2": "per-step working set ~41 GB >> 129 MB L2, no flush",
+                       "points_per_gpu": N},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_point": bytes_pp, "algorithmic_bytes_per_launch": bytes_launch,
+                         "avg_launch_ms": avg_launch_s * 1e3},
+            "gpu_launches": args.steps,
+            "device_flags": flags,
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * tfs.h -- C ABI of the time-fractional polymer-stress step (libtfs.so).
+ *
+ * The library advances the polymer extra stress of the macroscopic model of
+ * Beddrich, Lunowa & Wohlmuth (arXiv 2411.17294) on a periodic grid, one time
+ * step per call, on one CUDA GPU (sm_103a).  The law it integrates is the
+ * stress form of the macroscopic Fokker-Planck system of Section 3.4
+ * (eq. macroscopic_fokker_planck, coupling eqs. mm_contribution_order0 and
+ * mm_coupling_order2, stress eq. mm_ExtraStress):
+ *
+ *   D^alpha_C (sigma - sigma0) = kappa sigma + sigma kappa^T - sigma / Wi
+ *                                + G (kappa + kappa^T) t^(alpha-1)/Gamma(alpha)
+ *                                - u . grad sigma + eps Lap sigma,
+ *   G = (1 - beta) / (Wi Re),   kappa_ij = d u_i / d x_j,
+ *
+ * with the Caputo kernel t^-alpha/Gamma(1-alpha) compressed into a sum of m
+ * exponentials (Section 2.2, eq. tf_approximate_kernel); every grid point
+ * carries m mode tensors advanced by BDF2 (Section 4.1, eq. BDF_Phi_k_n+1) and
+ * the stress solves, per point, the small system obtained by inserting that
+ * push-forward into the mode sum (the eta, eta_k form of eq. FP_discrete):
+ *
+ *   (eta + dt/Wi) sigma^{n+1} - dt (kappa* sigma^{n+1} + sigma^{n+1} kappa*^T)
+ *     = eta sigma0 - sum_j eta_j (b1 sigma_j^n + b2 sigma_j^{n-1})
+ *       + dt G (kappa* + kappa*^T) g(t_{n+1}) - dt (u . grad_h - eps Lap_h) E,
+ *   kappa* = 2 kappa^n - kappa^{n-1},  E = 2 sigma^n - sigma^{n-1}
+ *   (extrapolation of eq. BDF_and_extrapolation).
+ * alpha = 1 is plain BDF2 (Oldroyd-B) with no modes.
+ *
+ * Conventions
+ *   Grid: periodic, n[0] x n[1] (x n[2]) points, x fastest: p = x + n0 (y + n1 z).
+ *   Packed stress components nc = 3 in 2D (xx, xy, yy), 6 in 3D
+ *   (xx, yy, zz, yz, xz, xy).  Stress fields are [nc][N] structure-of-arrays.
+ *   Velocity gradient [d*d][N] with component i*d + j = d u_i / d x_j;
+ *   velocity [d][N].
+ *   Element type of every field pointer: double for TFS_FP64, float for
+ *   TFS_FP32 / TFS_FP32_PLAIN.  Gradients returned by tfs_backward are double.
+ *   All field pointers are device pointers owned by the caller; the library
+ *   allocates no device memory: its state lives in a caller-bound workspace.
+ *   Streams: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Calls that take a stream only enqueue work on it; they do not synchronise.
+ *
+ * Errors: every call returns a TFS_* status (0 = TFS_OK).  Kernel-side
+ * conditions (non-finite result, near-singular point system, Courant limit
+ * exceeded) are latched in a device word and read by tfs_status.
+ */
+#ifndef TFS_H
+#define TFS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tfs_ctx* tfs_handle;
+
+/* status codes */
+enum {
+    TFS_OK = 0,
+    TFS_ERR_ARG = 1,          /* invalid argument (size, range, NULL, alignment) */
+    TFS_ERR_NOSOE = 2,        /* alpha < 1 and no SOE table set */
+    TFS_ERR_UNSTABLE = 3,     /* declared velocity bound exceeds the explicit-transport limit */
+    TFS_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+    TFS_ERR_STATE = 5,        /* call out of order (no state set, adjoint not begun, ...) */
+    TFS_ERR_NOWORKSPACE = 6,  /* no (or too small a) workspace bound */
+    TFS_ERR_FORMAT = 7        /* checkpoint buffer does not match this handle */
+};
+
+/* precision modes */
+enum {
+    TFS_FP64 = 0,             /* everything in double */
+    TFS_FP32 = 1,             /* float storage, compensated mode sum, FP64-accurate point solve */
+    TFS_FP32_PLAIN = 2        /* float storage, plain float mode sum (precision studies) */
+};
+
+/* tfs_set_param keys */
+enum {
+    TFS_PARAM_RE = 0,         /* Reynolds number, default 1 */
+    TFS_PARAM_EPS = 1,        /* centre-of-mass diffusion eps >= 0, default 0 */
+    TFS_PARAM_STENCIL = 2,    /* TFS_STENCIL_*, default upwind3 */
+    TFS_PARAM_TRANSPORT = 3,  /* 0: pointwise law (u ignored); 1: transport on (default 1) */
+    TFS_PARAM_UMAX = 4        /* declared bound on |u|_inf; checked against the Courant limit */
+};
+
+enum { TFS_STENCIL_UPWIND3 = 0, TFS_STENCIL_CENTRAL2 = 1 };
+
+/* device status flags (tfs_status) */
+enum {
+    TFS_FLAG_NONFINITE = 1u,  /* a new stress value was NaN or Inf */
+    TFS_FLAG_SINGULAR = 2u,   /* a point system had a pivot below 1e-300 / relative 1e-14 */
+    TFS_FLAG_COURANT = 4u     /* a point exceeded the explicit-transport Courant limit */
+};
+
+typedef struct {
+    int dim;        /* 2 or 3 */
+    int n[3];       /* points per axis (n[2] ignored in 2D); each >= 1 */
+    double L[3];    /* box lengths > 0 */
+} tfs_grid;
+
+/* Create a handle.  alpha in (0, 1]; Wi > 0; beta in [0, 1); dt > 0;
+   0 <= m <= 64 (m = 0 required when alpha == 1, m >= 1 otherwise);
+   precision one of TFS_FP64, TFS_FP32, TFS_FP32_PLAIN.  No device memory is
+   allocated.  On error *h is set to NULL. */
+int tfs_create(tfs_handle* h, const tfs_grid* grid, double alpha, double Wi, double beta,
+               int m, double dt, int precision);
+
+/* Set an optional parameter (TFS_PARAM_*).  Re > 0, eps >= 0, umax >= 0. */
+int tfs_set_param(tfs_handle h, int key, double value);
+
+/* Copy the SOE table: exponents mu_j >= 0 and weights w_j >= 0 (finite),
+   j < m, approximating t^-alpha/Gamma(1-alpha) by sum_j w_j exp(-mu_j t)
+   (Section 2.2).  Host arrays, copied; m must equal the handle's m.
+   Precomputes c_j = 1/(b0 + mu_j dt), rho_j = w_j dt c_j, eta_j = mu_j dt c_j
+   and eta = b0 sum_j rho_j in FP64. */
+int tfs_set_soe(tfs_handle h, const double* mu, const double* w, int m);
+
+/* Bytes of device workspace the handle needs (stress ring, modes, status). */
+size_t tfs_workspace_bytes(tfs_handle h);
+
+/* Bind caller-owned device memory of at least tfs_workspace_bytes bytes,
+   256-byte aligned.  The library never frees it. */
+int tfs_bind_workspace(tfs_handle h, void* dev_ptr, size_t bytes);
+
+/* Start from rest: sigma^0 = sigma^{-1} = sigma0 (NULL = zero stress), all
+   modes zero, step counter 0, status flags cleared. */
+int tfs_set_state(tfs_handle h, const void* sigma0, void* stream);
+
+/* One step t_n -> t_{n+1}.  grad_u_n = kappa^n, grad_u_nm1 = kappa^{n-1}
+   (NULL = same as grad_u_n); u = velocity [d][N] (NULL allowed when transport
+   is off).  Enqueues one kernel launch. */
+int tfs_step(tfs_handle h, const void* grad_u_n, const void* grad_u_nm1, const void* u, void* stream);
+
+/* Copy the current stress sigma^n to out [nc][N] (device). */
+int tfs_get_stress(tfs_handle h, void* out, void* stream);
+
+/* Current step index n (number of completed steps since tfs_set_state). */
+long tfs_step_index(tfs_handle h);
+
+/* Checkpoints: a device buffer holding the full state (header, stress at
+   levels n and n-1, modes at levels n and n-1). */
+size_t tfs_checkpoint_bytes(tfs_handle h);
+int tfs_save(tfs_handle h, void* dst, void* stream);
+/* Restore a checkpoint written by tfs_save on a handle of the same shape and
+   precision (checked: TFS_ERR_FORMAT).  Synchronises `stream` to read the
+   header. */
+int tfs_load(tfs_handle h, const void* src, void* stream);
+
+/* Adjoint workspace for checkpoint segments of `segment_steps` steps. */
+size_t tfs_adjoint_workspace_bytes(tfs_handle h, int segment_steps);
+int tfs_bind_adjoint_workspace(tfs_handle h, void* dev_ptr, size_t bytes);
+
+/* Reverse-mode derivative of J(sigma^T) for a run of `steps` steps from the
+   state set by tfs_set_state, with a frozen velocity gradient grad_u [d*d][N]
+   (and velocity u when transport is on), given dJ/dsigma(T) [nc][N] (element
+   type of the handle).  checkpoints[k] must hold tfs_save of step k*K for
+   k = 0 .. ceil(steps/K)-1; each segment is recomputed from its checkpoint
+   and then differentiated backwards.  Outputs (device, double): dJ_dsigma0
+   [nc][N], dJ_dgrad_u [d*d][N]; host doubles *dJ_dWi, *dJ_dbeta.  Synchronises
+   `stream` at the end to return the two scalars.  The handle's forward state
+   afterwards is that of the last recomputed segment. */
+int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* checkpoints, int K,
+                 int steps, const void* grad_u, const void* u, double* dJ_dsigma0,
+                 double* dJ_dgrad_u, double* dJ_dWi, double* dJ_dbeta, void* stream);
+
+/* Read (and keep) the latched device flags; synchronises the last stream
+   the handle used.  Returns TFS_OK or TFS_ERR_CUDA. */
+int tfs_status(tfs_handle h, unsigned* device_flags);
+
+/* Static description of a status code. */
+const char* tfs_strerror(int code);
+
+/* Free the handle (host memory only). */
+int tfs_destroy(tfs_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TFS_H */

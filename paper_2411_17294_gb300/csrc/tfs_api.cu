@@ -1,0 +1,667 @@
+// Host side of libtfs: the C ABI declared in include/tfs.h.
+//
+// The handle keeps the problem description, the FP64 SOE constants and the
+// layout of the caller-bound workspace; the step itself is one kernel launch
+// (tfs_forward.cu).  No device memory is allocated here.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "../../include/tfs.h"
+#include "tfs_internal.h"
+
+using namespace tfs;
+
+namespace {
+
+constexpr uint64_t kMagic = 0x3153464154434b50ull;   // checkpoint tag
+constexpr uint64_t kVersion = 1;
+constexpr size_t kAlign = 256;
+constexpr size_t kHeaderBytes = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+}  // namespace
+
+struct tfs_ctx {
+    int dim = 2;
+    long long n[3] = {1, 1, 1};
+    double L[3] = {1, 1, 1};
+    long long N = 0;
+    int nc = 3;
+    double alpha = 1, Wi = 1, beta = 0, Re = 1, eps = 0, dt = 1;
+    int m = 0;
+    int precision = TFS_FP64;
+    int stencil = TFS_STENCIL_UPWIND3;
+    int transport = 1;
+    double umax = -1.0;            // declared velocity bound (< 0: none)
+    // SOE
+    bool soe_set = false;
+    std::vector<double> mu, w;
+    ModeConstsD mcd{};
+    ModeConstsF mcf{};
+    double eta = 0.0;
+    // workspace
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    unsigned* flags = nullptr;
+    char* sigma0 = nullptr;        // copy of the initial stress
+    char* sig[3] = {nullptr, nullptr, nullptr};
+    char* modes[2] = {nullptr, nullptr};
+    int cur_sig = 0, prev_sig = 1; // ring slots of levels n and n-1
+    int cur_mode = 0;              // ring slot of modes level n (n-1 in the other)
+    bool sigma0_zero = true;
+    bool state_set = false;
+    long long step = 0;
+    cudaStream_t last_stream = nullptr;
+    // adjoint workspace
+    char* aws = nullptr;
+    size_t aws_bytes = 0;
+    int seg_capacity = 0;
+
+    size_t es() const { return precision == TFS_FP64 ? 8 : 4; }
+    bool is_double() const { return precision == TFS_FP64; }
+    bool classic() const { return alpha == 1.0; }
+    size_t field_bytes() const { return (size_t)nc * (size_t)N * es(); }
+    size_t modes_bytes() const { return (size_t)m * field_bytes(); }
+    int third_sig() const { return 3 - cur_sig - prev_sig; }
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? TFS_OK : TFS_ERR_CUDA; }
+
+double g_alpha(const tfs_ctx* h, long long step_index) {
+    if (h->classic()) return 1.0;
+    const double t = (double)(step_index + 1) * h->dt;
+    return std::pow(t, h->alpha - 1.0) / std::tgamma(h->alpha);
+}
+
+// Courant number of the explicit transport per unit velocity/grid-spacing:
+// C = dt^alpha / b0^alpha * sum_a |u_a| / h_a  (the fractional derivative
+// weights the transport like a time step dt^alpha / b0^alpha).
+double courant_coef(const tfs_ctx* h) { return std::pow(h->dt / kB0, h->alpha); }
+
+// Explicit-transport Courant limits from the von Neumann analysis of the
+// scheme (upwind3 / central2), see DESIGN notes in the test of the limit.
+double courant_limit(const tfs_ctx* h) { return h->stencil == TFS_STENCIL_CENTRAL2 ? 0.35 : 0.55; }
+
+void layout_forward(tfs_ctx* h, char* base) {
+    char* p = base;
+    h->flags = (unsigned*)p;
+    p += kAlign;
+    h->sigma0 = p;
+    p += align_up(h->field_bytes());
+    for (int i = 0; i < 3; ++i) {
+        h->sig[i] = p;
+        p += align_up(h->field_bytes());
+    }
+    for (int i = 0; i < 2; ++i) {
+        h->modes[i] = p;
+        p += align_up(h->modes_bytes());
+    }
+}
+
+size_t forward_bytes(const tfs_ctx* h) {
+    return kAlign + 4 * align_up(h->field_bytes()) + 2 * align_up(h->modes_bytes());
+}
+
+template <typename T>
+void fill_common(const tfs_ctx* h, FwdArgs<T>& a) {
+    a.N = h->N;
+    a.n0 = (int)h->n[0];
+    a.n1 = (int)h->n[1];
+    a.n2 = (int)h->n[2];
+    a.m = h->classic() ? 0 : h->m;
+    a.dt = h->dt;
+    a.eta = h->classic() ? kB0 : h->eta;
+    a.a = a.eta + h->dt / h->Wi;
+    a.G = (1.0 - h->beta) / (h->Wi * h->Re);
+    a.eps = h->eps;
+    for (int i = 0; i < 3; ++i) a.inv_h[i] = (double)h->n[i] / h->L[i];
+    a.courant_coef = (h->transport ? courant_coef(h) : 0.0);
+    a.courant_limit = courant_limit(h);
+    a.flags = h->flags;
+}
+
+LaunchCfg make_cfg(const tfs_ctx* h) {
+    LaunchCfg cfg;
+    cfg.dim = h->dim;
+    cfg.stencil = h->stencil;
+    cfg.transport = h->transport != 0;
+    cfg.classic = h->classic();
+    cfg.compensated = h->precision == TFS_FP32;
+    return cfg;
+}
+
+// One forward step; sig_copy optionally receives sigma^{n+1} as well.
+int do_step(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* sig_copy, cudaStream_t s) {
+    if (!h->ws) return TFS_ERR_NOWORKSPACE;
+    if (!h->state_set) return TFS_ERR_STATE;
+    if (!h->classic() && !h->soe_set) return TFS_ERR_NOSOE;
+    if (!kn) return TFS_ERR_ARG;
+    if (h->transport && !u) return TFS_ERR_ARG;
+    if (!knm1) knm1 = kn;
+    const int nxt = h->third_sig();
+    const int cm = h->cur_mode, pm = 1 - h->cur_mode;
+    cudaError_t e;
+    const LaunchCfg cfg = make_cfg(h);
+    if (h->is_double()) {
+        FwdArgs<double> a{};
+        fill_common(h, a);
+        a.kap_n = (const double*)kn;
+        a.kap_nm1 = (const double*)knm1;
+        a.u = (const double*)u;
+        a.sigma0 = h->sigma0_zero ? nullptr : (const double*)h->sigma0;
+        a.sig_n = (const double*)h->sig[h->cur_sig];
+        a.sig_nm1 = (const double*)h->sig[h->prev_sig];
+        a.sig_np1 = (double*)h->sig[nxt];
+        a.sig_copy = (double*)sig_copy;
+        a.modes_n = (const double*)h->modes[cm];
+        a.modes_nm1 = (double*)h->modes[pm];
+        a.g = g_alpha(h, h->step);
+        a.mc = h->mcd;
+        e = launch_forward_f64(a, cfg, s);
+    } else {
+        FwdArgs<float> a{};
+        fill_common(h, a);
+        a.kap_n = (const float*)kn;
+        a.kap_nm1 = (const float*)knm1;
+        a.u = (const float*)u;
+        a.sigma0 = h->sigma0_zero ? nullptr : (const float*)h->sigma0;
+        a.sig_n = (const float*)h->sig[h->cur_sig];
+        a.sig_nm1 = (const float*)h->sig[h->prev_sig];
+        a.sig_np1 = (float*)h->sig[nxt];
+        a.sig_copy = (float*)sig_copy;
+        a.modes_n = (const float*)h->modes[cm];
+        a.modes_nm1 = (float*)h->modes[pm];
+        a.g = g_alpha(h, h->step);
+        a.mc = h->mcf;
+        e = launch_forward_f32(a, cfg, s);
+    }
+    if (e != cudaSuccess) return TFS_ERR_CUDA;
+    h->prev_sig = h->cur_sig;
+    h->cur_sig = nxt;
+    if (!h->classic()) h->cur_mode = pm;
+    h->step += 1;
+    h->last_stream = s;
+    return TFS_OK;
+}
+
+bool valid_handle(tfs_handle h) { return h != nullptr; }
+
+}  // namespace
+
+extern "C" {
+
+int tfs_create(tfs_handle* out, const tfs_grid* grid, double alpha, double Wi, double beta, int m, double dt,
+               int precision) {
+    if (!out) return TFS_ERR_ARG;
+    *out = nullptr;
+    if (!grid || (grid->dim != 2 && grid->dim != 3)) return TFS_ERR_ARG;
+    if (!(alpha > 0.0 && alpha <= 1.0)) return TFS_ERR_ARG;
+    if (!(Wi > 0.0) || !std::isfinite(Wi)) return TFS_ERR_ARG;
+    if (!(beta >= 0.0 && beta < 1.0)) return TFS_ERR_ARG;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return TFS_ERR_ARG;
+    if (m < 0 || m > kMaxModes) return TFS_ERR_ARG;
+    if (alpha == 1.0 && m != 0) return TFS_ERR_ARG;
+    if (alpha < 1.0 && m < 1) return TFS_ERR_ARG;
+    if (precision != TFS_FP64 && precision != TFS_FP32 && precision != TFS_FP32_PLAIN) return TFS_ERR_ARG;
+    long long N = 1;
+    for (int a = 0; a < grid->dim; ++a) {
+        if (grid->n[a] < 1 || !(grid->L[a] > 0.0) || !std::isfinite(grid->L[a])) return TFS_ERR_ARG;
+        N *= grid->n[a];
+    }
+    if ((N + 31) / 32 > 0x7fffffffLL) return TFS_ERR_ARG;
+    tfs_ctx* h = new (std::nothrow) tfs_ctx();
+    if (!h) return TFS_ERR_ARG;
+    h->dim = grid->dim;
+    for (int a = 0; a < 3; ++a) {
+        h->n[a] = (a < grid->dim) ? grid->n[a] : 1;
+        h->L[a] = (a < grid->dim) ? grid->L[a] : 1.0;
+    }
+    h->N = N;
+    h->nc = grid->dim == 2 ? 3 : 6;
+    h->alpha = alpha;
+    h->Wi = Wi;
+    h->beta = beta;
+    h->dt = dt;
+    h->m = m;
+    h->precision = precision;
+    *out = h;
+    return TFS_OK;
+}
+
+int tfs_set_param(tfs_handle h, int key, double value) {
+    if (!valid_handle(h)) return TFS_ERR_ARG;
+    if (!std::isfinite(value)) return TFS_ERR_ARG;
+    switch (key) {
+        case TFS_PARAM_RE:
+            if (!(value > 0.0)) return TFS_ERR_ARG;
+            h->Re = value;
+            return TFS_OK;
+        case TFS_PARAM_EPS:
+            if (!(value >= 0.0)) return TFS_ERR_ARG;
+            h->eps = value;
+            return TFS_OK;
+        case TFS_PARAM_STENCIL:
+            if (value != TFS_STENCIL_UPWIND3 && value != TFS_STENCIL_CENTRAL2) return TFS_ERR_ARG;
+            h->stencil = (int)value;
+            return TFS_OK;
+        case TFS_PARAM_TRANSPORT:
+            if (value != 0.0 && value != 1.0) return TFS_ERR_ARG;
+            h->transport = (int)value;
+            return TFS_OK;
+        case TFS_PARAM_UMAX: {
+            if (!(value >= 0.0)) return TFS_ERR_ARG;
+            double sum_ih = 0.0;
+            for (int a = 0; a < h->dim; ++a) sum_ih += (double)h->n[a] / h->L[a];
+            if (h->transport && courant_coef(h) * value * sum_ih > courant_limit(h)) return TFS_ERR_UNSTABLE;
+            h->umax = value;
+            return TFS_OK;
+        }
+        default:
+            return TFS_ERR_ARG;
+    }
+}
+
+int tfs_set_soe(tfs_handle h, const double* mu, const double* w, int m) {
+    if (!valid_handle(h)) return TFS_ERR_ARG;
+    if (h->classic()) return m == 0 ? TFS_OK : TFS_ERR_ARG;
+    if (!mu || !w || m != h->m) return TFS_ERR_ARG;
+    for (int j = 0; j < m; ++j)
+        if (!(mu[j] >= 0.0) || !(w[j] >= 0.0) || !std::isfinite(mu[j]) || !std::isfinite(w[j])) return TFS_ERR_ARG;
+    h->mu.assign(mu, mu + m);
+    h->w.assign(w, w + m);
+    double eta = 0.0;
+    for (int j = 0; j < kMaxModes; ++j) {
+        double c = 0.0, rho = 0.0, et = 0.0;
+        if (j < m) {
+            c = 1.0 / (kB0 + mu[j] * h->dt);
+            rho = w[j] * h->dt * c;
+            et = mu[j] * h->dt * c;
+            eta += kB0 * rho;
+        }
+        h->mcd.c[j] = c;
+        h->mcd.rho[j] = rho;
+        h->mcd.eta[j] = et;
+        h->mcf.c[j] = (float)c;
+        h->mcf.rho[j] = (float)rho;
+        const float hi = (float)et;
+        h->mcf.eta_hi[j] = hi;
+        h->mcf.eta_lo[j] = (float)(et - (double)hi);
+    }
+    h->eta = eta;
+    h->soe_set = true;
+    return TFS_OK;
+}
+
+size_t tfs_workspace_bytes(tfs_handle h) {
+    if (!valid_handle(h)) return 0;
+    return forward_bytes(h);
+}
+
+int tfs_bind_workspace(tfs_handle h, void* dev_ptr, size_t bytes) {
+    if (!valid_handle(h) || !dev_ptr) return TFS_ERR_ARG;
+    if (((uintptr_t)dev_ptr) % kAlign) return TFS_ERR_ARG;
+    if (bytes < forward_bytes(h)) return TFS_ERR_NOWORKSPACE;
+    h->ws = (char*)dev_ptr;
+    h->ws_bytes = bytes;
+    layout_forward(h, h->ws);
+    h->state_set = false;
+    return TFS_OK;
+}
+
+int tfs_set_state(tfs_handle h, const void* sigma0, void* stream) {
+    if (!valid_handle(h)) return TFS_ERR_ARG;
+    if (!h->ws) return TFS_ERR_NOWORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    h->cur_sig = 0;
+    h->prev_sig = 1;
+    h->cur_mode = 0;
+    const long long count = (long long)h->nc * h->N;
+    cudaError_t e = launch_fill_levels(h->sig[0], h->sig[1], h->sigma0, sigma0, count, h->is_double(), s);
+    if (e == cudaSuccess && h->m > 0) e = launch_zero(h->modes[0], h->modes_bytes(), s);
+    if (e == cudaSuccess && h->m > 0) e = launch_zero(h->modes[1], h->modes_bytes(), s);
+    if (e == cudaSuccess) e = launch_zero(h->flags, kAlign, s);
+    if (e != cudaSuccess) return TFS_ERR_CUDA;
+    h->sigma0_zero = (sigma0 == nullptr);
+    h->step = 0;
+    h->state_set = true;
+    h->last_stream = s;
+    return TFS_OK;
+}
+
+int tfs_step(tfs_handle h, const void* grad_u_n, const void* grad_u_nm1, const void* u, void* stream) {
+    if (!valid_handle(h)) return TFS_ERR_ARG;
+    return do_step(h, grad_u_n, grad_u_nm1, u, nullptr, (cudaStream_t)stream);
+}
+
+int tfs_get_stress(tfs_handle h, void* out, void* stream) {
+    if (!valid_handle(h) || !out) return TFS_ERR_ARG;
+    if (!h->ws) return TFS_ERR_NOWORKSPACE;
+    if (!h->state_set) return TFS_ERR_STATE;
+    h->last_stream = (cudaStream_t)stream;
+    return cuda_err(cudaMemcpyAsync(out, h->sig[h->cur_sig], h->field_bytes(), cudaMemcpyDeviceToDevice,
+                                    (cudaStream_t)stream));
+}
+
+long tfs_step_index(tfs_handle h) { return valid_handle(h) ? (long)h->step : -1; }
+
+size_t tfs_checkpoint_bytes(tfs_handle h) {
+    if (!valid_handle(h)) return 0;
+    return kHeaderBytes + 3 * align_up(h->field_bytes()) + 2 * align_up(h->modes_bytes());
+}
+
+int tfs_save(tfs_handle h, void* dst, void* stream) {
+    if (!valid_handle(h) || !dst) return TFS_ERR_ARG;
+    if (((uintptr_t)dst) % 16) return TFS_ERR_ARG;
+    if (!h->ws) return TFS_ERR_NOWORKSPACE;
+    if (!h->state_set) return TFS_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t words[12] = {kMagic, kVersion, (uint64_t)h->dim, (uint64_t)h->n[0], (uint64_t)h->n[1],
+                          (uint64_t)h->n[2], (uint64_t)h->m, (uint64_t)h->precision, (uint64_t)h->step,
+                          (uint64_t)(h->sigma0_zero ? 1 : 0), 0, 0};
+    double scal[2] = {h->dt, h->alpha};
+    memcpy(&words[10], &scal[0], 8);
+    memcpy(&words[11], &scal[1], 8);
+    char* p = (char*)dst;
+    cudaError_t e = launch_write_header((uint64_t*)p, words, 12, s);
+    p += kHeaderBytes;
+    const size_t fb = h->field_bytes(), mb = h->modes_bytes();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->sig[h->cur_sig], fb, cudaMemcpyDeviceToDevice, s);
+    p += align_up(fb);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->sig[h->prev_sig], fb, cudaMemcpyDeviceToDevice, s);
+    p += align_up(fb);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->sigma0, fb, cudaMemcpyDeviceToDevice, s);
+    p += align_up(fb);
+    if (mb > 0) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->modes[h->cur_mode], mb, cudaMemcpyDeviceToDevice, s);
+        p += align_up(mb);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->modes[1 - h->cur_mode], mb, cudaMemcpyDeviceToDevice, s);
+    }
+    h->last_stream = s;
+    return cuda_err(e);
+}
+
+int tfs_load(tfs_handle h, const void* src, void* stream) {
+    if (!valid_handle(h) || !src) return TFS_ERR_ARG;
+    if (!h->ws) return TFS_ERR_NOWORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t words[12];
+    cudaError_t e = cudaMemcpyAsync(words, src, sizeof(words), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return TFS_ERR_CUDA;
+    double scal[2];
+    memcpy(&scal[0], &words[10], 8);
+    memcpy(&scal[1], &words[11], 8);
+    if (words[0] != kMagic || words[1] != kVersion || words[2] != (uint64_t)h->dim ||
+        words[3] != (uint64_t)h->n[0] || words[4] != (uint64_t)h->n[1] || words[5] != (uint64_t)h->n[2] ||
+        words[6] != (uint64_t)h->m || words[7] != (uint64_t)h->precision || scal[0] != h->dt ||
+        scal[1] != h->alpha)
+        return TFS_ERR_FORMAT;
+    h->cur_sig = 0;
+    h->prev_sig = 1;
+    h->cur_mode = 0;
+    const char* p = (const char*)src + kHeaderBytes;
+    const size_t fb = h->field_bytes(), mb = h->modes_bytes();
+    e = cudaMemcpyAsync(h->sig[0], p, fb, cudaMemcpyDeviceToDevice, s);
+    p += align_up(fb);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->sig[1], p, fb, cudaMemcpyDeviceToDevice, s);
+    p += align_up(fb);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->sigma0, p, fb, cudaMemcpyDeviceToDevice, s);
+    p += align_up(fb);
+    if (mb > 0) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->modes[0], p, mb, cudaMemcpyDeviceToDevice, s);
+        p += align_up(mb);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->modes[1], p, mb, cudaMemcpyDeviceToDevice, s);
+    }
+    if (e != cudaSuccess) return TFS_ERR_CUDA;
+    h->step = (long long)words[8];
+    h->sigma0_zero = words[9] != 0;
+    h->state_set = true;
+    h->last_stream = s;
+    return TFS_OK;
+}
+
+// ------------------------------------------------------------------ adjoint
+namespace {
+
+struct AdjLayout {
+    double* s[4];       // two ping-pong pairs (s1, s0)
+    double* lamR;
+    char* ell[2];
+    double* partials;   // 2 per block
+    double* out2;
+    char* seg;
+    size_t seg_stride;
+};
+
+size_t adj_bytes(const tfs_ctx* h, int seg_steps) {
+    const size_t dfield = (size_t)h->nc * (size_t)h->N * 8;
+    const long long blocks = (h->N + 31) / 32;
+    return 5 * align_up(dfield) + 2 * align_up(h->modes_bytes()) + align_up((size_t)blocks * 16) + kAlign +
+           (size_t)seg_steps * align_up(h->field_bytes());
+}
+
+AdjLayout adj_layout(const tfs_ctx* h) {
+    AdjLayout L;
+    const size_t dfield = (size_t)h->nc * (size_t)h->N * 8;
+    const long long blocks = (h->N + 31) / 32;
+    char* p = h->aws;
+    for (int i = 0; i < 4; ++i) {
+        L.s[i] = (double*)p;
+        p += align_up(dfield);
+    }
+    L.lamR = (double*)p;
+    p += align_up(dfield);
+    for (int i = 0; i < 2; ++i) {
+        L.ell[i] = p;
+        p += align_up(h->modes_bytes());
+    }
+    L.partials = (double*)p;
+    p += align_up((size_t)blocks * 16);
+    L.out2 = (double*)p;
+    p += kAlign;
+    L.seg = p;
+    L.seg_stride = align_up(h->field_bytes());
+    return L;
+}
+
+}  // namespace
+
+size_t tfs_adjoint_workspace_bytes(tfs_handle h, int segment_steps) {
+    if (!valid_handle(h) || segment_steps < 1) return 0;
+    return adj_bytes(h, segment_steps);
+}
+
+int tfs_bind_adjoint_workspace(tfs_handle h, void* dev_ptr, size_t bytes) {
+    if (!valid_handle(h) || !dev_ptr) return TFS_ERR_ARG;
+    if (((uintptr_t)dev_ptr) % kAlign) return TFS_ERR_ARG;
+    const size_t base = adj_bytes(h, 0);
+    if (bytes < adj_bytes(h, 1)) return TFS_ERR_NOWORKSPACE;
+    h->aws = (char*)dev_ptr;
+    h->aws_bytes = bytes;
+    h->seg_capacity = (int)((bytes - base) / align_up(h->field_bytes()));
+    return TFS_OK;
+}
+
+int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* checkpoints, int K, int steps,
+                 const void* grad_u, const void* u, double* dJ_dsigma0, double* dJ_dgrad_u, double* dJ_dWi,
+                 double* dJ_dbeta, void* stream) {
+    if (!valid_handle(h) || !dJ_dsigma_T || !checkpoints || !grad_u || !dJ_dsigma0 || !dJ_dgrad_u || !dJ_dWi ||
+        !dJ_dbeta)
+        return TFS_ERR_ARG;
+    if (K < 1 || steps < 1) return TFS_ERR_ARG;
+    if (h->transport && !u) return TFS_ERR_ARG;
+    if (!h->ws || !h->aws) return TFS_ERR_NOWORKSPACE;
+    if (K > h->seg_capacity) return TFS_ERR_NOWORKSPACE;
+    if (!h->classic() && !h->soe_set) return TFS_ERR_NOSOE;
+    cudaStream_t s = (cudaStream_t)stream;
+    AdjLayout L = adj_layout(h);
+    const size_t dfield = (size_t)h->nc * (size_t)h->N * 8;
+    const long long blocks = (h->N + 31) / 32;
+    const long long ncN = (long long)h->nc * h->N;
+    cudaError_t e = cudaSuccess;
+    e = launch_zero(dJ_dsigma0, dfield, s);
+    if (e == cudaSuccess) e = launch_zero(dJ_dgrad_u, (size_t)h->dim * h->dim * h->N * 8, s);
+    if (e == cudaSuccess) e = launch_zero(L.partials, (size_t)blocks * 16, s);
+    for (int i = 0; i < 2 && e == cudaSuccess && h->modes_bytes() > 0; ++i) e = launch_zero(L.ell[i], h->modes_bytes(), s);
+    if (e == cudaSuccess) e = launch_to_double(dJ_dsigma_T, L.s[0], ncN, h->is_double(), s);
+    if (e == cudaSuccess) e = launch_zero(L.s[1], dfield, s);
+    if (e != cudaSuccess) return TFS_ERR_CUDA;
+    int cur = 0;        // s[2*cur] = s1, s[2*cur+1] = s0
+    int ell_prev = 0;   // slot of lamQ of the later step; the other slot holds the one before
+    const LaunchCfg cfg = make_cfg(h);
+    const int nseg = (steps + K - 1) / K;
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+        const int start = seg * K;
+        const int end = (start + K < steps) ? start + K : steps;
+        int rc = tfs_load(h, checkpoints[seg], stream);
+        if (rc != TFS_OK) return rc;
+        if (h->step != start) return TFS_ERR_FORMAT;
+        for (int n = start; n < end; ++n) {
+            rc = do_step(h, grad_u, grad_u, u, L.seg + (size_t)(n - start) * L.seg_stride, s);
+            if (rc != TFS_OK) return rc;
+        }
+        for (int n = end - 1; n >= start; --n) {
+            const void* sig_np1 = L.seg + (size_t)(n - start) * L.seg_stride;
+            const int nxt = 1 - cur;
+            if (h->is_double()) {
+                AdjArgs<double> a{};
+                a.kap_n = (const double*)grad_u;
+                a.kap_nm1 = (const double*)grad_u;
+                a.u = (const double*)u;
+                a.sig_np1 = (const double*)sig_np1;
+                a.ell_prev = (const double*)L.ell[ell_prev];
+                a.ell_prev2 = (double*)L.ell[1 - ell_prev];
+                a.mc = h->mcd;
+                a.s1 = L.s[2 * cur];
+                a.s0 = L.s[2 * cur + 1];
+                a.s1_out = L.s[2 * nxt];
+                a.s0_out = L.s[2 * nxt + 1];
+                a.lamR = L.lamR;
+                a.g_sigma0 = dJ_dsigma0;
+                a.g_kap = dJ_dgrad_u;
+                a.partials = L.partials;
+                a.flags = h->flags;
+                a.N = h->N;
+                a.n0 = (int)h->n[0];
+                a.n1 = (int)h->n[1];
+                a.n2 = (int)h->n[2];
+                a.m = h->classic() ? 0 : h->m;
+                a.first = (n == steps - 1);
+                a.dt = h->dt;
+                a.eta = h->classic() ? kB0 : h->eta;
+                a.a = a.eta + h->dt / h->Wi;
+                a.G = (1.0 - h->beta) / (h->Wi * h->Re);
+                a.g = g_alpha(h, n);
+                a.eps = h->eps;
+                a.Wi = h->Wi;
+                a.Re = h->Re;
+                for (int i = 0; i < 3; ++i) a.inv_h[i] = (double)h->n[i] / h->L[i];
+                e = launch_adjoint_f64(a, cfg, s);
+                if (e == cudaSuccess && h->transport) e = launch_adjoint_transport(a, u, true, cfg, s);
+            } else {
+                AdjArgs<float> a{};
+                a.kap_n = (const float*)grad_u;
+                a.kap_nm1 = (const float*)grad_u;
+                a.u = (const float*)u;
+                a.sig_np1 = (const float*)sig_np1;
+                a.ell_prev = (const float*)L.ell[ell_prev];
+                a.ell_prev2 = (float*)L.ell[1 - ell_prev];
+                a.mc = h->mcd;
+                a.s1 = L.s[2 * cur];
+                a.s0 = L.s[2 * cur + 1];
+                a.s1_out = L.s[2 * nxt];
+                a.s0_out = L.s[2 * nxt + 1];
+                a.lamR = L.lamR;
+                a.g_sigma0 = dJ_dsigma0;
+                a.g_kap = dJ_dgrad_u;
+                a.partials = L.partials;
+                a.flags = h->flags;
+                a.N = h->N;
+                a.n0 = (int)h->n[0];
+                a.n1 = (int)h->n[1];
+                a.n2 = (int)h->n[2];
+                a.m = h->classic() ? 0 : h->m;
+                a.first = (n == steps - 1);
+                a.dt = h->dt;
+                a.eta = h->classic() ? kB0 : h->eta;
+                a.a = a.eta + h->dt / h->Wi;
+                a.G = (1.0 - h->beta) / (h->Wi * h->Re);
+                a.g = g_alpha(h, n);
+                a.eps = h->eps;
+                a.Wi = h->Wi;
+                a.Re = h->Re;
+                for (int i = 0; i < 3; ++i) a.inv_h[i] = (double)h->n[i] / h->L[i];
+                e = launch_adjoint_f32(a, cfg, s);
+                if (e == cudaSuccess && h->transport) {
+                    AdjArgs<double> ad{};
+                    ad.N = a.N;
+                    ad.n0 = a.n0;
+                    ad.n1 = a.n1;
+                    ad.n2 = a.n2;
+                    ad.dt = a.dt;
+                    ad.eps = a.eps;
+                    for (int i = 0; i < 3; ++i) ad.inv_h[i] = a.inv_h[i];
+                    ad.lamR = a.lamR;
+                    ad.s1_out = a.s1_out;
+                    ad.s0_out = a.s0_out;
+                    e = launch_adjoint_transport(ad, u, false, cfg, s);
+                }
+            }
+            if (e != cudaSuccess) return TFS_ERR_CUDA;
+            cur = nxt;
+            if (!h->classic()) ell_prev = 1 - ell_prev;
+        }
+    }
+    // initial state sigma^0 = sigma^{-1} = sigma0
+    e = launch_add_initial(dJ_dsigma0, L.s[2 * cur], L.s[2 * cur + 1], ncN, s);
+    if (e == cudaSuccess) e = launch_reduce_partials(L.partials, (int)blocks, L.out2, s);
+    double out2[2] = {0.0, 0.0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out2, L.out2, sizeof(out2), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return TFS_ERR_CUDA;
+    *dJ_dWi = out2[0];
+    *dJ_dbeta = out2[1];
+    h->last_stream = s;
+    return TFS_OK;
+}
+
+int tfs_status(tfs_handle h, unsigned* device_flags) {
+    if (!valid_handle(h) || !device_flags) return TFS_ERR_ARG;
+    if (!h->ws) return TFS_ERR_NOWORKSPACE;
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, h->flags, sizeof(v), cudaMemcpyDeviceToHost, h->last_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->last_stream);
+    if (e != cudaSuccess) return TFS_ERR_CUDA;
+    *device_flags = v;
+    return TFS_OK;
+}
+
+const char* tfs_strerror(int code) {
+    switch (code) {
+        case TFS_OK: return "ok";
+        case TFS_ERR_ARG: return "invalid argument";
+        case TFS_ERR_NOSOE: return "no SOE table set (alpha < 1)";
+        case TFS_ERR_UNSTABLE: return "velocity bound exceeds the explicit-transport Courant limit";
+        case TFS_ERR_CUDA: return "CUDA runtime error";
+        case TFS_ERR_STATE: return "call out of order (state not set)";
+        case TFS_ERR_NOWORKSPACE: return "workspace not bound or too small";
+        case TFS_ERR_FORMAT: return "checkpoint does not match this handle";
+        default: return "unknown status";
+    }
+}
+
+int tfs_destroy(tfs_handle h) {
+    if (!valid_handle(h)) return TFS_ERR_ARG;
+    delete h;
+    return TFS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+// Device-side building blocks of the stress step: packed component tables,
+// the per-point upper-convected operator, the small dense solve, and the
+// periodic stencil.  Used by tfs_forward.cu and tfs_adjoint.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <type_traits>
+
+#include "tfs_internal.h"
+
+namespace tfs {
+
+// Compile-time loop: calls f(std::integral_constant<int, I>) for I in [B, E).
+// Keeps every array index a constant so small matrices stay in registers.
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+template <int DIM> struct Packed;
+// 2D packed order (xx, xy, yy)
+template <> struct Packed<2> {
+    static constexpr int NC = 3;
+    __host__ __device__ static constexpr int I(int c) { return c == 0 ? 0 : (c == 1 ? 0 : 1); }
+    __host__ __device__ static constexpr int J(int c) { return c == 0 ? 0 : (c == 1 ? 1 : 1); }
+};
+// 3D packed order (xx, yy, zz, yz, xz, xy)
+template <> struct Packed<3> {
+    static constexpr int NC = 6;
+    __host__ __device__ static constexpr int I(int c) {
+        return c == 0 ? 0 : c == 1 ? 1 : c == 2 ? 2 : c == 3 ? 1 : c == 4 ? 0 : 0;
+    }
+    __host__ __device__ static constexpr int J(int c) {
+        return c == 0 ? 0 : c == 1 ? 1 : c == 2 ? 2 : c == 3 ? 2 : c == 4 ? 2 : 1;
+    }
+};
+
+// Entry (r, k) of the packed matrix of  S -> kappa S + S kappa^T, i.e. the
+// r-th packed component of kappa E_k + E_k kappa^T where E_k is the symmetric
+// unit matrix of packed component k.  All index tests fold at compile time
+// once the loops over r and k are unrolled.
+template <int DIM>
+__device__ __forceinline__ double uc_entry(const double K[3][3], int r, int k) {
+    const int ro = Packed<DIM>::I(r), so = Packed<DIM>::J(r);
+    const int i = Packed<DIM>::I(k), j = Packed<DIM>::J(k);
+    double v = 0.0;
+    // (kappa E)_{ro,so} = sum_l K[ro][l] E[l][so];  (E kappa^T)_{ro,so} = sum_l E[ro][l] K[so][l]
+    // E[l][s] = 1 for (l,s) in {(i,j), (j,i)}
+    if (so == j) v += K[ro][i];
+    if (i != j && so == i) v += K[ro][j];
+    if (ro == i) v += K[so][j];
+    if (i != j && ro == j) v += K[so][i];
+    return v;
+}
+
+// M = a I - dt L(kappa) in packed coordinates.
+template <int DIM>
+__device__ __forceinline__ void assemble_M(const double K[3][3], double a, double dt,
+                                           double M[Packed<DIM>::NC][Packed<DIM>::NC]) {
+    constexpr int NC = Packed<DIM>::NC;
+    static_for<0, NC>([&](auto rr) {
+        constexpr int r = decltype(rr)::value;
+        static_for<0, NC>([&](auto kk) {
+            constexpr int k = decltype(kk)::value;
+            const double l = uc_entry<DIM>(K, r, k);
+            M[r][k] = (r == k) ? fma(-dt, l, a) : -dt * l;
+        });
+    });
+}
+
+// In-place Gaussian elimination with partial pivoting on a small dense system.
+// Pivot search by compare-and-swap (no dynamic register indexing): the largest
+// |entry| of column k among rows k.. ends up in row k, ties keep the earlier row.
+// Returns false when a pivot is not larger than `tiny`.
+template <int NC>
+__device__ __forceinline__ bool gauss_pp(double M[NC][NC], double x[NC], double tiny) {
+    bool ok = true;
+    static_for<0, NC>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        static_for<k + 1, NC>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            const bool sw = fabs(M[i][k]) > fabs(M[k][k]);
+            static_for<k, NC>([&](auto jj) {
+                constexpr int j = decltype(jj)::value;
+                const double t0 = M[k][j], t1 = M[i][j];
+                M[k][j] = sw ? t1 : t0;
+                M[i][j] = sw ? t0 : t1;
+            });
+            const double t0 = x[k], t1 = x[i];
+            x[k] = sw ? t1 : t0;
+            x[i] = sw ? t0 : t1;
+        });
+        ok = ok && (fabs(M[k][k]) > tiny);
+        const double inv = 1.0 / M[k][k];
+        M[k][k] = inv;     // keep the reciprocal for back substitution
+        static_for<k + 1, NC>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            const double f = M[i][k] * inv;
+            static_for<k + 1, NC>([&](auto jj) {
+                constexpr int j = decltype(jj)::value;
+                M[i][j] = fma(-f, M[k][j], M[i][j]);
+            });
+            x[i] = fma(-f, x[k], x[i]);
+        });
+    });
+    static_for<0, NC>([&](auto rr) {
+        constexpr int i = NC - 1 - decltype(rr)::value;
+        double acc = x[i];
+        static_for<i + 1, NC>([&](auto jj) {
+            constexpr int j = decltype(jj)::value;
+            acc = fma(-M[i][j], x[j], acc);
+        });
+        x[i] = acc * M[i][i];
+    });
+    return ok;
+}
+
+// Periodic neighbour index along axis `ax` at offset `off` (|off| <= 2) from
+// point (x, y, z); correct for any axis length >= 1.
+struct GridIdx {
+    long long n0, n1, n2;
+    long long x, y, z;
+    __device__ __forceinline__ static long long wrap(long long v, long long n) {
+        if (v < 0) v += n;
+        if (v < 0) v += n;
+        if (v >= n) v -= n;
+        if (v >= n) v -= n;
+        return v;
+    }
+    __device__ __forceinline__ long long at(int ax, int off) const {
+        const long long xx = ax == 0 ? wrap(x + off, n0) : x;
+        const long long yy = ax == 1 ? wrap(y + off, n1) : y;
+        const long long zz = ax == 2 ? wrap(z + off, n2) : z;
+        return xx + n0 * (yy + n1 * zz);
+    }
+};
+
+// two-sum of a and b (Knuth): s + e == a + b exactly.  __fadd_rn/__fsub_rn are
+// never contracted into FMAs.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ double to_d(float v) { return (double)v; }
+__device__ __forceinline__ double to_d(double v) { return v; }
+
+}  // namespace tfs

@@ -1,0 +1,108 @@
+// Internal declarations shared by the host API and the kernels of libtfs.
+// Not part of the public ABI (see include/tfs.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tfs {
+
+constexpr int kMaxModes = 64;
+constexpr double kB0 = 1.5, kB1 = -2.0, kB2 = 0.5;   // BDF2 (Section 4.1)
+
+// Per-mode constants of the BDF2 push-forward (eq. BDF_Phi_k_n+1):
+// c_j = 1/(b0 + mu_j dt), rho_j = w_j dt c_j, eta_j = mu_j dt c_j.
+// The float copies carry a hi/lo split of eta_j for the compensated mode sum.
+struct ModeConstsD {
+    double c[kMaxModes], rho[kMaxModes], eta[kMaxModes];
+};
+struct ModeConstsF {
+    float c[kMaxModes], rho[kMaxModes], eta_hi[kMaxModes], eta_lo[kMaxModes];
+};
+
+template <typename T> struct ModeConsts;
+template <> struct ModeConsts<double> { using type = ModeConstsD; };
+template <> struct ModeConsts<float> { using type = ModeConstsF; };
+
+// Arguments of one forward step launch.  Field pointers follow the layouts of
+// include/tfs.h; the mode arrays are [m][nc][N].
+template <typename T>
+struct FwdArgs {
+    const T* kap_n;        // [d*d][N]
+    const T* kap_nm1;      // [d*d][N]
+    const T* u;            // [d][N] (transport only)
+    const T* sigma0;       // [nc][N] or nullptr for zero
+    const T* sig_n;        // [nc][N]
+    const T* sig_nm1;      // [nc][N]
+    T* sig_np1;            // [nc][N]
+    T* sig_copy;           // optional second destination of sigma^{n+1}
+    const T* modes_n;      // [m][nc][N]
+    T* modes_nm1;          // [m][nc][N]  read as level n-1, overwritten with level n+1
+    unsigned* flags;       // latched device status
+    long long N;
+    int n0, n1, n2;
+    int m;
+    double dt, eta, a, G, g, eps;   // eta, a = eta + dt/Wi, G, g = g_alpha(t_{n+1})
+    double inv_h[3];
+    double courant_coef;   // dt^alpha / b0^alpha (0: no Courant check)
+    double courant_limit;
+    typename ModeConsts<T>::type mc;
+};
+
+struct LaunchCfg {
+    int dim;
+    int stencil;       // 0 upwind3, 1 central2
+    bool transport;
+    bool classic;      // alpha == 1
+    bool compensated;  // FP32 compensated mode sum
+};
+
+// forward launchers (tfs_forward.cu)
+cudaError_t launch_forward_f64(const FwdArgs<double>& a, const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_forward_f32(const FwdArgs<float>& a, const LaunchCfg& cfg, cudaStream_t s);
+
+// Arguments of one adjoint step launch (see tfs_adjoint.cu).
+template <typename T>
+struct AdjArgs {
+    const T* kap_n;        // [d*d][N] forward velocity gradient of the step
+    const T* kap_nm1;
+    const T* u;            // [d][N]
+    const T* sig_np1;      // forward sigma^{n+1} of the step [nc][N]
+    // adjoint stress state: s1 = adjoint of sigma^{n+1}, s0 = adjoint of the copied sigma^n
+    const double* s1;      // [nc][N]
+    const double* s0;      // [nc][N]
+    double* s1_out;        // adjoint of sigma^n       (next step's s1)
+    double* s0_out;        // adjoint of sigma^{n-1}   (next step's s0)
+    double* lamR;          // [nc][N] scratch: adjoint of the right-hand side (for transport)
+    // adjoint mode ring: ell_prev = lamQ of the previous adjoint step, ell_prev2 the one before
+    const T* ell_prev;     // [m][nc][N]
+    T* ell_prev2;          // [m][nc][N] read, then overwritten with this step's lamQ
+    double* g_sigma0;      // [nc][N] accumulated
+    double* g_kap;         // [d*d][N] accumulated (frozen gradient: coefficient +1)
+    double* partials;      // [gridDim.x][2] per-block sums of dJ/dWi, dJ/dbeta
+    unsigned* flags;
+    long long N;
+    int n0, n1, n2;
+    int m;
+    int first;             // 1 on the first adjoint step (no previous lamQ)
+    double dt, eta, a, G, g, eps, Wi, Re;
+    double inv_h[3];
+    ModeConstsD mc;
+};
+
+cudaError_t launch_adjoint_f64(const AdjArgs<double>& a, const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_adjoint_f32(const AdjArgs<float>& a, const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_adjoint_transport(const AdjArgs<double>& a, const void* u, bool u_is_double,
+                                     const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_reduce_partials(const double* partials, int count, double* out2, cudaStream_t s);
+
+// small utility kernels (tfs_util.cu)
+cudaError_t launch_fill_levels(void* sig_n, void* sig_nm1, void* sigma0_copy, const void* sigma0,
+                               long long count, bool is_double, cudaStream_t s);
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s);
+cudaError_t launch_write_header(uint64_t* dst, const uint64_t* words, int count, cudaStream_t s);
+cudaError_t launch_to_double(const void* src, double* dst, long long count, bool is_double, cudaStream_t s);
+cudaError_t launch_add_initial(double* g_sigma0, const double* s1, const double* s0, long long count,
+                               cudaStream_t s);
+
+}  // namespace tfs

@@ -1,0 +1,113 @@
+"""Host-side FP64 construction of the sum-of-exponentials (SOE) kernel table.
+
+The stress law's memory term is the Caputo derivative of order alpha with kernel
+t^-alpha / Gamma(1-alpha).  Kernel compression (Section 2.2) replaces it by
+sum_j w_j exp(-mu_j t) with non-negative exponents and weights (completely
+monotone by Bernstein's theorem), so each grid point carries m mode tensors.
+The table is computed once on the host in FP64 and handed to tfs_set_soe.
+
+``build(alpha, dt, T, m)``  positive table with exactly m terms whose relative
+    error is small on [dt, T].  Exponents lie on a geometric grid spanning
+    [1/T, 1/dt] widened on both sides; weights are the non-negative least-squares
+    fit of the relative kernel error on log-spaced times in [dt/10, T].  The grid
+    density is searched so that exactly m weights come out positive.
+``aaa(alpha, dt, T, m)``  the paper's recipe: AAA rational approximation of
+    s^alpha (Laplace variable) divided by s, partial fractions, inverse Laplace
+    transform; valid while the poles stay real and negative (about m <= 20).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy import linalg, optimize, special
+
+
+def caputo_kernel(alpha: float, t):
+    t = np.asarray(t, dtype=np.float64)
+    return np.power(t, -alpha) / special.gamma(1.0 - alpha)
+
+
+def evaluate(mu, w, t):
+    t = np.asarray(t, dtype=np.float64)
+    return np.exp(-np.outer(t, np.asarray(mu))) @ np.asarray(w)
+
+
+def relative_error(alpha, mu, w, dt, T, samples=400):
+    t = np.geomspace(dt, T, samples)
+    k = caputo_kernel(alpha, t)
+    return float(np.max(np.abs(evaluate(mu, w, t) / k - 1.0)))
+
+
+def _fit(alpha, dt, T, count, widen_lo, widen_hi, times):
+    exps = np.geomspace(10.0 ** (-widen_lo) / T, 10.0 ** widen_hi / dt, count)
+    design = np.exp(-np.outer(times, exps)) / caputo_kernel(alpha, times)[:, None]
+    weights, _ = optimize.nnls(design, np.ones(len(times)), maxiter=60 * count * count)
+    keep = weights > 0
+    return exps[keep], weights[keep]
+
+
+def build(alpha: float, dt: float, T: float, m: int):
+    """Positive SOE table (mu, w) with exactly m terms, sorted by mu."""
+    if not 0.0 < alpha < 1.0:
+        raise ValueError("the SOE table is needed only for 0 < alpha < 1")
+    if m < 1 or dt <= 0 or T <= dt:
+        raise ValueError("need m >= 1 and 0 < dt < T")
+    times = np.geomspace(dt / 10.0, T, 1200)
+    best = None
+    for widen_hi in (1.0, 2.0, 3.0):
+        for widen_lo in (1.0, 1.5, 2.0):
+            # the number of positive weights grows with the grid size; scan upwards
+            for count in range(m, 2 * m + 8):
+                mu, w = _fit(alpha, dt, T, count, widen_lo, widen_hi, times)
+                if len(mu) < m:
+                    continue
+                if len(mu) > m:
+                    break
+                err = relative_error(alpha, mu, w, dt, T)
+                if best is None or err < best[0]:
+                    best = (err, mu, w)
+    if best is None:
+        raise ValueError(f"no positive table with exactly {m} terms")
+    order = np.argsort(best[1])
+    return best[1][order].copy(), best[2][order].copy()
+
+
+def aaa(alpha: float, dt: float, T: float, m: int, samples: int = 2000):
+    """AAA on s^alpha over [0.1/T, 10/dt], divided by s (Section 2.2); m terms
+    (m - 1 poles plus the residue at s = 0).  Raises ValueError when the table
+    is not real and non-negative."""
+    z = np.geomspace(0.1 / T, 10.0 / dt, samples)
+    f = z ** alpha
+    free = np.ones(samples, dtype=bool)
+    approx = np.full(samples, f.mean())
+    sup, val = [], []
+    bw = None
+    for _ in range(m):
+        resid = np.where(free, np.abs(f - approx), -1.0)
+        i = int(np.argmax(resid))
+        sup.append(z[i]); val.append(f[i]); free[i] = False
+        zs, fs = np.array(sup), np.array(val)
+        cauchy = 1.0 / (z[free][:, None] - zs[None, :])
+        loewner = (f[free][:, None] - fs[None, :]) * cauchy
+        bw = np.linalg.svd(loewner)[2][-1]
+        approx = f.copy()
+        approx[free] = (cauchy @ (bw * fs)) / (cauchy @ bw)
+    zs, fs = np.array(sup), np.array(val)
+    k = len(zs)
+    A = np.zeros((k + 1, k + 1)); A[0, 1:] = bw; A[1:, 0] = 1.0; A[1:, 1:] = np.diag(zs)
+    B = np.eye(k + 1); B[0, 0] = 0.0
+    poles = linalg.eigvals(A, B)
+    poles = poles[np.isfinite(poles)]
+    if np.any(np.abs(poles.imag) > 1e-8 * np.abs(poles)) or np.any(poles.real >= 0):
+        raise ValueError("AAA produced complex or non-negative poles")
+    poles = poles.real
+    num = lambda s: np.sum(bw * fs / (s - zs))
+    den = lambda s: np.sum(bw / (s - zs))
+    dden = lambda s: -np.sum(bw / (s - zs) ** 2)
+    mu = np.concatenate([-poles, [0.0]])
+    w = np.concatenate([[num(p) / (p * dden(p)) for p in poles], [num(0.0) / den(0.0)]])
+    if np.any(w < 0):
+        raise ValueError("AAA produced a negative weight")
+    order = np.argsort(mu)
+    return mu[order], w[order]

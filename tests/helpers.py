@@ -1,0 +1,72 @@
+"""Shared helpers of the test-suite: building the library, running the CUDA
+path through the C ABI, running the oracle on the same inputs, and the
+per-component error measure (max |difference| / max |oracle|)."""
+from __future__ import annotations
+
+import numpy as np
+
+from paper_2411_17294_gb300 import inputs
+
+
+def ensure_lib():
+    from paper_2411_17294_gb300 import build
+    return build.build()
+
+
+def rel_err_per_component(got: np.ndarray, ref: np.ndarray) -> np.ndarray:
+    """Normwise relative error of each stress component."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    scale = np.max(np.abs(ref), axis=1)
+    scale = np.where(scale > 0, scale, 1.0)
+    return np.max(np.abs(got - ref), axis=1) / scale
+
+
+def run_gpu(case: dict, sigma0, kap_seq, u, steps: int, precision: int, return_solver=False):
+    """Run the CUDA path; kap_seq is a frozen array [d*d][N] or a callable n -> array."""
+    import torch
+    from paper_2411_17294_gb300 import tfs
+    s = tfs.Solver(case["dim"], case["n"], case["alpha"], case["Wi"], case["beta"], case["dt"],
+                   m=len(case.get("mu", [])) if case["alpha"] < 1 else 0, precision=precision,
+                   mu=case.get("mu") if case["alpha"] < 1 else None, w=case.get("w"),
+                   eps=case.get("eps", 0.0), stencil=case.get("stencil", 0),
+                   transport=case.get("transport", False), L=case.get("L"))
+    dt = s.dtype
+    dev = s.device
+    s.set_state(None if sigma0 is None else torch.as_tensor(sigma0, dtype=dt, device=dev))
+    ut = None if u is None else torch.as_tensor(u, dtype=dt, device=dev).contiguous()
+    if callable(kap_seq):
+        cache = {}
+
+        def K(n):
+            if n not in cache:
+                cache.clear() if len(cache) > 4 else None
+                cache[n] = torch.as_tensor(kap_seq(n), dtype=dt, device=dev).contiguous()
+            return cache[n]
+        for n in range(steps):
+            s.step(K(n), K(n - 1) if n > 0 else None, ut)
+    else:
+        kt = torch.as_tensor(kap_seq, dtype=dt, device=dev).contiguous()
+        for n in range(steps):
+            s.step(kt, kt, ut)
+    out = s.stress().double().cpu().numpy()
+    if return_solver:
+        return out, s
+    s.close()
+    return out
+
+
+def run_oracle(case: dict, sigma0, kap_seq, u, steps: int):
+    from oracle import orc
+    prob = orc.Problem(dim=case["dim"], n=case["n"], alpha=case["alpha"], Wi=case["Wi"], beta=case["beta"],
+                       dt=case["dt"], mu=np.asarray(case.get("mu", np.zeros(0))),
+                       w=np.asarray(case.get("w", np.zeros(0))), eps=case.get("eps", 0.0),
+                       stencil=case.get("stencil", 0), transport=case.get("transport", False), L=case.get("L"))
+    o = orc.Oracle(prob, sigma0)
+    return o.run(steps, kap_seq, u)
+
+
+def spectral_case(dim, n, seed, kmax=None):
+    kmax = kmax or max(1, min(n) // 3)
+    u, kap = inputs.spectral_velocity(dim, n, kmax, seed)
+    return u, kap

@@ -1,0 +1,115 @@
+"""The C-ABI library loads on a machine without a GPU, exports every symbol
+declared in include/tfs.h, and its host-side argument checks behave as
+documented (no compute calls: no device is touched)."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from helpers import ensure_lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    ensure_lib()
+    from paper_2411_17294_gb300 import tfs
+    return tfs.load_library()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "tfs.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tfs_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2411_17294_gb300 import tfs
+    names = declared_functions()
+    assert len(names) >= 18
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(tfs.EXPORTS) == sorted(n for n in names if n in tfs.EXPORTS)
+    assert set(names) <= set(tfs.EXPORTS)
+
+
+def make(lib, dim=3, n=(8, 8, 8), alpha=0.6, Wi=2.0, beta=0.9, m=4, dt=2e-4, precision=1, L=None):
+    from paper_2411_17294_gb300 import tfs
+    g = tfs.TfsGrid()
+    g.dim = dim
+    Ls = L or [2 * math.pi] * 3
+    for a in range(3):
+        g.n[a] = n[a] if a < len(n) else 1
+        g.L[a] = Ls[a]
+    h = ctypes.c_void_p()
+    rc = lib.tfs_create(ctypes.byref(h), ctypes.byref(g), alpha, Wi, beta, m, dt, precision)
+    return rc, h
+
+
+def test_create_validation(lib):
+    from paper_2411_17294_gb300 import tfs
+    rc, h = make(lib)
+    assert rc == tfs.TFS_OK and h.value
+    assert lib.tfs_destroy(h) == tfs.TFS_OK
+    bad = [
+        dict(dim=4), dict(alpha=0.0), dict(alpha=1.2), dict(Wi=0.0), dict(beta=1.0), dict(beta=-0.1),
+        dict(dt=0.0), dict(m=65), dict(m=0), dict(alpha=1.0, m=3), dict(precision=7), dict(n=(0, 4, 4)),
+    ]
+    for kw in bad:
+        rc, h = make(lib, **kw)
+        assert rc == tfs.TFS_ERR_ARG, kw
+        assert not h.value
+    rc, h = make(lib, alpha=1.0, m=0)
+    assert rc == tfs.TFS_OK
+    lib.tfs_destroy(h)
+
+
+def test_soe_and_params_validation(lib):
+    from paper_2411_17294_gb300 import tfs
+    rc, h = make(lib, m=3)
+    dp = ctypes.POINTER(ctypes.c_double)
+    mu = np.array([1.0, 10.0, 100.0])
+    w = np.array([0.5, 0.4, 0.3])
+    assert lib.tfs_set_soe(h, mu.ctypes.data_as(dp), w.ctypes.data_as(dp), 2) == tfs.TFS_ERR_ARG
+    wn = np.array([0.5, -0.4, 0.3])
+    assert lib.tfs_set_soe(h, mu.ctypes.data_as(dp), wn.ctypes.data_as(dp), 3) == tfs.TFS_ERR_ARG
+    mnan = np.array([1.0, np.nan, 100.0])
+    assert lib.tfs_set_soe(h, mnan.ctypes.data_as(dp), w.ctypes.data_as(dp), 3) == tfs.TFS_ERR_ARG
+    assert lib.tfs_set_soe(h, mu.ctypes.data_as(dp), w.ctypes.data_as(dp), 3) == tfs.TFS_OK
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_RE, 0.0) == tfs.TFS_ERR_ARG
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_EPS, -1.0) == tfs.TFS_ERR_ARG
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_STENCIL, 5.0) == tfs.TFS_ERR_ARG
+    assert lib.tfs_set_param(h, 99, 1.0) == tfs.TFS_ERR_ARG
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_EPS, 0.01) == tfs.TFS_OK
+    # velocity bound above the explicit-transport Courant limit is refused
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_UMAX, 1e6) == tfs.TFS_ERR_UNSTABLE
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_UMAX, 1e-3) == tfs.TFS_OK
+    # with transport off any bound is accepted
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_TRANSPORT, 0.0) == tfs.TFS_OK
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_UMAX, 1e6) == tfs.TFS_OK
+    lib.tfs_destroy(h)
+
+
+def test_calls_out_of_order_and_workspace(lib):
+    from paper_2411_17294_gb300 import tfs
+    rc, h = make(lib, dim=2, n=(16, 16), m=4, precision=0)
+    # no workspace bound yet: no device access happens
+    assert lib.tfs_step(h, ctypes.c_void_p(16), None, ctypes.c_void_p(16), None) == tfs.TFS_ERR_NOWORKSPACE
+    assert lib.tfs_set_state(h, None, None) == tfs.TFS_ERR_NOWORKSPACE
+    need = lib.tfs_workspace_bytes(h)
+    N, nc, m = 256, 3, 4
+    field = nc * N * 8
+    up = lambda b: (b + 255) // 256 * 256
+    assert need == 256 + 4 * up(field) + 2 * up(m * field)
+    assert lib.tfs_bind_workspace(h, ctypes.c_void_p(256 * 1000), need - 1) == tfs.TFS_ERR_NOWORKSPACE
+    assert lib.tfs_bind_workspace(h, ctypes.c_void_p(256 * 1000 + 8), need) == tfs.TFS_ERR_ARG
+    assert lib.tfs_bind_workspace(h, ctypes.c_void_p(256 * 1000), need) == tfs.TFS_OK
+    # bound but no state: refused before any launch
+    assert lib.tfs_step(h, ctypes.c_void_p(256), None, ctypes.c_void_p(256), None) == tfs.TFS_ERR_STATE
+    assert lib.tfs_step_index(h) == 0
+    assert lib.tfs_strerror(tfs.TFS_ERR_UNSTABLE).decode().startswith("velocity")
+    lib.tfs_destroy(h)
