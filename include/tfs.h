@@ -59,7 +59,8 @@ enum {
     TFS_OK = 0,
     TFS_ERR_ARG = 1,          /* invalid argument (size, range, NULL, alignment) */
     TFS_ERR_NOSOE = 2,        /* alpha < 1 and no SOE table set */
-    TFS_ERR_UNSTABLE = 3,     /* declared velocity bound exceeds the explicit-transport limit */
+    TFS_ERR_UNSTABLE = 3,     /* declared velocity bound exceeds the explicit-transport limit
+                                 (tfs_set_param(TFS_PARAM_UMAX) or, once the SOE is known, tfs_step) */
     TFS_ERR_CUDA = 4,         /* a CUDA runtime call failed */
     TFS_ERR_STATE = 5,        /* call out of order (no state set, adjoint not begun, ...) */
     TFS_ERR_NOWORKSPACE = 6,  /* no (or too small a) workspace bound */
@@ -79,7 +80,7 @@ enum {
     TFS_PARAM_EPS = 1,        /* centre-of-mass diffusion eps >= 0, default 0 */
     TFS_PARAM_STENCIL = 2,    /* TFS_STENCIL_*, default upwind3 */
     TFS_PARAM_TRANSPORT = 3,  /* 0: pointwise law (u ignored); 1: transport on (default 1) */
-    TFS_PARAM_UMAX = 4        /* declared bound on |u|_inf; checked against the Courant limit */
+    TFS_PARAM_UMAX = 4        /* declared bound U on |u_a|; checked against tfs_transport_limit */
 };
 
 enum { TFS_STENCIL_UPWIND3 = 0, TFS_STENCIL_CENTRAL2 = 1 };
@@ -88,7 +89,7 @@ enum { TFS_STENCIL_UPWIND3 = 0, TFS_STENCIL_CENTRAL2 = 1 };
 enum {
     TFS_FLAG_NONFINITE = 1u,  /* a new stress value was NaN or Inf */
     TFS_FLAG_SINGULAR = 2u,   /* a point system had a pivot below 1e-300 / relative 1e-14 */
-    TFS_FLAG_COURANT = 4u     /* a point exceeded the explicit-transport Courant limit */
+    TFS_FLAG_COURANT = 4u     /* a point had dt sum_a |u_a|/h_a above the limit of tfs_transport_limit */
 };
 
 typedef struct {
@@ -113,6 +114,13 @@ int tfs_set_param(tfs_handle h, int key, double value);
    Precomputes c_j = 1/(b0 + mu_j dt), rho_j = w_j dt c_j, eta_j = mu_j dt c_j
    and eta = b0 sum_j rho_j in FP64. */
 int tfs_set_soe(tfs_handle h, const double* mu, const double* w, int m);
+
+/* Largest velocity bound U (TFS_PARAM_UMAX) for which the explicit transport
+   is stable: dt U sum_a 1/h_a <= 0.9 lambda*, where lambda* is the first
+   crossing of the scheme's boundary locus by the stencil symbol (von Neumann
+   analysis of the step with the handle's SOE table; relaxation and kappa
+   ignored).  Requires the SOE when alpha < 1 (TFS_ERR_NOSOE).  Host only. */
+int tfs_transport_limit(tfs_handle h, double* umax_out);
 
 /* Bytes of device workspace the handle needs (stress ring, modes, status). */
 size_t tfs_workspace_bytes(tfs_handle h);

@@ -58,6 +58,9 @@ struct tfs_ctx {
     bool state_set = false;
     long long step = 0;
     cudaStream_t last_stream = nullptr;
+    // cached explicit-transport limit (invalidated by SOE and stencil changes)
+    bool lim_valid = false;
+    double lim = 0.0;
     // adjoint workspace
     char* aws = nullptr;
     size_t aws_bytes = 0;
@@ -81,14 +84,115 @@ double g_alpha(const tfs_ctx* h, long long step_index) {
     return std::pow(t, h->alpha - 1.0) / std::tgamma(h->alpha);
 }
 
-// Courant number of the explicit transport per unit velocity/grid-spacing:
-// C = dt^alpha / b0^alpha * sum_a |u_a| / h_a  (the fractional derivative
-// weights the transport like a time step dt^alpha / b0^alpha).
-double courant_coef(const tfs_ctx* h) { return std::pow(h->dt / kB0, h->alpha); }
+// Stability of the explicit transport.  For one Fourier mode with stencil
+// symbol s(theta) (D_h e^{i theta x/h} = s(theta)/h e^{i theta x/h}) and
+// lambda = dt |u| / h, the generating function of the scheme's recursion is
+//   (W(zeta) + lambda s(theta) zeta (2 - zeta)) y(zeta) = data,
+//   W(zeta) = delta(zeta) sum_j w_j dt / (delta(zeta) + mu_j dt)   (alpha < 1),
+//   W(zeta) = delta(zeta) = b0 + b1 zeta + b2 zeta^2               (alpha = 1).
+// W is analytic in the closed unit disk (the roots of delta + mu dt lie
+// outside it), so the step is stable while f = W + lambda s zeta (2 - zeta)
+// has no zero in the disk, i.e. while the winding number of f(e^{i phi}),
+// 0 <= phi < 2 pi, about 0 vanishes for every theta (argument principle).
+// stability_lambda() bisects for the largest such lambda.
+struct Cplx {
+    double re, im;
+};
+inline Cplx cadd(Cplx a, Cplx b) { return {a.re + b.re, a.im + b.im}; }
+inline Cplx csub(Cplx a, Cplx b) { return {a.re - b.re, a.im - b.im}; }
+inline Cplx cmul(Cplx a, Cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+inline Cplx cdiv(Cplx a, Cplx b) {
+    const double d = b.re * b.re + b.im * b.im;
+    return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+inline Cplx cexpi(double t) { return {std::cos(t), std::sin(t)}; }
 
-// Explicit-transport Courant limits from the von Neumann analysis of the
-// scheme (upwind3 / central2), see DESIGN notes in the test of the limit.
-double courant_limit(const tfs_ctx* h) { return h->stencil == TFS_STENCIL_CENTRAL2 ? 0.35 : 0.55; }
+Cplx stencil_symbol(int stencil, double theta) {
+    const Cplx e1 = cexpi(theta), em1 = cexpi(-theta), em2 = cexpi(-2 * theta);
+    if (stencil == TFS_STENCIL_CENTRAL2) return {0.5 * (e1.re - em1.re), 0.5 * (e1.im - em1.im)};
+    // (e^{-2it} - 6 e^{-it} + 3 + 2 e^{it}) / 6
+    return {(em2.re - 6 * em1.re + 3 + 2 * e1.re) / 6.0, (em2.im - 6 * em1.im + 2 * e1.im) / 6.0};
+}
+
+double stability_lambda(const tfs_ctx* h) {
+    // contour |zeta| = 1, refined geometrically towards phi = 0 (zeta = 1)
+    std::vector<double> phis;
+    const int nlin = 2048, nlog = 200;
+    for (int i = nlog; i >= 1; --i) phis.push_back(2 * M_PI / nlin * std::pow(1e-6, (double)i / nlog));
+    for (int i = 1; i < nlin; ++i) phis.push_back(2 * M_PI * (double)i / nlin);
+    for (int i = 1; i <= nlog; ++i) phis.push_back(2 * M_PI - 2 * M_PI / nlin * std::pow(1e-6, (double)i / nlog));
+    const size_t K = phis.size();
+    std::vector<Cplx> W(K), G(K);
+    for (size_t k = 0; k < K; ++k) {
+        const Cplx z = cexpi(phis[k]);
+        const Cplx delta = cadd(cadd(Cplx{kB0, 0.0}, cmul(Cplx{kB1, 0.0}, z)), cmul(Cplx{kB2, 0.0}, cmul(z, z)));
+        Cplx w{0.0, 0.0};
+        if (h->classic()) {
+            w = delta;
+        } else {
+            for (int j = 0; j < h->m; ++j)
+                w = cadd(w, cdiv(Cplx{h->w[j] * h->dt, 0.0}, cadd(delta, Cplx{h->mu[j] * h->dt, 0.0})));
+            w = cmul(w, delta);
+        }
+        W[k] = w;
+        G[k] = cmul(z, csub(Cplx{2.0, 0.0}, z));
+    }
+    const int nth = 240;
+    std::vector<Cplx> S;
+    for (int t = 1; t < nth; ++t) S.push_back(stencil_symbol(h->stencil, 2 * M_PI * t / nth));
+    auto stable = [&](double lam) {
+        for (const Cplx& sv : S) {
+            const Cplx ls{lam * sv.re, lam * sv.im};
+            double wind = 0.0;
+            Cplx prev = cadd(W[K - 1], cmul(ls, G[K - 1]));
+            for (size_t k = 0; k < K; ++k) {
+                const Cplx f = cadd(W[k], cmul(ls, G[k]));
+                const Cplx r = cdiv(f, prev);
+                wind += std::atan2(r.im, r.re);
+                prev = f;
+            }
+            if (std::fabs(wind) > M_PI) return false;   // winding number != 0
+        }
+        return true;
+    };
+    double lo = 1e-12, hi = 1e-6;
+    if (!stable(lo)) return 0.0;
+    while (stable(hi) && hi < 1e6) {
+        lo = hi;
+        hi *= 2.0;
+    }
+    for (int it = 0; it < 50 && hi - lo > 1e-7 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (stable(mid)) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Velocity-independent part of the Courant check: the kernel flags points
+// with dt * sum_a |u_a| / h_a above `limit`, the library refuses a declared
+// bound above it.  0.9 x the boundary-locus value leaves a margin.
+double courant_coef(const tfs_ctx* h) { return h->dt; }
+
+double courant_limit(tfs_ctx* h) {
+    if (!h->classic() && !h->soe_set) return 1e300;   // not known yet
+    if (!h->lim_valid) {
+        h->lim = 0.9 * stability_lambda(h);
+        h->lim_valid = true;
+    }
+    return h->lim;
+}
+
+double sum_inv_h(const tfs_ctx* h) {
+    double s = 0.0;
+    for (int a = 0; a < h->dim; ++a) s += (double)h->n[a] / h->L[a];
+    return s;
+}
+
+// declared velocity bound exceeds the limit (transport on, limit known)
+bool umax_unstable(tfs_ctx* h) {
+    return h->transport && h->umax >= 0.0 && courant_coef(h) * h->umax * sum_inv_h(h) > courant_limit(h);
+}
 
 void layout_forward(tfs_ctx* h, char* base) {
     char* p = base;
@@ -111,7 +215,7 @@ size_t forward_bytes(const tfs_ctx* h) {
 }
 
 template <typename T>
-void fill_common(const tfs_ctx* h, FwdArgs<T>& a) {
+void fill_common(tfs_ctx* h, FwdArgs<T>& a) {
     a.N = h->N;
     a.n0 = (int)h->n[0];
     a.n1 = (int)h->n[1];
@@ -145,6 +249,7 @@ int do_step(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* s
     if (!h->classic() && !h->soe_set) return TFS_ERR_NOSOE;
     if (!kn) return TFS_ERR_ARG;
     if (h->transport && !u) return TFS_ERR_ARG;
+    if (umax_unstable(h)) return TFS_ERR_UNSTABLE;
     if (!knm1) knm1 = kn;
     const int nxt = h->third_sig();
     const int cm = h->cur_mode, pm = 1 - h->cur_mode;
@@ -251,6 +356,7 @@ int tfs_set_param(tfs_handle h, int key, double value) {
         case TFS_PARAM_STENCIL:
             if (value != TFS_STENCIL_UPWIND3 && value != TFS_STENCIL_CENTRAL2) return TFS_ERR_ARG;
             h->stencil = (int)value;
+            h->lim_valid = false;
             return TFS_OK;
         case TFS_PARAM_TRANSPORT:
             if (value != 0.0 && value != 1.0) return TFS_ERR_ARG;
@@ -258,9 +364,7 @@ int tfs_set_param(tfs_handle h, int key, double value) {
             return TFS_OK;
         case TFS_PARAM_UMAX: {
             if (!(value >= 0.0)) return TFS_ERR_ARG;
-            double sum_ih = 0.0;
-            for (int a = 0; a < h->dim; ++a) sum_ih += (double)h->n[a] / h->L[a];
-            if (h->transport && courant_coef(h) * value * sum_ih > courant_limit(h)) return TFS_ERR_UNSTABLE;
+            if (h->transport && courant_coef(h) * value * sum_inv_h(h) > courant_limit(h)) return TFS_ERR_UNSTABLE;
             h->umax = value;
             return TFS_OK;
         }
@@ -297,6 +401,14 @@ int tfs_set_soe(tfs_handle h, const double* mu, const double* w, int m) {
     }
     h->eta = eta;
     h->soe_set = true;
+    h->lim_valid = false;
+    return TFS_OK;
+}
+
+int tfs_transport_limit(tfs_handle h, double* umax_out) {
+    if (!valid_handle(h) || !umax_out) return TFS_ERR_ARG;
+    if (!h->classic() && !h->soe_set) return TFS_ERR_NOSOE;
+    *umax_out = courant_limit(h) / (courant_coef(h) * sum_inv_h(h));
     return TFS_OK;
 }
 

@@ -24,7 +24,7 @@ TFS_STENCIL_UPWIND3, TFS_STENCIL_CENTRAL2 = 0, 1
 TFS_FLAG_NONFINITE, TFS_FLAG_SINGULAR, TFS_FLAG_COURANT = 1, 2, 4
 
 EXPORTS = [
-    "tfs_create", "tfs_set_param", "tfs_set_soe", "tfs_workspace_bytes", "tfs_bind_workspace",
+    "tfs_create", "tfs_set_param", "tfs_set_soe", "tfs_transport_limit", "tfs_workspace_bytes", "tfs_bind_workspace",
     "tfs_set_state", "tfs_step", "tfs_get_stress", "tfs_step_index", "tfs_checkpoint_bytes", "tfs_save",
     "tfs_load", "tfs_adjoint_workspace_bytes", "tfs_bind_adjoint_workspace", "tfs_backward", "tfs_status",
     "tfs_strerror", "tfs_destroy",
@@ -60,6 +60,7 @@ def load_library(path: str | None = None):
                                       ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int]),
         "tfs_set_param": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_double]),
         "tfs_set_soe": (ctypes.c_int, [H, dp, dp, ctypes.c_int]),
+        "tfs_transport_limit": (ctypes.c_int, [H, dp]),
         "tfs_workspace_bytes": (sz, [H]),
         "tfs_bind_workspace": (ctypes.c_int, [H, vp, sz]),
         "tfs_set_state": (ctypes.c_int, [H, vp, vp]),
@@ -163,6 +164,12 @@ class Solver:
         w = np.ascontiguousarray(w, dtype=np.float64)
         dp = ctypes.POINTER(ctypes.c_double)
         check(self.lib.tfs_set_soe(self.h, mu.ctypes.data_as(dp), w.ctypes.data_as(dp), len(mu)), "tfs_set_soe")
+
+    def transport_limit(self) -> float:
+        """Largest stable velocity bound U (see tfs_transport_limit)."""
+        v = ctypes.c_double(0.0)
+        check(self.lib.tfs_transport_limit(self.h, ctypes.byref(v)), "tfs_transport_limit")
+        return v.value
 
     def _field(self, t, rows):
         if t is None:

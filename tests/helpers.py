@@ -66,6 +66,24 @@ def run_oracle(case: dict, sigma0, kap_seq, u, steps: int):
     return o.run(steps, kap_seq, u)
 
 
+def courant(case: dict, u) -> float:
+    """C = (dt/b0)^alpha * max_p sum_a |u_a(p)| / h_a, the explicit-transport
+    Courant number the library checks."""
+    n = case["n"]
+    L = case.get("L") or [2 * np.pi] * case["dim"]
+    inv_h = np.array([n[a] / L[a] for a in range(case["dim"])])
+    coef = (case["dt"] / 1.5) ** case["alpha"]
+    return float(coef * np.max(np.abs(np.asarray(u)).T @ inv_h))
+
+
+def stable_velocity(case: dict, u, target: float = 0.15):
+    """Scale u so that the case stays inside the explicit-transport stability
+    region (parity needs a stable recurrence: unstable modes amplify rounding
+    differences exponentially)."""
+    c = courant(case, u)
+    return u if c <= target else np.asarray(u) * (target / c)
+
+
 def spectral_case(dim, n, seed, kmax=None):
     kmax = kmax or max(1, min(n) // 3)
     u, kap = inputs.spectral_velocity(dim, n, kmax, seed)

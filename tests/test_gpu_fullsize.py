@@ -1,0 +1,99 @@
+"""Parity at the workload sizes, in the launch configuration the benchmark
+times, on sampled outputs the oracle computes one by one.
+
+3D 256^3 (m = 32, FP32 + compensated sum, alpha = 0.6, Wi = 2, beta = 0.9,
+dt = 2e-4, spectral velocity |k| <= 24 at unit RMS, transport on): a few steps;
+the stress at a sampled point after s steps depends only on the points within
+2 s grid cells (radius-2 stencil), so the oracle runs on the periodic
+(4 s + 1)^3 block centred on each sample and its centre value is exact.
+
+2D 1024^2 (m = 32, FP32, dt = 5e-4, alpha in {0.3, 0.5, 0.8}): the
+explicit transport is outside its stability region at these sizes, so these
+cases run the pointwise law (transport off) for many steps; the oracle then
+runs on the sampled points alone.
+"""
+import numpy as np
+import pytest
+
+from helpers import ensure_lib, rel_err_per_component
+from oracle import orc
+from oracle import soe as osoe
+from paper_2411_17294_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ensure_lib()
+
+
+def test_3d_256_bench_configuration_sampled():
+    import torch
+    from paper_2411_17294_gb300 import tfs
+    n, m, alpha, Wi, beta, dt, steps = (256, 256, 256), 32, 0.6, 2.0, 0.9, 2e-4, 3
+    mu, w = osoe.soe_nnls(alpha, dt, 200 * dt, m)
+    dev = torch.device("cuda", 0)
+    u, kap = inputs.spectral_velocity(3, n, 24, 3, device=dev)
+    s = tfs.Solver(3, n, alpha, Wi, beta, dt, m=m, precision=tfs.TFS_FP32, mu=mu, w=w, transport=True)
+    kt = torch.as_tensor(kap, dtype=torch.float32, device=dev).contiguous()
+    k2 = kt.clone()
+    ut = torch.as_tensor(u, dtype=torch.float32, device=dev).contiguous()
+    s.set_state(None)
+    for _ in range(steps):
+        s.step(kt, k2, ut)
+    out = s.stress().cpu().numpy().astype(np.float64)
+    s.close()
+    # the oracle sees the same (float-rounded) inputs
+    kap32 = kt.cpu().numpy().astype(np.float64)
+    u32 = ut.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(2024)
+    R = 2 * steps
+    B = 2 * R + 1
+    samples = [tuple(int(v) for v in rng.integers(0, 256, size=3)) for _ in range(12)] + [(0, 0, 0), (255, 255, 255)]
+    got, ref = [], []
+    L = 2 * np.pi
+    for (x, y, z) in samples:
+        xs = (np.arange(x - R, x + R + 1) % 256)
+        ys = (np.arange(y - R, y + R + 1) % 256)
+        zs = (np.arange(z - R, z + R + 1) % 256)
+        idx = (xs[None, None, :] + 256 * (ys[None, :, None] + 256 * zs[:, None, None])).ravel()
+        prob = orc.Problem(dim=3, n=(B, B, B), alpha=alpha, Wi=Wi, beta=beta, dt=dt, mu=mu, w=w, transport=True,
+                           L=(L * B / 256,) * 3)
+        o = orc.Oracle(prob)
+        kb = np.ascontiguousarray(kap32[:, idx])
+        ub = np.ascontiguousarray(u32[:, idx])
+        o.run(steps, kb, ub)
+        centre = R + B * (R + B * R)
+        ref.append(o.sig_n[:, centre])
+        got.append(out[:, x + 256 * (y + 256 * z)])
+    got = np.array(got).T
+    ref = np.array(ref).T
+    assert np.max(np.abs(ref)) > 0
+    assert np.all(rel_err_per_component(got, ref) < 2e-5)
+
+
+@pytest.mark.parametrize("alpha", [0.3, 0.5, 0.8])
+def test_2d_1024_pointwise_sampled(alpha):
+    import torch
+    from paper_2411_17294_gb300 import tfs
+    n, m, Wi, beta, dt, steps = (1024, 1024), 32, 1.0, 0.5, 5e-4, 300
+    mu, w = osoe.soe_nnls(alpha, dt, 1000 * dt, m)
+    dev = torch.device("cuda", 0)
+    u, kap = inputs.spectral_velocity(2, n, 32, 2, device=dev)
+    kap = 0.05 * kap      # keep the pointwise stress moderate over the run
+    s = tfs.Solver(2, n, alpha, Wi, beta, dt, m=m, precision=tfs.TFS_FP32, mu=mu, w=w, transport=False)
+    kt = torch.as_tensor(kap, dtype=torch.float32, device=dev).contiguous()
+    sig0 = inputs.random_stress(2, n, 5, amplitude=0.5)
+    s.set_state(torch.as_tensor(sig0, dtype=torch.float32, device=dev))
+    for _ in range(steps):
+        s.step(kt, kt, None)
+    out = s.stress().cpu().numpy().astype(np.float64)
+    s.close()
+    rng = np.random.default_rng(7)
+    pts = np.unique(np.concatenate([rng.integers(0, 1024 * 1024, size=64), [0, 1024 * 1024 - 1]]))
+    kap32 = kt.cpu().numpy().astype(np.float64)[:, pts]
+    sig032 = sig0.astype(np.float32).astype(np.float64)[:, pts]
+    prob = orc.Problem(dim=2, n=(len(pts), 1), alpha=alpha, Wi=Wi, beta=beta, dt=dt, mu=mu, w=w)
+    ref = orc.forward(prob, sig032, np.ascontiguousarray(kap32), None, steps)
+    assert np.all(rel_err_per_component(out[:, pts], ref) < 2e-5)

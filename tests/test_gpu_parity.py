@@ -11,7 +11,7 @@ import math
 import numpy as np
 import pytest
 
-from helpers import ensure_lib, rel_err_per_component, run_gpu, run_oracle
+from helpers import courant, ensure_lib, rel_err_per_component, run_gpu, run_oracle, stable_velocity
 from oracle import soe
 from paper_2411_17294_gb300 import inputs
 
@@ -38,6 +38,7 @@ def taylor_green_case():
     # dt = 1e-3, 100 steps, Taylor-Green gradient plus N(0, 1e-3) noise, sigma0 = 0
     c = case_dict(2, (64, 64), 0.5, 1.0, 0.5, 1e-3, 16, 1.0, transport=True)
     u, kap = inputs.taylor_green((64, 64), seed=1)
+    assert courant(c, u) < 0.25          # inside the upwind3 stability region as given
     return c, u, kap
 
 
@@ -84,6 +85,7 @@ def test_ragged_and_degenerate_grids(dim, n, alpha, m, transport, eps, stencil, 
     if kap is None:
         kap = rng.normal(size=(dim * dim, N))
         u = rng.normal(size=(dim, N))
+    u = stable_velocity(c, u)
     sigma0 = inputs.random_stress(dim, n, seed=8)
     ref = run_oracle(c, sigma0, kap, u if transport else None, steps)
     got = run_gpu(c, sigma0, kap, u if transport else None, steps, precision=precision)
@@ -98,6 +100,7 @@ def test_time_dependent_gradient_and_first_step(precision):
     dim, n, steps, dt = 3, (9, 8, 7), 25, 1e-3
     c = case_dict(dim, n, 0.4, 0.9, 0.2, dt, 10, steps * dt, transport=True, eps=0.01)
     u, k0 = inputs.spectral_velocity(dim, n, 3, seed=5)
+    u = stable_velocity(c, u)
 
     def kap(nn):
         return k0 * (1.0 + 0.3 * math.sin(0.7 * nn)) + 0.1 * nn / steps
