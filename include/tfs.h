@@ -105,7 +105,9 @@ typedef struct {
 int tfs_create(tfs_handle* h, const tfs_grid* grid, double alpha, double Wi, double beta,
                int m, double dt, int precision);
 
-/* Set an optional parameter (TFS_PARAM_*).  Re > 0, eps >= 0, umax >= 0. */
+/* Set an optional parameter (TFS_PARAM_*).  Re > 0, eps >= 0, umax >= 0.
+   With transport on and the SOE known, an eps or umax beyond the stability
+   limit of tfs_transport_limit returns TFS_ERR_UNSTABLE (and is not set). */
 int tfs_set_param(tfs_handle h, int key, double value);
 
 /* Copy the SOE table: exponents mu_j >= 0 and weights w_j >= 0 (finite),
@@ -116,10 +118,13 @@ int tfs_set_param(tfs_handle h, int key, double value);
 int tfs_set_soe(tfs_handle h, const double* mu, const double* w, int m);
 
 /* Largest velocity bound U (TFS_PARAM_UMAX) for which the explicit transport
-   is stable: dt U sum_a 1/h_a <= 0.9 lambda*, where lambda* is the first
-   crossing of the scheme's boundary locus by the stencil symbol (von Neumann
-   analysis of the step with the handle's SOE table; relaxation and kappa
-   ignored).  Requires the SOE when alpha < 1 (TFS_ERR_NOSOE).  Host only. */
+   is stable.  From a von Neumann analysis of the step with the handle's SOE
+   table (relaxation and kappa ignored): lambda* is the largest dt|u|/h for
+   which the stencil symbol keeps the step's characteristic function free of
+   zeros in the unit disk, z* the same for the diffusion symbol; the step is
+   accepted while dt U sum_a 1/h_a / lambda* + 4 eps dt sum_a 1/h_a^2 / z* <= 0.9.
+   Returns U >= 0 (0 when eps alone uses the whole margin).  Requires the SOE
+   when alpha < 1 (TFS_ERR_NOSOE).  Host only; computed once per SOE/stencil. */
 int tfs_transport_limit(tfs_handle h, double* umax_out);
 
 /* Bytes of device workspace the handle needs (stress ring, modes, status). */

@@ -58,9 +58,10 @@ struct tfs_ctx {
     bool state_set = false;
     long long step = 0;
     cudaStream_t last_stream = nullptr;
-    // cached explicit-transport limit (invalidated by SOE and stencil changes)
+    // cached stability bounds of the explicit transport (invalidated by SOE and stencil changes)
     bool lim_valid = false;
-    double lim = 0.0;
+    double lam_star = 0.0;   // advection: largest stable dt |u| / h (1D)
+    double z_star = 0.0;     // diffusion: largest stable 4 eps dt / h^2 (1D)
     // adjoint workspace
     char* aws = nullptr;
     size_t aws_bytes = 0;
@@ -94,7 +95,7 @@ double g_alpha(const tfs_ctx* h, long long step_index) {
 // outside it), so the step is stable while f = W + lambda s zeta (2 - zeta)
 // has no zero in the disk, i.e. while the winding number of f(e^{i phi}),
 // 0 <= phi < 2 pi, about 0 vanishes for every theta (argument principle).
-// stability_lambda() bisects for the largest such lambda.
+// stability_bound() bisects for the largest such lambda along given directions.
 struct Cplx {
     double re, im;
 };
@@ -114,7 +115,9 @@ Cplx stencil_symbol(int stencil, double theta) {
     return {(em2.re - 6 * em1.re + 3 + 2 * e1.re) / 6.0, (em2.im - 6 * em1.im + 2 * e1.im) / 6.0};
 }
 
-double stability_lambda(const tfs_ctx* h) {
+// Largest t such that f = W + t d zeta (2 - zeta) keeps winding number 0 about
+// the origin on |zeta| = 1 for every direction d in `dirs` (bisection).
+double stability_bound(const tfs_ctx* h, const std::vector<Cplx>& dirs) {
     // contour |zeta| = 1, refined geometrically towards phi = 0 (zeta = 1)
     std::vector<double> phis;
     const int nlin = 2048, nlog = 200;
@@ -137,12 +140,9 @@ double stability_lambda(const tfs_ctx* h) {
         W[k] = w;
         G[k] = cmul(z, csub(Cplx{2.0, 0.0}, z));
     }
-    const int nth = 240;
-    std::vector<Cplx> S;
-    for (int t = 1; t < nth; ++t) S.push_back(stencil_symbol(h->stencil, 2 * M_PI * t / nth));
-    auto stable = [&](double lam) {
-        for (const Cplx& sv : S) {
-            const Cplx ls{lam * sv.re, lam * sv.im};
+    auto stable = [&](double t) {
+        for (const Cplx& sv : dirs) {
+            const Cplx ls{t * sv.re, t * sv.im};
             double wind = 0.0;
             Cplx prev = cadd(W[K - 1], cmul(ls, G[K - 1]));
             for (size_t k = 0; k < K; ++k) {
@@ -169,18 +169,22 @@ double stability_lambda(const tfs_ctx* h) {
     return lo;
 }
 
-// Velocity-independent part of the Courant check: the kernel flags points
-// with dt * sum_a |u_a| / h_a above `limit`, the library refuses a declared
-// bound above it.  0.9 x the boundary-locus value leaves a margin.
-double courant_coef(const tfs_ctx* h) { return h->dt; }
+// Courant check.  With lambda_tot = dt sum_a |u_a|/h_a and nu_tot = eps dt sum_a 1/h_a^2
+// the step is accepted while lambda_tot / lambda* + 4 nu_tot / z* <= 0.9, where
+// lambda* bounds the advection symbol (directions s(theta)) and z* the
+// diffusion symbol 4 nu sin^2(theta/2) (direction +1): 10% margin on the sum of
+// the two fractions of the stable region.  The kernel flags points with
+// courant_coef * sum_a |u_a| / h_a > courant_limit.
+bool limits_known(const tfs_ctx* h) { return h->classic() || h->soe_set; }
 
-double courant_limit(tfs_ctx* h) {
-    if (!h->classic() && !h->soe_set) return 1e300;   // not known yet
-    if (!h->lim_valid) {
-        h->lim = 0.9 * stability_lambda(h);
-        h->lim_valid = true;
-    }
-    return h->lim;
+void ensure_limits(tfs_ctx* h) {
+    if (h->lim_valid) return;
+    const int nth = 240;
+    std::vector<Cplx> S;
+    for (int t = 1; t < nth; ++t) S.push_back(stencil_symbol(h->stencil, 2 * M_PI * t / nth));
+    h->lam_star = stability_bound(h, S);
+    h->z_star = stability_bound(h, std::vector<Cplx>{Cplx{1.0, 0.0}});
+    h->lim_valid = true;
 }
 
 double sum_inv_h(const tfs_ctx* h) {
@@ -189,9 +193,37 @@ double sum_inv_h(const tfs_ctx* h) {
     return s;
 }
 
-// declared velocity bound exceeds the limit (transport on, limit known)
-bool umax_unstable(tfs_ctx* h) {
-    return h->transport && h->umax >= 0.0 && courant_coef(h) * h->umax * sum_inv_h(h) > courant_limit(h);
+double sum_inv_h2(const tfs_ctx* h) {
+    double s = 0.0;
+    for (int a = 0; a < h->dim; ++a) s += ((double)h->n[a] / h->L[a]) * ((double)h->n[a] / h->L[a]);
+    return s;
+}
+
+// fraction of the stable region taken by the explicit diffusion term
+double diffusion_fraction(tfs_ctx* h, double eps) {
+    if (eps == 0.0 || !limits_known(h)) return 0.0;
+    ensure_limits(h);
+    if (!(h->z_star > 0.0)) return 1e300;
+    return 4.0 * eps * h->dt * sum_inv_h2(h) / h->z_star;
+}
+
+double courant_coef(tfs_ctx* h) {
+    if (!limits_known(h)) return 0.0;
+    ensure_limits(h);
+    return h->lam_star > 0.0 ? h->dt / h->lam_star : 1e300;
+}
+
+double courant_limit(tfs_ctx* h) {
+    if (!limits_known(h)) return 1e300;
+    return 0.9 - diffusion_fraction(h, h->eps);
+}
+
+// declared bounds (eps, and umax when given) exceed the limit
+bool limits_violated(tfs_ctx* h) {
+    if (!h->transport || !limits_known(h)) return false;
+    const double lim = courant_limit(h);
+    if (lim < 0.0) return true;
+    return h->umax >= 0.0 && courant_coef(h) * h->umax * sum_inv_h(h) > lim;
 }
 
 void layout_forward(tfs_ctx* h, char* base) {
@@ -227,7 +259,7 @@ void fill_common(tfs_ctx* h, FwdArgs<T>& a) {
     a.G = (1.0 - h->beta) / (h->Wi * h->Re);
     a.eps = h->eps;
     for (int i = 0; i < 3; ++i) a.inv_h[i] = (double)h->n[i] / h->L[i];
-    a.courant_coef = (h->transport ? courant_coef(h) : 0.0);
+    a.courant_coef = (h->transport && limits_known(h)) ? courant_coef(h) : 0.0;
     a.courant_limit = courant_limit(h);
     a.flags = h->flags;
 }
@@ -249,7 +281,7 @@ int do_step(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* s
     if (!h->classic() && !h->soe_set) return TFS_ERR_NOSOE;
     if (!kn) return TFS_ERR_ARG;
     if (h->transport && !u) return TFS_ERR_ARG;
-    if (umax_unstable(h)) return TFS_ERR_UNSTABLE;
+    if (limits_violated(h)) return TFS_ERR_UNSTABLE;
     if (!knm1) knm1 = kn;
     const int nxt = h->third_sig();
     const int cm = h->cur_mode, pm = 1 - h->cur_mode;
@@ -351,6 +383,7 @@ int tfs_set_param(tfs_handle h, int key, double value) {
             return TFS_OK;
         case TFS_PARAM_EPS:
             if (!(value >= 0.0)) return TFS_ERR_ARG;
+            if (h->transport && diffusion_fraction(h, value) > 0.9) return TFS_ERR_UNSTABLE;
             h->eps = value;
             return TFS_OK;
         case TFS_PARAM_STENCIL:
@@ -364,7 +397,8 @@ int tfs_set_param(tfs_handle h, int key, double value) {
             return TFS_OK;
         case TFS_PARAM_UMAX: {
             if (!(value >= 0.0)) return TFS_ERR_ARG;
-            if (h->transport && courant_coef(h) * value * sum_inv_h(h) > courant_limit(h)) return TFS_ERR_UNSTABLE;
+            if (h->transport && limits_known(h) && courant_coef(h) * value * sum_inv_h(h) > courant_limit(h))
+                return TFS_ERR_UNSTABLE;
             h->umax = value;
             return TFS_OK;
         }
@@ -408,7 +442,8 @@ int tfs_set_soe(tfs_handle h, const double* mu, const double* w, int m) {
 int tfs_transport_limit(tfs_handle h, double* umax_out) {
     if (!valid_handle(h) || !umax_out) return TFS_ERR_ARG;
     if (!h->classic() && !h->soe_set) return TFS_ERR_NOSOE;
-    *umax_out = courant_limit(h) / (courant_coef(h) * sum_inv_h(h));
+    const double lim = courant_limit(h);
+    *umax_out = lim > 0.0 ? lim / (courant_coef(h) * sum_inv_h(h)) : 0.0;
     return TFS_OK;
 }
 

@@ -66,21 +66,49 @@ def run_oracle(case: dict, sigma0, kap_seq, u, steps: int):
     return o.run(steps, kap_seq, u)
 
 
-def courant(case: dict, u) -> float:
-    """C = (dt/b0)^alpha * max_p sum_a |u_a(p)| / h_a, the explicit-transport
-    Courant number the library checks."""
+def transport_limit(case: dict) -> float:
+    """tfs_transport_limit for the case (host-only calls of the C ABI)."""
+    import ctypes
+    import math
+    ensure_lib()
+    from paper_2411_17294_gb300 import tfs
+    lib = tfs.load_library()
+    g = tfs.TfsGrid()
+    g.dim = case["dim"]
+    L = case.get("L") or [2 * math.pi] * case["dim"]
+    for a in range(3):
+        g.n[a] = case["n"][a] if a < case["dim"] else 1
+        g.L[a] = L[a] if a < case["dim"] else 1.0
+    h = ctypes.c_void_p()
+    m = len(case.get("mu", [])) if case["alpha"] < 1 else 0
+    tfs.check(lib.tfs_create(ctypes.byref(h), ctypes.byref(g), case["alpha"], 1.0, 0.5, m, case["dt"], 0), "create")
+    tfs.check(lib.tfs_set_param(h, tfs.TFS_PARAM_STENCIL, float(case.get("stencil", 0))), "stencil")
+    if m:
+        dp = ctypes.POINTER(ctypes.c_double)
+        mu = np.ascontiguousarray(case["mu"], dtype=np.float64)
+        w = np.ascontiguousarray(case["w"], dtype=np.float64)
+        tfs.check(lib.tfs_set_soe(h, mu.ctypes.data_as(dp), w.ctypes.data_as(dp), m), "soe")
+    tfs.check(lib.tfs_set_param(h, tfs.TFS_PARAM_EPS, float(case.get("eps", 0.0))), "eps")
+    U = ctypes.c_double(0.0)
+    tfs.check(lib.tfs_transport_limit(h, ctypes.byref(U)), "limit")
+    lib.tfs_destroy(h)
+    return U.value
+
+
+def courant_fraction(case: dict, u) -> float:
+    """max_p sum_a |u_a(p)|/h_a over U sum_a 1/h_a: the fraction of the
+    library's velocity limit that the field uses (flagged above 1)."""
     n = case["n"]
     L = case.get("L") or [2 * np.pi] * case["dim"]
     inv_h = np.array([n[a] / L[a] for a in range(case["dim"])])
-    coef = (case["dt"] / 1.5) ** case["alpha"]
-    return float(coef * np.max(np.abs(np.asarray(u)).T @ inv_h))
+    return float(np.max(np.abs(np.asarray(u)).T @ inv_h) / (transport_limit(case) * inv_h.sum()))
 
 
-def stable_velocity(case: dict, u, target: float = 0.15):
-    """Scale u so that the case stays inside the explicit-transport stability
-    region (parity needs a stable recurrence: unstable modes amplify rounding
-    differences exponentially)."""
-    c = courant(case, u)
+def stable_velocity(case: dict, u, target: float = 0.5):
+    """Scale u to use at most `target` of the library's explicit-transport
+    velocity limit (parity needs a stable recurrence: unstable modes amplify
+    rounding differences exponentially)."""
+    c = courant_fraction(case, u)
     return u if c <= target else np.asarray(u) * (target / c)
 
 

@@ -16,12 +16,10 @@ def _lib():
     ensure_lib()
 
 
-def gpu_gradients(dim, n, alpha, Wi, beta, dt, m, steps, K, sigma0, kap, u, dJ, precision, transport, eps=0.0):
+def gpu_gradients(dim, n, alpha, Wi, beta, dt, m, steps, K, sigma0, kap, u, dJ, precision, transport, mu, w,
+                  eps=0.0):
     import torch
     from paper_2411_17294_gb300 import tfs
-    mu = w = None
-    if alpha < 1:
-        mu, w = soe.soe_nnls(alpha, dt, steps * dt, m)
     s = tfs.Solver(dim, n, alpha, Wi, beta, dt, m=m if alpha < 1 else 0, precision=precision, mu=mu, w=w,
                    transport=transport, eps=eps)
     dt_ = s.dtype
@@ -58,14 +56,18 @@ def test_adjoint_matches_oracle(dim, n, alpha, m, steps, K, transport, eps, prec
     Wi, beta, dt = 1.3, 0.4, 2e-3
     N = int(np.prod(n))
     u, kap = inputs.spectral_velocity(dim, n, 2, seed=12)
-    case = dict(dim=dim, n=n, alpha=alpha, dt=dt)
+    mu = w = None
+    case = dict(dim=dim, n=n, alpha=alpha, dt=dt, eps=eps)
+    if alpha < 1:
+        mu, w = soe.soe_nnls(alpha, dt, steps * dt, m)
+        case.update(mu=mu, w=w)
     u = stable_velocity(case, u)
     sigma0 = inputs.random_stress(dim, n, 13)
     rng = np.random.default_rng(14)
     target = rng.normal(size=sigma0.shape)
     dJ = lambda sT: 2.0 * (sT - target)
     got, mu, w = gpu_gradients(dim, n, alpha, Wi, beta, dt, m, steps, K, sigma0, kap, u, dJ, precision,
-                               transport, eps)
+                               transport, mu, w, eps)
     p = orc.Problem(dim=dim, n=n, alpha=alpha, Wi=Wi, beta=beta, dt=dt,
                     mu=mu if mu is not None else np.zeros(0), w=w if w is not None else np.zeros(0),
                     transport=transport, eps=eps)

@@ -11,7 +11,7 @@ import math
 import numpy as np
 import pytest
 
-from helpers import courant, ensure_lib, rel_err_per_component, run_gpu, run_oracle, stable_velocity
+from helpers import courant_fraction, ensure_lib, rel_err_per_component, run_gpu, run_oracle, stable_velocity
 from oracle import soe
 from paper_2411_17294_gb300 import inputs
 
@@ -29,7 +29,9 @@ def _lib():
 def case_dict(dim, n, alpha, Wi, beta, dt, m, T, transport, eps=0.0, stencil=0, L=None):
     c = dict(dim=dim, n=n, alpha=alpha, Wi=Wi, beta=beta, dt=dt, transport=transport, eps=eps, stencil=stencil, L=L)
     if alpha < 1:
-        c["mu"], c["w"] = soe.soe_nnls(alpha, dt, T, m)
+        # the NNLS builder reaches exactly m positive terms up to m = 48; beyond,
+        # a trapezoidal table (positive, less accurate) serves parity just as well
+        c["mu"], c["w"] = soe.soe_nnls(alpha, dt, T, m) if m <= 48 else soe.soe_expquad(alpha, dt, T, m)
     return c
 
 
@@ -38,7 +40,7 @@ def taylor_green_case():
     # dt = 1e-3, 100 steps, Taylor-Green gradient plus N(0, 1e-3) noise, sigma0 = 0
     c = case_dict(2, (64, 64), 0.5, 1.0, 0.5, 1e-3, 16, 1.0, transport=True)
     u, kap = inputs.taylor_green((64, 64), seed=1)
-    assert courant(c, u) < 0.25          # inside the upwind3 stability region as given
+    assert courant_fraction(c, u) < 1.0   # inside the explicit-transport stability region as given
     return c, u, kap
 
 
@@ -61,7 +63,7 @@ def test_taylor_green_64_fp32(precision):
 RAGGED = [
     # dim, n, alpha, m, transport, eps, stencil
     (3, (7, 5, 9), 0.6, 8, True, 0.0, 0),
-    (3, (33, 3, 2), 0.3, 12, True, 0.05, 0),
+    (3, (33, 3, 2), 0.3, 12, True, 0.01, 0),
     (2, (37, 29), 0.8, 20, True, 0.02, 1),
     (2, (1, 1), 0.5, 5, False, 0.0, 0),
     (3, (1, 2, 1), 0.7, 3, True, 0.0, 0),

@@ -128,3 +128,43 @@ def test_central2_alpha1_unstable():
     lam = library_lambda(1, 1.0, 2e-4, 0, None)
     assert lam < 0.02
     assert radius(1.0, 2e-4, 0, 1, 0.05) > 1 + 1e-6
+
+
+def test_explicit_diffusion_bound():
+    # eps alone: accepted while 4 eps dt sum_a 1/h_a^2 <= 0.9 z*; the eigenvalues of
+    # the recurrence with the diffusion symbol z = 4 nu sin^2(theta/2) confirm z*
+    ensure_lib()
+    from paper_2411_17294_gb300 import tfs
+    lib = tfs.load_library()
+    alpha, dt, m = 0.3, 2e-3, 12
+    mu, w = soe.soe_nnls(alpha, dt, 200 * dt, m)
+    g = tfs.TfsGrid()
+    g.dim = 2
+    for a in range(3):
+        g.n[a] = 64 if a < 2 else 1
+        g.L[a] = 2 * math.pi
+    h = ctypes.c_void_p()
+    assert lib.tfs_create(ctypes.byref(h), ctypes.byref(g), alpha, 1.0, 0.5, m, dt, 1) == 0
+    dp = ctypes.POINTER(ctypes.c_double)
+    mu_c, w_c = np.ascontiguousarray(mu), np.ascontiguousarray(w)
+    assert lib.tfs_set_soe(h, mu_c.ctypes.data_as(dp), w_c.ctypes.data_as(dp), m) == 0
+    lo, hi = 0.0, 10.0
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if lib.tfs_set_param(h, tfs.TFS_PARAM_EPS, mid) == tfs.TFS_OK:
+            lo = mid
+        else:
+            hi = mid
+    U = ctypes.c_double(1.0)
+    assert lib.tfs_transport_limit(h, ctypes.byref(U)) == 0
+    assert U.value < 1e-6 * (1 + lo)           # eps at its bound leaves no room for velocity
+    lib.tfs_destroy(h)
+    inv_h2 = (64 / (2 * math.pi)) ** 2
+    z_star = 4 * lo * dt * 2 * inv_h2 / 0.9   # both axes
+
+    def rad(zmax):
+        th = np.linspace(0, 2 * np.pi, 361)[1:]
+        return max(np.max(np.abs(np.linalg.eigvals(recurrence(zmax * np.sin(t / 2) ** 2, mu, w, dt, False))))
+                   for t in th)
+    assert rad(0.9 * z_star) <= 1 + 1e-9
+    assert rad(1.1 * z_star) > 1 + 1e-6
