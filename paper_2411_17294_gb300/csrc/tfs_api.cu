@@ -246,6 +246,13 @@ size_t forward_bytes(const tfs_ctx* h) {
     return kAlign + 4 * align_up(h->field_bytes()) + 2 * align_up(h->modes_bytes());
 }
 
+F2c split_f2(double v) {
+    F2c r;
+    r.hi = (float)v;
+    r.lo = (float)(v - (double)r.hi);
+    return r;
+}
+
 template <typename T>
 void fill_common(tfs_ctx* h, FwdArgs<T>& a) {
     a.N = h->N;
@@ -262,6 +269,9 @@ void fill_common(tfs_ctx* h, FwdArgs<T>& a) {
     a.courant_coef = (h->transport && limits_known(h)) ? courant_coef(h) : 0.0;
     a.courant_limit = courant_limit(h);
     a.flags = h->flags;
+    a.eta_f2 = split_f2(a.eta);
+    a.a_f2 = split_f2(a.a);
+    a.dt_f2 = split_f2(a.dt);
 }
 
 LaunchCfg make_cfg(const tfs_ctx* h) {
@@ -317,6 +327,7 @@ int do_step(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* s
         a.modes_n = (const float*)h->modes[cm];
         a.modes_nm1 = (float*)h->modes[pm];
         a.g = g_alpha(h, h->step);
+        a.src_f2 = split_f2(a.dt * a.G * a.g);
         a.mc = h->mcf;
         e = launch_forward_f32(a, cfg, s);
     }

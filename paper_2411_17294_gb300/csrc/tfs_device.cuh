@@ -120,6 +120,133 @@ __device__ __forceinline__ bool gauss_pp(double M[NC][NC], double x[NC], double 
     return ok;
 }
 
+// FP32 LU factorisation with partial pivoting by compare-and-swap on whole
+// rows (the multipliers move with their rows), recording every swap decision so
+// that the factors can be applied to further right-hand sides:  P M = L U.
+// The diagonal keeps 1/u_kk.  Returns false when a pivot is not above `tiny`.
+template <int NC>
+struct LU32 {
+    float a[NC][NC];
+    bool sw[NC][NC];   // sw[k][i]: rows k and i exchanged at elimination step k (i > k)
+};
+
+template <int NC>
+__device__ __forceinline__ bool lu32_factor(LU32<NC>& F, float tiny) {
+    bool ok = true;
+    static_for<0, NC>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        static_for<k + 1, NC>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            const bool sw = fabsf(F.a[i][k]) > fabsf(F.a[k][k]);
+            F.sw[k][i] = sw;
+            static_for<0, NC>([&](auto jj) {
+                constexpr int j = decltype(jj)::value;
+                const float t0 = F.a[k][j], t1 = F.a[i][j];
+                F.a[k][j] = sw ? t1 : t0;
+                F.a[i][j] = sw ? t0 : t1;
+            });
+        });
+        ok = ok && (fabsf(F.a[k][k]) > tiny);
+        const float inv = 1.0f / F.a[k][k];
+        F.a[k][k] = inv;
+        static_for<k + 1, NC>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            const float f = F.a[i][k] * inv;
+            F.a[i][k] = f;                     // multiplier of L
+            static_for<k + 1, NC>([&](auto jj) {
+                constexpr int j = decltype(jj)::value;
+                F.a[i][j] = __fmaf_rn(-f, F.a[k][j], F.a[i][j]);
+            });
+        });
+    });
+    return ok;
+}
+
+// x <- M^{-1} x with the factors of lu32_factor (permutation, then L, then U).
+template <int NC>
+__device__ __forceinline__ void lu32_solve(const LU32<NC>& F, float x[NC]) {
+    static_for<0, NC>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        static_for<k + 1, NC>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            const float t0 = x[k], t1 = x[i];
+            x[k] = F.sw[k][i] ? t1 : t0;
+            x[i] = F.sw[k][i] ? t0 : t1;
+        });
+    });
+    static_for<0, NC>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        static_for<k + 1, NC>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            x[i] = __fmaf_rn(-F.a[i][k], x[k], x[i]);
+        });
+    });
+    static_for<0, NC>([&](auto rr) {
+        constexpr int i = NC - 1 - decltype(rr)::value;
+        float acc = x[i];
+        static_for<i + 1, NC>([&](auto jj) {
+            constexpr int j = decltype(jj)::value;
+            acc = __fmaf_rn(-F.a[i][j], x[j], acc);
+        });
+        x[i] = acc * F.a[i][i];
+    });
+}
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2, ~44-bit
+// significand, built from the error-free transformations TwoSum (Knuth) and
+// TwoProd (exact product by FMA).  Used to assemble the right-hand side and the
+// refinement residual of the point system in FP32 storage mode without the
+// FP64 pipe.
+struct f2 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ f2 f2_from(float a) { return {a, 0.0f}; }
+
+__device__ __forceinline__ f2 two_sum_f2(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+// |a| >= |b| (or a == 0)
+__device__ __forceinline__ f2 fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ f2 two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ f2 f2_neg(f2 a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+    const f2 s = two_sum_f2(a.hi, b.hi);
+    const float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return fast_two_sum(s.hi, lo);
+}
+
+__device__ __forceinline__ f2 f2_add_f(f2 a, float b) {
+    const f2 s = two_sum_f2(a.hi, b);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+__device__ __forceinline__ f2 f2_mul_f(f2 a, float b) {
+    f2 p = two_prod(a.hi, b);
+    p.lo = __fmaf_rn(a.lo, b, p.lo);
+    return fast_two_sum(p.hi, p.lo);
+}
+
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+    f2 p = two_prod(a.hi, b.hi);
+    p.lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+    return fast_two_sum(p.hi, p.lo);
+}
+
 // Periodic neighbour index along axis `ax` at offset `off` (|off| <= 2) from
 // point (x, y, z); correct for any axis length >= 1.
 struct GridIdx {

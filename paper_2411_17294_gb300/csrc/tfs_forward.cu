@@ -8,14 +8,25 @@
 //   solve (eta + dt/Wi) s - dt (kappa* s + s kappa*^T) = R   -> sigma^{n+1}
 //   sigma_j^{n+1} = -c_j (b1 sigma_j^n + b2 sigma_j^{n-1}) + rho_j (sigma^{n+1} - sigma0)
 //
-// Thread layout: a block covers 32 consecutive points; warp c of the block
-// handles stress component c for those points (lane = point).  Mode arrays are
-// [m][nc][N], so every warp load/store of one (mode, component) plane is a
-// single 128-byte line.  Each thread keeps the m history terms Q_j of its
-// (point, component) in registers between the history sum and the push-forward,
-// so every mode value is read once and written once per step.  The nc x nc
-// point systems of the block are solved by warp 0 (lane = point) in FP64; the
-// other warps exchange R and sigma^{n+1} - sigma0 through shared memory.
+// Structure.  A persistent block loops over tiles of 32 consecutive points.
+// The m x nc (mode, component) planes of both levels of the next tile are
+// copied global -> shared with cp.async (16-byte chunks, zero-filled past the
+// end of the grid) while the current tile is computed, so the mode stream --
+// 94% of the bytes -- is always in flight without holding registers.  Inside
+// a tile, warp c handles stress component c (lane = point): it forms
+// Q_j = b1 x + b2 y from shared memory (stored back in place of the older
+// level), the history sum H (FP32 storage: compensated Dot2 with eta_j split
+// hi + lo) and its component of the right-hand side (transport stencil read
+// through the read-only cache).  Warp 0 then solves the 32 point systems with
+// lane = point; the other warps write the new mode level from the Q_j kept in
+// shared memory.  Every mode value is read once and written once.
+//
+// Point solve.  FP64 storage: FP64 Gaussian elimination with partial
+// pivoting.  FP32 storage: FP32 LU with partial pivoting, one refinement step
+// whose residual R - M x0 is evaluated in double-float arithmetic (TwoSum /
+// TwoProd, ~44-bit), correction through the same factors: the solution of the
+// system as given is accurate far beyond the FP32 rounding of the stored
+// result, and the FP64 pipe (1/64 of the FP32 rate on this GPU) stays free.
 #include <cuda_runtime.h>
 
 #include "tfs_device.cuh"
@@ -24,219 +35,473 @@
 namespace tfs {
 namespace {
 
-template <typename T, int DIM, bool TRANSPORT>
-__device__ __forceinline__ double transport_term(const FwdArgs<T>& A, const GridIdx& g, int c,
-                                                 int stencil, long long p) {
-    // E = 2 sigma^n - sigma^{n-1} at a neighbour, in the storage precision
+constexpr int kTile = 32;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// 16-byte asynchronous copy global -> shared; bytes beyond src_bytes are zero.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES),
+                 "r"(src_bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Copy both mode levels of one tile into a stage buffer laid out as
+// [level][j][c][32] (level 0 = n, level 1 = n-1).
+template <typename T, int NC>
+__device__ __forceinline__ void issue_tile(const FwdArgs<T>& A, T* buf, long long t0, int tid, int nthr,
+                                           bool vec16) {
+    const int m = A.m;
+    const long long N = A.N;
+    const int planes_per_level = m * NC;
+    const int planes = 2 * planes_per_level;
+    if (vec16) {
+        constexpr int EPC = 16 / sizeof(T);    // elements per chunk
+        constexpr int CPP = kTile / EPC;       // chunks per plane segment
+        const int total = planes * CPP;
+        for (int q = tid; q < total; q += nthr) {
+            const int plane = q / CPP;
+            const int k = q - plane * CPP;
+            const int level = plane >= planes_per_level;
+            const int jc = plane - level * planes_per_level;
+            const long long p0 = t0 + (long long)k * EPC;
+            long long valid = N - p0;
+            valid = valid < 0 ? 0 : (valid > EPC ? EPC : valid);
+            const T* base = (level ? A.modes_nm1 : A.modes_n) + (long long)jc * N;
+            cp_async16(buf + plane * kTile + k * EPC, base + (valid > 0 ? p0 : 0), (int)(valid * sizeof(T)));
+        }
+    } else {
+        const int total = planes * kTile;
+        for (int q = tid; q < total; q += nthr) {
+            const int plane = q / kTile;
+            const int l = q - plane * kTile;
+            const int level = plane >= planes_per_level;
+            const int jc = plane - level * planes_per_level;
+            const long long p = t0 + l;
+            const T* base = (level ? A.modes_nm1 : A.modes_n) + (long long)jc * N;
+            cp_async_small<sizeof(T)>(buf + q, base + (p < N ? p : 0), p < N ? (int)sizeof(T) : 0);
+        }
+    }
+}
+
+// First derivative of E at a point: upwind3 (biased by the sign of u) or central2
+template <typename T>
+__device__ __forceinline__ T stencil_deriv(int stencil, T ua, T em2, T em1, T e0, T ep1, T ep2, T ih) {
+    if (stencil == 1) return (ep1 - em1) * ((T)0.5 * ih);
+    if (ua >= (T)0) return (em2 - (T)6 * em1 + (T)3 * e0 + (T)2 * ep1) * (ih / (T)6);
+    return ((T)-2 * em1 - (T)3 * e0 + (T)6 * ep1 - ep2) * (ih / (T)6);
+}
+
+// Transport term A (storage precision) for component c at point p = (x, y, z).
+template <typename T, int DIM>
+__device__ __forceinline__ T transport_term(const FwdArgs<T>& A, int c, int stencil, unsigned x, unsigned y,
+                                            unsigned z, long long p) {
     const T* sn = A.sig_n + (long long)c * A.N;
     const T* sm = A.sig_nm1 + (long long)c * A.N;
     auto E = [&](long long q) -> T { return (T)2 * __ldg(sn + q) - __ldg(sm + q); };
-    T adv = (T)0, lap = (T)0;
+    const unsigned n[3] = {(unsigned)A.n0, (unsigned)A.n1, (unsigned)A.n2};
+    const unsigned co[3] = {x, y, z};
+    const long long strides[3] = {1, (long long)A.n0, (long long)A.n0 * A.n1};
     const T e0 = E(p);
+    T adv = (T)0, lap = (T)0;
 #pragma unroll
     for (int ax = 0; ax < DIM; ++ax) {
+        // neighbour indices with periodic wrap (|offset| <= 2, any n >= 1)
+        auto nb = [&](int off) -> long long {
+            int v = (int)co[ax] + off;
+            const int nn = (int)n[ax];
+            if (v < 0) v += nn;
+            if (v < 0) v += nn;
+            if (v >= nn) v -= nn;
+            if (v >= nn) v -= nn;
+            return p + ((long long)v - (long long)co[ax]) * strides[ax];
+        };
         const T ua = __ldg(A.u + (long long)ax * A.N + p);
         const T ih = (T)A.inv_h[ax];
-        const T em1 = E(g.at(ax, -1)), ep1 = E(g.at(ax, 1));
-        T d;
-        if (stencil == 1) {
-            d = (ep1 - em1) * ((T)0.5 * ih);
-        } else if (ua >= (T)0) {
-            const T em2 = E(g.at(ax, -2));
-            d = (em2 - (T)6 * em1 + (T)3 * e0 + (T)2 * ep1) * (ih / (T)6);
-        } else {
-            const T ep2 = E(g.at(ax, 2));
-            d = ((T)-2 * em1 - (T)3 * e0 + (T)6 * ep1 - ep2) * (ih / (T)6);
+        const T em1 = E(nb(-1)), ep1 = E(nb(1));
+        T em2 = (T)0, ep2 = (T)0;
+        if (stencil == 0) {
+            if (ua >= (T)0) em2 = E(nb(-2));
+            else ep2 = E(nb(2));
         }
-        adv += ua * d;
+        adv += ua * stencil_deriv<T>(stencil, ua, em2, em1, e0, ep1, ep2, ih);
         if (A.eps != 0.0) lap += (em1 - (T)2 * e0 + ep1) * (ih * ih);
     }
-    return A.dt * to_d(adv) - A.eps * A.dt * to_d(lap);
+    return (T)A.dt * adv - (T)(A.eps * A.dt) * lap;
 }
 
-template <typename T, int DIM, int MT, bool TRANSPORT, bool COMP>
-__global__ void __launch_bounds__(32 * Packed<DIM>::NC)
-fwd_kernel(const FwdArgs<T> A, const int stencil, const int classic) {
+// ----------------------------------------------------------- FP32 point solve
+// Packed residual r = R - (a x - dt (K x + x K^T)) in double-float, K exact as f2.
+template <int DIM>
+__device__ __forceinline__ void residual_f2(const f2 K[3][3], F2c a, F2c dt, const f2 R[Packed<DIM>::NC],
+                                            const float x[Packed<DIM>::NC], f2 r[Packed<DIM>::NC]) {
     constexpr int NC = Packed<DIM>::NC;
-    __shared__ double sR[NC][32];
-    __shared__ double sD[NC][32];
+    float S[3][3];
+    static_for<0, NC>([&](auto cc) {
+        constexpr int c = decltype(cc)::value;
+        S[Packed<DIM>::I(c)][Packed<DIM>::J(c)] = x[c];
+        S[Packed<DIM>::J(c)][Packed<DIM>::I(c)] = x[c];
+    });
+    const f2 af{a.hi, a.lo}, dtf{dt.hi, dt.lo};
+    static_for<0, NC>([&](auto cc) {
+        constexpr int c = decltype(cc)::value;
+        constexpr int i = Packed<DIM>::I(c), j = Packed<DIM>::J(c);
+        f2 acc{0.0f, 0.0f};
+        static_for<0, DIM>([&](auto ll) {
+            constexpr int l = decltype(ll)::value;
+            acc = f2_add(acc, f2_mul_f(K[i][l], S[l][j]));
+            acc = f2_add(acc, f2_mul_f(K[j][l], S[i][l]));
+        });
+        // R - a x + dt acc
+        f2 t = f2_add(R[c], f2_neg(f2_mul_f(af, x[c])));
+        r[c] = f2_add(t, f2_mul(dtf, acc));
+    });
+}
 
+template <int DIM>
+__device__ __forceinline__ bool solve_point_f32(const f2 K[3][3], F2c a, F2c dt, const f2 R[Packed<DIM>::NC],
+                                                f2 x[Packed<DIM>::NC]) {
+    constexpr int NC = Packed<DIM>::NC;
+    LU32<NC> F;
+    const float af = a.hi, dtf = dt.hi;
+    static_for<0, NC>([&](auto rr) {
+        constexpr int r = decltype(rr)::value;
+        static_for<0, NC>([&](auto kk) {
+            constexpr int k = decltype(kk)::value;
+            constexpr int ro = Packed<DIM>::I(r), so = Packed<DIM>::J(r);
+            constexpr int i = Packed<DIM>::I(k), j = Packed<DIM>::J(k);
+            float v = 0.0f;
+            if (so == j) v += K[ro][i].hi;
+            if (i != j && so == i) v += K[ro][j].hi;
+            if (ro == i) v += K[so][j].hi;
+            if (i != j && ro == j) v += K[so][i].hi;
+            F.a[r][k] = (r == k) ? __fmaf_rn(-dtf, v, af) : -dtf * v;
+        });
+    });
+    const bool ok = lu32_factor<NC>(F, 1e-30f);
+    float x0[NC];
+    static_for<0, NC>([&](auto rr) {
+        constexpr int r = decltype(rr)::value;
+        x0[r] = R[r].hi + R[r].lo;
+    });
+    lu32_solve<NC>(F, x0);
+    f2 res[NC];
+    residual_f2<DIM>(K, a, dt, R, x0, res);
+    float d[NC];
+    static_for<0, NC>([&](auto rr) {
+        constexpr int r = decltype(rr)::value;
+        d[r] = res[r].hi + res[r].lo;
+    });
+    lu32_solve<NC>(F, d);
+    static_for<0, NC>([&](auto rr) {
+        constexpr int r = decltype(rr)::value;
+        x[r] = two_sum_f2(x0[r], d[r]);
+    });
+    return ok;
+}
+
+// ----------------------------------------------------------------- the kernel
+template <typename T, int DIM, bool TRANSPORT, bool COMP>
+__device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, T* buf, long long t0, int stencil, int classic,
+                                             void* sR_raw, float* sD) {
+    constexpr int NC = Packed<DIM>::NC;
+    constexpr bool F32 = sizeof(T) == 4;
     const int lane = threadIdx.x;
     const int c = threadIdx.y;
     const long long N = A.N;
-    const long long p = (long long)blockIdx.x * 32 + lane;
+    const long long p = t0 + lane;
     const bool active = p < N;
-    const long long pc = active ? p : 0;   // clamped index for inactive lanes
+    const int m = A.m;
 
-    // ---- (a4) history sum over the modes of component c -------------------
-    T Q[MT > 0 ? MT : 1];
-    double H = 0.0;
+    // ---- (a4) history sum over the modes of component c (Q_j stored in place of level n-1)
+    double Hd = 0.0;
+    f2 Hf{0.0f, 0.0f};
+    const double s0c = (active && A.sigma0) ? (double)A.sigma0[(long long)c * N + p] : 0.0;
     if (classic) {
         if (active) {
             const long long q = (long long)c * N + p;
-            const double s0 = A.sigma0 ? to_d(A.sigma0[q]) : 0.0;
-            H = kB1 * to_d(A.sig_n[q]) + kB2 * to_d(A.sig_nm1[q]) + kB0 * s0;
+            if constexpr (F32) {
+                // b1 sigma^n + b2 sigma^{n-1} + b0 sigma0, exact products by powers of two and TwoProd
+                f2 h = two_sum_f2(-2.0f * (float)A.sig_n[q], 0.5f * (float)A.sig_nm1[q]);
+                Hf = f2_add(h, two_prod(1.5f, (float)s0c));
+            } else {
+                Hd = kB1 * (double)A.sig_n[q] + kB2 * (double)A.sig_nm1[q] + kB0 * s0c;
+            }
         }
     } else {
-        const T* mn = A.modes_n + (long long)c * N + pc;
-        const T* mm = A.modes_nm1 + (long long)c * N + pc;
-        const long long stride = (long long)NC * N;
-        if constexpr (sizeof(T) == 4 && COMP) {
-            // compensated dot product (Ogita-Rump-Oishi Dot2): exact products by
-            // FMA, error-free sums, eta_j carried as hi + lo floats
+        T* lv0 = buf + (c * kTile + lane);
+        T* lv1 = buf + ((m * NC + c) * kTile + lane);
+        if constexpr (F32 && COMP) {
             float hs = 0.f, he = 0.f;
-#pragma unroll
-            for (int j = 0; j < MT; ++j) {
-                if (j < A.m) {
-                    const float x = __ldcs(mn + j * stride);
-                    const float y = __ldcs(mm + j * stride);
-                    const float qj = __fmaf_rn(0.5f, y, -2.0f * x);   // b1 x + b2 y, one rounding
-                    Q[j] = qj;
-                    const float pr = __fmul_rn(A.mc.eta_hi[j], qj);
-                    const float pe = __fmaf_rn(A.mc.eta_hi[j], qj, -pr);
-                    float s, e;
-                    two_sum(hs, pr, s, e);
-                    hs = s;
-                    he = __fadd_rn(he, __fadd_rn(e, __fmaf_rn(A.mc.eta_lo[j], qj, pe)));
-                }
+#pragma unroll 8
+            for (int j = 0; j < m; ++j) {
+                const float x = lv0[j * NC * kTile];
+                const float y = lv1[j * NC * kTile];
+                const float qj = __fmaf_rn(0.5f, y, -2.0f * x);
+                lv1[j * NC * kTile] = qj;
+                const float pr = __fmul_rn(A.mc.eta_hi[j], qj);
+                const float pe = __fmaf_rn(A.mc.eta_hi[j], qj, -pr);
+                const f2 s = two_sum_f2(hs, pr);
+                hs = s.hi;
+                he = __fadd_rn(he, __fadd_rn(s.lo, __fmaf_rn(A.mc.eta_lo[j], qj, pe)));
             }
-            H = (double)hs + (double)he;
-        } else if constexpr (sizeof(T) == 4) {
+            Hf = fast_two_sum(hs, he);
+        } else if constexpr (F32) {
             float hs = 0.f;
-#pragma unroll
-            for (int j = 0; j < MT; ++j) {
-                if (j < A.m) {
-                    const float x = __ldcs(mn + j * stride);
-                    const float y = __ldcs(mm + j * stride);
-                    const float qj = __fmaf_rn(0.5f, y, -2.0f * x);
-                    Q[j] = qj;
-                    hs = __fmaf_rn(A.mc.eta_hi[j], qj, hs);
-                }
+#pragma unroll 8
+            for (int j = 0; j < m; ++j) {
+                const float x = lv0[j * NC * kTile];
+                const float y = lv1[j * NC * kTile];
+                const float qj = __fmaf_rn(0.5f, y, -2.0f * x);
+                lv1[j * NC * kTile] = qj;
+                hs = __fmaf_rn(A.mc.eta_hi[j], qj, hs);
             }
-            H = (double)hs;
+            Hf = f2_from(hs);
         } else {
-#pragma unroll
-            for (int j = 0; j < MT; ++j) {
-                if (j < A.m) {
-                    const double x = __ldcs(mn + j * stride);
-                    const double y = __ldcs(mm + j * stride);
-                    const double qj = kB1 * x + kB2 * y;
-                    Q[j] = (T)qj;
-                    H = fma(A.mc.eta[j], qj, H);
-                }
+#pragma unroll 4
+            for (int j = 0; j < m; ++j) {
+                const double x = (double)lv0[j * NC * kTile];
+                const double y = (double)lv1[j * NC * kTile];
+                const double qj = kB1 * x + kB2 * y;
+                lv1[j * NC * kTile] = (T)qj;
+                Hd = fma(A.mc.eta[j], qj, Hd);
             }
         }
     }
 
-    // ---- right-hand side component c ------------------------------------
-    double R = 0.0;
-    const double s0c = (active && A.sigma0) ? to_d(A.sigma0[(long long)c * N + p]) : 0.0;
+    // ---- right-hand side component c
+    unsigned px = 0, py = 0, pz = 0;
     if (active) {
-        const int ci = Packed<DIM>::I(c), cj = Packed<DIM>::J(c);
-        const long long kij = (long long)(ci * DIM + cj) * N + p;
-        const long long kji = (long long)(cj * DIM + ci) * N + p;
-        const double ks = (2.0 * to_d(A.kap_n[kij]) - to_d(A.kap_nm1[kij])) +
-                          (2.0 * to_d(A.kap_n[kji]) - to_d(A.kap_nm1[kji]));
-        R = A.eta * s0c - H + A.dt * A.G * A.g * ks;
-        if constexpr (TRANSPORT) {
-            GridIdx g;
-            g.n0 = A.n0; g.n1 = A.n1; g.n2 = A.n2;
-            g.x = p % A.n0;
-            g.y = (p / A.n0) % A.n1;
-            g.z = p / ((long long)A.n0 * A.n1);
-            R -= transport_term<T, DIM, TRANSPORT>(A, g, c, stencil, p);
-        }
+        const unsigned pu = (unsigned)p;
+        px = pu % (unsigned)A.n0;
+        const unsigned r1 = pu / (unsigned)A.n0;
+        py = r1 % (unsigned)A.n1;
+        pz = r1 / (unsigned)A.n1;
     }
-    sR[c][lane] = R;
+    const int ci = Packed<DIM>::I(c), cj = Packed<DIM>::J(c);
+    if constexpr (F32) {
+        f2 R{0.0f, 0.0f};
+        if (active) {
+            const long long kij = (long long)(ci * DIM + cj) * N + p;
+            const long long kji = (long long)(cj * DIM + ci) * N + p;
+            const f2 kab = two_sum_f2(2.0f * (float)A.kap_n[kij], -(float)A.kap_nm1[kij]);
+            const f2 kba = two_sum_f2(2.0f * (float)A.kap_n[kji], -(float)A.kap_nm1[kji]);
+            const f2 ks = f2_add(kab, kba);
+            const f2 eta{A.eta_f2.hi, A.eta_f2.lo}, src{A.src_f2.hi, A.src_f2.lo};
+            R = f2_add(f2_mul_f(eta, (float)s0c), f2_neg(Hf));
+            R = f2_add(R, f2_mul(src, ks));
+            if constexpr (TRANSPORT) R = f2_add_f(R, -(float)transport_term<T, DIM>(A, c, stencil, px, py, pz, p));
+        }
+        f2* sR = reinterpret_cast<f2*>(sR_raw);
+        sR[c * kTile + lane] = R;
+    } else {
+        double R = 0.0;
+        if (active) {
+            const long long kij = (long long)(ci * DIM + cj) * N + p;
+            const long long kji = (long long)(cj * DIM + ci) * N + p;
+            const double ks = (2.0 * (double)A.kap_n[kij] - (double)A.kap_nm1[kij]) +
+                              (2.0 * (double)A.kap_n[kji] - (double)A.kap_nm1[kji]);
+            R = A.eta * s0c - Hd + A.dt * A.G * A.g * ks;
+            if constexpr (TRANSPORT) R -= (double)transport_term<T, DIM>(A, c, stencil, px, py, pz, p);
+        }
+        double* sR = reinterpret_cast<double*>(sR_raw);
+        sR[c * kTile + lane] = R;
+    }
     __syncthreads();
 
-    // ---- (a2) + (a5) per-point solve by warp 0 ---------------------------
+    // ---- (a2) + (a5) point solve by warp 0
     if (c == 0) {
-        double x[NC];
-#pragma unroll
-        for (int r = 0; r < NC; ++r) x[r] = sR[r][lane];
-        bool ok = true;
+        float dsig[NC];
         if (active) {
-            double K[3][3];
+            unsigned fl = 0u;
+            T out[NC];
+            if constexpr (F32) {
+                f2 K[3][3];
 #pragma unroll
-            for (int a = 0; a < DIM; ++a)
+                for (int a = 0; a < DIM; ++a)
 #pragma unroll
-                for (int b = 0; b < DIM; ++b) {
-                    const long long q = (long long)(a * DIM + b) * N + p;
-                    K[a][b] = 2.0 * to_d(A.kap_n[q]) - to_d(A.kap_nm1[q]);
-                }
-            double M[NC][NC];
-            assemble_M<DIM>(K, A.a, A.dt, M);
-            ok = gauss_pp<NC>(M, x, 1e-300);
+                    for (int b = 0; b < DIM; ++b) {
+                        const long long q = (long long)(a * DIM + b) * N + p;
+                        K[a][b] = two_sum_f2(2.0f * (float)A.kap_n[q], -(float)A.kap_nm1[q]);
+                    }
+                const f2* sR = reinterpret_cast<const f2*>(sR_raw);
+                f2 R[NC], x[NC];
+#pragma unroll
+                for (int r = 0; r < NC; ++r) R[r] = sR[r * kTile + lane];
+                if (!solve_point_f32<DIM>(K, A.a_f2, A.dt_f2, R, x)) fl |= 2u;
+#pragma unroll
+                for (int r = 0; r < NC; ++r) out[r] = (T)(x[r].hi + x[r].lo);
+            } else {
+                double K[3][3];
+#pragma unroll
+                for (int a = 0; a < DIM; ++a)
+#pragma unroll
+                    for (int b = 0; b < DIM; ++b) {
+                        const long long q = (long long)(a * DIM + b) * N + p;
+                        K[a][b] = 2.0 * (double)A.kap_n[q] - (double)A.kap_nm1[q];
+                    }
+                const double* sR = reinterpret_cast<const double*>(sR_raw);
+                double x[NC];
+#pragma unroll
+                for (int r = 0; r < NC; ++r) x[r] = sR[r * kTile + lane];
+                double M[NC][NC];
+                assemble_M<DIM>(K, A.a, A.dt, M);
+                if (!gauss_pp<NC>(M, x, 1e-300)) fl |= 2u;
+#pragma unroll
+                for (int r = 0; r < NC; ++r) out[r] = (T)x[r];
+            }
             bool finite = true;
 #pragma unroll
             for (int r = 0; r < NC; ++r) {
-                const T v = (T)x[r];
-                finite = finite && isfinite(to_d(v));
-                A.sig_np1[(long long)r * N + p] = v;
-                if (A.sig_copy) A.sig_copy[(long long)r * N + p] = v;
+                finite = finite && isfinite((double)out[r]);
+                A.sig_np1[(long long)r * N + p] = out[r];
+                if (A.sig_copy) A.sig_copy[(long long)r * N + p] = out[r];
+                const T s0r = A.sigma0 ? A.sigma0[(long long)r * N + p] : (T)0;
+                // the push-forward uses the stored value of sigma^{n+1}
+                dsig[r] = 0.0f;
+                if constexpr (F32) dsig[r] = __fsub_rn((float)out[r], (float)s0r);
+                else reinterpret_cast<double*>(sD)[r * kTile + lane] = (double)out[r] - (double)s0r;
             }
-            unsigned fl = (ok ? 0u : 2u) | (finite ? 0u : 1u);
+            if (!finite) fl |= 1u;
             if (TRANSPORT && A.courant_coef > 0.0) {
                 double cr = 0.0;
 #pragma unroll
-                for (int ax = 0; ax < DIM; ++ax) cr += fabs(to_d(A.u[(long long)ax * N + p])) * A.inv_h[ax];
+                for (int ax = 0; ax < DIM; ++ax) cr += fabs((double)A.u[(long long)ax * N + p]) * A.inv_h[ax];
                 if (A.courant_coef * cr > A.courant_limit) fl |= 4u;
             }
             if (fl) atomicOr(A.flags, fl);
-        }
+        } else {
 #pragma unroll
-        for (int r = 0; r < NC; ++r) {
-            const double s0r = (active && A.sigma0) ? to_d(A.sigma0[(long long)r * N + pc]) : 0.0;
-            // the push-forward uses the stored (rounded) value of sigma^{n+1}
-            sD[r][lane] = to_d((T)x[r]) - s0r;
+            for (int r = 0; r < NC; ++r) {
+                dsig[r] = 0.0f;
+                if constexpr (!F32) reinterpret_cast<double*>(sD)[r * kTile + lane] = 0.0;
+            }
+        }
+        if constexpr (F32) {
+#pragma unroll
+            for (int r = 0; r < NC; ++r) sD[r * kTile + lane] = dsig[r];
         }
     }
     __syncthreads();
 
-    // ---- (a6) mode push-forward over the oldest level ---------------------
+    // ---- (a6) push-forward of the modes over the oldest level
     if (!classic && active) {
-        const double d = sD[c][lane];
+        const T* qv = buf + ((m * NC + c) * kTile + lane);
         T* out = A.modes_nm1 + (long long)c * N + p;
         const long long stride = (long long)NC * N;
-        if constexpr (sizeof(T) == 4) {
-            const float df = (float)d;
-#pragma unroll
-            for (int j = 0; j < MT; ++j)
-                if (j < A.m) __stcs(out + j * stride, __fmaf_rn(A.mc.rho[j], df, -A.mc.c[j] * Q[j]));
+        if constexpr (F32) {
+            const float d = sD[c * kTile + lane];
+#pragma unroll 8
+            for (int j = 0; j < m; ++j)
+                __stcs(out + j * stride, __fmaf_rn(A.mc.rho[j], d, -A.mc.c[j] * qv[j * NC * kTile]));
         } else {
-#pragma unroll
-            for (int j = 0; j < MT; ++j)
-                if (j < A.m) __stcs(out + j * stride, (T)fma(A.mc.rho[j], d, -A.mc.c[j] * (double)Q[j]));
+            const double d = reinterpret_cast<const double*>(sD)[c * kTile + lane];
+#pragma unroll 4
+            for (int j = 0; j < m; ++j)
+                __stcs(out + j * stride, (T)fma(A.mc.rho[j], d, -A.mc.c[j] * (double)qv[j * NC * kTile]));
         }
     }
 }
 
-template <typename T, int DIM, int MT, bool TRANSPORT, bool COMP>
-cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s) {
+template <typename T, int DIM, bool TRANSPORT, bool COMP>
+__global__ void __launch_bounds__(32 * Packed<DIM>::NC, DIM == 3 ? 2 : 4)
+fwd_kernel(const FwdArgs<T> A, const int stencil, const int classic, const long long num_tiles, const int stages,
+           const int vec16) {
     constexpr int NC = Packed<DIM>::NC;
-    const long long blocks = (a.N + 31) / 32;
-    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    dim3 grid((unsigned)blocks), block(32, NC);
-    fwd_kernel<T, DIM, MT, TRANSPORT, COMP><<<grid, block, 0, s>>>(a, cfg.stencil, cfg.classic ? 1 : 0);
-    return cudaGetLastError();
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(16) double sR_store[NC * kTile];       // R per (component, point): double or f2
+    __shared__ __align__(16) double sD_store[NC * kTile];       // sigma^{n+1} - sigma0 (float or double)
+    const size_t stage_elems = (size_t)2 * A.m * NC * kTile;
+    T* buf0 = reinterpret_cast<T*>(smem);
+    T* buf1 = buf0 + stage_elems;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int nthr = 32 * NC;
+    const bool staged = !classic && A.m > 0;
+    float* sD = reinterpret_cast<float*>(sD_store);
+
+    if (stages == 2) {
+        long long tile = blockIdx.x;
+        if (staged && tile < num_tiles) issue_tile<T, NC>(A, buf0, tile * kTile, tid, nthr, vec16 != 0);
+        cp_async_commit();
+        for (int it = 0; tile < num_tiles; ++it, tile += gridDim.x) {
+            const long long next = tile + gridDim.x;
+            T* cur = (it & 1) ? buf1 : buf0;
+            T* nxt = (it & 1) ? buf0 : buf1;
+            if (staged && next < num_tiles) issue_tile<T, NC>(A, nxt, next * kTile, tid, nthr, vec16 != 0);
+            cp_async_commit();
+            cp_async_wait<1>();
+            __syncthreads();
+            compute_tile<T, DIM, TRANSPORT, COMP>(A, cur, tile * kTile, stencil, classic, sR_store, sD);
+            __syncthreads();
+        }
+        cp_async_wait<0>();
+    } else {
+        for (long long tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
+            if (staged) issue_tile<T, NC>(A, buf0, tile * kTile, tid, nthr, vec16 != 0);
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncthreads();
+            compute_tile<T, DIM, TRANSPORT, COMP>(A, buf0, tile * kTile, stencil, classic, sR_store, sD);
+            __syncthreads();
+        }
+    }
 }
 
 template <typename T, int DIM, bool TRANSPORT, bool COMP>
-cudaError_t dispatch_mt(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s) {
+cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s) {
+    constexpr int NC = Packed<DIM>::NC;
+    auto kern = fwd_kernel<T, DIM, TRANSPORT, COMP>;
+    const long long num_tiles = (a.N + kTile - 1) / kTile;
     const int m = cfg.classic ? 0 : a.m;
-    if (m <= 8) return launch_one<T, DIM, 8, TRANSPORT, COMP>(a, cfg, s);
-    if (m <= 16) return launch_one<T, DIM, 16, TRANSPORT, COMP>(a, cfg, s);
-    if (m <= 32) return launch_one<T, DIM, 32, TRANSPORT, COMP>(a, cfg, s);
-    if (m <= 48) return launch_one<T, DIM, 48, TRANSPORT, COMP>(a, cfg, s);
-    return launch_one<T, DIM, 64, TRANSPORT, COMP>(a, cfg, s);
+    const size_t stage_bytes = (size_t)2 * m * NC * kTile * sizeof(T);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int max_optin = 0, sms = 0;
+    e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const size_t static_bytes = 2 * NC * kTile * sizeof(double);
+    int stages = 2;
+    if (2 * stage_bytes + static_bytes > (size_t)max_optin) stages = 1;
+    if (stage_bytes + static_bytes > (size_t)max_optin) return cudaErrorInvalidConfiguration;
+    const size_t dyn = stages * stage_bytes;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * NC, dyn);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long grid = (long long)per_sm * sms;
+    if (grid > num_tiles) grid = num_tiles;
+    if (grid < 1) grid = 1;
+    const int vec16 = (a.N % (16 / (long long)sizeof(T))) == 0;
+    kern<<<dim3((unsigned)grid), dim3(32, NC), dyn, s>>>(a, cfg.stencil, cfg.classic ? 1 : 0, num_tiles, stages,
+                                                         vec16);
+    return cudaGetLastError();
 }
 
 template <typename T, bool COMP>
 cudaError_t dispatch(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s) {
     if (cfg.dim == 2)
-        return cfg.transport ? dispatch_mt<T, 2, true, COMP>(a, cfg, s) : dispatch_mt<T, 2, false, COMP>(a, cfg, s);
-    return cfg.transport ? dispatch_mt<T, 3, true, COMP>(a, cfg, s) : dispatch_mt<T, 3, false, COMP>(a, cfg, s);
+        return cfg.transport ? launch_one<T, 2, true, COMP>(a, cfg, s) : launch_one<T, 2, false, COMP>(a, cfg, s);
+    return cfg.transport ? launch_one<T, 3, true, COMP>(a, cfg, s) : launch_one<T, 3, false, COMP>(a, cfg, s);
 }
 
 }  // namespace

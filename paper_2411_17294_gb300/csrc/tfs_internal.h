@@ -24,6 +24,11 @@ template <typename T> struct ModeConsts;
 template <> struct ModeConsts<double> { using type = ModeConstsD; };
 template <> struct ModeConsts<float> { using type = ModeConstsF; };
 
+// A double scalar split into two floats, hi + lo (double-float arithmetic).
+struct F2c {
+    float hi, lo;
+};
+
 // Arguments of one forward step launch.  Field pointers follow the layouts of
 // include/tfs.h; the mode arrays are [m][nc][N].
 template <typename T>
@@ -44,8 +49,10 @@ struct FwdArgs {
     int m;
     double dt, eta, a, G, g, eps;   // eta, a = eta + dt/Wi, G, g = g_alpha(t_{n+1})
     double inv_h[3];
-    double courant_coef;   // dt^alpha / b0^alpha (0: no Courant check)
+    double courant_coef;   // per-point Courant number = coef * sum_a |u_a| / h_a (0: no check)
     double courant_limit;
+    // double-float copies of the step scalars (FP32 storage modes)
+    F2c eta_f2, a_f2, dt_f2, src_f2;   // src = dt G g
     typename ModeConsts<T>::type mc;
 };
 

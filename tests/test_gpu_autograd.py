@@ -50,8 +50,8 @@ def test_autograd_matches_central_differences(transport):
 
     with torch.no_grad():
         s0d, kd = s0.detach(), k.detach()
-        assert close(Wi.grad.item(), fd(lambda x: J(s0d, kd, torch.tensor(x, device=dev), beta.detach()).item(), 1.4))
-        assert close(beta.grad.item(), fd(lambda x: J(s0d, kd, Wi.detach(), torch.tensor(x, device=dev)).item(), 0.3))
+        assert close(Wi.grad.item(), fd(lambda x: J(s0d, kd, torch.tensor(x, dtype=torch.float64, device=dev), beta.detach()).item(), 1.4))
+        assert close(beta.grad.item(), fd(lambda x: J(s0d, kd, Wi.detach(), torch.tensor(x, dtype=torch.float64, device=dev)).item(), 0.3))
         for (c, q) in [(0, 0), (2, 63), (1, 17)]:
             def fs(x, c=c, q=q):
                 t = s0d.clone(); t[c, q] = x
