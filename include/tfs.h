@@ -64,7 +64,8 @@ enum {
     TFS_ERR_CUDA = 4,         /* a CUDA runtime call failed */
     TFS_ERR_STATE = 5,        /* call out of order (no state set, adjoint not begun, ...) */
     TFS_ERR_NOWORKSPACE = 6,  /* no (or too small a) workspace bound */
-    TFS_ERR_FORMAT = 7        /* checkpoint buffer does not match this handle */
+    TFS_ERR_FORMAT = 7,       /* checkpoint buffer does not match this handle */
+    TFS_ERR_TOOBIG = 8        /* problem state exceeds the fixed array of tfs_run_static */
 };
 
 /* precision modes */
@@ -184,6 +185,30 @@ const char* tfs_strerror(int code);
 
 /* Free the handle (host memory only). */
 int tfs_destroy(tfs_handle h);
+
+/* Run `steps` steps from sigma0 without any workspace, for callers that cannot
+   allocate device memory (code running where cudaMalloc is not allowed: a host
+   framework that owns all device memory, an allocation-free real-time loop, a
+   plug-in without an allocator).  The paper has no counterpart: this is an
+   interface convenience around the same step kernel.
+   The whole state (stress ring, sigma0 copy, status word, both mode levels)
+   lives in one fixed device array of 64 MiB compiled into the library, which
+   every GPU that loads the library holds until the process exits; problems
+   whose state needs more (256 + 4 up256(nc N s) + 2 up256(m nc N s) bytes,
+   s = element size, up256 = round up to 256) return TFS_ERR_TOOBIG before any
+   device work.  Arguments as tfs_create / tfs_set_soe (mu, w: host, m
+   entries, NULL when alpha == 1); Re = 1, eps = 0, upwind3 stencil, transport
+   on iff u != NULL, no Courant check; sigma0 [nc][N] (NULL = zero), grad_u
+   [d*d][N] frozen for all steps, sigma_out [nc][N]: device pointers of the
+   precision's element type.  Enqueues on `stream` and returns; the result is
+   in sigma_out once the stream reaches it.  The array's device address is
+   looked up on the first call on each device (with that device current): make
+   that first call before any stream capture.  Every call shares the array and
+   clears it at its start, so calls whose GPU work overlaps (other streams or
+   host threads) race and must not be issued.  Allocates nothing. */
+int tfs_run_static(const tfs_grid* grid, double alpha, double Wi, double beta, int m, double dt,
+                   int precision, const double* mu, const double* w, const void* sigma0,
+                   const void* grad_u, const void* u, int steps, void* sigma_out, void* stream);
 
 #ifdef __cplusplus
 }

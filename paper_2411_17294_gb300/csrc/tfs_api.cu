@@ -812,6 +812,7 @@ const char* tfs_strerror(int code) {
         case TFS_ERR_STATE: return "call out of order (state not set)";
         case TFS_ERR_NOWORKSPACE: return "workspace not bound or too small";
         case TFS_ERR_FORMAT: return "checkpoint does not match this handle";
+        case TFS_ERR_TOOBIG: return "problem state exceeds the 64 MiB array of tfs_run_static";
         default: return "unknown status";
     }
 }

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libtfs.so")
 
 # status codes (include/tfs.h)
 TFS_OK, TFS_ERR_ARG, TFS_ERR_NOSOE, TFS_ERR_UNSTABLE, TFS_ERR_CUDA, TFS_ERR_STATE, TFS_ERR_NOWORKSPACE, \
-    TFS_ERR_FORMAT = range(8)
+    TFS_ERR_FORMAT, TFS_ERR_TOOBIG = range(9)
 TFS_FP64, TFS_FP32, TFS_FP32_PLAIN = 0, 1, 2
 TFS_PARAM_RE, TFS_PARAM_EPS, TFS_PARAM_STENCIL, TFS_PARAM_TRANSPORT, TFS_PARAM_UMAX = range(5)
 TFS_STENCIL_UPWIND3, TFS_STENCIL_CENTRAL2 = 0, 1
@@ -27,7 +27,7 @@ EXPORTS = [
     "tfs_create", "tfs_set_param", "tfs_set_soe", "tfs_transport_limit", "tfs_workspace_bytes", "tfs_bind_workspace",
     "tfs_set_state", "tfs_step", "tfs_get_stress", "tfs_step_index", "tfs_checkpoint_bytes", "tfs_save",
     "tfs_load", "tfs_adjoint_workspace_bytes", "tfs_bind_adjoint_workspace", "tfs_backward", "tfs_status",
-    "tfs_strerror", "tfs_destroy",
+    "tfs_strerror", "tfs_destroy", "tfs_run_static",
 ]
 
 
@@ -77,6 +77,9 @@ def load_library(path: str | None = None):
         "tfs_status": (ctypes.c_int, [H, ctypes.POINTER(ctypes.c_uint)]),
         "tfs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "tfs_destroy": (ctypes.c_int, [H]),
+        "tfs_run_static": (ctypes.c_int, [ctypes.POINTER(TfsGrid), ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, dp, vp, vp, vp,
+                                          ctypes.c_int, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
