@@ -109,6 +109,64 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+ADJOINT = dict(name="adjoint 2D 512^2, m=32, alpha=0.5, checkpoint every 50", dim=2, n=(512, 512), alpha=0.5,
+               Wi=1.0, beta=0.5, m=32, dt=1e-3, steps=100, K=50, seed=2)
+
+
+def adjoint_ratio(dev, precision):
+    """Time of tfs_backward (segment recompute + reverse sweep) over the time of
+    the forward run with checkpoints, on the adjoint workload (frozen gradient,
+    transport off as in that workload).  Returns a dict for the JSON line."""
+    import numpy as np
+    import torch
+
+    from paper_2411_17294_gb300 import inputs, soe, tfs
+
+    A = ADJOINT
+    mu, w = soe.build(A["alpha"], A["dt"], A["steps"] * A["dt"], A["m"])
+    s = tfs.Solver(A["dim"], A["n"], A["alpha"], A["Wi"], A["beta"], A["dt"], m=A["m"], precision=precision,
+                   mu=mu, w=w, transport=False, device=dev)
+    _, kap = inputs.spectral_velocity(A["dim"], A["n"], 32, A["seed"], device=dev)
+    kt = torch.as_tensor(kap, dtype=s.dtype, device=dev).contiguous()
+    sig0 = torch.as_tensor(inputs.random_stress(A["dim"], A["n"], 5, 0.1), dtype=s.dtype, device=dev)
+    nck = (A["steps"] + A["K"] - 1) // A["K"]
+    ckpts = [s.new_checkpoint() for _ in range(nck)]
+    s.ensure_adjoint_workspace(A["K"])
+    stream = torch.cuda.Stream(device=dev)
+
+    def forward():
+        s.set_state(sig0, stream=stream)
+        for k in range(A["steps"]):
+            if k % A["K"] == 0:
+                s.save(ckpts[k // A["K"]], stream=stream)
+            s.step(kt, kt, None, stream=stream)
+
+    with torch.cuda.stream(stream):
+        forward()                                   # warm-up (also builds the stability cache)
+        torch.cuda.synchronize()
+        dJ = s.stress(stream=stream)
+        s.backward(dJ, ckpts, A["K"], A["steps"], kt, None, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        forward()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_fwd = e0.elapsed_time(e1)
+        dJ = s.stress(stream=stream)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        s.backward(dJ, ckpts, A["K"], A["steps"], kt, None, stream=stream)   # synchronises at its end
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_bwd = e0.elapsed_time(e1)
+        wall_bwd = (time.perf_counter() - t0) * 1e3
+    s.close()
+    return {"workload": A["name"], "precision": {0: "fp64", 1: "fp32", 2: "fp32plain"}[precision],
+            "steps": A["steps"], "forward_ms": t_fwd, "backward_ms": max(t_bwd, wall_bwd),
+            "ratio": max(t_bwd, wall_bwd) / t_fwd}
+
+
 def cpu_baseline(steps_hint: int = 3, budget_s: float = 15.0):
     """The FP64 C oracle, as it stands, on a bounded sample of the workload:
     a 64^3 periodic sub-problem with the same parameters and velocity recipe."""
@@ -164,6 +222,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32plain"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -289,6 +348,13 @@ def main():
         e2e = {"value": world * N * W["m"] * args.e2e_steps / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
 
+    adj = None
+    if not args.no_adjoint:
+        try:
+            adj = [adjoint_ratio(dev, tfs.TFS_FP64), adjoint_ratio(dev, tfs.TFS_FP32)]
+        except Exception as exc:  # pragma: no cover - reported, not fatal
+            adj = {"error": str(exc)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         try:
@@ -315,6 +381,7 @@ def main():
             "device_flags": flags,
             "clocks": clocks,
             "e2e": e2e,
+            "adjoint_forward": adj,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
