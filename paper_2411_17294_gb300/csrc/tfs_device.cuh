@@ -162,6 +162,49 @@ __device__ __forceinline__ bool lu32_factor(LU32<NC>& F, float tiny) {
     return ok;
 }
 
+// FP32 LU without row exchanges, for matrices that are strictly diagonally
+// dominant by rows (Gaussian elimination is then stable without pivoting);
+// the swap flags are cleared so that lu32_solve applies no permutation.
+template <int NC>
+__device__ __forceinline__ bool lu32_factor_nopivot(LU32<NC>& F, float tiny) {
+    bool ok = true;
+    static_for<0, NC>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        static_for<k + 1, NC>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            F.sw[k][i] = false;
+        });
+        ok = ok && (fabsf(F.a[k][k]) > tiny);
+        const float inv = 1.0f / F.a[k][k];
+        F.a[k][k] = inv;
+        static_for<k + 1, NC>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            const float f = F.a[i][k] * inv;
+            F.a[i][k] = f;
+            static_for<k + 1, NC>([&](auto jj) {
+                constexpr int j = decltype(jj)::value;
+                F.a[i][j] = __fmaf_rn(-f, F.a[k][j], F.a[i][j]);
+            });
+        });
+    });
+    return ok;
+}
+
+template <int NC>
+__device__ __forceinline__ bool row_dominant(const LU32<NC>& F) {
+    bool dom = true;
+    static_for<0, NC>([&](auto rr) {
+        constexpr int r = decltype(rr)::value;
+        float off = 0.0f;
+        static_for<0, NC>([&](auto kk) {
+            constexpr int k = decltype(kk)::value;
+            if (k != r) off += fabsf(F.a[r][k]);
+        });
+        dom = dom && (fabsf(F.a[r][r]) > off);
+    });
+    return dom;
+}
+
 // x <- M^{-1} x with the factors of lu32_factor (permutation, then L, then U).
 template <int NC>
 __device__ __forceinline__ void lu32_solve(const LU32<NC>& F, float x[NC]) {

@@ -108,46 +108,78 @@ __device__ __forceinline__ T stencil_deriv(int stencil, T ua, T em2, T em1, T e0
     return ((T)-2 * em1 - (T)3 * e0 + (T)6 * ep1 - ep2) * (ih / (T)6);
 }
 
-// Transport term A (storage precision) for component c at point p = (x, y, z).
+// Transport stencil of component c at point p = (x, y, z), in two halves: the
+// loads (E = 2 sigma^n - sigma^{n-1} at the taps, u at the point) are issued
+// before the mode sweep so that their latency overlaps it; the arithmetic runs
+// after it.  Both upwind sides are loaded so that no load waits for u.
 template <typename T, int DIM>
-__device__ __forceinline__ T transport_term(const FwdArgs<T>& A, int c, int stencil, unsigned x, unsigned y,
-                                            unsigned z, long long p) {
+struct StencilLoads {
+    T n0, m0;                // sigma^n, sigma^{n-1} at the point
+    T n[DIM][4], m[DIM][4];  // taps -2, -1, +1, +2 along each axis
+    T u[DIM];
+};
+
+template <typename T, int DIM>
+__device__ __forceinline__ void load_stencil(const FwdArgs<T>& A, int c, int stencil, unsigned x, unsigned y,
+                                             unsigned z, long long p, StencilLoads<T, DIM>& L) {
     const T* sn = A.sig_n + (long long)c * A.N;
     const T* sm = A.sig_nm1 + (long long)c * A.N;
-    auto E = [&](long long q) -> T { return (T)2 * __ldg(sn + q) - __ldg(sm + q); };
-    const unsigned n[3] = {(unsigned)A.n0, (unsigned)A.n1, (unsigned)A.n2};
+    const unsigned nn[3] = {(unsigned)A.n0, (unsigned)A.n1, (unsigned)A.n2};
     const unsigned co[3] = {x, y, z};
     const long long strides[3] = {1, (long long)A.n0, (long long)A.n0 * A.n1};
-    const T e0 = E(p);
-    T adv = (T)0, lap = (T)0;
+    L.n0 = __ldg(sn + p);
+    L.m0 = __ldg(sm + p);
 #pragma unroll
     for (int ax = 0; ax < DIM; ++ax) {
         // neighbour indices with periodic wrap (|offset| <= 2, any n >= 1)
         auto nb = [&](int off) -> long long {
             int v = (int)co[ax] + off;
-            const int nn = (int)n[ax];
-            if (v < 0) v += nn;
-            if (v < 0) v += nn;
-            if (v >= nn) v -= nn;
-            if (v >= nn) v -= nn;
+            const int nax = (int)nn[ax];
+            if (v < 0) v += nax;
+            if (v < 0) v += nax;
+            if (v >= nax) v -= nax;
+            if (v >= nax) v -= nax;
             return p + ((long long)v - (long long)co[ax]) * strides[ax];
         };
-        const T ua = __ldg(A.u + (long long)ax * A.N + p);
-        const T ih = (T)A.inv_h[ax];
-        const T em1 = E(nb(-1)), ep1 = E(nb(1));
-        T em2 = (T)0, ep2 = (T)0;
+        L.u[ax] = __ldg(A.u + (long long)ax * A.N + p);
+        const long long q1 = nb(-1), q2 = nb(1);
+        L.n[ax][1] = __ldg(sn + q1);
+        L.m[ax][1] = __ldg(sm + q1);
+        L.n[ax][2] = __ldg(sn + q2);
+        L.m[ax][2] = __ldg(sm + q2);
         if (stencil == 0) {
-            if (ua >= (T)0) em2 = E(nb(-2));
-            else ep2 = E(nb(2));
+            const long long q0 = nb(-2), q3 = nb(2);
+            L.n[ax][0] = __ldg(sn + q0);
+            L.m[ax][0] = __ldg(sm + q0);
+            L.n[ax][3] = __ldg(sn + q3);
+            L.m[ax][3] = __ldg(sm + q3);
+        } else {
+            L.n[ax][0] = L.m[ax][0] = L.n[ax][3] = L.m[ax][3] = (T)0;
         }
-        adv += ua * stencil_deriv<T>(stencil, ua, em2, em1, e0, ep1, ep2, ih);
+    }
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ T finish_stencil(const FwdArgs<T>& A, int stencil, const StencilLoads<T, DIM>& L) {
+    const T e0 = (T)2 * L.n0 - L.m0;
+    T adv = (T)0, lap = (T)0;
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) {
+        const T em2 = (T)2 * L.n[ax][0] - L.m[ax][0];
+        const T em1 = (T)2 * L.n[ax][1] - L.m[ax][1];
+        const T ep1 = (T)2 * L.n[ax][2] - L.m[ax][2];
+        const T ep2 = (T)2 * L.n[ax][3] - L.m[ax][3];
+        const T ih = (T)A.inv_h[ax];
+        adv += L.u[ax] * stencil_deriv<T>(stencil, L.u[ax], em2, em1, e0, ep1, ep2, ih);
         if (A.eps != 0.0) lap += (em1 - (T)2 * e0 + ep1) * (ih * ih);
     }
     return (T)A.dt * adv - (T)(A.eps * A.dt) * lap;
 }
 
 // ----------------------------------------------------------- FP32 point solve
-// Packed residual r = R - (a x - dt (K x + x K^T)) in double-float, K exact as f2.
+// Packed residual r = R - a x + dt (K x + x K^T) with R, a, dt, K as double-float
+// and x a float vector.  R - a x is formed exactly (TwoProd); the operator term
+// is a compensated dot product (Ogita-Rump-Oishi Dot2) of the K entries with x.
 template <int DIM>
 __device__ __forceinline__ void residual_f2(const f2 K[3][3], F2c a, F2c dt, const f2 R[Packed<DIM>::NC],
                                             const float x[Packed<DIM>::NC], f2 r[Packed<DIM>::NC]) {
@@ -158,19 +190,29 @@ __device__ __forceinline__ void residual_f2(const f2 K[3][3], F2c a, F2c dt, con
         S[Packed<DIM>::I(c)][Packed<DIM>::J(c)] = x[c];
         S[Packed<DIM>::J(c)][Packed<DIM>::I(c)] = x[c];
     });
-    const f2 af{a.hi, a.lo}, dtf{dt.hi, dt.lo};
+    const f2 dtf{dt.hi, dt.lo};
     static_for<0, NC>([&](auto cc) {
         constexpr int c = decltype(cc)::value;
         constexpr int i = Packed<DIM>::I(c), j = Packed<DIM>::J(c);
-        f2 acc{0.0f, 0.0f};
+        float bs = 0.0f, be = 0.0f;
+        auto term = [&](const f2 k, float v) {
+            const f2 pr = two_prod(k.hi, v);
+            const f2 sm = two_sum_f2(bs, pr.hi);
+            bs = sm.hi;
+            be = __fadd_rn(be, __fadd_rn(sm.lo, __fmaf_rn(k.lo, v, pr.lo)));
+        };
         static_for<0, DIM>([&](auto ll) {
             constexpr int l = decltype(ll)::value;
-            acc = f2_add(acc, f2_mul_f(K[i][l], S[l][j]));
-            acc = f2_add(acc, f2_mul_f(K[j][l], S[i][l]));
+            term(K[i][l], S[l][j]);
+            term(K[j][l], S[i][l]);
         });
-        // R - a x + dt acc
-        f2 t = f2_add(R[c], f2_neg(f2_mul_f(af, x[c])));
-        r[c] = f2_add(t, f2_mul(dtf, acc));
+        const f2 ax = [&] {
+            f2 pr = two_prod(a.hi, x[c]);
+            pr.lo = __fmaf_rn(a.lo, x[c], pr.lo);
+            return pr;
+        }();
+        const f2 t = f2_add(R[c], f2_neg(ax));
+        r[c] = f2_add(t, f2_mul(dtf, fast_two_sum(bs, be)));
     });
 }
 
@@ -194,7 +236,9 @@ __device__ __forceinline__ bool solve_point_f32(const f2 K[3][3], F2c a, F2c dt,
             F.a[r][k] = (r == k) ? __fmaf_rn(-dtf, v, af) : -dtf * v;
         });
     });
-    const bool ok = lu32_factor<NC>(F, 1e-30f);
+    // row diagonal dominance (the usual case: a = eta + dt/Wi against dt |kappa*|)
+    // allows elimination without row exchanges; otherwise partial pivoting
+    const bool ok = row_dominant<NC>(F) ? lu32_factor_nopivot<NC>(F, 1e-30f) : lu32_factor<NC>(F, 1e-30f);
     float x0[NC];
     static_for<0, NC>([&](auto rr) {
         constexpr int r = decltype(rr)::value;
@@ -228,6 +272,24 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, T* buf, long l
     const long long p = t0 + lane;
     const bool active = p < N;
     const int m = A.m;
+
+    // ---- global loads of this (point, component), issued before the mode sweep
+    unsigned px = 0, py = 0, pz = 0;
+    if (active) {
+        const unsigned pu = (unsigned)p;
+        px = pu % (unsigned)A.n0;
+        const unsigned r1 = pu / (unsigned)A.n0;
+        py = r1 % (unsigned)A.n1;
+        pz = r1 / (unsigned)A.n1;
+    }
+    const int ci = Packed<DIM>::I(c), cj = Packed<DIM>::J(c);
+    const long long kij = (long long)(ci * DIM + cj) * N + (active ? p : 0);
+    const long long kji = (long long)(cj * DIM + ci) * N + (active ? p : 0);
+    const T kn_ij = A.kap_n[kij], km_ij = A.kap_nm1[kij], kn_ji = A.kap_n[kji], km_ji = A.kap_nm1[kji];
+    StencilLoads<T, DIM> SL;
+    if constexpr (TRANSPORT) {
+        if (active) load_stencil<T, DIM>(A, c, stencil, px, py, pz, p, SL);
+    }
 
     // ---- (a4) history sum over the modes of component c (Q_j stored in place of level n-1)
     double Hd = 0.0;
@@ -286,39 +348,25 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, T* buf, long l
     }
 
     // ---- right-hand side component c
-    unsigned px = 0, py = 0, pz = 0;
-    if (active) {
-        const unsigned pu = (unsigned)p;
-        px = pu % (unsigned)A.n0;
-        const unsigned r1 = pu / (unsigned)A.n0;
-        py = r1 % (unsigned)A.n1;
-        pz = r1 / (unsigned)A.n1;
-    }
-    const int ci = Packed<DIM>::I(c), cj = Packed<DIM>::J(c);
     if constexpr (F32) {
         f2 R{0.0f, 0.0f};
         if (active) {
-            const long long kij = (long long)(ci * DIM + cj) * N + p;
-            const long long kji = (long long)(cj * DIM + ci) * N + p;
-            const f2 kab = two_sum_f2(2.0f * (float)A.kap_n[kij], -(float)A.kap_nm1[kij]);
-            const f2 kba = two_sum_f2(2.0f * (float)A.kap_n[kji], -(float)A.kap_nm1[kji]);
+            const f2 kab = two_sum_f2(2.0f * (float)kn_ij, -(float)km_ij);
+            const f2 kba = two_sum_f2(2.0f * (float)kn_ji, -(float)km_ji);
             const f2 ks = f2_add(kab, kba);
             const f2 eta{A.eta_f2.hi, A.eta_f2.lo}, src{A.src_f2.hi, A.src_f2.lo};
             R = f2_add(f2_mul_f(eta, (float)s0c), f2_neg(Hf));
             R = f2_add(R, f2_mul(src, ks));
-            if constexpr (TRANSPORT) R = f2_add_f(R, -(float)transport_term<T, DIM>(A, c, stencil, px, py, pz, p));
+            if constexpr (TRANSPORT) R = f2_add_f(R, -(float)finish_stencil<T, DIM>(A, stencil, SL));
         }
         f2* sR = reinterpret_cast<f2*>(sR_raw);
         sR[c * kTile + lane] = R;
     } else {
         double R = 0.0;
         if (active) {
-            const long long kij = (long long)(ci * DIM + cj) * N + p;
-            const long long kji = (long long)(cj * DIM + ci) * N + p;
-            const double ks = (2.0 * (double)A.kap_n[kij] - (double)A.kap_nm1[kij]) +
-                              (2.0 * (double)A.kap_n[kji] - (double)A.kap_nm1[kji]);
+            const double ks = (2.0 * (double)kn_ij - (double)km_ij) + (2.0 * (double)kn_ji - (double)km_ji);
             R = A.eta * s0c - Hd + A.dt * A.G * A.g * ks;
-            if constexpr (TRANSPORT) R -= (double)transport_term<T, DIM>(A, c, stencil, px, py, pz, p);
+            if constexpr (TRANSPORT) R -= (double)finish_stencil<T, DIM>(A, stencil, SL);
         }
         double* sR = reinterpret_cast<double*>(sR_raw);
         sR[c * kTile + lane] = R;
