@@ -128,7 +128,9 @@ int tfs_set_soe(tfs_handle h, const double* mu, const double* w, int m);
    when alpha < 1 (TFS_ERR_NOSOE).  Host only; computed once per SOE/stencil. */
 int tfs_transport_limit(tfs_handle h, double* umax_out);
 
-/* Bytes of device workspace the handle needs (stress ring, modes, status). */
+/* Bytes of device workspace the handle needs: 256 (status) + 5 fields of
+   nc N elements (sigma0 copy, stress ring of 3, transport term) + 2 mode levels
+   of m nc N elements, each rounded up to 256 bytes. */
 size_t tfs_workspace_bytes(tfs_handle h);
 
 /* Bind caller-owned device memory of at least tfs_workspace_bytes bytes,
@@ -141,7 +143,8 @@ int tfs_set_state(tfs_handle h, const void* sigma0, void* stream);
 
 /* One step t_n -> t_{n+1}.  grad_u_n = kappa^n, grad_u_nm1 = kappa^{n-1}
    (NULL = same as grad_u_n); u = velocity [d][N] (NULL allowed when transport
-   is off).  Enqueues one kernel launch. */
+   is off).  Enqueues the step kernel, preceded by the transport pre-pass when
+   transport is on. */
 int tfs_step(tfs_handle h, const void* grad_u_n, const void* grad_u_nm1, const void* u, void* stream);
 
 /* Copy the current stress sigma^n to out [nc][N] (device). */
@@ -191,10 +194,10 @@ int tfs_destroy(tfs_handle h);
    framework that owns all device memory, an allocation-free real-time loop, a
    plug-in without an allocator).  The paper has no counterpart: this is an
    interface convenience around the same step kernel.
-   The whole state (stress ring, sigma0 copy, status word, both mode levels)
+   The whole state (stress ring, sigma0 copy, transport term, status word, both mode levels)
    lives in one fixed device array of 64 MiB compiled into the library, which
    every GPU that loads the library holds until the process exits; problems
-   whose state needs more (256 + 4 up256(nc N s) + 2 up256(m nc N s) bytes,
+   whose state needs more (256 + 5 up256(nc N s) + 2 up256(m nc N s) bytes,
    s = element size, up256 = round up to 256) return TFS_ERR_TOOBIG before any
    device work.  Arguments as tfs_create / tfs_set_soe (mu, w: host, m
    entries, NULL when alpha == 1); Re = 1, eps = 0, upwind3 stencil, transport

@@ -51,6 +51,7 @@ struct tfs_ctx {
     unsigned* flags = nullptr;
     char* sigma0 = nullptr;        // copy of the initial stress
     char* sig[3] = {nullptr, nullptr, nullptr};
+    char* trans = nullptr;         // transport term A [nc][N] of the current step
     char* modes[2] = {nullptr, nullptr};
     int cur_sig = 0, prev_sig = 1; // ring slots of levels n and n-1
     int cur_mode = 0;              // ring slot of modes level n (n-1 in the other)
@@ -236,6 +237,8 @@ void layout_forward(tfs_ctx* h, char* base) {
         h->sig[i] = p;
         p += align_up(h->field_bytes());
     }
+    h->trans = p;
+    p += align_up(h->field_bytes());
     for (int i = 0; i < 2; ++i) {
         h->modes[i] = p;
         p += align_up(h->modes_bytes());
@@ -243,7 +246,7 @@ void layout_forward(tfs_ctx* h, char* base) {
 }
 
 size_t forward_bytes(const tfs_ctx* h) {
-    return kAlign + 4 * align_up(h->field_bytes()) + 2 * align_up(h->modes_bytes());
+    return kAlign + 5 * align_up(h->field_bytes()) + 2 * align_up(h->modes_bytes());
 }
 
 F2c split_f2(double v) {
@@ -308,6 +311,7 @@ int do_step(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* s
         a.sig_nm1 = (const double*)h->sig[h->prev_sig];
         a.sig_np1 = (double*)h->sig[nxt];
         a.sig_copy = (double*)sig_copy;
+        a.trans = (double*)h->trans;
         a.modes_n = (const double*)h->modes[cm];
         a.modes_nm1 = (double*)h->modes[pm];
         a.g = g_alpha(h, h->step);
@@ -324,6 +328,7 @@ int do_step(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* s
         a.sig_nm1 = (const float*)h->sig[h->prev_sig];
         a.sig_np1 = (float*)h->sig[nxt];
         a.sig_copy = (float*)sig_copy;
+        a.trans = (float*)h->trans;
         a.modes_n = (const float*)h->modes[cm];
         a.modes_nm1 = (float*)h->modes[pm];
         a.g = g_alpha(h, h->step);

@@ -8,18 +8,23 @@
 //   solve (eta + dt/Wi) s - dt (kappa* s + s kappa*^T) = R   -> sigma^{n+1}
 //   sigma_j^{n+1} = -c_j (b1 sigma_j^n + b2 sigma_j^{n-1}) + rho_j (sigma^{n+1} - sigma0)
 //
-// Structure.  A persistent block loops over tiles of 32 consecutive points.
-// The m x nc (mode, component) planes of both levels of the next tile are
-// copied global -> shared with cp.async (16-byte chunks, zero-filled past the
-// end of the grid) while the current tile is computed, so the mode stream --
-// 94% of the bytes -- is always in flight without holding registers.  Inside
-// a tile, warp c handles stress component c (lane = point): it forms
-// Q_j = b1 x + b2 y from shared memory (stored back in place of the older
-// level), the history sum H (FP32 storage: compensated Dot2 with eta_j split
-// hi + lo) and its component of the right-hand side (transport stencil read
-// through the read-only cache).  Warp 0 then solves the 32 point systems with
-// lane = point; the other warps write the new mode level from the Q_j kept in
-// shared memory.  Every mode value is read once and written once.
+// Structure.  When transport is on, a small pre-pass (transport_kernel)
+// evaluates the stencil term A at every point (one thread per point, all
+// components) and the step kernel reads it like any other per-point input.
+// The step kernel is persistent: each block loops over tiles of 32 consecutive
+// points, and everything a tile reads -- the m x nc (mode, component) planes of
+// both levels, kappa^n, kappa^{n-1}, A, sigma0, and for alpha = 1 the stress
+// levels -- is copied global -> shared with cp.async (16-byte chunks,
+// zero-filled past the end of the grid) while the previous tile is computed.
+// The mode stream (94% of the bytes) and every per-point input are therefore
+// in flight without holding registers, and the compute phase makes no global
+// loads.  Inside a tile, warp c handles stress component c (lane = point): it
+// forms Q_j = b1 x + b2 y from shared memory (stored back in place of the
+// older level), the history sum H (FP32 storage: compensated Dot2 with eta_j
+// split hi + lo) and its component of the right-hand side.  Warp 0 then solves
+// the 32 point systems with lane = point; all warps write the new mode level
+// from the Q_j kept in shared memory.  Every mode value is read once and
+// written once.
 //
 // Point solve.  FP64 storage: FP64 Gaussian elimination with partial
 // pivoting.  FP32 storage: FP32 LU with partial pivoting, one refinement step
@@ -62,39 +67,70 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Copy both mode levels of one tile into a stage buffer laid out as
-// [level][j][c][32] (level 0 = n, level 1 = n-1).
-template <typename T, int NC>
-__device__ __forceinline__ void issue_tile(const FwdArgs<T>& A, T* buf, long long t0, int tid, int nthr,
-                                           bool vec16) {
-    const int m = A.m;
+// Shared-memory stage of one tile: planes of 32 elements, in this order
+//   modes level n [m][nc], modes level n-1 [m][nc], kappa^n [d*d], kappa^{n-1} [d*d],
+//   A [nc] (transport), sigma0 [nc] (nonzero initial stress), sigma^n, sigma^{n-1} [nc] (alpha = 1).
+struct StageMap {
+    int modes;          // first plane of each group
+    int kn, km, tr, s0, sig;
+    int planes;         // total
+};
+
+template <int DIM>
+__host__ __device__ __forceinline__ StageMap stage_map(int m, bool transport, bool sigma0, bool classic) {
+    constexpr int NC = DIM == 2 ? 3 : 6;
+    StageMap S;
+    S.modes = 0;
+    S.kn = 2 * m * NC;
+    S.km = S.kn + DIM * DIM;
+    S.tr = S.km + DIM * DIM;
+    S.s0 = S.tr + (transport ? NC : 0);
+    S.sig = S.s0 + (sigma0 ? NC : 0);
+    S.planes = S.sig + (classic ? 2 * NC : 0);
+    return S;
+}
+
+// Global source of stage plane `plane` (the segment of 32 points starts at t0).
+template <typename T, int DIM>
+__device__ __forceinline__ const T* plane_src(const FwdArgs<T>& A, const StageMap& S, int plane) {
+    constexpr int NC = DIM == 2 ? 3 : 6;
     const long long N = A.N;
-    const int planes_per_level = m * NC;
-    const int planes = 2 * planes_per_level;
+    if (plane < S.kn) {
+        const int mnc = A.m * NC;
+        return plane < mnc ? A.modes_n + (long long)plane * N : A.modes_nm1 + (long long)(plane - mnc) * N;
+    }
+    if (plane < S.km) return A.kap_n + (long long)(plane - S.kn) * N;
+    if (plane < S.tr) return A.kap_nm1 + (long long)(plane - S.km) * N;
+    if (plane < S.s0) return A.trans + (long long)(plane - S.tr) * N;
+    if (plane < S.sig) return A.sigma0 + (long long)(plane - S.s0) * N;
+    const int k = plane - S.sig;
+    return k < NC ? A.sig_n + (long long)k * N : A.sig_nm1 + (long long)(k - NC) * N;
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ void issue_tile(const FwdArgs<T>& A, const StageMap& S, T* buf, long long t0, int tid,
+                                           int nthr, bool vec16) {
+    const long long N = A.N;
     if (vec16) {
         constexpr int EPC = 16 / sizeof(T);    // elements per chunk
         constexpr int CPP = kTile / EPC;       // chunks per plane segment
-        const int total = planes * CPP;
+        const int total = S.planes * CPP;
         for (int q = tid; q < total; q += nthr) {
             const int plane = q / CPP;
             const int k = q - plane * CPP;
-            const int level = plane >= planes_per_level;
-            const int jc = plane - level * planes_per_level;
             const long long p0 = t0 + (long long)k * EPC;
             long long valid = N - p0;
             valid = valid < 0 ? 0 : (valid > EPC ? EPC : valid);
-            const T* base = (level ? A.modes_nm1 : A.modes_n) + (long long)jc * N;
+            const T* base = plane_src<T, DIM>(A, S, plane);
             cp_async16(buf + plane * kTile + k * EPC, base + (valid > 0 ? p0 : 0), (int)(valid * sizeof(T)));
         }
     } else {
-        const int total = planes * kTile;
+        const int total = S.planes * kTile;
         for (int q = tid; q < total; q += nthr) {
             const int plane = q / kTile;
             const int l = q - plane * kTile;
-            const int level = plane >= planes_per_level;
-            const int jc = plane - level * planes_per_level;
             const long long p = t0 + l;
-            const T* base = (level ? A.modes_nm1 : A.modes_n) + (long long)jc * N;
+            const T* base = plane_src<T, DIM>(A, S, plane);
             cp_async_small<sizeof(T)>(buf + q, base + (p < N ? p : 0), p < N ? (int)sizeof(T) : 0);
         }
     }
@@ -260,10 +296,37 @@ __device__ __forceinline__ bool solve_point_f32(const f2 K[3][3], F2c a, F2c dt,
     return ok;
 }
 
-// ----------------------------------------------------------------- the kernel
+// ----------------------------------------------------------------- the kernels
+// Transport pre-pass: A_c(p) = dt sum_a u_a D_a(E_c) - eps dt Lap(E_c) for all
+// components at point p (one thread per point), and the Courant flag.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) transport_kernel(const FwdArgs<T> A, const int stencil) {
+    constexpr int NC = Packed<DIM>::NC;
+    const long long N = A.N;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        const unsigned pu = (unsigned)p;
+        const unsigned px = pu % (unsigned)A.n0;
+        const unsigned r1 = pu / (unsigned)A.n0;
+        const unsigned py = r1 % (unsigned)A.n1;
+        const unsigned pz = r1 / (unsigned)A.n1;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            StencilLoads<T, DIM> SL;
+            load_stencil<T, DIM>(A, c, stencil, px, py, pz, p, SL);
+            A.trans[(long long)c * N + p] = finish_stencil<T, DIM>(A, stencil, SL);
+        }
+        if (A.courant_coef > 0.0) {
+            double cr = 0.0;
+#pragma unroll
+            for (int ax = 0; ax < DIM; ++ax) cr += fabs((double)A.u[(long long)ax * N + p]) * A.inv_h[ax];
+            if (A.courant_coef * cr > A.courant_limit) atomicOr(A.flags, 4u);
+        }
+    }
+}
+
 template <typename T, int DIM, bool TRANSPORT, bool COMP>
-__device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, T* buf, long long t0, int stencil, int classic,
-                                             void* sR_raw, float* sD) {
+__device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap& S, const T* __restrict__ buf_c,
+                                             T* buf, long long t0, int classic, void* sR_raw, float* sD) {
     constexpr int NC = Packed<DIM>::NC;
     constexpr bool F32 = sizeof(T) == 4;
     const int lane = threadIdx.x;
@@ -272,42 +335,25 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, T* buf, long l
     const long long p = t0 + lane;
     const bool active = p < N;
     const int m = A.m;
-
-    // ---- global loads of this (point, component), issued before the mode sweep
-    unsigned px = 0, py = 0, pz = 0;
-    if (active) {
-        const unsigned pu = (unsigned)p;
-        px = pu % (unsigned)A.n0;
-        const unsigned r1 = pu / (unsigned)A.n0;
-        py = r1 % (unsigned)A.n1;
-        pz = r1 / (unsigned)A.n1;
-    }
-    const int ci = Packed<DIM>::I(c), cj = Packed<DIM>::J(c);
-    const long long kij = (long long)(ci * DIM + cj) * N + (active ? p : 0);
-    const long long kji = (long long)(cj * DIM + ci) * N + (active ? p : 0);
-    const T kn_ij = A.kap_n[kij], km_ij = A.kap_nm1[kij], kn_ji = A.kap_n[kji], km_ji = A.kap_nm1[kji];
-    StencilLoads<T, DIM> SL;
-    if constexpr (TRANSPORT) {
-        if (active) load_stencil<T, DIM>(A, c, stencil, px, py, pz, p, SL);
-    }
+    const bool has_s0 = A.sigma0 != nullptr;
+    (void)buf_c;
 
     // ---- (a4) history sum over the modes of component c (Q_j stored in place of level n-1)
     double Hd = 0.0;
     f2 Hf{0.0f, 0.0f};
-    const double s0c = (active && A.sigma0) ? (double)A.sigma0[(long long)c * N + p] : 0.0;
+    const T s0c = has_s0 ? buf[(S.s0 + c) * kTile + lane] : (T)0;
     if (classic) {
-        if (active) {
-            const long long q = (long long)c * N + p;
-            if constexpr (F32) {
-                // b1 sigma^n + b2 sigma^{n-1} + b0 sigma0, exact products by powers of two and TwoProd
-                f2 h = two_sum_f2(-2.0f * (float)A.sig_n[q], 0.5f * (float)A.sig_nm1[q]);
-                Hf = f2_add(h, two_prod(1.5f, (float)s0c));
-            } else {
-                Hd = kB1 * (double)A.sig_n[q] + kB2 * (double)A.sig_nm1[q] + kB0 * s0c;
-            }
+        const T sn = buf[(S.sig + c) * kTile + lane];
+        const T sm = buf[(S.sig + NC + c) * kTile + lane];
+        if constexpr (F32) {
+            // b1 sigma^n + b2 sigma^{n-1} + b0 sigma0: exact products by powers of two, TwoProd for b0
+            const f2 h = two_sum_f2(-2.0f * (float)sn, 0.5f * (float)sm);
+            Hf = f2_add(h, two_prod(1.5f, (float)s0c));
+        } else {
+            Hd = kB1 * (double)sn + kB2 * (double)sm + kB0 * (double)s0c;
         }
     } else {
-        T* lv0 = buf + (c * kTile + lane);
+        const T* lv0 = buf + (c * kTile + lane);
         T* lv1 = buf + ((m * NC + c) * kTile + lane);
         if constexpr (F32 && COMP) {
             float hs = 0.f, he = 0.f;
@@ -319,9 +365,9 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, T* buf, long l
                 lv1[j * NC * kTile] = qj;
                 const float pr = __fmul_rn(A.mc.eta_hi[j], qj);
                 const float pe = __fmaf_rn(A.mc.eta_hi[j], qj, -pr);
-                const f2 s = two_sum_f2(hs, pr);
-                hs = s.hi;
-                he = __fadd_rn(he, __fadd_rn(s.lo, __fmaf_rn(A.mc.eta_lo[j], qj, pe)));
+                const f2 sm = two_sum_f2(hs, pr);
+                hs = sm.hi;
+                he = __fadd_rn(he, __fadd_rn(sm.lo, __fmaf_rn(A.mc.eta_lo[j], qj, pe)));
             }
             Hf = fast_two_sum(hs, he);
         } else if constexpr (F32) {
@@ -348,102 +394,82 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, T* buf, long l
     }
 
     // ---- right-hand side component c
+    const int ci = Packed<DIM>::I(c), cj = Packed<DIM>::J(c);
+    const T kn_ij = buf[(S.kn + ci * DIM + cj) * kTile + lane];
+    const T km_ij = buf[(S.km + ci * DIM + cj) * kTile + lane];
+    const T kn_ji = buf[(S.kn + cj * DIM + ci) * kTile + lane];
+    const T km_ji = buf[(S.km + cj * DIM + ci) * kTile + lane];
     if constexpr (F32) {
-        f2 R{0.0f, 0.0f};
-        if (active) {
-            const f2 kab = two_sum_f2(2.0f * (float)kn_ij, -(float)km_ij);
-            const f2 kba = two_sum_f2(2.0f * (float)kn_ji, -(float)km_ji);
-            const f2 ks = f2_add(kab, kba);
-            const f2 eta{A.eta_f2.hi, A.eta_f2.lo}, src{A.src_f2.hi, A.src_f2.lo};
-            R = f2_add(f2_mul_f(eta, (float)s0c), f2_neg(Hf));
-            R = f2_add(R, f2_mul(src, ks));
-            if constexpr (TRANSPORT) R = f2_add_f(R, -(float)finish_stencil<T, DIM>(A, stencil, SL));
-        }
-        f2* sR = reinterpret_cast<f2*>(sR_raw);
-        sR[c * kTile + lane] = R;
+        const f2 kab = two_sum_f2(2.0f * (float)kn_ij, -(float)km_ij);
+        const f2 kba = two_sum_f2(2.0f * (float)kn_ji, -(float)km_ji);
+        const f2 ks = f2_add(kab, kba);
+        const f2 eta{A.eta_f2.hi, A.eta_f2.lo}, src{A.src_f2.hi, A.src_f2.lo};
+        f2 R = f2_add(f2_mul_f(eta, (float)s0c), f2_neg(Hf));
+        R = f2_add(R, f2_mul(src, ks));
+        if constexpr (TRANSPORT) R = f2_add_f(R, -(float)buf[(S.tr + c) * kTile + lane]);
+        reinterpret_cast<f2*>(sR_raw)[c * kTile + lane] = R;
     } else {
-        double R = 0.0;
-        if (active) {
-            const double ks = (2.0 * (double)kn_ij - (double)km_ij) + (2.0 * (double)kn_ji - (double)km_ji);
-            R = A.eta * s0c - Hd + A.dt * A.G * A.g * ks;
-            if constexpr (TRANSPORT) R -= (double)finish_stencil<T, DIM>(A, stencil, SL);
-        }
-        double* sR = reinterpret_cast<double*>(sR_raw);
-        sR[c * kTile + lane] = R;
+        const double ks = (2.0 * (double)kn_ij - (double)km_ij) + (2.0 * (double)kn_ji - (double)km_ji);
+        double R = A.eta * (double)s0c - Hd + A.dt * A.G * A.g * ks;
+        if constexpr (TRANSPORT) R -= (double)buf[(S.tr + c) * kTile + lane];
+        reinterpret_cast<double*>(sR_raw)[c * kTile + lane] = R;
     }
     __syncthreads();
 
     // ---- (a2) + (a5) point solve by warp 0
     if (c == 0) {
-        float dsig[NC];
+        T out[NC];
+        unsigned fl = 0u;
+        if constexpr (F32) {
+            f2 K[3][3];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a)
+#pragma unroll
+                for (int b = 0; b < DIM; ++b)
+                    K[a][b] = two_sum_f2(2.0f * (float)buf[(S.kn + a * DIM + b) * kTile + lane],
+                                         -(float)buf[(S.km + a * DIM + b) * kTile + lane]);
+            const f2* sR = reinterpret_cast<const f2*>(sR_raw);
+            f2 R[NC], x[NC];
+#pragma unroll
+            for (int r = 0; r < NC; ++r) R[r] = sR[r * kTile + lane];
+            if (!solve_point_f32<DIM>(K, A.a_f2, A.dt_f2, R, x)) fl |= 2u;
+#pragma unroll
+            for (int r = 0; r < NC; ++r) out[r] = (T)(x[r].hi + x[r].lo);
+        } else {
+            double K[3][3];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a)
+#pragma unroll
+                for (int b = 0; b < DIM; ++b)
+                    K[a][b] = 2.0 * (double)buf[(S.kn + a * DIM + b) * kTile + lane] -
+                              (double)buf[(S.km + a * DIM + b) * kTile + lane];
+            const double* sR = reinterpret_cast<const double*>(sR_raw);
+            double x[NC];
+#pragma unroll
+            for (int r = 0; r < NC; ++r) x[r] = sR[r * kTile + lane];
+            double M[NC][NC];
+            assemble_M<DIM>(K, A.a, A.dt, M);
+            if (!gauss_pp<NC>(M, x, 1e-300)) fl |= 2u;
+#pragma unroll
+            for (int r = 0; r < NC; ++r) out[r] = (T)x[r];
+        }
+        bool finite = true;
+#pragma unroll
+        for (int r = 0; r < NC; ++r) {
+            finite = finite && isfinite((double)out[r]);
+            const T s0r = has_s0 ? buf[(S.s0 + r) * kTile + lane] : (T)0;
+            // the push-forward uses the stored value of sigma^{n+1}
+            if constexpr (F32) sD[r * kTile + lane] = __fsub_rn((float)out[r], (float)s0r);
+            else reinterpret_cast<double*>(sD)[r * kTile + lane] = (double)out[r] - (double)s0r;
+        }
         if (active) {
-            unsigned fl = 0u;
-            T out[NC];
-            if constexpr (F32) {
-                f2 K[3][3];
-#pragma unroll
-                for (int a = 0; a < DIM; ++a)
-#pragma unroll
-                    for (int b = 0; b < DIM; ++b) {
-                        const long long q = (long long)(a * DIM + b) * N + p;
-                        K[a][b] = two_sum_f2(2.0f * (float)A.kap_n[q], -(float)A.kap_nm1[q]);
-                    }
-                const f2* sR = reinterpret_cast<const f2*>(sR_raw);
-                f2 R[NC], x[NC];
-#pragma unroll
-                for (int r = 0; r < NC; ++r) R[r] = sR[r * kTile + lane];
-                if (!solve_point_f32<DIM>(K, A.a_f2, A.dt_f2, R, x)) fl |= 2u;
-#pragma unroll
-                for (int r = 0; r < NC; ++r) out[r] = (T)(x[r].hi + x[r].lo);
-            } else {
-                double K[3][3];
-#pragma unroll
-                for (int a = 0; a < DIM; ++a)
-#pragma unroll
-                    for (int b = 0; b < DIM; ++b) {
-                        const long long q = (long long)(a * DIM + b) * N + p;
-                        K[a][b] = 2.0 * (double)A.kap_n[q] - (double)A.kap_nm1[q];
-                    }
-                const double* sR = reinterpret_cast<const double*>(sR_raw);
-                double x[NC];
-#pragma unroll
-                for (int r = 0; r < NC; ++r) x[r] = sR[r * kTile + lane];
-                double M[NC][NC];
-                assemble_M<DIM>(K, A.a, A.dt, M);
-                if (!gauss_pp<NC>(M, x, 1e-300)) fl |= 2u;
-#pragma unroll
-                for (int r = 0; r < NC; ++r) out[r] = (T)x[r];
-            }
-            bool finite = true;
 #pragma unroll
             for (int r = 0; r < NC; ++r) {
-                finite = finite && isfinite((double)out[r]);
                 A.sig_np1[(long long)r * N + p] = out[r];
                 if (A.sig_copy) A.sig_copy[(long long)r * N + p] = out[r];
-                const T s0r = A.sigma0 ? A.sigma0[(long long)r * N + p] : (T)0;
-                // the push-forward uses the stored value of sigma^{n+1}
-                dsig[r] = 0.0f;
-                if constexpr (F32) dsig[r] = __fsub_rn((float)out[r], (float)s0r);
-                else reinterpret_cast<double*>(sD)[r * kTile + lane] = (double)out[r] - (double)s0r;
             }
             if (!finite) fl |= 1u;
-            if (TRANSPORT && A.courant_coef > 0.0) {
-                double cr = 0.0;
-#pragma unroll
-                for (int ax = 0; ax < DIM; ++ax) cr += fabs((double)A.u[(long long)ax * N + p]) * A.inv_h[ax];
-                if (A.courant_coef * cr > A.courant_limit) fl |= 4u;
-            }
             if (fl) atomicOr(A.flags, fl);
-        } else {
-#pragma unroll
-            for (int r = 0; r < NC; ++r) {
-                dsig[r] = 0.0f;
-                if constexpr (!F32) reinterpret_cast<double*>(sD)[r * kTile + lane] = 0.0;
-            }
-        }
-        if constexpr (F32) {
-#pragma unroll
-            for (int r = 0; r < NC; ++r) sD[r * kTile + lane] = dsig[r];
         }
     }
     __syncthreads();
@@ -469,43 +495,42 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, T* buf, long l
 
 template <typename T, int DIM, bool TRANSPORT, bool COMP>
 __global__ void __launch_bounds__(32 * Packed<DIM>::NC, DIM == 3 ? 2 : 4)
-fwd_kernel(const FwdArgs<T> A, const int stencil, const int classic, const long long num_tiles, const int stages,
-           const int vec16) {
+fwd_kernel(const FwdArgs<T> A, const int classic, const long long num_tiles, const int stages, const int vec16) {
     constexpr int NC = Packed<DIM>::NC;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(16) double sR_store[NC * kTile];       // R per (component, point): double or f2
     __shared__ __align__(16) double sD_store[NC * kTile];       // sigma^{n+1} - sigma0 (float or double)
-    const size_t stage_elems = (size_t)2 * A.m * NC * kTile;
+    const StageMap S = stage_map<DIM>(classic ? 0 : A.m, TRANSPORT, A.sigma0 != nullptr, classic != 0);
+    const size_t stage_elems = (size_t)S.planes * kTile;
     T* buf0 = reinterpret_cast<T*>(smem);
     T* buf1 = buf0 + stage_elems;
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const int nthr = 32 * NC;
-    const bool staged = !classic && A.m > 0;
     float* sD = reinterpret_cast<float*>(sD_store);
 
     if (stages == 2) {
         long long tile = blockIdx.x;
-        if (staged && tile < num_tiles) issue_tile<T, NC>(A, buf0, tile * kTile, tid, nthr, vec16 != 0);
+        if (tile < num_tiles) issue_tile<T, DIM>(A, S, buf0, tile * kTile, tid, nthr, vec16 != 0);
         cp_async_commit();
         for (int it = 0; tile < num_tiles; ++it, tile += gridDim.x) {
             const long long next = tile + gridDim.x;
             T* cur = (it & 1) ? buf1 : buf0;
             T* nxt = (it & 1) ? buf0 : buf1;
-            if (staged && next < num_tiles) issue_tile<T, NC>(A, nxt, next * kTile, tid, nthr, vec16 != 0);
+            if (next < num_tiles) issue_tile<T, DIM>(A, S, nxt, next * kTile, tid, nthr, vec16 != 0);
             cp_async_commit();
             cp_async_wait<1>();
             __syncthreads();
-            compute_tile<T, DIM, TRANSPORT, COMP>(A, cur, tile * kTile, stencil, classic, sR_store, sD);
+            compute_tile<T, DIM, TRANSPORT, COMP>(A, S, cur, cur, tile * kTile, classic, sR_store, sD);
             __syncthreads();
         }
         cp_async_wait<0>();
     } else {
         for (long long tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
-            if (staged) issue_tile<T, NC>(A, buf0, tile * kTile, tid, nthr, vec16 != 0);
+            issue_tile<T, DIM>(A, S, buf0, tile * kTile, tid, nthr, vec16 != 0);
             cp_async_commit();
             cp_async_wait<0>();
             __syncthreads();
-            compute_tile<T, DIM, TRANSPORT, COMP>(A, buf0, tile * kTile, stencil, classic, sR_store, sD);
+            compute_tile<T, DIM, TRANSPORT, COMP>(A, S, buf0, buf0, tile * kTile, classic, sR_store, sD);
             __syncthreads();
         }
     }
@@ -514,10 +539,6 @@ fwd_kernel(const FwdArgs<T> A, const int stencil, const int classic, const long 
 template <typename T, int DIM, bool TRANSPORT, bool COMP>
 cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s) {
     constexpr int NC = Packed<DIM>::NC;
-    auto kern = fwd_kernel<T, DIM, TRANSPORT, COMP>;
-    const long long num_tiles = (a.N + kTile - 1) / kTile;
-    const int m = cfg.classic ? 0 : a.m;
-    const size_t stage_bytes = (size_t)2 * m * NC * kTile * sizeof(T);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -525,6 +546,19 @@ cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s
     e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    if (TRANSPORT) {
+        if (!a.trans) return cudaErrorInvalidValue;
+        const int threads = 256;
+        long long blocks = (a.N + threads - 1) / threads;
+        if (blocks > (long long)sms * 16) blocks = (long long)sms * 16;
+        transport_kernel<T, DIM><<<(unsigned)blocks, threads, 0, s>>>(a, cfg.stencil);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    auto kern = fwd_kernel<T, DIM, TRANSPORT, COMP>;
+    const long long num_tiles = (a.N + kTile - 1) / kTile;
+    const StageMap S = stage_map<DIM>(cfg.classic ? 0 : a.m, TRANSPORT, a.sigma0 != nullptr, cfg.classic);
+    const size_t stage_bytes = (size_t)S.planes * kTile * sizeof(T);
     const size_t static_bytes = 2 * NC * kTile * sizeof(double);
     int stages = 2;
     if (2 * stage_bytes + static_bytes > (size_t)max_optin) stages = 1;
@@ -540,8 +574,7 @@ cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s
     if (grid > num_tiles) grid = num_tiles;
     if (grid < 1) grid = 1;
     const int vec16 = (a.N % (16 / (long long)sizeof(T))) == 0;
-    kern<<<dim3((unsigned)grid), dim3(32, NC), dyn, s>>>(a, cfg.stencil, cfg.classic ? 1 : 0, num_tiles, stages,
-                                                         vec16);
+    kern<<<dim3((unsigned)grid), dim3(32, NC), dyn, s>>>(a, cfg.classic ? 1 : 0, num_tiles, stages, vec16);
     return cudaGetLastError();
 }
 

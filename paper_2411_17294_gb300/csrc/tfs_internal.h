@@ -41,6 +41,7 @@ struct FwdArgs {
     const T* sig_nm1;      // [nc][N]
     T* sig_np1;            // [nc][N]
     T* sig_copy;           // optional second destination of sigma^{n+1}
+    T* trans;              // [nc][N] transport term A: written by the pre-pass, read by the step
     const T* modes_n;      // [m][nc][N]
     T* modes_nm1;          // [m][nc][N]  read as level n-1, overwritten with level n+1
     unsigned* flags;       // latched device status

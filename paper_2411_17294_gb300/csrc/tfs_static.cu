@@ -4,7 +4,8 @@
 // not allowed (inside a host framework that owns all device memory, a real-time
 // loop that must not allocate, a plug-in without access to an allocator).  For
 // them this entry point keeps the whole step state -- the stress ring, the
-// initial-stress copy, the status word and both mode levels -- in one
+// initial-stress copy, the transport term, the status word and both mode
+// levels -- in one
 // file-scope device array of fixed size, kStaticBytes, instead of a
 // caller-bound workspace.  The caller passes only inputs and the output.
 //
@@ -113,7 +114,7 @@ extern "C" int tfs_run_static(const tfs_grid* grid, double alpha, double Wi, dou
     const size_t es = precision == TFS_FP64 ? 8 : 4;
     const size_t field = (size_t)nc * (size_t)N * es;
     const size_t modes = (size_t)m * field;
-    const size_t need = kAlignS + 4 * up256(field) + 2 * up256(modes);
+    const size_t need = kAlignS + 5 * up256(field) + 2 * up256(modes);
     if (need > kStaticBytes) return TFS_ERR_TOOBIG;
 
     // ---- SOE constants (FP64, as tfs_set_soe)
@@ -152,6 +153,8 @@ extern "C" int tfs_run_static(const tfs_grid* grid, double alpha, double Wi, dou
         sig[i] = p;
         p += up256(field);
     }
+    char* trans = p;
+    p += up256(field);
     char* md[2];
     for (int i = 0; i < 2; ++i) {
         md[i] = p;
@@ -186,6 +189,7 @@ extern "C" int tfs_run_static(const tfs_grid* grid, double alpha, double Wi, dou
             a.sig_nm1 = (const double*)sig[prev];
             a.sig_np1 = (double*)sig[nxt];
             a.sig_copy = nullptr;
+            a.trans = (double*)trans;
             a.modes_n = (const double*)md[cur_mode];
             a.modes_nm1 = (double*)md[1 - cur_mode];
             a.flags = flags;
@@ -202,6 +206,7 @@ extern "C" int tfs_run_static(const tfs_grid* grid, double alpha, double Wi, dou
             a.sig_nm1 = (const float*)sig[prev];
             a.sig_np1 = (float*)sig[nxt];
             a.sig_copy = nullptr;
+            a.trans = (float*)trans;
             a.modes_n = (const float*)md[cur_mode];
             a.modes_nm1 = (float*)md[1 - cur_mode];
             a.flags = flags;

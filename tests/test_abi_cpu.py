@@ -104,7 +104,7 @@ def test_calls_out_of_order_and_workspace(lib):
     N, nc, m = 256, 3, 4
     field = nc * N * 8
     up = lambda b: (b + 255) // 256 * 256
-    assert need == 256 + 4 * up(field) + 2 * up(m * field)
+    assert need == 256 + 5 * up(field) + 2 * up(m * field)
     assert lib.tfs_bind_workspace(h, ctypes.c_void_p(256 * 1000), need - 1) == tfs.TFS_ERR_NOWORKSPACE
     assert lib.tfs_bind_workspace(h, ctypes.c_void_p(256 * 1000 + 8), need) == tfs.TFS_ERR_ARG
     assert lib.tfs_bind_workspace(h, ctypes.c_void_p(256 * 1000), need) == tfs.TFS_OK
