@@ -20,8 +20,9 @@
 // in flight without holding registers, and the compute phase makes no global
 // loads.  Inside a tile, warp c handles stress component c (lane = point): it
 // forms Q_j = b1 x + b2 y from shared memory (stored back in place of the
-// older level), the history sum H (FP32 storage: compensated Dot2 with eta_j
-// split hi + lo) and its component of the right-hand side.  Warp 0 then solves
+// older level), the history sum H (FP32 storage: Kahan summation of terms
+// formed exactly by FMA, eta_j split hi + lo) and its component of the
+// right-hand side.  Warp 0 then solves
 // the 32 point systems with lane = point; all warps write the new mode level
 // from the Q_j kept in shared memory.  Every mode value is read once and
 // written once.
@@ -111,6 +112,26 @@ template <typename T, int DIM>
 __device__ __forceinline__ void issue_tile(const FwdArgs<T>& A, const StageMap& S, T* buf, long long t0, int tid,
                                            int nthr, bool vec16) {
     const long long N = A.N;
+    if (vec16 && t0 + kTile <= N) {
+        // full tile, 16-byte chunks: thread tid always copies chunk k = tid % CPP of
+        // planes tid / CPP, + nthr / CPP, ...; the mode planes of each level are
+        // equally spaced (N apart), so their sources advance by a fixed stride
+        constexpr int EPC = 16 / sizeof(T);
+        constexpr int CPP = kTile / EPC;
+        const int k = tid % CPP;
+        const int step = nthr / CPP;            // planes per round (nthr is a multiple of CPP)
+        const int mnc = A.m * (DIM == 2 ? 3 : 6);
+        const long long off = t0 + (long long)k * EPC;
+        int plane = tid / CPP;
+        const long long stride = (long long)step * N;
+        const T* src = A.modes_n + (long long)plane * N + off;
+        for (; plane < mnc; plane += step, src += stride) cp_async16(buf + plane * kTile + k * EPC, src, 16);
+        src = A.modes_nm1 + (long long)(plane - mnc) * N + off;
+        for (; plane < 2 * mnc; plane += step, src += stride) cp_async16(buf + plane * kTile + k * EPC, src, 16);
+        for (; plane < S.planes; plane += step)
+            cp_async16(buf + plane * kTile + k * EPC, plane_src<T, DIM>(A, S, plane) + off, 16);
+        return;
+    }
     if (vec16) {
         constexpr int EPC = 16 / sizeof(T);    // elements per chunk
         constexpr int CPP = kTile / EPC;       // chunks per plane segment
@@ -303,23 +324,24 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(256) transport_kernel(const FwdArgs<T> A, const int stencil) {
     constexpr int NC = Packed<DIM>::NC;
     const long long N = A.N;
+    const float ccoef = (float)A.courant_coef, climit = (float)A.courant_limit;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
         const unsigned pu = (unsigned)p;
         const unsigned px = pu % (unsigned)A.n0;
         const unsigned r1 = pu / (unsigned)A.n0;
         const unsigned py = r1 % (unsigned)A.n1;
         const unsigned pz = r1 / (unsigned)A.n1;
-#pragma unroll
+#pragma unroll 1
         for (int c = 0; c < NC; ++c) {
             StencilLoads<T, DIM> SL;
             load_stencil<T, DIM>(A, c, stencil, px, py, pz, p, SL);
             A.trans[(long long)c * N + p] = finish_stencil<T, DIM>(A, stencil, SL);
         }
-        if (A.courant_coef > 0.0) {
-            double cr = 0.0;
+        if (ccoef > 0.0f) {
+            float cr = 0.0f;
 #pragma unroll
-            for (int ax = 0; ax < DIM; ++ax) cr += fabs((double)A.u[(long long)ax * N + p]) * A.inv_h[ax];
-            if (A.courant_coef * cr > A.courant_limit) atomicOr(A.flags, 4u);
+            for (int ax = 0; ax < DIM; ++ax) cr += fabsf((float)A.u[(long long)ax * N + p]) * (float)A.inv_h[ax];
+            if (ccoef * cr > climit) atomicOr(A.flags, 4u);
         }
     }
 }
@@ -356,20 +378,23 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
         const T* lv0 = buf + (c * kTile + lane);
         T* lv1 = buf + ((m * NC + c) * kTile + lane);
         if constexpr (F32 && COMP) {
-            float hs = 0.f, he = 0.f;
+            // Kahan summation of the terms eta_j Q_j: each term enters as
+            // fma(eta_hi, Q, fma(eta_lo, Q, -comp)) -- the product is exact inside
+            // the FMA, so the term is rounded once -- and the rounding error of
+            // every addition is carried in `comp` (adds that are never contracted)
+            float hs = 0.f, comp = 0.f;
 #pragma unroll 8
             for (int j = 0; j < m; ++j) {
                 const float x = lv0[j * NC * kTile];
                 const float y = lv1[j * NC * kTile];
                 const float qj = __fmaf_rn(0.5f, y, -2.0f * x);
                 lv1[j * NC * kTile] = qj;
-                const float pr = __fmul_rn(A.mc.eta_hi[j], qj);
-                const float pe = __fmaf_rn(A.mc.eta_hi[j], qj, -pr);
-                const f2 sm = two_sum_f2(hs, pr);
-                hs = sm.hi;
-                he = __fadd_rn(he, __fadd_rn(sm.lo, __fmaf_rn(A.mc.eta_lo[j], qj, pe)));
+                const float yv = __fmaf_rn(A.mc.eta_hi[j], qj, __fmaf_rn(A.mc.eta_lo[j], qj, -comp));
+                const float t = __fadd_rn(hs, yv);
+                comp = __fsub_rn(__fsub_rn(t, hs), yv);
+                hs = t;
             }
-            Hf = fast_two_sum(hs, he);
+            Hf = fast_two_sum(hs, -comp);
         } else if constexpr (F32) {
             float hs = 0.f;
 #pragma unroll 8
