@@ -346,103 +346,144 @@ __global__ void __launch_bounds__(256) transport_kernel(const FwdArgs<T> A, cons
     }
 }
 
+// Warps per block of the step kernel: each warp handles NC / kWarps stress
+// components of the tile's 32 points (3D: 2 components per warp, 2D: 1).
+template <int DIM>
+struct StepShape {
+    static constexpr int NC = Packed<DIM>::NC;
+    static constexpr int W = 3;
+    static constexpr int CPW = NC / W;
+};
+
 template <typename T, int DIM, bool TRANSPORT, bool COMP>
-__device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap& S, const T* __restrict__ buf_c,
-                                             T* buf, long long t0, int classic, void* sR_raw, float* sD) {
+__device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap& S, T* buf, long long t0,
+                                             int classic, void* sR_raw, float* sD) {
     constexpr int NC = Packed<DIM>::NC;
+    constexpr int W = StepShape<DIM>::W;
+    constexpr int CPW = StepShape<DIM>::CPW;
     constexpr bool F32 = sizeof(T) == 4;
     const int lane = threadIdx.x;
-    const int c = threadIdx.y;
+    const int w = threadIdx.y;
     const long long N = A.N;
     const long long p = t0 + lane;
     const bool active = p < N;
     const int m = A.m;
     const bool has_s0 = A.sigma0 != nullptr;
-    (void)buf_c;
 
-    // ---- (a4) history sum over the modes of component c (Q_j stored in place of level n-1)
-    double Hd = 0.0;
-    f2 Hf{0.0f, 0.0f};
-    const T s0c = has_s0 ? buf[(S.s0 + c) * kTile + lane] : (T)0;
+    // ---- (a4) history sums over the modes of this thread's components
+    //      (Q_j stored in place of level n-1)
+    double Hd[CPW];
+    f2 Hf[CPW];
+    T s0c[CPW];
+#pragma unroll
+    for (int cc = 0; cc < CPW; ++cc) {
+        const int c = w + cc * W;
+        Hd[cc] = 0.0;
+        Hf[cc] = f2{0.0f, 0.0f};
+        s0c[cc] = has_s0 ? buf[(S.s0 + c) * kTile + lane] : (T)0;
+    }
     if (classic) {
-        const T sn = buf[(S.sig + c) * kTile + lane];
-        const T sm = buf[(S.sig + NC + c) * kTile + lane];
-        if constexpr (F32) {
-            // b1 sigma^n + b2 sigma^{n-1} + b0 sigma0: exact products by powers of two, TwoProd for b0
-            const f2 h = two_sum_f2(-2.0f * (float)sn, 0.5f * (float)sm);
-            Hf = f2_add(h, two_prod(1.5f, (float)s0c));
-        } else {
-            Hd = kB1 * (double)sn + kB2 * (double)sm + kB0 * (double)s0c;
+#pragma unroll
+        for (int cc = 0; cc < CPW; ++cc) {
+            const int c = w + cc * W;
+            const T sn = buf[(S.sig + c) * kTile + lane];
+            const T sm = buf[(S.sig + NC + c) * kTile + lane];
+            if constexpr (F32) {
+                // b1 sigma^n + b2 sigma^{n-1} + b0 sigma0: exact products by powers of two, TwoProd for b0
+                const f2 h = two_sum_f2(-2.0f * (float)sn, 0.5f * (float)sm);
+                Hf[cc] = f2_add(h, two_prod(1.5f, (float)s0c[cc]));
+            } else {
+                Hd[cc] = kB1 * (double)sn + kB2 * (double)sm + kB0 * (double)s0c[cc];
+            }
         }
     } else {
-        const T* lv0 = buf + (c * kTile + lane);
-        T* lv1 = buf + ((m * NC + c) * kTile + lane);
+        const T* lv0 = buf + (w * kTile + lane);
+        T* lv1 = buf + ((m * NC + w) * kTile + lane);
         if constexpr (F32 && COMP) {
             // Kahan summation of the terms eta_j Q_j: each term enters as
             // fma(eta_hi, Q, fma(eta_lo, Q, -comp)) -- the product is exact inside
             // the FMA, so the term is rounded once -- and the rounding error of
             // every addition is carried in `comp` (adds that are never contracted)
-            float hs = 0.f, comp = 0.f;
-#pragma unroll 8
-            for (int j = 0; j < m; ++j) {
-                const float x = lv0[j * NC * kTile];
-                const float y = lv1[j * NC * kTile];
-                const float qj = __fmaf_rn(0.5f, y, -2.0f * x);
-                lv1[j * NC * kTile] = qj;
-                const float yv = __fmaf_rn(A.mc.eta_hi[j], qj, __fmaf_rn(A.mc.eta_lo[j], qj, -comp));
-                const float t = __fadd_rn(hs, yv);
-                comp = __fsub_rn(__fsub_rn(t, hs), yv);
-                hs = t;
-            }
-            Hf = fast_two_sum(hs, -comp);
-        } else if constexpr (F32) {
-            float hs = 0.f;
-#pragma unroll 8
-            for (int j = 0; j < m; ++j) {
-                const float x = lv0[j * NC * kTile];
-                const float y = lv1[j * NC * kTile];
-                const float qj = __fmaf_rn(0.5f, y, -2.0f * x);
-                lv1[j * NC * kTile] = qj;
-                hs = __fmaf_rn(A.mc.eta_hi[j], qj, hs);
-            }
-            Hf = f2_from(hs);
-        } else {
+            float hs[CPW], comp[CPW];
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc) hs[cc] = comp[cc] = 0.0f;
 #pragma unroll 4
             for (int j = 0; j < m; ++j) {
-                const double x = (double)lv0[j * NC * kTile];
-                const double y = (double)lv1[j * NC * kTile];
-                const double qj = kB1 * x + kB2 * y;
-                lv1[j * NC * kTile] = (T)qj;
-                Hd = fma(A.mc.eta[j], qj, Hd);
+                const float eh = A.mc.eta_hi[j], el = A.mc.eta_lo[j];
+#pragma unroll
+                for (int cc = 0; cc < CPW; ++cc) {
+                    const int o = (j * NC + cc * W) * kTile;
+                    const float x = lv0[o];
+                    const float y = lv1[o];
+                    const float qj = __fmaf_rn(0.5f, y, -2.0f * x);
+                    lv1[o] = qj;
+                    const float yv = __fmaf_rn(eh, qj, __fmaf_rn(el, qj, -comp[cc]));
+                    const float t = __fadd_rn(hs[cc], yv);
+                    comp[cc] = __fsub_rn(__fsub_rn(t, hs[cc]), yv);
+                    hs[cc] = t;
+                }
+            }
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc) Hf[cc] = fast_two_sum(hs[cc], -comp[cc]);
+        } else if constexpr (F32) {
+            float hs[CPW];
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc) hs[cc] = 0.0f;
+#pragma unroll 4
+            for (int j = 0; j < m; ++j) {
+#pragma unroll
+                for (int cc = 0; cc < CPW; ++cc) {
+                    const int o = (j * NC + cc * W) * kTile;
+                    const float qj = __fmaf_rn(0.5f, lv1[o], -2.0f * lv0[o]);
+                    lv1[o] = qj;
+                    hs[cc] = __fmaf_rn(A.mc.eta_hi[j], qj, hs[cc]);
+                }
+            }
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc) Hf[cc] = f2_from(hs[cc]);
+        } else {
+#pragma unroll 2
+            for (int j = 0; j < m; ++j) {
+#pragma unroll
+                for (int cc = 0; cc < CPW; ++cc) {
+                    const int o = (j * NC + cc * W) * kTile;
+                    const double qj = kB1 * (double)lv0[o] + kB2 * (double)lv1[o];
+                    lv1[o] = (T)qj;
+                    Hd[cc] = fma(A.mc.eta[j], qj, Hd[cc]);
+                }
             }
         }
     }
 
-    // ---- right-hand side component c
-    const int ci = Packed<DIM>::I(c), cj = Packed<DIM>::J(c);
-    const T kn_ij = buf[(S.kn + ci * DIM + cj) * kTile + lane];
-    const T km_ij = buf[(S.km + ci * DIM + cj) * kTile + lane];
-    const T kn_ji = buf[(S.kn + cj * DIM + ci) * kTile + lane];
-    const T km_ji = buf[(S.km + cj * DIM + ci) * kTile + lane];
-    if constexpr (F32) {
-        const f2 kab = two_sum_f2(2.0f * (float)kn_ij, -(float)km_ij);
-        const f2 kba = two_sum_f2(2.0f * (float)kn_ji, -(float)km_ji);
-        const f2 ks = f2_add(kab, kba);
-        const f2 eta{A.eta_f2.hi, A.eta_f2.lo}, src{A.src_f2.hi, A.src_f2.lo};
-        f2 R = f2_add(f2_mul_f(eta, (float)s0c), f2_neg(Hf));
-        R = f2_add(R, f2_mul(src, ks));
-        if constexpr (TRANSPORT) R = f2_add_f(R, -(float)buf[(S.tr + c) * kTile + lane]);
-        reinterpret_cast<f2*>(sR_raw)[c * kTile + lane] = R;
-    } else {
-        const double ks = (2.0 * (double)kn_ij - (double)km_ij) + (2.0 * (double)kn_ji - (double)km_ji);
-        double R = A.eta * (double)s0c - Hd + A.dt * A.G * A.g * ks;
-        if constexpr (TRANSPORT) R -= (double)buf[(S.tr + c) * kTile + lane];
-        reinterpret_cast<double*>(sR_raw)[c * kTile + lane] = R;
+    // ---- right-hand side components
+#pragma unroll
+    for (int cc = 0; cc < CPW; ++cc) {
+        const int c = w + cc * W;
+        const int ci = Packed<DIM>::I(c), cj = Packed<DIM>::J(c);
+        const T kn_ij = buf[(S.kn + ci * DIM + cj) * kTile + lane];
+        const T km_ij = buf[(S.km + ci * DIM + cj) * kTile + lane];
+        const T kn_ji = buf[(S.kn + cj * DIM + ci) * kTile + lane];
+        const T km_ji = buf[(S.km + cj * DIM + ci) * kTile + lane];
+        if constexpr (F32) {
+            const f2 kab = two_sum_f2(2.0f * (float)kn_ij, -(float)km_ij);
+            const f2 kba = two_sum_f2(2.0f * (float)kn_ji, -(float)km_ji);
+            const f2 ks = f2_add(kab, kba);
+            const f2 eta{A.eta_f2.hi, A.eta_f2.lo}, src{A.src_f2.hi, A.src_f2.lo};
+            f2 R = f2_add(f2_mul_f(eta, (float)s0c[cc]), f2_neg(Hf[cc]));
+            R = f2_add(R, f2_mul(src, ks));
+            if constexpr (TRANSPORT) R = f2_add_f(R, -(float)buf[(S.tr + c) * kTile + lane]);
+            reinterpret_cast<f2*>(sR_raw)[c * kTile + lane] = R;
+        } else {
+            const double ks = (2.0 * (double)kn_ij - (double)km_ij) + (2.0 * (double)kn_ji - (double)km_ji);
+            double R = A.eta * (double)s0c[cc] - Hd[cc] + A.dt * A.G * A.g * ks;
+            if constexpr (TRANSPORT) R -= (double)buf[(S.tr + c) * kTile + lane];
+            reinterpret_cast<double*>(sR_raw)[c * kTile + lane] = R;
+        }
     }
     __syncthreads();
 
     // ---- (a2) + (a5) point solve by warp 0
-    if (c == 0) {
+    if (w == 0) {
         T out[NC];
         unsigned fl = 0u;
         if constexpr (F32) {
@@ -501,25 +542,37 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
 
     // ---- (a6) push-forward of the modes over the oldest level
     if (!classic && active) {
-        const T* qv = buf + ((m * NC + c) * kTile + lane);
-        T* out = A.modes_nm1 + (long long)c * N + p;
+        const T* qv = buf + ((m * NC + w) * kTile + lane);
+        T* out = A.modes_nm1 + (long long)w * N + p;
         const long long stride = (long long)NC * N;
         if constexpr (F32) {
-            const float d = sD[c * kTile + lane];
-#pragma unroll 8
-            for (int j = 0; j < m; ++j)
-                __stcs(out + j * stride, __fmaf_rn(A.mc.rho[j], d, -A.mc.c[j] * qv[j * NC * kTile]));
-        } else {
-            const double d = reinterpret_cast<const double*>(sD)[c * kTile + lane];
+            float d[CPW];
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc) d[cc] = sD[(w + cc * W) * kTile + lane];
 #pragma unroll 4
+            for (int j = 0; j < m; ++j) {
+                const float rho = A.mc.rho[j], cj = A.mc.c[j];
+#pragma unroll
+                for (int cc = 0; cc < CPW; ++cc)
+                    __stcs(out + j * stride + (long long)cc * W * N,
+                           __fmaf_rn(rho, d[cc], -cj * qv[(j * NC + cc * W) * kTile]));
+            }
+        } else {
+            double d[CPW];
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc) d[cc] = reinterpret_cast<const double*>(sD)[(w + cc * W) * kTile + lane];
+#pragma unroll 2
             for (int j = 0; j < m; ++j)
-                __stcs(out + j * stride, (T)fma(A.mc.rho[j], d, -A.mc.c[j] * (double)qv[j * NC * kTile]));
+#pragma unroll
+                for (int cc = 0; cc < CPW; ++cc)
+                    __stcs(out + j * stride + (long long)cc * W * N,
+                           (T)fma(A.mc.rho[j], d[cc], -A.mc.c[j] * (double)qv[(j * NC + cc * W) * kTile]));
         }
     }
 }
 
 template <typename T, int DIM, bool TRANSPORT, bool COMP>
-__global__ void __launch_bounds__(32 * Packed<DIM>::NC, DIM == 3 ? 2 : 4)
+__global__ void __launch_bounds__(32 * StepShape<DIM>::W, 4)
 fwd_kernel(const FwdArgs<T> A, const int classic, const long long num_tiles, const int stages, const int vec16) {
     constexpr int NC = Packed<DIM>::NC;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -530,7 +583,7 @@ fwd_kernel(const FwdArgs<T> A, const int classic, const long long num_tiles, con
     T* buf0 = reinterpret_cast<T*>(smem);
     T* buf1 = buf0 + stage_elems;
     const int tid = threadIdx.y * 32 + threadIdx.x;
-    const int nthr = 32 * NC;
+    const int nthr = 32 * StepShape<DIM>::W;
     float* sD = reinterpret_cast<float*>(sD_store);
 
     if (stages == 2) {
@@ -545,7 +598,7 @@ fwd_kernel(const FwdArgs<T> A, const int classic, const long long num_tiles, con
             cp_async_commit();
             cp_async_wait<1>();
             __syncthreads();
-            compute_tile<T, DIM, TRANSPORT, COMP>(A, S, cur, cur, tile * kTile, classic, sR_store, sD);
+            compute_tile<T, DIM, TRANSPORT, COMP>(A, S, cur, tile * kTile, classic, sR_store, sD);
             __syncthreads();
         }
         cp_async_wait<0>();
@@ -555,7 +608,7 @@ fwd_kernel(const FwdArgs<T> A, const int classic, const long long num_tiles, con
             cp_async_commit();
             cp_async_wait<0>();
             __syncthreads();
-            compute_tile<T, DIM, TRANSPORT, COMP>(A, S, buf0, buf0, tile * kTile, classic, sR_store, sD);
+            compute_tile<T, DIM, TRANSPORT, COMP>(A, S, buf0, tile * kTile, classic, sR_store, sD);
             __syncthreads();
         }
     }
@@ -585,21 +638,34 @@ cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s
     const StageMap S = stage_map<DIM>(cfg.classic ? 0 : a.m, TRANSPORT, a.sigma0 != nullptr, cfg.classic);
     const size_t stage_bytes = (size_t)S.planes * kTile * sizeof(T);
     const size_t static_bytes = 2 * NC * kTile * sizeof(double);
-    int stages = 2;
-    if (2 * stage_bytes + static_bytes > (size_t)max_optin) stages = 1;
+    // one or two stages per block: more resident blocks (more tiles and point
+    // solves in flight per SM) win; on a tie the second stage adds prefetch
     if (stage_bytes + static_bytes > (size_t)max_optin) return cudaErrorInvalidConfiguration;
+    int best_stages = 1, per_sm = 0;
+    for (int st = 1; st <= 2; ++st) {
+        const size_t dyn_try = st * stage_bytes;
+        if (dyn_try + static_bytes > (size_t)max_optin) continue;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_try);
+        if (e != cudaSuccess) return e;
+        int blocks = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, 32 * StepShape<DIM>::W, dyn_try);
+        if (e != cudaSuccess) return e;
+        if (blocks >= per_sm) {
+            per_sm = blocks;
+            best_stages = st;
+        }
+    }
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int stages = best_stages;
     const size_t dyn = stages * stage_bytes;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * NC, dyn);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
     long long grid = (long long)per_sm * sms;
     if (grid > num_tiles) grid = num_tiles;
     if (grid < 1) grid = 1;
     const int vec16 = (a.N % (16 / (long long)sizeof(T))) == 0;
-    kern<<<dim3((unsigned)grid), dim3(32, NC), dyn, s>>>(a, cfg.classic ? 1 : 0, num_tiles, stages, vec16);
+    kern<<<dim3((unsigned)grid), dim3(32, StepShape<DIM>::W), dyn, s>>>(a, cfg.classic ? 1 : 0, num_tiles, stages,
+                                                                       vec16);
     return cudaGetLastError();
 }
 
