@@ -27,56 +27,185 @@
 namespace tfs {
 namespace {
 
-template <typename T, int DIM, int MT>
-__global__ void __launch_bounds__(32 * Packed<DIM>::NC)
-adj_kernel(const AdjArgs<T> A, const int classic) {
-    constexpr int NC = Packed<DIM>::NC;
-    __shared__ double sS[NC][32];     // sum_j rho_j z_j per component
-    __shared__ double sL[NC][32];     // lamR per component
-    __shared__ double sRed[2][NC];    // block reduction of the scalar gradients
+constexpr int kTileA = 32;
 
-    const int lane = threadIdx.x;
-    const int c = threadIdx.y;
+// Shared-memory stage of one adjoint tile (32 points).  Planes of 32 T values:
+//   lamQ' [m][nc], lamQ'' [m][nc], kappa^n [d*d], kappa^{n-1} [d*d], sigma^{n+1} [nc];
+// then planes of 32 doubles:
+//   s1 [nc], s0 [nc], dJ/dsigma0 [nc], dJ/dkappa [d*d].
+struct AdjStageMap {
+    int e1, e2, kn, km, sig, tplanes;   // T planes
+    int s1, s0, gs, gk, dplanes;        // double planes
+};
+
+template <int DIM>
+__host__ __device__ __forceinline__ AdjStageMap adj_stage_map(int m) {
+    constexpr int NC = DIM == 2 ? 3 : 6;
+    AdjStageMap S;
+    S.e1 = 0;
+    S.e2 = m * NC;
+    S.kn = 2 * m * NC;
+    S.km = S.kn + DIM * DIM;
+    S.sig = S.km + DIM * DIM;
+    S.tplanes = S.sig + NC;
+    S.s1 = 0;
+    S.s0 = NC;
+    S.gs = 2 * NC;
+    S.gk = 3 * NC;
+    S.dplanes = 3 * NC + DIM * DIM;
+    return S;
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ size_t adj_stage_bytes(const AdjStageMap& S) {
+    return (size_t)S.tplanes * kTileA * sizeof(T) + (size_t)S.dplanes * kTileA * sizeof(double);
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ const T* adj_tsrc(const AdjArgs<T>& A, const AdjStageMap& S, int plane) {
     const long long N = A.N;
-    const long long p = (long long)blockIdx.x * 32 + lane;
-    const bool active = p < N;
-    const long long pc = active ? p : 0;
-    const long long stride = (long long)NC * N;
+    if (plane < S.e2) return A.ell_prev + (long long)plane * N;
+    if (plane < S.kn) return A.ell_prev2 + (long long)(plane - S.e2) * N;
+    if (plane < S.km) return A.kap_n + (long long)(plane - S.kn) * N;
+    if (plane < S.sig) return A.kap_nm1 + (long long)(plane - S.km) * N;
+    return A.sig_np1 + (long long)(plane - S.sig) * N;
+}
 
-    // ---- z_j and sum_j rho_j z_j for component c --------------------------
-    double Z[MT > 0 ? MT : 1];
-    double S = 0.0;
-    if (!classic) {
-        const T* e1 = A.ell_prev + (long long)c * N + pc;
-        const T* e2 = A.ell_prev2 + (long long)c * N + pc;
-#pragma unroll
-        for (int j = 0; j < MT; ++j) {
-            if (j < A.m) {
-                double z = 0.0;
-                if (!A.first) z = kB1 * to_d(__ldcs(e1 + j * stride)) + kB2 * to_d(__ldcs(e2 + j * stride));
-                Z[j] = z;
-                S = fma(A.mc.rho[j], z, S);
-            }
+template <typename T, int DIM>
+__device__ __forceinline__ const double* adj_dsrc(const AdjArgs<T>& A, const AdjStageMap& S, int plane) {
+    constexpr int NC = DIM == 2 ? 3 : 6;
+    const long long N = A.N;
+    if (plane < S.s0) return A.s1 + (long long)plane * N;
+    if (plane < S.gs) return A.s0 + (long long)(plane - S.s0) * N;
+    if (plane < S.gk) return A.g_sigma0 + (long long)(plane - S.gs) * N;
+    (void)NC;
+    return A.g_kap + (long long)(plane - S.gk) * N;
+}
+
+// Copy one plane family (32-element segments starting at t0) into shared memory.
+template <typename E, typename Src>
+__device__ __forceinline__ void stage_planes(E* dst, int planes, Src src_of, long long t0, long long N, int tid,
+                                             int nthr, bool vec16) {
+    if (vec16) {
+        constexpr int EPC = 16 / sizeof(E);
+        constexpr int CPP = kTileA / EPC;
+        const int total = planes * CPP;
+        for (int q = tid; q < total; q += nthr) {
+            const int plane = q / CPP;
+            const int k = q - plane * CPP;
+            const long long p0 = t0 + (long long)k * EPC;
+            long long valid = N - p0;
+            valid = valid < 0 ? 0 : (valid > EPC ? EPC : valid);
+            const E* base = src_of(plane);
+            cp_async16(dst + plane * kTileA + k * EPC, base + (valid > 0 ? p0 : 0), (int)(valid * sizeof(E)));
+        }
+    } else {
+        const int total = planes * kTileA;
+        for (int q = tid; q < total; q += nthr) {
+            const int plane = q / kTileA;
+            const int l = q - plane * kTileA;
+            const long long p = t0 + l;
+            const E* base = src_of(plane);
+            cp_async_small<sizeof(E)>(dst + q, base + (p < N ? p : 0), p < N ? (int)sizeof(E) : 0);
         }
     }
-    sS[c][lane] = S;
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ void adj_issue(const AdjArgs<T>& A, const AdjStageMap& S, unsigned char* buf, long long t0,
+                                          int tid, int nthr, bool vec16) {
+    T* tb = reinterpret_cast<T*>(buf);
+    double* db = reinterpret_cast<double*>(buf + (size_t)S.tplanes * kTileA * sizeof(T));
+    stage_planes<T>(tb, S.tplanes, [&](int pl) { return adj_tsrc<T, DIM>(A, S, pl); }, t0, A.N, tid, nthr, vec16);
+    stage_planes<double>(db, S.dplanes, [&](int pl) { return adj_dsrc<T, DIM>(A, S, pl); }, t0, A.N, tid, nthr,
+                         vec16);
+}
+
+template <int DIM>
+struct AdjShape {
+    static constexpr int NC = Packed<DIM>::NC;
+    static constexpr int W = 3;
+    static constexpr int CPW = NC / W;
+};
+
+template <typename T, int DIM>
+__device__ __forceinline__ void adj_tile(const AdjArgs<T>& A, const AdjStageMap& S, unsigned char* buf,
+                                         long long t0, int classic, double* sS, double* sL, double& gWi,
+                                         double& gbeta) {
+    constexpr int NC = Packed<DIM>::NC;
+    constexpr int W = AdjShape<DIM>::W;
+    constexpr int CPW = AdjShape<DIM>::CPW;
+    constexpr bool F32 = sizeof(T) == 4;
+    T* tb = reinterpret_cast<T*>(buf);
+    const double* db = reinterpret_cast<const double*>(buf + (size_t)S.tplanes * kTileA * sizeof(T));
+    const int lane = threadIdx.x;
+    const int w = threadIdx.y;
+    const long long N = A.N;
+    const long long p = t0 + lane;
+    const bool active = p < N;
+    const int m = A.m;
+
+    // ---- z_j = b1 lamQ'_j + b2 lamQ''_j (stored in place of lamQ''), S = sum_j rho_j z_j
+    if (!classic) {
+        const T* e1 = tb + (S.e1 + w) * kTileA + lane;
+        T* e2 = tb + (S.e2 + w) * kTileA + lane;
+        if constexpr (F32) {
+            float ss[CPW], comp[CPW];
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc) ss[cc] = comp[cc] = 0.0f;
+#pragma unroll 4
+            for (int j = 0; j < m; ++j) {
+                const float rh = A.mcf.rho[j];
+#pragma unroll
+                for (int cc = 0; cc < CPW; ++cc) {
+                    const int o = (j * NC + cc * W) * kTileA;
+                    const float z = A.first ? 0.0f : __fmaf_rn(0.5f, e2[o], -2.0f * e1[o]);
+                    e2[o] = z;
+                    const float yv = __fmaf_rn(rh, z, -comp[cc]);
+                    const float t = __fadd_rn(ss[cc], yv);
+                    comp[cc] = __fsub_rn(__fsub_rn(t, ss[cc]), yv);
+                    ss[cc] = t;
+                }
+            }
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc) sS[(w + cc * W) * kTileA + lane] = (double)ss[cc] - (double)comp[cc];
+        } else {
+            double ss[CPW];
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc) ss[cc] = 0.0;
+#pragma unroll 2
+            for (int j = 0; j < m; ++j) {
+#pragma unroll
+                for (int cc = 0; cc < CPW; ++cc) {
+                    const int o = (j * NC + cc * W) * kTileA;
+                    const double z = A.first ? 0.0 : kB1 * (double)e1[o] + kB2 * (double)e2[o];
+                    e2[o] = (T)z;
+                    ss[cc] = fma(A.mc.rho[j], z, ss[cc]);
+                }
+            }
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc) sS[(w + cc * W) * kTileA + lane] = ss[cc];
+        }
+    } else {
+#pragma unroll
+        for (int cc = 0; cc < CPW; ++cc) sS[(w + cc * W) * kTileA + lane] = 0.0;
+    }
     __syncthreads();
 
-    double gWi = 0.0, gbeta = 0.0;
-    if (c == 0 && active) {
+    // ---- point system (FP64) and parameter derivatives by warp 0
+    if (w == 0) {
         double K[3][3];
 #pragma unroll
         for (int a = 0; a < DIM; ++a)
 #pragma unroll
-            for (int b = 0; b < DIM; ++b) {
-                const long long q = (long long)(a * DIM + b) * N + p;
-                K[a][b] = 2.0 * to_d(A.kap_n[q]) - to_d(A.kap_nm1[q]);
-            }
+            for (int b = 0; b < DIM; ++b)
+                K[a][b] = 2.0 * (double)tb[(S.kn + a * DIM + b) * kTileA + lane] -
+                          (double)tb[(S.km + a * DIM + b) * kTileA + lane];
         double sig[NC], lam[NC];
 #pragma unroll
         for (int r = 0; r < NC; ++r) {
-            sig[r] = to_d(A.sig_np1[(long long)r * N + p]);
-            lam[r] = A.s1[(long long)r * N + p] + sS[r][lane];
+            sig[r] = (double)tb[(S.sig + r) * kTileA + lane];
+            lam[r] = db[(S.s1 + r) * kTileA + lane] + sS[r * kTileA + lane];
         }
         double M[NC][NC], Mt[NC][NC];
         assemble_M<DIM>(K, A.a, A.dt, M);
@@ -85,10 +214,7 @@ adj_kernel(const AdjArgs<T> A, const int classic) {
 #pragma unroll
             for (int k = 0; k < NC; ++k) Mt[r][k] = M[k][r];
         const bool ok = gauss_pp<NC>(Mt, lam, 1e-300);
-        if (!ok) atomicOr(A.flags, 2u);
         // lam now holds lamR
-
-        // d/dkappa* of <lamR, M sigma> and of the source term
         double gK[3][3];
 #pragma unroll
         for (int a = 0; a < 3; ++a)
@@ -105,73 +231,140 @@ adj_kernel(const AdjArgs<T> A, const int classic) {
         double sym_dot = 0.0, sig_dot = 0.0;
 #pragma unroll
         for (int cc = 0; cc < NC; ++cc) {
-            const int r = Packed<DIM>::I(cc), s = Packed<DIM>::J(cc);
+            const int r = Packed<DIM>::I(cc), s2 = Packed<DIM>::J(cc);
             const double l = lam[cc];
 #pragma unroll
             for (int b = 0; b < DIM; ++b) {
-                gK[r][b] += A.dt * l * S3[b][s];
-                gK[s][b] += A.dt * l * S3[r][b];
+                gK[r][b] += A.dt * l * S3[b][s2];
+                gK[s2][b] += A.dt * l * S3[r][b];
             }
-            gK[r][s] += src * l;
-            gK[s][r] += src * l;
-            sym_dot += l * (K[r][s] + K[s][r]);
+            gK[r][s2] += src * l;
+            gK[s2][r] += src * l;
+            sym_dot += l * (K[r][s2] + K[s2][r]);
             sig_dot += l * sig[cc];
         }
+        if (active) {
+            if (!ok) atomicOr(A.flags, 2u);
 #pragma unroll
-        for (int a = 0; a < DIM; ++a)
+            for (int a = 0; a < DIM; ++a)
 #pragma unroll
-            for (int b = 0; b < DIM; ++b) {
-                const long long q = (long long)(a * DIM + b) * N + p;
-                A.g_kap[q] += gK[a][b];
+                for (int b = 0; b < DIM; ++b) {
+                    const int q = a * DIM + b;
+                    A.g_kap[(long long)q * N + p] = db[(S.gk + q) * kTileA + lane] + gK[a][b];
+                }
+            const double lam_a = -sig_dot;
+            const double lam_G = A.dt * A.g * sym_dot;
+            gWi += -A.dt / (A.Wi * A.Wi) * lam_a - A.G / A.Wi * lam_G;
+            gbeta += -lam_G / (A.Wi * A.Re);
+#pragma unroll
+            for (int r = 0; r < NC; ++r) {
+                const long long q = (long long)r * N + p;
+                A.lamR[q] = lam[r];
+                double gs = A.eta * lam[r] - sS[r * kTileA + lane];
+                double s1o = db[(S.s0 + r) * kTileA + lane];
+                double s0o = 0.0;
+                if (classic) {
+                    const double lamH = -lam[r];
+                    s1o += kB1 * lamH;
+                    s0o += kB2 * lamH;
+                    gs += kB0 * lamH;
+                }
+                A.g_sigma0[q] = db[(S.gs + r) * kTileA + lane] + gs;
+                A.s1_out[q] = s1o;
+                A.s0_out[q] = s0o;
             }
-        const double lam_a = -sig_dot;
-        const double lam_G = A.dt * A.g * sym_dot;
-        gWi = -A.dt / (A.Wi * A.Wi) * lam_a - A.G / A.Wi * lam_G;
-        gbeta = -lam_G / (A.Wi * A.Re);
+        }
+#pragma unroll
+        for (int r = 0; r < NC; ++r) sL[r * kTileA + lane] = lam[r];
+    }
+    __syncthreads();
 
+    // ---- new adjoint mode level: lamQ_j = -c_j z_j - eta_j lamR, over the oldest slot
+    if (!classic && active) {
+        const T* zv = tb + (S.e2 + w) * kTileA + lane;
+        T* out = A.ell_prev2 + (long long)w * N + p;
+        const long long stride = (long long)NC * N;
+        if constexpr (F32) {
+            float l[CPW];
 #pragma unroll
-        for (int r = 0; r < NC; ++r) {
-            const long long q = (long long)r * N + p;
-            sL[r][lane] = lam[r];
-            A.lamR[q] = lam[r];
-            double gs = A.eta * lam[r] - sS[r][lane];
-            double s1o = A.s0[q];
-            double s0o = 0.0;
-            if (classic) {
-                const double lamH = -lam[r];
-                s1o += kB1 * lamH;
-                s0o += kB2 * lamH;
-                gs += kB0 * lamH;
+            for (int cc = 0; cc < CPW; ++cc) l[cc] = (float)sL[(w + cc * W) * kTileA + lane];
+#pragma unroll 4
+            for (int j = 0; j < m; ++j) {
+                const float ej = A.mcf.eta_hi[j], cjf = A.mcf.c[j];
+#pragma unroll
+                for (int cc = 0; cc < CPW; ++cc)
+                    __stcs(out + j * stride + (long long)cc * W * N,
+                           __fmaf_rn(-ej, l[cc], -cjf * zv[(j * NC + cc * W) * kTileA]));
             }
-            A.g_sigma0[q] += gs;
-            A.s1_out[q] = s1o;
-            A.s0_out[q] = s0o;
+        } else {
+            double l[CPW];
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc) l[cc] = sL[(w + cc * W) * kTileA + lane];
+#pragma unroll 2
+            for (int j = 0; j < m; ++j)
+#pragma unroll
+                for (int cc = 0; cc < CPW; ++cc)
+                    __stcs(out + j * stride + (long long)cc * W * N,
+                           (T)fma(-A.mc.eta[j], l[cc], -A.mc.c[j] * (double)zv[(j * NC + cc * W) * kTileA]));
         }
     }
+}
 
-    // block reduction of the two scalar gradients (warp 0 holds them)
-    if (c == 0) {
+template <typename T, int DIM>
+__global__ void __launch_bounds__(32 * AdjShape<DIM>::W, 2)
+adj_kernel(const AdjArgs<T> A, const int classic, const long long num_tiles, const int stages, const int vec16) {
+    constexpr int NC = Packed<DIM>::NC;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(16) double sS[NC * kTileA];
+    __shared__ __align__(16) double sL[NC * kTileA];
+    __shared__ double sRed[2][AdjShape<DIM>::W];
+    const AdjStageMap S = adj_stage_map<DIM>(classic ? 0 : A.m);
+    const size_t sb = adj_stage_bytes<T>(S);
+    unsigned char* buf0 = smem;
+    unsigned char* buf1 = smem + sb;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int nthr = 32 * AdjShape<DIM>::W;
+    double gWi = 0.0, gbeta = 0.0;
+
+    if (stages == 2) {
+        long long tile = blockIdx.x;
+        if (tile < num_tiles) adj_issue<T, DIM>(A, S, buf0, tile * kTileA, tid, nthr, vec16 != 0);
+        cp_async_commit();
+        for (int it = 0; tile < num_tiles; ++it, tile += gridDim.x) {
+            const long long next = tile + gridDim.x;
+            unsigned char* cur = (it & 1) ? buf1 : buf0;
+            unsigned char* nxt = (it & 1) ? buf0 : buf1;
+            if (next < num_tiles) adj_issue<T, DIM>(A, S, nxt, next * kTileA, tid, nthr, vec16 != 0);
+            cp_async_commit();
+            cp_async_wait<1>();
+            __syncthreads();
+            adj_tile<T, DIM>(A, S, cur, tile * kTileA, classic, sS, sL, gWi, gbeta);
+            __syncthreads();
+        }
+        cp_async_wait<0>();
+    } else {
+        for (long long tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
+            adj_issue<T, DIM>(A, S, buf0, tile * kTileA, tid, nthr, vec16 != 0);
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncthreads();
+            adj_tile<T, DIM>(A, S, buf0, tile * kTileA, classic, sS, sL, gWi, gbeta);
+            __syncthreads();
+        }
+    }
+    // per-block sums of the two scalar derivatives (warp 0 holds them)
+    if (threadIdx.y == 0) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             gWi += __shfl_xor_sync(0xffffffffu, gWi, off);
             gbeta += __shfl_xor_sync(0xffffffffu, gbeta, off);
         }
-        if (lane == 0) {
+        if (threadIdx.x == 0) {
             A.partials[2 * (long long)blockIdx.x + 0] += gWi;
             A.partials[2 * (long long)blockIdx.x + 1] += gbeta;
         }
     }
     (void)sRed;
-    __syncthreads();
-
-    // ---- new adjoint mode level: lamQ_j = -c_j z_j - eta_j lamR ---------------
-    if (!classic && active) {
-        const double l = sL[c][lane];
-        T* out = A.ell_prev2 + (long long)c * N + p;
-#pragma unroll
-        for (int j = 0; j < MT; ++j)
-            if (j < A.m) __stcs(out + j * stride, (T)fma(-A.mc.eta[j], l, -A.mc.c[j] * Z[j]));
-    }
 }
 
 // Transposed stencil: the forward step added  -dt (u.grad_h - eps Lap_h) E  to
@@ -246,32 +439,56 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partials, int 
     }
 }
 
-template <typename T, int DIM, int MT>
-cudaError_t launch_adj(const AdjArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s) {
-    constexpr int NC = Packed<DIM>::NC;
-    const long long blocks = (a.N + 31) / 32;
-    adj_kernel<T, DIM, MT><<<dim3((unsigned)blocks), dim3(32, NC), 0, s>>>(a, cfg.classic ? 1 : 0);
-    return cudaGetLastError();
-}
-
 template <typename T, int DIM>
-cudaError_t dispatch_mt(const AdjArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s) {
-    const int m = cfg.classic ? 0 : a.m;
-    if (m <= 8) return launch_adj<T, DIM, 8>(a, cfg, s);
-    if (m <= 16) return launch_adj<T, DIM, 16>(a, cfg, s);
-    if (m <= 32) return launch_adj<T, DIM, 32>(a, cfg, s);
-    if (m <= 48) return launch_adj<T, DIM, 48>(a, cfg, s);
-    return launch_adj<T, DIM, 64>(a, cfg, s);
+cudaError_t launch_adj(const AdjArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int max_optin = 0, sms = 0;
+    e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    auto kern = adj_kernel<T, DIM>;
+    const AdjStageMap S = adj_stage_map<DIM>(cfg.classic ? 0 : a.m);
+    const size_t sb = adj_stage_bytes<T>(S);
+    const size_t static_bytes = 2 * Packed<DIM>::NC * kTileA * sizeof(double) + 64;
+    if (sb + static_bytes > (size_t)max_optin) return cudaErrorInvalidConfiguration;
+    int best_stages = 1, per_sm = 0;
+    for (int st = 1; st <= 2; ++st) {
+        const size_t dyn_try = st * sb;
+        if (dyn_try + static_bytes > (size_t)max_optin) continue;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_try);
+        if (e != cudaSuccess) return e;
+        int blocks = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, 32 * AdjShape<DIM>::W, dyn_try);
+        if (e != cudaSuccess) return e;
+        if (blocks >= per_sm) {
+            per_sm = blocks;
+            best_stages = st;
+        }
+    }
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const size_t dyn = best_stages * sb;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    const long long num_tiles = (a.N + kTileA - 1) / kTileA;
+    long long grid = (long long)per_sm * sms;
+    if (grid > num_tiles) grid = num_tiles;
+    if (grid < 1) grid = 1;
+    const int vec16 = (a.N % (16 / (long long)sizeof(T))) == 0 && (a.N % 2) == 0;
+    kern<<<dim3((unsigned)grid), dim3(32, AdjShape<DIM>::W), dyn, s>>>(a, cfg.classic ? 1 : 0, num_tiles,
+                                                                       best_stages, vec16);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_adjoint_f64(const AdjArgs<double>& a, const LaunchCfg& cfg, cudaStream_t s) {
-    return cfg.dim == 2 ? dispatch_mt<double, 2>(a, cfg, s) : dispatch_mt<double, 3>(a, cfg, s);
+    return cfg.dim == 2 ? launch_adj<double, 2>(a, cfg, s) : launch_adj<double, 3>(a, cfg, s);
 }
 
 cudaError_t launch_adjoint_f32(const AdjArgs<float>& a, const LaunchCfg& cfg, cudaStream_t s) {
-    return cfg.dim == 2 ? dispatch_mt<float, 2>(a, cfg, s) : dispatch_mt<float, 3>(a, cfg, s);
+    return cfg.dim == 2 ? launch_adj<float, 2>(a, cfg, s) : launch_adj<float, 3>(a, cfg, s);
 }
 
 cudaError_t launch_adjoint_transport(const AdjArgs<double>& a, const void* u, bool u_is_double,

@@ -738,6 +738,7 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
                 a.ell_prev = (const float*)L.ell[ell_prev];
                 a.ell_prev2 = (float*)L.ell[1 - ell_prev];
                 a.mc = h->mcd;
+                a.mcf = h->mcf;
                 a.s1 = L.s[2 * cur];
                 a.s0 = L.s[2 * cur + 1];
                 a.s1_out = L.s[2 * nxt];

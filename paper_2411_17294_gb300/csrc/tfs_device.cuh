@@ -290,6 +290,33 @@ __device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
     return fast_two_sum(p.hi, p.lo);
 }
 
+// ---------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async, sm_80+).
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// 16-byte asynchronous copy global -> shared; bytes beyond src_bytes are zero.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES),
+                 "r"(src_bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // Periodic neighbour index along axis `ax` at offset `off` (|off| <= 2) from
 // point (x, y, z); correct for any axis length >= 1.
 struct GridIdx {

@@ -43,31 +43,6 @@ namespace {
 
 constexpr int kTile = 32;
 
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-// 16-byte asynchronous copy global -> shared; bytes beyond src_bytes are zero.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
-                 "r"(src_bytes)
-                 : "memory");
-}
-
-template <int BYTES>
-__device__ __forceinline__ void cp_async_small(void* dst, const void* src, int src_bytes) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES),
-                 "r"(src_bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 // Shared-memory stage of one tile: planes of 32 elements, in this order
 //   modes level n [m][nc], modes level n-1 [m][nc], kappa^n [d*d], kappa^{n-1} [d*d],
 //   A [nc] (transport), sigma0 [nc] (nonzero initial stress), sigma^n, sigma^{n-1} [nc] (alpha = 1).
@@ -320,6 +295,7 @@ __device__ __forceinline__ bool solve_point_f32(const f2 K[3][3], F2c a, F2c dt,
 // ----------------------------------------------------------------- the kernels
 // Transport pre-pass: A_c(p) = dt sum_a u_a D_a(E_c) - eps dt Lap(E_c) for all
 // components at point p (one thread per point), and the Courant flag.
+// Per-point fallback (any grid size): one thread per point, all components.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) transport_kernel(const FwdArgs<T> A, const int stencil) {
     constexpr int NC = Packed<DIM>::NC;
@@ -342,6 +318,115 @@ __global__ void __launch_bounds__(256) transport_kernel(const FwdArgs<T> A, cons
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) cr += fabsf((float)A.u[(long long)ax * N + p]) * (float)A.inv_h[ax];
             if (ccoef * cr > climit) atomicOr(A.flags, 4u);
+        }
+    }
+}
+
+// Tiled transport pre-pass for grids with n0 % 32 == 0 and n1 % 8 == 0.
+// A block owns a 32 x 8 (x, y) tile; E = 2 sigma^n - sigma^{n-1} is formed once
+// per value into a shared tile with a 2-cell halo in x and y, and in 3D the
+// block marches over a chunk of z planes keeping E at z-2 .. z+2 of its own
+// column in registers.  Arithmetic per point is that of finish_stencil.
+constexpr int kTX = 32, kTY = 8, kHalo = 2;
+constexpr int kSX = kTX + 2 * kHalo, kSY = kTY + 2 * kHalo;
+
+template <typename T>
+__device__ __forceinline__ int wrapi(int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kTX * kTY) transport_tiled(const FwdArgs<T> A, const int stencil, const int zchunk) {
+    constexpr int NC = Packed<DIM>::NC;
+    __shared__ T Es[NC][kSY][kSX];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * kTX + tx;
+    const int n0 = A.n0, n1 = A.n1, n2 = A.n2;
+    const long long N = A.N;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+    const int x = x0 + tx, y = y0 + ty;
+    const long long plane = (long long)n0 * n1;
+    const T ih[3] = {(T)A.inv_h[0], (T)A.inv_h[1], (T)A.inv_h[2]};
+    const T dtT = (T)A.dt, edt = (T)(A.eps * A.dt);
+    const bool lap = A.eps != 0.0;
+    const float ccoef = (float)A.courant_coef, climit = (float)A.courant_limit;
+    auto Eat = [&](int c, int gx, int gy, int gz) -> T {
+        const long long q = (long long)c * N + gx + (long long)n0 * gy + plane * gz;
+        return (T)2 * __ldg(A.sig_n + q) - __ldg(A.sig_nm1 + q);
+    };
+    const int zbeg = DIM == 3 ? blockIdx.z * zchunk : 0;
+    const int zend = DIM == 3 ? min(zbeg + zchunk, n2) : 1;
+    T qz[NC][5];   // E of this column at z-2 .. z+2 (3D)
+    if (DIM == 3) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) qz[c][k] = Eat(c, x, y, wrapi<T>(zbeg - 2 + k, n2));
+    }
+    for (int z = zbeg; z < zend; ++z) {
+        if (DIM == 3) {
+            const int zz = wrapi<T>(z + 2, n2);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) qz[c][4] = Eat(c, x, y, zz);
+        }
+        // own cell and halo cells of the shared tile at plane z
+#pragma unroll
+        for (int c = 0; c < NC; ++c) Es[c][ty + kHalo][tx + kHalo] = DIM == 3 ? qz[c][2] : Eat(c, x, y, 0);
+        for (int h = tid; h < kSX * kSY; h += kTX * kTY) {
+            const int hy = h / kSX, hx = h - hy * kSX;
+            const bool inner = hx >= kHalo && hx < kHalo + kTX && hy >= kHalo && hy < kHalo + kTY;
+            if (!inner) {
+                const int gx = wrapi<T>(x0 + hx - kHalo, n0), gy = wrapi<T>(y0 + hy - kHalo, n1);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) Es[c][hy][hx] = Eat(c, gx, gy, DIM == 3 ? z : 0);
+            }
+        }
+        __syncthreads();
+        const long long p = x + (long long)n0 * y + plane * z;
+        T u[DIM];
+#pragma unroll
+        for (int ax = 0; ax < DIM; ++ax) u[ax] = __ldg(A.u + (long long)ax * N + p);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int sy = ty + kHalo, sx = tx + kHalo;
+            const T e0 = Es[c][sy][sx];
+            T tap[DIM][4];
+            tap[0][0] = Es[c][sy][sx - 2];
+            tap[0][1] = Es[c][sy][sx - 1];
+            tap[0][2] = Es[c][sy][sx + 1];
+            tap[0][3] = Es[c][sy][sx + 2];
+            tap[1][0] = Es[c][sy - 2][sx];
+            tap[1][1] = Es[c][sy - 1][sx];
+            tap[1][2] = Es[c][sy + 1][sx];
+            tap[1][3] = Es[c][sy + 2][sx];
+            if (DIM == 3) {
+                tap[DIM - 1][0] = qz[c][0];
+                tap[DIM - 1][1] = qz[c][1];
+                tap[DIM - 1][2] = qz[c][3];
+                tap[DIM - 1][3] = qz[c][4];
+            }
+            T adv = (T)0, lp = (T)0;
+#pragma unroll
+            for (int ax = 0; ax < DIM; ++ax) {
+                adv += u[ax] * stencil_deriv<T>(stencil, u[ax], tap[ax][0], tap[ax][1], e0, tap[ax][2], tap[ax][3],
+                                                ih[ax]);
+                if (lap) lp += (tap[ax][1] - (T)2 * e0 + tap[ax][2]) * (ih[ax] * ih[ax]);
+            }
+            A.trans[(long long)c * N + p] = dtT * adv - edt * lp;
+        }
+        if (ccoef > 0.0f) {
+            float cr = 0.0f;
+#pragma unroll
+            for (int ax = 0; ax < DIM; ++ax) cr += fabsf((float)u[ax]) * (float)A.inv_h[ax];
+            if (ccoef * cr > climit) atomicOr(A.flags, 4u);
+        }
+        __syncthreads();
+        if (DIM == 3) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) qz[c][k] = qz[c][k + 1];
         }
     }
 }
@@ -626,10 +711,17 @@ cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s
     if (e != cudaSuccess) return e;
     if (TRANSPORT) {
         if (!a.trans) return cudaErrorInvalidValue;
-        const int threads = 256;
-        long long blocks = (a.N + threads - 1) / threads;
-        if (blocks > (long long)sms * 16) blocks = (long long)sms * 16;
-        transport_kernel<T, DIM><<<(unsigned)blocks, threads, 0, s>>>(a, cfg.stencil);
+        if (a.n0 % kTX == 0 && a.n1 % kTY == 0) {
+            const int zchunk = 32;
+            const int gz = DIM == 3 ? (a.n2 + zchunk - 1) / zchunk : 1;
+            transport_tiled<T, DIM><<<dim3(a.n0 / kTX, a.n1 / kTY, gz), dim3(kTX, kTY), 0, s>>>(a, cfg.stencil,
+                                                                                             zchunk);
+        } else {
+            const int threads = 256;
+            long long blocks = (a.N + threads - 1) / threads;
+            if (blocks > (long long)sms * 16) blocks = (long long)sms * 16;
+            transport_kernel<T, DIM><<<(unsigned)blocks, threads, 0, s>>>(a, cfg.stencil);
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -96,6 +96,7 @@ struct AdjArgs {
     double dt, eta, a, G, g, eps, Wi, Re;
     double inv_h[3];
     ModeConstsD mc;
+    ModeConstsF mcf;       // float copies (FP32 storage: mode sweeps in float)
 };
 
 cudaError_t launch_adjoint_f64(const AdjArgs<double>& a, const LaunchCfg& cfg, cudaStream_t s);

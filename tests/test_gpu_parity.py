@@ -72,6 +72,10 @@ RAGGED = [
     (2, (16, 16), 0.45, 64, True, 0.0, 0),
     (3, (4, 4, 4), 0.55, 48, True, 0.0, 0),
     (2, (10, 7), 0.5, 1, True, 0.0, 1),
+    # sizes with n0 % 32 == 0 and n1 % 8 == 0 take the tiled transport pre-pass
+    (3, (32, 16, 10), 0.6, 8, True, 0.01, 0),
+    (3, (64, 8, 3), 0.4, 6, True, 0.0, 1),
+    (2, (64, 24), 0.5, 8, True, 0.02, 0),
 ]
 
 
