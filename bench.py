@@ -48,6 +48,47 @@ def algorithmic_bytes_per_point(dim: int, m: int, elem: int, sigma0_nonzero: boo
     return b
 
 
+def step_kernel_bytes_per_point(dim: int, m: int, elem: int, transport: bool) -> int:
+    """Algorithmic bytes of the step kernel alone: 3 words per (mode, component),
+    both velocity-gradient levels, the stress written, and either the transport
+    term (written by the pre-pass) or the two stress levels it reads."""
+    nc = 3 if dim == 2 else 6
+    b = 3 * m * nc * elem + 2 * dim * dim * elem + nc * elem
+    b += nc * elem if transport else 2 * nc * elem
+    return b
+
+
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fwd_kernel_3d256_fp32_traffic.md")
+STEP_KERNEL_SOURCES = [os.path.join(ROOT, "paper_2411_17294_gb300", "csrc", f)
+                       for f in ("tfs_forward.cu", "tfs_device.cuh", "tfs_internal.h")]
+
+
+def step_kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in STEP_KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def read_traffic():
+    """DRAM bytes per step-kernel launch from the committed ncu capture, or None
+    when the step kernel's sources changed since that capture."""
+    try:
+        fields = {}
+        with open(TRAFFIC_FILE) as f:
+            for ln in f:
+                if ":" in ln and ln.startswith("- "):
+                    k, v = ln[2:].split(":", 1)
+                    fields[k.strip()] = v.strip().strip("`")
+        if fields.get("source_sha256") != step_kernel_source_hash():
+            return None
+        return float(fields["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def read_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -269,7 +310,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     N = s.N
     elem = 8 if prec == tfs.TFS_FP64 else 4
-    bytes_pp = algorithmic_bytes_per_point(3, W["m"], elem)
+    bytes_pp = step_kernel_bytes_per_point(3, W["m"], elem, transport=True)
     bytes_launch = bytes_pp * N
 
     with torch.cuda.stream(stream):
@@ -288,17 +329,23 @@ def main():
     sampler = ClockSampler(gpu_uuid)
     sampler.start()
     time.sleep(0.3)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    kb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ka = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for e in kb + ka:
+        e.record(stream)                        # creates the event handles
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         ev[0].record(stream)
         for k in range(args.steps):
+            s.set_step_events(kb[k], ka[k])     # recorded on `stream` around the step kernel only
             s.step(kap_n, kap_nm1, u, stream=stream)
-            ev[k + 1].record(stream)
+        ev[1].record(stream)
     torch.cuda.synchronize()
+    s.set_step_events(None, None)
     clocks = sampler.stop()
-    launch_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
+    launch_ms = [kb[k].elapsed_time(ka[k]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[1])
     flags = s.status()
     t_max = total_ms
     if dist is not None:
@@ -310,6 +357,8 @@ def main():
     avg_launch_s = statistics.mean(launch_ms) * 1e-3
     achieved = bytes_launch / avg_launch_s / 1e9
     peak, peak_kind = read_peaks()
+    traffic = read_traffic() if prec == tfs.TFS_FP32 else None
+    launches_per_step = 2         # transport pre-pass + step kernel
 
     # ---- end to end through the C ABI with host buffers ----------------------
     e2e = None
@@ -373,11 +422,13 @@ def main():
                        "Wi": W["Wi"], "beta": W["beta"], "dt": W["dt"], "transport": True,
                        "precision": args.precision, "l2": "per-step working set ~41 GB >> 129 MB L2, no flush",
                        "points_per_gpu": N},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                         "algorithmic_bytes_per_point": bytes_pp, "algorithmic_bytes_per_launch": bytes_launch,
-                         "avg_launch_ms": avg_launch_s * 1e3},
-            "gpu_launches": args.steps,
+            "roofline": {"bound": "hbm", "kernel": "fwd_kernel<float,3> (step kernel)", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": peak_kind, "algorithmic_bytes_per_point": bytes_pp,
+                         "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": avg_launch_s * 1e3,
+                         "step_share": sum(launch_ms) / total_ms,
+                         "whole_step_gbs": algorithmic_bytes_per_point(3, W["m"], elem) * N / (ms_per_step * 1e-3) / 1e9},
+            "gpu_launches": launches_per_step * args.steps,
             "device_flags": flags,
             "clocks": clocks,
             "e2e": e2e,

@@ -150,6 +150,13 @@ int tfs_step(tfs_handle h, const void* grad_u_n, const void* grad_u_nm1, const v
 /* Copy the current stress sigma^n to out [nc][N] (device). */
 int tfs_get_stress(tfs_handle h, void* out, void* stream);
 
+/* Measurement hook (no counterpart in the paper): with two cudaEvent_t
+   (passed as void*, both or neither), every later tfs_step records ev_before
+   on its stream just before the step kernel and ev_after just after it (the
+   transport pre-pass runs before ev_before), so that the step kernel alone
+   can be timed.  NULL, NULL turns it off.  The events are not owned. */
+int tfs_set_step_events(tfs_handle h, void* ev_before, void* ev_after);
+
 /* Current step index n (number of completed steps since tfs_set_state). */
 long tfs_step_index(tfs_handle h);
 

@@ -11,7 +11,7 @@
 // therefore a two-level ring like the forward modes: read two levels, write
 // one.  The stress part per point:
 //     lam_sigma^{n+1} = s1 + sum_j rho_j z_j
-//     M(kappa*)^T lamR = lam_sigma^{n+1}          (FP64 point solve)
+//     M(kappa*)^T lamR = lam_sigma^{n+1}          (point solve: FP64, or FP32 in FP32 storage)
 //     dJ/dsigma0 += eta lamR - sum_j rho_j z_j
 //     dJ/dkappa* += dt <lamR, dM/dkappa sigma^{n+1}>-terms + dt G g d(kappa+kappa^T)^T lamR
 //     dJ/dWi     += -dt/Wi^2 (-<lamR, sigma^{n+1}>) - G/Wi (dt g <lamR, sym kappa*>)
@@ -20,6 +20,8 @@
 // sends -lamR back through the transposed stencil (second kernel).
 // The forward modes themselves are never needed: only sigma^{n+1} and kappa.
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "tfs_device.cuh"
 #include "tfs_internal.h"
@@ -192,51 +194,76 @@ __device__ __forceinline__ void adj_tile(const AdjArgs<T>& A, const AdjStageMap&
     }
     __syncthreads();
 
-    // ---- point system (FP64) and parameter derivatives by warp 0
+    // ---- point system and parameter derivatives by warp 0.  FP64 storage:
+    //      FP64 throughout.  FP32 storage: the per-point arithmetic in FP32 (FP32
+    //      LU of M^T with partial pivoting), accumulations into the FP64 fields.
     if (w == 0) {
-        double K[3][3];
+        using R = typename std::conditional<F32, float, double>::type;
+        R K[3][3];
 #pragma unroll
         for (int a = 0; a < DIM; ++a)
 #pragma unroll
             for (int b = 0; b < DIM; ++b)
-                K[a][b] = 2.0 * (double)tb[(S.kn + a * DIM + b) * kTileA + lane] -
-                          (double)tb[(S.km + a * DIM + b) * kTileA + lane];
-        double sig[NC], lam[NC];
+                K[a][b] = (R)2 * (R)tb[(S.kn + a * DIM + b) * kTileA + lane] - (R)tb[(S.km + a * DIM + b) * kTileA + lane];
+        R sig[NC], lam[NC];
 #pragma unroll
         for (int r = 0; r < NC; ++r) {
-            sig[r] = (double)tb[(S.sig + r) * kTileA + lane];
-            lam[r] = db[(S.s1 + r) * kTileA + lane] + sS[r * kTileA + lane];
+            sig[r] = (R)tb[(S.sig + r) * kTileA + lane];
+            lam[r] = (R)(db[(S.s1 + r) * kTileA + lane] + sS[r * kTileA + lane]);
         }
-        double M[NC][NC], Mt[NC][NC];
-        assemble_M<DIM>(K, A.a, A.dt, M);
+        bool ok;
+        if constexpr (F32) {
+            LU32<NC> F;
+            static_for<0, NC>([&](auto rr) {
+                constexpr int r = decltype(rr)::value;
+                static_for<0, NC>([&](auto kk) {
+                    constexpr int k = decltype(kk)::value;
+                    // transpose: entry (r, k) of M^T is entry (k, r) of M
+                    constexpr int ro = Packed<DIM>::I(k), so = Packed<DIM>::J(k);
+                    constexpr int i = Packed<DIM>::I(r), j = Packed<DIM>::J(r);
+                    float v = 0.0f;
+                    if (so == j) v += K[ro][i];
+                    if (i != j && so == i) v += K[ro][j];
+                    if (ro == i) v += K[so][j];
+                    if (i != j && ro == j) v += K[so][i];
+                    F.a[r][k] = (r == k) ? __fmaf_rn(-(float)A.dt, v, (float)A.a) : -(float)A.dt * v;
+                });
+            });
+            ok = lu32_factor<NC>(F, 1e-30f);
+            lu32_solve<NC>(F, lam);
+        } else {
+            double M[NC][NC], Mt[NC][NC];
+            assemble_M<DIM>(K, A.a, A.dt, M);
 #pragma unroll
-        for (int r = 0; r < NC; ++r)
+            for (int r = 0; r < NC; ++r)
 #pragma unroll
-            for (int k = 0; k < NC; ++k) Mt[r][k] = M[k][r];
-        const bool ok = gauss_pp<NC>(Mt, lam, 1e-300);
+                for (int k = 0; k < NC; ++k) Mt[r][k] = M[k][r];
+            ok = gauss_pp<NC>(Mt, lam, 1e-300);
+        }
         // lam now holds lamR
-        double gK[3][3];
+        R gK[3][3];
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int b = 0; b < 3; ++b) gK[a][b] = 0.0;
-        double S3[3][3];
+            for (int b = 0; b < 3; ++b) gK[a][b] = (R)0;
+        R S3[3][3];
 #pragma unroll
         for (int r = 0; r < NC; ++r) {
             const int i = Packed<DIM>::I(r), j = Packed<DIM>::J(r);
             S3[i][j] = sig[r];
             S3[j][i] = sig[r];
         }
-        const double src = A.dt * A.G * A.g;
-        double sym_dot = 0.0, sig_dot = 0.0;
+        const R dtR = (R)A.dt;
+        const R src = (R)(A.dt * A.G * A.g);
+        R sym_dot = (R)0, sig_dot = (R)0;
 #pragma unroll
         for (int cc = 0; cc < NC; ++cc) {
             const int r = Packed<DIM>::I(cc), s2 = Packed<DIM>::J(cc);
-            const double l = lam[cc];
+            const R l = lam[cc];
 #pragma unroll
             for (int b = 0; b < DIM; ++b) {
-                gK[r][b] += A.dt * l * S3[b][s2];
-                gK[s2][b] += A.dt * l * S3[r][b];
+                gK[r][b] += dtR * l * S3[b][s2];
+                gK[s2][b] += dtR * l * S3[r][b];
             }
             gK[r][s2] += src * l;
             gK[s2][r] += src * l;
@@ -250,24 +277,24 @@ __device__ __forceinline__ void adj_tile(const AdjArgs<T>& A, const AdjStageMap&
 #pragma unroll
                 for (int b = 0; b < DIM; ++b) {
                     const int q = a * DIM + b;
-                    A.g_kap[(long long)q * N + p] = db[(S.gk + q) * kTileA + lane] + gK[a][b];
+                    A.g_kap[(long long)q * N + p] = db[(S.gk + q) * kTileA + lane] + (double)gK[a][b];
                 }
-            const double lam_a = -sig_dot;
-            const double lam_G = A.dt * A.g * sym_dot;
+            const double lam_a = -(double)sig_dot;
+            const double lam_G = A.dt * A.g * (double)sym_dot;
             gWi += -A.dt / (A.Wi * A.Wi) * lam_a - A.G / A.Wi * lam_G;
             gbeta += -lam_G / (A.Wi * A.Re);
 #pragma unroll
             for (int r = 0; r < NC; ++r) {
                 const long long q = (long long)r * N + p;
-                A.lamR[q] = lam[r];
-                double gs = A.eta * lam[r] - sS[r * kTileA + lane];
+                const double lr = (double)lam[r];
+                A.lamR[q] = lr;
+                double gs = A.eta * lr - sS[r * kTileA + lane];
                 double s1o = db[(S.s0 + r) * kTileA + lane];
                 double s0o = 0.0;
                 if (classic) {
-                    const double lamH = -lam[r];
-                    s1o += kB1 * lamH;
-                    s0o += kB2 * lamH;
-                    gs += kB0 * lamH;
+                    s1o += kB1 * -lr;
+                    s0o += kB2 * -lr;
+                    gs += kB0 * -lr;
                 }
                 A.g_sigma0[q] = db[(S.gs + r) * kTileA + lane] + gs;
                 A.s1_out[q] = s1o;
@@ -275,7 +302,7 @@ __device__ __forceinline__ void adj_tile(const AdjArgs<T>& A, const AdjStageMap&
             }
         }
 #pragma unroll
-        for (int r = 0; r < NC; ++r) sL[r * kTileA + lane] = lam[r];
+        for (int r = 0; r < NC; ++r) sL[r * kTileA + lane] = (double)lam[r];
     }
     __syncthreads();
 

@@ -59,6 +59,8 @@ struct tfs_ctx {
     bool state_set = false;
     long long step = 0;
     cudaStream_t last_stream = nullptr;
+    // optional events recorded around the step kernel of every tfs_step
+    cudaEvent_t ev_before = nullptr, ev_after = nullptr;
     // cached stability bounds of the explicit transport (invalidated by SOE and stencil changes)
     bool lim_valid = false;
     double lam_star = 0.0;   // advection: largest stable dt |u| / h (1D)
@@ -284,6 +286,8 @@ LaunchCfg make_cfg(const tfs_ctx* h) {
     cfg.transport = h->transport != 0;
     cfg.classic = h->classic();
     cfg.compensated = h->precision == TFS_FP32;
+    cfg.ev_before = h->ev_before;
+    cfg.ev_after = h->ev_after;
     return cfg;
 }
 
@@ -452,6 +456,14 @@ int tfs_set_soe(tfs_handle h, const double* mu, const double* w, int m) {
     h->eta = eta;
     h->soe_set = true;
     h->lim_valid = false;
+    return TFS_OK;
+}
+
+int tfs_set_step_events(tfs_handle h, void* ev_before, void* ev_after) {
+    if (!valid_handle(h)) return TFS_ERR_ARG;
+    if ((ev_before == nullptr) != (ev_after == nullptr)) return TFS_ERR_ARG;
+    h->ev_before = (cudaEvent_t)ev_before;
+    h->ev_after = (cudaEvent_t)ev_after;
     return TFS_OK;
 }
 

@@ -83,37 +83,43 @@ __device__ __forceinline__ const T* plane_src(const FwdArgs<T>& A, const StageMa
     return k < NC ? A.sig_n + (long long)k * N : A.sig_nm1 + (long long)(k - NC) * N;
 }
 
+// Copy the stage planes [pb, pe) of the tile starting at point t0.
 template <typename T, int DIM>
-__device__ __forceinline__ void issue_tile(const FwdArgs<T>& A, const StageMap& S, T* buf, long long t0, int tid,
-                                           int nthr, bool vec16) {
+__device__ __forceinline__ void issue_planes(const FwdArgs<T>& A, const StageMap& S, T* buf, long long t0, int tid,
+                                             int nthr, bool vec16, int pb, int pe) {
     const long long N = A.N;
     if (vec16 && t0 + kTile <= N) {
         // full tile, 16-byte chunks: thread tid always copies chunk k = tid % CPP of
-        // planes tid / CPP, + nthr / CPP, ...; the mode planes of each level are
-        // equally spaced (N apart), so their sources advance by a fixed stride
+        // planes pb + tid / CPP, + nthr / CPP, ...; the mode planes of each level
+        // are equally spaced (N apart), so their sources advance by a fixed stride
         constexpr int EPC = 16 / sizeof(T);
         constexpr int CPP = kTile / EPC;
         const int k = tid % CPP;
         const int step = nthr / CPP;            // planes per round (nthr is a multiple of CPP)
         const int mnc = A.m * (DIM == 2 ? 3 : 6);
         const long long off = t0 + (long long)k * EPC;
-        int plane = tid / CPP;
         const long long stride = (long long)step * N;
-        const T* src = A.modes_n + (long long)plane * N + off;
-        for (; plane < mnc; plane += step, src += stride) cp_async16(buf + plane * kTile + k * EPC, src, 16);
-        src = A.modes_nm1 + (long long)(plane - mnc) * N + off;
-        for (; plane < 2 * mnc; plane += step, src += stride) cp_async16(buf + plane * kTile + k * EPC, src, 16);
-        for (; plane < S.planes; plane += step)
+        int plane = pb + tid / CPP;
+        if (plane < min(pe, mnc)) {
+            const T* src = A.modes_n + (long long)plane * N + off;
+            for (; plane < min(pe, mnc); plane += step, src += stride) cp_async16(buf + plane * kTile + k * EPC, src, 16);
+        }
+        if (plane >= mnc && plane < min(pe, 2 * mnc)) {
+            const T* src = A.modes_nm1 + (long long)(plane - mnc) * N + off;
+            for (; plane < min(pe, 2 * mnc); plane += step, src += stride)
+                cp_async16(buf + plane * kTile + k * EPC, src, 16);
+        }
+        for (; plane < pe; plane += step)
             cp_async16(buf + plane * kTile + k * EPC, plane_src<T, DIM>(A, S, plane) + off, 16);
         return;
     }
     if (vec16) {
         constexpr int EPC = 16 / sizeof(T);    // elements per chunk
         constexpr int CPP = kTile / EPC;       // chunks per plane segment
-        const int total = S.planes * CPP;
+        const int total = (pe - pb) * CPP;
         for (int q = tid; q < total; q += nthr) {
-            const int plane = q / CPP;
-            const int k = q - plane * CPP;
+            const int plane = pb + q / CPP;
+            const int k = q % CPP;
             const long long p0 = t0 + (long long)k * EPC;
             long long valid = N - p0;
             valid = valid < 0 ? 0 : (valid > EPC ? EPC : valid);
@@ -121,15 +127,21 @@ __device__ __forceinline__ void issue_tile(const FwdArgs<T>& A, const StageMap& 
             cp_async16(buf + plane * kTile + k * EPC, base + (valid > 0 ? p0 : 0), (int)(valid * sizeof(T)));
         }
     } else {
-        const int total = S.planes * kTile;
+        const int total = (pe - pb) * kTile;
         for (int q = tid; q < total; q += nthr) {
-            const int plane = q / kTile;
-            const int l = q - plane * kTile;
+            const int plane = pb + q / kTile;
+            const int l = q % kTile;
             const long long p = t0 + l;
             const T* base = plane_src<T, DIM>(A, S, plane);
-            cp_async_small<sizeof(T)>(buf + q, base + (p < N ? p : 0), p < N ? (int)sizeof(T) : 0);
+            cp_async_small<sizeof(T)>(buf + plane * kTile + l, base + (p < N ? p : 0), p < N ? (int)sizeof(T) : 0);
         }
     }
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ void issue_tile(const FwdArgs<T>& A, const StageMap& S, T* buf, long long t0, int tid,
+                                           int nthr, bool vec16) {
+    issue_planes<T, DIM>(A, S, buf, t0, tid, nthr, vec16, 0, S.planes);
 }
 
 // First derivative of E at a point: upwind3 (biased by the sign of u) or central2
@@ -440,9 +452,9 @@ struct StepShape {
     static constexpr int CPW = NC / W;
 };
 
-template <typename T, int DIM, bool TRANSPORT, bool COMP>
+template <typename T, int DIM, bool TRANSPORT, bool COMP, typename Hook>
 __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap& S, T* buf, long long t0,
-                                             int classic, void* sR_raw, float* sD) {
+                                             int classic, void* sR_raw, float* sD, Hook after_pass1) {
     constexpr int NC = Packed<DIM>::NC;
     constexpr int W = StepShape<DIM>::W;
     constexpr int CPW = StepShape<DIM>::CPW;
@@ -566,6 +578,8 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
         }
     }
     __syncthreads();
+    // level n of the mode planes is no longer read in this tile
+    after_pass1();
 
     // ---- (a2) + (a5) point solve by warp 0
     if (w == 0) {
@@ -671,6 +685,7 @@ fwd_kernel(const FwdArgs<T> A, const int classic, const long long num_tiles, con
     const int nthr = 32 * StepShape<DIM>::W;
     float* sD = reinterpret_cast<float*>(sD_store);
 
+    auto none = [] {};
     if (stages == 2) {
         long long tile = blockIdx.x;
         if (tile < num_tiles) issue_tile<T, DIM>(A, S, buf0, tile * kTile, tid, nthr, vec16 != 0);
@@ -683,19 +698,33 @@ fwd_kernel(const FwdArgs<T> A, const int classic, const long long num_tiles, con
             cp_async_commit();
             cp_async_wait<1>();
             __syncthreads();
-            compute_tile<T, DIM, TRANSPORT, COMP>(A, S, cur, tile * kTile, classic, sR_store, sD);
+            compute_tile<T, DIM, TRANSPORT, COMP>(A, S, cur, tile * kTile, classic, sR_store, sD, none);
             __syncthreads();
         }
         cp_async_wait<0>();
     } else {
-        for (long long tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
-            issue_tile<T, DIM>(A, S, buf0, tile * kTile, tid, nthr, vec16 != 0);
-            cp_async_commit();
+        // one stage: the next tile's level-n mode planes are copied as soon as
+        // the current tile has read its own (after its history sums), the rest
+        // (level n-1 and the per-point inputs) after its push-forward
+        const int mnc = (classic ? 0 : A.m) * NC;
+        long long tile = blockIdx.x;
+        if (tile < num_tiles) issue_tile<T, DIM>(A, S, buf0, tile * kTile, tid, nthr, vec16 != 0);
+        cp_async_commit();
+        for (; tile < num_tiles; tile += gridDim.x) {
+            const long long next = tile + gridDim.x;
             cp_async_wait<0>();
             __syncthreads();
-            compute_tile<T, DIM, TRANSPORT, COMP>(A, S, buf0, tile * kTile, classic, sR_store, sD);
+            auto early = [&] {
+                if (next < num_tiles && mnc > 0)
+                    issue_planes<T, DIM>(A, S, buf0, next * kTile, tid, nthr, vec16 != 0, 0, mnc);
+                cp_async_commit();
+            };
+            compute_tile<T, DIM, TRANSPORT, COMP>(A, S, buf0, tile * kTile, classic, sR_store, sD, early);
             __syncthreads();
+            if (next < num_tiles) issue_planes<T, DIM>(A, S, buf0, next * kTile, tid, nthr, vec16 != 0, mnc, S.planes);
+            cp_async_commit();
         }
+        cp_async_wait<0>();
     }
 }
 
@@ -756,9 +785,16 @@ cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s
     if (grid > num_tiles) grid = num_tiles;
     if (grid < 1) grid = 1;
     const int vec16 = (a.N % (16 / (long long)sizeof(T))) == 0;
+    if (cfg.ev_before) {
+        e = cudaEventRecord(cfg.ev_before, s);
+        if (e != cudaSuccess) return e;
+    }
     kern<<<dim3((unsigned)grid), dim3(32, StepShape<DIM>::W), dyn, s>>>(a, cfg.classic ? 1 : 0, num_tiles, stages,
                                                                        vec16);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (cfg.ev_after) e = cudaEventRecord(cfg.ev_after, s);
+    return e;
 }
 
 template <typename T, bool COMP>

@@ -63,6 +63,8 @@ struct LaunchCfg {
     bool transport;
     bool classic;      // alpha == 1
     bool compensated;  // FP32 compensated mode sum
+    cudaEvent_t ev_before = nullptr;   // recorded just before / after the step kernel
+    cudaEvent_t ev_after = nullptr;    // (not around the transport pre-pass), if set
 };
 
 // forward launchers (tfs_forward.cu)

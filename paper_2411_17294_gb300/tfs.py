@@ -25,7 +25,7 @@ TFS_FLAG_NONFINITE, TFS_FLAG_SINGULAR, TFS_FLAG_COURANT = 1, 2, 4
 
 EXPORTS = [
     "tfs_create", "tfs_set_param", "tfs_set_soe", "tfs_transport_limit", "tfs_workspace_bytes", "tfs_bind_workspace",
-    "tfs_set_state", "tfs_step", "tfs_get_stress", "tfs_step_index", "tfs_checkpoint_bytes", "tfs_save",
+    "tfs_set_state", "tfs_step", "tfs_get_stress", "tfs_set_step_events", "tfs_step_index", "tfs_checkpoint_bytes", "tfs_save",
     "tfs_load", "tfs_adjoint_workspace_bytes", "tfs_bind_adjoint_workspace", "tfs_backward", "tfs_status",
     "tfs_strerror", "tfs_destroy", "tfs_run_static",
 ]
@@ -66,6 +66,7 @@ def load_library(path: str | None = None):
         "tfs_set_state": (ctypes.c_int, [H, vp, vp]),
         "tfs_step": (ctypes.c_int, [H, vp, vp, vp, vp]),
         "tfs_get_stress": (ctypes.c_int, [H, vp, vp]),
+        "tfs_set_step_events": (ctypes.c_int, [H, vp, vp]),
         "tfs_step_index": (ctypes.c_long, [H]),
         "tfs_checkpoint_bytes": (sz, [H]),
         "tfs_save": (ctypes.c_int, [H, vp, vp]),
@@ -204,6 +205,20 @@ class Solver:
         check(self.lib.tfs_get_stress(self.h, ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
               "tfs_get_stress")
         return out
+
+    def set_step_events(self, ev_before, ev_after):
+        """Record torch.cuda.Event objects around the step kernel of each later
+        step (None, None turns it off).  torch creates an event's handle on its
+        first record, so each event must have been recorded once before."""
+        def handle(ev):
+            if ev is None:
+                return 0
+            if not ev.cuda_event:
+                raise ValueError("set_step_events: record the event once first (torch creates it lazily)")
+            return ev.cuda_event
+        b = ctypes.c_void_p(handle(ev_before))
+        a = ctypes.c_void_p(handle(ev_after))
+        check(self.lib.tfs_set_step_events(self.h, b, a), "tfs_set_step_events")
 
     def step_index(self) -> int:
         return int(self.lib.tfs_step_index(self.h))
