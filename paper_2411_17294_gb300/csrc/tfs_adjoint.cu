@@ -84,17 +84,18 @@ __device__ __forceinline__ const double* adj_dsrc(const AdjArgs<T>& A, const Adj
     return A.g_kap + (long long)(plane - S.gk) * N;
 }
 
-// Copy one plane family (32-element segments starting at t0) into shared memory.
+// Copy planes [p_begin, p_end) of one plane family (32-element segments
+// starting at t0) into shared memory.
 template <typename E, typename Src>
-__device__ __forceinline__ void stage_planes(E* dst, int planes, Src src_of, long long t0, long long N, int tid,
-                                             int nthr, bool vec16) {
+__device__ __forceinline__ void stage_planes(E* dst, int p_begin, int p_end, Src src_of, long long t0, long long N,
+                                             int tid, int nthr, bool vec16) {
     if (vec16) {
         constexpr int EPC = 16 / sizeof(E);
         constexpr int CPP = kTileA / EPC;
-        const int total = planes * CPP;
+        const int total = (p_end - p_begin) * CPP;
         for (int q = tid; q < total; q += nthr) {
-            const int plane = q / CPP;
-            const int k = q - plane * CPP;
+            const int plane = p_begin + q / CPP;
+            const int k = q - (plane - p_begin) * CPP;
             const long long p0 = t0 + (long long)k * EPC;
             long long valid = N - p0;
             valid = valid < 0 ? 0 : (valid > EPC ? EPC : valid);
@@ -102,25 +103,34 @@ __device__ __forceinline__ void stage_planes(E* dst, int planes, Src src_of, lon
             cp_async16(dst + plane * kTileA + k * EPC, base + (valid > 0 ? p0 : 0), (int)(valid * sizeof(E)));
         }
     } else {
-        const int total = planes * kTileA;
+        const int total = (p_end - p_begin) * kTileA;
         for (int q = tid; q < total; q += nthr) {
-            const int plane = q / kTileA;
-            const int l = q - plane * kTileA;
+            const int plane = p_begin + q / kTileA;
+            const int l = q - (plane - p_begin) * kTileA;
             const long long p = t0 + l;
             const E* base = src_of(plane);
-            cp_async_small<sizeof(E)>(dst + q, base + (p < N ? p : 0), p < N ? (int)sizeof(E) : 0);
+            cp_async_small<sizeof(E)>(dst + plane * kTileA + l, base + (p < N ? p : 0), p < N ? (int)sizeof(E) : 0);
         }
     }
 }
 
+// Stage T planes [tb_begin, tb_end) of a tile, and the double planes if asked.
 template <typename T, int DIM>
 __device__ __forceinline__ void adj_issue(const AdjArgs<T>& A, const AdjStageMap& S, unsigned char* buf, long long t0,
-                                          int tid, int nthr, bool vec16) {
+                                          int tid, int nthr, bool vec16, int tb_begin, int tb_end, bool doubles) {
     T* tb = reinterpret_cast<T*>(buf);
     double* db = reinterpret_cast<double*>(buf + (size_t)S.tplanes * kTileA * sizeof(T));
-    stage_planes<T>(tb, S.tplanes, [&](int pl) { return adj_tsrc<T, DIM>(A, S, pl); }, t0, A.N, tid, nthr, vec16);
-    stage_planes<double>(db, S.dplanes, [&](int pl) { return adj_dsrc<T, DIM>(A, S, pl); }, t0, A.N, tid, nthr,
-                         vec16);
+    stage_planes<T>(tb, tb_begin, tb_end, [&](int pl) { return adj_tsrc<T, DIM>(A, S, pl); }, t0, A.N, tid, nthr,
+                    vec16);
+    if (doubles)
+        stage_planes<double>(db, 0, S.dplanes, [&](int pl) { return adj_dsrc<T, DIM>(A, S, pl); }, t0, A.N, tid,
+                             nthr, vec16);
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ void adj_issue_all(const AdjArgs<T>& A, const AdjStageMap& S, unsigned char* buf,
+                                              long long t0, int tid, int nthr, bool vec16) {
+    adj_issue<T, DIM>(A, S, buf, t0, tid, nthr, vec16, 0, S.tplanes, true);
 }
 
 template <int DIM>
@@ -130,10 +140,19 @@ struct AdjShape {
     static constexpr int CPW = NC / W;
 };
 
+// Resident blocks asked of the register allocator: the most that compile
+// without spills (2D: 6; 3D: 5 in FP32, 4 in FP64).
 template <typename T, int DIM>
+constexpr int adj_min_blocks() {
+    return DIM == 2 ? 6 : (sizeof(T) == 4 ? 5 : 4);
+}
+
+// One tile.  `after_pass1` runs on all threads right after the barrier that
+// ends the first pass, when the lamQ' planes are no longer read.
+template <typename T, int DIM, typename Hook>
 __device__ __forceinline__ void adj_tile(const AdjArgs<T>& A, const AdjStageMap& S, unsigned char* buf,
                                          long long t0, int classic, double* sS, double* sL, double& gWi,
-                                         double& gbeta) {
+                                         double& gbeta, Hook after_pass1) {
     constexpr int NC = Packed<DIM>::NC;
     constexpr int W = AdjShape<DIM>::W;
     constexpr int CPW = AdjShape<DIM>::CPW;
@@ -193,6 +212,7 @@ __device__ __forceinline__ void adj_tile(const AdjArgs<T>& A, const AdjStageMap&
         for (int cc = 0; cc < CPW; ++cc) sS[(w + cc * W) * kTileA + lane] = 0.0;
     }
     __syncthreads();
+    after_pass1();
 
     // ---- point system and parameter derivatives by warp 0.  FP64 storage:
     //      FP64 throughout.  FP32 storage: the per-point arithmetic in FP32 (FP32
@@ -338,7 +358,7 @@ __device__ __forceinline__ void adj_tile(const AdjArgs<T>& A, const AdjStageMap&
 }
 
 template <typename T, int DIM>
-__global__ void __launch_bounds__(32 * AdjShape<DIM>::W, 2)
+__global__ void __launch_bounds__(32 * AdjShape<DIM>::W, adj_min_blocks<T, DIM>())
 adj_kernel(const AdjArgs<T> A, const int classic, const long long num_tiles, const int stages, const int vec16) {
     constexpr int NC = Packed<DIM>::NC;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -353,31 +373,42 @@ adj_kernel(const AdjArgs<T> A, const int classic, const long long num_tiles, con
     const int nthr = 32 * AdjShape<DIM>::W;
     double gWi = 0.0, gbeta = 0.0;
 
+    const bool v16 = vec16 != 0;
     if (stages == 2) {
         long long tile = blockIdx.x;
-        if (tile < num_tiles) adj_issue<T, DIM>(A, S, buf0, tile * kTileA, tid, nthr, vec16 != 0);
+        if (tile < num_tiles) adj_issue_all<T, DIM>(A, S, buf0, tile * kTileA, tid, nthr, v16);
         cp_async_commit();
         for (int it = 0; tile < num_tiles; ++it, tile += gridDim.x) {
             const long long next = tile + gridDim.x;
             unsigned char* cur = (it & 1) ? buf1 : buf0;
             unsigned char* nxt = (it & 1) ? buf0 : buf1;
-            if (next < num_tiles) adj_issue<T, DIM>(A, S, nxt, next * kTileA, tid, nthr, vec16 != 0);
+            if (next < num_tiles) adj_issue_all<T, DIM>(A, S, nxt, next * kTileA, tid, nthr, v16);
             cp_async_commit();
             cp_async_wait<1>();
             __syncthreads();
-            adj_tile<T, DIM>(A, S, cur, tile * kTileA, classic, sS, sL, gWi, gbeta);
+            adj_tile<T, DIM>(A, S, cur, tile * kTileA, classic, sS, sL, gWi, gbeta, [] {});
             __syncthreads();
         }
         cp_async_wait<0>();
     } else {
-        for (long long tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
-            adj_issue<T, DIM>(A, S, buf0, tile * kTileA, tid, nthr, vec16 != 0);
-            cp_async_commit();
+        // One stage: the next tile's lamQ' planes are fetched while this tile
+        // solves and writes its new level; the other planes after it is done.
+        long long tile = blockIdx.x;
+        if (tile < num_tiles) adj_issue_all<T, DIM>(A, S, buf0, tile * kTileA, tid, nthr, v16);
+        cp_async_commit();
+        for (; tile < num_tiles; tile += gridDim.x) {
+            const long long next = tile + gridDim.x;
             cp_async_wait<0>();
             __syncthreads();
-            adj_tile<T, DIM>(A, S, buf0, tile * kTileA, classic, sS, sL, gWi, gbeta);
+            adj_tile<T, DIM>(A, S, buf0, tile * kTileA, classic, sS, sL, gWi, gbeta, [&] {
+                if (next < num_tiles) adj_issue<T, DIM>(A, S, buf0, next * kTileA, tid, nthr, v16, 0, S.e2, false);
+                cp_async_commit();
+            });
             __syncthreads();
+            if (next < num_tiles) adj_issue<T, DIM>(A, S, buf0, next * kTileA, tid, nthr, v16, S.e2, S.tplanes, true);
+            cp_async_commit();
         }
+        cp_async_wait<0>();
     }
     // per-block sums of the two scalar derivatives (warp 0 holds them)
     if (threadIdx.y == 0) {
