@@ -265,6 +265,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32plain"])
+    ap.add_argument("--grid", type=int, default=WORKLOAD["n"][0],
+                    help="cube side of the step workload (default 256; smaller sides are for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -295,7 +297,10 @@ def main():
     if dist is not None:
         dist.barrier()
 
-    W = WORKLOAD
+    W = dict(WORKLOAD)
+    if args.grid != WORKLOAD["n"][0]:
+        W["n"] = (args.grid,) * 3
+        W["name"] = W["name"].replace("256^3", f"{args.grid}^3")
     prec = {"fp32": tfs.TFS_FP32, "fp64": tfs.TFS_FP64, "fp32plain": tfs.TFS_FP32_PLAIN}[args.precision]
     dt = W["dt"]
     mu, w = soe.build(W["alpha"], dt, W["horizon_steps"] * dt, W["m"])
@@ -420,7 +425,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": W["name"], "grid": list(W["n"]), "m": W["m"], "alpha": W["alpha"],
                        "Wi": W["Wi"], "beta": W["beta"], "dt": W["dt"], "transport": True,
-                       "precision": args.precision, "l2": "per-step working set ~41 GB >> 129 MB L2, no flush",
+                       "precision": args.precision, "l2": f"per-step working set {algorithmic_bytes_per_point(3, W['m'], elem) * N / 1e9:.1f} GB "
+                             f">> 129 MB L2, no flush",
                        "points_per_gpu": N},
             "roofline": {"bound": "hbm", "kernel": "fwd_kernel<float,3> (step kernel)", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,

@@ -90,7 +90,9 @@ enum { TFS_STENCIL_UPWIND3 = 0, TFS_STENCIL_CENTRAL2 = 1 };
 enum {
     TFS_FLAG_NONFINITE = 1u,  /* a new stress value was NaN or Inf */
     TFS_FLAG_SINGULAR = 2u,   /* a point system had a pivot below 1e-300 / relative 1e-14 */
-    TFS_FLAG_COURANT = 4u     /* a point had dt sum_a |u_a|/h_a above the limit of tfs_transport_limit */
+    TFS_FLAG_COURANT = 4u,    /* a point had dt sum_a |u_a|/h_a above the limit of tfs_transport_limit */
+    TFS_FLAG_TIMEOUT = 8u     /* a kernel gave up waiting for its own tile copies (bounded wait; the
+                                 step's output is then incomplete) */
 };
 
 typedef struct {

@@ -499,38 +499,18 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partials, int 
 
 template <typename T, int DIM>
 cudaError_t launch_adj(const AdjArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    int max_optin = 0, sms = 0;
-    e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
     auto kern = adj_kernel<T, DIM>;
     const AdjStageMap S = adj_stage_map<DIM>(cfg.classic ? 0 : a.m);
     const size_t sb = adj_stage_bytes<T>(S);
     const size_t static_bytes = 2 * Packed<DIM>::NC * kTileA * sizeof(double) + 64;
-    if (sb + static_bytes > (size_t)max_optin) return cudaErrorInvalidConfiguration;
-    int best_stages = 1, per_sm = 0;
-    for (int st = 1; st <= 2; ++st) {
-        const size_t dyn_try = st * sb;
-        if (dyn_try + static_bytes > (size_t)max_optin) continue;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_try);
-        if (e != cudaSuccess) return e;
-        int blocks = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, 32 * AdjShape<DIM>::W, dyn_try);
-        if (e != cudaSuccess) return e;
-        if (blocks >= per_sm) {
-            per_sm = blocks;
-            best_stages = st;
-        }
-    }
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const size_t dyn = best_stages * sb;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    PersistPlan plan;
+    cudaError_t e = persistent_plan(reinterpret_cast<const void*>(kern), 32 * AdjShape<DIM>::W, sb, static_bytes, 2,
+                                    &plan);
     if (e != cudaSuccess) return e;
+    const int best_stages = plan.stages;
+    const size_t dyn = plan.dyn;
     const long long num_tiles = (a.N + kTileA - 1) / kTileA;
-    long long grid = (long long)per_sm * sms;
+    long long grid = (long long)plan.per_sm * plan.sms;
     if (grid > num_tiles) grid = num_tiles;
     if (grid < 1) grid = 1;
     const int vec16 = (a.N % (16 / (long long)sizeof(T))) == 0 && (a.N % 2) == 0;

@@ -35,6 +35,8 @@
 // result, and the FP64 pipe (1/64 of the FP32 rate on this GPU) stays free.
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "tfs_device.cuh"
 #include "tfs_internal.h"
 
@@ -142,6 +144,36 @@ template <typename T, int DIM>
 __device__ __forceinline__ void issue_tile(const FwdArgs<T>& A, const StageMap& S, T* buf, long long t0, int tid,
                                            int nthr, bool vec16) {
     issue_planes<T, DIM>(A, S, buf, t0, tid, nthr, vec16, 0, S.planes);
+}
+
+// TMA staging (one thread issues): the level-n mode planes complete on bar_e,
+// everything else (level n-1, kappa levels, A, sigma0, stress levels) on bar_l.
+template <typename T, int DIM, bool TRANSPORT>
+__device__ __forceinline__ void tma_issue(const TmaPlan& tp, const StageMap& S, T* buf, long long t0, int mnc,
+                                          bool has_s0, bool classic, bool early, bool late, uint64_t* bar_e,
+                                          uint64_t* bar_l) {
+    constexpr int NC = Packed<DIM>::NC;
+    constexpr unsigned kPlaneBytes = kTile * sizeof(T);
+    const int x = (int)t0;
+    fence_proxy_async_smem();
+    if (early && mnc > 0) {
+        mbar_arrive_expect_tx(bar_e, (unsigned)mnc * kPlaneBytes);
+        for (int b = 0; b < tp.mode_boxes; ++b)
+            tma_load_2d(buf + (size_t)b * tp.mode_box * kTile, &tp.lv_n, x, b * tp.mode_box, bar_e);
+    }
+    if (late) {
+        mbar_arrive_expect_tx(bar_l, (unsigned)(S.planes - mnc) * kPlaneBytes);
+        for (int b = 0; b < tp.mode_boxes && mnc > 0; ++b)
+            tma_load_2d(buf + (size_t)(mnc + b * tp.mode_box) * kTile, &tp.lv_nm1, x, b * tp.mode_box, bar_l);
+        tma_load_2d(buf + (size_t)S.kn * kTile, &tp.kn, x, 0, bar_l);
+        tma_load_2d(buf + (size_t)S.km * kTile, &tp.km, x, 0, bar_l);
+        if (TRANSPORT) tma_load_2d(buf + (size_t)S.tr * kTile, &tp.tr, x, 0, bar_l);
+        if (has_s0) tma_load_2d(buf + (size_t)S.s0 * kTile, &tp.s0, x, 0, bar_l);
+        if (classic) {
+            tma_load_2d(buf + (size_t)S.sig * kTile, &tp.sn, x, 0, bar_l);
+            tma_load_2d(buf + (size_t)(S.sig + NC) * kTile, &tp.sm, x, 0, bar_l);
+        }
+    }
 }
 
 // First derivative of E at a point: upwind3 (biased by the sign of u) or central2
@@ -670,73 +702,108 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
     }
 }
 
+// Persistent step kernel.  Tiles are staged either by TMA (tp.on: one thread
+// issues tensor-map copies that complete on mbarriers; every wait is bounded
+// and a wait that gives up latches TFS_FLAG_TIMEOUT) or by cp.async (any grid).
+// Two stage buffers double-buffer whole tiles; with one, the next tile's
+// level-n mode planes are fetched as soon as the current tile has read its
+// own (after its history sums) and the rest after its push-forward.  One loop
+// serves every variant, so that the tile code is instantiated once.
 template <typename T, int DIM, bool TRANSPORT, bool COMP>
 __global__ void __launch_bounds__(32 * StepShape<DIM>::W, 4)
-fwd_kernel(const FwdArgs<T> A, const int classic, const long long num_tiles, const int stages, const int vec16) {
+fwd_kernel(const FwdArgs<T> A, const __grid_constant__ TmaPlan tp, const int classic, const long long num_tiles,
+           const int stages, const int vec16) {
     constexpr int NC = Packed<DIM>::NC;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(16) double sR_store[NC * kTile];       // R per (component, point): double or f2
     __shared__ __align__(16) double sD_store[NC * kTile];       // sigma^{n+1} - sigma0 (float or double)
+    __shared__ __align__(8) uint64_t bars[2][2];                // TMA: [stage buffer][early, late]
     const StageMap S = stage_map<DIM>(classic ? 0 : A.m, TRANSPORT, A.sigma0 != nullptr, classic != 0);
     const size_t stage_elems = (size_t)S.planes * kTile;
-    T* buf0 = reinterpret_cast<T*>(smem);
+    // stage buffers start on a 128-byte boundary (TMA destination)
+    T* buf0 = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(smem) + 127) & ~uintptr_t(127));
     T* buf1 = buf0 + stage_elems;
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const int nthr = 32 * StepShape<DIM>::W;
     float* sD = reinterpret_cast<float*>(sD_store);
+    const bool use_tma = tp.on != 0;
+    const bool v16 = vec16 != 0;
+    const int mnc = (classic ? 0 : A.m) * NC;
+    const bool has_s0 = A.sigma0 != nullptr;
+    const bool two = stages == 2;
 
-    auto none = [] {};
-    if (stages == 2) {
-        long long tile = blockIdx.x;
-        if (tile < num_tiles) issue_tile<T, DIM>(A, S, buf0, tile * kTile, tid, nthr, vec16 != 0);
-        cp_async_commit();
-        for (int it = 0; tile < num_tiles; ++it, tile += gridDim.x) {
-            const long long next = tile + gridDim.x;
-            T* cur = (it & 1) ? buf1 : buf0;
-            T* nxt = (it & 1) ? buf0 : buf1;
-            if (next < num_tiles) issue_tile<T, DIM>(A, S, nxt, next * kTile, tid, nthr, vec16 != 0);
-            cp_async_commit();
-            cp_async_wait<1>();
-            __syncthreads();
-            compute_tile<T, DIM, TRANSPORT, COMP>(A, S, cur, tile * kTile, classic, sR_store, sD, none);
-            __syncthreads();
+    if (use_tma) {
+        if (tid == 0) {
+            mbar_init(&bars[0][0], 1);
+            mbar_init(&bars[0][1], 1);
+            mbar_init(&bars[1][0], 1);
+            mbar_init(&bars[1][1], 1);
+            fence_mbar_init();
         }
-        cp_async_wait<0>();
-    } else {
-        // one stage: the next tile's level-n mode planes are copied as soon as
-        // the current tile has read its own (after its history sums), the rest
-        // (level n-1 and the per-point inputs) after its push-forward
-        const int mnc = (classic ? 0 : A.m) * NC;
-        long long tile = blockIdx.x;
-        if (tile < num_tiles) issue_tile<T, DIM>(A, S, buf0, tile * kTile, tid, nthr, vec16 != 0);
-        cp_async_commit();
-        for (; tile < num_tiles; tile += gridDim.x) {
-            const long long next = tile + gridDim.x;
-            cp_async_wait<0>();
-            __syncthreads();
-            auto early = [&] {
-                if (next < num_tiles && mnc > 0)
-                    issue_planes<T, DIM>(A, S, buf0, next * kTile, tid, nthr, vec16 != 0, 0, mnc);
-                cp_async_commit();
-            };
-            compute_tile<T, DIM, TRANSPORT, COMP>(A, S, buf0, tile * kTile, classic, sR_store, sD, early);
-            __syncthreads();
-            if (next < num_tiles) issue_planes<T, DIM>(A, S, buf0, next * kTile, tid, nthr, vec16 != 0, mnc, S.planes);
-            cp_async_commit();
-        }
-        cp_async_wait<0>();
+        __syncthreads();
     }
+    // stage planes of tile t into buffer b: early = level-n mode planes, late = the rest
+    auto issue = [&](int b, long long t, bool early, bool late) {
+        T* dst = b ? buf1 : buf0;
+        if (use_tma) {
+            if (tid == 0)
+                tma_issue<T, DIM, TRANSPORT>(tp, S, dst, t * kTile, mnc, has_s0, classic != 0, early, late, &bars[b][0],
+                                             &bars[b][1]);
+        } else {
+            issue_planes<T, DIM>(A, S, dst, t * kTile, tid, nthr, v16, early ? 0 : mnc, late ? S.planes : mnc);
+            cp_async_commit();
+        }
+    };
+    // each TMA barrier completes one phase per tile staged in its buffer
+    auto wait_tma = [&](int b, unsigned parity) -> bool {
+        bool ok = true;
+        if (mnc > 0) ok = mbar_wait(&bars[b][0], parity);
+        return mbar_wait(&bars[b][1], parity) && ok;
+    };
+
+    long long tile = blockIdx.x;
+    if (tile < num_tiles) issue(0, tile, true, true);
+    for (int it = 0; tile < num_tiles; ++it, tile += gridDim.x) {
+        const long long next = tile + gridDim.x;
+        const int b = two ? (it & 1) : 0;
+        if (two && next < num_tiles) issue(b ^ 1, next, true, true);
+        if (use_tma) {
+            const unsigned parity = two ? ((unsigned)(it >> 1) & 1u) : ((unsigned)it & 1u);
+            const bool ok = wait_tma(b, parity);
+            if (__syncthreads_or(!ok)) {
+                // give up: flag it and let the copies still in flight land (bounded) before exiting
+                if (tid == 0) atomicOr(A.flags, 8u);
+                wait_tma(b, parity);
+                if (two && next < num_tiles) wait_tma(b ^ 1, (unsigned)((it + 1) >> 1) & 1u);
+                return;
+            }
+        } else {
+            if (two && next < num_tiles) cp_async_wait<1>();
+            else cp_async_wait<0>();
+            __syncthreads();
+        }
+        auto early = [&] {
+            if (!two && next < num_tiles) issue(0, next, true, false);
+        };
+        compute_tile<T, DIM, TRANSPORT, COMP>(A, S, b ? buf1 : buf0, tile * kTile, classic, sR_store, sD, early);
+        __syncthreads();
+        if (!two && next < num_tiles) issue(0, next, false, true);
+    }
+    if (!use_tma) cp_async_wait<0>();
 }
 
 template <typename T, int DIM, bool TRANSPORT, bool COMP>
 cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s) {
     constexpr int NC = Packed<DIM>::NC;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    int max_optin = 0, sms = 0;
-    e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e;
+    auto kern = fwd_kernel<T, DIM, TRANSPORT, COMP>;
+    const long long num_tiles = (a.N + kTile - 1) / kTile;
+    const StageMap S = stage_map<DIM>(cfg.classic ? 0 : a.m, TRANSPORT, a.sigma0 != nullptr, cfg.classic);
+    const size_t stage_bytes = (size_t)S.planes * kTile * sizeof(T);
+    const size_t static_bytes = 2 * NC * kTile * sizeof(double) + 32;
+    PersistPlan plan;
+    e = persistent_plan(reinterpret_cast<const void*>(kern), 32 * StepShape<DIM>::W, stage_bytes, static_bytes, 2,
+                        &plan);
     if (e != cudaSuccess) return e;
     if (TRANSPORT) {
         if (!a.trans) return cudaErrorInvalidValue;
@@ -748,49 +815,48 @@ cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s
         } else {
             const int threads = 256;
             long long blocks = (a.N + threads - 1) / threads;
-            if (blocks > (long long)sms * 16) blocks = (long long)sms * 16;
+            if (blocks > (long long)plan.sms * 16) blocks = (long long)plan.sms * 16;
             transport_kernel<T, DIM><<<(unsigned)blocks, threads, 0, s>>>(a, cfg.stencil);
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    auto kern = fwd_kernel<T, DIM, TRANSPORT, COMP>;
-    const long long num_tiles = (a.N + kTile - 1) / kTile;
-    const StageMap S = stage_map<DIM>(cfg.classic ? 0 : a.m, TRANSPORT, a.sigma0 != nullptr, cfg.classic);
-    const size_t stage_bytes = (size_t)S.planes * kTile * sizeof(T);
-    const size_t static_bytes = 2 * NC * kTile * sizeof(double);
-    // one or two stages per block: more resident blocks (more tiles and point
-    // solves in flight per SM) win; on a tie the second stage adds prefetch
-    if (stage_bytes + static_bytes > (size_t)max_optin) return cudaErrorInvalidConfiguration;
-    int best_stages = 1, per_sm = 0;
-    for (int st = 1; st <= 2; ++st) {
-        const size_t dyn_try = st * stage_bytes;
-        if (dyn_try + static_bytes > (size_t)max_optin) continue;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_try);
-        if (e != cudaSuccess) return e;
-        int blocks = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, 32 * StepShape<DIM>::W, dyn_try);
-        if (e != cudaSuccess) return e;
-        if (blocks >= per_sm) {
-            per_sm = blocks;
-            best_stages = st;
-        }
-    }
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int stages = best_stages;
-    const size_t dyn = stages * stage_bytes;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    if (e != cudaSuccess) return e;
-    long long grid = (long long)per_sm * sms;
+    const int stages = plan.stages;
+    const size_t dyn = plan.dyn;
+    long long grid = (long long)plan.per_sm * plan.sms;
     if (grid > num_tiles) grid = num_tiles;
     if (grid < 1) grid = 1;
     const int vec16 = (a.N % (16 / (long long)sizeof(T))) == 0;
+    // tensor maps of every staged plane group; any refusal selects cp.async
+    TmaPlan tp;
+    memset(&tp, 0, sizeof(tp));
+    {
+        const bool dbl = sizeof(T) == 8;
+        const int mnc = (cfg.classic ? 0 : a.m) * NC;
+        int boxes = (mnc + 255) / 256;
+        while (boxes > 0 && boxes <= mnc && mnc % boxes != 0) ++boxes;
+        tp.mode_boxes = mnc > 0 ? boxes : 0;
+        tp.mode_box = mnc > 0 ? mnc / boxes : 0;
+        bool ok = a.N < (1ll << 31);
+        if (ok && mnc > 0) {
+            ok = encode_plane_map(&tp.lv_n, a.modes_n, a.N, mnc, tp.mode_box, dbl) &&
+                 encode_plane_map(&tp.lv_nm1, a.modes_nm1, a.N, mnc, tp.mode_box, dbl);
+        }
+        ok = ok && encode_plane_map(&tp.kn, a.kap_n, a.N, DIM * DIM, DIM * DIM, dbl) &&
+             encode_plane_map(&tp.km, a.kap_nm1, a.N, DIM * DIM, DIM * DIM, dbl);
+        if (ok && TRANSPORT) ok = encode_plane_map(&tp.tr, a.trans, a.N, NC, NC, dbl);
+        if (ok && a.sigma0) ok = encode_plane_map(&tp.s0, a.sigma0, a.N, NC, NC, dbl);
+        if (ok && cfg.classic)
+            ok = encode_plane_map(&tp.sn, a.sig_n, a.N, NC, NC, dbl) &&
+                 encode_plane_map(&tp.sm, a.sig_nm1, a.N, NC, NC, dbl);
+        tp.on = ok ? 1 : 0;
+    }
     if (cfg.ev_before) {
         e = cudaEventRecord(cfg.ev_before, s);
         if (e != cudaSuccess) return e;
     }
-    kern<<<dim3((unsigned)grid), dim3(32, StepShape<DIM>::W), dyn, s>>>(a, cfg.classic ? 1 : 0, num_tiles, stages,
-                                                                       vec16);
+    kern<<<dim3((unsigned)grid), dim3(32, StepShape<DIM>::W), dyn, s>>>(a, tp, cfg.classic ? 1 : 0, num_tiles,
+                                                                       stages, vec16);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (cfg.ev_after) e = cudaEventRecord(cfg.ev_after, s);

@@ -2,6 +2,7 @@
 // Not part of the public ABI (see include/tfs.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -56,6 +57,34 @@ struct FwdArgs {
     F2c eta_f2, a_f2, dt_f2, src_f2;   // src = dt G g
     typename ModeConsts<T>::type mc;
 };
+
+// Tensor maps of the plane groups a tile stages, each a 2D view [planes][N]
+// (x = point, y = plane) with a box of 32 points; `on` = 0 selects the
+// cp.async path (grids whose N * element size is not a multiple of 16 bytes,
+// or unaligned fields).
+struct TmaPlan {
+    CUtensorMap lv_n, lv_nm1;   // mode levels n and n-1: box height mode_box, mode_boxes boxes per level
+    CUtensorMap kn, km;         // velocity gradient levels [d*d]
+    CUtensorMap tr, s0;         // transport term, initial stress [nc]
+    CUtensorMap sn, sm;         // stress levels n, n-1 [nc] (alpha = 1)
+    int on;
+    int mode_box, mode_boxes;
+};
+
+// Host: encode a [planes][N] tensor map with a box of 32 x box_h (false if the
+// layout does not allow one).
+bool encode_plane_map(CUtensorMap* map, const void* base, long long N, int planes, int box_h, bool dbl);
+
+// Launch shape of a persistent tile kernel: stage buffers per block, resident
+// blocks per SM, SM count and dynamic shared memory (stages * stage bytes +
+// 128 bytes of alignment slack).  Computed once per kernel, device and stage
+// size (the kernel's dynamic shared-memory limit is set then) and cached.
+struct PersistPlan {
+    int stages, per_sm, sms;
+    size_t dyn;
+};
+cudaError_t persistent_plan(const void* kern, int threads, size_t stage_bytes, size_t static_bytes, int max_stages,
+                            PersistPlan* out);
 
 struct LaunchCfg {
     int dim;

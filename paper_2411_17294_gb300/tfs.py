@@ -21,7 +21,7 @@ TFS_OK, TFS_ERR_ARG, TFS_ERR_NOSOE, TFS_ERR_UNSTABLE, TFS_ERR_CUDA, TFS_ERR_STAT
 TFS_FP64, TFS_FP32, TFS_FP32_PLAIN = 0, 1, 2
 TFS_PARAM_RE, TFS_PARAM_EPS, TFS_PARAM_STENCIL, TFS_PARAM_TRANSPORT, TFS_PARAM_UMAX = range(5)
 TFS_STENCIL_UPWIND3, TFS_STENCIL_CENTRAL2 = 0, 1
-TFS_FLAG_NONFINITE, TFS_FLAG_SINGULAR, TFS_FLAG_COURANT = 1, 2, 4
+TFS_FLAG_NONFINITE, TFS_FLAG_SINGULAR, TFS_FLAG_COURANT, TFS_FLAG_TIMEOUT = 1, 2, 4, 8
 
 EXPORTS = [
     "tfs_create", "tfs_set_param", "tfs_set_soe", "tfs_transport_limit", "tfs_workspace_bytes", "tfs_bind_workspace",

@@ -50,6 +50,8 @@ def run_gpu(case: dict, sigma0, kap_seq, u, steps: int, precision: int, return_s
         for n in range(steps):
             s.step(kt, kt, ut)
     out = s.stress().double().cpu().numpy()
+    # no kernel gave up waiting for its own tile copies
+    assert not (s.status() & tfs.TFS_FLAG_TIMEOUT)
     if return_solver:
         return out, s
     s.close()
