@@ -60,7 +60,7 @@ def step_kernel_bytes_per_point(dim: int, m: int, elem: int, transport: bool) ->
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fwd_kernel_3d256_fp32_traffic.md")
 STEP_KERNEL_SOURCES = [os.path.join(ROOT, "paper_2411_17294_gb300", "csrc", f)
-                       for f in ("tfs_forward.cu", "tfs_device.cuh", "tfs_internal.h")]
+                       for f in ("tfs_forward.cu", "tfs_device.cuh", "tfs_internal.h", "tfs_util.cu")]
 
 
 def step_kernel_source_hash() -> str:
@@ -264,6 +264,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-only", default=None, choices=["fp32", "fp64"],
+                    help="time only the adjoint workload in one precision and print its record (profiling)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32plain"])
     ap.add_argument("--grid", type=int, default=WORKLOAD["n"][0],
                     help="cube side of the step workload (default 256; smaller sides are for profiling)")
@@ -276,6 +278,15 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.adjoint_only:
+        import torch
+        from paper_2411_17294_gb300 import build as tbuild
+        from paper_2411_17294_gb300 import tfs
+        tbuild.build()
+        torch.cuda.set_device(0)
+        prec = tfs.TFS_FP32 if args.adjoint_only == "fp32" else tfs.TFS_FP64
+        print(json.dumps(adjoint_ratio(torch.device("cuda", 0), prec)), flush=True)
         return
 
     import numpy as np

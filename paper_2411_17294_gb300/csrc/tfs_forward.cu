@@ -345,6 +345,7 @@ __global__ void __launch_bounds__(256) transport_kernel(const FwdArgs<T> A, cons
     constexpr int NC = Packed<DIM>::NC;
     const long long N = A.N;
     const float ccoef = (float)A.courant_coef, climit = (float)A.courant_limit;
+    const float ihf[3] = {(float)A.inv_h[0], (float)A.inv_h[1], (float)A.inv_h[2]};
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
         const unsigned pu = (unsigned)p;
         const unsigned px = pu % (unsigned)A.n0;
@@ -360,7 +361,7 @@ __global__ void __launch_bounds__(256) transport_kernel(const FwdArgs<T> A, cons
         if (ccoef > 0.0f) {
             float cr = 0.0f;
 #pragma unroll
-            for (int ax = 0; ax < DIM; ++ax) cr += fabsf((float)A.u[(long long)ax * N + p]) * (float)A.inv_h[ax];
+            for (int ax = 0; ax < DIM; ++ax) cr += fabsf((float)A.u[(long long)ax * N + p]) * ihf[ax];
             if (ccoef * cr > climit) atomicOr(A.flags, 4u);
         }
     }
@@ -395,6 +396,7 @@ __global__ void __launch_bounds__(kTX * kTY) transport_tiled(const FwdArgs<T> A,
     const T dtT = (T)A.dt, edt = (T)(A.eps * A.dt);
     const bool lap = A.eps != 0.0;
     const float ccoef = (float)A.courant_coef, climit = (float)A.courant_limit;
+    const float ihf[3] = {(float)A.inv_h[0], (float)A.inv_h[1], (float)A.inv_h[2]};
     auto Eat = [&](int c, int gx, int gy, int gz) -> T {
         const long long q = (long long)c * N + gx + (long long)n0 * gy + plane * gz;
         return (T)2 * __ldg(A.sig_n + q) - __ldg(A.sig_nm1 + q);
@@ -462,7 +464,7 @@ __global__ void __launch_bounds__(kTX * kTY) transport_tiled(const FwdArgs<T> A,
         if (ccoef > 0.0f) {
             float cr = 0.0f;
 #pragma unroll
-            for (int ax = 0; ax < DIM; ++ax) cr += fabsf((float)u[ax]) * (float)A.inv_h[ax];
+            for (int ax = 0; ax < DIM; ++ax) cr += fabsf((float)u[ax]) * ihf[ax];
             if (ccoef * cr > climit) atomicOr(A.flags, 4u);
         }
         __syncthreads();
