@@ -1,0 +1,102 @@
+"""Precision sweep: FP64 storage, FP32 storage with the compensated mode sum,
+and FP32 storage with a plain mode sum, against the FP64 oracle.
+
+Workload: 3D periodic 192^3, m in {16, 32, 48}, alpha in {0.2, 0.5, 0.9},
+Wi = 2, beta = 0.9, dt = 2e-4, 500 steps from rest (sigma0 = 0), frozen
+divergence-free k^-5/3 velocity |k| <= 24 (seed 4) whose gradient is scaled
+by 0.1 (max |kappa| ~ 1, so Wi |kappa| stays near the coil-stretch threshold;
+at unit RMS, max |kappa| ~ 10, the stress grows without bound within the 500
+steps and overflows at alpha = 0.2).  The explicit transport is outside its
+stability region for alpha = 0.5 and 0.2 at this resolution, so the sweep
+runs the pointwise law (transport off) for every alpha; points are then
+independent and the oracle runs on sampled points alone, fed the velocity
+gradient the GPU saw (rounded to FP32 in the FP32 modes), so the measured
+error is that of the storage and arithmetic.
+
+Error per stress component: max |GPU - oracle| / max |oracle| and the RMS
+version, over the sampled points.  By default one combination runs (alpha =
+0.5, m = 32); TFS_PRECISION_SWEEP=1 runs all nine and prints the table.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from helpers import ensure_lib
+from oracle import orc
+from oracle import soe as osoe
+from paper_2411_17294_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+N3 = (192, 192, 192)
+WI, BETA, DT, STEPS = 2.0, 0.9, 2e-4, 500
+SAMPLES = 1024
+FULL = os.environ.get("TFS_PRECISION_SWEEP") == "1"
+COMBOS = [(a, m) for a in (0.2, 0.5, 0.9) for m in (16, 32, 48)] if FULL else [(0.5, 32)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ensure_lib()
+
+
+@pytest.fixture(scope="module")
+def field():
+    _, kap = inputs.spectral_velocity(3, N3, 24, 4)
+    kap = np.ascontiguousarray(0.1 * kap)
+    rng = np.random.default_rng(11)
+    N = int(np.prod(N3))
+    pts = np.unique(np.concatenate([rng.integers(0, N, size=SAMPLES), [0, N - 1]]))
+    return kap, pts
+
+
+def gpu_run(kap, alpha, m, mu, w, precision):
+    """Whole-grid run; returns the final stress and the gradient as the GPU
+    stored it (FP32-rounded in the FP32 modes)."""
+    import torch
+    from paper_2411_17294_gb300 import tfs
+    s = tfs.Solver(3, N3, alpha, WI, BETA, DT, m=m, precision=precision, mu=mu, w=w, transport=False)
+    kt = torch.tensor(kap, dtype=s.dtype, device=s.device)
+    seen = kt.double().cpu().numpy()
+    s.set_state(None)
+    for _ in range(STEPS):
+        s.step(kt, kt, None)
+    out = s.stress().double().cpu().numpy()
+    assert not (s.status() & (tfs.TFS_FLAG_NONFINITE | tfs.TFS_FLAG_TIMEOUT))
+    s.close()
+    return out, seen
+
+
+def oracle_run(kap_s, alpha, mu, w):
+    prob = orc.Problem(dim=3, n=(kap_s.shape[1], 1, 1), alpha=alpha, Wi=WI, beta=BETA, dt=DT, mu=mu, w=w)
+    return orc.forward(prob, None, np.ascontiguousarray(kap_s), None, STEPS)
+
+
+def errors(got, ref):
+    scale = np.max(np.abs(ref), axis=1)
+    d = got - ref
+    return np.max(np.abs(d), axis=1) / scale, np.sqrt(np.mean(d * d, axis=1)) / np.sqrt(np.mean(ref * ref, axis=1))
+
+
+@pytest.mark.parametrize("alpha,m", COMBOS)
+def test_precision_sweep(field, alpha, m):
+    from paper_2411_17294_gb300 import tfs
+    kap, pts = field
+    mu, w = osoe.soe_nnls(alpha, DT, STEPS * DT, m)
+    rows, refs = {}, {}
+    for name, prec in (("fp64", tfs.TFS_FP64), ("fp32+kahan", tfs.TFS_FP32), ("fp32", tfs.TFS_FP32_PLAIN)):
+        out, kseen = gpu_run(kap, alpha, m, mu, w, prec)
+        key = "fp64" if prec == tfs.TFS_FP64 else "fp32"
+        if key not in refs:
+            refs[key] = oracle_run(kseen[:, pts], alpha, mu, w)
+            big = np.max(np.abs(refs[key]))
+            assert big > 1e-3, (key, big, np.max(np.abs(kseen)), np.max(np.abs(out)))
+        rows[name] = errors(out[:, pts], refs[key])
+    if FULL:
+        comps = ["xx", "yy", "zz", "yz", "xz", "xy"]
+        for name, (mx, rms) in rows.items():
+            print(f"alpha={alpha} m={m} {name:10s} max " + " ".join(f"{c}={v:.2e}" for c, v in zip(comps, mx)) +
+                  " | rms " + " ".join(f"{v:.2e}" for v in rms))
+    assert np.all(rows["fp64"][0] < 1e-11)
+    assert np.all(rows["fp32+kahan"][0] < 2e-5)
