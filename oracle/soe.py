@@ -190,6 +190,13 @@ def soe_nnls(alpha: float, dt: float, T: float, m: int):
                 mu, w = _nnls_on_grid(alpha, dt, T, count, lo, hi)
                 if len(mu) != m:
                     continue
+                # a term whose decay is complete long before dt is invisible to
+                # the error on [dt, T] yet enters the scheme through its mass
+                # w_j / mu_j (the per-mode weight rho_j of the BDF2 update);
+                # NNLS sometimes gives such terms huge weights, so fits whose
+                # mass on [0, T] exceeds the kernel's are rejected
+                if soe_mass(mu, w, T) > 1.01 * kernel_mass(alpha, T):
+                    continue
                 err = max_rel_error(alpha, mu, w, dt, T)
                 if best is None or err < best[0]:
                     best = (err, mu, w)
@@ -201,6 +208,18 @@ def soe_nnls(alpha: float, dt: float, T: float, m: int):
 def soe_build(alpha: float, dt: float, T: float, m: int):
     """Default SOE used by the tests: ``soe_nnls``."""
     return soe_nnls(alpha, dt, T, m)
+
+
+def kernel_mass(alpha: float, T: float) -> float:
+    """Closed form of int_0^T t^-alpha / Gamma(1-alpha) dt = T^(1-alpha) / Gamma(2-alpha)."""
+    return T ** (1.0 - alpha) / math.gamma(2.0 - alpha)
+
+
+def soe_mass(mu, w, T: float) -> float:
+    """int_0^T sum_j w_j exp(-mu_j t) dt."""
+    mu = np.asarray(mu, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    return float(np.sum(w * -np.expm1(-mu * T) / mu))
 
 
 def max_rel_error(alpha: float, mu, w, dt: float, T: float, points: int = 400) -> float:

@@ -64,6 +64,13 @@ def build(alpha: float, dt: float, T: float, m: int):
                     continue
                 if len(mu) > m:
                     break
+                # NNLS may put a huge weight on an exponent so large that its
+                # term has died out before dt: the error on [dt, T] cannot see
+                # it, but the step sees its mass w/mu.  Keep only tables whose
+                # mass on [0, T] does not exceed the kernel's.
+                mass = float(np.sum(w * -np.expm1(-mu * T) / mu))
+                if mass > 1.01 * T ** (1.0 - alpha) / special.gamma(2.0 - alpha):
+                    continue
                 err = relative_error(alpha, mu, w, dt, T)
                 if best is None or err < best[0]:
                     best = (err, mu, w)

@@ -137,3 +137,27 @@ def test_cq_soe_weights():
     # first weight is eta = b0 sum_j w_j dt / (b0 + mu_j dt)
     eta = sum(1.5 * w * dt / (1.5 + m * dt) for m, w in [(3.0, 1.0), (40.0, 0.5)])
     assert abs(W[0] - eta) < 1e-16
+
+
+def test_kernel_mass_closed_form():
+    import scipy.integrate
+    for alpha in (0.2, 0.5, 0.9):
+        for T in (0.03, 1.0):
+            num, _ = scipy.integrate.quad(lambda t: t ** -alpha / scipy.special.gamma(1 - alpha), 0.0, T, limit=200)
+            assert abs(soe.kernel_mass(alpha, T) - num) < 1e-8 * num
+
+
+@pytest.mark.parametrize("alpha", [0.2, 0.3, 0.5, 0.9])
+@pytest.mark.parametrize("dt,T", [(2e-4, 0.1), (1e-3, 1.0), (5e-4, 0.5)])
+def test_soe_mass_bounded_by_kernel_mass(alpha, dt, T):
+    # Each mode enters the BDF2 step through its mass w_j / mu_j; a term that
+    # has decayed before dt cannot be seen by the error on [dt, T] but would
+    # swamp eta.  The tables must not carry more mass on [0, T] than the kernel
+    # (they carry a little less: the singular part below the fitted times).
+    # Both builders are checked: the oracle's and the library's (independent code).
+    from paper_2411_17294_gb300 import soe as psoe
+    for m in (16, 48):
+        for mu, w in (soe.soe_nnls(alpha, dt, T, m), psoe.build(alpha, dt, T, m)):
+            ratio = soe.soe_mass(mu, w, T) / soe.kernel_mass(alpha, T)
+            assert 0.5 < ratio <= 1.01, (alpha, m, ratio)
+            assert np.max(w / mu) < 1e3
