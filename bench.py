@@ -241,6 +241,22 @@ def cpu_baseline(steps_hint: int = 3, budget_s: float = 15.0):
                       f"FP64 C oracle with OpenMP", "seconds": el}
 
 
+def max_over_ranks(local_ms: float, dist, device) -> float:
+    """The slowest rank's time (all ranks get it); local_ms itself on one process."""
+    if dist is None:
+        return local_ms
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, t_max_ms: float) -> float:
+    """G units per second for the whole job: every rank processes units_per_rank
+    (weak scaling), the job takes as long as its slowest rank."""
+    return world * units_per_rank / (t_max_ms * 1e-3) / 1e9
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -358,18 +374,16 @@ def main():
             s.step(kap_n, kap_nm1, u, stream=stream)
         ev[1].record(stream)
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     s.set_step_events(None, None)
     clocks = sampler.stop()
     launch_ms = [kb[k].elapsed_time(ka[k]) for k in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[1])
     flags = s.status()
-    t_max = total_ms
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(total_ms, dist, dev)
     ms_per_step = t_max / args.steps
-    value = world * N * W["m"] * args.steps / (t_max * 1e-3) / 1e9
+    value = whole_job_rate(N * W["m"] * args.steps, world, t_max)
     avg_launch_s = statistics.mean(launch_ms) * 1e-3
     achieved = bytes_launch / avg_launch_s / 1e9
     peak, peak_kind = read_peaks()
@@ -403,14 +417,12 @@ def main():
                 h_sig.copy_(d_sig, non_blocking=True)
             e1.record(stream)
         torch.cuda.synchronize()
-        e2e_ms = e0.elapsed_time(e1)
         if dist is not None:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+            dist.barrier()
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
         bi = (h_kn.numel() + h_knm1.numel() + h_u.numel()) * elem
         bo = h_sig.numel() * elem
-        e2e = {"value": world * N * W["m"] * args.e2e_steps / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+        e2e = {"value": whole_job_rate(N * W["m"] * args.e2e_steps, world, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
 
     adj = None
