@@ -810,7 +810,7 @@ cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s
     if (TRANSPORT) {
         if (!a.trans) return cudaErrorInvalidValue;
         if (a.n0 % kTX == 0 && a.n1 % kTY == 0) {
-            const int zchunk = 32;
+            const int zchunk = 8;
             const int gz = DIM == 3 ? (a.n2 + zchunk - 1) / zchunk : 1;
             transport_tiled<T, DIM><<<dim3(a.n0 / kTX, a.n1 / kTY, gz), dim3(kTX, kTY), 0, s>>>(a, cfg.stencil,
                                                                                              zchunk);

@@ -79,3 +79,68 @@ def test_adjoint_matches_oracle(dim, n, alpha, m, steps, K, transport, eps, prec
         assert np.max(np.abs(got[key] - ref[key])) <= tol * scale, key
     for key in ("Wi", "beta"):
         assert abs(got[key] - ref[key]) <= tol * max(abs(ref[key]), 1e-12), key
+
+
+def test_adjoint_workload_512_against_central_differences():
+    # The adjoint workload at full size: 2D periodic 512^2, m = 32, alpha = 0.5,
+    # dt = 1e-3, 500 steps, checkpoint every 50, transport off, FP64;
+    # J = ||sigma(T) - sigma_target||^2 with the target from a seeded run at
+    # Wi = 1.5.  Gradients with respect to Wi, beta and sampled entries of
+    # sigma0 and grad_u against central differences of the CUDA forward, to
+    # 1e-6 relative.  J(x+h) - J(x-h) is summed as sum (s+ - s-)(s+ + s- - 2 t),
+    # which has no cancellation (the perturbed runs differ from each other only
+    # where the perturbation reaches).
+    import torch
+    from paper_2411_17294_gb300 import tfs
+    dim, n, alpha, m, dt, steps, K = 2, (512, 512), 0.5, 32, 1e-3, 500, 50
+    Wi, beta = 1.0, 0.5
+    N = n[0] * n[1]
+    mu, w = soe.soe_nnls(alpha, dt, steps * dt, m)
+    dev = torch.device("cuda", 0)
+    _, kap = inputs.spectral_velocity(dim, n, 32, 2)
+    kap = torch.as_tensor(0.05 * kap, device=dev)
+    sigma0 = torch.as_tensor(inputs.random_stress(dim, n, 5, amplitude=0.5), device=dev)
+
+    def run(Wi_, beta_, s0, k, grads_for=None):
+        s = tfs.Solver(dim, n, alpha, Wi_, beta_, dt, m=m, precision=tfs.TFS_FP64, mu=mu, w=w, transport=False)
+        s.set_state(s0)
+        ckpts = []
+        for i in range(steps):
+            if grads_for is not None and i % K == 0:
+                buf = s.new_checkpoint()
+                s.save(buf)
+                ckpts.append(buf)
+            s.step(k, k, None)
+        sT = s.stress()
+        out = sT
+        if grads_for is not None:
+            out = (sT, s.backward(2.0 * (sT - grads_for), ckpts, K, steps, k, None))
+        s.close()
+        return out
+
+    target = run(1.5, beta, sigma0, kap)
+    _, (g_s0, g_k, gWi, gbeta) = run(Wi, beta, sigma0, kap, grads_for=target)
+
+    def dJ(sp, sm):
+        return float(torch.sum((sp - sm) * (sp + sm - 2.0 * target)).item())
+
+    def close(a, b):
+        return abs(a - b) <= 1e-6 * max(abs(a), abs(b))
+
+    h = 1e-5
+    fd_Wi = dJ(run(Wi + h, beta, sigma0, kap), run(Wi - h, beta, sigma0, kap)) / (2 * h)
+    fd_beta = dJ(run(Wi, beta + h, sigma0, kap), run(Wi, beta - h, sigma0, kap)) / (2 * h)
+    assert close(gWi, fd_Wi), (gWi, fd_Wi)
+    assert close(gbeta, fd_beta), (gbeta, fd_beta)
+    for (c, q) in [(0, 1234), (2, N - 77)]:
+        sp, sm = sigma0.clone(), sigma0.clone()
+        sp[c, q] += h
+        sm[c, q] -= h
+        fd = dJ(run(Wi, beta, sp, kap), run(Wi, beta, sm, kap)) / (2 * h)
+        assert close(g_s0[c, q].item(), fd), (c, q, g_s0[c, q].item(), fd)
+    for (c, q) in [(1, 4321), (3, 99999)]:
+        kp, km = kap.clone(), kap.clone()
+        kp[c, q] += h
+        km[c, q] -= h
+        fd = dJ(run(Wi, beta, sigma0, kp), run(Wi, beta, sigma0, km)) / (2 * h)
+        assert close(g_k[c, q].item(), fd), (c, q, g_k[c, q].item(), fd)
