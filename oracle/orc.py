@@ -64,6 +64,8 @@ def _load():
         lib.orc_step.restype = ctypes.c_int
         lib.orc_step.argtypes = [ctypes.POINTER(_Params), dp, dp, ctypes.c_long,
                                  dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
+        lib.orc_step_implicit.restype = ctypes.c_int
+        lib.orc_step_implicit.argtypes = lib.orc_step.argtypes
         lib.orc_adjoint_step.restype = ctypes.c_int
         lib.orc_adjoint_step.argtypes = [ctypes.POINTER(_Params), dp, dp, ctypes.c_long,
                                          dp, dp, dp, dp, dp,
@@ -98,6 +100,7 @@ class Problem:
     stencil: int = 0            # 0 upwind3 (radius 2), 1 central2 (radius 1)
     transport: bool = False
     full: bool = False          # store the full d x d tensor instead of packed
+    implicit: bool = False      # transport at t_{n+1} inside a global solve (small grids)
 
     @property
     def N(self) -> int:
@@ -167,7 +170,8 @@ class Oracle:
             u = None
         sig_np1 = np.empty_like(self.sig_n)
         modes_np1 = np.zeros_like(self.modes_n)
-        fails = _load().orc_step(ctypes.byref(self._p), _ptr(self.mu), _ptr(self.w), self.n,
+        fn = _load().orc_step_implicit if prob.implicit else _load().orc_step
+        fails = fn(ctypes.byref(self._p), _ptr(self.mu), _ptr(self.w), self.n,
                                  _ptr(self.sig_n), _ptr(self.sig_nm1), _ptr(self.modes_n), _ptr(self.modes_nm1),
                                  _ptr(self.sigma0), _ptr(kap_n), _ptr(kap_nm1), _ptr(u),
                                  _ptr(sig_np1), _ptr(modes_np1))

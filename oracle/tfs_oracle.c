@@ -315,6 +315,123 @@ int orc_step(const orc_params* p, const double* mu, const double* w, long step_i
 }
 
 /*
+ * One step with the transport treated implicitly (the form in which the paper's
+ * scheme, eq. FP_discrete, carries u.grad and eps Lap: at t_{n+1}, inside the
+ * solve).  The per-point relation becomes a coupled system over the grid:
+ *
+ *   (eta + dt/Wi) sigma_p - dt (kappa*_p sigma_p + sigma_p kappa*_p^T)
+ *     + dt [ sum_a u_a(p) D_a(sigma) - eps Lap(sigma) ]_p  =  R_p,
+ *   R_p = eta sigma0_p - H_p + dt G (kappa*_p + kappa*_p^T) g_alpha(t_{n+1}),
+ *
+ * with the same stencils as the explicit form (D_a upwinded on the sign of
+ * u_a at p), acting on each stress component.  The global matrix (nc N)^2 is
+ * assembled column by column by applying the operator to unit fields and solved
+ * by Gaussian elimination with partial pivoting: small grids only.  The modes
+ * are then pushed forward exactly as in orc_step.  Returns 1 if the system was
+ * singular.
+ */
+int orc_step_implicit(const orc_params* p, const double* mu, const double* w, long step_index,
+                      const double* sig_n, const double* sig_nm1,
+                      const double* modes_n, const double* modes_nm1,
+                      const double* sigma0,
+                      const double* kap_n, const double* kap_nm1, const double* u,
+                      double* sig_np1, double* modes_np1) {
+    const int d = p->dim, nc = ncomp(p);
+    const long N = npoints(p);
+    const long n = (long)nc * N;
+    const int classic = (p->alpha == 1.0);
+    const int m = classic ? 0 : p->m;
+    step_scalars s = scalars(p, mu, w, step_index);
+
+    double* G = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+    double* rhs = (double*)malloc(sizeof(double) * (size_t)n);
+    double* unit = (double*)calloc((size_t)N, sizeof(double));
+    if (!G || !rhs || !unit) { free(G); free(rhs); free(unit); return 1; }
+
+    /* columns: unknown k = (component ck, point pk) */
+    for (long k = 0; k < n; ++k) {
+        const int ck = (int)(k / N);
+        const long pk = k % N;
+        for (long r = 0; r < n; ++r) G[r * n + k] = 0.0;
+        /* local part at point pk: the block a I - dt L(kappa*_pk) applied to e_ck */
+        {
+            double K[3][3] = {{0}};
+            for (int i = 0; i < d; ++i)
+                for (int j = 0; j < d; ++j) {
+                    long q = (long)(i * d + j) * N + pk;
+                    K[i][j] = 2.0 * kap_n[q] - kap_nm1[q];
+                }
+            double e[9], img[9];
+            for (int c = 0; c < nc; ++c) e[c] = (c == ck) ? 1.0 : 0.0;
+            upper_convected(p, K, e, img);
+            for (int c = 0; c < nc; ++c) G[((long)c * N + pk) * n + k] += s.a * e[c] - p->dt * img[c];
+        }
+        /* transport part: component ck of the unit field is 1 at pk; its image
+           is nonzero at the points whose stencils reach pk */
+        if (p->transport) {
+            unit[pk] = 1.0;
+            for (long pt = 0; pt < N; ++pt) {
+                long x = pt % p->n[0];
+                long y = (pt / p->n[0]) % p->n[1];
+                long z = (d == 3) ? pt / ((long)p->n[0] * p->n[1]) : 0;
+                double t = 0.0;
+                for (int a = 0; a < d; ++a) {
+                    double va = u[(long)a * N + pt];
+                    t += va * deriv(p, unit, a, x, y, z, va);
+                }
+                if (p->eps != 0.0) t -= p->eps * laplace(p, unit, x, y, z);
+                if (t != 0.0) G[((long)ck * N + pt) * n + k] += p->dt * t;
+            }
+            unit[pk] = 0.0;
+        }
+    }
+
+    for (long pt = 0; pt < N; ++pt) {
+        double K[3][3] = {{0}};
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) {
+                long q = (long)(i * d + j) * N + pt;
+                K[i][j] = 2.0 * kap_n[q] - kap_nm1[q];
+            }
+        double KS[3][3], sym[9];
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) KS[i][j] = K[i][j] + K[j][i];
+        from_matrix(p, KS, sym);
+        for (int c = 0; c < nc; ++c) {
+            double H;
+            if (classic) {
+                H = B1 * sig_n[(long)c * N + pt] + B2 * sig_nm1[(long)c * N + pt] + B0 * sigma0[(long)c * N + pt];
+            } else {
+                H = 0.0;
+                for (int j = 0; j < m; ++j) {
+                    double cj = 1.0 / (B0 + mu[j] * p->dt);
+                    double etaj = mu[j] * p->dt * cj;
+                    long q = ((long)j * nc + c) * N + pt;
+                    H += etaj * (B1 * modes_n[q] + B2 * modes_nm1[q]);
+                }
+            }
+            rhs[(long)c * N + pt] = s.eta * sigma0[(long)c * N + pt] - H + p->dt * s.G * sym[c] * s.g;
+        }
+    }
+    int failed = gauss_solve((int)n, G, rhs);
+    for (long q = 0; q < n; ++q) sig_np1[q] = rhs[q];
+
+    for (long pt = 0; pt < N; ++pt)
+        for (int j = 0; j < m; ++j) {
+            double cj = 1.0 / (B0 + mu[j] * p->dt);
+            double rhoj = w[j] * p->dt * cj;
+            for (int c = 0; c < nc; ++c) {
+                long q = ((long)j * nc + c) * N + pt;
+                modes_np1[q] = cj * (-B1 * modes_n[q] - B2 * modes_nm1[q]) + rhoj * (rhs[(long)c * N + pt] - sigma0[(long)c * N + pt]);
+            }
+        }
+    free(G);
+    free(rhs);
+    free(unit);
+    return failed;
+}
+
+/*
  * Reference adjoint (reverse-mode derivative) of orc_step, for packed storage.
  *
  * The step maps (sigma^n, sigma^{n-1}, modes^n, modes^{n-1}) to
