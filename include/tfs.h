@@ -80,8 +80,16 @@ enum {
     TFS_PARAM_RE = 0,         /* Reynolds number, default 1 */
     TFS_PARAM_EPS = 1,        /* centre-of-mass diffusion eps >= 0, default 0 */
     TFS_PARAM_STENCIL = 2,    /* TFS_STENCIL_*, default upwind3 */
-    TFS_PARAM_TRANSPORT = 3,  /* 0: pointwise law (u ignored); 1: transport on (default 1) */
-    TFS_PARAM_UMAX = 4        /* declared bound U on |u_a|; checked against tfs_transport_limit */
+    TFS_PARAM_TRANSPORT = 3,  /* 0: pointwise law (u ignored); 1: explicit transport (default);
+                                 2: implicit transport -- u.grad and eps Lap at t_{n+1} inside a global
+                                 solve, the form of the paper's eq. FP_discrete: BiCGStab with a
+                                 block-Jacobi preconditioner on FP64 Krylov vectors, no Courant limit;
+                                 the workspace grows by 10 nc N doubles; tfs_step then synchronises its
+                                 stream; tfs_backward refuses it (TFS_ERR_ARG) */
+    TFS_PARAM_UMAX = 4,       /* declared bound U on |u_a|; checked against tfs_transport_limit */
+    TFS_PARAM_KRYLOV_TOL = 5, /* implicit transport: relative residual target, default 1e-13 (FP64)
+                                 or 1e-9 (FP32 storage) */
+    TFS_PARAM_KRYLOV_MAXIT = 6 /* implicit transport: iteration limit, default 500 */
 };
 
 enum { TFS_STENCIL_UPWIND3 = 0, TFS_STENCIL_CENTRAL2 = 1 };
@@ -91,8 +99,10 @@ enum {
     TFS_FLAG_NONFINITE = 1u,  /* a new stress value was NaN or Inf */
     TFS_FLAG_SINGULAR = 2u,   /* a point system had a pivot below 1e-300 / relative 1e-14 */
     TFS_FLAG_COURANT = 4u,    /* a point had dt sum_a |u_a|/h_a above the limit of tfs_transport_limit */
-    TFS_FLAG_TIMEOUT = 8u     /* a kernel gave up waiting for its own tile copies (bounded wait; the
+    TFS_FLAG_TIMEOUT = 8u,    /* a kernel gave up waiting for its own tile copies (bounded wait; the
                                  step's output is then incomplete) */
+    TFS_FLAG_NOCONV = 16u     /* an implicit-transport solve stopped above its tolerance (the best
+                                 iterate was kept) */
 };
 
 typedef struct {
@@ -161,6 +171,11 @@ int tfs_set_step_events(tfs_handle h, void* ev_before, void* ev_after);
 
 /* Current step index n (number of completed steps since tfs_set_state). */
 long tfs_step_index(tfs_handle h);
+
+/* Iterations and final relative residual |b - Op x| / |b| of the last
+   implicit-transport solve (TFS_PARAM_TRANSPORT = 2); either pointer may be
+   NULL.  Host-side, no synchronisation. */
+int tfs_last_solve(tfs_handle h, int* iterations, double* relative_residual);
 
 /* Checkpoints: a device buffer holding the full state (header, stress at
    levels n and n-1, modes at levels n and n-1). */

@@ -65,6 +65,13 @@ struct tfs_ctx {
     bool lim_valid = false;
     double lam_star = 0.0;   // advection: largest stable dt |u| / h (1D)
     double z_star = 0.0;     // diffusion: largest stable 4 eps dt / h^2 (1D)
+    // implicit transport: Krylov workspace after the modes, solver controls, last solve
+    double* kry = nullptr;
+    double* partials = nullptr;
+    double krylov_tol = -1.0;      // < 0: default for the precision
+    int krylov_maxit = 500;
+    int last_iters = 0;
+    double last_relres = 0.0;
     // adjoint workspace
     char* aws = nullptr;
     size_t aws_bytes = 0;
@@ -76,6 +83,8 @@ struct tfs_ctx {
     size_t field_bytes() const { return (size_t)nc * (size_t)N * es(); }
     size_t modes_bytes() const { return (size_t)m * field_bytes(); }
     int third_sig() const { return 3 - cur_sig - prev_sig; }
+    bool explicit_transport() const { return transport == 1; }
+    bool implicit_transport() const { return transport == 2; }
 };
 
 namespace {
@@ -223,11 +232,14 @@ double courant_limit(tfs_ctx* h) {
 
 // declared bounds (eps, and umax when given) exceed the limit
 bool limits_violated(tfs_ctx* h) {
-    if (!h->transport || !limits_known(h)) return false;
+    if (!h->explicit_transport() || !limits_known(h)) return false;
     const double lim = courant_limit(h);
     if (lim < 0.0) return true;
     return h->umax >= 0.0 && courant_coef(h) * h->umax * sum_inv_h(h) > lim;
 }
+
+size_t krylov_vector_bytes(const tfs_ctx* h) { return (size_t)h->nc * (size_t)h->N * sizeof(double); }
+size_t forward_bytes_for(const tfs_ctx* h, int transport);
 
 void layout_forward(tfs_ctx* h, char* base) {
     char* p = base;
@@ -245,11 +257,22 @@ void layout_forward(tfs_ctx* h, char* base) {
         h->modes[i] = p;
         p += align_up(h->modes_bytes());
     }
+    h->kry = nullptr;
+    h->partials = nullptr;
+    if (h->implicit_transport()) {
+        h->kry = (double*)p;
+        p += align_up(10 * krylov_vector_bytes(h));
+        h->partials = (double*)p;
+    }
 }
 
-size_t forward_bytes(const tfs_ctx* h) {
-    return kAlign + 5 * align_up(h->field_bytes()) + 2 * align_up(h->modes_bytes());
+size_t forward_bytes_for(const tfs_ctx* h, int transport) {
+    size_t b = kAlign + 5 * align_up(h->field_bytes()) + 2 * align_up(h->modes_bytes());
+    if (transport == 2) b += align_up(10 * krylov_vector_bytes(h)) + align_up(sizeof(double) * kImpBlocks);
+    return b;
 }
+
+size_t forward_bytes(const tfs_ctx* h) { return forward_bytes_for(h, h->transport); }
 
 F2c split_f2(double v) {
     F2c r;
@@ -271,7 +294,7 @@ void fill_common(tfs_ctx* h, FwdArgs<T>& a) {
     a.G = (1.0 - h->beta) / (h->Wi * h->Re);
     a.eps = h->eps;
     for (int i = 0; i < 3; ++i) a.inv_h[i] = (double)h->n[i] / h->L[i];
-    a.courant_coef = (h->transport && limits_known(h)) ? courant_coef(h) : 0.0;
+    a.courant_coef = (h->explicit_transport() && limits_known(h)) ? courant_coef(h) : 0.0;
     a.courant_limit = courant_limit(h);
     a.flags = h->flags;
     a.eta_f2 = split_f2(a.eta);
@@ -292,6 +315,74 @@ LaunchCfg make_cfg(const tfs_ctx* h) {
 }
 
 // One forward step; sig_copy optionally receives sigma^{n+1} as well.
+template <typename T>
+void fill_implicit(tfs_ctx* h, ImpArgs<T>& a, const void* kn, const void* knm1, const void* u, void* sig_copy,
+                   int nxt, int cm, int pm) {
+    a.kap_n = (const T*)kn;
+    a.kap_nm1 = (const T*)knm1;
+    a.u = (const T*)u;
+    a.sigma0 = h->sigma0_zero ? nullptr : (const T*)h->sigma0;
+    a.sig_n = (const T*)h->sig[h->cur_sig];
+    a.sig_nm1 = (const T*)h->sig[h->prev_sig];
+    a.sig_np1 = (T*)h->sig[nxt];
+    a.sig_copy = (T*)sig_copy;
+    a.modes_n = (const T*)h->modes[cm];
+    a.modes_nm1 = (T*)h->modes[pm];
+    a.flags = h->flags;
+    a.N = h->N;
+    a.dim = h->dim;
+    a.n0 = (int)h->n[0];
+    a.n1 = (int)h->n[1];
+    a.n2 = (int)h->n[2];
+    a.m = h->classic() ? 0 : h->m;
+    a.stencil = h->stencil;
+    a.classic = h->classic() ? 1 : 0;
+    a.dt = h->dt;
+    a.eta = h->classic() ? kB0 : h->eta;
+    a.a = a.eta + h->dt / h->Wi;
+    a.G = (1.0 - h->beta) / (h->Wi * h->Re);
+    a.g = g_alpha(h, h->step);
+    a.eps = h->eps;
+    for (int i = 0; i < 3; ++i) a.inv_h[i] = (double)h->n[i] / h->L[i];
+    a.mcd = h->mcd;
+    a.eta_f2 = split_f2(a.eta);
+    a.src_f2 = split_f2(a.dt * a.G * a.g);
+    a.kry = h->kry;
+    a.partials = h->partials;
+    a.tol = h->krylov_tol > 0.0 ? h->krylov_tol : (h->is_double() ? 1e-13 : 1e-9);
+    a.maxit = h->krylov_maxit;
+}
+
+// One step with implicit transport (tfs_implicit.cu); synchronises the stream.
+int do_step_implicit(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* sig_copy, cudaStream_t s) {
+    if (!h->kry || h->ws_bytes < forward_bytes(h)) return TFS_ERR_NOWORKSPACE;
+    const int nxt = h->third_sig();
+    const int cm = h->cur_mode, pm = 1 - h->cur_mode;
+    int iters = 0;
+    double relres = 0.0;
+    cudaError_t e;
+    if (h->is_double()) {
+        ImpArgs<double> a{};
+        fill_implicit(h, a, kn, knm1, u, sig_copy, nxt, cm, pm);
+        a.mc = h->mcd;
+        e = run_implicit_f64(a, s, &iters, &relres);
+    } else {
+        ImpArgs<float> a{};
+        fill_implicit(h, a, kn, knm1, u, sig_copy, nxt, cm, pm);
+        a.mc = h->mcf;
+        e = run_implicit_f32(a, s, h->precision == TFS_FP32, &iters, &relres);
+    }
+    if (e != cudaSuccess) return TFS_ERR_CUDA;
+    h->last_iters = iters;
+    h->last_relres = relres;
+    h->prev_sig = h->cur_sig;
+    h->cur_sig = nxt;
+    if (!h->classic()) h->cur_mode = pm;
+    h->step += 1;
+    h->last_stream = s;
+    return TFS_OK;
+}
+
 int do_step(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* sig_copy, cudaStream_t s) {
     if (!h->ws) return TFS_ERR_NOWORKSPACE;
     if (!h->state_set) return TFS_ERR_STATE;
@@ -300,6 +391,7 @@ int do_step(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* s
     if (h->transport && !u) return TFS_ERR_ARG;
     if (limits_violated(h)) return TFS_ERR_UNSTABLE;
     if (!knm1) knm1 = kn;
+    if (h->implicit_transport()) return do_step_implicit(h, kn, knm1, u, sig_copy, s);
     const int nxt = h->third_sig();
     const int cm = h->cur_mode, pm = 1 - h->cur_mode;
     cudaError_t e;
@@ -403,7 +495,7 @@ int tfs_set_param(tfs_handle h, int key, double value) {
             return TFS_OK;
         case TFS_PARAM_EPS:
             if (!(value >= 0.0)) return TFS_ERR_ARG;
-            if (h->transport && diffusion_fraction(h, value) > 0.9) return TFS_ERR_UNSTABLE;
+            if (h->explicit_transport() && diffusion_fraction(h, value) > 0.9) return TFS_ERR_UNSTABLE;
             h->eps = value;
             return TFS_OK;
         case TFS_PARAM_STENCIL:
@@ -412,16 +504,26 @@ int tfs_set_param(tfs_handle h, int key, double value) {
             h->lim_valid = false;
             return TFS_OK;
         case TFS_PARAM_TRANSPORT:
-            if (value != 0.0 && value != 1.0) return TFS_ERR_ARG;
+            if (value != 0.0 && value != 1.0 && value != 2.0) return TFS_ERR_ARG;
+            if (value == 2.0 && h->ws && h->ws_bytes < forward_bytes_for(h, 2)) return TFS_ERR_NOWORKSPACE;
             h->transport = (int)value;
+            if (h->ws) layout_forward(h, h->ws);
             return TFS_OK;
         case TFS_PARAM_UMAX: {
             if (!(value >= 0.0)) return TFS_ERR_ARG;
-            if (h->transport && limits_known(h) && courant_coef(h) * value * sum_inv_h(h) > courant_limit(h))
+            if (h->explicit_transport() && limits_known(h) && courant_coef(h) * value * sum_inv_h(h) > courant_limit(h))
                 return TFS_ERR_UNSTABLE;
             h->umax = value;
             return TFS_OK;
         }
+        case TFS_PARAM_KRYLOV_TOL:
+            if (!(value > 0.0 && value < 1.0)) return TFS_ERR_ARG;
+            h->krylov_tol = value;
+            return TFS_OK;
+        case TFS_PARAM_KRYLOV_MAXIT:
+            if (!(value >= 1.0 && value <= 100000.0) || value != std::floor(value)) return TFS_ERR_ARG;
+            h->krylov_maxit = (int)value;
+            return TFS_OK;
         default:
             return TFS_ERR_ARG;
     }
@@ -526,6 +628,13 @@ int tfs_get_stress(tfs_handle h, void* out, void* stream) {
 }
 
 long tfs_step_index(tfs_handle h) { return valid_handle(h) ? (long)h->step : -1; }
+
+int tfs_last_solve(tfs_handle h, int* iterations, double* relative_residual) {
+    if (!valid_handle(h)) return TFS_ERR_ARG;
+    if (iterations) *iterations = h->last_iters;
+    if (relative_residual) *relative_residual = h->last_relres;
+    return TFS_OK;
+}
 
 size_t tfs_checkpoint_bytes(tfs_handle h) {
     if (!valid_handle(h)) return 0;
@@ -668,6 +777,7 @@ int tfs_bind_adjoint_workspace(tfs_handle h, void* dev_ptr, size_t bytes) {
 int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* checkpoints, int K, int steps,
                  const void* grad_u, const void* u, double* dJ_dsigma0, double* dJ_dgrad_u, double* dJ_dWi,
                  double* dJ_dbeta, void* stream) {
+    if (valid_handle(h) && h->implicit_transport()) return TFS_ERR_ARG;   // adjoint of the implicit step not built
     if (!valid_handle(h) || !dJ_dsigma_T || !checkpoints || !grad_u || !dJ_dsigma0 || !dJ_dgrad_u || !dJ_dWi ||
         !dJ_dbeta)
         return TFS_ERR_ARG;

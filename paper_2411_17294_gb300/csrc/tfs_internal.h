@@ -86,6 +86,39 @@ struct PersistPlan {
 cudaError_t persistent_plan(const void* kern, int threads, size_t stage_bytes, size_t static_bytes, int max_stages,
                             PersistPlan* out);
 
+// Arguments of one step with implicit transport (tfs_implicit.cu).
+template <typename T>
+struct ImpArgs {
+    const T* kap_n;
+    const T* kap_nm1;
+    const T* u;            // [d][N]
+    const T* sigma0;       // [nc][N] or nullptr for zero
+    const T* sig_n;
+    const T* sig_nm1;
+    T* sig_np1;
+    T* sig_copy;           // optional second destination of sigma^{n+1}
+    const T* modes_n;      // [m][nc][N]
+    T* modes_nm1;          // level n-1 in; Q_j after the right-hand side; level n+1 out
+    unsigned* flags;
+    long long N;
+    int dim, n0, n1, n2, m, stencil, classic;
+    double dt, eta, a, G, g, eps;
+    double inv_h[3];
+    typename ModeConsts<T>::type mc;
+    ModeConstsD mcd;
+    F2c eta_f2, src_f2;
+    double* kry;           // 10 vectors of nc N doubles (Krylov workspace)
+    double* partials;      // reduction scratch, kImpBlocks doubles
+    double tol;            // relative residual target
+    int maxit;
+};
+constexpr int kImpBlocks = 1024;   // blocks of the implicit-step kernels (and reduction partials)
+
+// host driver of one implicit step (BiCGStab, block-Jacobi preconditioned);
+// synchronises `s`; returns the iterations used and the final relative residual
+cudaError_t run_implicit_f64(const ImpArgs<double>& a, cudaStream_t s, int* iters, double* relres);
+cudaError_t run_implicit_f32(const ImpArgs<float>& a, cudaStream_t s, bool compensated, int* iters, double* relres);
+
 struct LaunchCfg {
     int dim;
     int stencil;       // 0 upwind3, 1 central2

@@ -19,13 +19,14 @@ LIB_PATH = os.path.join(_HERE, "_build", "libtfs.so")
 TFS_OK, TFS_ERR_ARG, TFS_ERR_NOSOE, TFS_ERR_UNSTABLE, TFS_ERR_CUDA, TFS_ERR_STATE, TFS_ERR_NOWORKSPACE, \
     TFS_ERR_FORMAT, TFS_ERR_TOOBIG = range(9)
 TFS_FP64, TFS_FP32, TFS_FP32_PLAIN = 0, 1, 2
-TFS_PARAM_RE, TFS_PARAM_EPS, TFS_PARAM_STENCIL, TFS_PARAM_TRANSPORT, TFS_PARAM_UMAX = range(5)
+(TFS_PARAM_RE, TFS_PARAM_EPS, TFS_PARAM_STENCIL, TFS_PARAM_TRANSPORT, TFS_PARAM_UMAX, TFS_PARAM_KRYLOV_TOL,
+ TFS_PARAM_KRYLOV_MAXIT) = range(7)
 TFS_STENCIL_UPWIND3, TFS_STENCIL_CENTRAL2 = 0, 1
-TFS_FLAG_NONFINITE, TFS_FLAG_SINGULAR, TFS_FLAG_COURANT, TFS_FLAG_TIMEOUT = 1, 2, 4, 8
+TFS_FLAG_NONFINITE, TFS_FLAG_SINGULAR, TFS_FLAG_COURANT, TFS_FLAG_TIMEOUT, TFS_FLAG_NOCONV = 1, 2, 4, 8, 16
 
 EXPORTS = [
     "tfs_create", "tfs_set_param", "tfs_set_soe", "tfs_transport_limit", "tfs_workspace_bytes", "tfs_bind_workspace",
-    "tfs_set_state", "tfs_step", "tfs_get_stress", "tfs_set_step_events", "tfs_step_index", "tfs_checkpoint_bytes", "tfs_save",
+    "tfs_set_state", "tfs_step", "tfs_get_stress", "tfs_set_step_events", "tfs_step_index", "tfs_last_solve", "tfs_checkpoint_bytes", "tfs_save",
     "tfs_load", "tfs_adjoint_workspace_bytes", "tfs_bind_adjoint_workspace", "tfs_backward", "tfs_status",
     "tfs_strerror", "tfs_destroy", "tfs_run_static",
 ]
@@ -68,6 +69,7 @@ def load_library(path: str | None = None):
         "tfs_get_stress": (ctypes.c_int, [H, vp, vp]),
         "tfs_set_step_events": (ctypes.c_int, [H, vp, vp]),
         "tfs_step_index": (ctypes.c_long, [H]),
+        "tfs_last_solve": (ctypes.c_int, [H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
         "tfs_checkpoint_bytes": (sz, [H]),
         "tfs_save": (ctypes.c_int, [H, vp, vp]),
         "tfs_load": (ctypes.c_int, [H, vp, vp]),
@@ -125,7 +127,7 @@ class Solver:
 
     def __init__(self, dim: int, n, alpha: float, Wi: float, beta: float, dt: float, m: int = 0,
                  precision: int = TFS_FP64, L=None, mu=None, w=None, Re: float = 1.0, eps: float = 0.0,
-                 stencil: int = TFS_STENCIL_UPWIND3, transport: bool = True, device=None):
+                 stencil: int = TFS_STENCIL_UPWIND3, transport=True, device=None):
         torch = _torch()
         lib = load_library()
         self.lib = lib
@@ -147,11 +149,14 @@ class Solver:
                              float(dt), int(precision)), "tfs_create")
         self.h = h
         self.m = m
+        # transport: False (pointwise), True (explicit) or "implicit"
+        self.implicit = transport == "implicit"
         self.transport = bool(transport)
         check(lib.tfs_set_param(h, TFS_PARAM_RE, float(Re)), "tfs_set_param(Re)")
         check(lib.tfs_set_param(h, TFS_PARAM_EPS, float(eps)), "tfs_set_param(eps)")
         check(lib.tfs_set_param(h, TFS_PARAM_STENCIL, float(stencil)), "tfs_set_param(stencil)")
-        check(lib.tfs_set_param(h, TFS_PARAM_TRANSPORT, 1.0 if transport else 0.0), "tfs_set_param(transport)")
+        check(lib.tfs_set_param(h, TFS_PARAM_TRANSPORT, 2.0 if self.implicit else (1.0 if transport else 0.0)),
+              "tfs_set_param(transport)")
         if mu is not None:
             self.set_soe(mu, w)
         nbytes = lib.tfs_workspace_bytes(h)
@@ -219,6 +224,20 @@ class Solver:
         b = ctypes.c_void_p(handle(ev_before))
         a = ctypes.c_void_p(handle(ev_after))
         check(self.lib.tfs_set_step_events(self.h, b, a), "tfs_set_step_events")
+
+    def last_solve(self):
+        """(iterations, relative residual) of the last implicit-transport solve."""
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        check(self.lib.tfs_last_solve(self.h, ctypes.byref(it), ctypes.byref(rr)), "tfs_last_solve")
+        return it.value, rr.value
+
+    def set_krylov(self, tol=None, maxit=None):
+        """Implicit transport: relative residual target and iteration limit."""
+        if tol is not None:
+            check(self.lib.tfs_set_param(self.h, TFS_PARAM_KRYLOV_TOL, float(tol)), "tfs_set_param(tol)")
+        if maxit is not None:
+            check(self.lib.tfs_set_param(self.h, TFS_PARAM_KRYLOV_MAXIT, float(maxit)), "tfs_set_param(maxit)")
 
     def step_index(self) -> int:
         return int(self.lib.tfs_step_index(self.h))

@@ -1,0 +1,114 @@
+"""Implicit transport (TFS_PARAM_TRANSPORT = 2) through the C ABI against the
+oracle's dense global solve, in the regime where the explicit transport is
+unstable (velocity several times the explicit limit).
+
+Tolerances: FP64 1e-10 per component (the Krylov solve stops at a relative
+residual of 1e-13; the block-Jacobi-preconditioned systems here have
+condition numbers below ~100, so the solution error stays below 1e-11 per
+step and accumulates over the steps); FP32 storage 2e-5 as for the default
+step (Krylov tolerance 1e-9, far below the FP32 rounding of the stored
+fields).
+"""
+import numpy as np
+import pytest
+
+from helpers import courant_fraction, ensure_lib, rel_err_per_component
+from oracle import orc, soe
+from paper_2411_17294_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ensure_lib()
+
+
+def gpu_run(case, sigma0, kap, u, steps, precision):
+    import torch
+    from paper_2411_17294_gb300 import tfs
+    s = tfs.Solver(case["dim"], case["n"], case["alpha"], case["Wi"], case["beta"], case["dt"],
+                   m=len(case["mu"]) if case["alpha"] < 1 else 0, precision=precision,
+                   mu=case["mu"] if case["alpha"] < 1 else None, w=case["w"] if case["alpha"] < 1 else None,
+                   eps=case["eps"], stencil=case["stencil"], transport="implicit")
+    dt_ = s.dtype
+    s.set_state(torch.as_tensor(sigma0, dtype=dt_, device=s.device))
+    kt = torch.as_tensor(kap, dtype=dt_, device=s.device).contiguous()
+    ut = torch.as_tensor(u, dtype=dt_, device=s.device).contiguous()
+    iters = []
+    for _ in range(steps):
+        s.step(kt, kt, ut)
+        iters.append(s.last_solve())
+    out = s.stress().double().cpu().numpy()
+    flags = s.status()
+    s.close()
+    return out, iters, flags
+
+
+CASES = [
+    # dim, n, alpha, m, eps, stencil, speed (times the explicit limit)
+    (2, (16, 12), 0.5, 8, 0.0, 0, 4.0),
+    (2, (12, 10), 1.0, 0, 0.02, 0, 3.0),
+    (3, (6, 5, 4), 0.6, 6, 0.0, 1, 3.0),
+    (3, (5, 4, 6), 0.35, 8, 0.01, 0, 5.0),
+]
+
+
+@pytest.mark.parametrize("dim,n,alpha,m,eps,stencil,speed", CASES)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_implicit_matches_oracle(dim, n, alpha, m, eps, stencil, speed, precision):
+    from paper_2411_17294_gb300 import tfs
+    steps, dt, Wi, beta = 10, 2e-3, 1.3, 0.4
+    mu, w = soe.soe_nnls(alpha, dt, steps * dt, m) if alpha < 1 else (np.zeros(0), np.zeros(0))
+    case = dict(dim=dim, n=n, alpha=alpha, Wi=Wi, beta=beta, dt=dt, mu=mu, w=w, eps=eps, stencil=stencil)
+    u, kap = inputs.spectral_velocity(dim, n, 2, seed=17)
+    u = np.asarray(u) * (speed / courant_fraction(dict(case, transport=True), u))
+    assert courant_fraction(dict(case, transport=True), u) > 2.0     # explicit step would be unstable
+    sigma0 = inputs.random_stress(dim, n, 18)
+    if precision == 1:
+        kap, u, sigma0 = (np.asarray(a, np.float32).astype(np.float64) for a in (kap, u, sigma0))
+    prob = orc.Problem(dim=dim, n=n, alpha=alpha, Wi=Wi, beta=beta, dt=dt, mu=mu, w=w, eps=eps, stencil=stencil,
+                       transport=True, implicit=True)
+    ref = orc.forward(prob, sigma0, kap, u, steps)
+    got, iters, flags = gpu_run(case, sigma0, kap, u, steps, precision)
+    assert not (flags & (tfs.TFS_FLAG_NOCONV | tfs.TFS_FLAG_NONFINITE))
+    assert all(0 < it < 200 for it, _ in iters)
+    assert np.all(rel_err_per_component(got, ref) < (1e-10 if precision == 0 else 2e-5))
+
+
+def test_implicit_without_velocity_equals_explicit_step():
+    import torch
+    from paper_2411_17294_gb300 import tfs
+    dim, n, alpha, m, dt, steps = 3, (8, 6, 5), 0.5, 8, 2e-3, 6
+    mu, w = soe.soe_nnls(alpha, dt, steps * dt, m)
+    _, kap = inputs.spectral_velocity(dim, n, 2, seed=21)
+    sigma0 = inputs.random_stress(dim, n, 22)
+    outs = []
+    for mode in ("implicit", True):
+        s = tfs.Solver(dim, n, alpha, 1.1, 0.3, dt, m=m, precision=tfs.TFS_FP64, mu=mu, w=w, transport=mode)
+        s.set_state(torch.as_tensor(sigma0, device=s.device))
+        kt = torch.as_tensor(kap, device=s.device).contiguous()
+        zu = torch.zeros((dim, int(np.prod(n))), dtype=torch.float64, device=s.device)
+        for _ in range(steps):
+            s.step(kt, kt, zu)
+        outs.append(s.stress().cpu().numpy())
+        s.close()
+    assert np.all(rel_err_per_component(outs[0], outs[1]) < 1e-12)
+
+
+def test_implicit_refuses_adjoint_and_reports_its_solve():
+    import torch
+    from paper_2411_17294_gb300 import tfs
+    dim, n, dt = 2, (8, 8), 1e-2
+    s = tfs.Solver(dim, n, 1.0, 1.0, 0.5, dt, m=0, precision=tfs.TFS_FP64, transport="implicit")
+    s.set_state(torch.ones((3, 64), dtype=torch.float64, device=s.device))
+    k = torch.zeros((4, 64), dtype=torch.float64, device=s.device)
+    u = torch.full((2, 64), 3.0, dtype=torch.float64, device=s.device)
+    ck = s.new_checkpoint()
+    s.save(ck)
+    s.step(k, k, u)
+    it, rr = s.last_solve()
+    assert rr <= 1e-13 and it >= 0
+    with pytest.raises(RuntimeError):
+        s.backward(s.stress(), [ck], 1, 1, k, u)
+    s.close()
