@@ -301,6 +301,50 @@ def end_to_end(s, kap, u, steps: int, stream, dev):
     return e0.elapsed_time(e1), (h_k.numel() + h_u.numel()) * elem, h_sig[0].numel() * elem
 
 
+IMPLICIT = dict(name="implicit transport, 2D periodic 1024^2, m=32 SOE modes, alpha=0.5, dt=5e-4, FP32 storage",
+                dim=2, n=(1024, 1024), alpha=0.5, Wi=1.0, beta=0.5, m=32, dt=5e-4, steps=10, warmup=2, kmax=32,
+                seed=2)
+
+
+def implicit_transport_record(dev):
+    """The 2D 1024^2 alpha = 0.5 workload with transport at unit-RMS velocity,
+    where the explicit transport is unstable, run with implicit transport:
+    time per step, BiCGStab iterations per step and the explicit Courant
+    fraction (> 1: explicit unstable)."""
+    import numpy as np
+    import torch
+
+    from paper_2411_17294_gb300 import inputs, soe, tfs
+    I = IMPLICIT
+    mu, w = soe.build(I["alpha"], I["dt"], 200 * I["dt"], I["m"])
+    u, kap = inputs.spectral_velocity(2, I["n"], I["kmax"], I["seed"], device=dev)
+    s = tfs.Solver(2, I["n"], I["alpha"], I["Wi"], I["beta"], I["dt"], m=I["m"], precision=tfs.TFS_FP32, mu=mu,
+                   w=w, transport="implicit", device=dev)
+    kt = torch.as_tensor(kap, dtype=torch.float32, device=dev).contiguous()
+    ut = torch.as_tensor(u, dtype=torch.float32, device=dev).contiguous()
+    U = s.transport_limit()
+    courant = float(torch.max(torch.abs(ut).sum(dim=0)).item()) / (2 * U) if U > 0 else float("inf")
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        s.set_state(None, stream=stream)
+        for _ in range(I["warmup"]):
+            s.step(kt, kt, ut, stream=stream)
+        torch.cuda.synchronize()
+        its = []
+        t0 = time.perf_counter()
+        for _ in range(I["steps"]):
+            s.step(kt, kt, ut, stream=stream)      # synchronises its stream (convergence checks)
+            its.append(s.last_solve())
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / I["steps"]
+    flags = s.status()
+    s.close()
+    return {"workload": I["name"], "ms_per_step": ms,
+            "G_point_mode_updates_per_s": I["n"][0] * I["n"][1] * I["m"] / (ms * 1e-3) / 1e9,
+            "krylov_iterations": [it for it, _ in its], "max_relative_residual": max(r for _, r in its),
+            "explicit_courant_fraction": courant, "device_flags": flags}
+
+
 def max_over_ranks(local_ms: float, dist, device) -> float:
     """The slowest rank's time (all ranks get it); local_ms itself on one process."""
     if dist is None:
@@ -468,6 +512,13 @@ def main():
         except Exception as exc:  # pragma: no cover - reported, not fatal
             adj = {"error": str(exc)}
 
+    imp = None
+    if not args.no_adjoint:
+        try:
+            imp = implicit_transport_record(dev)
+        except Exception as exc:  # pragma: no cover - reported, not fatal
+            imp = {"error": str(exc)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         try:
@@ -498,6 +549,7 @@ def main():
             "clocks": clocks,
             "e2e": e2e,
             "adjoint_forward": adj,
+            "implicit_transport": imp,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

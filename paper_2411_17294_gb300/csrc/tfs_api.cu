@@ -238,7 +238,11 @@ bool limits_violated(tfs_ctx* h) {
     return h->umax >= 0.0 && courant_coef(h) * h->umax * sum_inv_h(h) > lim;
 }
 
-size_t krylov_vector_bytes(const tfs_ctx* h) { return (size_t)h->nc * (size_t)h->N * sizeof(double); }
+// implicit transport: 10 Krylov vectors [nc][N] plus the point blocks and the
+// preconditioner inverses [nc*nc][N], all FP64
+size_t krylov_bytes(const tfs_ctx* h) {
+    return (10 + 2 * (size_t)h->nc) * (size_t)h->nc * (size_t)h->N * sizeof(double);
+}
 size_t forward_bytes_for(const tfs_ctx* h, int transport);
 
 void layout_forward(tfs_ctx* h, char* base) {
@@ -261,14 +265,14 @@ void layout_forward(tfs_ctx* h, char* base) {
     h->partials = nullptr;
     if (h->implicit_transport()) {
         h->kry = (double*)p;
-        p += align_up(10 * krylov_vector_bytes(h));
+        p += align_up(krylov_bytes(h));
         h->partials = (double*)p;
     }
 }
 
 size_t forward_bytes_for(const tfs_ctx* h, int transport) {
     size_t b = kAlign + 5 * align_up(h->field_bytes()) + 2 * align_up(h->modes_bytes());
-    if (transport == 2) b += align_up(10 * krylov_vector_bytes(h)) + align_up(sizeof(double) * kImpBlocks);
+    if (transport == 2) b += align_up(krylov_bytes(h)) + align_up(sizeof(double) * (2 * kImpBlocks + 32));
     return b;
 }
 

@@ -90,17 +90,51 @@ __global__ void __launch_bounds__(kThreads) imp_rhs_kernel(const ImpArgs<T> A, d
     }
 }
 
+// Per step: the point blocks M_p = a I - dt L(kappa*_p) and the inverses of
+// the preconditioner blocks P_p = M_p + dt (diagonal of the transport stencil) I,
+// stored [nc*nc][N] (entry r*nc + k of point p at (r*nc + k) N + p).
 template <typename T, int DIM>
-__device__ __forceinline__ void point_block(const ImpArgs<T>& A, long long p, double M[Packed<DIM>::NC][Packed<DIM>::NC]) {
-    double K[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+__global__ void __launch_bounds__(kThreads) imp_setup_kernel(const ImpArgs<T> A, double* Mb, double* Pinv) {
+    constexpr int NC = Packed<DIM>::NC;
+    const long long N = A.N;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        double K[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
 #pragma unroll
-    for (int i = 0; i < DIM; ++i)
+        for (int i = 0; i < DIM; ++i)
 #pragma unroll
-        for (int j = 0; j < DIM; ++j) {
-            const long long q = (long long)(i * DIM + j) * A.N + p;
-            K[i][j] = 2.0 * (double)A.kap_n[q] - (double)A.kap_nm1[q];
+            for (int j = 0; j < DIM; ++j) {
+                const long long q = (long long)(i * DIM + j) * N + p;
+                K[i][j] = 2.0 * (double)A.kap_n[q] - (double)A.kap_nm1[q];
+            }
+        double M[NC][NC];
+        assemble_M<DIM>(K, A.a, A.dt, M);
+        double diag = 0.0;
+#pragma unroll
+        for (int ax = 0; ax < DIM; ++ax) {
+            const double ua = (double)A.u[(long long)ax * N + p];
+            if (A.stencil == 0) diag += fabs(ua) * 0.5 * A.inv_h[ax];
+            diag += 2.0 * A.eps * A.inv_h[ax] * A.inv_h[ax];
         }
-    assemble_M<DIM>(K, A.a, A.dt, M);
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            double P[NC][NC], col[NC];
+#pragma unroll
+            for (int r = 0; r < NC; ++r) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) P[r][c] = M[r][c] + (r == c ? A.dt * diag : 0.0);
+                col[r] = r == k ? 1.0 : 0.0;
+            }
+            ok = gauss_pp<NC>(P, col, 1e-300) && ok;
+#pragma unroll
+            for (int r = 0; r < NC; ++r) Pinv[(long long)(r * NC + k) * N + p] = col[r];
+        }
+        if (!ok) atomicOr(A.flags, 2u);
+#pragma unroll
+        for (int r = 0; r < NC; ++r)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) Mb[(long long)(r * NC + c) * N + p] = M[r][c];
+    }
 }
 
 // first derivative along axis ax of field f at point p (taps -2..2), upwinded on the sign of v
@@ -114,13 +148,42 @@ __device__ __forceinline__ double deriv_at(const double* f, const GridIdx& g, in
     return (-2.0 * fm1 - 3.0 * f0 + 6.0 * fp1 - f[g.at(ax, 2)]) * (ih / 6.0);
 }
 
+// Device scalars of the iteration.
+enum : int { S_RHO = 0, S_RHO_NEW, S_ALPHA, S_OMEGA, S_BETA, S_RHV, S_TS, S_TT, S_RR, S_BNORM2, S_DONE, S_ITERS,
+             S_BREAK, S_TOL2, S_COUNT };
+constexpr int kPartialSets = 2;    // dot products reduced in one pass
+
+__device__ __forceinline__ bool done(const double* sc) { return sc[S_DONE] != 0.0; }
+
+// block-level reduction of two values into partials[set * kImpBlocks + block]
+__device__ __forceinline__ void block_partials(double a0, double a1, int nsets, double* partials) {
+    __shared__ double sh[2][kThreads];
+    sh[0][threadIdx.x] = a0;
+    sh[1][threadIdx.x] = a1;
+    __syncthreads();
+    for (int st = kThreads / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + st];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + st];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = sh[0][0];
+        if (nsets > 1) partials[kImpBlocks + blockIdx.x] = sh[1][0];
+    }
+}
+
+// y = Op(x); partial sums of (w0, y) and (w1, y) when w0 / w1 are given
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kThreads) imp_apply_kernel(const ImpArgs<T> A, const double* x, double* y) {
+__global__ void __launch_bounds__(kThreads) imp_apply_kernel(const ImpArgs<T> A, const double* Mb, const double* x,
+                                                             double* y, const double* w0, const double* w1,
+                                                             double* partials, const double* sc) {
     constexpr int NC = Packed<DIM>::NC;
+    if (done(sc)) return;
     const long long N = A.N;
+    double a0 = 0.0, a1 = 0.0;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-        double M[NC][NC];
-        point_block<T, DIM>(A, p, M);
         GridIdx g;
         g.n0 = A.n0;
         g.n1 = A.n1;
@@ -138,7 +201,7 @@ __global__ void __launch_bounds__(kThreads) imp_apply_kernel(const ImpArgs<T> A,
         for (int r = 0; r < NC; ++r) {
             double acc = 0.0;
 #pragma unroll
-            for (int k = 0; k < NC; ++k) acc = fma(M[r][k], xp[k], acc);
+            for (int k = 0; k < NC; ++k) acc = fma(Mb[(long long)(r * NC + k) * N + p], xp[k], acc);
             const double* f = x + (long long)r * N;
             double t = 0.0;
 #pragma unroll
@@ -147,60 +210,140 @@ __global__ void __launch_bounds__(kThreads) imp_apply_kernel(const ImpArgs<T> A,
                 if (A.eps != 0.0)
                     t -= A.eps * (f[g.at(ax, -1)] - 2.0 * xp[r] + f[g.at(ax, 1)]) * (A.inv_h[ax] * A.inv_h[ax]);
             }
-            y[(long long)r * N + p] = acc + A.dt * t;
+            const long long q = (long long)r * N + p;
+            const double yv = acc + A.dt * t;
+            y[q] = yv;
+            if (w0) a0 = fma(w0[q], yv, a0);
+            if (w1) a1 = fma(w1[q], yv, a1);
+        }
+    }
+    if (w0) block_partials(a0, a1, w1 ? 2 : 1, partials);
+}
+
+// z = P^-1 v with v = a x + b y (+ c w): forms the combination, stores it in
+// `comb` (when given) and its preconditioned image in z
+template <int NC>
+__global__ void __launch_bounds__(kThreads) imp_comb_precond_kernel(long long N, const double* Pinv, int mode,
+                                                                    double* p, const double* r, const double* v,
+                                                                    double* z, const double* sc) {
+    if (done(sc)) return;
+    // mode 0: p = r + beta (p - omega v);  mode 1: p (as s) = r - alpha v
+    const double beta = sc[S_BETA], omega = sc[S_OMEGA], alpha = sc[S_ALPHA];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        double w[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const long long q = (long long)c * N + i;
+            const double nv = mode == 0 ? fma(beta, p[q] - omega * v[q], r[q]) : fma(-alpha, v[q], r[q]);
+            p[q] = nv;
+            w[c] = nv;
+        }
+#pragma unroll
+        for (int rr = 0; rr < NC; ++rr) {
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < NC; ++k) acc = fma(Pinv[(long long)(rr * NC + k) * N + i], w[k], acc);
+            z[(long long)rr * N + i] = acc;
         }
     }
 }
 
-// z = P^-1 r: the point block M_p plus the diagonal of the transport stencil
-template <typename T, int DIM>
-__global__ void __launch_bounds__(kThreads) imp_precond_kernel(const ImpArgs<T> A, const double* r, double* z) {
-    constexpr int NC = Packed<DIM>::NC;
-    const long long N = A.N;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-        double M[NC][NC];
-        point_block<T, DIM>(A, p, M);
-        double diag = 0.0;
-#pragma unroll
-        for (int ax = 0; ax < DIM; ++ax) {
-            const double ua = (double)A.u[(long long)ax * N + p];
-            if (A.stencil == 0) diag += fabs(ua) * 0.5 * A.inv_h[ax];
-            diag += 2.0 * A.eps * A.inv_h[ax] * A.inv_h[ax];
-        }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) M[c][c] += A.dt * diag;
-        double v[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) v[c] = r[(long long)c * N + p];
-        if (!gauss_pp<NC>(M, v, 1e-300)) atomicOr(A.flags, 2u);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) z[(long long)c * N + p] = v[c];
+// x += alpha ph + omega sh;  r = s - omega t;  partial sums of (r, r) and (rh, r)
+__global__ void __launch_bounds__(kThreads) imp_xr_kernel(long long n, double* x, const double* ph, const double* sh,
+                                                          double* r, const double* s, const double* t, const double* rh,
+                                                          double* partials, const double* sc) {
+    if (done(sc)) return;
+    const double alpha = sc[S_ALPHA], omega = sc[S_OMEGA];
+    double a0 = 0.0, a1 = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        x[i] = fma(alpha, ph[i], fma(omega, sh[i], x[i]));
+        const double rv = fma(-omega, t[i], s[i]);
+        r[i] = rv;
+        a0 = fma(rv, rv, a0);
+        a1 = fma(rh[i], rv, a1);
     }
+    block_partials(a0, a1, 2, partials);
 }
 
-// per-block partial sums of x.y (x.x when y == x), block reduce in shared memory
-__global__ void __launch_bounds__(kThreads) imp_dot_kernel(const double* x, const double* y, long long n,
-                                                           double* partials) {
-    __shared__ double sh[kThreads];
-    double acc = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        acc = fma(x[i], y[i], acc);
-    sh[threadIdx.x] = acc;
+// per-block partial sums of x.y and x.z (z may be null), for the start of the iteration
+__global__ void __launch_bounds__(kThreads) imp_dot2_kernel(const double* x, const double* y, const double* z,
+                                                            long long n, double* partials) {
+    double a0 = 0.0, a1 = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        a0 = fma(x[i], y[i], a0);
+        if (z) a1 = fma(x[i], z[i], a1);
+    }
+    block_partials(a0, a1, z ? 2 : 1, partials);
+}
+
+// One block: add the partial sums in a fixed order into scalar slots, then the
+// scalar step of the iteration.
+//   op 0: RR, RHO_NEW <- (r, r), (rh, r); convergence test; beta for the next pass
+//   op 1: RHV <- (rh, v); alpha
+//   op 2: TS, TT <- (t, s), (t, t); omega
+//   op 3: BNORM2 <- (b, b)
+//   op 4: RR, RHO_NEW <- (r, r), (rh, r) at the start (no beta)
+__global__ void __launch_bounds__(kThreads) imp_scalar_kernel(const double* partials, double* sc, int op) {
+    __shared__ double sh[2][kThreads];
+    double a0 = 0.0, a1 = 0.0;
+    for (int i = threadIdx.x; i < kImpBlocks; i += kThreads) {
+        a0 += partials[i];
+        a1 += partials[kImpBlocks + i];
+    }
+    sh[0][threadIdx.x] = a0;
+    sh[1][threadIdx.x] = a1;
     __syncthreads();
-    for (int s = kThreads / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    for (int st = kThreads / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + st];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + st];
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+    if (threadIdx.x != 0) return;
+    const double v0 = sh[0][0], v1 = sh[1][0];
+    if (op == 3) {
+        sc[S_BNORM2] = v0;
+        return;
+    }
+    if (op == 4) {
+        sc[S_RR] = v0;
+        sc[S_RHO_NEW] = v1;
+        if (v0 <= sc[S_TOL2] * sc[S_BNORM2]) sc[S_DONE] = 1.0;
+        return;
+    }
+    if (done(sc)) return;
+    if (op == 1) {
+        sc[S_RHV] = v0;
+        if (v0 == 0.0) {
+            sc[S_BREAK] = 1.0;
+            sc[S_DONE] = 1.0;
+        } else {
+            sc[S_ALPHA] = sc[S_RHO] / v0;
+        }
+    } else if (op == 2) {
+        sc[S_TS] = v0;
+        sc[S_TT] = v1;
+        sc[S_OMEGA] = v1 > 0.0 ? v0 / v1 : 0.0;
+    } else {
+        sc[S_RR] = v0;
+        sc[S_RHO_NEW] = v1;
+        sc[S_ITERS] += 1.0;
+        if (v0 <= sc[S_TOL2] * sc[S_BNORM2]) {
+            sc[S_DONE] = 1.0;
+        } else if (v1 == 0.0 || sc[S_OMEGA] == 0.0) {
+            sc[S_BREAK] = 1.0;
+            sc[S_DONE] = 1.0;
+        }
+    }
+    if (op == 0 || op == 4) return;
 }
 
-// y = a x + b y + c z (any of the inputs may alias y)
-__global__ void __launch_bounds__(kThreads) imp_axpbypcz_kernel(double a, const double* x, double b, double* y, double c,
-                                                                const double* z, long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const double xv = x ? x[i] : 0.0, zv = z ? z[i] : 0.0;
-        y[i] = a * xv + b * y[i] + c * zv;
-    }
+// beta and rho for the next direction (after op 0 / op 4)
+__global__ void imp_beta_kernel(double* sc) {
+    if (done(sc)) return;
+    sc[S_BETA] = (sc[S_RHO_NEW] / sc[S_RHO]) * (sc[S_ALPHA] / sc[S_OMEGA]);
+    sc[S_RHO] = sc[S_RHO_NEW];
 }
 
 template <typename T, int DIM>
@@ -236,124 +379,108 @@ __global__ void __launch_bounds__(kThreads) imp_push_kernel(const ImpArgs<T> A, 
     }
 }
 
-// ------------------------------------------------------------------ host side
-struct Krylov {
-    double *b, *x, *r, *rh, *p, *v, *s, *t, *ph, *sh;
-};
+// r = b - r (r holds Op(x0)); rh = r; p = v = 0
+__global__ void __launch_bounds__(kThreads) imp_init_kernel(long long n, const double* b, double* r, double* rh,
+                                                            double* p, double* v) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double rv = b[i] - r[i];
+        r[i] = rv;
+        rh[i] = rv;
+        p[i] = 0.0;
+        v[i] = 0.0;
+    }
+}
 
+// ------------------------------------------------------------------ host side
 template <typename T, int DIM, bool COMP>
 cudaError_t run_implicit(const ImpArgs<T>& a, cudaStream_t st, int* iters, double* relres) {
     constexpr int NC = Packed<DIM>::NC;
-    const long long n = (long long)NC * a.N;
-    const long long bs = (long long)kImpBlocks;
-    Krylov K;
-    double* base = a.kry;
-    double** slots[] = {&K.b, &K.x, &K.r, &K.rh, &K.p, &K.v, &K.s, &K.t, &K.ph, &K.sh};
-    for (int i = 0; i < 10; ++i) *slots[i] = base + (size_t)i * (size_t)n;
-    std::vector<double> host(kImpBlocks);
+    const long long N = a.N;
+    const long long n = (long long)NC * N;
+    const unsigned bs = (unsigned)kImpBlocks;
+    // workspace: 10 vectors, the point blocks and preconditioner inverses, partial sums, scalars
+    double* w = a.kry;
+    double *b = w, *x = w + n, *r = w + 2 * n, *rh = w + 3 * n, *p = w + 4 * n, *v = w + 5 * n, *sv = w + 6 * n,
+           *t = w + 7 * n, *ph = w + 8 * n, *sh = w + 9 * n;
+    double* Mb = w + 10 * n;
+    double* Pinv = Mb + (long long)NC * NC * N;
+    double* partials = a.partials;
+    double* sc = partials + kPartialSets * kImpBlocks;
     cudaError_t e = cudaSuccess;
-    auto check = [&]() { if (e == cudaSuccess) e = cudaGetLastError(); return e == cudaSuccess; };
-    // dot product: partial sums on the device, added on the host in block order
-    auto dot = [&](const double* x, const double* y, double* out) {
-        if (e != cudaSuccess) return;
-        imp_dot_kernel<<<(unsigned)bs, kThreads, 0, st>>>(x, y, n, a.partials);
-        if (!check()) return;
-        e = cudaMemcpyAsync(host.data(), a.partials, sizeof(double) * kImpBlocks, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        double acc = 0.0;
-        for (int i = 0; i < kImpBlocks; ++i) acc += host[i];
-        *out = acc;
+    auto ok = [&]() {
+        if (e == cudaSuccess) e = cudaGetLastError();
+        return e == cudaSuccess;
     };
-    auto lin = [&](double ca, const double* x, double cb, double* y, double cc, const double* z) {
-        if (e != cudaSuccess) return;
-        imp_axpbypcz_kernel<<<(unsigned)bs, kThreads, 0, st>>>(ca, x, cb, y, cc, z, n);
-        check();
-    };
-    auto apply = [&](const double* x, double* y) {
-        if (e != cudaSuccess) return;
-        imp_apply_kernel<T, DIM><<<(unsigned)bs, kThreads, 0, st>>>(a, x, y);
-        check();
-    };
-    auto precond = [&](const double* r, double* z) {
-        if (e != cudaSuccess) return;
-        imp_precond_kernel<T, DIM><<<(unsigned)bs, kThreads, 0, st>>>(a, r, z);
-        check();
-    };
-
-    imp_rhs_kernel<T, DIM, COMP><<<(unsigned)bs, kThreads, 0, st>>>(a, K.b, K.x);
-    check();
-    double bnorm2 = 0.0;
-    dot(K.b, K.b, &bnorm2);
-    const double bnorm = std::sqrt(bnorm2);
-    int it = 0;
-    double res = 0.0;
+    double hs[S_COUNT] = {};
+    hs[S_RHO] = hs[S_ALPHA] = hs[S_OMEGA] = 1.0;
+    hs[S_TOL2] = a.tol * a.tol;
+    e = cudaMemcpyAsync(sc, hs, sizeof(hs), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    imp_setup_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, Mb, Pinv);
+    if (!ok()) return e;
+    imp_rhs_kernel<T, DIM, COMP><<<bs, kThreads, 0, st>>>(a, b, x);
+    if (!ok()) return e;
+    imp_dot2_kernel<<<bs, kThreads, 0, st>>>(b, b, nullptr, n, partials);
+    if (!ok()) return e;
+    imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 3);
+    if (!ok()) return e;
+    e = cudaMemcpyAsync(hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    const double bnorm2 = hs[S_BNORM2];
     bool converged = false;
-    if (e == cudaSuccess && bnorm == 0.0) {
-        lin(0.0, nullptr, 0.0, K.x, 0.0, nullptr);   // R = 0: sigma^{n+1} = 0
+    if (bnorm2 == 0.0) {
+        e = cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, st);   // R = 0: sigma^{n+1} = 0
         converged = true;
-    } else if (e == cudaSuccess) {
-        apply(K.x, K.r);
-        lin(1.0, K.b, -1.0, K.r, 0.0, nullptr);      // r = b - Op(x0)
-        lin(1.0, K.r, 0.0, K.rh, 0.0, nullptr);      // shadow residual
-        lin(0.0, nullptr, 0.0, K.p, 0.0, nullptr);
-        lin(0.0, nullptr, 0.0, K.v, 0.0, nullptr);
-        double rr = 0.0;
-        dot(K.r, K.r, &rr);
-        res = std::sqrt(rr) / bnorm;
-        converged = res <= a.tol;
-        double rho = 1.0, alpha = 1.0, omega = 1.0;
-        while (e == cudaSuccess && !converged && it < a.maxit) {
-            ++it;
-            double rho_new = 0.0;
-            dot(K.rh, K.r, &rho_new);
-            if (rho_new == 0.0 || omega == 0.0) break;   // breakdown
-            const double beta = (rho_new / rho) * (alpha / omega);
-            rho = rho_new;
-            lin(-beta * omega, K.v, beta, K.p, 1.0, K.r);   // p = r + beta (p - omega v)
-            precond(K.p, K.ph);
-            apply(K.ph, K.v);
-            double rhv = 0.0;
-            dot(K.rh, K.v, &rhv);
-            if (rhv == 0.0) break;
-            alpha = rho / rhv;
-            lin(1.0, K.r, 0.0, K.s, -alpha, K.v);          // s = r - alpha v
-            double ss = 0.0;
-            dot(K.s, K.s, &ss);
-            if (std::sqrt(ss) / bnorm <= a.tol) {
-                lin(alpha, K.ph, 1.0, K.x, 0.0, nullptr);   // x += alpha ph
-                res = std::sqrt(ss) / bnorm;
-                converged = true;
-                break;
+        hs[S_RR] = 0.0;
+        hs[S_ITERS] = 0.0;
+    } else {
+        imp_apply_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, Mb, x, r, nullptr, nullptr, partials, sc);
+        if (!ok()) return e;
+        imp_init_kernel<<<bs, kThreads, 0, st>>>(n, b, r, rh, p, v);
+        if (!ok()) return e;
+        imp_dot2_kernel<<<bs, kThreads, 0, st>>>(r, r, rh, n, partials);
+        if (!ok()) return e;
+        imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 4);
+        if (!ok()) return e;
+        // the iteration runs on device scalars; the host looks at them every kCheck passes
+        constexpr int kCheck = 8;
+        for (int it = 0; it < a.maxit; ++it) {
+            imp_beta_kernel<<<1, 1, 0, st>>>(sc);
+            imp_comb_precond_kernel<NC><<<bs, kThreads, 0, st>>>(N, Pinv, 0, p, r, v, ph, sc);
+            imp_apply_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, Mb, ph, v, rh, nullptr, partials, sc);
+            imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 1);
+            imp_comb_precond_kernel<NC><<<bs, kThreads, 0, st>>>(N, Pinv, 1, sv, r, v, sh, sc);
+            imp_apply_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, Mb, sh, t, sv, t, partials, sc);
+            imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 2);
+            imp_xr_kernel<<<bs, kThreads, 0, st>>>(n, x, ph, sh, r, sv, t, rh, partials, sc);
+            imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 0);
+            if (!ok()) return e;
+            if ((it + 1) % kCheck == 0 || it + 1 == a.maxit) {
+                e = cudaMemcpyAsync(hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                if (e != cudaSuccess) return e;
+                if (hs[S_DONE] != 0.0) break;
             }
-            precond(K.s, K.sh);
-            apply(K.sh, K.t);
-            double ts = 0.0, tt = 0.0;
-            dot(K.t, K.s, &ts);
-            dot(K.t, K.t, &tt);
-            omega = tt > 0.0 ? ts / tt : 0.0;
-            lin(alpha, K.ph, 1.0, K.x, omega, K.sh);        // x += alpha ph + omega sh
-            lin(1.0, K.s, 0.0, K.r, -omega, K.t);           // r = s - omega t
-            dot(K.r, K.r, &rr);
-            res = std::sqrt(rr) / bnorm;
-            converged = res <= a.tol;
         }
-    }
-    if (e == cudaSuccess && !converged) {
-        unsigned nc_flag = 16u;
-        e = cudaMemcpyAsync(host.data(), a.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        converged = hs[S_RR] <= hs[S_TOL2] * bnorm2;
+    }
+    if (!converged) {
         unsigned f = 0u;
-        memcpy(&f, host.data(), sizeof(unsigned));
-        f |= nc_flag;
+        e = cudaMemcpyAsync(&f, a.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        f |= 16u;
         if (e == cudaSuccess) e = cudaMemcpyAsync(a.flags, &f, sizeof(unsigned), cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
     }
-    if (e == cudaSuccess) {
-        imp_push_kernel<T, DIM><<<(unsigned)bs, kThreads, 0, st>>>(a, K.x);
-        check();
-    }
-    *iters = it;
-    *relres = res;
+    imp_push_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, x);
+    if (!ok()) return e;
+    *iters = (int)hs[S_ITERS];
+    *relres = bnorm2 > 0.0 ? std::sqrt(hs[S_RR] / bnorm2) : 0.0;
     return e;
 }
 
