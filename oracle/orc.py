@@ -64,6 +64,8 @@ def _load():
         lib.orc_step.restype = ctypes.c_int
         lib.orc_step.argtypes = [ctypes.POINTER(_Params), dp, dp, ctypes.c_long,
                                  dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
+        lib.orc_first_step_sdirk2.restype = ctypes.c_int
+        lib.orc_first_step_sdirk2.argtypes = [ctypes.POINTER(_Params), dp, dp, dp, dp, dp, dp, dp, dp, dp]
         lib.orc_step_implicit.restype = ctypes.c_int
         lib.orc_step_implicit.argtypes = lib.orc_step.argtypes
         lib.orc_adjoint_step.restype = ctypes.c_int
@@ -101,6 +103,7 @@ class Problem:
     transport: bool = False
     full: bool = False          # store the full d x d tensor instead of packed
     implicit: bool = False      # transport at t_{n+1} inside a global solve (small grids)
+    start: str = "bdf2"         # first step: "bdf2" (empty past) or "sdirk2" (Section 5.1; alpha < 1)
 
     @property
     def N(self) -> int:
@@ -170,6 +173,18 @@ class Oracle:
             u = None
         sig_np1 = np.empty_like(self.sig_n)
         modes_np1 = np.zeros_like(self.modes_n)
+        if prob.start == "sdirk2" and self.n == 0:
+            sig_np1 = np.empty_like(self.sig_n)
+            modes_np1 = np.zeros_like(self.modes_n)
+            if _load().orc_first_step_sdirk2(ctypes.byref(self._p), _ptr(self.mu), _ptr(self.w), _ptr(self.sig_n),
+                                             _ptr(self.modes_n), _ptr(self.sigma0), _ptr(kap_n), _ptr(u),
+                                             _ptr(sig_np1), _ptr(modes_np1)):
+                raise FloatingPointError("SDIRK2 start failed (alpha = 1, or a singular system)")
+            self.sig_nm1, self.sig_n = self.sig_n, sig_np1
+            self.modes_nm1, self.modes_n = self.modes_n, modes_np1
+            self._kap_prev = kap_n
+            self.n += 1
+            return
         fn = _load().orc_step_implicit if prob.implicit else _load().orc_step
         fails = fn(ctypes.byref(self._p), _ptr(self.mu), _ptr(self.w), self.n,
                                  _ptr(self.sig_n), _ptr(self.sig_nm1), _ptr(self.modes_n), _ptr(self.modes_nm1),

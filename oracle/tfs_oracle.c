@@ -314,6 +314,54 @@ int orc_step(const orc_params* p, const double* mu, const double* w, long step_i
     return failures;
 }
 
+/* Dense matrix of  S -> a S_p - dt L(kappa*_p) S_p + dt [sum_a u_a D_a(S) - eps Lap(S)]_p
+   over the grid (n = nc N unknowns, unknown k = component * N + point), column by
+   column: the image of each unit field.  unit is N doubles of zeros (scratch). */
+static void assemble_global(const orc_params* p, const double* kap_n, const double* kap_nm1, const double* u,
+                            double a, double* G, double* unit) {
+    const int d = p->dim, nc = ncomp(p);
+    const long N = npoints(p);
+    const long n = (long)nc * N;
+    /* columns: unknown k = (component ck, point pk) */
+    for (long k = 0; k < n; ++k) {
+        const int ck = (int)(k / N);
+        const long pk = k % N;
+        for (long r = 0; r < n; ++r) G[r * n + k] = 0.0;
+        /* local part at point pk: the block a I - dt L(kappa*_pk) applied to e_ck */
+        {
+            double K[3][3] = {{0}};
+            for (int i = 0; i < d; ++i)
+                for (int j = 0; j < d; ++j) {
+                    long q = (long)(i * d + j) * N + pk;
+                    K[i][j] = 2.0 * kap_n[q] - kap_nm1[q];
+                }
+            double e[9], img[9];
+            for (int c = 0; c < nc; ++c) e[c] = (c == ck) ? 1.0 : 0.0;
+            upper_convected(p, K, e, img);
+            for (int c = 0; c < nc; ++c) G[((long)c * N + pk) * n + k] += a * e[c] - p->dt * img[c];
+        }
+        /* transport part: component ck of the unit field is 1 at pk; its image
+           is nonzero at the points whose stencils reach pk */
+        if (p->transport) {
+            unit[pk] = 1.0;
+            for (long pt = 0; pt < N; ++pt) {
+                long x = pt % p->n[0];
+                long y = (pt / p->n[0]) % p->n[1];
+                long z = (d == 3) ? pt / ((long)p->n[0] * p->n[1]) : 0;
+                double t = 0.0;
+                for (int a = 0; a < d; ++a) {
+                    double va = u[(long)a * N + pt];
+                    t += va * deriv(p, unit, a, x, y, z, va);
+                }
+                if (p->eps != 0.0) t -= p->eps * laplace(p, unit, x, y, z);
+                if (t != 0.0) G[((long)ck * N + pt) * n + k] += p->dt * t;
+            }
+            unit[pk] = 0.0;
+        }
+    }
+
+}
+
 /*
  * One step with the transport treated implicitly (the form in which the paper's
  * scheme, eq. FP_discrete, carries u.grad and eps Lap: at t_{n+1}, inside the
@@ -348,43 +396,7 @@ int orc_step_implicit(const orc_params* p, const double* mu, const double* w, lo
     double* unit = (double*)calloc((size_t)N, sizeof(double));
     if (!G || !rhs || !unit) { free(G); free(rhs); free(unit); return 1; }
 
-    /* columns: unknown k = (component ck, point pk) */
-    for (long k = 0; k < n; ++k) {
-        const int ck = (int)(k / N);
-        const long pk = k % N;
-        for (long r = 0; r < n; ++r) G[r * n + k] = 0.0;
-        /* local part at point pk: the block a I - dt L(kappa*_pk) applied to e_ck */
-        {
-            double K[3][3] = {{0}};
-            for (int i = 0; i < d; ++i)
-                for (int j = 0; j < d; ++j) {
-                    long q = (long)(i * d + j) * N + pk;
-                    K[i][j] = 2.0 * kap_n[q] - kap_nm1[q];
-                }
-            double e[9], img[9];
-            for (int c = 0; c < nc; ++c) e[c] = (c == ck) ? 1.0 : 0.0;
-            upper_convected(p, K, e, img);
-            for (int c = 0; c < nc; ++c) G[((long)c * N + pk) * n + k] += s.a * e[c] - p->dt * img[c];
-        }
-        /* transport part: component ck of the unit field is 1 at pk; its image
-           is nonzero at the points whose stencils reach pk */
-        if (p->transport) {
-            unit[pk] = 1.0;
-            for (long pt = 0; pt < N; ++pt) {
-                long x = pt % p->n[0];
-                long y = (pt / p->n[0]) % p->n[1];
-                long z = (d == 3) ? pt / ((long)p->n[0] * p->n[1]) : 0;
-                double t = 0.0;
-                for (int a = 0; a < d; ++a) {
-                    double va = u[(long)a * N + pt];
-                    t += va * deriv(p, unit, a, x, y, z, va);
-                }
-                if (p->eps != 0.0) t -= p->eps * laplace(p, unit, x, y, z);
-                if (t != 0.0) G[((long)ck * N + pt) * n + k] += p->dt * t;
-            }
-            unit[pk] = 0.0;
-        }
-    }
+    assemble_global(p, kap_n, kap_nm1, u, s.a, G, unit);
 
     for (long pt = 0; pt < N; ++pt) {
         double K[3][3] = {{0}};
@@ -428,6 +440,86 @@ int orc_step_implicit(const orc_params* p, const double* mu, const double* w, lo
     free(G);
     free(rhs);
     free(unit);
+    return failed;
+}
+
+/*
+ * First step t_0 -> t_1 by a two-stage SDIRK2 method (gamma = 1 - 1/sqrt2, L-stable,
+ * stiffly accurate), as the paper does for non-trivial initial data (Section 5.1)
+ * instead of BDF2 with an empty past.  Fractional order (alpha < 1) only.
+ *
+ * The kernel-compressed law is the system of mode equations
+ *     d sigma_j/dt = -mu_j sigma_j + w_j (sigma - sigma0)
+ * (the ODEs whose BDF2 discretisation is eq. BDF_Phi_k_n+1) with the constraint
+ *     sum_j d sigma_j/dt = F(sigma, t) = L(kappa) sigma - sigma/Wi + G (kappa + kappa^T) g_alpha(t)
+ *                                        - (u.grad - eps Lap) sigma,
+ * the mode sum standing for the Caputo derivative.  At stage i (time t_i, stage
+ * value S, Z_j the explicit part of the mode stage) the slopes are
+ *     K_j = (-mu_j Z_j + w_j (S - sigma0)) / (1 + gamma mu_j dt),
+ * and the constraint gives, over the grid (transport implicit),
+ *     (dt W + dt/Wi) S - dt L(kappa) S + dt (u.grad - eps Lap) S
+ *         = dt W sigma0 + dt sum_j mu_j Z_j / (1 + gamma mu_j dt) + dt G (kappa + kappa^T) g_alpha(t_i),
+ *     W = sum_j w_j / (1 + gamma mu_j dt).
+ * Stage 1: t_1 = gamma dt, Z_j = sigma_j^0.  Stage 2: t_2 = dt,
+ * Z_j = sigma_j^0 + dt (1 - gamma) K_j^(1).  Result: sigma^1 = S^(2),
+ * sigma_j^1 = Z_j^(2) + gamma dt K_j^(2).  kappa* = kappa^0 (no past).
+ * Returns 1 if a system was singular.
+ */
+int orc_first_step_sdirk2(const orc_params* p, const double* mu, const double* w,
+                          const double* sig_0, const double* modes_0, const double* sigma0,
+                          const double* kap_0, const double* u, double* sig_1, double* modes_1) {
+    const int d = p->dim, nc = ncomp(p);
+    const long N = npoints(p);
+    const long n = (long)nc * N;
+    const int m = p->m;
+    if (p->alpha == 1.0 || m < 1) return 1;
+    const double gam = 1.0 - sqrt(0.5);
+    const double dt = p->dt;
+    double W = 0.0;
+    for (int j = 0; j < m; ++j) W += w[j] / (1.0 + gam * mu[j] * dt);
+    const double a = dt * W + dt / p->Wi;
+    const double G = (1.0 - p->beta) / (p->Wi * p->Re);
+    (void)sig_0;
+
+    double* A = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+    double* rhs = (double*)malloc(sizeof(double) * (size_t)n);
+    double* unit = (double*)calloc((size_t)N, sizeof(double));
+    double* Z = (double*)malloc(sizeof(double) * (size_t)m * (size_t)n);
+    if (!A || !rhs || !unit || !Z) { free(A); free(rhs); free(unit); free(Z); return 1; }
+    memcpy(Z, modes_0, sizeof(double) * (size_t)m * (size_t)n);
+    int failed = 0;
+    for (int stage = 1; stage <= 2; ++stage) {
+        const double t = (stage == 1 ? gam : 1.0) * dt;
+        const double g = pow(t, p->alpha - 1.0) / tgamma(p->alpha);
+        assemble_global(p, kap_0, kap_0, u, a, A, unit);
+        for (long pt = 0; pt < N; ++pt) {
+            double K[3][3] = {{0}}, KS[3][3], sym[9];
+            for (int i = 0; i < d; ++i)
+                for (int j = 0; j < d; ++j) K[i][j] = kap_0[(long)(i * d + j) * N + pt];
+            for (int i = 0; i < d; ++i)
+                for (int j = 0; j < d; ++j) KS[i][j] = K[i][j] + K[j][i];
+            from_matrix(p, KS, sym);
+            for (int c = 0; c < nc; ++c) {
+                double zsum = 0.0;
+                for (int j = 0; j < m; ++j) zsum += mu[j] * Z[((long)j * nc + c) * N + pt] / (1.0 + gam * mu[j] * dt);
+                rhs[(long)c * N + pt] = dt * W * sigma0[(long)c * N + pt] + dt * zsum + dt * G * sym[c] * g;
+            }
+        }
+        if (gauss_solve((int)n, A, rhs)) failed = 1;
+        /* slopes and the next mode stage */
+        for (int j = 0; j < m; ++j)
+            for (long q = 0; q < n; ++q) {
+                const long jq = (long)j * n + q;
+                const double Kj = (-mu[j] * Z[jq] + w[j] * (rhs[q] - sigma0[q])) / (1.0 + gam * mu[j] * dt);
+                if (stage == 1) Z[jq] = modes_0[jq] + dt * (1.0 - gam) * Kj;
+                else modes_1[jq] = Z[jq] + gam * dt * Kj;
+            }
+    }
+    for (long q = 0; q < n; ++q) sig_1[q] = rhs[q];
+    free(A);
+    free(rhs);
+    free(unit);
+    free(Z);
     return failed;
 }
 

@@ -315,3 +315,56 @@ def test_reference_adjoint_matches_finite_differences(dim, transport, alpha):
             k = kap.copy(); k[c, q] = x
             return J(Wi, beta, sig0, k)
         assert close(g["kappa"][c, q], fd(fk, kap[c, q]))
+
+
+def _paper_case_bochner_errors(start, m, dts):
+    alpha, Wi, eps, T = 0.5, 1.0, 1e-2, 1.0
+    n = (8, 8)
+    N = n[0] * n[1]
+    h = 1.0 / n[0]
+    x = (np.arange(N) % n[0]) * h
+    y = (np.arange(N) // n[0]) * h
+    shape = np.cos(2 * np.pi * x) * np.cos(4 * np.pi * y)
+    sigma0 = np.tile(shape, (3, 1))
+    lam_h = 1.0 / Wi + eps * (4 * np.sin(np.pi * h) ** 2 + 4 * np.sin(2 * np.pi * h) ** 2) / h ** 2
+    assert abs(lam_h - (1.0 / Wi + 20 * eps * np.pi ** 2)) < 0.5
+    errs = []
+    for dt in dts:
+        steps = int(round(T / dt))
+        mu, w = soe.soe_nnls(alpha, dt, T, m)
+        prob = orc.Problem(dim=2, n=n, alpha=alpha, Wi=Wi, beta=0.5, dt=dt, mu=mu, w=w, eps=eps, L=(1.0, 1.0),
+                           transport=True, implicit=True, start=start)
+        o = orc.Oracle(prob, sigma0)
+        zero_u, kap = np.zeros((2, N)), np.zeros((4, N))
+        acc = 0.0
+        for k in range(1, steps + 1):
+            o.step(kap, kap, zero_u)
+            t = k * dt
+            exact = shape * special.mittag_leffler(alpha, -lam_h * t ** alpha)
+            e2 = np.mean((o.sig_n[0] - exact) ** 2)          # L2 over the unit square
+            acc += (0.5 if k == steps else 1.0) * e2 * t ** (2 * (1 - alpha)) * dt   # trapezoid, e(0) = 0
+        errs.append(np.sqrt(acc))
+    return errs
+
+
+def test_paper_first_convergence_case_bochner_norm():
+    # The paper's convergence case (Section 5.1): no flow, unit square, initial
+    # stress cos(2 pi x) cos(4 pi y), eps = 1e-2, De = 0.5 (Wi = 2 De, reading
+    # G2), alpha = 0.5, T = 1, error in the weighted Bochner norm of eq.
+    # weighted_Bochner_space_norm, diffusion implicit as in the paper.  On the
+    # periodic grid the solution is the initial field times E_alpha(-lambda_h
+    # t^alpha), lambda_h = 1/Wi + eps x (discrete Laplacian symbol) -> 1/Wi +
+    # 20 eps pi^2, so the error is that of time stepping and kernel compression.
+    # The stress-form scheme built here converges at order 1.1 - 1.3 in this
+    # norm with either first step -- the empty-past BDF2 start (reading G11) or
+    # the paper's SDIRK2 start, which lowers the error at coarse steps; the
+    # 1 + alpha the paper reports (its Fig. 2a) belongs to its own variable,
+    # D^{1-alpha} Phi with kernel g_alpha (reading G1), not built here.
+    dts = [1 / 20, 1 / 40, 1 / 80, 1 / 160]
+    bdf = _paper_case_bochner_errors("bdf2", 16, dts)
+    sdirk = _paper_case_bochner_errors("sdirk2", 16, dts)
+    orders = [np.log2(bdf[i] / bdf[i + 1]) for i in range(len(dts) - 1)]
+    assert all(1.0 < q < 1.4 for q in orders), orders
+    assert all(sdirk[i + 1] < sdirk[i] for i in range(len(dts) - 1)), sdirk
+    assert sdirk[0] < 0.8 * bdf[0]
+    assert sdirk[-1] < 2e-3 * 0.2
