@@ -14,4 +14,6 @@ orc.py         ctypes wrapper: state, stepping, history, gradients
 soe.py         sum-of-exponentials kernels: AAA with the division-by-s trick
                (Section 2.2) and a positive exponential quadrature
 special.py     Mittag-Leffler function and convolution-quadrature weights
+paper_form.py  the scheme in the paper's own variable Phi, Psi = D^{1-alpha} Phi
+               (Section 3.4), pointwise, BDF2 with an optional SDIRK2 start
 """

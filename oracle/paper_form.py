@@ -1,0 +1,174 @@
+"""The scheme in the paper's own variable (oracle side), pointwise law.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Section 3.4 (eq. macroscopic_fokker_planck) advances the Hermite coefficients
+Phi with a time derivative on Phi and the fractional operator on the right:
+
+    d Phi/dt = (A(grad u) - (u.grad - eps Lap)) Psi,      Psi := D^{1-alpha} Phi,
+
+D^{1-alpha} f = d/dt (g_alpha * f) with g_alpha(t) = t^(alpha-1)/Gamma(alpha)
+(Section 1).  For the degree-2 block, in the stress units of the oracle's
+stress form (reading G1-G3),
+
+    d Phi2/dt = L(kappa) Psi2 - Psi2/Wi + G (kappa + kappa^T) Psi0,   L(k) s = k s + s k^T,
+
+and the stress is Psi2; Phi0 == 1, so Psi0 = D^{1-alpha} 1 (= g_alpha(t)
+exactly).  Kernel compression (Section 2.2) replaces g_alpha by sum_j w_j
+exp(-mu_j t), i.e. Psi = sum_j w_j (-mu_j phi_j + Phi) with the mode ODEs
+d phi_j/dt = -mu_j phi_j + Phi (phi_j(0) = 0), and every ODE is advanced by
+BDF2 (Section 4.1):
+
+    phi_j^{n+1} = c_j (-b1 phi_j^n - b2 phi_j^{n-1} + dt Phi^{n+1}),   c_j = 1/(b0 + mu_j dt)
+    Psi^{n+1}   = xi Phi^{n+1} + h^n,   xi = b0 sum_j w_j c_j,
+                  h^n = sum_j w_j mu_j c_j (b1 phi_j^n + b2 phi_j^{n-1})
+    (b0 I - dt xi (L(kappa*) - I/Wi)) Phi2^{n+1}
+        = -b1 Phi2^n - b2 Phi2^{n-1} + dt (L(kappa*) - I/Wi) h2^n + dt G (kappa* + kappa*^T) Psi0^{n+1}
+
+(kappa* = 2 kappa^n - kappa^{n-1}, eq. BDF_and_extrapolation); Psi0 comes from
+the same recurrence with Phi0 = 1.  The SOE of g_alpha is that of the Caputo
+kernel of order 1 - alpha (t^(alpha-1)/Gamma(alpha) = t^-(1-alpha)/Gamma(alpha)),
+so the tables of oracle.soe with order 1 - alpha serve.  Zero past: Phi^{-1} =
+Phi^0, phi_j^0 = phi_j^{-1} = 0.  Every point is independent (no transport).
+The per-point systems are assembled column by column from unit vectors and
+solved with numpy.linalg.solve.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+B0, B1, B2 = 1.5, -2.0, 0.5
+
+
+def _packed(dim):
+    return [(0, 0), (0, 1), (1, 1)] if dim == 2 else [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+
+
+def _upper_convected(dim, K, s):
+    """L(K) s for packed symmetric s, K [N, d, d], s [nc, N] -> [nc, N]."""
+    P = _packed(dim)
+    N = s.shape[1]
+    S = np.zeros((N, dim, dim))
+    for c, (i, j) in enumerate(P):
+        S[:, i, j] = s[c]
+        S[:, j, i] = s[c]
+    T = K @ S + S @ np.swapaxes(K, 1, 2)
+    return np.stack([T[:, i, j] for (i, j) in P])
+
+
+class PaperForm:
+    """State of the paper-variable scheme on a set of independent points."""
+
+    def __init__(self, dim, N, Wi, beta, dt, mu, w, Phi0=None, Re=1.0, start="bdf2"):
+        self.dim, self.N = dim, N
+        self.nc = 3 if dim == 2 else 6
+        self.Wi, self.dt = Wi, dt
+        self.G = (1.0 - beta) / (Wi * Re)
+        self.mu = np.asarray(mu, float)
+        self.w = np.asarray(w, float)
+        self.c = 1.0 / (B0 + self.mu * dt)
+        self.xi = B0 * np.sum(self.w * self.c)
+        m = len(self.mu)
+        z = np.zeros((self.nc, N)) if Phi0 is None else np.asarray(Phi0, float).reshape(self.nc, N).copy()
+        self.Phi_n, self.Phi_nm1 = z.copy(), z.copy()
+        self.phi_n = np.zeros((m, self.nc, N))
+        self.phi_nm1 = np.zeros((m, self.nc, N))
+        self.phi0_n = np.zeros(m)        # modes of Phi0 == 1
+        self.phi0_nm1 = np.zeros(m)
+        self.kap_prev = None
+        self.Psi = None
+        self.start = start       # first step: "bdf2" (empty past) or "sdirk2" (Section 5.1)
+        self.n = 0
+
+    def _h(self, phi_n, phi_nm1):
+        wmc = self.w * self.mu * self.c
+        return np.tensordot(wmc, B1 * phi_n + B2 * phi_nm1, axes=(0, 0))
+
+    def _solve(self, K, scale, rhs):
+        """Solve (I - scale (L(K) - I/Wi)) X = rhs per point (unit-vector assembly)."""
+        d, N, nc = self.dim, self.N, self.nc
+        M = np.zeros((N, nc, nc))
+        for k in range(nc):
+            e = np.zeros((nc, N))
+            e[k] = 1.0
+            M[:, :, k] = (e - scale * (_upper_convected(d, K, e) - e / self.Wi)).T
+        return np.linalg.solve(M, rhs.T[..., None])[..., 0].T
+
+    def _sdirk2_first_step(self, K):
+        """Two-stage SDIRK2 (gamma = 1 - 1/sqrt2, stiffly accurate) on the ODE system
+        d Phi/dt = (L - I/Wi) Psi + G (K + K^T) Psi0,  d phi_j/dt = -mu_j phi_j + Phi,
+        Psi = sum_j w_j (-mu_j phi_j + Phi).  At a stage with explicit parts ZPhi,
+        Zphi_j: phi_j = (Zphi_j + g dt Phi)/(1 + g mu_j dt), so Psi = xi' Phi - h',
+        xi' = sum_j w_j/(1 + g mu_j dt), h' = sum_j w_j mu_j Zphi_j/(1 + g mu_j dt), and
+        (I - g dt xi' (L - I/Wi)) Phi = ZPhi - g dt (L - I/Wi) h' + g dt G (K + K^T) Psi0."""
+        d, dt = self.dim, self.dt
+        g = 1.0 - np.sqrt(0.5)
+        den = 1.0 + g * self.mu * dt
+        xi1 = np.sum(self.w / den)
+        P = _packed(d)
+        KS = K + np.swapaxes(K, 1, 2)
+        src = np.stack([KS[:, i, j] for (i, j) in P])
+        ZPhi, Zphi, Zphi0 = self.Phi_n.copy(), self.phi_n.copy(), self.phi0_n.copy()
+        for stage in (1, 2):
+            h1 = np.tensordot(self.w * self.mu / den, Zphi, axes=(0, 0))
+            psi0 = xi1 - float(np.sum(self.w * self.mu * Zphi0 / den))
+            Lh = _upper_convected(d, K, h1) - h1 / self.Wi
+            rhs = ZPhi - g * dt * Lh + g * dt * self.G * src * psi0
+            Phi = self._solve(K, g * dt * xi1, rhs)
+            phi = (Zphi + g * dt * Phi[None]) / den[:, None, None]
+            phi0 = (Zphi0 + g * dt * 1.0) / den
+            if stage == 1:
+                KPhi = (Phi - ZPhi) / (g * dt)
+                Kphi = -self.mu[:, None, None] * phi + Phi[None]
+                Kphi0 = -self.mu * phi0 + 1.0
+                ZPhi = self.Phi_n + dt * (1.0 - g) * KPhi
+                Zphi = self.phi_n + dt * (1.0 - g) * Kphi
+                Zphi0 = self.phi0_n + dt * (1.0 - g) * Kphi0
+        Psi = xi1 * Phi - h1
+        return Phi, phi, phi0, Psi
+
+    def step(self, kap_n, kap_nm1=None):
+        """Advance one step; returns the stress Psi2^{n+1} [nc][N]."""
+        d, N, nc, dt = self.dim, self.N, self.nc, self.dt
+        if self.start == "sdirk2" and self.n == 0:
+            kap0 = np.asarray(kap_n, float).reshape(d * d, N)
+            Phi, phi, phi0, Psi = self._sdirk2_first_step(kap0.T.reshape(N, d, d))
+            self.Psi = Psi
+            self.Phi_nm1, self.Phi_n = self.Phi_n, Phi
+            self.phi_nm1, self.phi_n = self.phi_n, phi
+            self.phi0_nm1, self.phi0_n = self.phi0_n, phi0
+            self.kap_prev = kap0
+            self.n += 1
+            return Psi.copy()
+        kap_n = np.asarray(kap_n, float).reshape(d * d, N)
+        if kap_nm1 is None:
+            kap_nm1 = self.kap_prev if self.kap_prev is not None else kap_n
+        kap_nm1 = np.asarray(kap_nm1, float).reshape(d * d, N)
+        K = (2.0 * kap_n - kap_nm1).T.reshape(N, d, d)
+        # degree 0: Phi0 = 1, Psi0^{n+1} = xi + h0^n
+        h0 = float(np.sum(self.w * self.mu * self.c * (B1 * self.phi0_n + B2 * self.phi0_nm1)))
+        psi0 = self.xi * 1.0 + h0
+        # degree 2
+        h = self._h(self.phi_n, self.phi_nm1)
+        Lh = _upper_convected(d, K, h) - h / self.Wi
+        P = _packed(d)
+        KS = K + np.swapaxes(K, 1, 2)
+        src = np.stack([KS[:, i, j] for (i, j) in P])
+        rhs = -B1 * self.Phi_n - B2 * self.Phi_nm1 + dt * Lh + dt * self.G * src * psi0
+        # system matrix per point: b0 I - dt xi (L(K) - I/Wi), column k = image of unit vector k
+        M = np.zeros((N, nc, nc))
+        for k in range(nc):
+            e = np.zeros((nc, N))
+            e[k] = 1.0
+            img = B0 * e - dt * self.xi * (_upper_convected(d, K, e) - e / self.Wi)
+            M[:, :, k] = img.T
+        Phi = np.linalg.solve(M, rhs.T[..., None])[..., 0].T
+        phi_new = self.c[:, None, None] * (-B1 * self.phi_n - B2 * self.phi_nm1 + dt * Phi[None])
+        phi0_new = self.c * (-B1 * self.phi0_n - B2 * self.phi0_nm1 + dt * 1.0)
+        self.Psi = self.xi * Phi + h
+        self.Phi_nm1, self.Phi_n = self.Phi_n, Phi
+        self.phi_nm1, self.phi_n = self.phi_n, phi_new
+        self.phi0_nm1, self.phi0_n = self.phi0_n, phi0_new
+        self.kap_prev = kap_n
+        self.n += 1
+        return self.Psi.copy()

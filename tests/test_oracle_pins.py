@@ -317,7 +317,8 @@ def test_reference_adjoint_matches_finite_differences(dim, transport, alpha):
         assert close(g["kappa"][c, q], fd(fk, kap[c, q]))
 
 
-def _paper_case_bochner_errors(start, m, dts):
+def _paper_case_bochner_errors(start, m, dts, fit_from=1e-3):
+    # the SOE table is fitted on [fit_from * dt, T]
     alpha, Wi, eps, T = 0.5, 1.0, 1e-2, 1.0
     n = (8, 8)
     N = n[0] * n[1]
@@ -331,7 +332,7 @@ def _paper_case_bochner_errors(start, m, dts):
     errs = []
     for dt in dts:
         steps = int(round(T / dt))
-        mu, w = soe.soe_nnls(alpha, dt, T, m)
+        mu, w = soe.soe_nnls(alpha, dt * fit_from, T, m)
         prob = orc.Problem(dim=2, n=n, alpha=alpha, Wi=Wi, beta=0.5, dt=dt, mu=mu, w=w, eps=eps, L=(1.0, 1.0),
                            transport=True, implicit=True, start=start)
         o = orc.Oracle(prob, sigma0)
@@ -347,6 +348,13 @@ def _paper_case_bochner_errors(start, m, dts):
     return errs
 
 
+def _orders(errs):
+    return [float(np.log2(errs[i] / errs[i + 1])) for i in range(len(errs) - 1)]
+
+
+DTS_PAPER_CASE = [1 / 20, 1 / 40, 1 / 80, 1 / 160]
+
+
 def test_paper_first_convergence_case_bochner_norm():
     # The paper's convergence case (Section 5.1): no flow, unit square, initial
     # stress cos(2 pi x) cos(4 pi y), eps = 1e-2, De = 0.5 (Wi = 2 De, reading
@@ -355,16 +363,58 @@ def test_paper_first_convergence_case_bochner_norm():
     # periodic grid the solution is the initial field times E_alpha(-lambda_h
     # t^alpha), lambda_h = 1/Wi + eps x (discrete Laplacian symbol) -> 1/Wi +
     # 20 eps pi^2, so the error is that of time stepping and kernel compression.
-    # The stress-form scheme built here converges at order 1.1 - 1.3 in this
-    # norm with either first step -- the empty-past BDF2 start (reading G11) or
-    # the paper's SDIRK2 start, which lowers the error at coarse steps; the
-    # 1 + alpha the paper reports (its Fig. 2a) belongs to its own variable,
-    # D^{1-alpha} Phi with kernel g_alpha (reading G1), not built here.
-    dts = [1 / 20, 1 / 40, 1 / 80, 1 / 160]
-    bdf = _paper_case_bochner_errors("bdf2", 16, dts)
-    sdirk = _paper_case_bochner_errors("sdirk2", 16, dts)
-    orders = [np.log2(bdf[i] / bdf[i + 1]) for i in range(len(dts) - 1)]
-    assert all(1.0 < q < 1.4 for q in orders), orders
-    assert all(sdirk[i + 1] < sdirk[i] for i in range(len(dts) - 1)), sdirk
-    assert sdirk[0] < 0.8 * bdf[0]
-    assert sdirk[-1] < 2e-3 * 0.2
+    # The paper reports order 1 + alpha (its Fig. 2a) with an SDIRK2 first
+    # step.  The stress-form scheme reaches it too, given that start and an SOE
+    # table fitted down to 1e-3 dt (the kernel's mass below the fitted range is
+    # otherwise missing from every step); the empty-past BDF2 start gives
+    # order 1 whatever the table.
+    sdirk = _orders(_paper_case_bochner_errors("sdirk2", 32, DTS_PAPER_CASE))
+    bdf = _orders(_paper_case_bochner_errors("bdf2", 32, DTS_PAPER_CASE))
+    assert all(q > 1.3 for q in sdirk) and sdirk[-1] > 1.38, sdirk
+    assert sdirk == sorted(sdirk), sdirk
+    assert all(0.95 < q < 1.1 for q in bdf), bdf
+
+
+def test_paper_variable_scheme_convergence_and_agreement():
+    # The scheme in the paper's own variable (oracle.paper_form: BDF2 on Phi,
+    # Psi = D^{1-alpha} Phi through kernel compression of g_alpha) on the same
+    # decay, one point with the diffusion of the single Fourier mode folded
+    # into the rate (exact for an eigenfunction of the Laplacian): order
+    # -> 1 + alpha with the SDIRK2 start.  Then, from rest under the smooth
+    # sin^2 ramp of the forcing (Section 5.1), its stress Psi2 and the stress
+    # form's sigma approach each other as dt -> 0.
+    from oracle.paper_form import PaperForm
+    alpha, T = 0.5, 1.0
+    lam = 1.0 + 20 * 1e-2 * np.pi ** 2
+    errs = []
+    for dt in DTS_PAPER_CASE:
+        mu, w = soe.soe_nnls(1 - alpha, dt * 1e-3, T, 32)
+        pf = PaperForm(2, 1, 1.0 / lam, 0.5, dt, mu, w, Phi0=np.ones((3, 1)), start="sdirk2")
+        acc = 0.0
+        steps = int(round(T / dt))
+        for k in range(1, steps + 1):
+            pf.step(np.zeros((4, 1)))
+            t = k * dt
+            e2 = (pf.Phi_n[0, 0] - special.mittag_leffler(alpha, -lam * t ** alpha)) ** 2
+            acc += (0.5 if k == steps else 1.0) * e2 * t ** (2 * (1 - alpha)) * dt
+        errs.append(np.sqrt(acc))
+    q = _orders(errs)
+    assert all(x > 1.3 for x in q) and q[-1] > 1.4, q
+
+    rng = np.random.default_rng(4)
+    N, Wi, beta, T2 = 6, 1.3, 0.4, 0.5
+    K0 = 0.6 * rng.normal(size=(4, N))
+    ramp = lambda t: np.sin(0.5 * np.pi * min(max(0.0, 4 * t - 1), 1.0)) ** 2
+    diffs = []
+    for dt in [1 / 40, 1 / 80, 1 / 160]:
+        steps = int(round(T2 / dt))
+        mu_s, w_s = soe.soe_nnls(alpha, dt * 1e-3, T2, 32)
+        o = orc.Oracle(orc.Problem(dim=2, n=(N, 1), alpha=alpha, Wi=Wi, beta=beta, dt=dt, mu=mu_s, w=w_s), None)
+        mu_p, w_p = soe.soe_nnls(1 - alpha, dt * 1e-3, T2, 32)
+        pf = PaperForm(2, N, Wi, beta, dt, mu_p, w_p)
+        for k in range(steps):
+            kap, kprev = K0 * ramp(k * dt), K0 * ramp(max(k - 1, 0) * dt)
+            o.step(kap, kprev)
+            psi = pf.step(kap, kprev)
+        diffs.append(np.max(np.abs(o.sig_n - psi)) / np.max(np.abs(o.sig_n)))
+    assert diffs[-1] < diffs[0] / 3 and diffs[-1] < 1e-2, diffs
