@@ -89,8 +89,20 @@ enum {
     TFS_PARAM_UMAX = 4,       /* declared bound U on |u_a|; checked against tfs_transport_limit */
     TFS_PARAM_KRYLOV_TOL = 5, /* implicit transport: relative residual target, default 1e-13 (FP64)
                                  or 1e-9 (FP32 storage) */
-    TFS_PARAM_KRYLOV_MAXIT = 6 /* implicit transport: iteration limit, default 500 */
+    TFS_PARAM_KRYLOV_MAXIT = 6, /* implicit transport: iteration limit, default 500 */
+    TFS_PARAM_START = 7       /* first step from the initial state, TFS_START_*: BDF2 with an empty
+                                 past (default), or the two-stage SDIRK2 the paper takes for
+                                 non-trivial initial data (Section 5.1; gamma = 1 - 1/sqrt2, stiffly
+                                 accurate, L-stable; kappa of the first call, both stage systems solved
+                                 in FP64).  SDIRK2 needs alpha < 1 (else TFS_ERR_ARG here) and transport
+                                 0 or 2: with explicit transport the first tfs_step returns TFS_ERR_ARG.
+                                 With transport 2 both stage systems go through the implicit solver
+                                 (tfs_last_solve: iterations summed, larger residual).  tfs_backward
+                                 refuses a handle with this start (TFS_ERR_ARG) */
 };
+
+/* first-step methods (TFS_PARAM_START) */
+enum { TFS_START_BDF2 = 0, TFS_START_SDIRK2 = 1 };
 
 enum { TFS_STENCIL_UPWIND3 = 0, TFS_STENCIL_CENTRAL2 = 1 };
 

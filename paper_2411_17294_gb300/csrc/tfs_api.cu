@@ -38,6 +38,7 @@ struct tfs_ctx {
     int precision = TFS_FP64;
     int stencil = TFS_STENCIL_UPWIND3;
     int transport = 1;
+    int start = TFS_START_BDF2;    // first step from the initial state
     double umax = -1.0;            // declared velocity bound (< 0: none)
     // SOE
     bool soe_set = false;
@@ -387,6 +388,79 @@ int do_step_implicit(tfs_ctx* h, const void* kn, const void* knm1, const void* u
     return TFS_OK;
 }
 
+// SDIRK2 constants of the first step (Section 5.1): gamma = 1 - 1/sqrt2,
+// 1/(1 + gamma mu_j dt), W = sum_j w_j/(1 + gamma mu_j dt), g_alpha at both stage times
+StartConsts start_consts(const tfs_ctx* h) {
+    StartConsts c{};
+    c.gam = 1.0 - std::sqrt(0.5);
+    c.W = 0.0;
+    for (int j = 0; j < h->m; ++j) {
+        c.mu[j] = h->mu[j];
+        c.w[j] = h->w[j];
+        c.inv_den[j] = 1.0 / (1.0 + c.gam * h->mu[j] * h->dt);
+        c.W += h->w[j] * c.inv_den[j];
+    }
+    c.g[0] = std::pow(c.gam * h->dt, h->alpha - 1.0) / std::tgamma(h->alpha);
+    c.g[1] = std::pow(h->dt, h->alpha - 1.0) / std::tgamma(h->alpha);
+    return c;
+}
+
+// The first step by SDIRK2: pointwise (transport off, tfs_start.cu) or with the
+// implicit transport inside both stage systems (tfs_implicit.cu).  The stress
+// and mode rings then advance as after any step: level n-1 = the initial state.
+int do_first_step_sdirk2(tfs_ctx* h, const void* kn, const void* u, void* sig_copy, cudaStream_t s) {
+    if (h->explicit_transport()) return TFS_ERR_ARG;
+    const StartConsts c = start_consts(h);
+    const int nxt = h->third_sig();
+    const int cm = h->cur_mode, pm = 1 - h->cur_mode;
+    const double a_stage = h->dt * c.W + h->dt / h->Wi;
+    cudaError_t e;
+    if (h->implicit_transport()) {
+        if (!h->kry || h->ws_bytes < forward_bytes(h)) return TFS_ERR_NOWORKSPACE;
+        int iters = 0;
+        double relres = 0.0;
+        if (h->is_double()) {
+            ImpArgs<double> a{};
+            fill_implicit(h, a, kn, kn, u, sig_copy, nxt, cm, pm);
+            a.mc = h->mcd;
+            a.a = a_stage;
+            e = run_start_implicit_f64(a, c, s, &iters, &relres);
+        } else {
+            ImpArgs<float> a{};
+            fill_implicit(h, a, kn, kn, u, sig_copy, nxt, cm, pm);
+            a.mc = h->mcf;
+            a.a = a_stage;
+            e = run_start_implicit_f32(a, c, s, &iters, &relres);
+        }
+        h->last_iters = iters;
+        h->last_relres = relres;
+    } else {
+        if (h->ev_before) e = cudaEventRecord(h->ev_before, s);
+        else e = cudaSuccess;
+        if (e == cudaSuccess && h->is_double()) {
+            StartArgs<double> a{(const double*)kn, h->sigma0_zero ? nullptr : (const double*)h->sigma0,
+                                (const double*)h->modes[cm], (double*)h->modes[pm], (double*)h->sig[nxt],
+                                (double*)sig_copy, h->flags, h->N, h->m, h->dt, a_stage,
+                                (1.0 - h->beta) / (h->Wi * h->Re)};
+            e = launch_start_point_f64(a, c, h->dim, s);
+        } else if (e == cudaSuccess) {
+            StartArgs<float> a{(const float*)kn, h->sigma0_zero ? nullptr : (const float*)h->sigma0,
+                               (const float*)h->modes[cm], (float*)h->modes[pm], (float*)h->sig[nxt],
+                               (float*)sig_copy, h->flags, h->N, h->m, h->dt, a_stage,
+                               (1.0 - h->beta) / (h->Wi * h->Re)};
+            e = launch_start_point_f32(a, c, h->dim, s);
+        }
+        if (e == cudaSuccess && h->ev_after) e = cudaEventRecord(h->ev_after, s);
+    }
+    if (e != cudaSuccess) return TFS_ERR_CUDA;
+    h->prev_sig = h->cur_sig;
+    h->cur_sig = nxt;
+    h->cur_mode = pm;
+    h->step += 1;
+    h->last_stream = s;
+    return TFS_OK;
+}
+
 int do_step(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* sig_copy, cudaStream_t s) {
     if (!h->ws) return TFS_ERR_NOWORKSPACE;
     if (!h->state_set) return TFS_ERR_STATE;
@@ -395,6 +469,7 @@ int do_step(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* s
     if (h->transport && !u) return TFS_ERR_ARG;
     if (limits_violated(h)) return TFS_ERR_UNSTABLE;
     if (!knm1) knm1 = kn;
+    if (h->start == TFS_START_SDIRK2 && h->step == 0) return do_first_step_sdirk2(h, kn, u, sig_copy, s);
     if (h->implicit_transport()) return do_step_implicit(h, kn, knm1, u, sig_copy, s);
     const int nxt = h->third_sig();
     const int cm = h->cur_mode, pm = 1 - h->cur_mode;
@@ -527,6 +602,11 @@ int tfs_set_param(tfs_handle h, int key, double value) {
         case TFS_PARAM_KRYLOV_MAXIT:
             if (!(value >= 1.0 && value <= 100000.0) || value != std::floor(value)) return TFS_ERR_ARG;
             h->krylov_maxit = (int)value;
+            return TFS_OK;
+        case TFS_PARAM_START:
+            if (value != TFS_START_BDF2 && value != TFS_START_SDIRK2) return TFS_ERR_ARG;
+            if (value == TFS_START_SDIRK2 && h->classic()) return TFS_ERR_ARG;
+            h->start = (int)value;
             return TFS_OK;
         default:
             return TFS_ERR_ARG;
@@ -782,6 +862,7 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
                  const void* grad_u, const void* u, double* dJ_dsigma0, double* dJ_dgrad_u, double* dJ_dWi,
                  double* dJ_dbeta, void* stream) {
     if (valid_handle(h) && h->implicit_transport()) return TFS_ERR_ARG;   // adjoint of the implicit step not built
+    if (valid_handle(h) && h->start == TFS_START_SDIRK2) return TFS_ERR_ARG;   // nor of the SDIRK2 first step
     if (!valid_handle(h) || !dJ_dsigma_T || !checkpoints || !grad_u || !dJ_dsigma0 || !dJ_dgrad_u || !dJ_dWi ||
         !dJ_dbeta)
         return TFS_ERR_ARG;

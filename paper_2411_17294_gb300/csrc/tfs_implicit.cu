@@ -391,21 +391,94 @@ __global__ void __launch_bounds__(kThreads) imp_init_kernel(long long n, const d
     }
 }
 
+// ------------------------------------------------------------------ first step (SDIRK2)
+// Stage right-hand side over the grid: b = dt W sigma0 + dt sum_j mu_j Z_j/(1 + gamma mu_j dt)
+// + dt G (kappa^0 + kappa^0T) g_alpha(t_i), Z the explicit mode stage; x0 = sigma^0 when given.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) start_rhs_kernel(const ImpArgs<T> A, const StartConsts C, int stage,
+                                                             const T* Z, double* b, double* x0) {
+    constexpr int NC = Packed<DIM>::NC;
+    const long long N = A.N;
+    const double gs = C.g[stage - 1];
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const long long qc = (long long)c * N + p;
+            const int i = Packed<DIM>::I(c), j = Packed<DIM>::J(c);
+            const double ks = (double)A.kap_n[(long long)(i * DIM + j) * N + p] +
+                              (double)A.kap_n[(long long)(j * DIM + i) * N + p];
+            const double s0 = A.sigma0 ? (double)A.sigma0[qc] : 0.0;
+            double zs = 0.0;
+            for (int jj = 0; jj < A.m; ++jj)
+                zs = fma(C.mu[jj] * C.inv_den[jj], (double)Z[((long long)jj * NC + c) * N + p], zs);
+            b[qc] = A.dt * (C.W * s0 + zs + A.G * ks * gs);
+            if (x0) x0[qc] = (double)A.sig_n[qc];
+        }
+    }
+}
+
+// After stage 1 (x = S1): the level-(n-1) slot receives the stage-2 explicit part
+//   Z_j = sigma_j^0 + dt (1 - gamma) K_j,  K_j = (-mu_j sigma_j^0 + w_j (S1 - sigma0)) / (1 + gamma mu_j dt).
+// After stage 2 (x = S2): sigma^1 = S2 and sigma_j^1 = Z_j + gamma dt K_j with K_j from Z_j and S2.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) start_push_kernel(const ImpArgs<T> A, const StartConsts C, int stage,
+                                                              const double* x) {
+    constexpr int NC = Packed<DIM>::NC;
+    const long long N = A.N;
+    const double f = stage == 1 ? A.dt * (1.0 - C.gam) : A.dt * C.gam;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        bool finite = true;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const long long qc = (long long)c * N + p;
+            const double s0 = A.sigma0 ? (double)A.sigma0[qc] : 0.0;
+            const double d = x[qc] - s0;
+            for (int jj = 0; jj < A.m; ++jj) {
+                const long long q = ((long long)jj * NC + c) * N + p;
+                const double z = stage == 1 ? (double)A.modes_n[q] : (double)A.modes_nm1[q];
+                const double kj = (-C.mu[jj] * z + C.w[jj] * d) * C.inv_den[jj];
+                A.modes_nm1[q] = (T)fma(f, kj, z);
+            }
+            if (stage == 2) {
+                const T out = (T)x[qc];
+                finite = finite && isfinite((double)out);
+                A.sig_np1[qc] = out;
+                if (A.sig_copy) A.sig_copy[qc] = out;
+            }
+        }
+        if (!finite) atomicOr(A.flags, 1u);
+    }
+}
+
 // ------------------------------------------------------------------ host side
-template <typename T, int DIM, bool COMP>
-cudaError_t run_implicit(const ImpArgs<T>& a, cudaStream_t st, int* iters, double* relres) {
+// Krylov workspace views (10 vectors of nc N, the point blocks and the
+// preconditioner inverses, partial sums, device scalars)
+template <int NC>
+struct KryView {
+    double *b, *x, *r, *rh, *p, *v, *sv, *t, *ph, *sh, *Mb, *Pinv, *partials, *sc;
+    KryView(double* w, double* parts, long long N) {
+        const long long n = (long long)NC * N;
+        b = w; x = w + n; r = w + 2 * n; rh = w + 3 * n; p = w + 4 * n; v = w + 5 * n; sv = w + 6 * n;
+        t = w + 7 * n; ph = w + 8 * n; sh = w + 9 * n;
+        Mb = w + 10 * n;
+        Pinv = Mb + (long long)NC * NC * N;
+        partials = parts;
+        sc = parts + kPartialSets * kImpBlocks;
+    }
+};
+
+// BiCGStab on Op x = b from the initial guess in x (b and x filled, Mb and Pinv
+// set up, all on stream st).  Leaves the last iterate in x, latches
+// TFS_FLAG_NOCONV when the tolerance was not reached; synchronises st.
+template <typename T, int DIM>
+cudaError_t krylov_solve(const ImpArgs<T>& a, const KryView<Packed<DIM>::NC>& K, cudaStream_t st, int* iters,
+                         double* relres) {
     constexpr int NC = Packed<DIM>::NC;
     const long long N = a.N;
     const long long n = (long long)NC * N;
     const unsigned bs = (unsigned)kImpBlocks;
-    // workspace: 10 vectors, the point blocks and preconditioner inverses, partial sums, scalars
-    double* w = a.kry;
-    double *b = w, *x = w + n, *r = w + 2 * n, *rh = w + 3 * n, *p = w + 4 * n, *v = w + 5 * n, *sv = w + 6 * n,
-           *t = w + 7 * n, *ph = w + 8 * n, *sh = w + 9 * n;
-    double* Mb = w + 10 * n;
-    double* Pinv = Mb + (long long)NC * NC * N;
-    double* partials = a.partials;
-    double* sc = partials + kPartialSets * kImpBlocks;
+    double* partials = K.partials;
+    double* sc = K.sc;
     cudaError_t e = cudaSuccess;
     auto ok = [&]() {
         if (e == cudaSuccess) e = cudaGetLastError();
@@ -416,11 +489,7 @@ cudaError_t run_implicit(const ImpArgs<T>& a, cudaStream_t st, int* iters, doubl
     hs[S_TOL2] = a.tol * a.tol;
     e = cudaMemcpyAsync(sc, hs, sizeof(hs), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
-    imp_setup_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, Mb, Pinv);
-    if (!ok()) return e;
-    imp_rhs_kernel<T, DIM, COMP><<<bs, kThreads, 0, st>>>(a, b, x);
-    if (!ok()) return e;
-    imp_dot2_kernel<<<bs, kThreads, 0, st>>>(b, b, nullptr, n, partials);
+    imp_dot2_kernel<<<bs, kThreads, 0, st>>>(K.b, K.b, nullptr, n, partials);
     if (!ok()) return e;
     imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 3);
     if (!ok()) return e;
@@ -430,16 +499,16 @@ cudaError_t run_implicit(const ImpArgs<T>& a, cudaStream_t st, int* iters, doubl
     const double bnorm2 = hs[S_BNORM2];
     bool converged = false;
     if (bnorm2 == 0.0) {
-        e = cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, st);   // R = 0: sigma^{n+1} = 0
+        e = cudaMemsetAsync(K.x, 0, sizeof(double) * (size_t)n, st);   // b = 0: x = 0
         converged = true;
         hs[S_RR] = 0.0;
         hs[S_ITERS] = 0.0;
     } else {
-        imp_apply_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, Mb, x, r, nullptr, nullptr, partials, sc);
+        imp_apply_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.x, K.r, nullptr, nullptr, partials, sc);
         if (!ok()) return e;
-        imp_init_kernel<<<bs, kThreads, 0, st>>>(n, b, r, rh, p, v);
+        imp_init_kernel<<<bs, kThreads, 0, st>>>(n, K.b, K.r, K.rh, K.p, K.v);
         if (!ok()) return e;
-        imp_dot2_kernel<<<bs, kThreads, 0, st>>>(r, r, rh, n, partials);
+        imp_dot2_kernel<<<bs, kThreads, 0, st>>>(K.r, K.r, K.rh, n, partials);
         if (!ok()) return e;
         imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 4);
         if (!ok()) return e;
@@ -447,13 +516,13 @@ cudaError_t run_implicit(const ImpArgs<T>& a, cudaStream_t st, int* iters, doubl
         constexpr int kCheck = 8;
         for (int it = 0; it < a.maxit; ++it) {
             imp_beta_kernel<<<1, 1, 0, st>>>(sc);
-            imp_comb_precond_kernel<NC><<<bs, kThreads, 0, st>>>(N, Pinv, 0, p, r, v, ph, sc);
-            imp_apply_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, Mb, ph, v, rh, nullptr, partials, sc);
+            imp_comb_precond_kernel<NC><<<bs, kThreads, 0, st>>>(N, K.Pinv, 0, K.p, K.r, K.v, K.ph, sc);
+            imp_apply_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.ph, K.v, K.rh, nullptr, partials, sc);
             imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 1);
-            imp_comb_precond_kernel<NC><<<bs, kThreads, 0, st>>>(N, Pinv, 1, sv, r, v, sh, sc);
-            imp_apply_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, Mb, sh, t, sv, t, partials, sc);
+            imp_comb_precond_kernel<NC><<<bs, kThreads, 0, st>>>(N, K.Pinv, 1, K.sv, K.r, K.v, K.sh, sc);
+            imp_apply_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.sh, K.t, K.sv, K.t, partials, sc);
             imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 2);
-            imp_xr_kernel<<<bs, kThreads, 0, st>>>(n, x, ph, sh, r, sv, t, rh, partials, sc);
+            imp_xr_kernel<<<bs, kThreads, 0, st>>>(n, K.x, K.ph, K.sh, K.r, K.sv, K.t, K.rh, partials, sc);
             imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 0);
             if (!ok()) return e;
             if ((it + 1) % kCheck == 0 || it + 1 == a.maxit) {
@@ -477,10 +546,54 @@ cudaError_t run_implicit(const ImpArgs<T>& a, cudaStream_t st, int* iters, doubl
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return e;
     }
-    imp_push_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, x);
-    if (!ok()) return e;
     *iters = (int)hs[S_ITERS];
     *relres = bnorm2 > 0.0 ? std::sqrt(hs[S_RR] / bnorm2) : 0.0;
+    return e;
+}
+
+template <typename T, int DIM, bool COMP>
+cudaError_t run_implicit(const ImpArgs<T>& a, cudaStream_t st, int* iters, double* relres) {
+    constexpr int NC = Packed<DIM>::NC;
+    const KryView<NC> K(a.kry, a.partials, a.N);
+    const unsigned bs = (unsigned)kImpBlocks;
+    imp_setup_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Pinv);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    imp_rhs_kernel<T, DIM, COMP><<<bs, kThreads, 0, st>>>(a, K.b, K.x);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = krylov_solve<T, DIM>(a, K, st, iters, relres);
+    if (e != cudaSuccess) return e;
+    imp_push_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.x);
+    return cudaGetLastError();
+}
+
+template <typename T, int DIM>
+cudaError_t run_start_implicit(const ImpArgs<T>& a, const StartConsts& c, cudaStream_t st, int* iters,
+                               double* relres) {
+    constexpr int NC = Packed<DIM>::NC;
+    const KryView<NC> K(a.kry, a.partials, a.N);
+    const unsigned bs = (unsigned)kImpBlocks;
+    imp_setup_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Pinv);
+    cudaError_t e = cudaGetLastError();
+    *iters = 0;
+    *relres = 0.0;
+    for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage) {
+        // stage 1 reads the level-0 modes and starts from sigma^0; stage 2 reads the
+        // explicit part written by the first push and starts from S1 (left in x)
+        start_rhs_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, c, stage, stage == 1 ? a.modes_n : a.modes_nm1, K.b,
+                                                          stage == 1 ? K.x : nullptr);
+        e = cudaGetLastError();
+        int it = 0;
+        double rr = 0.0;
+        if (e == cudaSuccess) e = krylov_solve<T, DIM>(a, K, st, &it, &rr);
+        *iters += it;
+        *relres = rr > *relres ? rr : *relres;
+        if (e == cudaSuccess) {
+            start_push_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, c, stage, K.x);
+            e = cudaGetLastError();
+        }
+    }
     return e;
 }
 
@@ -495,6 +608,18 @@ cudaError_t run_implicit_f32(const ImpArgs<float>& a, cudaStream_t s, bool comp,
     if (a.dim == 2)
         return comp ? run_implicit<float, 2, true>(a, s, iters, relres) : run_implicit<float, 2, false>(a, s, iters, relres);
     return comp ? run_implicit<float, 3, true>(a, s, iters, relres) : run_implicit<float, 3, false>(a, s, iters, relres);
+}
+
+cudaError_t run_start_implicit_f64(const ImpArgs<double>& a, const StartConsts& c, cudaStream_t s, int* iters,
+                                   double* relres) {
+    return a.dim == 2 ? run_start_implicit<double, 2>(a, c, s, iters, relres)
+                      : run_start_implicit<double, 3>(a, c, s, iters, relres);
+}
+
+cudaError_t run_start_implicit_f32(const ImpArgs<float>& a, const StartConsts& c, cudaStream_t s, int* iters,
+                                   double* relres) {
+    return a.dim == 2 ? run_start_implicit<float, 2>(a, c, s, iters, relres)
+                      : run_start_implicit<float, 3>(a, c, s, iters, relres);
 }
 
 }  // namespace tfs

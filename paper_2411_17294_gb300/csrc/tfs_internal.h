@@ -119,6 +119,45 @@ constexpr int kImpBlocks = 1024;   // blocks of the implicit-step kernels (and r
 cudaError_t run_implicit_f64(const ImpArgs<double>& a, cudaStream_t s, int* iters, double* relres);
 cudaError_t run_implicit_f32(const ImpArgs<float>& a, cudaStream_t s, bool compensated, int* iters, double* relres);
 
+// First step t_0 -> t_1 by two-stage SDIRK2 (gamma = 1 - 1/sqrt2, stiffly
+// accurate, L-stable; Section 5.1) on the mode ODEs
+//   d sigma_j/dt = -mu_j sigma_j + w_j (sigma - sigma0),  sum_j d sigma_j/dt = F(sigma, t),
+// each stage solving (dt W + dt/Wi) S - dt L(kappa^0) S [+ dt (u.grad - eps Lap) S]
+//   = dt W sigma0 + dt sum_j mu_j Z_j / (1 + gamma mu_j dt) + dt G (kappa^0 + kappa^0T) g_alpha(t_i),
+// W = sum_j w_j / (1 + gamma mu_j dt), Z_j the explicit part of the mode stage.
+struct StartConsts {
+    double mu[kMaxModes], w[kMaxModes];
+    double inv_den[kMaxModes];   // 1 / (1 + gamma mu_j dt)
+    double W, gam;
+    double g[2];                 // g_alpha(gamma dt), g_alpha(dt)
+};
+
+// Arguments of the pointwise first step (transport off): level-0 fields in,
+// sigma^1 and the level-1 modes out; all arithmetic in FP64.
+template <typename T>
+struct StartArgs {
+    const T* kap0;         // [d*d][N]
+    const T* sigma0;       // [nc][N] or nullptr for zero
+    const T* modes0;       // [m][nc][N] level 0
+    T* modes1;             // [m][nc][N] level 1 (out)
+    T* sig1;               // [nc][N] (out)
+    T* sig_copy;           // optional second destination of sigma^1
+    unsigned* flags;
+    long long N;
+    int m;
+    double dt, a, G;       // a = dt W + dt/Wi
+};
+
+cudaError_t launch_start_point_f64(const StartArgs<double>& a, const StartConsts& c, int dim, cudaStream_t s);
+cudaError_t launch_start_point_f32(const StartArgs<float>& a, const StartConsts& c, int dim, cudaStream_t s);
+// implicit transport: the two stage systems by the Krylov solver of the implicit step
+// (a.a, a.kap_n = a.kap_nm1 = kappa^0 set by the caller); synchronises `s`;
+// iterations summed and the larger relative residual of the two stages
+cudaError_t run_start_implicit_f64(const ImpArgs<double>& a, const StartConsts& c, cudaStream_t s, int* iters,
+                                   double* relres);
+cudaError_t run_start_implicit_f32(const ImpArgs<float>& a, const StartConsts& c, cudaStream_t s, int* iters,
+                                   double* relres);
+
 struct LaunchCfg {
     int dim;
     int stencil;       // 0 upwind3, 1 central2

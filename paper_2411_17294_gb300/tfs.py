@@ -20,7 +20,8 @@ TFS_OK, TFS_ERR_ARG, TFS_ERR_NOSOE, TFS_ERR_UNSTABLE, TFS_ERR_CUDA, TFS_ERR_STAT
     TFS_ERR_FORMAT, TFS_ERR_TOOBIG = range(9)
 TFS_FP64, TFS_FP32, TFS_FP32_PLAIN = 0, 1, 2
 (TFS_PARAM_RE, TFS_PARAM_EPS, TFS_PARAM_STENCIL, TFS_PARAM_TRANSPORT, TFS_PARAM_UMAX, TFS_PARAM_KRYLOV_TOL,
- TFS_PARAM_KRYLOV_MAXIT) = range(7)
+ TFS_PARAM_KRYLOV_MAXIT, TFS_PARAM_START) = range(8)
+TFS_START_BDF2, TFS_START_SDIRK2 = 0, 1
 TFS_STENCIL_UPWIND3, TFS_STENCIL_CENTRAL2 = 0, 1
 TFS_FLAG_NONFINITE, TFS_FLAG_SINGULAR, TFS_FLAG_COURANT, TFS_FLAG_TIMEOUT, TFS_FLAG_NOCONV = 1, 2, 4, 8, 16
 
@@ -127,7 +128,7 @@ class Solver:
 
     def __init__(self, dim: int, n, alpha: float, Wi: float, beta: float, dt: float, m: int = 0,
                  precision: int = TFS_FP64, L=None, mu=None, w=None, Re: float = 1.0, eps: float = 0.0,
-                 stencil: int = TFS_STENCIL_UPWIND3, transport=True, device=None):
+                 stencil: int = TFS_STENCIL_UPWIND3, transport=True, device=None, start: str = "bdf2"):
         torch = _torch()
         lib = load_library()
         self.lib = lib
@@ -157,6 +158,12 @@ class Solver:
         check(lib.tfs_set_param(h, TFS_PARAM_STENCIL, float(stencil)), "tfs_set_param(stencil)")
         check(lib.tfs_set_param(h, TFS_PARAM_TRANSPORT, 2.0 if self.implicit else (1.0 if transport else 0.0)),
               "tfs_set_param(transport)")
+        # first step: "bdf2" (empty past) or "sdirk2" (Section 5.1; alpha < 1, transport off or implicit)
+        if start not in ("bdf2", "sdirk2"):
+            raise ValueError("start must be 'bdf2' or 'sdirk2'")
+        self.start = start
+        check(lib.tfs_set_param(h, TFS_PARAM_START, float(TFS_START_SDIRK2 if start == "sdirk2" else TFS_START_BDF2)),
+              "tfs_set_param(start)")
         if mu is not None:
             self.set_soe(mu, w)
         nbytes = lib.tfs_workspace_bytes(h)
