@@ -90,7 +90,7 @@ enum {
     TFS_PARAM_KRYLOV_TOL = 5, /* implicit transport: relative residual target, default 1e-13 (FP64)
                                  or 1e-9 (FP32 storage) */
     TFS_PARAM_KRYLOV_MAXIT = 6, /* implicit transport: iteration limit, default 500 */
-    TFS_PARAM_START = 7       /* first step from the initial state, TFS_START_*: BDF2 with an empty
+    TFS_PARAM_START = 7,      /* first step from the initial state, TFS_START_*: BDF2 with an empty
                                  past (default), or the two-stage SDIRK2 the paper takes for
                                  non-trivial initial data (Section 5.1; gamma = 1 - 1/sqrt2, stiffly
                                  accurate, L-stable; kappa of the first call, both stage systems solved
@@ -99,10 +99,24 @@ enum {
                                  With transport 2 both stage systems go through the implicit solver
                                  (tfs_last_solve: iterations summed, larger residual).  tfs_backward
                                  refuses a handle with this start (TFS_ERR_ARG) */
+    TFS_PARAM_FORM = 8        /* variable carried, TFS_FORM_*: the stress (default), or the paper's own
+                                 variable (Section 3.4): Phi with d Phi/dt = (L(kappa) - I/Wi) Psi +
+                                 G (kappa + kappa^T) Psi0, Psi = D^{1-alpha} Phi by kernel compression of
+                                 g_alpha = t^(alpha-1)/Gamma(alpha), so the SOE table of tfs_set_soe
+                                 approximates g_alpha (the Caputo kernel of order 1 - alpha); Psi0 =
+                                 D^{1-alpha} 1 from the same modes, on the host.  The stress returned is
+                                 Psi (zero before the first step); tfs_set_state sets Phi(0) (NULL: 0).
+                                 BDF2 on Phi and the modes (Section 4.1), one point system per point.
+                                 Needs alpha < 1 (else TFS_ERR_ARG here), transport 0 and the BDF2 start
+                                 (else tfs_step returns TFS_ERR_ARG); tfs_backward refuses it (TFS_ERR_ARG).
+                                 Changing the form discards the state (call tfs_set_state again) */
 };
 
 /* first-step methods (TFS_PARAM_START) */
 enum { TFS_START_BDF2 = 0, TFS_START_SDIRK2 = 1 };
+
+/* variables carried (TFS_PARAM_FORM) */
+enum { TFS_FORM_STRESS = 0, TFS_FORM_PAPER = 1 };
 
 enum { TFS_STENCIL_UPWIND3 = 0, TFS_STENCIL_CENTRAL2 = 1 };
 
@@ -171,7 +185,8 @@ int tfs_set_state(tfs_handle h, const void* sigma0, void* stream);
    transport is on. */
 int tfs_step(tfs_handle h, const void* grad_u_n, const void* grad_u_nm1, const void* u, void* stream);
 
-/* Copy the current stress sigma^n to out [nc][N] (device). */
+/* Copy the current stress sigma^n to out [nc][N] (device); with TFS_FORM_PAPER
+   the stress Psi^n. */
 int tfs_get_stress(tfs_handle h, void* out, void* stream);
 
 /* Measurement hook (no counterpart in the paper): with two cudaEvent_t
@@ -190,7 +205,8 @@ long tfs_step_index(tfs_handle h);
 int tfs_last_solve(tfs_handle h, int* iterations, double* relative_residual);
 
 /* Checkpoints: a device buffer holding the full state (header, stress at
-   levels n and n-1, modes at levels n and n-1). */
+   levels n and n-1, the initial stress, modes at levels n and n-1; with
+   TFS_FORM_PAPER the levels of Phi in place of the stress, then Psi^n). */
 size_t tfs_checkpoint_bytes(tfs_handle h);
 int tfs_save(tfs_handle h, void* dst, void* stream);
 /* Restore a checkpoint written by tfs_save on a handle of the same shape and

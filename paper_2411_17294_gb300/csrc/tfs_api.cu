@@ -19,7 +19,7 @@ using namespace tfs;
 namespace {
 
 constexpr uint64_t kMagic = 0x3153464154434b50ull;   // checkpoint tag
-constexpr uint64_t kVersion = 1;
+constexpr uint64_t kVersion = 2;
 constexpr size_t kAlign = 256;
 constexpr size_t kHeaderBytes = 256;
 
@@ -39,6 +39,7 @@ struct tfs_ctx {
     int stencil = TFS_STENCIL_UPWIND3;
     int transport = 1;
     int start = TFS_START_BDF2;    // first step from the initial state
+    int form = TFS_FORM_STRESS;    // variable carried: the stress, or the paper's Phi
     double umax = -1.0;            // declared velocity bound (< 0: none)
     // SOE
     bool soe_set = false;
@@ -46,6 +47,12 @@ struct tfs_ctx {
     ModeConstsD mcd{};
     ModeConstsF mcf{};
     double eta = 0.0;
+    // the paper's variable: c_j, dt c_j, w_j mu_j c_j, xi = b0 sum_j w_j c_j, and the
+    // modes of Phi0 == 1 (the same at every point; host FP64)
+    ModeConstsD mcd_p{};
+    ModeConstsF mcf_p{};
+    double xi_p = 0.0;
+    std::vector<double> phi0_n, phi0_nm1;
     // workspace
     char* ws = nullptr;
     size_t ws_bytes = 0;
@@ -86,6 +93,7 @@ struct tfs_ctx {
     int third_sig() const { return 3 - cur_sig - prev_sig; }
     bool explicit_transport() const { return transport == 1; }
     bool implicit_transport() const { return transport == 2; }
+    bool paper() const { return form == TFS_FORM_PAPER; }
 };
 
 namespace {
@@ -388,6 +396,45 @@ int do_step_implicit(tfs_ctx* h, const void* kn, const void* knm1, const void* u
     return TFS_OK;
 }
 
+// The paper's variable: Psi0^{n+1} = xi + sum_j w_j mu_j c_j (b1 phi0_j^n + b2 phi0_j^{n-1}),
+// the discrete D^{1-alpha} 1 that multiplies the source, and the push-forward of
+// the modes phi0_j of Phi0 == 1 after a step.
+double paper_psi0(const tfs_ctx* h) {
+    double s = h->xi_p;
+    for (int j = 0; j < h->m; ++j) s += h->mcd_p.eta[j] * (kB1 * h->phi0_n[j] + kB2 * h->phi0_nm1[j]);
+    return s;
+}
+
+void paper_advance_phi0(tfs_ctx* h) {
+    for (int j = 0; j < h->m; ++j) {
+        const double nx = h->mcd_p.c[j] * (-kB1 * h->phi0_n[j] - kB2 * h->phi0_nm1[j] + h->dt);
+        h->phi0_nm1[j] = h->phi0_n[j];
+        h->phi0_n[j] = nx;
+    }
+}
+
+void paper_reset_phi0(tfs_ctx* h, long long steps) {
+    h->phi0_n.assign(h->m, 0.0);
+    h->phi0_nm1.assign(h->m, 0.0);
+    for (long long k = 0; k < steps; ++k) paper_advance_phi0(h);
+}
+
+template <typename T>
+void fill_paper(tfs_ctx* h, FwdArgs<T>& a) {
+    const double psi0 = paper_psi0(h);
+    a.sigma0 = nullptr;
+    a.psi = (T*)h->trans;
+    a.xi = h->xi_p;
+    a.inv_wi = 1.0 / h->Wi;
+    a.a = kB0 + h->dt * h->xi_p / h->Wi;
+    a.g = psi0;
+    a.a_f2 = split_f2(a.a);
+    a.dt_f2 = split_f2(h->dt);
+    a.src_f2 = split_f2(h->dt * a.G * psi0);
+    a.xi_f2 = split_f2(h->xi_p);
+    a.dtxi_f2 = split_f2(h->dt * h->xi_p);
+}
+
 // SDIRK2 constants of the first step (Section 5.1): gamma = 1 - 1/sqrt2,
 // 1/(1 + gamma mu_j dt), W = sum_j w_j/(1 + gamma mu_j dt), g_alpha at both stage times
 StartConsts start_consts(const tfs_ctx* h) {
@@ -469,12 +516,14 @@ int do_step(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* s
     if (h->transport && !u) return TFS_ERR_ARG;
     if (limits_violated(h)) return TFS_ERR_UNSTABLE;
     if (!knm1) knm1 = kn;
+    if (h->paper() && (h->transport != 0 || (h->start == TFS_START_SDIRK2 && h->step == 0))) return TFS_ERR_ARG;
     if (h->start == TFS_START_SDIRK2 && h->step == 0) return do_first_step_sdirk2(h, kn, u, sig_copy, s);
     if (h->implicit_transport()) return do_step_implicit(h, kn, knm1, u, sig_copy, s);
     const int nxt = h->third_sig();
     const int cm = h->cur_mode, pm = 1 - h->cur_mode;
     cudaError_t e;
-    const LaunchCfg cfg = make_cfg(h);
+    LaunchCfg cfg = make_cfg(h);
+    cfg.paper = h->paper();
     if (h->is_double()) {
         FwdArgs<double> a{};
         fill_common(h, a);
@@ -491,6 +540,10 @@ int do_step(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* s
         a.modes_nm1 = (double*)h->modes[pm];
         a.g = g_alpha(h, h->step);
         a.mc = h->mcd;
+        if (h->paper()) {
+            a.mc = h->mcd_p;
+            fill_paper(h, a);
+        }
         e = launch_forward_f64(a, cfg, s);
     } else {
         FwdArgs<float> a{};
@@ -509,9 +562,14 @@ int do_step(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* s
         a.g = g_alpha(h, h->step);
         a.src_f2 = split_f2(a.dt * a.G * a.g);
         a.mc = h->mcf;
+        if (h->paper()) {
+            a.mc = h->mcf_p;
+            fill_paper(h, a);
+        }
         e = launch_forward_f32(a, cfg, s);
     }
     if (e != cudaSuccess) return TFS_ERR_CUDA;
+    if (h->paper()) paper_advance_phi0(h);
     h->prev_sig = h->cur_sig;
     h->cur_sig = nxt;
     if (!h->classic()) h->cur_mode = pm;
@@ -603,6 +661,12 @@ int tfs_set_param(tfs_handle h, int key, double value) {
             if (!(value >= 1.0 && value <= 100000.0) || value != std::floor(value)) return TFS_ERR_ARG;
             h->krylov_maxit = (int)value;
             return TFS_OK;
+        case TFS_PARAM_FORM:
+            if (value != TFS_FORM_STRESS && value != TFS_FORM_PAPER) return TFS_ERR_ARG;
+            if (value == TFS_FORM_PAPER && h->classic()) return TFS_ERR_ARG;
+            if ((int)value != h->form) h->state_set = false;   // the state means something else now
+            h->form = (int)value;
+            return TFS_OK;
         case TFS_PARAM_START:
             if (value != TFS_START_BDF2 && value != TFS_START_SDIRK2) return TFS_ERR_ARG;
             if (value == TFS_START_SDIRK2 && h->classic()) return TFS_ERR_ARG;
@@ -640,6 +704,24 @@ int tfs_set_soe(tfs_handle h, const double* mu, const double* w, int m) {
         h->mcf.eta_lo[j] = (float)(et - (double)hi);
     }
     h->eta = eta;
+    double xi = 0.0;
+    for (int j = 0; j < kMaxModes; ++j) {
+        double c = 0.0, pe = 0.0;
+        if (j < m) {
+            c = 1.0 / (kB0 + mu[j] * h->dt);
+            pe = w[j] * mu[j] * c;
+            xi += kB0 * w[j] * c;
+        }
+        h->mcd_p.c[j] = c;
+        h->mcd_p.rho[j] = c * h->dt;
+        h->mcd_p.eta[j] = pe;
+        h->mcf_p.c[j] = (float)c;
+        h->mcf_p.rho[j] = (float)(c * h->dt);
+        const float hi = (float)pe;
+        h->mcf_p.eta_hi[j] = hi;
+        h->mcf_p.eta_lo[j] = (float)(pe - (double)hi);
+    }
+    h->xi_p = xi;
     h->soe_set = true;
     h->lim_valid = false;
     return TFS_OK;
@@ -689,7 +771,9 @@ int tfs_set_state(tfs_handle h, const void* sigma0, void* stream) {
     if (e == cudaSuccess && h->m > 0) e = launch_zero(h->modes[0], h->modes_bytes(), s);
     if (e == cudaSuccess && h->m > 0) e = launch_zero(h->modes[1], h->modes_bytes(), s);
     if (e == cudaSuccess) e = launch_zero(h->flags, kAlign, s);
+    if (e == cudaSuccess) e = launch_zero(h->trans, h->field_bytes(), s);   // Psi before the first step: 0
     if (e != cudaSuccess) return TFS_ERR_CUDA;
+    paper_reset_phi0(h, 0);
     h->sigma0_zero = (sigma0 == nullptr);
     h->step = 0;
     h->state_set = true;
@@ -707,8 +791,8 @@ int tfs_get_stress(tfs_handle h, void* out, void* stream) {
     if (!h->ws) return TFS_ERR_NOWORKSPACE;
     if (!h->state_set) return TFS_ERR_STATE;
     h->last_stream = (cudaStream_t)stream;
-    return cuda_err(cudaMemcpyAsync(out, h->sig[h->cur_sig], h->field_bytes(), cudaMemcpyDeviceToDevice,
-                                    (cudaStream_t)stream));
+    const void* src = h->paper() ? (const void*)h->trans : (const void*)h->sig[h->cur_sig];
+    return cuda_err(cudaMemcpyAsync(out, src, h->field_bytes(), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
 }
 
 long tfs_step_index(tfs_handle h) { return valid_handle(h) ? (long)h->step : -1; }
@@ -722,7 +806,7 @@ int tfs_last_solve(tfs_handle h, int* iterations, double* relative_residual) {
 
 size_t tfs_checkpoint_bytes(tfs_handle h) {
     if (!valid_handle(h)) return 0;
-    return kHeaderBytes + 3 * align_up(h->field_bytes()) + 2 * align_up(h->modes_bytes());
+    return kHeaderBytes + (h->paper() ? 4 : 3) * align_up(h->field_bytes()) + 2 * align_up(h->modes_bytes());
 }
 
 int tfs_save(tfs_handle h, void* dst, void* stream) {
@@ -731,14 +815,14 @@ int tfs_save(tfs_handle h, void* dst, void* stream) {
     if (!h->ws) return TFS_ERR_NOWORKSPACE;
     if (!h->state_set) return TFS_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
-    uint64_t words[12] = {kMagic, kVersion, (uint64_t)h->dim, (uint64_t)h->n[0], (uint64_t)h->n[1],
+    uint64_t words[13] = {kMagic, kVersion, (uint64_t)h->dim, (uint64_t)h->n[0], (uint64_t)h->n[1],
                           (uint64_t)h->n[2], (uint64_t)h->m, (uint64_t)h->precision, (uint64_t)h->step,
-                          (uint64_t)(h->sigma0_zero ? 1 : 0), 0, 0};
+                          (uint64_t)(h->sigma0_zero ? 1 : 0), 0, 0, (uint64_t)h->form};
     double scal[2] = {h->dt, h->alpha};
     memcpy(&words[10], &scal[0], 8);
     memcpy(&words[11], &scal[1], 8);
     char* p = (char*)dst;
-    cudaError_t e = launch_write_header((uint64_t*)p, words, 12, s);
+    cudaError_t e = launch_write_header((uint64_t*)p, words, 13, s);
     p += kHeaderBytes;
     const size_t fb = h->field_bytes(), mb = h->modes_bytes();
     if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->sig[h->cur_sig], fb, cudaMemcpyDeviceToDevice, s);
@@ -751,7 +835,9 @@ int tfs_save(tfs_handle h, void* dst, void* stream) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->modes[h->cur_mode], mb, cudaMemcpyDeviceToDevice, s);
         p += align_up(mb);
         if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->modes[1 - h->cur_mode], mb, cudaMemcpyDeviceToDevice, s);
+        p += align_up(mb);
     }
+    if (h->paper() && e == cudaSuccess) e = cudaMemcpyAsync(p, h->trans, fb, cudaMemcpyDeviceToDevice, s);
     h->last_stream = s;
     return cuda_err(e);
 }
@@ -760,7 +846,7 @@ int tfs_load(tfs_handle h, const void* src, void* stream) {
     if (!valid_handle(h) || !src) return TFS_ERR_ARG;
     if (!h->ws) return TFS_ERR_NOWORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
-    uint64_t words[12];
+    uint64_t words[13];
     cudaError_t e = cudaMemcpyAsync(words, src, sizeof(words), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return TFS_ERR_CUDA;
@@ -770,7 +856,7 @@ int tfs_load(tfs_handle h, const void* src, void* stream) {
     if (words[0] != kMagic || words[1] != kVersion || words[2] != (uint64_t)h->dim ||
         words[3] != (uint64_t)h->n[0] || words[4] != (uint64_t)h->n[1] || words[5] != (uint64_t)h->n[2] ||
         words[6] != (uint64_t)h->m || words[7] != (uint64_t)h->precision || scal[0] != h->dt ||
-        scal[1] != h->alpha)
+        scal[1] != h->alpha || words[12] != (uint64_t)h->form)
         return TFS_ERR_FORMAT;
     h->cur_sig = 0;
     h->prev_sig = 1;
@@ -787,9 +873,12 @@ int tfs_load(tfs_handle h, const void* src, void* stream) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->modes[0], p, mb, cudaMemcpyDeviceToDevice, s);
         p += align_up(mb);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->modes[1], p, mb, cudaMemcpyDeviceToDevice, s);
+        p += align_up(mb);
     }
+    if (h->paper() && e == cudaSuccess) e = cudaMemcpyAsync(h->trans, p, fb, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return TFS_ERR_CUDA;
     h->step = (long long)words[8];
+    if (h->paper()) paper_reset_phi0(h, h->step);
     h->sigma0_zero = words[9] != 0;
     h->state_set = true;
     h->last_stream = s;
@@ -863,6 +952,7 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
                  double* dJ_dbeta, void* stream) {
     if (valid_handle(h) && h->implicit_transport()) return TFS_ERR_ARG;   // adjoint of the implicit step not built
     if (valid_handle(h) && h->start == TFS_START_SDIRK2) return TFS_ERR_ARG;   // nor of the SDIRK2 first step
+    if (valid_handle(h) && h->paper()) return TFS_ERR_ARG;                     // nor of the paper's variable
     if (!valid_handle(h) || !dJ_dsigma_T || !checkpoints || !grad_u || !dJ_dsigma0 || !dJ_dgrad_u || !dJ_dWi ||
         !dJ_dbeta)
         return TFS_ERR_ARG;

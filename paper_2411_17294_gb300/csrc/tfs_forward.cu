@@ -47,7 +47,8 @@ constexpr int kTile = 32;
 
 // Shared-memory stage of one tile: planes of 32 elements, in this order
 //   modes level n [m][nc], modes level n-1 [m][nc], kappa^n [d*d], kappa^{n-1} [d*d],
-//   A [nc] (transport), sigma0 [nc] (nonzero initial stress), sigma^n, sigma^{n-1} [nc] (alpha = 1).
+//   A [nc] (transport), sigma0 [nc] (nonzero initial stress), sigma^n, sigma^{n-1} [nc] (alpha = 1;
+//   the levels of Phi in the paper's variable).
 struct StageMap {
     int modes;          // first plane of each group
     int kn, km, tr, s0, sig;
@@ -55,7 +56,7 @@ struct StageMap {
 };
 
 template <int DIM>
-__host__ __device__ __forceinline__ StageMap stage_map(int m, bool transport, bool sigma0, bool classic) {
+__host__ __device__ __forceinline__ StageMap stage_map(int m, bool transport, bool sigma0, bool levels) {
     constexpr int NC = DIM == 2 ? 3 : 6;
     StageMap S;
     S.modes = 0;
@@ -64,7 +65,7 @@ __host__ __device__ __forceinline__ StageMap stage_map(int m, bool transport, bo
     S.tr = S.km + DIM * DIM;
     S.s0 = S.tr + (transport ? NC : 0);
     S.sig = S.s0 + (sigma0 ? NC : 0);
-    S.planes = S.sig + (classic ? 2 * NC : 0);
+    S.planes = S.sig + (levels ? 2 * NC : 0);
     return S;
 }
 
@@ -150,7 +151,7 @@ __device__ __forceinline__ void issue_tile(const FwdArgs<T>& A, const StageMap& 
 // everything else (level n-1, kappa levels, A, sigma0, stress levels) on bar_l.
 template <typename T, int DIM, bool TRANSPORT>
 __device__ __forceinline__ void tma_issue(const TmaPlan& tp, const StageMap& S, T* buf, long long t0, int mnc,
-                                          bool has_s0, bool classic, bool early, bool late, uint64_t* bar_e,
+                                          bool has_s0, bool levels, bool early, bool late, uint64_t* bar_e,
                                           uint64_t* bar_l) {
     constexpr int NC = Packed<DIM>::NC;
     constexpr unsigned kPlaneBytes = kTile * sizeof(T);
@@ -169,7 +170,7 @@ __device__ __forceinline__ void tma_issue(const TmaPlan& tp, const StageMap& S, 
         tma_load_2d(buf + (size_t)S.km * kTile, &tp.km, x, 0, bar_l);
         if (TRANSPORT) tma_load_2d(buf + (size_t)S.tr * kTile, &tp.tr, x, 0, bar_l);
         if (has_s0) tma_load_2d(buf + (size_t)S.s0 * kTile, &tp.s0, x, 0, bar_l);
-        if (classic) {
+        if (levels) {
             tma_load_2d(buf + (size_t)S.sig * kTile, &tp.sn, x, 0, bar_l);
             tma_load_2d(buf + (size_t)(S.sig + NC) * kTile, &tp.sm, x, 0, bar_l);
         }
@@ -486,7 +487,7 @@ struct StepShape {
     static constexpr int CPW = NC / W;
 };
 
-template <typename T, int DIM, bool TRANSPORT, bool COMP, typename Hook>
+template <typename T, int DIM, bool TRANSPORT, bool COMP, bool PAPER, typename Hook>
 __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap& S, T* buf, long long t0,
                                              int classic, void* sR_raw, float* sD, Hook after_pass1) {
     constexpr int NC = Packed<DIM>::NC;
@@ -586,9 +587,17 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
         }
     }
 
-    // ---- right-hand side components
+    // ---- right-hand side components (the paper's variable: the history sums h
+    //      themselves; its right-hand side couples the components and is formed
+    //      by the solving warp)
 #pragma unroll
-    for (int cc = 0; cc < CPW; ++cc) {
+    for (int cc = 0; cc < CPW && PAPER; ++cc) {
+        const int c = w + cc * W;
+        if constexpr (F32) reinterpret_cast<f2*>(sR_raw)[c * kTile + lane] = Hf[cc];
+        else reinterpret_cast<double*>(sR_raw)[c * kTile + lane] = Hd[cc];
+    }
+#pragma unroll
+    for (int cc = 0; cc < CPW && !PAPER; ++cc) {
         const int c = w + cc * W;
         const int ci = Packed<DIM>::I(c), cj = Packed<DIM>::J(c);
         const T kn_ij = buf[(S.kn + ci * DIM + cj) * kTile + lane];
@@ -618,8 +627,91 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
     // ---- (a2) + (a5) point solve by warp 0
     if (w == 0) {
         T out[NC];
+        T psi[NC];
         unsigned fl = 0u;
-        if constexpr (F32) {
+        if constexpr (PAPER) {
+            // (b0 + dt xi/Wi) Phi - dt xi L(kappa*) Phi
+            //     = -b1 Phi^n - b2 Phi^{n-1} + dt (L(kappa*) h - h/Wi) + dt G (kappa* + kappa*^T) Psi0
+            // Psi^{n+1} = xi Phi^{n+1} + h
+            if constexpr (F32) {
+                f2 K[3][3];
+                float Kf[3][3];
+#pragma unroll
+                for (int a = 0; a < DIM; ++a)
+#pragma unroll
+                    for (int b = 0; b < DIM; ++b) {
+                        K[a][b] = two_sum_f2(2.0f * (float)buf[(S.kn + a * DIM + b) * kTile + lane],
+                                             -(float)buf[(S.km + a * DIM + b) * kTile + lane]);
+                        Kf[a][b] = K[a][b].hi;
+                    }
+                const f2* sH = reinterpret_cast<const f2*>(sR_raw);
+                f2 h[NC], R[NC], x[NC];
+                float Hs[3][3];
+#pragma unroll
+                for (int r = 0; r < NC; ++r) {
+                    h[r] = sH[r * kTile + lane];
+                    Hs[Packed<DIM>::I(r)][Packed<DIM>::J(r)] = h[r].hi;
+                    Hs[Packed<DIM>::J(r)][Packed<DIM>::I(r)] = h[r].hi;
+                }
+                const f2 src{A.src_f2.hi, A.src_f2.lo};
+                const float dtf = A.dt_f2.hi, iwi = (float)A.inv_wi;
+#pragma unroll
+                for (int r = 0; r < NC; ++r) {
+                    const int i = Packed<DIM>::I(r), j = Packed<DIM>::J(r);
+                    const float pn = (float)buf[(S.sig + r) * kTile + lane];
+                    const float pm = (float)buf[(S.sig + NC + r) * kTile + lane];
+                    f2 v = two_sum_f2(2.0f * pn, -0.5f * pm);
+                    v = f2_add(v, f2_mul(src, f2_add(K[i][j], K[j][i])));
+                    // the operator on h enters scaled by dt: float accuracy suffices
+                    float lh = -iwi * Hs[i][j];
+#pragma unroll
+                    for (int l = 0; l < DIM; ++l) lh = __fmaf_rn(Kf[i][l], Hs[l][j], __fmaf_rn(Hs[i][l], Kf[j][l], lh));
+                    R[r] = f2_add_f(v, dtf * lh);
+                }
+                if (!solve_point_f32<DIM>(K, A.a_f2, A.dtxi_f2, R, x)) fl |= 2u;
+                const f2 xi{A.xi_f2.hi, A.xi_f2.lo};
+#pragma unroll
+                for (int r = 0; r < NC; ++r) {
+                    out[r] = (T)(x[r].hi + x[r].lo);
+                    const f2 ps = f2_add(f2_mul(xi, x[r]), h[r]);
+                    psi[r] = (T)(ps.hi + ps.lo);
+                }
+            } else {
+                double K[3][3], Hs[3][3];
+#pragma unroll
+                for (int a = 0; a < DIM; ++a)
+#pragma unroll
+                    for (int b = 0; b < DIM; ++b)
+                        K[a][b] = 2.0 * (double)buf[(S.kn + a * DIM + b) * kTile + lane] -
+                                  (double)buf[(S.km + a * DIM + b) * kTile + lane];
+                const double* sH = reinterpret_cast<const double*>(sR_raw);
+                double h[NC], x[NC];
+#pragma unroll
+                for (int r = 0; r < NC; ++r) {
+                    h[r] = sH[r * kTile + lane];
+                    Hs[Packed<DIM>::I(r)][Packed<DIM>::J(r)] = h[r];
+                    Hs[Packed<DIM>::J(r)][Packed<DIM>::I(r)] = h[r];
+                }
+#pragma unroll
+                for (int r = 0; r < NC; ++r) {
+                    const int i = Packed<DIM>::I(r), j = Packed<DIM>::J(r);
+                    double lh = -A.inv_wi * Hs[i][j];
+#pragma unroll
+                    for (int l = 0; l < DIM; ++l) lh = fma(K[i][l], Hs[l][j], fma(Hs[i][l], K[j][l], lh));
+                    const double pn = (double)buf[(S.sig + r) * kTile + lane];
+                    const double pm = (double)buf[(S.sig + NC + r) * kTile + lane];
+                    x[r] = (2.0 * pn - 0.5 * pm) + A.dt * lh + A.dt * A.G * A.g * (K[i][j] + K[j][i]);
+                }
+                double M[NC][NC];
+                assemble_M<DIM>(K, A.a, A.dt * A.xi, M);
+                if (!gauss_pp<NC>(M, x, 1e-300)) fl |= 2u;
+#pragma unroll
+                for (int r = 0; r < NC; ++r) {
+                    out[r] = (T)x[r];
+                    psi[r] = (T)fma(A.xi, x[r], h[r]);
+                }
+            }
+        } else if constexpr (F32) {
             f2 K[3][3];
 #pragma unroll
             for (int a = 0; a < DIM; ++a)
@@ -665,7 +757,13 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
 #pragma unroll
             for (int r = 0; r < NC; ++r) {
                 A.sig_np1[(long long)r * N + p] = out[r];
-                if (A.sig_copy) A.sig_copy[(long long)r * N + p] = out[r];
+                if constexpr (PAPER) {
+                    finite = finite && isfinite((double)psi[r]);
+                    A.psi[(long long)r * N + p] = psi[r];
+                    if (A.sig_copy) A.sig_copy[(long long)r * N + p] = psi[r];
+                } else {
+                    if (A.sig_copy) A.sig_copy[(long long)r * N + p] = out[r];
+                }
             }
             if (!finite) fl |= 1u;
             if (fl) atomicOr(A.flags, fl);
@@ -711,7 +809,7 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
 // level-n mode planes are fetched as soon as the current tile has read its
 // own (after its history sums) and the rest after its push-forward.  One loop
 // serves every variant, so that the tile code is instantiated once.
-template <typename T, int DIM, bool TRANSPORT, bool COMP>
+template <typename T, int DIM, bool TRANSPORT, bool COMP, bool PAPER>
 __global__ void __launch_bounds__(32 * StepShape<DIM>::W, 4)
 fwd_kernel(const FwdArgs<T> A, const __grid_constant__ TmaPlan tp, const int classic, const long long num_tiles,
            const int stages, const int vec16) {
@@ -720,7 +818,7 @@ fwd_kernel(const FwdArgs<T> A, const __grid_constant__ TmaPlan tp, const int cla
     __shared__ __align__(16) double sR_store[NC * kTile];       // R per (component, point): double or f2
     __shared__ __align__(16) double sD_store[NC * kTile];       // sigma^{n+1} - sigma0 (float or double)
     __shared__ __align__(8) uint64_t bars[2][2];                // TMA: [stage buffer][early, late]
-    const StageMap S = stage_map<DIM>(classic ? 0 : A.m, TRANSPORT, A.sigma0 != nullptr, classic != 0);
+    const StageMap S = stage_map<DIM>(classic ? 0 : A.m, TRANSPORT, A.sigma0 != nullptr, classic != 0 || PAPER);
     const size_t stage_elems = (size_t)S.planes * kTile;
     // stage buffers start on a 128-byte boundary (TMA destination)
     T* buf0 = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(smem) + 127) & ~uintptr_t(127));
@@ -749,7 +847,7 @@ fwd_kernel(const FwdArgs<T> A, const __grid_constant__ TmaPlan tp, const int cla
         T* dst = b ? buf1 : buf0;
         if (use_tma) {
             if (tid == 0)
-                tma_issue<T, DIM, TRANSPORT>(tp, S, dst, t * kTile, mnc, has_s0, classic != 0, early, late, &bars[b][0],
+                tma_issue<T, DIM, TRANSPORT>(tp, S, dst, t * kTile, mnc, has_s0, classic != 0 || PAPER, early, late, &bars[b][0],
                                              &bars[b][1]);
         } else {
             issue_planes<T, DIM>(A, S, dst, t * kTile, tid, nthr, v16, early ? 0 : mnc, late ? S.planes : mnc);
@@ -787,20 +885,23 @@ fwd_kernel(const FwdArgs<T> A, const __grid_constant__ TmaPlan tp, const int cla
         auto early = [&] {
             if (!two && next < num_tiles) issue(0, next, true, false);
         };
-        compute_tile<T, DIM, TRANSPORT, COMP>(A, S, b ? buf1 : buf0, tile * kTile, classic, sR_store, sD, early);
+        compute_tile<T, DIM, TRANSPORT, COMP, PAPER>(A, S, b ? buf1 : buf0, tile * kTile, classic, sR_store, sD,
+                                                     early);
         __syncthreads();
         if (!two && next < num_tiles) issue(0, next, false, true);
     }
     if (!use_tma) cp_async_wait<0>();
 }
 
-template <typename T, int DIM, bool TRANSPORT, bool COMP>
+template <typename T, int DIM, bool TRANSPORT, bool COMP, bool PAPER>
 cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s) {
     constexpr int NC = Packed<DIM>::NC;
     cudaError_t e;
-    auto kern = fwd_kernel<T, DIM, TRANSPORT, COMP>;
+    auto kern = fwd_kernel<T, DIM, TRANSPORT, COMP, PAPER>;
     const long long num_tiles = (a.N + kTile - 1) / kTile;
-    const StageMap S = stage_map<DIM>(cfg.classic ? 0 : a.m, TRANSPORT, a.sigma0 != nullptr, cfg.classic);
+    const bool levels = cfg.classic || PAPER;
+    if (PAPER && (cfg.classic || !a.psi)) return cudaErrorInvalidValue;
+    const StageMap S = stage_map<DIM>(cfg.classic ? 0 : a.m, TRANSPORT, a.sigma0 != nullptr, levels);
     const size_t stage_bytes = (size_t)S.planes * kTile * sizeof(T);
     const size_t static_bytes = 2 * NC * kTile * sizeof(double) + 32;
     PersistPlan plan;
@@ -848,7 +949,7 @@ cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s
              encode_plane_map(&tp.km, a.kap_nm1, a.N, DIM * DIM, DIM * DIM, dbl);
         if (ok && TRANSPORT) ok = encode_plane_map(&tp.tr, a.trans, a.N, NC, NC, dbl);
         if (ok && a.sigma0) ok = encode_plane_map(&tp.s0, a.sigma0, a.N, NC, NC, dbl);
-        if (ok && cfg.classic)
+        if (ok && levels)
             ok = encode_plane_map(&tp.sn, a.sig_n, a.N, NC, NC, dbl) &&
                  encode_plane_map(&tp.sm, a.sig_nm1, a.N, NC, NC, dbl);
         tp.on = ok ? 1 : 0;
@@ -867,9 +968,16 @@ cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s
 
 template <typename T, bool COMP>
 cudaError_t dispatch(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s) {
+    if (cfg.paper) {
+        // the paper's variable is built for the pointwise law only
+        if (cfg.transport) return cudaErrorInvalidValue;
+        return cfg.dim == 2 ? launch_one<T, 2, false, COMP, true>(a, cfg, s)
+                            : launch_one<T, 3, false, COMP, true>(a, cfg, s);
+    }
     if (cfg.dim == 2)
-        return cfg.transport ? launch_one<T, 2, true, COMP>(a, cfg, s) : launch_one<T, 2, false, COMP>(a, cfg, s);
-    return cfg.transport ? launch_one<T, 3, true, COMP>(a, cfg, s) : launch_one<T, 3, false, COMP>(a, cfg, s);
+        return cfg.transport ? launch_one<T, 2, true, COMP, false>(a, cfg, s)
+                             : launch_one<T, 2, false, COMP, false>(a, cfg, s);
+    return cfg.transport ? launch_one<T, 3, true, COMP, false>(a, cfg, s) : launch_one<T, 3, false, COMP, false>(a, cfg, s);
 }
 
 }  // namespace

@@ -56,6 +56,12 @@ struct FwdArgs {
     // double-float copies of the step scalars (FP32 storage modes)
     F2c eta_f2, a_f2, dt_f2, src_f2;   // src = dt G g
     typename ModeConsts<T>::type mc;
+    // the paper's own variable (Section 3.4): sig_* hold the levels of Phi, g holds
+    // Psi0^{n+1}, a = b0 + dt xi/Wi, mc holds c_j, dt c_j, w_j mu_j c_j; psi receives
+    // the stress Psi^{n+1} = xi Phi^{n+1} + h
+    T* psi;                // [nc][N]
+    double xi, inv_wi;
+    F2c xi_f2, dtxi_f2;    // xi, dt xi
 };
 
 // Tensor maps of the plane groups a tile stages, each a 2D view [planes][N]
@@ -164,6 +170,7 @@ struct LaunchCfg {
     bool transport;
     bool classic;      // alpha == 1
     bool compensated;  // FP32 compensated mode sum
+    bool paper = false; // the paper's own variable (transport off only)
     cudaEvent_t ev_before = nullptr;   // recorded just before / after the step kernel
     cudaEvent_t ev_after = nullptr;    // (not around the transport pre-pass), if set
 };

@@ -20,8 +20,9 @@ TFS_OK, TFS_ERR_ARG, TFS_ERR_NOSOE, TFS_ERR_UNSTABLE, TFS_ERR_CUDA, TFS_ERR_STAT
     TFS_ERR_FORMAT, TFS_ERR_TOOBIG = range(9)
 TFS_FP64, TFS_FP32, TFS_FP32_PLAIN = 0, 1, 2
 (TFS_PARAM_RE, TFS_PARAM_EPS, TFS_PARAM_STENCIL, TFS_PARAM_TRANSPORT, TFS_PARAM_UMAX, TFS_PARAM_KRYLOV_TOL,
- TFS_PARAM_KRYLOV_MAXIT, TFS_PARAM_START) = range(8)
+ TFS_PARAM_KRYLOV_MAXIT, TFS_PARAM_START, TFS_PARAM_FORM) = range(9)
 TFS_START_BDF2, TFS_START_SDIRK2 = 0, 1
+TFS_FORM_STRESS, TFS_FORM_PAPER = 0, 1
 TFS_STENCIL_UPWIND3, TFS_STENCIL_CENTRAL2 = 0, 1
 TFS_FLAG_NONFINITE, TFS_FLAG_SINGULAR, TFS_FLAG_COURANT, TFS_FLAG_TIMEOUT, TFS_FLAG_NOCONV = 1, 2, 4, 8, 16
 
@@ -128,7 +129,8 @@ class Solver:
 
     def __init__(self, dim: int, n, alpha: float, Wi: float, beta: float, dt: float, m: int = 0,
                  precision: int = TFS_FP64, L=None, mu=None, w=None, Re: float = 1.0, eps: float = 0.0,
-                 stencil: int = TFS_STENCIL_UPWIND3, transport=True, device=None, start: str = "bdf2"):
+                 stencil: int = TFS_STENCIL_UPWIND3, transport=True, device=None, start: str = "bdf2",
+                 form: str = "stress"):
         torch = _torch()
         lib = load_library()
         self.lib = lib
@@ -164,6 +166,13 @@ class Solver:
         self.start = start
         check(lib.tfs_set_param(h, TFS_PARAM_START, float(TFS_START_SDIRK2 if start == "sdirk2" else TFS_START_BDF2)),
               "tfs_set_param(start)")
+        # variable carried: "stress" or "paper" (Phi with Psi = D^{1-alpha} Phi, Section 3.4; the SOE
+        # then approximates g_alpha, i.e. the kernel of order 1 - alpha; transport off)
+        if form not in ("stress", "paper"):
+            raise ValueError("form must be 'stress' or 'paper'")
+        self.form = form
+        check(lib.tfs_set_param(h, TFS_PARAM_FORM, float(TFS_FORM_PAPER if form == "paper" else TFS_FORM_STRESS)),
+              "tfs_set_param(form)")
         if mu is not None:
             self.set_soe(mu, w)
         nbytes = lib.tfs_workspace_bytes(h)

@@ -97,9 +97,15 @@ def test_soe_and_params_validation(lib):
     assert lib.tfs_set_param(h, tfs.TFS_PARAM_START, float(tfs.TFS_START_SDIRK2)) == tfs.TFS_OK
     assert lib.tfs_backward(h, None, None, 1, 1, None, None, None, None, None, None, None) == tfs.TFS_ERR_ARG
     assert lib.tfs_set_param(h, tfs.TFS_PARAM_START, float(tfs.TFS_START_BDF2)) == tfs.TFS_OK
+    # variable carried: stress or the paper's Phi; the adjoint refuses the latter
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_FORM, 2.0) == tfs.TFS_ERR_ARG
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_FORM, float(tfs.TFS_FORM_PAPER)) == tfs.TFS_OK
+    assert lib.tfs_backward(h, None, None, 1, 1, None, None, None, None, None, None, None) == tfs.TFS_ERR_ARG
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_FORM, float(tfs.TFS_FORM_STRESS)) == tfs.TFS_OK
     lib.tfs_destroy(h)
     rc, h = make(lib, alpha=1.0, m=0)
     assert lib.tfs_set_param(h, tfs.TFS_PARAM_START, float(tfs.TFS_START_SDIRK2)) == tfs.TFS_ERR_ARG
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_FORM, float(tfs.TFS_FORM_PAPER)) == tfs.TFS_ERR_ARG
     lib.tfs_destroy(h)
 
 
