@@ -345,6 +345,64 @@ def implicit_transport_record(dev):
             "explicit_courant_fraction": courant, "device_flags": flags}
 
 
+def paper_form_bytes_per_point(dim: int, m: int, elem: int) -> int:
+    """Algorithmic bytes of the step kernel in the paper's variable: 3 words per
+    (mode, component), both velocity-gradient levels, Phi^n and Phi^{n-1} read,
+    Phi^{n+1} and the stress Psi^{n+1} written."""
+    nc = 3 if dim == 2 else 6
+    return 3 * m * nc * elem + 2 * dim * dim * elem + 4 * nc * elem
+
+
+def paper_form_record(dev, steps: int, warmup: int):
+    """The step in the paper's own variable (Phi, Psi = D^{1-alpha} Phi; the SOE
+    approximates g_alpha) on the 3D 256^3 m = 32 FP32 grid of the main workload,
+    pointwise (this form carries no transport): time per step and the HBM
+    roofline fraction of its step kernel, timed with events around the kernel."""
+    import torch
+
+    from paper_2411_17294_gb300 import inputs, soe, tfs
+    W = WORKLOAD
+    dt = W["dt"]
+    mu, w = soe.build(1.0 - W["alpha"], dt, W["horizon_steps"] * dt, W["m"])
+    _, kap = inputs.spectral_velocity(3, W["n"], W["kmax"], W["seed"], device=dev)
+    s = tfs.Solver(3, W["n"], W["alpha"], W["Wi"], W["beta"], dt, m=W["m"], precision=tfs.TFS_FP32, mu=mu, w=w,
+                   transport=False, form="paper", device=dev)
+    kn = torch.as_tensor(kap, dtype=torch.float32, device=dev).contiguous()
+    km = kn.clone()
+    del kap
+    stream = torch.cuda.Stream(device=dev)
+    kb = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ka = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        s.set_state(None, stream=stream)
+        for _ in range(warmup):
+            s.step(kn, km, stream=stream)
+        for e in kb + ka:
+            e.record(stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(steps):
+            s.set_step_events(kb[k], ka[k])
+            s.step(kn, km, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    s.set_step_events(None, None)
+    flags = s.status()
+    N = s.N
+    s.close()
+    launch_ms = statistics.mean(kb[k].elapsed_time(ka[k]) for k in range(steps))
+    bpp = paper_form_bytes_per_point(3, W["m"], 4)
+    peak, peak_kind = read_peaks()
+    achieved = bpp * N / (launch_ms * 1e-3) / 1e9
+    return {"workload": "paper's variable Phi, Psi = D^{1-alpha} Phi (Section 3.4), 3D 256^3, m=32, FP32, "
+                        "pointwise (no transport), alpha=0.6, SOE of g_alpha",
+            "ms_per_step": e0.elapsed_time(e1) / steps, "avg_launch_ms": launch_ms,
+            "G_point_mode_updates_per_s": N * W["m"] / (launch_ms * 1e-3) / 1e9,
+            "algorithmic_bytes_per_point": bpp, "achieved_gbs": achieved, "peak": peak, "peak_kind": peak_kind,
+            "frac": achieved / peak, "device_flags": flags}
+
+
 def max_over_ranks(local_ms: float, dist, device) -> float:
     """The slowest rank's time (all ranks get it); local_ms itself on one process."""
     if dist is None:
@@ -386,6 +444,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adjoint-only", default=None, choices=["fp32", "fp64"],
                     help="time only the adjoint workload in one precision and print its record (profiling)")
+    ap.add_argument("--paper-only", action="store_true",
+                    help="time only the step in the paper's variable and print its record (profiling)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32plain"])
     ap.add_argument("--grid", type=int, default=WORKLOAD["n"][0],
                     help="cube side of the step workload (default 256; smaller sides are for profiling)")
@@ -407,6 +467,14 @@ def main():
         torch.cuda.set_device(0)
         prec = tfs.TFS_FP32 if args.adjoint_only == "fp32" else tfs.TFS_FP64
         print(json.dumps(adjoint_ratio(torch.device("cuda", 0), prec)), flush=True)
+        return
+
+    if args.paper_only:
+        import torch
+        from paper_2411_17294_gb300 import build as tbuild
+        tbuild.build()
+        torch.cuda.set_device(0)
+        print(json.dumps(paper_form_record(torch.device("cuda", 0), steps=args.steps, warmup=args.warmup)), flush=True)
         return
 
     import numpy as np
@@ -519,6 +587,13 @@ def main():
         except Exception as exc:  # pragma: no cover - reported, not fatal
             imp = {"error": str(exc)}
 
+    paper = None
+    if not args.no_adjoint:
+        try:
+            paper = paper_form_record(dev, steps=10, warmup=3)
+        except Exception as exc:  # pragma: no cover - reported, not fatal
+            paper = {"error": str(exc)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         try:
@@ -550,6 +625,7 @@ def main():
             "e2e": e2e,
             "adjoint_forward": adj,
             "implicit_transport": imp,
+            "paper_form": paper,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
