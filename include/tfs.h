@@ -97,7 +97,8 @@ enum {
                                  in FP64).  SDIRK2 needs alpha < 1 (else TFS_ERR_ARG here) and transport
                                  0 or 2: with explicit transport the first tfs_step returns TFS_ERR_ARG.
                                  With transport 2 both stage systems go through the implicit solver
-                                 (tfs_last_solve: iterations summed, larger residual).  tfs_backward
+                                 (tfs_last_solve: iterations summed, larger residual).  With
+                                 TFS_FORM_PAPER the same method on Phi and its modes.  tfs_backward
                                  refuses a handle with this start (TFS_ERR_ARG) */
     TFS_PARAM_FORM = 8        /* variable carried, TFS_FORM_*: the stress (default), or the paper's own
                                  variable (Section 3.4): Phi with d Phi/dt = (L(kappa) - I/Wi) Psi +
@@ -107,8 +108,8 @@ enum {
                                  D^{1-alpha} 1 from the same modes, on the host.  The stress returned is
                                  Psi (zero before the first step); tfs_set_state sets Phi(0) (NULL: 0).
                                  BDF2 on Phi and the modes (Section 4.1), one point system per point.
-                                 Needs alpha < 1 (else TFS_ERR_ARG here), transport 0 and the BDF2 start
-                                 (else tfs_step returns TFS_ERR_ARG); tfs_backward refuses it (TFS_ERR_ARG).
+                                 Needs alpha < 1 (else TFS_ERR_ARG here) and transport 0 (else tfs_step
+                                 returns TFS_ERR_ARG); either start; tfs_backward refuses it (TFS_ERR_ARG).
                                  Changing the form discards the state (call tfs_set_state again) */
 };
 

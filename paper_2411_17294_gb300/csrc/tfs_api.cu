@@ -413,10 +413,42 @@ void paper_advance_phi0(tfs_ctx* h) {
     }
 }
 
+// SDIRK2 first step on the modes of Phi0 == 1 (the scalar case of the
+// paper-variable start in tfs_start.cu): returns Psi0 at the two stage times
+// in psi0[2] and advances phi0 to level 1.
+void paper_sdirk2_phi0(tfs_ctx* h, double psi0[2]) {
+    const double gam = 1.0 - std::sqrt(0.5), gd = gam * h->dt, f1 = h->dt * (1.0 - gam);
+    double W = 0.0;
+    for (int j = 0; j < h->m; ++j) W += h->w[j] / (1.0 + gam * h->mu[j] * h->dt);
+    std::vector<double> z2(h->m);
+    double s1 = W, s2 = W;
+    for (int j = 0; j < h->m; ++j) {
+        const double inv = 1.0 / (1.0 + gam * h->mu[j] * h->dt);
+        const double z0 = h->phi0_n[j];
+        s1 -= h->w[j] * h->mu[j] * z0 * inv;
+        const double ph = (z0 + gd) * inv;
+        z2[j] = z0 + f1 * (1.0 - h->mu[j] * ph);
+        s2 -= h->w[j] * h->mu[j] * z2[j] * inv;
+    }
+    psi0[0] = s1;
+    psi0[1] = s2;
+    for (int j = 0; j < h->m; ++j) {
+        h->phi0_nm1[j] = h->phi0_n[j];
+        h->phi0_n[j] = (z2[j] + gd) / (1.0 + gam * h->mu[j] * h->dt);
+    }
+}
+
 void paper_reset_phi0(tfs_ctx* h, long long steps) {
     h->phi0_n.assign(h->m, 0.0);
     h->phi0_nm1.assign(h->m, 0.0);
-    for (long long k = 0; k < steps; ++k) paper_advance_phi0(h);
+    for (long long k = 0; k < steps; ++k) {
+        if (k == 0 && h->start == TFS_START_SDIRK2) {
+            double unused[2];
+            paper_sdirk2_phi0(h, unused);
+        } else {
+            paper_advance_phi0(h);
+        }
+    }
 }
 
 template <typename T>
@@ -457,7 +489,7 @@ StartConsts start_consts(const tfs_ctx* h) {
 // and mode rings then advance as after any step: level n-1 = the initial state.
 int do_first_step_sdirk2(tfs_ctx* h, const void* kn, const void* u, void* sig_copy, cudaStream_t s) {
     if (h->explicit_transport()) return TFS_ERR_ARG;
-    const StartConsts c = start_consts(h);
+    StartConsts c = start_consts(h);
     const int nxt = h->third_sig();
     const int cm = h->cur_mode, pm = 1 - h->cur_mode;
     const double a_stage = h->dt * c.W + h->dt / h->Wi;
@@ -481,6 +513,30 @@ int do_first_step_sdirk2(tfs_ctx* h, const void* kn, const void* u, void* sig_co
         }
         h->last_iters = iters;
         h->last_relres = relres;
+    } else if (h->paper()) {
+        // Phi^0 is level n of the ring; Psi0 at the stage times from the host
+        const std::vector<double> keep_n = h->phi0_n, keep_nm1 = h->phi0_nm1;
+        paper_sdirk2_phi0(h, c.g);
+        const double a_p = 1.0 + h->dt * c.gam * c.W / h->Wi;
+        const double G = (1.0 - h->beta) / (h->Wi * h->Re);
+        if (h->ev_before) e = cudaEventRecord(h->ev_before, s);
+        else e = cudaSuccess;
+        if (e == cudaSuccess && h->is_double()) {
+            StartArgs<double> a{(const double*)kn, (const double*)h->sig[h->cur_sig], (const double*)h->modes[cm],
+                                (double*)h->modes[pm], (double*)h->sig[nxt], (double*)sig_copy, h->flags, h->N, h->m,
+                                h->dt, a_p, G, (double*)h->trans, 1.0 / h->Wi};
+            e = launch_start_paper_f64(a, c, h->dim, s);
+        } else if (e == cudaSuccess) {
+            StartArgs<float> a{(const float*)kn, (const float*)h->sig[h->cur_sig], (const float*)h->modes[cm],
+                               (float*)h->modes[pm], (float*)h->sig[nxt], (float*)sig_copy, h->flags, h->N, h->m,
+                               h->dt, a_p, G, (float*)h->trans, 1.0 / h->Wi};
+            e = launch_start_paper_f32(a, c, h->dim, s);
+        }
+        if (e == cudaSuccess && h->ev_after) e = cudaEventRecord(h->ev_after, s);
+        if (e != cudaSuccess) {
+            h->phi0_n = keep_n;
+            h->phi0_nm1 = keep_nm1;
+        }
     } else {
         if (h->ev_before) e = cudaEventRecord(h->ev_before, s);
         else e = cudaSuccess;
@@ -488,13 +544,13 @@ int do_first_step_sdirk2(tfs_ctx* h, const void* kn, const void* u, void* sig_co
             StartArgs<double> a{(const double*)kn, h->sigma0_zero ? nullptr : (const double*)h->sigma0,
                                 (const double*)h->modes[cm], (double*)h->modes[pm], (double*)h->sig[nxt],
                                 (double*)sig_copy, h->flags, h->N, h->m, h->dt, a_stage,
-                                (1.0 - h->beta) / (h->Wi * h->Re)};
+                                (1.0 - h->beta) / (h->Wi * h->Re), nullptr, 1.0 / h->Wi};
             e = launch_start_point_f64(a, c, h->dim, s);
         } else if (e == cudaSuccess) {
             StartArgs<float> a{(const float*)kn, h->sigma0_zero ? nullptr : (const float*)h->sigma0,
                                (const float*)h->modes[cm], (float*)h->modes[pm], (float*)h->sig[nxt],
                                (float*)sig_copy, h->flags, h->N, h->m, h->dt, a_stage,
-                               (1.0 - h->beta) / (h->Wi * h->Re)};
+                               (1.0 - h->beta) / (h->Wi * h->Re), nullptr, 1.0 / h->Wi};
             e = launch_start_point_f32(a, c, h->dim, s);
         }
         if (e == cudaSuccess && h->ev_after) e = cudaEventRecord(h->ev_after, s);
@@ -516,7 +572,7 @@ int do_step(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* s
     if (h->transport && !u) return TFS_ERR_ARG;
     if (limits_violated(h)) return TFS_ERR_UNSTABLE;
     if (!knm1) knm1 = kn;
-    if (h->paper() && (h->transport != 0 || (h->start == TFS_START_SDIRK2 && h->step == 0))) return TFS_ERR_ARG;
+    if (h->paper() && h->transport != 0) return TFS_ERR_ARG;
     if (h->start == TFS_START_SDIRK2 && h->step == 0) return do_first_step_sdirk2(h, kn, u, sig_copy, s);
     if (h->implicit_transport()) return do_step_implicit(h, kn, knm1, u, sig_copy, s);
     const int nxt = h->third_sig();

@@ -151,11 +151,16 @@ struct StartArgs {
     unsigned* flags;
     long long N;
     int m;
-    double dt, a, G;       // a = dt W + dt/Wi
+    double dt, a, G;       // a = dt W + dt/Wi (the paper's variable: 1 + gamma dt W/Wi)
+    T* psi;                // the paper's variable: Psi^1 [nc][N] (out); sigma0 then points at Phi^0
+    double inv_wi;
 };
 
 cudaError_t launch_start_point_f64(const StartArgs<double>& a, const StartConsts& c, int dim, cudaStream_t s);
 cudaError_t launch_start_point_f32(const StartArgs<float>& a, const StartConsts& c, int dim, cudaStream_t s);
+// the same first step in the paper's variable (c.g holds Psi0 at the two stage times)
+cudaError_t launch_start_paper_f64(const StartArgs<double>& a, const StartConsts& c, int dim, cudaStream_t s);
+cudaError_t launch_start_paper_f32(const StartArgs<float>& a, const StartConsts& c, int dim, cudaStream_t s);
 // implicit transport: the two stage systems by the Krylov solver of the implicit step
 // (a.a, a.kap_n = a.kap_nm1 = kappa^0 set by the caller); synchronises `s`;
 // iterations summed and the larger relative residual of the two stages

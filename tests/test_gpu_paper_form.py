@@ -10,7 +10,8 @@ compression of g_alpha, stress = Psi).
    sampled points (every point is independent in this form, so the oracle
    runs on the samples alone).
 3. Checkpoint round trip (Psi and the host modes of Phi0 = 1 restored).
-4. Refusals: transport on, the SDIRK2 start, alpha = 1.
+4. The SDIRK2 first step in this variable (Section 5.1).
+5. Refusals: transport (explicit or implicit), alpha = 1.
 
 Tolerances: FP64 1e-11 per component; FP32 storage 2e-5 (Psi = xi Phi + h
 cancels: xi ~ (b0/dt)^(1-alpha), so the float rounding of Phi and of the
@@ -92,6 +93,62 @@ def test_paper_form_matches_oracle(dim, n, alpha, m, phi0, varying, precision):
     assert np.all(rel_err_per_component(got, ref) < tol), rel_err_per_component(got, ref)
 
 
+@pytest.mark.parametrize("dim,n,alpha,m,phi0", [(2, (37, 29), 0.5, 8, True), (3, (9, 7, 5), 0.35, 12, True),
+                                                 (2, (20, 9), 0.7, 6, False)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_paper_form_sdirk2_start_matches_oracle(dim, n, alpha, m, phi0, precision):
+    import torch
+    from paper_2411_17294_gb300 import tfs
+    steps, dt, Wi, beta = 5, 4e-3, 1.3, 0.4
+    N = int(np.prod(n))
+    mu, w = soe.soe_nnls(1 - alpha, dt, 50 * dt, m)
+    K = kap_sequence(dim, n, 71, True)
+    P0 = inputs.random_stress(dim, n, 72) if phi0 else None
+    if precision != 0:
+        cast = lambda a: np.asarray(a, np.float32).astype(np.float64)
+        K0 = K
+        K = lambda k: cast(K0(k))
+        P0 = None if P0 is None else cast(P0)
+    pf = PaperForm(dim, N, Wi, beta, dt, mu, w, Phi0=P0, start="sdirk2")
+    pb = PaperForm(dim, N, Wi, beta, dt, mu, w, Phi0=P0)
+    s = make_solver(dim, n, alpha, Wi, beta, dt, mu, w, precision, start="sdirk2")
+    s.set_state(None if P0 is None else torch.as_tensor(P0, dtype=s.dtype, device=s.device))
+    for k in range(steps):
+        kn, km = K(k), K(k - 1) if k > 0 else K(0)
+        ref = pf.step(kn, km)
+        other = pb.step(kn, km)
+        s.step(torch.as_tensor(kn, dtype=s.dtype, device=s.device).contiguous(),
+               torch.as_tensor(km, dtype=s.dtype, device=s.device).contiguous() if k > 0 else None)
+    got = s.stress().double().cpu().numpy()
+    assert not (s.status() & (tfs.TFS_FLAG_NONFINITE | tfs.TFS_FLAG_SINGULAR))
+    s.close()
+    # the start matters, and the library follows the oracle's
+    assert np.max(np.abs(ref - other)) > 1e3 * (1e-11 if precision == 0 else 2e-5) * np.max(np.abs(ref))
+    assert np.all(rel_err_per_component(got, ref) < (1e-11 if precision == 0 else 2e-5))
+
+
+def test_paper_form_sdirk2_checkpoint_restores_the_host_modes():
+    import torch
+    dim, n, alpha, m, dt = 2, (16, 8), 0.5, 8, 5e-3
+    mu, w = soe.soe_nnls(1 - alpha, dt, 1.0, m)
+    _, kap = inputs.spectral_velocity(dim, n, 2, seed=81)
+    s = make_solver(dim, n, alpha, 1.1, 0.3, dt, mu, w, 0, start="sdirk2")
+    s.set_state(torch.as_tensor(inputs.random_stress(dim, n, 82), device=s.device))
+    kt = torch.as_tensor(0.5 * np.asarray(kap), device=s.device).contiguous()
+    for _ in range(3):
+        s.step(kt, kt)
+    ck = s.new_checkpoint()
+    s.save(ck)
+    for _ in range(4):
+        s.step(kt, kt)
+    a = s.stress().clone()
+    s.load(ck)
+    for _ in range(4):
+        s.step(kt, kt)
+    assert torch.equal(s.stress(), a)
+    s.close()
+
+
 def test_paper_form_256_cubed_bench_configuration_sampled():
     import torch
     from paper_2411_17294_gb300 import tfs
@@ -148,7 +205,7 @@ def test_paper_form_refusals():
     mu, w = soe.soe_nnls(0.5, dt, 1.0, 4)
     k = torch.zeros((4, 64), dtype=torch.float64, device="cuda")
     u = torch.zeros((2, 64), dtype=torch.float64, device="cuda")
-    for kw in (dict(transport=True), dict(transport=False, start="sdirk2")):
+    for kw in (dict(transport=True), dict(transport="implicit")):
         s = tfs.Solver(2, n, 0.5, 1.0, 0.5, dt, m=4, precision=tfs.TFS_FP64, mu=mu, w=w, form="paper", **kw)
         s.set_state(None)
         with pytest.raises(tfs.TfsError):
