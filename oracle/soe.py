@@ -22,8 +22,16 @@ kernel that means AAA on s^alpha, then r(s)/s ~ s^(alpha-1).
                 squares on the relative kernel error over [dt/10, T]; the grid
                 size is raised until exactly m weights are positive.  AAA in
                 FP64 produces spurious (complex or positive) poles beyond about
-                20 terms for the ranges used here, so this is the default
-                builder (``soe_build``).
+                20 terms for the ranges used here, so this is the fit the
+                default builder (``soe_build``) completes.
+``soe_complete`` appends one term that carries the kernel's mass on [0, T]
+                missing from a table (the singular part below the fitted
+                times): a Dirac term w_inf delta(t) of the Khristenko form (eq.
+                tf_approximate_kernel_khristenko) realised as one exponential
+                with mu = 1e12/dt and w = w_inf mu, which the BDF2 mode update
+                turns into w_inf times the BDF2 difference quotient of sigma
+                up to a relative 1e-12.  ``soe_build`` = ``soe_nnls`` with m - 1
+                terms completed this way.
 ``soe_expquad`` a plain positive construction: the trapezoidal rule on
                 k(t) = sin(pi alpha)/pi * int exp(alpha x - t e^x) dx.
 ``soe_eval``    evaluates sum_j w_j exp(-mu_j t).
@@ -172,13 +180,14 @@ def _nnls_on_grid(alpha, dt, T, count, lo_dec, hi_dec):
     return mu[keep], w[keep]
 
 
-def soe_nnls(alpha: float, dt: float, T: float, m: int):
+def soe_nnls(alpha: float, dt: float, T: float, m: int, max_mass: float = 1.01):
     """Positive SOE with exactly m terms (see the module docstring).
 
     For each grid extension (lo, hi) in decades beyond [1/T, 1/dt] and each
     grid size from m upwards, NNLS picks the positive weights; among the fits
-    with exactly m positive weights the one with the smallest maximum relative
-    error on [dt, T] is returned as (mu, w), sorted by mu."""
+    with exactly m positive weights (and mass at most max_mass times the
+    kernel's) the one with the smallest maximum relative error on [dt, T] is
+    returned as (mu, w), sorted by mu."""
     if not (0.0 < alpha < 1.0):
         raise ValueError("alpha must lie in (0, 1)")
     if m < 1:
@@ -194,8 +203,8 @@ def soe_nnls(alpha: float, dt: float, T: float, m: int):
                 # the error on [dt, T] yet enters the scheme through its mass
                 # w_j / mu_j (the per-mode weight rho_j of the BDF2 update);
                 # NNLS sometimes gives such terms huge weights, so fits whose
-                # mass on [0, T] exceeds the kernel's are rejected
-                if soe_mass(mu, w, T) > 1.01 * kernel_mass(alpha, T):
+                # mass on [0, T] exceeds max_mass times the kernel's are rejected
+                if soe_mass(mu, w, T) > max_mass * kernel_mass(alpha, T):
                     continue
                 err = max_rel_error(alpha, mu, w, dt, T)
                 if best is None or err < best[0]:
@@ -205,8 +214,32 @@ def soe_nnls(alpha: float, dt: float, T: float, m: int):
     return best[1], best[2]
 
 
+DIRAC_RATE = 1e12        # mu dt of the completing term
+
+
+def soe_complete(alpha: float, mu, w, dt: float, T: float):
+    """(mu, w) with one term appended that carries kernel_mass - soe_mass on
+    [0, T] (see the module docstring); unchanged when nothing is missing."""
+    mu = np.asarray(mu, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    missing = kernel_mass(alpha, T) - soe_mass(mu, w, T)
+    if not missing > 1e-12 * kernel_mass(alpha, T):
+        return mu.copy(), w.copy()
+    rate = DIRAC_RATE / dt
+    return np.append(mu, rate), np.append(w, missing * rate)
+
+
 def soe_build(alpha: float, dt: float, T: float, m: int):
-    """Default SOE used by the tests: ``soe_nnls``."""
+    """Default SOE: ``soe_nnls`` with m - 1 terms and no more mass than the
+    kernel, plus the completing term (m terms; the m-term fit when no such fit
+    exists or nothing is missing)."""
+    if m >= 2:
+        try:
+            mu, w = soe_complete(alpha, *soe_nnls(alpha, dt, T, m - 1, max_mass=1.0 + 1e-9), dt, T)
+            if len(mu) == m:
+                return mu, w
+        except ValueError:
+            pass
     return soe_nnls(alpha, dt, T, m)
 
 

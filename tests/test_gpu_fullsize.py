@@ -7,16 +7,18 @@ the stress at a sampled point after s steps depends only on the points within
 2 s grid cells (radius-2 stencil), so the oracle runs on the periodic
 (4 s + 1)^3 block centred on each sample and its centre value is exact.
 
-2D 1024^2 (m = 32, FP32, dt = 5e-4, alpha in {0.3, 0.5, 0.8}): the
-explicit transport is outside its stability region at these sizes, so these
-cases run the pointwise law (transport off) for many steps; the oracle then
-runs on the sampled points alone.
+2D 1024^2 (m = 32, FP32 and FP64, dt = 5e-4, alpha in {0.3, 0.5, 0.8}, 1000
+steps): the explicit transport is outside its stability region at these sizes,
+so these cases run the pointwise law (transport off); the oracle then runs on
+the sampled points alone, FP32 storage is compared with the FP64 form over the
+whole field, and the zero-flow case is compared with the Mittag-Leffler closed
+form.
 """
 import numpy as np
 import pytest
 
 from helpers import ensure_lib, rel_err_per_component
-from oracle import orc
+from oracle import orc, special
 from oracle import soe as osoe
 from paper_2411_17294_gb300 import inputs
 
@@ -77,23 +79,57 @@ def test_3d_256_bench_configuration_sampled():
 def test_2d_1024_pointwise_sampled(alpha):
     import torch
     from paper_2411_17294_gb300 import tfs
-    n, m, Wi, beta, dt, steps = (1024, 1024), 32, 1.0, 0.5, 5e-4, 300
+    n, m, Wi, beta, dt, steps = (1024, 1024), 32, 1.0, 0.5, 5e-4, 1000
     mu, w = osoe.soe_nnls(alpha, dt, 1000 * dt, m)
     dev = torch.device("cuda", 0)
     u, kap = inputs.spectral_velocity(2, n, 32, 2, device=dev)
     kap = 0.05 * kap      # keep the pointwise stress moderate over the run
-    s = tfs.Solver(2, n, alpha, Wi, beta, dt, m=m, precision=tfs.TFS_FP32, mu=mu, w=w, transport=False)
-    kt = torch.as_tensor(kap, dtype=torch.float32, device=dev).contiguous()
     sig0 = inputs.random_stress(2, n, 5, amplitude=0.5)
-    s.set_state(torch.as_tensor(sig0, dtype=torch.float32, device=dev))
-    for _ in range(steps):
-        s.step(kt, kt, None)
-    out = s.stress().cpu().numpy().astype(np.float64)
-    s.close()
+    outs = {}
+    for prec in (tfs.TFS_FP32, tfs.TFS_FP64):
+        s = tfs.Solver(2, n, alpha, Wi, beta, dt, m=m, precision=prec, mu=mu, w=w, transport=False)
+        kt = torch.as_tensor(kap, dtype=s.dtype, device=dev).contiguous()
+        s.set_state(torch.as_tensor(sig0, dtype=s.dtype, device=dev))
+        for _ in range(steps):
+            s.step(kt, kt, None)
+        outs[prec] = s.stress().cpu().numpy().astype(np.float64)
+        s.close()
     rng = np.random.default_rng(7)
     pts = np.unique(np.concatenate([rng.integers(0, 1024 * 1024, size=64), [0, 1024 * 1024 - 1]]))
-    kap32 = kt.cpu().numpy().astype(np.float64)[:, pts]
+    kap64 = torch.as_tensor(kap, dtype=torch.float64).cpu().numpy()[:, pts]
+    kap32 = kap64.astype(np.float32).astype(np.float64)
     sig032 = sig0.astype(np.float32).astype(np.float64)[:, pts]
-    prob = orc.Problem(dim=2, n=(len(pts), 1), alpha=alpha, Wi=Wi, beta=beta, dt=dt, mu=mu, w=w)
-    ref = orc.forward(prob, sig032, np.ascontiguousarray(kap32), None, steps)
-    assert np.all(rel_err_per_component(out[:, pts], ref) < 2e-5)
+    ref32 = orc.forward(orc.Problem(dim=2, n=(len(pts), 1), alpha=alpha, Wi=Wi, beta=beta, dt=dt, mu=mu, w=w),
+                        sig032, np.ascontiguousarray(kap32), None, steps)
+    ref64 = orc.forward(orc.Problem(dim=2, n=(len(pts), 1), alpha=alpha, Wi=Wi, beta=beta, dt=dt, mu=mu, w=w),
+                        np.ascontiguousarray(sig0[:, pts]), np.ascontiguousarray(kap64), None, steps)
+    assert np.all(rel_err_per_component(outs[tfs.TFS_FP32][:, pts], ref32) < 2e-5)
+    assert np.all(rel_err_per_component(outs[tfs.TFS_FP64][:, pts], ref64) < 1e-11)
+    # FP32 storage against the FP64 form over the whole field (inputs rounded once)
+    assert np.all(rel_err_per_component(outs[tfs.TFS_FP32], outs[tfs.TFS_FP64]) < 2e-5)
+
+
+@pytest.mark.parametrize("alpha", [0.3, 0.5, 0.8])
+def test_2d_1024_zero_flow_mittag_leffler(alpha):
+    # Zero flow on the full 1024^2 grid, 1000 steps of 5e-4: sigma(T) = sigma0
+    # E_alpha(-T^alpha/Wi) at every point, up to the scheme's error, with the
+    # mass-completed SOE and the SDIRK2 start (about 1e-6 on the oracle).
+    import torch
+    from paper_2411_17294_gb300 import tfs
+    n, m, Wi, dt, steps = (1024, 1024), 32, 1.0, 5e-4, 1000
+    T = dt * steps
+    mu, w = osoe.soe_build(alpha, dt, T, m)
+    exact = special.mittag_leffler(alpha, -T ** alpha / Wi)
+    dev = torch.device("cuda", 0)
+    sig0 = inputs.random_stress(2, n, 9, amplitude=1.0)
+    for prec, tol in ((tfs.TFS_FP64, 5e-6), (tfs.TFS_FP32, 3e-5)):
+        s = tfs.Solver(2, n, alpha, Wi, 0.5, dt, m=m, precision=prec, mu=mu, w=w, transport=False, start="sdirk2")
+        s0 = torch.as_tensor(sig0, dtype=s.dtype, device=dev)
+        k = torch.zeros((4, n[0] * n[1]), dtype=s.dtype, device=dev)
+        s.set_state(s0)
+        for _ in range(steps):
+            s.step(k, k, None)
+        out = s.stress().double()
+        s.close()
+        err = (out - exact * s0.double()).abs().amax(dim=1) / (exact * s0.double()).abs().amax(dim=1)
+        assert float(err.max()) < tol, (prec, err)
