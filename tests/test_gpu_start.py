@@ -6,7 +6,7 @@ BDF2 steps whose history is the initial state.
 2. Implicit transport: both stage systems through the Krylov solver.
 3. The paper's convergence case on the GPU (no flow, cos(2 pi x) cos(4 pi y),
    eps = 1e-2, alpha = 0.5, weighted Bochner norm): order -> 1 + alpha with
-   the SDIRK2 start and an SOE fitted down to 1e-3 dt, order 1 with BDF2.
+   the SDIRK2 start and the mass-completed SOE, order 1 with BDF2.
 4. Refusals: explicit transport at the first step, alpha = 1 at creation.
 
 Tolerances as for the default step: FP64 1e-11 per component (1e-10 with the
@@ -102,7 +102,7 @@ def test_sdirk2_start_implicit_transport_matches_oracle(dim, n, alpha, m, eps, s
     assert np.all(rel_err_per_component(got, ref) < (1e-10 if precision == 0 else 2e-5))
 
 
-def _gpu_bochner_errors(start, dts, m=32, fit_from=1e-3):
+def _gpu_bochner_errors(start, dts, m=32):
     import torch
     from paper_2411_17294_gb300 import tfs
     alpha, Wi, eps, T = 0.5, 1.0, 1e-2, 1.0
@@ -116,7 +116,7 @@ def _gpu_bochner_errors(start, dts, m=32, fit_from=1e-3):
     errs = []
     for dt in dts:
         steps = int(round(T / dt))
-        mu, w = soe.soe_nnls(alpha, dt * fit_from, T, m)
+        mu, w = soe.soe_build(alpha, dt, T, m)
         s = tfs.Solver(2, n, alpha, Wi, 0.5, dt, m=m, precision=tfs.TFS_FP64, mu=mu, w=w, eps=eps, L=(1.0, 1.0),
                        transport="implicit", start=start)
         s.set_state(torch.as_tensor(np.tile(shape, (3, 1)), device=s.device))

@@ -100,6 +100,25 @@ def test_mittag_leffler_special_cases():
     # complex argument: E_1(i y) = exp(i y)
     y = np.linspace(-2, 2, 9)
     assert np.allclose(special.mittag_leffler(1.0, 1j * y), np.exp(1j * y), rtol=1e-13, atol=1e-14)
+    # the spectral-integral branch (real z < -0.5, alpha < 1): erfcx far out
+    xl = np.linspace(0.6, 40.0, 30)
+    assert np.allclose(special.mittag_leffler(0.5, -xl), scipy.special.erfcx(xl), rtol=1e-12, atol=0.0)
+
+
+@pytest.mark.parametrize("alpha", [0.2, 0.3, 0.7, 0.9])
+def test_mittag_leffler_branches_agree_and_large_argument(alpha):
+    # near the switch the power series is still accurate: both branches agree
+    for x in (0.51, 0.7, 0.9):
+        series = math.fsum((-x) ** k / math.gamma(alpha * k + 1.0) for k in range(150))
+        assert abs(special._ml_negative_real(alpha, x) / series - 1.0) < 1e-13
+    # far out: E_alpha(-x) ~ sum_{k>=1} (-1)^(k+1) x^-k / Gamma(1 - alpha k)
+    x = 1e4
+    asym = sum((-1) ** (k + 1) * x ** -k * scipy.special.rgamma(1.0 - alpha * k) for k in range(1, 7))
+    assert abs(special.mittag_leffler(alpha, -x) / asym - 1.0) < 1e-12
+    # the decay case of the paper-variable pin (alpha = 0.3, lambda t^alpha ~ 3),
+    # where the power series loses every digit: between the neighbours' bounds
+    e = special.mittag_leffler(alpha, -2.97)
+    assert 0.0 < e < special.mittag_leffler(alpha, -2.5) < 1.0
 
 
 def test_mittag_leffler_against_mpmath():
