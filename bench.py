@@ -353,7 +353,7 @@ def paper_form_bytes_per_point(dim: int, m: int, elem: int) -> int:
     return 3 * m * nc * elem + 2 * dim * dim * elem + 4 * nc * elem
 
 
-def paper_form_record(dev, steps: int, warmup: int):
+def paper_form_record(dev, steps: int, warmup: int, grid: int | None = None):
     """The step in the paper's own variable (Phi, Psi = D^{1-alpha} Phi; the SOE
     approximates g_alpha) on the 3D 256^3 m = 32 FP32 grid of the main workload,
     pointwise (this form carries no transport): time per step and the HBM
@@ -361,7 +361,9 @@ def paper_form_record(dev, steps: int, warmup: int):
     import torch
 
     from paper_2411_17294_gb300 import inputs, soe, tfs
-    W = WORKLOAD
+    W = dict(WORKLOAD)
+    if grid:
+        W["n"] = (grid,) * 3
     dt = W["dt"]
     mu, w = soe.build(1.0 - W["alpha"], dt, W["horizon_steps"] * dt, W["m"])
     _, kap = inputs.spectral_velocity(3, W["n"], W["kmax"], W["seed"], device=dev)
@@ -395,8 +397,8 @@ def paper_form_record(dev, steps: int, warmup: int):
     bpp = paper_form_bytes_per_point(3, W["m"], 4)
     peak, peak_kind = read_peaks()
     achieved = bpp * N / (launch_ms * 1e-3) / 1e9
-    return {"workload": "paper's variable Phi, Psi = D^{1-alpha} Phi (Section 3.4), 3D 256^3, m=32, FP32, "
-                        "pointwise (no transport), alpha=0.6, SOE of g_alpha",
+    return {"workload": f"paper's variable Phi, Psi = D^{{1-alpha}} Phi (Section 3.4), 3D {W['n'][0]}^3, m=32, "
+                        "FP32, pointwise (no transport), alpha=0.6, SOE of g_alpha",
             "ms_per_step": e0.elapsed_time(e1) / steps, "avg_launch_ms": launch_ms,
             "G_point_mode_updates_per_s": N * W["m"] / (launch_ms * 1e-3) / 1e9,
             "algorithmic_bytes_per_point": bpp, "achieved_gbs": achieved, "peak": peak, "peak_kind": peak_kind,
@@ -474,7 +476,8 @@ def main():
         from paper_2411_17294_gb300 import build as tbuild
         tbuild.build()
         torch.cuda.set_device(0)
-        print(json.dumps(paper_form_record(torch.device("cuda", 0), steps=args.steps, warmup=args.warmup)), flush=True)
+        print(json.dumps(paper_form_record(torch.device("cuda", 0), steps=args.steps, warmup=args.warmup,
+                                           grid=args.grid)), flush=True)
         return
 
     import numpy as np
