@@ -29,7 +29,14 @@ BDF2 (Section 4.1):
 the same recurrence with Phi0 = 1.  The SOE of g_alpha is that of the Caputo
 kernel of order 1 - alpha (t^(alpha-1)/Gamma(alpha) = t^-(1-alpha)/Gamma(alpha)),
 so the tables of oracle.soe with order 1 - alpha serve.  Zero past: Phi^{-1} =
-Phi^0, phi_j^0 = phi_j^{-1} = 0.  Every point is independent (no transport).
+Phi^0, phi_j^0 = phi_j^{-1} = 0, Psi^0 = Psi^{-1} = 0.
+
+Transport (optional, on a periodic grid): the operator (u.grad - eps Lap) acts
+on Psi; taken explicitly on the extrapolation E = 2 Psi^n - Psi^{n-1} (the
+choice the stress form makes for sigma), it adds -dt (sum_a u_a D_a E - eps Lap E)
+to the right-hand side, with D_a the upwind-biased third-order difference
+(radius 2, biased by the sign of u_a at the point) or the central second-order
+one, and Lap the three-point Laplacian per axis, periodic (numpy.roll).
 The per-point systems are assembled column by column from unit vectors and
 solved with numpy.linalg.solve.
 """
@@ -59,8 +66,15 @@ def _upper_convected(dim, K, s):
 class PaperForm:
     """State of the paper-variable scheme on a set of independent points."""
 
-    def __init__(self, dim, N, Wi, beta, dt, mu, w, Phi0=None, Re=1.0, start="bdf2"):
+    def __init__(self, dim, N, Wi, beta, dt, mu, w, Phi0=None, Re=1.0, start="bdf2", grid=None, L=None,
+                 eps=0.0, stencil=0):
         self.dim, self.N = dim, N
+        # transport: grid shape (x fastest), box lengths, eps, stencil (0 upwind3, 1 central2)
+        self.grid = tuple(grid) if grid is not None else None
+        if self.grid is not None and int(np.prod(self.grid)) != N:
+            raise ValueError("grid does not match N")
+        self.L = tuple(L) if L is not None else (2 * np.pi,) * dim
+        self.eps, self.stencil = eps, stencil
         self.nc = 3 if dim == 2 else 6
         self.Wi, self.dt = Wi, dt
         self.G = (1.0 - beta) / (Wi * Re)
@@ -77,6 +91,8 @@ class PaperForm:
         self.phi0_nm1 = np.zeros(m)
         self.kap_prev = None
         self.Psi = None
+        self.Psi_n = np.zeros((self.nc, N))
+        self.Psi_nm1 = np.zeros((self.nc, N))
         self.start = start       # first step: "bdf2" (empty past) or "sdirk2" (Section 5.1)
         self.n = 0
 
@@ -127,13 +143,42 @@ class PaperForm:
         Psi = xi1 * Phi - h1
         return Phi, phi, phi0, Psi
 
-    def step(self, kap_n, kap_nm1=None):
-        """Advance one step; returns the stress Psi2^{n+1} [nc][N]."""
+    def _transport(self, E, u):
+        """dt (sum_a u_a D_a E - eps Lap E) for E [nc][N], u [d][N], periodic."""
+        d, dt = self.dim, self.dt
+        shp = (self.nc,) + tuple(reversed(self.grid))          # [nc][(z)][y][x]
+        F = E.reshape(shp)
+        U = np.asarray(u, float).reshape((d,) + tuple(reversed(self.grid)))
+        out = np.zeros(shp)
+        for a in range(d):
+            ax = F.ndim - 1 - a                                  # x is the last array axis
+            h = self.L[a] / self.grid[a]
+            at = lambda k: np.roll(F, -k, axis=ax)               # F at offset k along axis a
+            ua = U[a][None]
+            if self.stencil == 1:
+                D = (at(1) - at(-1)) / (2 * h)
+            else:
+                fw = (at(-2) - 6 * at(-1) + 3 * F + 2 * at(1)) / (6 * h)
+                bw = (-2 * at(-1) - 3 * F + 6 * at(1) - at(2)) / (6 * h)
+                D = np.where(ua >= 0, fw, bw)
+            out += ua * D
+            if self.eps != 0.0:
+                out -= self.eps * (at(-1) - 2 * F + at(1)) / h ** 2
+        return dt * out.reshape(self.nc, self.N)
+
+    def step(self, kap_n, kap_nm1=None, u=None):
+        """Advance one step; returns the stress Psi2^{n+1} [nc][N].  u [d][N]
+        turns the transport on (grid required)."""
         d, N, nc, dt = self.dim, self.N, self.nc, self.dt
+        if u is not None and self.grid is None:
+            raise ValueError("transport needs the grid")
         if self.start == "sdirk2" and self.n == 0:
+            if u is not None:
+                raise ValueError("the SDIRK2 start is pointwise here")
             kap0 = np.asarray(kap_n, float).reshape(d * d, N)
             Phi, phi, phi0, Psi = self._sdirk2_first_step(kap0.T.reshape(N, d, d))
             self.Psi = Psi
+            self.Psi_nm1, self.Psi_n = self.Psi_n, Psi
             self.Phi_nm1, self.Phi_n = self.Phi_n, Phi
             self.phi_nm1, self.phi_n = self.phi_n, phi
             self.phi0_nm1, self.phi0_n = self.phi0_n, phi0
@@ -155,6 +200,8 @@ class PaperForm:
         KS = K + np.swapaxes(K, 1, 2)
         src = np.stack([KS[:, i, j] for (i, j) in P])
         rhs = -B1 * self.Phi_n - B2 * self.Phi_nm1 + dt * Lh + dt * self.G * src * psi0
+        if u is not None:
+            rhs = rhs - self._transport(2.0 * self.Psi_n - self.Psi_nm1, u)
         # system matrix per point: b0 I - dt xi (L(K) - I/Wi), column k = image of unit vector k
         M = np.zeros((N, nc, nc))
         for k in range(nc):
@@ -166,6 +213,7 @@ class PaperForm:
         phi_new = self.c[:, None, None] * (-B1 * self.phi_n - B2 * self.phi_nm1 + dt * Phi[None])
         phi0_new = self.c * (-B1 * self.phi0_n - B2 * self.phi0_nm1 + dt * 1.0)
         self.Psi = self.xi * Phi + h
+        self.Psi_nm1, self.Psi_n = self.Psi_n, self.Psi
         self.Phi_nm1, self.Phi_n = self.Phi_n, Phi
         self.phi_nm1, self.phi_n = self.phi_n, phi_new
         self.phi0_nm1, self.phi0_n = self.phi0_n, phi0_new
