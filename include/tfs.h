@@ -108,8 +108,14 @@ enum {
                                  D^{1-alpha} 1 from the same modes, on the host.  The stress returned is
                                  Psi (zero before the first step); tfs_set_state sets Phi(0) (NULL: 0).
                                  BDF2 on Phi and the modes (Section 4.1), one point system per point.
-                                 Needs alpha < 1 (else TFS_ERR_ARG here) and transport 0 (else tfs_step
-                                 returns TFS_ERR_ARG); either start; tfs_backward refuses it (TFS_ERR_ARG).
+                                 With transport 1 the operator u.grad - eps Lap acts on the
+                                 extrapolation 2 Psi^n - Psi^{n-1}, explicitly, with the stencils of the
+                                 stress form; the Courant check of tfs_transport_limit (derived for the
+                                 stress form) is not applied.  Needs alpha < 1 and transport 0 or 1
+                                 (TFS_ERR_ARG here, or from tfs_set_param(TFS_PARAM_TRANSPORT, 2));
+                                 either start (SDIRK2 without transport); tfs_backward refuses it
+                                 (TFS_ERR_ARG).  The workspace grows by 2 nc N elements (Psi^n, Psi^{n-1});
+                                 with a workspace bound, a form it does not fit returns TFS_ERR_NOWORKSPACE.
                                  Changing the form discards the state (call tfs_set_state again) */
 };
 

@@ -62,6 +62,8 @@ struct tfs_ctx {
     char* trans = nullptr;         // transport term A [nc][N] of the current step
     char* modes[2] = {nullptr, nullptr};
     int cur_sig = 0, prev_sig = 1; // ring slots of levels n and n-1
+    char* psi[2] = {nullptr, nullptr};   // the paper's variable: Psi^n (psi[cur_psi]) and Psi^{n-1}
+    int cur_psi = 0;
     int cur_mode = 0;              // ring slot of modes level n (n-1 in the other)
     bool sigma0_zero = true;
     bool state_set = false;
@@ -92,6 +94,8 @@ struct tfs_ctx {
     size_t modes_bytes() const { return (size_t)m * field_bytes(); }
     int third_sig() const { return 3 - cur_sig - prev_sig; }
     bool explicit_transport() const { return transport == 1; }
+    // the stability bound of the explicit transport is derived for the stress form
+    bool checked_transport() const { return transport == 1 && form == TFS_FORM_STRESS; }
     bool implicit_transport() const { return transport == 2; }
     bool paper() const { return form == TFS_FORM_PAPER; }
 };
@@ -241,7 +245,7 @@ double courant_limit(tfs_ctx* h) {
 
 // declared bounds (eps, and umax when given) exceed the limit
 bool limits_violated(tfs_ctx* h) {
-    if (!h->explicit_transport() || !limits_known(h)) return false;
+    if (!h->checked_transport() || !limits_known(h)) return false;
     const double lim = courant_limit(h);
     if (lim < 0.0) return true;
     return h->umax >= 0.0 && courant_coef(h) * h->umax * sum_inv_h(h) > lim;
@@ -252,7 +256,7 @@ bool limits_violated(tfs_ctx* h) {
 size_t krylov_bytes(const tfs_ctx* h) {
     return (10 + 2 * (size_t)h->nc) * (size_t)h->nc * (size_t)h->N * sizeof(double);
 }
-size_t forward_bytes_for(const tfs_ctx* h, int transport);
+size_t forward_bytes_for(const tfs_ctx* h, int transport, int form);
 
 void layout_forward(tfs_ctx* h, char* base) {
     char* p = base;
@@ -270,6 +274,13 @@ void layout_forward(tfs_ctx* h, char* base) {
         h->modes[i] = p;
         p += align_up(h->modes_bytes());
     }
+    h->psi[0] = h->psi[1] = nullptr;
+    if (h->paper()) {
+        for (int i = 0; i < 2; ++i) {
+            h->psi[i] = p;
+            p += align_up(h->field_bytes());
+        }
+    }
     h->kry = nullptr;
     h->partials = nullptr;
     if (h->implicit_transport()) {
@@ -279,13 +290,14 @@ void layout_forward(tfs_ctx* h, char* base) {
     }
 }
 
-size_t forward_bytes_for(const tfs_ctx* h, int transport) {
+size_t forward_bytes_for(const tfs_ctx* h, int transport, int form) {
     size_t b = kAlign + 5 * align_up(h->field_bytes()) + 2 * align_up(h->modes_bytes());
+    if (form == TFS_FORM_PAPER) b += 2 * align_up(h->field_bytes());
     if (transport == 2) b += align_up(krylov_bytes(h)) + align_up(sizeof(double) * (2 * kImpBlocks + 32));
     return b;
 }
 
-size_t forward_bytes(const tfs_ctx* h) { return forward_bytes_for(h, h->transport); }
+size_t forward_bytes(const tfs_ctx* h) { return forward_bytes_for(h, h->transport, h->form); }
 
 F2c split_f2(double v) {
     F2c r;
@@ -307,7 +319,7 @@ void fill_common(tfs_ctx* h, FwdArgs<T>& a) {
     a.G = (1.0 - h->beta) / (h->Wi * h->Re);
     a.eps = h->eps;
     for (int i = 0; i < 3; ++i) a.inv_h[i] = (double)h->n[i] / h->L[i];
-    a.courant_coef = (h->explicit_transport() && limits_known(h)) ? courant_coef(h) : 0.0;
+    a.courant_coef = (h->checked_transport() && limits_known(h)) ? courant_coef(h) : 0.0;
     a.courant_limit = courant_limit(h);
     a.flags = h->flags;
     a.eta_f2 = split_f2(a.eta);
@@ -455,7 +467,10 @@ template <typename T>
 void fill_paper(tfs_ctx* h, FwdArgs<T>& a) {
     const double psi0 = paper_psi0(h);
     a.sigma0 = nullptr;
-    a.psi = (T*)h->trans;
+    a.psi = (T*)h->psi[1 - h->cur_psi];          // Psi^{n+1} over Psi^{n-1}, after the pre-pass has read it
+    a.psi_n = (const T*)h->psi[h->cur_psi];
+    a.psi_nm1 = (const T*)h->psi[1 - h->cur_psi];
+    a.courant_coef = 0.0;                        // the explicit-transport bound is the stress form's
     a.xi = h->xi_p;
     a.inv_wi = 1.0 / h->Wi;
     a.a = kB0 + h->dt * h->xi_p / h->Wi;
@@ -524,12 +539,12 @@ int do_first_step_sdirk2(tfs_ctx* h, const void* kn, const void* u, void* sig_co
         if (e == cudaSuccess && h->is_double()) {
             StartArgs<double> a{(const double*)kn, (const double*)h->sig[h->cur_sig], (const double*)h->modes[cm],
                                 (double*)h->modes[pm], (double*)h->sig[nxt], (double*)sig_copy, h->flags, h->N, h->m,
-                                h->dt, a_p, G, (double*)h->trans, 1.0 / h->Wi};
+                                h->dt, a_p, G, (double*)h->psi[1 - h->cur_psi], 1.0 / h->Wi};
             e = launch_start_paper_f64(a, c, h->dim, s);
         } else if (e == cudaSuccess) {
             StartArgs<float> a{(const float*)kn, (const float*)h->sig[h->cur_sig], (const float*)h->modes[cm],
                                (float*)h->modes[pm], (float*)h->sig[nxt], (float*)sig_copy, h->flags, h->N, h->m,
-                               h->dt, a_p, G, (float*)h->trans, 1.0 / h->Wi};
+                               h->dt, a_p, G, (float*)h->psi[1 - h->cur_psi], 1.0 / h->Wi};
             e = launch_start_paper_f32(a, c, h->dim, s);
         }
         if (e == cudaSuccess && h->ev_after) e = cudaEventRecord(h->ev_after, s);
@@ -559,6 +574,7 @@ int do_first_step_sdirk2(tfs_ctx* h, const void* kn, const void* u, void* sig_co
     h->prev_sig = h->cur_sig;
     h->cur_sig = nxt;
     h->cur_mode = pm;
+    if (h->paper()) h->cur_psi = 1 - h->cur_psi;
     h->step += 1;
     h->last_stream = s;
     return TFS_OK;
@@ -572,7 +588,7 @@ int do_step(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* s
     if (h->transport && !u) return TFS_ERR_ARG;
     if (limits_violated(h)) return TFS_ERR_UNSTABLE;
     if (!knm1) knm1 = kn;
-    if (h->paper() && h->transport != 0) return TFS_ERR_ARG;
+    if (h->paper() && h->implicit_transport()) return TFS_ERR_ARG;
     if (h->start == TFS_START_SDIRK2 && h->step == 0) return do_first_step_sdirk2(h, kn, u, sig_copy, s);
     if (h->implicit_transport()) return do_step_implicit(h, kn, knm1, u, sig_copy, s);
     const int nxt = h->third_sig();
@@ -625,7 +641,10 @@ int do_step(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* s
         e = launch_forward_f32(a, cfg, s);
     }
     if (e != cudaSuccess) return TFS_ERR_CUDA;
-    if (h->paper()) paper_advance_phi0(h);
+    if (h->paper()) {
+        paper_advance_phi0(h);
+        h->cur_psi = 1 - h->cur_psi;
+    }
     h->prev_sig = h->cur_sig;
     h->cur_sig = nxt;
     if (!h->classic()) h->cur_mode = pm;
@@ -688,7 +707,7 @@ int tfs_set_param(tfs_handle h, int key, double value) {
             return TFS_OK;
         case TFS_PARAM_EPS:
             if (!(value >= 0.0)) return TFS_ERR_ARG;
-            if (h->explicit_transport() && diffusion_fraction(h, value) > 0.9) return TFS_ERR_UNSTABLE;
+            if (h->checked_transport() && diffusion_fraction(h, value) > 0.9) return TFS_ERR_UNSTABLE;
             h->eps = value;
             return TFS_OK;
         case TFS_PARAM_STENCIL:
@@ -698,13 +717,14 @@ int tfs_set_param(tfs_handle h, int key, double value) {
             return TFS_OK;
         case TFS_PARAM_TRANSPORT:
             if (value != 0.0 && value != 1.0 && value != 2.0) return TFS_ERR_ARG;
-            if (value == 2.0 && h->ws && h->ws_bytes < forward_bytes_for(h, 2)) return TFS_ERR_NOWORKSPACE;
+            if (value == 2.0 && h->paper()) return TFS_ERR_ARG;
+            if (h->ws && h->ws_bytes < forward_bytes_for(h, (int)value, h->form)) return TFS_ERR_NOWORKSPACE;
             h->transport = (int)value;
             if (h->ws) layout_forward(h, h->ws);
             return TFS_OK;
         case TFS_PARAM_UMAX: {
             if (!(value >= 0.0)) return TFS_ERR_ARG;
-            if (h->explicit_transport() && limits_known(h) && courant_coef(h) * value * sum_inv_h(h) > courant_limit(h))
+            if (h->checked_transport() && limits_known(h) && courant_coef(h) * value * sum_inv_h(h) > courant_limit(h))
                 return TFS_ERR_UNSTABLE;
             h->umax = value;
             return TFS_OK;
@@ -719,9 +739,11 @@ int tfs_set_param(tfs_handle h, int key, double value) {
             return TFS_OK;
         case TFS_PARAM_FORM:
             if (value != TFS_FORM_STRESS && value != TFS_FORM_PAPER) return TFS_ERR_ARG;
-            if (value == TFS_FORM_PAPER && h->classic()) return TFS_ERR_ARG;
+            if (value == TFS_FORM_PAPER && (h->classic() || h->implicit_transport())) return TFS_ERR_ARG;
+            if (h->ws && h->ws_bytes < forward_bytes_for(h, h->transport, (int)value)) return TFS_ERR_NOWORKSPACE;
             if ((int)value != h->form) h->state_set = false;   // the state means something else now
             h->form = (int)value;
+            if (h->ws) layout_forward(h, h->ws);
             return TFS_OK;
         case TFS_PARAM_START:
             if (value != TFS_START_BDF2 && value != TFS_START_SDIRK2) return TFS_ERR_ARG;
@@ -822,12 +844,14 @@ int tfs_set_state(tfs_handle h, const void* sigma0, void* stream) {
     h->cur_sig = 0;
     h->prev_sig = 1;
     h->cur_mode = 0;
+    h->cur_psi = 0;
     const long long count = (long long)h->nc * h->N;
     cudaError_t e = launch_fill_levels(h->sig[0], h->sig[1], h->sigma0, sigma0, count, h->is_double(), s);
     if (e == cudaSuccess && h->m > 0) e = launch_zero(h->modes[0], h->modes_bytes(), s);
     if (e == cudaSuccess && h->m > 0) e = launch_zero(h->modes[1], h->modes_bytes(), s);
     if (e == cudaSuccess) e = launch_zero(h->flags, kAlign, s);
-    if (e == cudaSuccess) e = launch_zero(h->trans, h->field_bytes(), s);   // Psi before the first step: 0
+    for (int i = 0; i < 2 && h->paper(); ++i)    // Psi before the first step, and its past: 0
+        if (e == cudaSuccess) e = launch_zero(h->psi[i], h->field_bytes(), s);
     if (e != cudaSuccess) return TFS_ERR_CUDA;
     paper_reset_phi0(h, 0);
     h->sigma0_zero = (sigma0 == nullptr);
@@ -847,7 +871,7 @@ int tfs_get_stress(tfs_handle h, void* out, void* stream) {
     if (!h->ws) return TFS_ERR_NOWORKSPACE;
     if (!h->state_set) return TFS_ERR_STATE;
     h->last_stream = (cudaStream_t)stream;
-    const void* src = h->paper() ? (const void*)h->trans : (const void*)h->sig[h->cur_sig];
+    const void* src = h->paper() ? (const void*)h->psi[h->cur_psi] : (const void*)h->sig[h->cur_sig];
     return cuda_err(cudaMemcpyAsync(out, src, h->field_bytes(), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
 }
 
@@ -862,7 +886,7 @@ int tfs_last_solve(tfs_handle h, int* iterations, double* relative_residual) {
 
 size_t tfs_checkpoint_bytes(tfs_handle h) {
     if (!valid_handle(h)) return 0;
-    return kHeaderBytes + (h->paper() ? 4 : 3) * align_up(h->field_bytes()) + 2 * align_up(h->modes_bytes());
+    return kHeaderBytes + (h->paper() ? 5 : 3) * align_up(h->field_bytes()) + 2 * align_up(h->modes_bytes());
 }
 
 int tfs_save(tfs_handle h, void* dst, void* stream) {
@@ -893,7 +917,11 @@ int tfs_save(tfs_handle h, void* dst, void* stream) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->modes[1 - h->cur_mode], mb, cudaMemcpyDeviceToDevice, s);
         p += align_up(mb);
     }
-    if (h->paper() && e == cudaSuccess) e = cudaMemcpyAsync(p, h->trans, fb, cudaMemcpyDeviceToDevice, s);
+    if (h->paper()) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->psi[h->cur_psi], fb, cudaMemcpyDeviceToDevice, s);
+        p += align_up(fb);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->psi[1 - h->cur_psi], fb, cudaMemcpyDeviceToDevice, s);
+    }
     h->last_stream = s;
     return cuda_err(e);
 }
@@ -931,7 +959,12 @@ int tfs_load(tfs_handle h, const void* src, void* stream) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->modes[1], p, mb, cudaMemcpyDeviceToDevice, s);
         p += align_up(mb);
     }
-    if (h->paper() && e == cudaSuccess) e = cudaMemcpyAsync(h->trans, p, fb, cudaMemcpyDeviceToDevice, s);
+    if (h->paper()) {
+        h->cur_psi = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->psi[0], p, fb, cudaMemcpyDeviceToDevice, s);
+        p += align_up(fb);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->psi[1], p, fb, cudaMemcpyDeviceToDevice, s);
+    }
     if (e != cudaSuccess) return TFS_ERR_CUDA;
     h->step = (long long)words[8];
     if (h->paper()) paper_reset_phi0(h, h->step);

@@ -631,7 +631,8 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
         unsigned fl = 0u;
         if constexpr (PAPER) {
             // (b0 + dt xi/Wi) Phi - dt xi L(kappa*) Phi
-            //     = -b1 Phi^n - b2 Phi^{n-1} + dt (L(kappa*) h - h/Wi) + dt G (kappa* + kappa*^T) Psi0
+            //     = -b1 Phi^n - b2 Phi^{n-1} + dt (L(kappa*) h - h/Wi) + dt G (kappa* + kappa*^T) Psi0 [- A]
+            // (A: the transport of E = 2 Psi^n - Psi^{n-1}, from the pre-pass)
             // Psi^{n+1} = xi Phi^{n+1} + h
             if constexpr (F32) {
                 f2 K[3][3];
@@ -662,6 +663,7 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
                     const float pm = (float)buf[(S.sig + NC + r) * kTile + lane];
                     f2 v = two_sum_f2(2.0f * pn, -0.5f * pm);
                     v = f2_add(v, f2_mul(src, f2_add(K[i][j], K[j][i])));
+                    if constexpr (TRANSPORT) v = f2_add_f(v, -(float)buf[(S.tr + r) * kTile + lane]);
                     // the operator on h enters scaled by dt: float accuracy suffices
                     float lh = -iwi * Hs[i][j];
 #pragma unroll
@@ -701,6 +703,7 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
                     const double pn = (double)buf[(S.sig + r) * kTile + lane];
                     const double pm = (double)buf[(S.sig + NC + r) * kTile + lane];
                     x[r] = (2.0 * pn - 0.5 * pm) + A.dt * lh + A.dt * A.G * A.g * (K[i][j] + K[j][i]);
+                    if constexpr (TRANSPORT) x[r] -= (double)buf[(S.tr + r) * kTile + lane];
                 }
                 double M[NC][NC];
                 assemble_M<DIM>(K, A.a, A.dt * A.xi, M);
@@ -910,16 +913,23 @@ cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s
     if (e != cudaSuccess) return e;
     if (TRANSPORT) {
         if (!a.trans) return cudaErrorInvalidValue;
+        // the transported field: sigma, or Psi in the paper's variable
+        FwdArgs<T> ta = a;
+        if (PAPER) {
+            if (!a.psi_n || !a.psi_nm1) return cudaErrorInvalidValue;
+            ta.sig_n = a.psi_n;
+            ta.sig_nm1 = a.psi_nm1;
+        }
         if (a.n0 % kTX == 0 && a.n1 % kTY == 0) {
             const int zchunk = 8;
             const int gz = DIM == 3 ? (a.n2 + zchunk - 1) / zchunk : 1;
-            transport_tiled<T, DIM><<<dim3(a.n0 / kTX, a.n1 / kTY, gz), dim3(kTX, kTY), 0, s>>>(a, cfg.stencil,
+            transport_tiled<T, DIM><<<dim3(a.n0 / kTX, a.n1 / kTY, gz), dim3(kTX, kTY), 0, s>>>(ta, cfg.stencil,
                                                                                              zchunk);
         } else {
             const int threads = 256;
             long long blocks = (a.N + threads - 1) / threads;
             if (blocks > (long long)plan.sms * 16) blocks = (long long)plan.sms * 16;
-            transport_kernel<T, DIM><<<(unsigned)blocks, threads, 0, s>>>(a, cfg.stencil);
+            transport_kernel<T, DIM><<<(unsigned)blocks, threads, 0, s>>>(ta, cfg.stencil);
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -969,10 +979,10 @@ cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s
 template <typename T, bool COMP>
 cudaError_t dispatch(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s) {
     if (cfg.paper) {
-        // the paper's variable is built for the pointwise law only
-        if (cfg.transport) return cudaErrorInvalidValue;
-        return cfg.dim == 2 ? launch_one<T, 2, false, COMP, true>(a, cfg, s)
-                            : launch_one<T, 3, false, COMP, true>(a, cfg, s);
+        if (cfg.dim == 2)
+            return cfg.transport ? launch_one<T, 2, true, COMP, true>(a, cfg, s)
+                                 : launch_one<T, 2, false, COMP, true>(a, cfg, s);
+        return cfg.transport ? launch_one<T, 3, true, COMP, true>(a, cfg, s) : launch_one<T, 3, false, COMP, true>(a, cfg, s);
     }
     if (cfg.dim == 2)
         return cfg.transport ? launch_one<T, 2, true, COMP, false>(a, cfg, s)

@@ -60,6 +60,8 @@ struct FwdArgs {
     // Psi0^{n+1}, a = b0 + dt xi/Wi, mc holds c_j, dt c_j, w_j mu_j c_j; psi receives
     // the stress Psi^{n+1} = xi Phi^{n+1} + h
     T* psi;                // [nc][N]
+    const T* psi_n;        // Psi^n, Psi^{n-1}: the transported field of this variable
+    const T* psi_nm1;
     double xi, inv_wi;
     F2c xi_f2, dtxi_f2;    // xi, dt xi
 };

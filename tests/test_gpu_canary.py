@@ -55,6 +55,8 @@ CASES = [
     (3, (3, 5, 7), "implicit", "stress", "sdirk2", 0),
     (2, (33, 9), "implicit", "stress", "bdf2", 1),
     (2, (40, 1), False, "stress", "sdirk2", 1),
+    (2, (32, 8), True, "paper", "bdf2", 1),
+    (3, (3, 5, 7), True, "paper", "bdf2", 0),
 ]
 
 

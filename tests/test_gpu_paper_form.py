@@ -11,7 +11,8 @@ compression of g_alpha, stress = Psi).
    runs on the samples alone).
 3. Checkpoint round trip (Psi and the host modes of Phi0 = 1 restored).
 4. The SDIRK2 first step in this variable (Section 5.1).
-5. Refusals: transport (explicit or implicit), alpha = 1.
+5. Explicit transport of Psi, with the tiled and the per-point pre-pass.
+6. Refusals: implicit transport, alpha = 1, explicit transport with the SDIRK2 start.
 
 Tolerances: FP64 1e-11 per component; FP32 storage 2e-5 (Psi = xi Phi + h
 cancels: xi ~ (b0/dt)^(1-alpha), so the float rounding of Phi and of the
@@ -203,14 +204,65 @@ def test_paper_form_refusals():
     from paper_2411_17294_gb300 import tfs
     n, dt = (8, 8), 1e-2
     mu, w = soe.soe_nnls(0.5, dt, 1.0, 4)
-    k = torch.zeros((4, 64), dtype=torch.float64, device="cuda")
-    u = torch.zeros((2, 64), dtype=torch.float64, device="cuda")
-    for kw in (dict(transport=True), dict(transport="implicit")):
-        s = tfs.Solver(2, n, 0.5, 1.0, 0.5, dt, m=4, precision=tfs.TFS_FP64, mu=mu, w=w, form="paper", **kw)
-        s.set_state(None)
-        with pytest.raises(tfs.TfsError):
-            s.step(k, k, u)
-        assert s.step_index() == 0
-        s.close()
+    with pytest.raises(tfs.TfsError):
+        tfs.Solver(2, n, 0.5, 1.0, 0.5, dt, m=4, precision=tfs.TFS_FP64, mu=mu, w=w, form="paper",
+                   transport="implicit")
     with pytest.raises(tfs.TfsError):
         tfs.Solver(2, n, 1.0, 1.0, 0.5, dt, m=0, precision=tfs.TFS_FP64, transport=False, form="paper")
+    # explicit transport and the SDIRK2 start together are refused at the first step
+    s = tfs.Solver(2, n, 0.5, 1.0, 0.5, dt, m=4, precision=tfs.TFS_FP64, mu=mu, w=w, form="paper",
+                   transport=True, start="sdirk2")
+    s.set_state(None)
+    k = torch.zeros((4, 64), dtype=torch.float64, device=s.device)
+    u = torch.zeros((2, 64), dtype=torch.float64, device=s.device)
+    with pytest.raises(tfs.TfsError):
+        s.step(k, k, u)
+    assert s.step_index() == 0
+    s.close()
+
+
+TRANSPORT_CASES = [
+    # dim, n, alpha, m, stencil, eps   (n0 % 32 == 0 and n1 % 8 == 0: the tiled pre-pass)
+    (2, (37, 29), 0.5, 8, 0, 0.0),
+    (2, (64, 16), 0.4, 8, 1, 0.02),
+    (3, (9, 7, 5), 0.6, 6, 1, 0.01),
+    (3, (32, 8, 5), 0.3, 6, 0, 0.0),
+]
+
+
+@pytest.mark.parametrize("dim,n,alpha,m,stencil,eps", TRANSPORT_CASES)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_paper_form_with_transport_matches_oracle(dim, n, alpha, m, stencil, eps, precision):
+    import torch
+    from paper_2411_17294_gb300 import tfs
+    steps, dt, Wi, beta = 6, 4e-3, 1.3, 0.4
+    N = int(np.prod(n))
+    mu, w = soe.soe_nnls(1 - alpha, dt, 50 * dt, m)
+    K = kap_sequence(dim, n, 91, True)
+    u, _ = inputs.spectral_velocity(dim, n, 2, seed=92)
+    u = 0.3 * np.asarray(u)
+    P0 = inputs.random_stress(dim, n, 93)
+    if precision != 0:
+        cast = lambda a: np.asarray(a, np.float32).astype(np.float64)
+        K0 = K
+        K = lambda k: cast(K0(k))
+        P0, u = cast(P0), cast(u)
+    pf = PaperForm(dim, N, Wi, beta, dt, mu, w, Phi0=P0, grid=n, eps=eps, stencil=stencil)
+    s = tfs.Solver(dim, n, alpha, Wi, beta, dt, m=m, precision=precision, mu=mu, w=w, transport=True,
+                   form="paper", stencil=stencil, eps=eps)
+    s.set_state(torch.as_tensor(P0, dtype=s.dtype, device=s.device))
+    ut = torch.as_tensor(u, dtype=s.dtype, device=s.device).contiguous()
+    for k in range(steps):
+        kn, km = K(k), K(k - 1) if k > 0 else K(0)
+        ref = pf.step(kn, km, u)
+        s.step(torch.as_tensor(kn, dtype=s.dtype, device=s.device).contiguous(),
+               torch.as_tensor(km, dtype=s.dtype, device=s.device).contiguous() if k > 0 else None, ut)
+    got = s.stress().double().cpu().numpy()
+    assert not (s.status() & (tfs.TFS_FLAG_NONFINITE | tfs.TFS_FLAG_SINGULAR | tfs.TFS_FLAG_TIMEOUT))
+    s.close()
+    # the transport changes the result, and the library follows the oracle's
+    pb = PaperForm(dim, N, Wi, beta, dt, mu, w, Phi0=P0)
+    for k in range(steps):
+        other = pb.step(K(k), K(k - 1) if k > 0 else K(0))
+    assert np.max(np.abs(ref - other)) > 1e-3 * np.max(np.abs(ref))
+    assert np.all(rel_err_per_component(got, ref) < (1e-11 if precision == 0 else 2e-5))
