@@ -37,6 +37,12 @@ choice the stress form makes for sigma), it adds -dt (sum_a u_a D_a E - eps Lap 
 to the right-hand side, with D_a the upwind-biased third-order difference
 (radius 2, biased by the sign of u_a at the point) or the central second-order
 one, and Lap the three-point Laplacian per axis, periodic (numpy.roll).
+Implicit transport (the form of eq. FP_discrete): the operator acts on
+Psi^{n+1} = xi Phi^{n+1} + h^n inside the solve,
+    (b0 I - dt xi (L(kappa*) - I/Wi)) Phi + dt xi T(Phi)
+        = -b1 Phi^n - b2 Phi^{n-1} + dt (L(kappa*) - I/Wi) h + dt G (kappa* + kappa*^T) Psi0 - dt T(h),
+T = u.grad - eps Lap with the same stencils; the global system is assembled
+densely from unit vectors (small grids only) and solved with numpy.linalg.solve.
 The per-point systems are assembled column by column from unit vectors and
 solved with numpy.linalg.solve.
 """
@@ -67,7 +73,7 @@ class PaperForm:
     """State of the paper-variable scheme on a set of independent points."""
 
     def __init__(self, dim, N, Wi, beta, dt, mu, w, Phi0=None, Re=1.0, start="bdf2", grid=None, L=None,
-                 eps=0.0, stencil=0):
+                 eps=0.0, stencil=0, implicit=False):
         self.dim, self.N = dim, N
         # transport: grid shape (x fastest), box lengths, eps, stencil (0 upwind3, 1 central2)
         self.grid = tuple(grid) if grid is not None else None
@@ -75,6 +81,7 @@ class PaperForm:
             raise ValueError("grid does not match N")
         self.L = tuple(L) if L is not None else (2 * np.pi,) * dim
         self.eps, self.stencil = eps, stencil
+        self.implicit = implicit
         self.nc = 3 if dim == 2 else 6
         self.Wi, self.dt = Wi, dt
         self.G = (1.0 - beta) / (Wi * Re)
@@ -145,7 +152,11 @@ class PaperForm:
 
     def _transport(self, E, u):
         """dt (sum_a u_a D_a E - eps Lap E) for E [nc][N], u [d][N], periodic."""
-        d, dt = self.dim, self.dt
+        return self.dt * self._transport_op(E, u)
+
+    def _transport_op(self, E, u):
+        """sum_a u_a D_a E - eps Lap E for E [nc][N], u [d][N], periodic."""
+        d = self.dim
         shp = (self.nc,) + tuple(reversed(self.grid))          # [nc][(z)][y][x]
         F = E.reshape(shp)
         U = np.asarray(u, float).reshape((d,) + tuple(reversed(self.grid)))
@@ -164,7 +175,20 @@ class PaperForm:
             out += ua * D
             if self.eps != 0.0:
                 out -= self.eps * (at(-1) - 2 * F + at(1)) / h ** 2
-        return dt * out.reshape(self.nc, self.N)
+        return out.reshape(self.nc, self.N)
+
+    def _solve_implicit(self, K, rhs, u):
+        """Solve (b0 I - dt xi (L(K) - I/Wi)) Phi + dt xi T(Phi) = rhs over the grid (dense)."""
+        d, N, nc, dt = self.dim, self.N, self.nc, self.dt
+        n = nc * N
+        A = np.zeros((n, n))
+        for k in range(n):
+            e = np.zeros((nc, N))
+            e.flat[k] = 1.0
+            img = B0 * e - dt * self.xi * (_upper_convected(d, K, e) - e / self.Wi)
+            img = img + dt * self.xi * self._transport_op(e, u)
+            A[:, k] = img.ravel()
+        return np.linalg.solve(A, rhs.ravel()).reshape(nc, N)
 
     def step(self, kap_n, kap_nm1=None, u=None):
         """Advance one step; returns the stress Psi2^{n+1} [nc][N].  u [d][N]
@@ -200,16 +224,19 @@ class PaperForm:
         KS = K + np.swapaxes(K, 1, 2)
         src = np.stack([KS[:, i, j] for (i, j) in P])
         rhs = -B1 * self.Phi_n - B2 * self.Phi_nm1 + dt * Lh + dt * self.G * src * psi0
-        if u is not None:
+        if u is not None and self.implicit:
+            Phi = self._solve_implicit(K, rhs - self._transport(h, u), u)
+        elif u is not None:
             rhs = rhs - self._transport(2.0 * self.Psi_n - self.Psi_nm1, u)
         # system matrix per point: b0 I - dt xi (L(K) - I/Wi), column k = image of unit vector k
-        M = np.zeros((N, nc, nc))
-        for k in range(nc):
-            e = np.zeros((nc, N))
-            e[k] = 1.0
-            img = B0 * e - dt * self.xi * (_upper_convected(d, K, e) - e / self.Wi)
-            M[:, :, k] = img.T
-        Phi = np.linalg.solve(M, rhs.T[..., None])[..., 0].T
+        if not (u is not None and self.implicit):
+            M = np.zeros((N, nc, nc))
+            for k in range(nc):
+                e = np.zeros((nc, N))
+                e[k] = 1.0
+                img = B0 * e - dt * self.xi * (_upper_convected(d, K, e) - e / self.Wi)
+                M[:, :, k] = img.T
+            Phi = np.linalg.solve(M, rhs.T[..., None])[..., 0].T
         phi_new = self.c[:, None, None] * (-B1 * self.phi_n - B2 * self.phi_nm1 + dt * Phi[None])
         phi0_new = self.c * (-B1 * self.phi0_n - B2 * self.phi0_nm1 + dt * 1.0)
         self.Psi = self.xi * Phi + h

@@ -470,3 +470,48 @@ def test_paper_variable_transport_single_fourier_mode(stencil, U, eps):
     ref = (S_n * np.exp(1j * kx * x)).real
     assert np.max(np.abs(got[0] - ref)) < 1e-12 * np.max(np.abs(ref))
     assert np.max(np.abs(got[1:])) == 0.0
+
+
+@pytest.mark.parametrize("stencil,U,eps", [(0, 6.0, 0.0), (0, -6.0, 0.05), (1, 6.0, 0.02)])
+def test_paper_variable_implicit_transport_single_fourier_mode(stencil, U, eps):
+    # As above with the transport inside the solve, acting on Psi^{n+1} = xi Phi + h:
+    # (b0 + dt xi/Wi + dt xi s) Phi = -b1 Phi^n - b2 Phi^{n-1} - dt h/Wi - dt s h,
+    # at a velocity where the explicit form of the stress variable is unstable.
+    from oracle.paper_form import PaperForm
+    alpha, m, Wi, dt, steps = 0.5, 8, 1.3, 0.02, 12
+    n, kx = (16, 3), 3
+    N = n[0] * n[1]
+    h = 2 * math.pi / n[0]
+    assert abs(U) * dt / h > 0.25
+    mu, w = soe.soe_nnls(1 - alpha, dt, steps * dt, m)
+    x = (np.arange(N) % n[0]) * h
+    phi0 = np.zeros((3, N))
+    phi0[0] = np.cos(kx * x)
+    u = np.zeros((2, N))
+    u[0] = U
+    pf = PaperForm(2, N, Wi, 0.5, dt, mu, w, Phi0=phi0, grid=n, eps=eps, stencil=stencil, implicit=True)
+    for _ in range(steps):
+        got = pf.step(np.zeros((4, N)), None, u)
+    th = kx * h
+    if stencil == 1:
+        D = 1j * math.sin(th) / h
+    elif U >= 0:
+        D = (np.exp(-2j * th) - 6 * np.exp(-1j * th) + 3 + 2 * np.exp(1j * th)) / (6 * h)
+    else:
+        D = (-2 * np.exp(-1j * th) - 3 + 6 * np.exp(1j * th) - np.exp(2j * th)) / (6 * h)
+    sym = U * D + eps * 4.0 * math.sin(th / 2) ** 2 / h ** 2
+    b0, b1, b2 = 1.5, -2.0, 0.5
+    c = 1.0 / (b0 + mu * dt)
+    xi = b0 * np.sum(w * c)
+    P_n = P_nm1 = 1.0 + 0j
+    q_n = np.zeros(m, complex)
+    q_nm1 = np.zeros(m, complex)
+    for _ in range(steps):
+        hh = np.sum(w * mu * c * (b1 * q_n + b2 * q_nm1))
+        P = (-b1 * P_n - b2 * P_nm1 - dt * hh / Wi - dt * sym * hh) / (b0 + dt * xi / Wi + dt * xi * sym)
+        q = c * (-b1 * q_n - b2 * q_nm1 + dt * P)
+        S = xi * P + hh
+        P_nm1, P_n, q_nm1, q_n = P_n, P, q_n, q
+    ref = (S * np.exp(1j * kx * x)).real
+    assert np.max(np.abs(got[0] - ref)) < 1e-12 * np.max(np.abs(ref))
+    assert np.max(np.abs(got[1:])) == 0.0
