@@ -111,9 +111,12 @@ enum {
                                  With transport 1 the operator u.grad - eps Lap acts on the
                                  extrapolation 2 Psi^n - Psi^{n-1}, explicitly, with the stencils of the
                                  stress form; the Courant check of tfs_transport_limit (derived for the
-                                 stress form) is not applied.  Needs alpha < 1 and transport 0 or 1
-                                 (TFS_ERR_ARG here, or from tfs_set_param(TFS_PARAM_TRANSPORT, 2));
-                                 either start (SDIRK2 without transport); tfs_backward refuses it
+                                 stress form) is not applied.  With transport 2 it acts on
+                                 Psi^{n+1} = xi Phi^{n+1} + h inside the solve (eq. FP_discrete): the
+                                 operator (b0 + dt xi/Wi) I - dt xi L(kappa*) + dt xi (u.grad - eps Lap)
+                                 through the same Krylov solver, and one more nc N FP64 vector.  Needs
+                                 alpha < 1 (else TFS_ERR_ARG here); either start (SDIRK2 without
+                                 transport, else tfs_step returns TFS_ERR_ARG); tfs_backward refuses it
                                  (TFS_ERR_ARG).  The workspace grows by 2 nc N elements (Psi^n, Psi^{n-1});
                                  with a workspace bound, a form it does not fit returns TFS_ERR_NOWORKSPACE.
                                  Changing the form discards the state (call tfs_set_state again) */

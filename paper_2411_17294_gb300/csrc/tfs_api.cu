@@ -254,7 +254,8 @@ bool limits_violated(tfs_ctx* h) {
 // implicit transport: 10 Krylov vectors [nc][N] plus the point blocks and the
 // preconditioner inverses [nc*nc][N], all FP64
 size_t krylov_bytes(const tfs_ctx* h) {
-    return (10 + 2 * (size_t)h->nc) * (size_t)h->nc * (size_t)h->N * sizeof(double);
+    // (the paper's variable keeps h, one more vector, after the preconditioner blocks)
+    return (10 + 2 * (size_t)h->nc + (h->paper() ? 1 : 0)) * (size_t)h->nc * (size_t)h->N * sizeof(double);
 }
 size_t forward_bytes_for(const tfs_ctx* h, int transport, int form);
 
@@ -293,7 +294,11 @@ void layout_forward(tfs_ctx* h, char* base) {
 size_t forward_bytes_for(const tfs_ctx* h, int transport, int form) {
     size_t b = kAlign + 5 * align_up(h->field_bytes()) + 2 * align_up(h->modes_bytes());
     if (form == TFS_FORM_PAPER) b += 2 * align_up(h->field_bytes());
-    if (transport == 2) b += align_up(krylov_bytes(h)) + align_up(sizeof(double) * (2 * kImpBlocks + 32));
+    if (transport == 2) {
+        const size_t kb = (10 + 2 * (size_t)h->nc + (form == TFS_FORM_PAPER ? 1 : 0)) * (size_t)h->nc * (size_t)h->N *
+                          sizeof(double);
+        b += align_up(kb) + align_up(sizeof(double) * (2 * kImpBlocks + 32));
+    }
     return b;
 }
 
@@ -378,6 +383,27 @@ void fill_implicit(tfs_ctx* h, ImpArgs<T>& a, const void* kn, const void* knm1, 
     a.maxit = h->krylov_maxit;
 }
 
+double paper_psi0(const tfs_ctx* h);
+void paper_advance_phi0(tfs_ctx* h);
+
+// The paper's variable with implicit transport: the operator is
+// (b0 + dt xi/Wi) I - dt xi L(kappa*) + dt xi (u.grad - eps Lap), i.e. the stress
+// form's with a = b0 + dt xi/Wi and transport scale dt xi.
+template <typename T>
+void fill_implicit_paper(tfs_ctx* h, ImpArgs<T>& a) {
+    a.paper = 1;
+    a.sigma0 = nullptr;
+    a.classic = 0;
+    a.dt_rhs = h->dt;
+    a.dt = h->dt * h->xi_p;
+    a.a = kB0 + h->dt * h->xi_p / h->Wi;
+    a.g = paper_psi0(h);
+    a.xi = h->xi_p;
+    a.inv_wi = 1.0 / h->Wi;
+    a.mcd = h->mcd_p;
+    a.psi = (T*)h->psi[1 - h->cur_psi];
+}
+
 // One step with implicit transport (tfs_implicit.cu); synchronises the stream.
 int do_step_implicit(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* sig_copy, cudaStream_t s) {
     if (!h->kry || h->ws_bytes < forward_bytes(h)) return TFS_ERR_NOWORKSPACE;
@@ -390,14 +416,26 @@ int do_step_implicit(tfs_ctx* h, const void* kn, const void* knm1, const void* u
         ImpArgs<double> a{};
         fill_implicit(h, a, kn, knm1, u, sig_copy, nxt, cm, pm);
         a.mc = h->mcd;
+        if (h->paper()) {
+            fill_implicit_paper(h, a);
+            a.mc = h->mcd_p;
+        }
         e = run_implicit_f64(a, s, &iters, &relres);
     } else {
         ImpArgs<float> a{};
         fill_implicit(h, a, kn, knm1, u, sig_copy, nxt, cm, pm);
         a.mc = h->mcf;
+        if (h->paper()) {
+            fill_implicit_paper(h, a);
+            a.mc = h->mcf_p;
+        }
         e = run_implicit_f32(a, s, h->precision == TFS_FP32, &iters, &relres);
     }
     if (e != cudaSuccess) return TFS_ERR_CUDA;
+    if (h->paper()) {
+        paper_advance_phi0(h);
+        h->cur_psi = 1 - h->cur_psi;
+    }
     h->last_iters = iters;
     h->last_relres = relres;
     h->prev_sig = h->cur_sig;
@@ -504,6 +542,7 @@ StartConsts start_consts(const tfs_ctx* h) {
 // and mode rings then advance as after any step: level n-1 = the initial state.
 int do_first_step_sdirk2(tfs_ctx* h, const void* kn, const void* u, void* sig_copy, cudaStream_t s) {
     if (h->explicit_transport()) return TFS_ERR_ARG;
+    if (h->paper() && h->transport != 0) return TFS_ERR_ARG;   // the paper's variable starts pointwise only
     StartConsts c = start_consts(h);
     const int nxt = h->third_sig();
     const int cm = h->cur_mode, pm = 1 - h->cur_mode;
@@ -588,7 +627,6 @@ int do_step(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* s
     if (h->transport && !u) return TFS_ERR_ARG;
     if (limits_violated(h)) return TFS_ERR_UNSTABLE;
     if (!knm1) knm1 = kn;
-    if (h->paper() && h->implicit_transport()) return TFS_ERR_ARG;
     if (h->start == TFS_START_SDIRK2 && h->step == 0) return do_first_step_sdirk2(h, kn, u, sig_copy, s);
     if (h->implicit_transport()) return do_step_implicit(h, kn, knm1, u, sig_copy, s);
     const int nxt = h->third_sig();
@@ -717,7 +755,6 @@ int tfs_set_param(tfs_handle h, int key, double value) {
             return TFS_OK;
         case TFS_PARAM_TRANSPORT:
             if (value != 0.0 && value != 1.0 && value != 2.0) return TFS_ERR_ARG;
-            if (value == 2.0 && h->paper()) return TFS_ERR_ARG;
             if (h->ws && h->ws_bytes < forward_bytes_for(h, (int)value, h->form)) return TFS_ERR_NOWORKSPACE;
             h->transport = (int)value;
             if (h->ws) layout_forward(h, h->ws);
@@ -739,7 +776,7 @@ int tfs_set_param(tfs_handle h, int key, double value) {
             return TFS_OK;
         case TFS_PARAM_FORM:
             if (value != TFS_FORM_STRESS && value != TFS_FORM_PAPER) return TFS_ERR_ARG;
-            if (value == TFS_FORM_PAPER && (h->classic() || h->implicit_transport())) return TFS_ERR_ARG;
+            if (value == TFS_FORM_PAPER && h->classic()) return TFS_ERR_ARG;
             if (h->ws && h->ws_bytes < forward_bytes_for(h, h->transport, (int)value)) return TFS_ERR_NOWORKSPACE;
             if ((int)value != h->form) h->state_set = false;   // the state means something else now
             h->form = (int)value;

@@ -391,6 +391,129 @@ __global__ void __launch_bounds__(kThreads) imp_init_kernel(long long n, const d
     }
 }
 
+// ------------------------------------------------------------------ the paper's variable
+// Right-hand side of the implicit step in the paper's variable, per point:
+//   h = sum_j w_j mu_j c_j Q_j, Q_j = b1 phi_j^n + b2 phi_j^{n-1} (written over the oldest level),
+//   b = -b1 Phi^n - b2 Phi^{n-1} + dt (L(kappa*) h - h/Wi) + dt G (kappa* + kappa*^T) Psi0
+// (the transport of h is subtracted by imp_sub_transport_kernel); h is kept for
+// Psi^{n+1} = xi Phi^{n+1} + h, and the initial guess is 2 Phi^n - Phi^{n-1}.
+template <typename T, int DIM, bool COMP>
+__global__ void __launch_bounds__(kThreads) imp_rhs_paper_kernel(const ImpArgs<T> A, double* b, double* x0,
+                                                                 double* H) {
+    constexpr int NC = Packed<DIM>::NC;
+    constexpr bool F32 = sizeof(T) == 4;
+    const long long N = A.N;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        double K[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+        for (int i = 0; i < DIM; ++i)
+#pragma unroll
+            for (int j = 0; j < DIM; ++j) {
+                const long long q = (long long)(i * DIM + j) * N + p;
+                K[i][j] = 2.0 * (double)A.kap_n[q] - (double)A.kap_nm1[q];
+            }
+        double h[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            if constexpr (F32) {
+                float hs = 0.0f, comp = 0.0f;
+                for (int jj = 0; jj < A.m; ++jj) {
+                    const long long q = ((long long)jj * NC + c) * N + p;
+                    const float qj = __fmaf_rn(0.5f, (float)A.modes_nm1[q], -2.0f * (float)A.modes_n[q]);
+                    A.modes_nm1[q] = (T)qj;
+                    if (COMP) {
+                        const float yv = __fmaf_rn(A.mc.eta_hi[jj], qj, __fmaf_rn(A.mc.eta_lo[jj], qj, -comp));
+                        const float t = __fadd_rn(hs, yv);
+                        comp = __fsub_rn(__fsub_rn(t, hs), yv);
+                        hs = t;
+                    } else {
+                        hs = __fmaf_rn(A.mc.eta_hi[jj], qj, hs);
+                    }
+                }
+                h[c] = (double)hs - (double)comp;
+            } else {
+                double hs = 0.0;
+                for (int jj = 0; jj < A.m; ++jj) {
+                    const long long q = ((long long)jj * NC + c) * N + p;
+                    const double qj = kB1 * (double)A.modes_n[q] + kB2 * (double)A.modes_nm1[q];
+                    A.modes_nm1[q] = (T)qj;
+                    hs = fma(A.mcd.eta[jj], qj, hs);
+                }
+                h[c] = hs;
+            }
+        }
+        double Hs[3][3];
+#pragma unroll
+        for (int r = 0; r < NC; ++r) {
+            Hs[Packed<DIM>::I(r)][Packed<DIM>::J(r)] = h[r];
+            Hs[Packed<DIM>::J(r)][Packed<DIM>::I(r)] = h[r];
+        }
+#pragma unroll
+        for (int r = 0; r < NC; ++r) {
+            const int i = Packed<DIM>::I(r), j = Packed<DIM>::J(r);
+            double lh = -A.inv_wi * h[r];
+#pragma unroll
+            for (int l = 0; l < DIM; ++l) lh = fma(K[i][l], Hs[l][j], fma(Hs[i][l], K[j][l], lh));
+            const long long q = (long long)r * N + p;
+            const double pn = (double)A.sig_n[q], pm = (double)A.sig_nm1[q];
+            b[q] = (2.0 * pn - 0.5 * pm) + A.dt_rhs * lh + A.dt_rhs * A.G * A.g * (K[i][j] + K[j][i]);
+            x0[q] = 2.0 * pn - pm;
+            H[q] = h[r];
+        }
+    }
+}
+
+// b -= dt (u.grad - eps Lap) H, the stencils of the operator
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) imp_sub_transport_kernel(const ImpArgs<T> A, const double* H, double* b) {
+    constexpr int NC = Packed<DIM>::NC;
+    const long long N = A.N;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        GridIdx g;
+        g.n0 = A.n0;
+        g.n1 = A.n1;
+        g.n2 = A.n2;
+        g.x = p % A.n0;
+        g.y = (p / A.n0) % A.n1;
+        g.z = p / ((long long)A.n0 * A.n1);
+        double u[3] = {0, 0, 0};
+#pragma unroll
+        for (int ax = 0; ax < DIM; ++ax) u[ax] = (double)A.u[(long long)ax * N + p];
+#pragma unroll
+        for (int r = 0; r < NC; ++r) {
+            const double* f = H + (long long)r * N;
+            const double f0 = f[p];
+            double t = 0.0;
+#pragma unroll
+            for (int ax = 0; ax < DIM; ++ax) {
+                t += u[ax] * deriv_at<DIM>(f, g, ax, A.stencil, u[ax], A.inv_h[ax]);
+                if (A.eps != 0.0)
+                    t -= A.eps * (f[g.at(ax, -1)] - 2.0 * f0 + f[g.at(ax, 1)]) * (A.inv_h[ax] * A.inv_h[ax]);
+            }
+            b[(long long)r * N + p] -= A.dt_rhs * t;
+        }
+    }
+}
+
+// Psi^{n+1} = xi Phi^{n+1} + h into psi (and the caller's copy)
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) imp_psi_kernel(const ImpArgs<T> A, const double* x, const double* H) {
+    constexpr int NC = Packed<DIM>::NC;
+    const long long N = A.N;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        bool finite = true;
+#pragma unroll
+        for (int r = 0; r < NC; ++r) {
+            const long long q = (long long)r * N + p;
+            const T v = (T)fma(A.xi, x[q], H[q]);
+            finite = finite && isfinite((double)v);
+            A.psi[q] = v;
+            if (A.sig_copy) A.sig_copy[q] = v;
+        }
+        if (!finite) atomicOr(A.flags, 1u);
+    }
+}
+
 // ------------------------------------------------------------------ first step (SDIRK2)
 // Stage right-hand side over the grid: b = dt W sigma0 + dt sum_j mu_j Z_j/(1 + gamma mu_j dt)
 // + dt G (kappa^0 + kappa^0T) g_alpha(t_i), Z the explicit mode stage; x0 = sigma^0 when given.
@@ -556,15 +679,30 @@ cudaError_t run_implicit(const ImpArgs<T>& a, cudaStream_t st, int* iters, doubl
     constexpr int NC = Packed<DIM>::NC;
     const KryView<NC> K(a.kry, a.partials, a.N);
     const unsigned bs = (unsigned)kImpBlocks;
+    // the paper's variable keeps h after the preconditioner blocks
+    double* H = K.Pinv + (long long)NC * NC * a.N;
     imp_setup_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Pinv);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    imp_rhs_kernel<T, DIM, COMP><<<bs, kThreads, 0, st>>>(a, K.b, K.x);
+    if (a.paper) {
+        imp_rhs_paper_kernel<T, DIM, COMP><<<bs, kThreads, 0, st>>>(a, K.b, K.x, H);
+        imp_sub_transport_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, H, K.b);
+    } else {
+        imp_rhs_kernel<T, DIM, COMP><<<bs, kThreads, 0, st>>>(a, K.b, K.x);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = krylov_solve<T, DIM>(a, K, st, iters, relres);
     if (e != cudaSuccess) return e;
-    imp_push_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.x);
+    if (a.paper) {
+        // Phi^{n+1} and the modes by the stress form's push (sigma0 = 0, rho_j = dt c_j), then Psi
+        ImpArgs<T> pa = a;
+        pa.sig_copy = nullptr;
+        imp_push_kernel<T, DIM><<<bs, kThreads, 0, st>>>(pa, K.x);
+        imp_psi_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.x, H);
+    } else {
+        imp_push_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.x);
+    }
     return cudaGetLastError();
 }
 

@@ -119,6 +119,14 @@ struct ImpArgs {
     double* partials;      // reduction scratch, kImpBlocks doubles
     double tol;            // relative residual target
     int maxit;
+    // the paper's variable (Section 3.4): the unknown is Phi^{n+1}, the operator's
+    // transport acts on Psi^{n+1} = xi Phi + h, so dt above is dt xi (the transport
+    // scale of the operator) and a = b0 + dt xi/Wi; g holds Psi0^{n+1}, mc the
+    // per-mode constants c_j, dt c_j, w_j mu_j c_j; the right-hand side takes the
+    // step's dt_rhs; psi receives Psi^{n+1}
+    int paper;
+    double dt_rhs, xi, inv_wi;
+    T* psi;
 };
 constexpr int kImpBlocks = 1024;   // blocks of the implicit-step kernels (and reduction partials)
 

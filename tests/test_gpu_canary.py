@@ -57,6 +57,7 @@ CASES = [
     (2, (40, 1), False, "stress", "sdirk2", 1),
     (2, (32, 8), True, "paper", "bdf2", 1),
     (3, (3, 5, 7), True, "paper", "bdf2", 0),
+    (2, (9, 7), "implicit", "paper", "bdf2", 1),
 ]
 
 

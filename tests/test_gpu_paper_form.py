@@ -12,7 +12,9 @@ compression of g_alpha, stress = Psi).
 3. Checkpoint round trip (Psi and the host modes of Phi0 = 1 restored).
 4. The SDIRK2 first step in this variable (Section 5.1).
 5. Explicit transport of Psi, with the tiled and the per-point pre-pass.
-6. Refusals: implicit transport, alpha = 1, explicit transport with the SDIRK2 start.
+6. Implicit transport of Psi (eq. FP_discrete) through the Krylov solver, far
+   above the explicit limit.
+7. Refusals: alpha = 1, transport with the SDIRK2 start.
 
 Tolerances: FP64 1e-11 per component; FP32 storage 2e-5 (Psi = xi Phi + h
 cancels: xi ~ (b0/dt)^(1-alpha), so the float rounding of Phi and of the
@@ -205,20 +207,18 @@ def test_paper_form_refusals():
     n, dt = (8, 8), 1e-2
     mu, w = soe.soe_nnls(0.5, dt, 1.0, 4)
     with pytest.raises(tfs.TfsError):
-        tfs.Solver(2, n, 0.5, 1.0, 0.5, dt, m=4, precision=tfs.TFS_FP64, mu=mu, w=w, form="paper",
-                   transport="implicit")
-    with pytest.raises(tfs.TfsError):
         tfs.Solver(2, n, 1.0, 1.0, 0.5, dt, m=0, precision=tfs.TFS_FP64, transport=False, form="paper")
-    # explicit transport and the SDIRK2 start together are refused at the first step
-    s = tfs.Solver(2, n, 0.5, 1.0, 0.5, dt, m=4, precision=tfs.TFS_FP64, mu=mu, w=w, form="paper",
-                   transport=True, start="sdirk2")
-    s.set_state(None)
-    k = torch.zeros((4, 64), dtype=torch.float64, device=s.device)
-    u = torch.zeros((2, 64), dtype=torch.float64, device=s.device)
-    with pytest.raises(tfs.TfsError):
-        s.step(k, k, u)
-    assert s.step_index() == 0
-    s.close()
+    # transport (explicit or implicit) and the SDIRK2 start together are refused at the first step
+    for tr in (True, "implicit"):
+        s = tfs.Solver(2, n, 0.5, 1.0, 0.5, dt, m=4, precision=tfs.TFS_FP64, mu=mu, w=w, form="paper",
+                       transport=tr, start="sdirk2")
+        s.set_state(None)
+        k = torch.zeros((4, 64), dtype=torch.float64, device=s.device)
+        u = torch.zeros((2, 64), dtype=torch.float64, device=s.device)
+        with pytest.raises(tfs.TfsError):
+            s.step(k, k, u)
+        assert s.step_index() == 0
+        s.close()
 
 
 TRANSPORT_CASES = [
@@ -266,3 +266,51 @@ def test_paper_form_with_transport_matches_oracle(dim, n, alpha, m, stencil, eps
         other = pb.step(K(k), K(k - 1) if k > 0 else K(0))
     assert np.max(np.abs(ref - other)) > 1e-3 * np.max(np.abs(ref))
     assert np.all(rel_err_per_component(got, ref) < (1e-11 if precision == 0 else 2e-5))
+
+
+IMPLICIT_CASES = [
+    # dim, n, alpha, m, stencil, eps, dt max|u| / h
+    (2, (16, 12), 0.5, 8, 0, 0.0, 0.5),
+    (2, (12, 10), 0.3, 6, 1, 0.02, 0.08),   # xi ~ 100 at alpha = 0.3: dt xi |u|/h ~ 5x the diagonal
+    (3, (6, 5, 4), 0.6, 6, 0, 0.01, 0.4),
+]
+
+
+@pytest.mark.parametrize("dim,n,alpha,m,stencil,eps,speed", IMPLICIT_CASES)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_paper_form_implicit_transport_matches_oracle(dim, n, alpha, m, stencil, eps, speed, precision):
+    import torch
+    from paper_2411_17294_gb300 import tfs
+    steps, dt, Wi, beta = 6, 2e-3, 1.3, 0.4
+    N = int(np.prod(n))
+    mu, w = soe.soe_nnls(1 - alpha, dt, 50 * dt, m)
+    K = kap_sequence(dim, n, 95, True)
+    u, _ = inputs.spectral_velocity(dim, n, 2, seed=96)
+    h = 2 * np.pi / min(n)
+    u = np.asarray(u) * (speed * h / dt / np.abs(np.asarray(u)).max())   # dt max|u| / h = speed
+    # (the explicit transport of the stress variable is stable only to dt max|u| / h of about 0.01 here)
+    P0 = inputs.random_stress(dim, n, 97)
+    if precision != 0:
+        cast = lambda a: np.asarray(a, np.float32).astype(np.float64)
+        K0 = K
+        K = lambda k: cast(K0(k))
+        P0, u = cast(P0), cast(u)
+    pf = PaperForm(dim, N, Wi, beta, dt, mu, w, Phi0=P0, grid=n, eps=eps, stencil=stencil, implicit=True)
+    s = tfs.Solver(dim, n, alpha, Wi, beta, dt, m=m, precision=precision, mu=mu, w=w, transport="implicit",
+                   form="paper", stencil=stencil, eps=eps)
+    s.set_state(torch.as_tensor(P0, dtype=s.dtype, device=s.device))
+    s.set_krylov(maxit=2000)
+    ut = torch.as_tensor(u, dtype=s.dtype, device=s.device).contiguous()
+    for k in range(steps):
+        kn, km = K(k), K(k - 1) if k > 0 else K(0)
+        ref = pf.step(kn, km, u)
+        s.step(torch.as_tensor(kn, dtype=s.dtype, device=s.device).contiguous(),
+               torch.as_tensor(km, dtype=s.dtype, device=s.device).contiguous() if k > 0 else None, ut)
+        it, rr = s.last_solve()
+        assert 0 < it < 2000
+    got = s.stress().double().cpu().numpy()
+    assert not (s.status() & (tfs.TFS_FLAG_NONFINITE | tfs.TFS_FLAG_NOCONV | tfs.TFS_FLAG_TIMEOUT))
+    s.close()
+    assert np.max(np.abs(ref)) > 1e-2
+    assert np.all(rel_err_per_component(got, ref) < (1e-10 if precision == 0 else 2e-5)), \
+        rel_err_per_component(got, ref)
