@@ -115,8 +115,8 @@ enum {
                                  Psi^{n+1} = xi Phi^{n+1} + h inside the solve (eq. FP_discrete): the
                                  operator (b0 + dt xi/Wi) I - dt xi L(kappa*) + dt xi (u.grad - eps Lap)
                                  through the same Krylov solver, and one more nc N FP64 vector.  Needs
-                                 alpha < 1 (else TFS_ERR_ARG here); either start (SDIRK2 without
-                                 transport, else tfs_step returns TFS_ERR_ARG); tfs_backward refuses it
+                                 alpha < 1 (else TFS_ERR_ARG here); either start (SDIRK2 with transport
+                                 0 or 2, else tfs_step returns TFS_ERR_ARG); tfs_backward refuses it
                                  (TFS_ERR_ARG).  The workspace grows by 2 nc N elements (Psi^n, Psi^{n-1});
                                  with a workspace bound, a form it does not fit returns TFS_ERR_NOWORKSPACE.
                                  Changing the form discards the state (call tfs_set_state again) */

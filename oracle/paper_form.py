@@ -117,13 +117,15 @@ class PaperForm:
             M[:, :, k] = (e - scale * (_upper_convected(d, K, e) - e / self.Wi)).T
         return np.linalg.solve(M, rhs.T[..., None])[..., 0].T
 
-    def _sdirk2_first_step(self, K):
+    def _sdirk2_first_step(self, K, u=None):
         """Two-stage SDIRK2 (gamma = 1 - 1/sqrt2, stiffly accurate) on the ODE system
         d Phi/dt = (L - I/Wi) Psi + G (K + K^T) Psi0,  d phi_j/dt = -mu_j phi_j + Phi,
         Psi = sum_j w_j (-mu_j phi_j + Phi).  At a stage with explicit parts ZPhi,
         Zphi_j: phi_j = (Zphi_j + g dt Phi)/(1 + g mu_j dt), so Psi = xi' Phi - h',
         xi' = sum_j w_j/(1 + g mu_j dt), h' = sum_j w_j mu_j Zphi_j/(1 + g mu_j dt), and
-        (I - g dt xi' (L - I/Wi)) Phi = ZPhi - g dt (L - I/Wi) h' + g dt G (K + K^T) Psi0."""
+        (I - g dt xi' (L - I/Wi)) Phi = ZPhi - g dt (L - I/Wi) h' + g dt G (K + K^T) Psi0;
+        with implicit transport T = u.grad - eps Lap acting on Psi = xi' Phi - h' the
+        left side gains g dt xi' T(Phi) and the right side g dt T(h') (global solve)."""
         d, dt = self.dim, self.dt
         g = 1.0 - np.sqrt(0.5)
         den = 1.0 + g * self.mu * dt
@@ -137,7 +139,10 @@ class PaperForm:
             psi0 = xi1 - float(np.sum(self.w * self.mu * Zphi0 / den))
             Lh = _upper_convected(d, K, h1) - h1 / self.Wi
             rhs = ZPhi - g * dt * Lh + g * dt * self.G * src * psi0
-            Phi = self._solve(K, g * dt * xi1, rhs)
+            if u is not None:
+                Phi = self._solve_implicit(K, rhs + g * dt * self._transport_op(h1, u), u, 1.0, g * dt * xi1)
+            else:
+                Phi = self._solve(K, g * dt * xi1, rhs)
             phi = (Zphi + g * dt * Phi[None]) / den[:, None, None]
             phi0 = (Zphi0 + g * dt * 1.0) / den
             if stage == 1:
@@ -177,16 +182,19 @@ class PaperForm:
                 out -= self.eps * (at(-1) - 2 * F + at(1)) / h ** 2
         return out.reshape(self.nc, self.N)
 
-    def _solve_implicit(self, K, rhs, u):
-        """Solve (b0 I - dt xi (L(K) - I/Wi)) Phi + dt xi T(Phi) = rhs over the grid (dense)."""
+    def _solve_implicit(self, K, rhs, u, diag=B0, scale=None):
+        """Solve (diag I - scale (L(K) - I/Wi)) Phi + scale T(Phi) = rhs over the grid (dense);
+        scale defaults to dt xi (the BDF2 step)."""
         d, N, nc, dt = self.dim, self.N, self.nc, self.dt
+        if scale is None:
+            scale = dt * self.xi
         n = nc * N
         A = np.zeros((n, n))
         for k in range(n):
             e = np.zeros((nc, N))
             e.flat[k] = 1.0
-            img = B0 * e - dt * self.xi * (_upper_convected(d, K, e) - e / self.Wi)
-            img = img + dt * self.xi * self._transport_op(e, u)
+            img = diag * e - scale * (_upper_convected(d, K, e) - e / self.Wi)
+            img = img + scale * self._transport_op(e, u)
             A[:, k] = img.ravel()
         return np.linalg.solve(A, rhs.ravel()).reshape(nc, N)
 
@@ -197,10 +205,10 @@ class PaperForm:
         if u is not None and self.grid is None:
             raise ValueError("transport needs the grid")
         if self.start == "sdirk2" and self.n == 0:
-            if u is not None:
-                raise ValueError("the SDIRK2 start is pointwise here")
+            if u is not None and not self.implicit:
+                raise ValueError("the SDIRK2 start takes the transport implicitly only")
             kap0 = np.asarray(kap_n, float).reshape(d * d, N)
-            Phi, phi, phi0, Psi = self._sdirk2_first_step(kap0.T.reshape(N, d, d))
+            Phi, phi, phi0, Psi = self._sdirk2_first_step(kap0.T.reshape(N, d, d), u)
             self.Psi = Psi
             self.Psi_nm1, self.Psi_n = self.Psi_n, Psi
             self.Phi_nm1, self.Phi_n = self.Phi_n, Phi

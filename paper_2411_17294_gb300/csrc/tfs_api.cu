@@ -542,7 +542,7 @@ StartConsts start_consts(const tfs_ctx* h) {
 // and mode rings then advance as after any step: level n-1 = the initial state.
 int do_first_step_sdirk2(tfs_ctx* h, const void* kn, const void* u, void* sig_copy, cudaStream_t s) {
     if (h->explicit_transport()) return TFS_ERR_ARG;
-    if (h->paper() && h->transport != 0) return TFS_ERR_ARG;   // the paper's variable starts pointwise only
+
     StartConsts c = start_consts(h);
     const int nxt = h->third_sig();
     const int cm = h->cur_mode, pm = 1 - h->cur_mode;
@@ -552,18 +552,37 @@ int do_first_step_sdirk2(tfs_ctx* h, const void* kn, const void* u, void* sig_co
         if (!h->kry || h->ws_bytes < forward_bytes(h)) return TFS_ERR_NOWORKSPACE;
         int iters = 0;
         double relres = 0.0;
+        // the paper's variable: stage operator a = 1 + gamma dt W/Wi, scale gamma dt W; Psi0 at the stages
+        const std::vector<double> keep_n = h->phi0_n, keep_nm1 = h->phi0_nm1;
+        if (h->paper()) paper_sdirk2_phi0(h, c.g);
+        auto paper_stage = [&](auto& a) {
+            a.paper = 1;
+            a.sigma0 = nullptr;
+            a.dt_rhs = h->dt;
+            a.dt = c.gam * h->dt * c.W;
+            a.a = 1.0 + c.gam * h->dt * c.W / h->Wi;
+            a.inv_wi = 1.0 / h->Wi;
+            a.xi = c.W;
+            a.psi = (decltype(a.psi))h->psi[1 - h->cur_psi];
+        };
         if (h->is_double()) {
             ImpArgs<double> a{};
             fill_implicit(h, a, kn, kn, u, sig_copy, nxt, cm, pm);
             a.mc = h->mcd;
             a.a = a_stage;
+            if (h->paper()) paper_stage(a);
             e = run_start_implicit_f64(a, c, s, &iters, &relres);
         } else {
             ImpArgs<float> a{};
             fill_implicit(h, a, kn, kn, u, sig_copy, nxt, cm, pm);
             a.mc = h->mcf;
             a.a = a_stage;
+            if (h->paper()) paper_stage(a);
             e = run_start_implicit_f32(a, c, s, &iters, &relres);
+        }
+        if (e != cudaSuccess && h->paper()) {
+            h->phi0_n = keep_n;
+            h->phi0_nm1 = keep_nm1;
         }
         h->last_iters = iters;
         h->last_relres = relres;

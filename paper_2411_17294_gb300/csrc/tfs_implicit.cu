@@ -463,9 +463,10 @@ __global__ void __launch_bounds__(kThreads) imp_rhs_paper_kernel(const ImpArgs<T
     }
 }
 
-// b -= dt (u.grad - eps Lap) H, the stencils of the operator
+// b -= scale (u.grad - eps Lap) H, the stencils of the operator
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kThreads) imp_sub_transport_kernel(const ImpArgs<T> A, const double* H, double* b) {
+__global__ void __launch_bounds__(kThreads) imp_sub_transport_kernel(const ImpArgs<T> A, const double* H, double* b,
+                                                                     double scale) {
     constexpr int NC = Packed<DIM>::NC;
     const long long N = A.N;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
@@ -490,7 +491,7 @@ __global__ void __launch_bounds__(kThreads) imp_sub_transport_kernel(const ImpAr
                 if (A.eps != 0.0)
                     t -= A.eps * (f[g.at(ax, -1)] - 2.0 * f0 + f[g.at(ax, 1)]) * (A.inv_h[ax] * A.inv_h[ax]);
             }
-            b[(long long)r * N + p] -= A.dt_rhs * t;
+            b[(long long)r * N + p] -= scale * t;
         }
     }
 }
@@ -686,7 +687,7 @@ cudaError_t run_implicit(const ImpArgs<T>& a, cudaStream_t st, int* iters, doubl
     if (e != cudaSuccess) return e;
     if (a.paper) {
         imp_rhs_paper_kernel<T, DIM, COMP><<<bs, kThreads, 0, st>>>(a, K.b, K.x, H);
-        imp_sub_transport_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, H, K.b);
+        imp_sub_transport_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, H, K.b, a.dt_rhs);
     } else {
         imp_rhs_kernel<T, DIM, COMP><<<bs, kThreads, 0, st>>>(a, K.b, K.x);
     }
@@ -706,6 +707,101 @@ cudaError_t run_implicit(const ImpArgs<T>& a, cudaStream_t st, int* iters, doubl
     return cudaGetLastError();
 }
 
+// The SDIRK2 first step in the paper's variable with implicit transport.  At a
+// stage with explicit parts ZPhi, Zphi_j, phi_j = (Zphi_j + gamma dt Phi)/(1 +
+// gamma mu_j dt), Psi = W Phi - h, h = sum_j w_j mu_j Zphi_j/(1 + gamma mu_j dt), and
+//   (1 + gamma dt W/Wi) Phi - gamma dt W L(kappa^0) Phi + gamma dt W T(Phi)
+//       = ZPhi - gamma dt (L(kappa^0) h - h/Wi) + gamma dt G (kappa^0 + kappa^0T) Psi0(t_i) + gamma dt T(h),
+// T = u.grad - eps Lap: the stress form's operator with a = 1 + gamma dt W/Wi and
+// scale gamma dt W (set by the caller).  Stage 2 takes ZPhi = Phi^0 + dt (1 -
+// gamma)(Phi^(1) - Phi^0)/(gamma dt), Zphi_j = phi_j^0 + dt (1 - gamma)(Phi^(1) -
+// mu_j phi_j^(1)); Phi^(1) is kept in the Psi output buffer until the end.
+// Right-hand side without the transport of h (added by imp_sub_transport_kernel
+// with scale -gamma dt); h goes to H; x0 = Phi^0 at stage 1 (stage 2 starts
+// from Phi^(1), left in x).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) start_rhs_paper_kernel(const ImpArgs<T> A, const StartConsts C, int stage,
+                                                                   double* b, double* x0, double* H) {
+    constexpr int NC = Packed<DIM>::NC;
+    const long long N = A.N;
+    const double gd = C.gam * A.dt_rhs, f1 = A.dt_rhs * (1.0 - C.gam);
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        double K[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+        for (int i = 0; i < DIM; ++i)
+#pragma unroll
+            for (int j = 0; j < DIM; ++j) K[i][j] = (double)A.kap_n[(long long)(i * DIM + j) * N + p];
+        double h[NC], zP[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const long long qc = (long long)c * N + p;
+            const double P0 = (double)A.sig_n[qc];
+            const double P1 = stage == 2 ? (double)A.psi[qc] : 0.0;
+            zP[c] = stage == 1 ? P0 : P0 + f1 * (P1 - P0) / gd;
+            double hs = 0.0;
+            for (int jj = 0; jj < A.m; ++jj) {
+                const double z0 = (double)A.modes_n[((long long)jj * NC + c) * N + p];
+                double z = z0;
+                if (stage == 2) z = fma(f1, P1 - C.mu[jj] * (fma(gd, P1, z0) * C.inv_den[jj]), z0);
+                hs = fma(C.w[jj] * C.mu[jj] * C.inv_den[jj], z, hs);
+            }
+            h[c] = hs;
+        }
+        double Hs[3][3];
+#pragma unroll
+        for (int r = 0; r < NC; ++r) {
+            Hs[Packed<DIM>::I(r)][Packed<DIM>::J(r)] = h[r];
+            Hs[Packed<DIM>::J(r)][Packed<DIM>::I(r)] = h[r];
+        }
+#pragma unroll
+        for (int r = 0; r < NC; ++r) {
+            const int i = Packed<DIM>::I(r), j = Packed<DIM>::J(r);
+            double lh = -A.inv_wi * h[r];
+#pragma unroll
+            for (int l = 0; l < DIM; ++l) lh = fma(K[i][l], Hs[l][j], fma(Hs[i][l], K[j][l], lh));
+            const long long q = (long long)r * N + p;
+            b[q] = zP[r] - gd * lh + gd * A.G * (K[i][j] + K[j][i]) * C.g[stage - 1];
+            if (x0) x0[q] = (double)A.sig_n[q];
+            H[q] = h[r];
+        }
+    }
+}
+
+// After a stage solve (x = Phi of the stage): stage 1 keeps Phi^(1) in the Psi
+// buffer; stage 2 writes Phi^1 = x, phi_j^1 = (Zphi_j + gamma dt Phi^1)/(1 + gamma
+// mu_j dt) (Zphi_j from phi_j^0 and Phi^(1)), and Psi^1 = W Phi^1 - h over Phi^(1).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) start_push_paper_kernel(const ImpArgs<T> A, const StartConsts C, int stage,
+                                                                    const double* x, const double* H) {
+    constexpr int NC = Packed<DIM>::NC;
+    const long long N = A.N;
+    const double gd = C.gam * A.dt_rhs, f1 = A.dt_rhs * (1.0 - C.gam);
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        bool finite = true;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const long long qc = (long long)c * N + p;
+            if (stage == 1) {
+                A.psi[qc] = (T)x[qc];
+                continue;
+            }
+            const double P1 = (double)A.psi[qc], P2 = x[qc];
+            for (int jj = 0; jj < A.m; ++jj) {
+                const long long q = ((long long)jj * NC + c) * N + p;
+                const double z0 = (double)A.modes_n[q];
+                const double z = fma(f1, P1 - C.mu[jj] * (fma(gd, P1, z0) * C.inv_den[jj]), z0);
+                A.modes_nm1[q] = (T)(fma(gd, P2, z) * C.inv_den[jj]);
+            }
+            const T phi = (T)P2, psi = (T)fma(C.W, P2, -H[qc]);
+            finite = finite && isfinite((double)phi) && isfinite((double)psi);
+            A.sig_np1[qc] = phi;
+            A.psi[qc] = psi;
+            if (A.sig_copy) A.sig_copy[qc] = psi;
+        }
+        if (!finite) atomicOr(A.flags, 1u);
+    }
+}
+
 template <typename T, int DIM>
 cudaError_t run_start_implicit(const ImpArgs<T>& a, const StartConsts& c, cudaStream_t st, int* iters,
                                double* relres) {
@@ -716,11 +812,17 @@ cudaError_t run_start_implicit(const ImpArgs<T>& a, const StartConsts& c, cudaSt
     cudaError_t e = cudaGetLastError();
     *iters = 0;
     *relres = 0.0;
+    double* H = K.Pinv + (long long)NC * NC * a.N;     // the paper's variable: h of the stage
     for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage) {
         // stage 1 reads the level-0 modes and starts from sigma^0; stage 2 reads the
         // explicit part written by the first push and starts from S1 (left in x)
-        start_rhs_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, c, stage, stage == 1 ? a.modes_n : a.modes_nm1, K.b,
-                                                          stage == 1 ? K.x : nullptr);
+        if (a.paper) {
+            start_rhs_paper_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, c, stage, K.b, stage == 1 ? K.x : nullptr, H);
+            imp_sub_transport_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, H, K.b, -c.gam * a.dt_rhs);
+        } else {
+            start_rhs_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, c, stage, stage == 1 ? a.modes_n : a.modes_nm1, K.b,
+                                                              stage == 1 ? K.x : nullptr);
+        }
         e = cudaGetLastError();
         int it = 0;
         double rr = 0.0;
@@ -728,7 +830,8 @@ cudaError_t run_start_implicit(const ImpArgs<T>& a, const StartConsts& c, cudaSt
         *iters += it;
         *relres = rr > *relres ? rr : *relres;
         if (e == cudaSuccess) {
-            start_push_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, c, stage, K.x);
+            if (a.paper) start_push_paper_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, c, stage, K.x, H);
+            else start_push_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, c, stage, K.x);
             e = cudaGetLastError();
         }
     }

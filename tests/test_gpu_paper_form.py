@@ -14,7 +14,8 @@ compression of g_alpha, stress = Psi).
 5. Explicit transport of Psi, with the tiled and the per-point pre-pass.
 6. Implicit transport of Psi (eq. FP_discrete) through the Krylov solver, far
    above the explicit limit.
-7. Refusals: alpha = 1, transport with the SDIRK2 start.
+   With either start (the SDIRK2 stages solve with the transport inside too).
+7. Refusals: alpha = 1, explicit transport with the SDIRK2 start.
 
 Tolerances: FP64 1e-11 per component; FP32 storage 2e-5 (Psi = xi Phi + h
 cancels: xi ~ (b0/dt)^(1-alpha), so the float rounding of Phi and of the
@@ -208,8 +209,8 @@ def test_paper_form_refusals():
     mu, w = soe.soe_nnls(0.5, dt, 1.0, 4)
     with pytest.raises(tfs.TfsError):
         tfs.Solver(2, n, 1.0, 1.0, 0.5, dt, m=0, precision=tfs.TFS_FP64, transport=False, form="paper")
-    # transport (explicit or implicit) and the SDIRK2 start together are refused at the first step
-    for tr in (True, "implicit"):
+    # explicit transport and the SDIRK2 start together are refused at the first step
+    for tr in (True,):
         s = tfs.Solver(2, n, 0.5, 1.0, 0.5, dt, m=4, precision=tfs.TFS_FP64, mu=mu, w=w, form="paper",
                        transport=tr, start="sdirk2")
         s.set_state(None)
@@ -278,7 +279,8 @@ IMPLICIT_CASES = [
 
 @pytest.mark.parametrize("dim,n,alpha,m,stencil,eps,speed", IMPLICIT_CASES)
 @pytest.mark.parametrize("precision", [0, 1])
-def test_paper_form_implicit_transport_matches_oracle(dim, n, alpha, m, stencil, eps, speed, precision):
+@pytest.mark.parametrize("start", ["bdf2", "sdirk2"])
+def test_paper_form_implicit_transport_matches_oracle(dim, n, alpha, m, stencil, eps, speed, precision, start):
     import torch
     from paper_2411_17294_gb300 import tfs
     steps, dt, Wi, beta = 6, 2e-3, 1.3, 0.4
@@ -295,9 +297,10 @@ def test_paper_form_implicit_transport_matches_oracle(dim, n, alpha, m, stencil,
         K0 = K
         K = lambda k: cast(K0(k))
         P0, u = cast(P0), cast(u)
-    pf = PaperForm(dim, N, Wi, beta, dt, mu, w, Phi0=P0, grid=n, eps=eps, stencil=stencil, implicit=True)
+    pf = PaperForm(dim, N, Wi, beta, dt, mu, w, Phi0=P0, grid=n, eps=eps, stencil=stencil, implicit=True,
+                   start=start)
     s = tfs.Solver(dim, n, alpha, Wi, beta, dt, m=m, precision=precision, mu=mu, w=w, transport="implicit",
-                   form="paper", stencil=stencil, eps=eps)
+                   form="paper", stencil=stencil, eps=eps, start=start)
     s.set_state(torch.as_tensor(P0, dtype=s.dtype, device=s.device))
     s.set_krylov(maxit=2000)
     ut = torch.as_tensor(u, dtype=s.dtype, device=s.device).contiguous()

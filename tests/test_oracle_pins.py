@@ -515,3 +515,51 @@ def test_paper_variable_implicit_transport_single_fourier_mode(stencil, U, eps):
     ref = (S * np.exp(1j * kx * x)).real
     assert np.max(np.abs(got[0] - ref)) < 1e-12 * np.max(np.abs(ref))
     assert np.max(np.abs(got[1:])) == 0.0
+
+
+def test_paper_variable_sdirk2_start_with_implicit_transport_single_fourier_mode():
+    # The SDIRK2 start with the transport inside both stage solves, one Fourier
+    # mode, kappa = 0: Psi = W Phi - h at a stage, so (1 + g dt W/Wi + g dt W s) Phi
+    # = ZPhi + g dt h/Wi + g dt s h, with h = sum_j w_j mu_j Zphi_j / (1 + g mu_j dt),
+    # W = sum_j w_j / (1 + g mu_j dt); then BDF2 steps as in the test above.
+    from oracle.paper_form import PaperForm
+    alpha, m, Wi, dt, steps, U = 0.5, 8, 1.3, 0.02, 6, 6.0
+    n, kx = (16, 3), 3
+    N = n[0] * n[1]
+    hgrid = 2 * math.pi / n[0]
+    mu, w = soe.soe_nnls(1 - alpha, dt, steps * dt, m)
+    x = (np.arange(N) % n[0]) * hgrid
+    phi0 = np.zeros((3, N))
+    phi0[0] = np.cos(kx * x)
+    u = np.zeros((2, N))
+    u[0] = U
+    pf = PaperForm(2, N, Wi, 0.5, dt, mu, w, Phi0=phi0, grid=n, implicit=True, start="sdirk2")
+    for _ in range(steps):
+        got = pf.step(np.zeros((4, N)), None, u)
+    th = kx * hgrid
+    s = U * (np.exp(-2j * th) - 6 * np.exp(-1j * th) + 3 + 2 * np.exp(1j * th)) / (6 * hgrid)
+    g = 1.0 - math.sqrt(0.5)
+    den = 1.0 + g * mu * dt
+    W = np.sum(w / den)
+    P0, q0 = 1.0 + 0j, np.zeros(m, complex)
+    ZP, Zq = P0, q0.copy()
+    for stage in (1, 2):
+        hh = np.sum(w * mu * Zq / den)
+        P = (ZP + g * dt * hh / Wi + g * dt * s * hh) / (1.0 + g * dt * W / Wi + g * dt * W * s)
+        q = (Zq + g * dt * P) / den
+        if stage == 1:
+            ZP = P0 + dt * (1 - g) * (P - P0) / (g * dt)
+            Zq = q0 + dt * (1 - g) * (P - mu * q)
+    S = W * P - hh
+    b0, b1, b2 = 1.5, -2.0, 0.5
+    c = 1.0 / (b0 + mu * dt)
+    xi = b0 * np.sum(w * c)
+    P_n, P_nm1, q_n, q_nm1 = P, P0, q, q0
+    for _ in range(steps - 1):
+        hh = np.sum(w * mu * c * (b1 * q_n + b2 * q_nm1))
+        Pn = (-b1 * P_n - b2 * P_nm1 - dt * hh / Wi - dt * s * hh) / (b0 + dt * xi / Wi + dt * xi * s)
+        qn = c * (-b1 * q_n - b2 * q_nm1 + dt * Pn)
+        S = xi * Pn + hh
+        P_nm1, P_n, q_nm1, q_n = P_n, Pn, q_n, qn
+    ref = (S * np.exp(1j * kx * x)).real
+    assert np.max(np.abs(got[0] - ref)) < 1e-12 * np.max(np.abs(ref))
