@@ -128,3 +128,35 @@ def test_calls_out_of_order_and_workspace(lib):
     assert lib.tfs_step_index(h) == 0
     assert lib.tfs_strerror(tfs.TFS_ERR_UNSTABLE).decode().startswith("velocity")
     lib.tfs_destroy(h)
+
+
+def test_form_and_transport_resize_checks(lib):
+    # The paper's variable adds two stress-sized buffers (Psi^n, Psi^{n-1}) and,
+    # with implicit transport, one more FP64 vector; with a workspace bound, a
+    # parameter change that needs more than it returns TFS_ERR_NOWORKSPACE and
+    # changes nothing.  Host logic only: no device memory is touched.
+    from paper_2411_17294_gb300 import tfs
+    rc, h = make(lib, dim=2, n=(16, 16), m=4, precision=0)
+    assert rc == tfs.TFS_OK
+    stress = lib.tfs_workspace_bytes(h)
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_FORM, float(tfs.TFS_FORM_PAPER)) == tfs.TFS_OK
+    paper = lib.tfs_workspace_bytes(h)
+    field = 3 * 256 * 8
+    assert paper == stress + 2 * field
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_TRANSPORT, 2.0) == tfs.TFS_OK
+    paper_imp = lib.tfs_workspace_bytes(h)
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_FORM, float(tfs.TFS_FORM_STRESS)) == tfs.TFS_OK
+    stress_imp = lib.tfs_workspace_bytes(h)
+    assert paper_imp == stress_imp + 2 * field + field      # Psi ring + h
+    # bind the stress-form workspace (explicit transport), then ask for more
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_TRANSPORT, 1.0) == tfs.TFS_OK
+    assert lib.tfs_bind_workspace(h, ctypes.c_void_p(256 * 1000), stress) == tfs.TFS_OK
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_FORM, float(tfs.TFS_FORM_PAPER)) == tfs.TFS_ERR_NOWORKSPACE
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_TRANSPORT, 2.0) == tfs.TFS_ERR_NOWORKSPACE
+    assert lib.tfs_workspace_bytes(h) == stress
+    # a large enough workspace takes both
+    assert lib.tfs_bind_workspace(h, ctypes.c_void_p(256 * 1000), paper_imp) == tfs.TFS_OK
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_FORM, float(tfs.TFS_FORM_PAPER)) == tfs.TFS_OK
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_TRANSPORT, 2.0) == tfs.TFS_OK
+    assert lib.tfs_checkpoint_bytes(h) == 256 + 5 * field + 2 * 4 * field
+    lib.tfs_destroy(h)
