@@ -177,6 +177,49 @@ def test_paper_form_256_cubed_bench_configuration_sampled():
     assert np.all(rel_err_per_component(out[:, idx], ref) < 2e-5)
 
 
+def test_paper_form_with_transport_256_cubed_sampled():
+    # The 256^3 m = 32 FP32 grid with explicit transport of Psi: after s steps a
+    # point depends only on the points within 2 s cells (radius-2 stencil on the
+    # extrapolated Psi), so the oracle runs on the periodic (4 s + 1)^3 block
+    # around each sample and its centre value is exact.
+    import torch
+    from paper_2411_17294_gb300 import tfs
+    n, m, alpha, Wi, beta, dt, steps = (256, 256, 256), 32, 0.6, 2.0, 0.9, 2e-4, 3
+    mu, w = soe.soe_nnls(1 - alpha, dt, 200 * dt, m)
+    dev = torch.device("cuda", 0)
+    u, kap = inputs.spectral_velocity(3, n, 24, 3, device=dev)
+    s = tfs.Solver(3, n, alpha, Wi, beta, dt, m=m, precision=tfs.TFS_FP32, mu=mu, w=w, transport=True,
+                   form="paper")
+    kt = torch.as_tensor(kap, dtype=torch.float32, device=dev).contiguous()
+    ut = (0.1 * torch.as_tensor(u, dtype=torch.float32, device=dev)).contiguous()
+    s.set_state(None)
+    for _ in range(steps):
+        s.step(kt, kt, ut)
+    out = s.stress().cpu().numpy().astype(np.float64)
+    assert not (s.status() & (tfs.TFS_FLAG_NONFINITE | tfs.TFS_FLAG_TIMEOUT))
+    s.close()
+    kap32 = kt.cpu().numpy().astype(np.float64)
+    u32 = ut.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(2025)
+    R = 2 * steps
+    B = 2 * R + 1
+    samples = [tuple(int(v) for v in rng.integers(0, 256, size=3)) for _ in range(6)] + [(0, 0, 0), (255, 255, 255)]
+    got, ref = [], []
+    for (x, y, z) in samples:
+        xs, ys, zs = (np.arange(c - R, c + R + 1) % 256 for c in (x, y, z))
+        idx = (xs[None, None, :] + 256 * (ys[None, :, None] + 256 * zs[:, None, None])).ravel()
+        pf = PaperForm(3, B ** 3, Wi, beta, dt, mu, w, grid=(B, B, B), L=(2 * np.pi * B / 256,) * 3)
+        kb, ub = np.ascontiguousarray(kap32[:, idx]), np.ascontiguousarray(u32[:, idx])
+        for _ in range(steps):
+            psi = pf.step(kb, kb, ub)
+        centre = R + B * (R + B * R)
+        ref.append(psi[:, centre])
+        got.append(out[:, x + 256 * (y + 256 * z)])
+    got, ref = np.array(got).T, np.array(ref).T
+    assert np.max(np.abs(ref)) > 0
+    assert np.all(rel_err_per_component(got, ref) < 2e-5), rel_err_per_component(got, ref)
+
+
 def test_paper_form_checkpoint_round_trip():
     import torch
     dim, n, alpha, m, dt = 2, (40, 24), 0.5, 8, 5e-3
