@@ -174,26 +174,63 @@ __device__ __forceinline__ void block_partials(double a0, double a1, int nsets, 
     }
 }
 
-// y = Op(x); partial sums of (w0, y) and (w1, y) when w0 / w1 are given
+// Periodic neighbour offsets of point p along every axis (taps -2..2, index k + 2)
+// and the transport stencil's coefficient of each tap at p: sum_a u_a D_a f -
+// eps Lap f = sum_a sum_k cf[a][k] f[p + off[a][k]], with D_a the stencils of
+// deriv_at (upwinded on the sign of u_a(p)).  Computed once per point for all
+// components; the grid index fits 32 bits here (an implicit-transport workspace
+// for 2^31 points would not fit any device).
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kThreads) imp_apply_kernel(const ImpArgs<T> A, const double* Mb, const double* x,
-                                                             double* y, const double* w0, const double* w1,
-                                                             double* partials, const double* sc) {
+__device__ __forceinline__ void point_stencil(const ImpArgs<T>& A, long long p, long long off[3][5], double cf[3][5]) {
+    const unsigned n0 = (unsigned)A.n0, n1 = (unsigned)A.n1, n2 = (unsigned)A.n2;
+    const unsigned pp = (unsigned)p;
+    const unsigned q1 = pp / n0;
+    const unsigned c[3] = {pp - q1 * n0, q1 % n1, q1 / n1};
+    const unsigned len[3] = {n0, n1, n2};
+    const long long str[3] = {1, (long long)n0, (long long)n0 * n1};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+#pragma unroll
+        for (int k = -2; k <= 2; ++k) {
+            int v = (int)c[a] + k;
+            const int L = (int)len[a];
+            if (v < 0) v += L;
+            if (v < 0) v += L;
+            if (v >= L) v -= L;
+            if (v >= L) v -= L;
+            off[a][k + 2] = ((long long)v - (long long)c[a]) * str[a];
+        }
+        const double ua = (double)A.u[(long long)a * A.N + p];
+        const double ih = A.inv_h[a];
+        const double e = A.eps * ih * ih;
+        if (A.stencil == 1) {
+            const double s = 0.5 * ua * ih;
+            cf[a][0] = 0.0; cf[a][1] = -s - e; cf[a][2] = 2.0 * e; cf[a][3] = s - e; cf[a][4] = 0.0;
+        } else if (ua >= 0.0) {
+            const double s = ua * ih / 6.0;
+            cf[a][0] = s; cf[a][1] = -6.0 * s - e; cf[a][2] = 3.0 * s + 2.0 * e; cf[a][3] = 2.0 * s - e; cf[a][4] = 0.0;
+        } else {
+            const double s = ua * ih / 6.0;
+            cf[a][0] = 0.0; cf[a][1] = -2.0 * s - e; cf[a][2] = -3.0 * s + 2.0 * e; cf[a][3] = 6.0 * s - e; cf[a][4] = -s;
+        }
+    }
+}
+
+// y = Op(x); partial sums of (w0, y) and (w1, y) when w0 / w1 are given (w1 may be
+// y itself: the (t, t) product)
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) imp_apply_kernel(const ImpArgs<T> A, const double* __restrict__ Mb,
+                                                             const double* __restrict__ x, double* y,
+                                                             const double* w0, const double* w1, double* partials,
+                                                             const double* sc) {
     constexpr int NC = Packed<DIM>::NC;
     if (done(sc)) return;
     const long long N = A.N;
     double a0 = 0.0, a1 = 0.0;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-        GridIdx g;
-        g.n0 = A.n0;
-        g.n1 = A.n1;
-        g.n2 = A.n2;
-        g.x = p % A.n0;
-        g.y = (p / A.n0) % A.n1;
-        g.z = p / ((long long)A.n0 * A.n1);
-        double u[3] = {0, 0, 0};
-#pragma unroll
-        for (int ax = 0; ax < DIM; ++ax) u[ax] = (double)A.u[(long long)ax * N + p];
+        long long off[3][5];
+        double cf[3][5];
+        point_stencil<T, DIM>(A, p, off, cf);
         double xp[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) xp[c] = x[(long long)c * N + p];
@@ -202,16 +239,17 @@ __global__ void __launch_bounds__(kThreads) imp_apply_kernel(const ImpArgs<T> A,
             double acc = 0.0;
 #pragma unroll
             for (int k = 0; k < NC; ++k) acc = fma(Mb[(long long)(r * NC + k) * N + p], xp[k], acc);
-            const double* f = x + (long long)r * N;
+            const double* f = x + (long long)r * N + p;
             double t = 0.0;
 #pragma unroll
-            for (int ax = 0; ax < DIM; ++ax) {
-                t += u[ax] * deriv_at<DIM>(f, g, ax, A.stencil, u[ax], A.inv_h[ax]);
-                if (A.eps != 0.0)
-                    t -= A.eps * (f[g.at(ax, -1)] - 2.0 * xp[r] + f[g.at(ax, 1)]) * (A.inv_h[ax] * A.inv_h[ax]);
+            for (int a = 0; a < DIM; ++a) {
+                t = fma(cf[a][2], xp[r], t);
+#pragma unroll
+                for (int k = 0; k < 5; ++k)
+                    if (k != 2 && cf[a][k] != 0.0) t = fma(cf[a][k], f[off[a][k]], t);
             }
             const long long q = (long long)r * N + p;
-            const double yv = acc + A.dt * t;
+            const double yv = fma(A.dt, t, acc);
             y[q] = yv;
             if (w0) a0 = fma(w0[q], yv, a0);
             if (w1) a1 = fma(w1[q], yv, a1);
