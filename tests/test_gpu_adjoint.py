@@ -144,3 +144,39 @@ def test_adjoint_workload_512_against_central_differences():
         km[c, q] -= h
         fd = dJ(run(Wi, beta, sigma0, kp), run(Wi, beta, sigma0, km)) / (2 * h)
         assert close(g_k[c, q].item(), fd), (c, q, g_k[c, q].item(), fd)
+
+
+@pytest.mark.parametrize("dim,n,alpha,transport", [(2, (20, 17), 0.5, True), (3, (6, 5, 7), 0.3, False),
+                                                   (2, (16, 9), 1.0, True)])
+def test_adjoint_dot_product_exact_directions(dim, n, alpha, transport):
+    # Directions in which the step map is affine give dot-product tests with no
+    # finite-difference error: sigma(T) is affine in sigma0 (the initial stress
+    # enters every step linearly), so <lambda, sigma(T; sigma0 + d) - sigma(T;
+    # sigma0)> = <d, dJ/dsigma0> for J = <lambda, sigma(T)>; and it is affine in G =
+    # (1 - beta)/(Wi Re), itself affine in beta, so (J(beta2) - J(beta1))/(beta2 -
+    # beta1) = dJ/dbeta.  FP64, to rounding.
+    Wi, beta, dt, steps, K = 1.3, 0.4, 2e-3, 14, 4
+    m = 0 if alpha == 1.0 else 8
+    mu, w = soe.soe_build(alpha, dt, steps * dt, m) if m else (None, None)
+    u, kap = inputs.spectral_velocity(dim, n, 2, seed=31)
+    case = dict(dim=dim, n=n, alpha=alpha, dt=dt, eps=0.0)
+    if m:
+        case.update(mu=mu, w=w)
+    u = stable_velocity(case, u)
+    rng = np.random.default_rng(32)
+    nc = 3 if dim == 2 else 6
+    N = int(np.prod(n))
+    sigma0 = rng.normal(size=(nc, N))
+    d = rng.normal(size=(nc, N))
+    lam = rng.normal(size=(nc, N))
+    run = lambda s0, b: gpu_gradients(dim, n, alpha, Wi, b, dt, m, steps, K, s0, kap, u, lambda sT: lam, 0,
+                                      transport, mu, w)[0]
+    base = run(sigma0, beta)
+    moved = run(sigma0 + d, beta)
+    lhs = np.sum(lam * (moved["sigma_T"] - base["sigma_T"]))
+    rhs = np.sum(d * base["sigma0"])
+    assert abs(lhs - rhs) <= 1e-11 * (abs(lhs) + abs(rhs)), (lhs, rhs)
+    b2 = beta + 0.05
+    other = run(sigma0, b2)
+    dJ = (np.sum(lam * other["sigma_T"]) - np.sum(lam * base["sigma_T"])) / (b2 - beta)
+    assert abs(dJ - base["beta"]) <= 1e-9 * abs(dJ), (dJ, base["beta"])
