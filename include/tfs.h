@@ -209,6 +209,17 @@ int tfs_set_step_events(tfs_handle h, void* ev_before, void* ev_after);
 /* Current step index n (number of completed steps since tfs_set_state). */
 long tfs_step_index(tfs_handle h);
 
+/* Check of the bounded device wait (no counterpart in the paper).  Every
+   mbarrier wait of the library gives up after about 2 s, latches
+   TFS_FLAG_TIMEOUT and lets its kernel return, so that a copy that never
+   completes cannot hang the GPU.  This launches one block whose thread waits
+   on an mbarrier that nothing arrives at, through that same wait, and reports
+   the flag it latched (*flags, TFS_FLAG_TIMEOUT when the wait gave up) and the
+   time the wait took (*seconds).  Synchronises `stream`; allocates nothing
+   (a file-scope device array holds the result).  TFS_ERR_ARG for NULL
+   pointers, TFS_ERR_CUDA if the launch or copy fails. */
+int tfs_check_wait_bound(unsigned* flags, double* seconds, void* stream);
+
 /* Iterations and final relative residual |b - Op x| / |b| of the last
    implicit-transport solve (TFS_PARAM_TRANSPORT = 2); either pointer may be
    NULL.  Host-side, no synchronisation. */

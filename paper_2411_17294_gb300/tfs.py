@@ -30,7 +30,7 @@ EXPORTS = [
     "tfs_create", "tfs_set_param", "tfs_set_soe", "tfs_transport_limit", "tfs_workspace_bytes", "tfs_bind_workspace",
     "tfs_set_state", "tfs_step", "tfs_get_stress", "tfs_set_step_events", "tfs_step_index", "tfs_last_solve", "tfs_checkpoint_bytes", "tfs_save",
     "tfs_load", "tfs_adjoint_workspace_bytes", "tfs_bind_adjoint_workspace", "tfs_backward", "tfs_status",
-    "tfs_strerror", "tfs_destroy", "tfs_run_static",
+    "tfs_strerror", "tfs_destroy", "tfs_run_static", "tfs_check_wait_bound",
 ]
 
 
@@ -82,6 +82,7 @@ def load_library(path: str | None = None):
         "tfs_status": (ctypes.c_int, [H, ctypes.POINTER(ctypes.c_uint)]),
         "tfs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "tfs_destroy": (ctypes.c_int, [H]),
+        "tfs_check_wait_bound": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint), dp, vp]),
         "tfs_run_static": (ctypes.c_int, [ctypes.POINTER(TfsGrid), ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, dp, vp, vp, vp,
                                           ctypes.c_int, vp, vp]),
