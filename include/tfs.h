@@ -99,7 +99,8 @@ enum {
                                  With transport 2 both stage systems go through the implicit solver
                                  (tfs_last_solve: iterations summed, larger residual).  With
                                  TFS_FORM_PAPER the same method on Phi and its modes.  tfs_backward
-                                 refuses a handle with this start (TFS_ERR_ARG) */
+                                 differentiates the start with transport 0 (zero initial modes, as
+                                 tfs_set_state leaves them) and refuses it with transport (TFS_ERR_ARG) */
     TFS_PARAM_FORM = 8        /* variable carried, TFS_FORM_*: the stress (default), or the paper's own
                                  variable (Section 3.4): Phi with d Phi/dt = (L(kappa) - I/Wi) Psi +
                                  G (kappa + kappa^T) Psi0, Psi = D^{1-alpha} Phi by kernel compression of

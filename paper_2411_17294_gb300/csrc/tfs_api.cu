@@ -1096,7 +1096,8 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
                  const void* grad_u, const void* u, double* dJ_dsigma0, double* dJ_dgrad_u, double* dJ_dWi,
                  double* dJ_dbeta, void* stream) {
     if (valid_handle(h) && h->implicit_transport()) return TFS_ERR_ARG;   // adjoint of the implicit step not built
-    if (valid_handle(h) && h->start == TFS_START_SDIRK2) return TFS_ERR_ARG;   // nor of the SDIRK2 first step
+    // the SDIRK2 first step's adjoint is built for the pointwise law
+    if (valid_handle(h) && h->start == TFS_START_SDIRK2 && h->transport != 0) return TFS_ERR_ARG;
     if (valid_handle(h) && h->paper()) return TFS_ERR_ARG;                     // nor of the paper's variable
     if (!valid_handle(h) || !dJ_dsigma_T || !checkpoints || !grad_u || !dJ_dsigma0 || !dJ_dgrad_u || !dJ_dWi ||
         !dJ_dbeta)
@@ -1136,6 +1137,29 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
         for (int n = end - 1; n >= start; --n) {
             const void* sig_np1 = L.seg + (size_t)(n - start) * L.seg_stride;
             const int nxt = 1 - cur;
+            if (n == 0 && h->start == TFS_START_SDIRK2) {
+                const StartConsts c = start_consts(h);
+                const double a_stage = h->dt * c.W + h->dt / h->Wi;
+                const double G = (1.0 - h->beta) / (h->Wi * h->Re);
+                if (h->is_double()) {
+                    StartAdjArgs<double> a{(const double*)grad_u, h->sigma0_zero ? nullptr : (const double*)h->sigma0,
+                                           L.s[2 * cur], L.s[2 * cur + 1], (const double*)L.ell[ell_prev],
+                                           (const double*)L.ell[1 - ell_prev], L.s[2 * nxt], L.s[2 * nxt + 1],
+                                           dJ_dgrad_u, L.partials, h->flags, h->N, h->m, h->dt, a_stage, G, h->Wi,
+                                           h->Re};
+                    e = launch_start_adjoint_f64(a, c, h->dim, s);
+                } else {
+                    StartAdjArgs<float> a{(const float*)grad_u, h->sigma0_zero ? nullptr : (const float*)h->sigma0,
+                                          L.s[2 * cur], L.s[2 * cur + 1], (const float*)L.ell[ell_prev],
+                                          (const float*)L.ell[1 - ell_prev], L.s[2 * nxt], L.s[2 * nxt + 1],
+                                          dJ_dgrad_u, L.partials, h->flags, h->N, h->m, h->dt, a_stage, G, h->Wi,
+                                          h->Re};
+                    e = launch_start_adjoint_f32(a, c, h->dim, s);
+                }
+                if (e != cudaSuccess) return TFS_ERR_CUDA;
+                cur = nxt;
+                continue;
+            }
             if (h->is_double()) {
                 AdjArgs<double> a{};
                 a.kap_n = (const double*)grad_u;

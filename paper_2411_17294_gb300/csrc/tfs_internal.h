@@ -171,6 +171,30 @@ cudaError_t launch_start_point_f32(const StartArgs<float>& a, const StartConsts&
 // the same first step in the paper's variable (c.g holds Psi0 at the two stage times)
 cudaError_t launch_start_paper_f64(const StartArgs<double>& a, const StartConsts& c, int dim, cudaStream_t s);
 cudaError_t launch_start_paper_f32(const StartArgs<float>& a, const StartConsts& c, int dim, cudaStream_t s);
+// Adjoint of the pointwise SDIRK2 first step (transport off, zero initial modes):
+// inputs the adjoints of sigma^1 (s1), of sigma^0 as the next step's level n-1
+// (s0) and of the level-1 modes (z_j = b1 ell_prev + b2 ell_prev2); outputs the
+// adjoint of sigma0 in s1_out (s0_out = 0), and adds dJ/dkappa^0 to g_kap and the
+// per-block dJ/dWi, dJ/dbeta to partials[2 b], [2 b + 1] (b = point / 32).
+template <typename T>
+struct StartAdjArgs {
+    const T* kap0;
+    const T* sigma0;       // nullptr for zero
+    const double* s1;
+    const double* s0;
+    const T* ell_prev;
+    const T* ell_prev2;
+    double* s1_out;
+    double* s0_out;
+    double* g_kap;
+    double* partials;
+    unsigned* flags;
+    long long N;
+    int m;
+    double dt, a, G, Wi, Re;
+};
+cudaError_t launch_start_adjoint_f64(const StartAdjArgs<double>& a, const StartConsts& c, int dim, cudaStream_t s);
+cudaError_t launch_start_adjoint_f32(const StartAdjArgs<float>& a, const StartConsts& c, int dim, cudaStream_t s);
 // implicit transport: the two stage systems by the Krylov solver of the implicit step
 // (a.a, a.kap_n = a.kap_nm1 = kappa^0 set by the caller); synchronises `s`;
 // iterations summed and the larger relative residual of the two stages

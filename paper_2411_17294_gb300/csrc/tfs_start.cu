@@ -218,6 +218,182 @@ __global__ void __launch_bounds__(kThreads) start_paper_kernel(const StartArgs<T
     }
 }
 
+// Adjoint of start_point_kernel for zero initial modes (the state tfs_set_state
+// leaves).  With Z_j^(1) = 0 the forward reads
+//   r1 = dt (W s0 + G k g1),                      S1 = M^-1 r1
+//   Z2_j = dt (1 - gamma) w_j iota_j (S1 - s0),    iota_j = 1/(1 + gamma mu_j dt)
+//   r2 = dt (W s0 + sum_j mu_j iota_j Z2_j + G k g2),  S2 = M^-1 r2
+//   sigma_j^1 = Z2_j (1 - gamma dt mu_j iota_j) + gamma dt w_j iota_j (S2 - s0),  sigma^1 = S2
+// (M = (dt W + dt/Wi) I - dt L(kappa^0), k = kappa^0 + kappa^0T, s0 = sigma0 = sigma^0), and
+// its reverse, given the adjoints lam1 of sigma^1, z_j of sigma_j^1 and s0in of
+// sigma^0 (as the next step's level n-1):
+//   lamS2 = lam1 + sum_j z_j gamma dt w_j iota_j;    lamZ2_j = z_j (1 - gamma dt mu_j iota_j)
+//   lamr2 = M^-T lamS2;  lamZ2_j += dt mu_j iota_j lamr2
+//   lamS1 = sum_j lamZ2_j dt (1 - gamma) w_j iota_j;  lamr1 = M^-T lamS1
+//   dJ/dsigma0 = s0in + dt W (lamr1 + lamr2) - sum_j (z_j gamma dt + lamZ2_j dt (1 - gamma)) w_j iota_j
+// and for each stage i the terms of the BDF2 adjoint with (lamR, sigma, g) =
+// (lamr_i, S_i, g_i): dJ/dkappa += dt lamr_i-weighted (S kappa-derivatives) + dt G g_i
+// (sym), dJ/dWi += (dt/Wi^2) <lamr_i, S_i> - (G/Wi) dt g_i <lamr_i, k>, dJ/dbeta +=
+// -dt g_i <lamr_i, k> / (Wi Re).  FP64 per point whatever the storage.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(32) start_adjoint_kernel(const StartAdjArgs<T> A, const StartConsts C) {
+    constexpr int NC = Packed<DIM>::NC;
+    const long long N = A.N;
+    const long long p = (long long)blockIdx.x * 32 + threadIdx.x;
+    double gWi = 0.0, gbeta = 0.0;
+    if (p < N) {
+        double K[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+        for (int i = 0; i < DIM; ++i)
+#pragma unroll
+            for (int j = 0; j < DIM; ++j) K[i][j] = (double)A.kap0[(long long)(i * DIM + j) * N + p];
+        double M0[NC][NC];
+        assemble_M<DIM>(K, A.a, A.dt, M0);
+        const double f1 = A.dt * (1.0 - C.gam), f2 = A.dt * C.gam;
+        double s0[NC], ks[NC], S1[NC], S2[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int i = Packed<DIM>::I(c), j = Packed<DIM>::J(c);
+            s0[c] = A.sigma0 ? (double)A.sigma0[(long long)c * N + p] : 0.0;
+            ks[c] = K[i][j] + K[j][i];
+        }
+        bool ok = true;
+        // forward stages (zero initial modes)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) S1[c] = A.dt * (C.W * s0[c] + A.G * ks[c] * C.g[0]);
+        {
+            double M[NC][NC];
+#pragma unroll
+            for (int r = 0; r < NC; ++r)
+#pragma unroll
+                for (int k = 0; k < NC; ++k) M[r][k] = M0[r][k];
+            ok = gauss_pp<NC>(M, S1, 1e-300) && ok;
+        }
+        double c1 = 0.0;     // sum_j mu_j iota_j f1 w_j iota_j: Z2 enters r2 through it
+        for (int jj = 0; jj < A.m; ++jj) c1 += C.mu[jj] * C.inv_den[jj] * f1 * C.w[jj] * C.inv_den[jj];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) S2[c] = A.dt * (C.W * s0[c] + c1 * (S1[c] - s0[c]) + A.G * ks[c] * C.g[1]);
+        {
+            double M[NC][NC];
+#pragma unroll
+            for (int r = 0; r < NC; ++r)
+#pragma unroll
+                for (int k = 0; k < NC; ++k) M[r][k] = M0[r][k];
+            ok = gauss_pp<NC>(M, S2, 1e-300) && ok;
+        }
+        // reverse
+        double lamS2[NC], lamS1[NC], gs0[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            lamS2[c] = A.s1[(long long)c * N + p];
+            gs0[c] = A.s0[(long long)c * N + p];
+        }
+        // lamZ2_j = z_j (1 - f2 mu_j iota_j) + dt mu_j iota_j lamr2 needs lamr2 first:
+        // accumulate the z-only parts now, the lamr2 part after the solve
+        double zq[NC];   // sum_j z_j (1 - f2 mu_j iota_j) f1 w_j iota_j
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            double a1 = 0.0, a2 = 0.0;
+            for (int jj = 0; jj < A.m; ++jj) {
+                const long long q = ((long long)jj * NC + c) * N + p;
+                const double z = kB1 * (double)A.ell_prev[q] + kB2 * (double)A.ell_prev2[q];
+                const double wi = C.w[jj] * C.inv_den[jj];
+                a1 = fma(z, f2 * wi, a1);
+                a2 = fma(z * (1.0 - f2 * C.mu[jj] * C.inv_den[jj]), f1 * wi, a2);
+            }
+            zq[c] = a2;
+            lamS2[c] += a1;
+            gs0[c] -= a1;
+        }
+        double Mt[NC][NC];
+#pragma unroll
+        for (int r = 0; r < NC; ++r)
+#pragma unroll
+            for (int k = 0; k < NC; ++k) Mt[r][k] = M0[k][r];
+        double lr2[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) lr2[c] = lamS2[c];
+        {
+            double M[NC][NC];
+#pragma unroll
+            for (int r = 0; r < NC; ++r)
+#pragma unroll
+                for (int k = 0; k < NC; ++k) M[r][k] = Mt[r][k];
+            ok = gauss_pp<NC>(M, lr2, 1e-300) && ok;
+        }
+        // lamS1 = sum_j lamZ2_j f1 w_j iota_j = zq + dt c1 lamr2
+#pragma unroll
+        for (int c = 0; c < NC; ++c) lamS1[c] = zq[c] + A.dt * c1 * lr2[c];
+        double lr1[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) lr1[c] = lamS1[c];
+        ok = gauss_pp<NC>(Mt, lr1, 1e-300) && ok;
+        // dJ/dsigma0
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            gs0[c] += A.dt * C.W * (lr1[c] + lr2[c]) - lamS1[c];
+            A.s1_out[(long long)c * N + p] = gs0[c];
+            A.s0_out[(long long)c * N + p] = 0.0;
+        }
+        // parameter derivatives, per stage
+        double gK[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int st = 0; st < 2; ++st) {
+            const double* lam = st == 0 ? lr1 : lr2;
+            const double* sig = st == 0 ? S1 : S2;
+            double S3[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+            for (int r = 0; r < NC; ++r) {
+                const int i = Packed<DIM>::I(r), j = Packed<DIM>::J(r);
+                S3[i][j] = sig[r];
+                S3[j][i] = sig[r];
+            }
+            const double src = A.dt * A.G * C.g[st];
+            double sym_dot = 0.0, sig_dot = 0.0;
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc) {
+                const int r = Packed<DIM>::I(cc), s2 = Packed<DIM>::J(cc);
+                const double l = lam[cc];
+#pragma unroll
+                for (int b = 0; b < DIM; ++b) {
+                    gK[r][b] += A.dt * l * S3[b][s2];
+                    gK[s2][b] += A.dt * l * S3[r][b];
+                }
+                gK[r][s2] += src * l;
+                gK[s2][r] += src * l;
+                sym_dot += l * ks[cc];
+                sig_dot += l * sig[cc];
+            }
+            const double lam_a = -sig_dot;
+            const double lam_G = A.dt * C.g[st] * sym_dot;
+            gWi += -A.dt / (A.Wi * A.Wi) * lam_a - A.G / A.Wi * lam_G;
+            gbeta += -lam_G / (A.Wi * A.Re);
+        }
+#pragma unroll
+        for (int a = 0; a < DIM; ++a)
+#pragma unroll
+            for (int b = 0; b < DIM; ++b) A.g_kap[(long long)(a * DIM + b) * N + p] += gK[a][b];
+        if (!ok) atomicOr(A.flags, 2u);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        gWi += __shfl_xor_sync(0xffffffffu, gWi, off);
+        gbeta += __shfl_xor_sync(0xffffffffu, gbeta, off);
+    }
+    if (threadIdx.x == 0) {
+        A.partials[2 * (long long)blockIdx.x + 0] += gWi;
+        A.partials[2 * (long long)blockIdx.x + 1] += gbeta;
+    }
+}
+
+template <typename T>
+cudaError_t launch_adj(const StartAdjArgs<T>& a, const StartConsts& c, int dim, cudaStream_t s) {
+    const long long blocks = (a.N + 31) / 32;
+    if (blocks < 1 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (dim == 2) start_adjoint_kernel<T, 2><<<(unsigned)blocks, 32, 0, s>>>(a, c);
+    else start_adjoint_kernel<T, 3><<<(unsigned)blocks, 32, 0, s>>>(a, c);
+    return cudaGetLastError();
+}
+
 template <typename T, bool PAPER>
 cudaError_t launch(const StartArgs<T>& a, const StartConsts& c, int dim, cudaStream_t s) {
     long long blocks = (a.N + kThreads - 1) / kThreads;
@@ -242,6 +418,14 @@ cudaError_t launch_start_point_f64(const StartArgs<double>& a, const StartConsts
 
 cudaError_t launch_start_point_f32(const StartArgs<float>& a, const StartConsts& c, int dim, cudaStream_t s) {
     return launch<float, false>(a, c, dim, s);
+}
+
+cudaError_t launch_start_adjoint_f64(const StartAdjArgs<double>& a, const StartConsts& c, int dim, cudaStream_t s) {
+    return launch_adj(a, c, dim, s);
+}
+
+cudaError_t launch_start_adjoint_f32(const StartAdjArgs<float>& a, const StartConsts& c, int dim, cudaStream_t s) {
+    return launch_adj(a, c, dim, s);
 }
 
 cudaError_t launch_start_paper_f64(const StartArgs<double>& a, const StartConsts& c, int dim, cudaStream_t s) {

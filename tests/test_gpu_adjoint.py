@@ -17,11 +17,11 @@ def _lib():
 
 
 def gpu_gradients(dim, n, alpha, Wi, beta, dt, m, steps, K, sigma0, kap, u, dJ, precision, transport, mu, w,
-                  eps=0.0):
+                  eps=0.0, start="bdf2"):
     import torch
     from paper_2411_17294_gb300 import tfs
     s = tfs.Solver(dim, n, alpha, Wi, beta, dt, m=m if alpha < 1 else 0, precision=precision, mu=mu, w=w,
-                   transport=transport, eps=eps)
+                   transport=transport, eps=eps, start=start)
     dt_ = s.dtype
     dev = s.device
     kt = torch.as_tensor(kap, dtype=dt_, device=dev).contiguous()
@@ -180,3 +180,44 @@ def test_adjoint_dot_product_exact_directions(dim, n, alpha, transport):
     other = run(sigma0, b2)
     dJ = (np.sum(lam * other["sigma_T"]) - np.sum(lam * base["sigma_T"])) / (b2 - beta)
     assert abs(dJ - base["beta"]) <= 1e-9 * abs(dJ), (dJ, base["beta"])
+
+
+
+@pytest.mark.parametrize("dim,n,alpha,steps,K", [(2, (9, 7), 0.5, 8, 3), (3, (4, 5, 3), 0.3, 5, 5), (2, (6, 5), 0.7, 1, 1)])
+def test_sdirk2_start_adjoint(dim, n, alpha, steps, K):
+    # The adjoint of a run that starts with the SDIRK2 step (pointwise law):
+    # exact in the affine directions (sigma0, beta), FP64 central differences
+    # for Wi and entries of kappa, and the FP32-storage adjoint near the FP64 one.
+    Wi, beta, dt, m = 1.3, 0.4, 2e-3, 6
+    mu, w = soe.soe_build(alpha, dt, 50 * dt, m)
+    _, kap = inputs.spectral_velocity(dim, n, 2, seed=41)
+    kap = 0.5 * np.asarray(kap)
+    rng = np.random.default_rng(42)
+    nc = 3 if dim == 2 else 6
+    N = int(np.prod(n))
+    sigma0 = rng.normal(size=(nc, N))
+    lam = rng.normal(size=(nc, N))
+    run = lambda s0, k, wi, b, prec=0: gpu_gradients(dim, n, alpha, wi, b, dt, m, steps, K, s0, k, None,
+                                                     lambda sT: lam, prec, False, mu, w, start="sdirk2")[0]
+    J = lambda out: float(np.sum(lam * out["sigma_T"]))
+    base = run(sigma0, kap, Wi, beta)
+    d = rng.normal(size=(nc, N))
+    moved = run(sigma0 + d, kap, Wi, beta)
+    lhs, rhs = J(moved) - J(base), float(np.sum(d * base["sigma0"]))
+    assert abs(lhs - rhs) <= 1e-10 * (abs(lhs) + abs(rhs)), (lhs, rhs)
+    db = 0.05
+    fd_b = (J(run(sigma0, kap, Wi, beta + db)) - J(base)) / db
+    assert abs(fd_b - base["beta"]) <= 1e-9 * abs(fd_b), (fd_b, base["beta"])
+    hW = 1e-5 * Wi
+    fd_w = (J(run(sigma0, kap, Wi + hW, beta)) - J(run(sigma0, kap, Wi - hW, beta))) / (2 * hW)
+    assert abs(fd_w - base["Wi"]) <= 1e-6 * abs(fd_w), (fd_w, base["Wi"])
+    for c, q in [(0, 0), (dim * dim - 1, N - 1), (1, N // 2)]:
+        hk = 1e-6
+        kp, km = kap.copy(), kap.copy()
+        kp[c, q] += hk
+        km[c, q] -= hk
+        fd_k = (J(run(sigma0, kp, Wi, beta)) - J(run(sigma0, km, Wi, beta))) / (2 * hk)
+        assert abs(fd_k - base["kappa"][c, q]) <= 1e-6 * max(abs(fd_k), 1e-3), (c, q, fd_k, base["kappa"][c, q])
+    f32 = run(sigma0, kap, Wi, beta, prec=1)
+    assert np.max(np.abs(f32["sigma0"] - base["sigma0"])) < 1e-4 * np.max(np.abs(base["sigma0"]))
+    assert abs(f32["Wi"] - base["Wi"]) < 1e-4 * abs(base["Wi"])
