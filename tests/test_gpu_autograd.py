@@ -16,8 +16,8 @@ def _lib():
     ensure_lib()
 
 
-@pytest.mark.parametrize("transport", [False, True])
-def test_autograd_matches_central_differences(transport):
+@pytest.mark.parametrize("transport,start", [(False, "bdf2"), (True, "bdf2"), (False, "sdirk2")])
+def test_autograd_matches_central_differences(transport, start):
     import torch
     from paper_2411_17294_gb300.autograd import fractional_stress
     dim, n, alpha, dt, steps, K, m = 2, (8, 8), 0.5, 2e-3, 30, 7, 8
@@ -28,7 +28,7 @@ def test_autograd_matches_central_differences(transport):
     s0_np = inputs.random_stress(dim, n, 32)
     target = torch.as_tensor(np.random.default_rng(33).normal(size=s0_np.shape), device=dev)
     kw = dict(dim=dim, n=n, alpha=alpha, dt=dt, steps=steps, K=K, mu=mu, w=w,
-              u=torch.as_tensor(u_np, device=dev) if transport else None)
+              u=torch.as_tensor(u_np, device=dev) if transport else None, start=start)
 
     def J(s0, k, Wi, beta):
         sT = fractional_stress(s0, k, Wi, beta, **kw)
