@@ -253,10 +253,13 @@ bool limits_violated(tfs_ctx* h) {
 
 // implicit transport: 10 Krylov vectors [nc][N] plus the point blocks and the
 // preconditioner inverses [nc*nc][N], all FP64
-size_t krylov_bytes(const tfs_ctx* h) {
-    // (the paper's variable keeps h, one more vector, after the preconditioner blocks)
-    return (10 + 2 * (size_t)h->nc + (h->paper() ? 1 : 0)) * (size_t)h->nc * (size_t)h->N * sizeof(double);
+size_t krylov_bytes_for(const tfs_ctx* h, int form) {
+    // 10 vectors, the point blocks and their inverses, 4 stencil coefficients per
+    // axis, and (the paper's variable) h
+    return ((10 + 2 * (size_t)h->nc + (form == TFS_FORM_PAPER ? 1 : 0)) * (size_t)h->nc + 4 * (size_t)h->dim) *
+           (size_t)h->N * sizeof(double);
 }
+size_t krylov_bytes(const tfs_ctx* h) { return krylov_bytes_for(h, h->form); }
 size_t forward_bytes_for(const tfs_ctx* h, int transport, int form);
 
 void layout_forward(tfs_ctx* h, char* base) {
@@ -294,11 +297,7 @@ void layout_forward(tfs_ctx* h, char* base) {
 size_t forward_bytes_for(const tfs_ctx* h, int transport, int form) {
     size_t b = kAlign + 5 * align_up(h->field_bytes()) + 2 * align_up(h->modes_bytes());
     if (form == TFS_FORM_PAPER) b += 2 * align_up(h->field_bytes());
-    if (transport == 2) {
-        const size_t kb = (10 + 2 * (size_t)h->nc + (form == TFS_FORM_PAPER ? 1 : 0)) * (size_t)h->nc * (size_t)h->N *
-                          sizeof(double);
-        b += align_up(kb) + align_up(sizeof(double) * (2 * kImpBlocks + 32));
-    }
+    if (transport == 2) b += align_up(krylov_bytes_for(h, form)) + align_up(sizeof(double) * (2 * kImpBlocks + 32));
     return b;
 }
 

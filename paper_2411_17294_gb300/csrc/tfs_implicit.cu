@@ -90,11 +90,17 @@ __global__ void __launch_bounds__(kThreads) imp_rhs_kernel(const ImpArgs<T> A, d
     }
 }
 
-// Per step: the point blocks M_p = a I - dt L(kappa*_p) and the inverses of
-// the preconditioner blocks P_p = M_p + dt (diagonal of the transport stencil) I,
-// stored [nc*nc][N] (entry r*nc + k of point p at (r*nc + k) N + p).
+// Per step: the point blocks P_p = M_p + dt c0_p I, M_p = a I - dt L(kappa*_p),
+// c0_p the centre coefficient of the transport stencil at p (sum over the axes),
+// and their inverses (the block-Jacobi preconditioner), stored [nc*nc][N]
+// (entry r*nc + k of point p at (r*nc + k) N + p); and the four off-centre tap
+// coefficients of every axis times dt, Cf[(a*4 + t) N + p] for the taps -2, -1,
+// +1, +2 (the stencils of deriv_at, upwinded on the sign of u_a(p), and eps Lap).
+// The operator is then Op(x)_p = P_p x_p + sum_a sum_t Cf x_{p + tap}, the same
+// for every Krylov iteration of the step.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kThreads) imp_setup_kernel(const ImpArgs<T> A, double* Mb, double* Pinv) {
+__global__ void __launch_bounds__(kThreads) imp_setup_kernel(const ImpArgs<T> A, double* Mb, double* Pinv,
+                                                             double* Cf) {
     constexpr int NC = Packed<DIM>::NC;
     const long long N = A.N;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
@@ -109,12 +115,30 @@ __global__ void __launch_bounds__(kThreads) imp_setup_kernel(const ImpArgs<T> A,
         double M[NC][NC];
         assemble_M<DIM>(K, A.a, A.dt, M);
         double diag = 0.0;
+        constexpr double kSixth = 1.0 / 6.0;
 #pragma unroll
         for (int ax = 0; ax < DIM; ++ax) {
             const double ua = (double)A.u[(long long)ax * N + p];
-            if (A.stencil == 0) diag += fabs(ua) * 0.5 * A.inv_h[ax];
-            diag += 2.0 * A.eps * A.inv_h[ax] * A.inv_h[ax];
+            const double ih = A.inv_h[ax];
+            const double e = A.eps * ih * ih;
+            if (A.stencil == 0) diag += fabs(ua) * 0.5 * ih;
+            diag += 2.0 * e;
+            double c[4];   // taps -2, -1, +1, +2
+            if (A.stencil == 1) {
+                const double h2 = 0.5 * ua * ih;
+                c[0] = 0.0; c[1] = -h2 - e; c[2] = h2 - e; c[3] = 0.0;
+            } else if (ua >= 0.0) {
+                const double s6 = ua * ih * kSixth;
+                c[0] = s6; c[1] = -6.0 * s6 - e; c[2] = 2.0 * s6 - e; c[3] = 0.0;
+            } else {
+                const double s6 = ua * ih * kSixth;
+                c[0] = 0.0; c[1] = -2.0 * s6 - e; c[2] = 6.0 * s6 - e; c[3] = -s6;
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) Cf[(long long)(ax * 4 + t) * N + p] = A.dt * c[t];
         }
+#pragma unroll
+        for (int r = 0; r < NC; ++r) M[r][r] += A.dt * diag;
         bool ok = true;
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
@@ -122,7 +146,7 @@ __global__ void __launch_bounds__(kThreads) imp_setup_kernel(const ImpArgs<T> A,
 #pragma unroll
             for (int r = 0; r < NC; ++r) {
 #pragma unroll
-                for (int c = 0; c < NC; ++c) P[r][c] = M[r][c] + (r == c ? A.dt * diag : 0.0);
+                for (int c = 0; c < NC; ++c) P[r][c] = M[r][c];
                 col[r] = r == k ? 1.0 : 0.0;
             }
             ok = gauss_pp<NC>(P, col, 1e-300) && ok;
@@ -174,85 +198,62 @@ __device__ __forceinline__ void block_partials(double a0, double a1, int nsets, 
     }
 }
 
-// Periodic neighbour offsets of point p along every axis (taps -2..2, index k + 2)
-// and the transport stencil's coefficient of each tap at p: sum_a u_a D_a f -
-// eps Lap f = sum_a sum_k cf[a][k] f[p + off[a][k]], with D_a the stencils of
-// deriv_at (upwinded on the sign of u_a(p)).  Computed once per point for all
-// components; the grid index fits 32 bits here (an implicit-transport workspace
-// for 2^31 points would not fit any device).
-template <typename T, int DIM>
-__device__ __forceinline__ void point_stencil(const ImpArgs<T>& A, long long p, long long off[3][5], double cf[3][5]) {
-    const unsigned n0 = (unsigned)A.n0, n1 = (unsigned)A.n1, n2 = (unsigned)A.n2;
-    const unsigned pp = (unsigned)p;
-    const unsigned q1 = pp / n0;
-    const unsigned c[3] = {pp - q1 * n0, q1 % n1, q1 / n1};
-    const unsigned len[3] = {n0, n1, n2};
-    const long long str[3] = {1, (long long)n0, (long long)n0 * n1};
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-#pragma unroll
-        for (int k = -2; k <= 2; ++k) {
-            int v = (int)c[a] + k;
-            const int L = (int)len[a];
-            if (v < 0) v += L;
-            if (v < 0) v += L;
-            if (v >= L) v -= L;
-            if (v >= L) v -= L;
-            off[a][k + 2] = ((long long)v - (long long)c[a]) * str[a];
-        }
-        const double ua = (double)A.u[(long long)a * A.N + p];
-        const double ih = A.inv_h[a];
-        const double e = A.eps * ih * ih;
-        if (A.stencil == 1) {
-            const double s = 0.5 * ua * ih;
-            cf[a][0] = 0.0; cf[a][1] = -s - e; cf[a][2] = 2.0 * e; cf[a][3] = s - e; cf[a][4] = 0.0;
-        } else if (ua >= 0.0) {
-            const double s = ua * ih / 6.0;
-            cf[a][0] = s; cf[a][1] = -6.0 * s - e; cf[a][2] = 3.0 * s + 2.0 * e; cf[a][3] = 2.0 * s - e; cf[a][4] = 0.0;
-        } else {
-            const double s = ua * ih / 6.0;
-            cf[a][0] = 0.0; cf[a][1] = -2.0 * s - e; cf[a][2] = -3.0 * s + 2.0 * e; cf[a][3] = 6.0 * s - e; cf[a][4] = -s;
-        }
-    }
-}
-
-// y = Op(x); partial sums of (w0, y) and (w1, y) when w0 / w1 are given (w1 may be
-// y itself: the (t, t) product)
+// y = Op(x) = P_p x_p + sum_a sum_t Cf x_{p + tap} with the per-step blocks and
+// coefficients of imp_setup_kernel; partial sums of (w0, y) and (w1, y) when
+// w0 / w1 are given (w1 may be y itself: the (t, t) product).  The periodic
+// neighbour offsets are 32-bit (an implicit-transport workspace for 2^31 points
+// would not fit any device).
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads) imp_apply_kernel(const ImpArgs<T> A, const double* __restrict__ Mb,
+                                                             const double* __restrict__ Cf,
                                                              const double* __restrict__ x, double* y,
                                                              const double* w0, const double* w1, double* partials,
                                                              const double* sc) {
     constexpr int NC = Packed<DIM>::NC;
     if (done(sc)) return;
     const long long N = A.N;
+    const int n0 = A.n0, n1 = A.n1, n2 = A.n2;
     double a0 = 0.0, a1 = 0.0;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-        long long off[3][5];
-        double cf[3][5];
-        point_stencil<T, DIM>(A, p, off, cf);
+        const unsigned pp = (unsigned)p;
+        const unsigned q1 = pp / (unsigned)n0;
+        const int c[3] = {(int)(pp - q1 * (unsigned)n0), (int)(q1 % (unsigned)n1), (int)(q1 / (unsigned)n1)};
+        const int len[3] = {n0, n1, n2};
+        const int str[3] = {1, n0, n0 * n1};
+        int off[3][4];
+        double cf[3][4];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int k = t < 2 ? t - 2 : t - 1;
+                int v = c[a] + k;
+                if (v < 0) v += len[a];
+                if (v < 0) v += len[a];
+                if (v >= len[a]) v -= len[a];
+                if (v >= len[a]) v -= len[a];
+                off[a][t] = (v - c[a]) * str[a];
+                cf[a][t] = Cf[(long long)(a * 4 + t) * N + p];
+            }
+        }
         double xp[NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) xp[c] = x[(long long)c * N + p];
+        for (int k = 0; k < NC; ++k) xp[k] = x[(long long)k * N + p];
 #pragma unroll
         for (int r = 0; r < NC; ++r) {
             double acc = 0.0;
 #pragma unroll
             for (int k = 0; k < NC; ++k) acc = fma(Mb[(long long)(r * NC + k) * N + p], xp[k], acc);
             const double* f = x + (long long)r * N + p;
-            double t = 0.0;
 #pragma unroll
-            for (int a = 0; a < DIM; ++a) {
-                t = fma(cf[a][2], xp[r], t);
+            for (int a = 0; a < DIM; ++a)
 #pragma unroll
-                for (int k = 0; k < 5; ++k)
-                    if (k != 2 && cf[a][k] != 0.0) t = fma(cf[a][k], f[off[a][k]], t);
-            }
+                for (int t = 0; t < 4; ++t)
+                    if (cf[a][t] != 0.0) acc = fma(cf[a][t], f[off[a][t]], acc);
             const long long q = (long long)r * N + p;
-            const double yv = fma(A.dt, t, acc);
-            y[q] = yv;
-            if (w0) a0 = fma(w0[q], yv, a0);
-            if (w1) a1 = fma(w1[q], yv, a1);
+            y[q] = acc;
+            if (w0) a0 = fma(w0[q], acc, a0);
+            if (w1) a1 = fma(w1[q], acc, a1);
         }
     }
     if (w0) block_partials(a0, a1, w1 ? 2 : 1, partials);
@@ -617,13 +618,15 @@ __global__ void __launch_bounds__(kThreads) start_push_kernel(const ImpArgs<T> A
 // preconditioner inverses, partial sums, device scalars)
 template <int NC>
 struct KryView {
-    double *b, *x, *r, *rh, *p, *v, *sv, *t, *ph, *sh, *Mb, *Pinv, *partials, *sc;
+    double *b, *x, *r, *rh, *p, *v, *sv, *t, *ph, *sh, *Mb, *Pinv, *Cf, *H, *partials, *sc;
     KryView(double* w, double* parts, long long N) {
         const long long n = (long long)NC * N;
         b = w; x = w + n; r = w + 2 * n; rh = w + 3 * n; p = w + 4 * n; v = w + 5 * n; sv = w + 6 * n;
         t = w + 7 * n; ph = w + 8 * n; sh = w + 9 * n;
         Mb = w + 10 * n;
         Pinv = Mb + (long long)NC * NC * N;
+        Cf = Pinv + (long long)NC * NC * N;                  // 4 taps x dim axes
+        H = Cf + 4LL * (NC == 3 ? 2 : 3) * N;                 // the paper's variable only
         partials = parts;
         sc = parts + kPartialSets * kImpBlocks;
     }
@@ -666,7 +669,7 @@ cudaError_t krylov_solve(const ImpArgs<T>& a, const KryView<Packed<DIM>::NC>& K,
         hs[S_RR] = 0.0;
         hs[S_ITERS] = 0.0;
     } else {
-        imp_apply_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.x, K.r, nullptr, nullptr, partials, sc);
+        imp_apply_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Cf, K.x, K.r, nullptr, nullptr, partials, sc);
         if (!ok()) return e;
         imp_init_kernel<<<bs, kThreads, 0, st>>>(n, K.b, K.r, K.rh, K.p, K.v);
         if (!ok()) return e;
@@ -679,10 +682,10 @@ cudaError_t krylov_solve(const ImpArgs<T>& a, const KryView<Packed<DIM>::NC>& K,
         for (int it = 0; it < a.maxit; ++it) {
             imp_beta_kernel<<<1, 1, 0, st>>>(sc);
             imp_comb_precond_kernel<NC><<<bs, kThreads, 0, st>>>(N, K.Pinv, 0, K.p, K.r, K.v, K.ph, sc);
-            imp_apply_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.ph, K.v, K.rh, nullptr, partials, sc);
+            imp_apply_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Cf, K.ph, K.v, K.rh, nullptr, partials, sc);
             imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 1);
             imp_comb_precond_kernel<NC><<<bs, kThreads, 0, st>>>(N, K.Pinv, 1, K.sv, K.r, K.v, K.sh, sc);
-            imp_apply_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.sh, K.t, K.sv, K.t, partials, sc);
+            imp_apply_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Cf, K.sh, K.t, K.sv, K.t, partials, sc);
             imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 2);
             imp_xr_kernel<<<bs, kThreads, 0, st>>>(n, K.x, K.ph, K.sh, K.r, K.sv, K.t, K.rh, partials, sc);
             imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 0);
@@ -719,8 +722,8 @@ cudaError_t run_implicit(const ImpArgs<T>& a, cudaStream_t st, int* iters, doubl
     const KryView<NC> K(a.kry, a.partials, a.N);
     const unsigned bs = (unsigned)kImpBlocks;
     // the paper's variable keeps h after the preconditioner blocks
-    double* H = K.Pinv + (long long)NC * NC * a.N;
-    imp_setup_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Pinv);
+    double* H = K.H;
+    imp_setup_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Pinv, K.Cf);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (a.paper) {
@@ -846,11 +849,11 @@ cudaError_t run_start_implicit(const ImpArgs<T>& a, const StartConsts& c, cudaSt
     constexpr int NC = Packed<DIM>::NC;
     const KryView<NC> K(a.kry, a.partials, a.N);
     const unsigned bs = (unsigned)kImpBlocks;
-    imp_setup_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Pinv);
+    imp_setup_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Pinv, K.Cf);
     cudaError_t e = cudaGetLastError();
     *iters = 0;
     *relres = 0.0;
-    double* H = K.Pinv + (long long)NC * NC * a.N;     // the paper's variable: h of the stage
+    double* H = K.H;     // the paper's variable: h of the stage
     for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage) {
         // stage 1 reads the level-0 modes and starts from sigma^0; stage 2 reads the
         // explicit part written by the first push and starts from S1 (left in x)
