@@ -126,7 +126,13 @@ class Solver:
 
     Owns a handle and a torch-allocated workspace; fields are torch tensors of
     the precision's dtype, shaped [nc, N] (stress), [d*d, N] (velocity
-    gradient) and [d, N] (velocity)."""
+    gradient) and [d, N] (velocity).
+
+    transport: False (pointwise law), True (explicit, extrapolated) or
+    "implicit" (inside a Krylov solve, eq. FP_discrete); start: "bdf2" (empty
+    past) or "sdirk2" (Section 5.1); form: "stress" or "paper" (the paper's
+    variable Phi with stress Psi = D^{1-alpha} Phi, Section 3.4; the SOE table
+    then approximates g_alpha, i.e. the kernel of order 1 - alpha)."""
 
     def __init__(self, dim: int, n, alpha: float, Wi: float, beta: float, dt: float, m: int = 0,
                  precision: int = TFS_FP64, L=None, mu=None, w=None, Re: float = 1.0, eps: float = 0.0,
