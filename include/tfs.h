@@ -111,8 +111,10 @@ enum {
                                  BDF2 on Phi and the modes (Section 4.1), one point system per point.
                                  With transport 1 the operator u.grad - eps Lap acts on the
                                  extrapolation 2 Psi^n - Psi^{n-1}, explicitly, with the stencils of the
-                                 stress form; the Courant check of tfs_transport_limit (derived for the
-                                 stress form) is not applied.  With transport 2 it acts on
+                                 stress form; tfs_transport_limit, the eps and umax checks and the
+                                 Courant flag then use this variable's own bound (the transport acts on
+                                 Psi = V Phi, V the discrete D^{1-alpha}, which makes it far tighter for
+                                 small alpha).  With transport 2 it acts on
                                  Psi^{n+1} = xi Phi^{n+1} + h inside the solve (eq. FP_discrete): the
                                  operator (b0 + dt xi/Wi) I - dt xi L(kappa*) + dt xi (u.grad - eps Lap)
                                  through the same Krylov solver, and one more nc N FP64 vector.  Needs

@@ -94,8 +94,8 @@ struct tfs_ctx {
     size_t modes_bytes() const { return (size_t)m * field_bytes(); }
     int third_sig() const { return 3 - cur_sig - prev_sig; }
     bool explicit_transport() const { return transport == 1; }
-    // the stability bound of the explicit transport is derived for the stress form
-    bool checked_transport() const { return transport == 1 && form == TFS_FORM_STRESS; }
+    // explicit transport: the Courant bound of the form carried applies
+    bool checked_transport() const { return transport == 1; }
     bool implicit_transport() const { return transport == 2; }
     bool paper() const { return form == TFS_FORM_PAPER; }
 };
@@ -121,6 +121,10 @@ double g_alpha(const tfs_ctx* h, long long step_index) {
 // has no zero in the disk, i.e. while the winding number of f(e^{i phi}),
 // 0 <= phi < 2 pi, about 0 vanishes for every theta (argument principle).
 // stability_bound() bisects for the largest such lambda along given directions.
+// In the paper's variable the transport acts on Psi = V(zeta) Phi, V = sum_j w_j
+// delta / (delta + mu_j dt) (the discrete D^{1-alpha} of the mode recursion), and
+// the BDF2 equation on Phi gives f = delta + lambda s V zeta (2 - zeta): the same
+// test with delta in place of W and V zeta (2 - zeta) in place of zeta (2 - zeta).
 struct Cplx {
     double re, im;
 };
@@ -155,6 +159,15 @@ double stability_bound(const tfs_ctx* h, const std::vector<Cplx>& dirs) {
         const Cplx z = cexpi(phis[k]);
         const Cplx delta = cadd(cadd(Cplx{kB0, 0.0}, cmul(Cplx{kB1, 0.0}, z)), cmul(Cplx{kB2, 0.0}, cmul(z, z)));
         Cplx w{0.0, 0.0};
+        const Cplx ext = cmul(z, csub(Cplx{2.0, 0.0}, z));
+        if (h->paper()) {
+            Cplx v{0.0, 0.0};
+            for (int j = 0; j < h->m; ++j)
+                v = cadd(v, cdiv(cmul(Cplx{h->w[j], 0.0}, delta), cadd(delta, Cplx{h->mu[j] * h->dt, 0.0})));
+            W[k] = delta;
+            G[k] = cmul(v, ext);
+            continue;
+        }
         if (h->classic()) {
             w = delta;
         } else {
@@ -163,7 +176,7 @@ double stability_bound(const tfs_ctx* h, const std::vector<Cplx>& dirs) {
             w = cmul(w, delta);
         }
         W[k] = w;
-        G[k] = cmul(z, csub(Cplx{2.0, 0.0}, z));
+        G[k] = ext;
     }
     auto stable = [&](double t) {
         for (const Cplx& sv : dirs) {
@@ -507,7 +520,6 @@ void fill_paper(tfs_ctx* h, FwdArgs<T>& a) {
     a.psi = (T*)h->psi[1 - h->cur_psi];          // Psi^{n+1} over Psi^{n-1}, after the pre-pass has read it
     a.psi_n = (const T*)h->psi[h->cur_psi];
     a.psi_nm1 = (const T*)h->psi[1 - h->cur_psi];
-    a.courant_coef = 0.0;                        // the explicit-transport bound is the stress form's
     a.xi = h->xi_p;
     a.inv_wi = 1.0 / h->Wi;
     a.a = kB0 + h->dt * h->xi_p / h->Wi;
@@ -798,6 +810,7 @@ int tfs_set_param(tfs_handle h, int key, double value) {
             if (h->ws && h->ws_bytes < forward_bytes_for(h, h->transport, (int)value)) return TFS_ERR_NOWORKSPACE;
             if ((int)value != h->form) h->state_set = false;   // the state means something else now
             h->form = (int)value;
+            h->lim_valid = false;                              // the Courant bound depends on the form
             if (h->ws) layout_forward(h, h->ws);
             return TFS_OK;
         case TFS_PARAM_START:

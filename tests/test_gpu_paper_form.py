@@ -268,7 +268,7 @@ def test_paper_form_refusals():
 TRANSPORT_CASES = [
     # dim, n, alpha, m, stencil, eps   (n0 % 32 == 0 and n1 % 8 == 0: the tiled pre-pass)
     (2, (37, 29), 0.5, 8, 0, 0.0),
-    (2, (64, 16), 0.4, 8, 1, 0.02),
+    (2, (64, 16), 0.4, 8, 1, 0.005),   # inside this variable's explicit diffusion bound
     (3, (9, 7, 5), 0.6, 6, 1, 0.01),
     (3, (32, 8, 5), 0.3, 6, 0, 0.0),
 ]

@@ -168,3 +168,73 @@ def test_explicit_diffusion_bound():
                    for t in th)
     assert rad(0.9 * z_star) <= 1 + 1e-9
     assert rad(1.1 * z_star) > 1 + 1e-6
+
+
+def paper_recurrence(z, mu, w, dt):
+    """One Fourier mode of the scheme in the paper's variable (Phi, the modes
+    phi_j of Phi, Psi = xi Phi + h), the transport z (2 Psi^n - Psi^{n-1})
+    explicit, no relaxation: state (Phi^n, Phi^{n-1}, Psi^n, Psi^{n-1}, phi^n,
+    phi^{n-1})."""
+    m = len(mu)
+    c = 1 / (B0 + mu * dt)
+    xi = B0 * np.sum(w * c)
+    D = 4 + 2 * m
+    T = np.zeros((D, D), complex)
+    # Phi^{n+1} = (-b1 Phi^n - b2 Phi^{n-1} - z (2 Psi^n - Psi^{n-1})) / b0
+    phi_row = np.zeros(D, complex)
+    phi_row[0], phi_row[1] = -B1 / B0, -B2 / B0
+    phi_row[2], phi_row[3] = -2 * z / B0, z / B0
+    T[0] = phi_row
+    T[1, 0] = 1
+    # h^n = sum_j w_j mu_j c_j (b1 phi_j^n + b2 phi_j^{n-1});  Psi^{n+1} = xi Phi^{n+1} + h^n
+    T[2] = xi * phi_row
+    T[2, 4:4 + m] += w * mu * c * B1
+    T[2, 4 + m:] += w * mu * c * B2
+    T[3, 2] = 1
+    for j in range(m):
+        T[4 + j] = c[j] * dt * phi_row
+        T[4 + j, 4 + j] += -c[j] * B1
+        T[4 + j, 4 + m + j] += -c[j] * B2
+        T[4 + m + j, 4 + j] = 1
+    return T
+
+
+def paper_library_lambda(stencil, alpha, dt, m, soe_tab):
+    ensure_lib()
+    from paper_2411_17294_gb300 import tfs
+    lib = tfs.load_library()
+    g = tfs.TfsGrid()
+    g.dim = 2
+    for a in range(3):
+        g.n[a] = 64 if a < 2 else 1
+        g.L[a] = 2 * math.pi
+    h = ctypes.c_void_p()
+    assert lib.tfs_create(ctypes.byref(h), ctypes.byref(g), alpha, 1.0, 0.5, m, dt, 1) == 0
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_STENCIL, float(stencil)) == 0
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_FORM, float(tfs.TFS_FORM_PAPER)) == 0
+    dp = ctypes.POINTER(ctypes.c_double)
+    mu, w = [np.ascontiguousarray(a) for a in soe_tab]
+    assert lib.tfs_set_soe(h, mu.ctypes.data_as(dp), w.ctypes.data_as(dp), m) == 0
+    U = ctypes.c_double(0)
+    assert lib.tfs_transport_limit(h, ctypes.byref(U)) == 0
+    lam_lib = dt * U.value * 64 / (2 * math.pi)
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_UMAX, U.value * 0.999) == 0
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_UMAX, U.value * 1.001) == tfs.TFS_ERR_UNSTABLE
+    lib.tfs_destroy(h)
+    return 2 * lam_lib / 0.9
+
+
+@pytest.mark.parametrize("alpha,m", [(0.3, 8), (0.5, 12), (0.8, 8)])
+def test_paper_variable_limit_matches_eigenvalue_scan(alpha, m):
+    # The Courant bound of the explicit transport in the paper's variable (the
+    # transport acts on Psi = V(zeta) Phi) against the spectral radius of its
+    # one-mode recurrence: stable at 0.9 lambda*, unstable just beyond lambda*.
+    dt = 2e-4
+    tab = soe.soe_nnls(1 - alpha, dt, 200 * dt, m)
+    lam_star = paper_library_lambda(0, alpha, dt, m, tab)
+    th = np.linspace(0, 2 * np.pi, 361)[1:]
+    rad = lambda lam: max(np.max(np.abs(np.linalg.eigvals(paper_recurrence(lam * symbol(t, 0), *tab, dt))))
+                          for t in th)
+    assert rad(0.9 * lam_star) <= 1 + 1e-9
+    assert rad(0.995 * lam_star) <= 1 + 1e-6
+    assert rad(1.05 * lam_star) > 1 + 1e-6
