@@ -448,6 +448,8 @@ def main():
                     help="time only the adjoint workload in one precision and print its record (profiling)")
     ap.add_argument("--paper-only", action="store_true",
                     help="time only the step in the paper's variable and print its record (profiling)")
+    ap.add_argument("--implicit-only", action="store_true",
+                    help="time only the implicit-transport step and print its record (profiling)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32plain"])
     ap.add_argument("--grid", type=int, default=WORKLOAD["n"][0],
                     help="cube side of the step workload (default 256; smaller sides are for profiling)")
@@ -471,6 +473,13 @@ def main():
         print(json.dumps(adjoint_ratio(torch.device("cuda", 0), prec)), flush=True)
         return
 
+    if args.implicit_only:
+        import torch
+        from paper_2411_17294_gb300 import build as tbuild
+        tbuild.build()
+        torch.cuda.set_device(0)
+        print(json.dumps(implicit_transport_record(torch.device("cuda", 0))), flush=True)
+        return
     if args.paper_only:
         import torch
         from paper_2411_17294_gb300 import build as tbuild
