@@ -119,8 +119,8 @@ enum {
                                  operator (b0 + dt xi/Wi) I - dt xi L(kappa*) + dt xi (u.grad - eps Lap)
                                  through the same Krylov solver, and one more nc N FP64 vector.  Needs
                                  alpha < 1 (else TFS_ERR_ARG here); either start (SDIRK2 with transport
-                                 0 or 2, else tfs_step returns TFS_ERR_ARG); tfs_backward refuses it
-                                 (TFS_ERR_ARG).  The workspace grows by 2 nc N elements (Psi^n, Psi^{n-1});
+                                 0 or 2, else tfs_step returns TFS_ERR_ARG); tfs_backward takes it
+                                 with transport 0 and the BDF2 start (else TFS_ERR_ARG).  The workspace grows by 2 nc N elements (Psi^n, Psi^{n-1});
                                  with a workspace bound, a form it does not fit returns TFS_ERR_NOWORKSPACE.
                                  Changing the form discards the state (call tfs_set_state again) */
 };
@@ -250,7 +250,8 @@ int tfs_bind_adjoint_workspace(tfs_handle h, void* dev_ptr, size_t bytes);
    and then differentiated backwards.  Outputs (device, double): dJ_dsigma0
    [nc][N], dJ_dgrad_u [d*d][N]; host doubles *dJ_dWi, *dJ_dbeta.  Synchronises
    `stream` at the end to return the two scalars.  The handle's forward state
-   afterwards is that of the last recomputed segment. */
+   afterwards is that of the last recomputed segment.  With TFS_FORM_PAPER,
+   J is a function of Psi(T) and dJ_dsigma0 is the derivative in Phi(0). */
 int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* checkpoints, int K,
                  int steps, const void* grad_u, const void* u, double* dJ_dsigma0,
                  double* dJ_dgrad_u, double* dJ_dWi, double* dJ_dbeta, void* stream);

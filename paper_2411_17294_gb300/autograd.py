@@ -26,7 +26,7 @@ class TFSFunction(torch.autograd.Function):
         s = tfs.Solver(dim, n, alpha, float(Wi), float(beta), dt, m=0 if alpha == 1.0 else len(mu),
                        precision=precision, mu=mu, w=w, transport=transport, eps=cfg.get("eps", 0.0),
                        stencil=cfg.get("stencil", tfs.TFS_STENCIL_UPWIND3), L=cfg.get("L"), Re=cfg.get("Re", 1.0),
-                       device=grad_u.device, start=cfg.get("start", "bdf2"))
+                       device=grad_u.device, start=cfg.get("start", "bdf2"), form=cfg.get("form", "stress"))
         kt = grad_u.detach().to(s.dtype).reshape(dim * dim, -1).contiguous()
         ut = u.detach().to(s.dtype).reshape(dim, -1).contiguous() if transport else None
         s.set_state(sigma0.detach())
@@ -59,12 +59,15 @@ class TFSFunction(torch.autograd.Function):
 
 def fractional_stress(sigma0, grad_u, Wi, beta, *, dim, n, alpha, dt, steps, K=50, mu=None, w=None, u=None,
                       precision=tfs.TFS_FP64, transport=None, eps=0.0, stencil=tfs.TFS_STENCIL_UPWIND3, L=None,
-                      Re=1.0, start="bdf2"):
+                      Re=1.0, start="bdf2", form="stress"):
     """sigma(T) after `steps` steps from sigma0 [nc, N] with the frozen velocity
     gradient grad_u [d*d, N] (and velocity u [d, N] when transport is on);
     differentiable in sigma0, grad_u, Wi and beta (0-d tensors).  start:
-    "bdf2" (empty past) or "sdirk2" (the paper's first step; pointwise law)."""
+    "bdf2" (empty past) or "sdirk2" (the paper's first step; pointwise law).
+    form="paper": the paper's variable (Section 3.4; sigma0 is Phi(0), the
+    result Psi(T), mu/w the SOE of the kernel of order 1 - alpha; pointwise
+    law, BDF2 start)."""
     cfg = dict(dim=dim, n=tuple(n), alpha=alpha, dt=dt, steps=int(steps), K=int(K), mu=mu, w=w,
                precision=precision, transport=(u is not None) if transport is None else transport, eps=eps,
-               stencil=stencil, L=L, Re=Re, start=start)
+               stencil=stencil, L=L, Re=Re, start=start, form=form)
     return TFSFunction.apply(sigma0, grad_u, Wi, beta, u, cfg)

@@ -1,0 +1,39 @@
+// Declarations of the adjoint of the paper's variable (tfs_adjoint_paper.cu),
+// kept apart from the step kernel's shared header.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "tfs_internal.h"
+
+namespace tfs {
+
+// Adjoint of one BDF2 step in the paper's variable (pointwise law).  psi is the
+// step's output Psi^{n+1}; lam_psi the adjoint of Psi at the final step (else
+// nullptr); s1 / s0 the adjoints of Phi^{n+1} and (partial) of Phi^n, s1_out /
+// s0_out those of Phi^n and (partial) Phi^{n-1}; the mode adjoint ring as in the
+// stress form (lamQ written over ell_prev2).  mc / mcf: c_j, dt c_j, w_j mu_j c_j.
+template <typename T>
+struct PaperAdjArgs {
+    const T* kap;
+    const T* psi;
+    const double* lam_psi;
+    const double* s1;
+    const double* s0;
+    const T* ell_prev;
+    T* ell_prev2;
+    double* s1_out;
+    double* s0_out;
+    double* g_kap;
+    double* partials;
+    unsigned* flags;
+    long long N;
+    int m;
+    double dt, a, xi, G, psi0, Wi, Re;
+    ModeConstsD mc;
+    ModeConstsF mcf;
+};
+cudaError_t launch_paper_adjoint_f64(const PaperAdjArgs<double>& a, int dim, cudaStream_t s);
+cudaError_t launch_paper_adjoint_f32(const PaperAdjArgs<float>& a, int dim, cudaStream_t s);
+
+}  // namespace tfs

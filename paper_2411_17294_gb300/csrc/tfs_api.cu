@@ -13,6 +13,7 @@
 
 #include "../../include/tfs.h"
 #include "tfs_internal.h"
+#include "tfs_adjoint_paper.h"
 
 using namespace tfs;
 
@@ -1086,6 +1087,56 @@ AdjLayout adj_layout(const tfs_ctx* h) {
     return L;
 }
 
+// One reverse step of the paper's variable (pointwise law, BDF2): psi is the
+// step's Psi^{n+1}, lam_psi the adjoint of Psi at the final step (else null),
+// psi0 the step's Psi0^{n+1}.
+extern "C++" template <typename T>
+cudaError_t paper_adjoint_step(const tfs_ctx* h, const AdjLayout& L, int cur, int ell_prev, const void* grad_u,
+                               const void* psi, const double* lam_psi, double psi0, double* g_kap, cudaStream_t s) {
+    const int nxt = 1 - cur;
+    PaperAdjArgs<T> a{};
+    a.kap = (const T*)grad_u;
+    a.psi = (const T*)psi;
+    a.lam_psi = lam_psi;
+    a.s1 = L.s[2 * cur];
+    a.s0 = L.s[2 * cur + 1];
+    a.ell_prev = (const T*)L.ell[ell_prev];
+    a.ell_prev2 = (T*)L.ell[1 - ell_prev];
+    a.s1_out = L.s[2 * nxt];
+    a.s0_out = L.s[2 * nxt + 1];
+    a.g_kap = g_kap;
+    a.partials = L.partials;
+    a.flags = h->flags;
+    a.N = h->N;
+    a.m = h->m;
+    a.dt = h->dt;
+    a.a = kB0 + h->dt * h->xi_p / h->Wi;
+    a.xi = h->xi_p;
+    a.G = (1.0 - h->beta) / (h->Wi * h->Re);
+    a.psi0 = psi0;
+    a.Wi = h->Wi;
+    a.Re = h->Re;
+    a.mc = h->mcd_p;
+    a.mcf = h->mcf_p;
+    if constexpr (sizeof(T) == 8) return launch_paper_adjoint_f64(a, h->dim, s);
+    else return launch_paper_adjoint_f32(a, h->dim, s);
+}
+
+// Psi0^{n+1} of steps 0 .. steps-1 (BDF2 from the start), leaving the host
+// modes of Phi0 as they were.
+std::vector<double> paper_psi0_sequence(tfs_ctx* h, int steps) {
+    const std::vector<double> keep_n = h->phi0_n, keep_nm1 = h->phi0_nm1;
+    paper_reset_phi0(h, 0);
+    std::vector<double> out((size_t)steps);
+    for (int k = 0; k < steps; ++k) {
+        out[(size_t)k] = paper_psi0(h);
+        paper_advance_phi0(h);
+    }
+    h->phi0_n = keep_n;
+    h->phi0_nm1 = keep_nm1;
+    return out;
+}
+
 }  // namespace
 
 size_t tfs_adjoint_workspace_bytes(tfs_handle h, int segment_steps) {
@@ -1110,7 +1161,8 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
     if (valid_handle(h) && h->implicit_transport()) return TFS_ERR_ARG;   // adjoint of the implicit step not built
     // the SDIRK2 first step's adjoint is built for the pointwise law
     if (valid_handle(h) && h->start == TFS_START_SDIRK2 && h->transport != 0) return TFS_ERR_ARG;
-    if (valid_handle(h) && h->paper()) return TFS_ERR_ARG;                     // nor of the paper's variable
+    // the paper's variable: the pointwise law with the BDF2 start
+    if (valid_handle(h) && h->paper() && (h->transport != 0 || h->start == TFS_START_SDIRK2)) return TFS_ERR_ARG;
     if (!valid_handle(h) || !dJ_dsigma_T || !checkpoints || !grad_u || !dJ_dsigma0 || !dJ_dgrad_u || !dJ_dWi ||
         !dJ_dbeta)
         return TFS_ERR_ARG;
@@ -1129,9 +1181,13 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
     if (e == cudaSuccess) e = launch_zero(dJ_dgrad_u, (size_t)h->dim * h->dim * h->N * 8, s);
     if (e == cudaSuccess) e = launch_zero(L.partials, (size_t)blocks * 16, s);
     for (int i = 0; i < 2 && e == cudaSuccess && h->modes_bytes() > 0; ++i) e = launch_zero(L.ell[i], h->modes_bytes(), s);
-    if (e == cudaSuccess) e = launch_to_double(dJ_dsigma_T, L.s[0], ncN, h->is_double(), s);
+    // J = <dJ, sigma^T>, or in the paper's variable <dJ, Psi^T> (held in lamR, the
+    // adjoint of Phi^T then starts at 0)
+    if (e == cudaSuccess) e = launch_to_double(dJ_dsigma_T, h->paper() ? L.lamR : L.s[0], ncN, h->is_double(), s);
+    if (e == cudaSuccess && h->paper()) e = launch_zero(L.s[0], dfield, s);
     if (e == cudaSuccess) e = launch_zero(L.s[1], dfield, s);
     if (e != cudaSuccess) return TFS_ERR_CUDA;
+    const std::vector<double> psi0s = h->paper() ? paper_psi0_sequence(h, steps) : std::vector<double>();
     int cur = 0;        // s[2*cur] = s1, s[2*cur+1] = s0
     int ell_prev = 0;   // slot of lamQ of the later step; the other slot holds the one before
     const LaunchCfg cfg = make_cfg(h);
@@ -1149,6 +1205,17 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
         for (int n = end - 1; n >= start; --n) {
             const void* sig_np1 = L.seg + (size_t)(n - start) * L.seg_stride;
             const int nxt = 1 - cur;
+            if (h->paper()) {
+                const double* lam_psi = (n == steps - 1) ? L.lamR : nullptr;
+                e = h->is_double() ? paper_adjoint_step<double>(h, L, cur, ell_prev, grad_u, sig_np1, lam_psi,
+                                                                psi0s[(size_t)n], dJ_dgrad_u, s)
+                                   : paper_adjoint_step<float>(h, L, cur, ell_prev, grad_u, sig_np1, lam_psi,
+                                                               psi0s[(size_t)n], dJ_dgrad_u, s);
+                if (e != cudaSuccess) return TFS_ERR_CUDA;
+                cur = nxt;
+                ell_prev = 1 - ell_prev;
+                continue;
+            }
             if (n == 0 && h->start == TFS_START_SDIRK2) {
                 const StartConsts c = start_consts(h);
                 const double a_stage = h->dt * c.W + h->dt / h->Wi;
