@@ -120,7 +120,7 @@ enum {
                                  through the same Krylov solver, and one more nc N FP64 vector.  Needs
                                  alpha < 1 (else TFS_ERR_ARG here); either start (SDIRK2 with transport
                                  0 or 2, else tfs_step returns TFS_ERR_ARG); tfs_backward takes it
-                                 with transport 0 and the BDF2 start (else TFS_ERR_ARG).  The workspace grows by 2 nc N elements (Psi^n, Psi^{n-1});
+                                 with transport 0 or 1 and the BDF2 start (else TFS_ERR_ARG).  The workspace grows by 2 nc N elements (Psi^n, Psi^{n-1});
                                  with a workspace bound, a form it does not fit returns TFS_ERR_NOWORKSPACE.
                                  Changing the form discards the state (call tfs_set_state again) */
 };

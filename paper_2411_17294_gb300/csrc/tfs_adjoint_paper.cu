@@ -70,7 +70,11 @@ __global__ void __launch_bounds__(kThreads) paper_adjoint_kernel(const PaperAdjA
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             const long long q = (long long)c * N + p;
-            const double l = A.lam_psi ? A.lam_psi[q] : 0.0;
+            const double l = A.t1 ? A.t1[q] : A.lam_psi ? A.lam_psi[q] : 0.0;
+            if (A.t1) {
+                A.t1_out[q] = A.t0[q];
+                A.t0_out[q] = 0.0;
+            }
             lp[c] = (R)l;
             psi[c] = (R)A.psi[q];
             lamd[c] = A.s1[q] + A.xi * l;
@@ -181,6 +185,7 @@ __global__ void __launch_bounds__(kThreads) paper_adjoint_kernel(const PaperAdjA
             const long long q = (long long)c * N + p;
             A.s1_out[q] = A.s0[q] - kB1 * (double)lam[c];
             A.s0_out[q] = -kB2 * (double)lam[c];
+            if (A.lamR_out) A.lamR_out[q] = (double)lam[c];
         }
         // parameter derivatives (the stress form's with sigma^{n+1} -> Psi^{n+1})
         R S3[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};

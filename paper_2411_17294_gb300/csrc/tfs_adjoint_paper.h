@@ -13,6 +13,10 @@ namespace tfs {
 // nullptr); s1 / s0 the adjoints of Phi^{n+1} and (partial) of Phi^n, s1_out /
 // s0_out those of Phi^n and (partial) Phi^{n-1}; the mode adjoint ring as in the
 // stress form (lamQ written over ell_prev2).  mc / mcf: c_j, dt c_j, w_j mu_j c_j.
+// With explicit transport (acting on 2 Psi^n - Psi^{n-1}) the adjoint of Psi has
+// a ring too: t1 the full adjoint of Psi^{n+1} (it then replaces lam_psi), t0
+// the partial one of Psi^n; the kernel sets t1_out = t0, t0_out = 0 and writes
+// lamR to lamR_out, and the transposed stencil adds its terms to t1_out, t0_out.
 template <typename T>
 struct PaperAdjArgs {
     const T* kap;
@@ -25,6 +29,11 @@ struct PaperAdjArgs {
     double* s1_out;
     double* s0_out;
     double* g_kap;
+    const double* t1;
+    const double* t0;
+    double* t1_out;
+    double* t0_out;
+    double* lamR_out;
     double* partials;
     unsigned* flags;
     long long N;

@@ -1048,6 +1048,7 @@ namespace {
 
 struct AdjLayout {
     double* s[4];       // two ping-pong pairs (s1, s0)
+    double* t[4];       // the paper's variable with transport: the same for the adjoint of Psi
     double* lamR;
     char* ell[2];
     double* partials;   // 2 per block
@@ -1056,10 +1057,12 @@ struct AdjLayout {
     size_t seg_stride;
 };
 
+bool paper_psi_ring(const tfs_ctx* h) { return h->paper() && h->transport == 1; }
+
 size_t adj_bytes(const tfs_ctx* h, int seg_steps) {
     const size_t dfield = (size_t)h->nc * (size_t)h->N * 8;
     const long long blocks = (h->N + 31) / 32;
-    return 5 * align_up(dfield) + 2 * align_up(h->modes_bytes()) + align_up((size_t)blocks * 16) + kAlign +
+    return (paper_psi_ring(h) ? 9 : 5) * align_up(dfield) + 2 * align_up(h->modes_bytes()) + align_up((size_t)blocks * 16) + kAlign +
            (size_t)seg_steps * align_up(h->field_bytes());
 }
 
@@ -1074,6 +1077,13 @@ AdjLayout adj_layout(const tfs_ctx* h) {
     }
     L.lamR = (double*)p;
     p += align_up(dfield);
+    for (int i = 0; i < 4; ++i) {
+        L.t[i] = nullptr;
+        if (paper_psi_ring(h)) {
+            L.t[i] = (double*)p;
+            p += align_up(dfield);
+        }
+    }
     for (int i = 0; i < 2; ++i) {
         L.ell[i] = p;
         p += align_up(h->modes_bytes());
@@ -1087,12 +1097,14 @@ AdjLayout adj_layout(const tfs_ctx* h) {
     return L;
 }
 
-// One reverse step of the paper's variable (pointwise law, BDF2): psi is the
-// step's Psi^{n+1}, lam_psi the adjoint of Psi at the final step (else null),
-// psi0 the step's Psi0^{n+1}.
+// One reverse step of the paper's variable (BDF2; pointwise law or explicit
+// transport): psi is the step's Psi^{n+1}, lam_psi the adjoint of Psi at the
+// final step (else null; with transport the Psi ring carries it), psi0 the
+// step's Psi0^{n+1}.
 extern "C++" template <typename T>
 cudaError_t paper_adjoint_step(const tfs_ctx* h, const AdjLayout& L, int cur, int ell_prev, const void* grad_u,
-                               const void* psi, const double* lam_psi, double psi0, double* g_kap, cudaStream_t s) {
+                               const void* u, const void* psi, const double* lam_psi, double psi0, double* g_kap,
+                               cudaStream_t s) {
     const int nxt = 1 - cur;
     PaperAdjArgs<T> a{};
     a.kap = (const T*)grad_u;
@@ -1105,6 +1117,13 @@ cudaError_t paper_adjoint_step(const tfs_ctx* h, const AdjLayout& L, int cur, in
     a.s1_out = L.s[2 * nxt];
     a.s0_out = L.s[2 * nxt + 1];
     a.g_kap = g_kap;
+    if (paper_psi_ring(h)) {
+        a.t1 = L.t[2 * cur];
+        a.t0 = L.t[2 * cur + 1];
+        a.t1_out = L.t[2 * nxt];
+        a.t0_out = L.t[2 * nxt + 1];
+        a.lamR_out = L.lamR;
+    }
     a.partials = L.partials;
     a.flags = h->flags;
     a.N = h->N;
@@ -1118,8 +1137,23 @@ cudaError_t paper_adjoint_step(const tfs_ctx* h, const AdjLayout& L, int cur, in
     a.Re = h->Re;
     a.mc = h->mcd_p;
     a.mcf = h->mcf_p;
-    if constexpr (sizeof(T) == 8) return launch_paper_adjoint_f64(a, h->dim, s);
-    else return launch_paper_adjoint_f32(a, h->dim, s);
+    cudaError_t e;
+    if constexpr (sizeof(T) == 8) e = launch_paper_adjoint_f64(a, h->dim, s);
+    else e = launch_paper_adjoint_f32(a, h->dim, s);
+    if (e != cudaSuccess || !paper_psi_ring(h)) return e;
+    // the transposed stencil of -dt (u.grad - eps Lap)(2 Psi^n - Psi^{n-1})
+    AdjArgs<double> ad{};
+    ad.N = h->N;
+    ad.n0 = (int)h->n[0];
+    ad.n1 = (int)h->n[1];
+    ad.n2 = (int)h->n[2];
+    ad.dt = h->dt;
+    ad.eps = h->eps;
+    for (int i = 0; i < 3; ++i) ad.inv_h[i] = (double)h->n[i] / h->L[i];
+    ad.lamR = L.lamR;
+    ad.s1_out = L.t[2 * nxt];
+    ad.s0_out = L.t[2 * nxt + 1];
+    return launch_adjoint_transport(ad, u, sizeof(T) == 8, make_cfg(h), s);
 }
 
 // Psi0^{n+1} of steps 0 .. steps-1 (BDF2 from the start), leaving the host
@@ -1161,15 +1195,15 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
     if (valid_handle(h) && h->implicit_transport()) return TFS_ERR_ARG;   // adjoint of the implicit step not built
     // the SDIRK2 first step's adjoint is built for the pointwise law
     if (valid_handle(h) && h->start == TFS_START_SDIRK2 && h->transport != 0) return TFS_ERR_ARG;
-    // the paper's variable: the pointwise law with the BDF2 start
-    if (valid_handle(h) && h->paper() && (h->transport != 0 || h->start == TFS_START_SDIRK2)) return TFS_ERR_ARG;
+    // the paper's variable: the BDF2 start (implicit transport is refused above)
+    if (valid_handle(h) && h->paper() && h->start == TFS_START_SDIRK2) return TFS_ERR_ARG;
     if (!valid_handle(h) || !dJ_dsigma_T || !checkpoints || !grad_u || !dJ_dsigma0 || !dJ_dgrad_u || !dJ_dWi ||
         !dJ_dbeta)
         return TFS_ERR_ARG;
     if (K < 1 || steps < 1) return TFS_ERR_ARG;
     if (h->transport && !u) return TFS_ERR_ARG;
     if (!h->ws || !h->aws) return TFS_ERR_NOWORKSPACE;
-    if (K > h->seg_capacity) return TFS_ERR_NOWORKSPACE;
+    if (h->aws_bytes < adj_bytes(h, K)) return TFS_ERR_NOWORKSPACE;   // also after a change of form
     if (!h->classic() && !h->soe_set) return TFS_ERR_NOSOE;
     cudaStream_t s = (cudaStream_t)stream;
     AdjLayout L = adj_layout(h);
@@ -1183,8 +1217,10 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
     for (int i = 0; i < 2 && e == cudaSuccess && h->modes_bytes() > 0; ++i) e = launch_zero(L.ell[i], h->modes_bytes(), s);
     // J = <dJ, sigma^T>, or in the paper's variable <dJ, Psi^T> (held in lamR, the
     // adjoint of Phi^T then starts at 0)
-    if (e == cudaSuccess) e = launch_to_double(dJ_dsigma_T, h->paper() ? L.lamR : L.s[0], ncN, h->is_double(), s);
+    double* dJ_into = h->paper() ? (paper_psi_ring(h) ? L.t[0] : L.lamR) : L.s[0];
+    if (e == cudaSuccess) e = launch_to_double(dJ_dsigma_T, dJ_into, ncN, h->is_double(), s);
     if (e == cudaSuccess && h->paper()) e = launch_zero(L.s[0], dfield, s);
+    if (e == cudaSuccess && paper_psi_ring(h)) e = launch_zero(L.t[1], dfield, s);
     if (e == cudaSuccess) e = launch_zero(L.s[1], dfield, s);
     if (e != cudaSuccess) return TFS_ERR_CUDA;
     const std::vector<double> psi0s = h->paper() ? paper_psi0_sequence(h, steps) : std::vector<double>();
@@ -1206,10 +1242,10 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
             const void* sig_np1 = L.seg + (size_t)(n - start) * L.seg_stride;
             const int nxt = 1 - cur;
             if (h->paper()) {
-                const double* lam_psi = (n == steps - 1) ? L.lamR : nullptr;
-                e = h->is_double() ? paper_adjoint_step<double>(h, L, cur, ell_prev, grad_u, sig_np1, lam_psi,
+                const double* lam_psi = (n == steps - 1 && !paper_psi_ring(h)) ? L.lamR : nullptr;
+                e = h->is_double() ? paper_adjoint_step<double>(h, L, cur, ell_prev, grad_u, u, sig_np1, lam_psi,
                                                                 psi0s[(size_t)n], dJ_dgrad_u, s)
-                                   : paper_adjoint_step<float>(h, L, cur, ell_prev, grad_u, sig_np1, lam_psi,
+                                   : paper_adjoint_step<float>(h, L, cur, ell_prev, grad_u, u, sig_np1, lam_psi,
                                                                psi0s[(size_t)n], dJ_dgrad_u, s);
                 if (e != cudaSuccess) return TFS_ERR_CUDA;
                 cur = nxt;

@@ -1,15 +1,17 @@
 """The adjoint of the paper's own variable (TFS_FORM_PAPER, Section 3.4;
-pointwise law, BDF2 start) through tfs_backward: J = <dJ, Psi(T)>.
+BDF2 start; pointwise law or explicit transport) through tfs_backward:
+J = <dJ, Psi(T)>.
 
 1. Against FP64 central differences of the oracle's scheme in that variable
    (oracle.paper_form.PaperForm), in random directions of Phi(0) (exact: Psi(T)
    is affine in Phi(0)) and of the velocity gradient, and in Wi and beta;
-   several checkpoint segments, 2D and 3D, FP64 and FP32 storage.
+   several checkpoint segments, 2D and 3D, both stencils, with and without
+   diffusion, FP64 and FP32 storage.
 2. torch.autograd (fractional_stress(form="paper")) against central
    differences of the CUDA forward, 1e-6 relative.
 3. A 2D 256^2, m = 32, 200-step run (checkpoint every 50) against central
    differences of the CUDA forward at sampled entries, 1e-6 relative.
-4. Refusals: transport and the SDIRK2 start in this variable.
+4. Refusals: implicit transport and the SDIRK2 start in this variable.
 
 Tolerances: FP64 1e-6 relative to the largest entry of each gradient (the
 central differences carry O(h^2) truncation, h = 1e-5); FP32 storage 5e-4
@@ -32,20 +34,21 @@ def _lib():
     ensure_lib()
 
 
-def oracle_J(dim, n, Wi, beta, dt, mu, w, P0, kap, steps, dJ):
+def oracle_J(dim, n, Wi, beta, dt, mu, w, P0, kap, steps, dJ, u=None, eps=0.0, stencil=0):
     N = int(np.prod(n))
-    pf = PaperForm(dim, N, Wi, beta, dt, mu, w, Phi0=P0)
+    pf = PaperForm(dim, N, Wi, beta, dt, mu, w, Phi0=P0, grid=n, eps=eps, stencil=stencil)
     for _ in range(steps):
-        psi = pf.step(kap, kap)
+        psi = pf.step(kap, kap, u)
     return float(np.sum(dJ * psi))
 
 
-def gpu_grads(dim, n, alpha, Wi, beta, dt, mu, w, P0, kap, steps, K, dJ, precision):
+def gpu_grads(dim, n, alpha, Wi, beta, dt, mu, w, P0, kap, steps, K, dJ, precision, u=None, eps=0.0, stencil=0):
     import torch
     from paper_2411_17294_gb300 import tfs
-    s = tfs.Solver(dim, n, alpha, Wi, beta, dt, m=len(mu), precision=precision, mu=mu, w=w, transport=False,
-                   form="paper")
+    s = tfs.Solver(dim, n, alpha, Wi, beta, dt, m=len(mu), precision=precision, mu=mu, w=w,
+                   transport=u is not None, eps=eps, stencil=stencil, form="paper")
     kt = torch.as_tensor(kap, dtype=s.dtype, device=s.device).contiguous()
+    ut = None if u is None else torch.as_tensor(u, dtype=s.dtype, device=s.device).contiguous()
     s.set_state(torch.as_tensor(P0, dtype=s.dtype, device=s.device))
     ckpts = []
     for k in range(steps):
@@ -53,8 +56,8 @@ def gpu_grads(dim, n, alpha, Wi, beta, dt, mu, w, P0, kap, steps, K, dJ, precisi
             c = s.new_checkpoint()
             s.save(c)
             ckpts.append(c)
-        s.step(kt, kt, None)
-    g_p0, g_k, gWi, gb = s.backward(torch.as_tensor(dJ, dtype=s.dtype, device=s.device), ckpts, K, steps, kt, None)
+        s.step(kt, kt, ut)
+    g_p0, g_k, gWi, gb = s.backward(torch.as_tensor(dJ, dtype=s.dtype, device=s.device), ckpts, K, steps, kt, ut)
     flags = s.status()
     s.close()
     assert not (flags & (tfs.TFS_FLAG_NONFINITE | tfs.TFS_FLAG_SINGULAR | tfs.TFS_FLAG_TIMEOUT))
@@ -62,17 +65,21 @@ def gpu_grads(dim, n, alpha, Wi, beta, dt, mu, w, P0, kap, steps, K, dJ, precisi
 
 
 CASES = [
-    # dim, n, alpha, m, steps, K
-    (2, (11, 7), 0.5, 8, 12, 5),
-    (3, (4, 3, 5), 0.3, 12, 9, 4),
-    (2, (40, 1), 0.7, 6, 7, 7),
-    (3, (3, 3, 3), 0.6, 32, 10, 3),
+    # dim, n, alpha, m, steps, K, transport, stencil, eps
+    (2, (11, 7), 0.5, 8, 12, 5, False, 0, 0.0),
+    (3, (4, 3, 5), 0.3, 12, 9, 4, False, 0, 0.0),
+    (2, (40, 1), 0.7, 6, 7, 7, False, 0, 0.0),
+    (3, (3, 3, 3), 0.6, 32, 10, 3, False, 0, 0.0),
+    (2, (12, 10), 0.5, 8, 11, 4, True, 0, 0.0),
+    (2, (16, 9), 0.4, 8, 9, 9, True, 1, 0.005),
+    (3, (5, 4, 6), 0.6, 6, 8, 3, True, 1, 0.01),
+    (3, (4, 5, 3), 0.35, 16, 7, 7, True, 0, 0.0),
 ]
 
 
-@pytest.mark.parametrize("dim,n,alpha,m,steps,K", CASES)
+@pytest.mark.parametrize("dim,n,alpha,m,steps,K,transport,stencil,eps", CASES)
 @pytest.mark.parametrize("precision", [0, 1])
-def test_paper_adjoint_against_oracle_differences(dim, n, alpha, m, steps, K, precision):
+def test_paper_adjoint_against_oracle_differences(dim, n, alpha, m, steps, K, transport, stencil, eps, precision):
     dt, Wi, beta = 4e-3, 1.3, 0.4
     mu, w = soe.soe_nnls(1 - alpha, dt, 50 * dt, m)
     _, kap = inputs.spectral_velocity(dim, n, 2, seed=81)
@@ -80,11 +87,19 @@ def test_paper_adjoint_against_oracle_differences(dim, n, alpha, m, steps, K, pr
     P0 = inputs.random_stress(dim, n, 82)
     rng = np.random.default_rng(83)
     dJ = rng.normal(size=P0.shape)
+    u = 0.3 * np.asarray(inputs.spectral_velocity(dim, n, 2, seed=84)[0]) if transport else None
     if precision == 1:
         cast = lambda a: np.asarray(a, np.float32).astype(np.float64)
         kap, P0, dJ = cast(kap), cast(P0), cast(dJ)
-    g_p0, g_k, gWi, gb = gpu_grads(dim, n, alpha, Wi, beta, dt, mu, w, P0, kap, steps, K, dJ, precision)
-    J = lambda P, k, Wi_, b_: oracle_J(dim, n, Wi_, b_, dt, mu, w, P, k, steps, dJ)
+        u = None if u is None else cast(u)
+    g_p0, g_k, gWi, gb = gpu_grads(dim, n, alpha, Wi, beta, dt, mu, w, P0, kap, steps, K, dJ, precision, u, eps,
+                                   stencil)
+    J = lambda P, k, Wi_, b_: oracle_J(dim, n, Wi_, b_, dt, mu, w, P, k, steps, dJ, u, eps, stencil)
+    if transport:
+        # the transport changes the gradient (else the test would not see its adjoint)
+        Jp = lambda P: oracle_J(dim, n, Wi, beta, dt, mu, w, P, kap, steps, dJ)
+        d = np.random.default_rng(5).normal(size=P0.shape)
+        assert abs((Jp(P0 + d) - Jp(P0 - d)) / 2.0 - float(np.sum(g_p0 * d))) > 1e-3 * np.sum(np.abs(g_p0 * d))
     tol = 1e-6 if precision == 0 else 5e-4
     h = 1e-5
 
@@ -213,7 +228,7 @@ def test_paper_adjoint_256_against_central_differences():
         assert close(g_k[c, q].item(), fd), (c, q, g_k[c, q].item(), fd)
 
 
-@pytest.mark.parametrize("transport,start", [(True, "bdf2"), ("implicit", "bdf2"), (False, "sdirk2")])
+@pytest.mark.parametrize("transport,start", [("implicit", "bdf2"), (False, "sdirk2")])
 def test_paper_adjoint_refusals(transport, start):
     import torch
     from paper_2411_17294_gb300 import tfs
