@@ -99,8 +99,9 @@ enum {
                                  With transport 2 both stage systems go through the implicit solver
                                  (tfs_last_solve: iterations summed, larger residual).  With
                                  TFS_FORM_PAPER the same method on Phi and its modes.  tfs_backward
-                                 differentiates the start with transport 0 (zero initial modes, as
-                                 tfs_set_state leaves them) and refuses it with transport (TFS_ERR_ARG) */
+                                 differentiates the start with transport 0 in either form (zero initial
+                                 modes, as tfs_set_state leaves them) and refuses it with transport
+                                 (TFS_ERR_ARG) */
     TFS_PARAM_FORM = 8        /* variable carried, TFS_FORM_*: the stress (default), or the paper's own
                                  variable (Section 3.4): Phi with d Phi/dt = (L(kappa) - I/Wi) Psi +
                                  G (kappa + kappa^T) Psi0, Psi = D^{1-alpha} Phi by kernel compression of
@@ -120,7 +121,7 @@ enum {
                                  through the same Krylov solver, and one more nc N FP64 vector.  Needs
                                  alpha < 1 (else TFS_ERR_ARG here); either start (SDIRK2 with transport
                                  0 or 2, else tfs_step returns TFS_ERR_ARG); tfs_backward takes it
-                                 with transport 0 or 1 and the BDF2 start (else TFS_ERR_ARG).  The workspace grows by 2 nc N elements (Psi^n, Psi^{n-1});
+                                 with transport 0 (either start) or 1 (BDF2 start), else TFS_ERR_ARG.  The workspace grows by 2 nc N elements (Psi^n, Psi^{n-1});
                                  with a workspace bound, a form it does not fit returns TFS_ERR_NOWORKSPACE.
                                  Changing the form discards the state (call tfs_set_state again) */
 };

@@ -65,8 +65,8 @@ def fractional_stress(sigma0, grad_u, Wi, beta, *, dim, n, alpha, dt, steps, K=5
     differentiable in sigma0, grad_u, Wi and beta (0-d tensors).  start:
     "bdf2" (empty past) or "sdirk2" (the paper's first step; pointwise law).
     form="paper": the paper's variable (Section 3.4; sigma0 is Phi(0), the
-    result Psi(T), mu/w the SOE of the kernel of order 1 - alpha; pointwise
-    law, BDF2 start)."""
+    result Psi(T), mu/w the SOE of the kernel of order 1 - alpha; explicit
+    transport with the BDF2 start, either start without transport)."""
     cfg = dict(dim=dim, n=tuple(n), alpha=alpha, dt=dt, steps=int(steps), K=int(K), mu=mu, w=w,
                precision=precision, transport=(u is not None) if transport is None else transport, eps=eps,
                stencil=stencil, L=L, Re=Re, start=start, form=form)

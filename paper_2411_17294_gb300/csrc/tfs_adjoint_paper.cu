@@ -234,6 +234,181 @@ __global__ void __launch_bounds__(kThreads) paper_adjoint_kernel(const PaperAdjA
     }
 }
 
+// Terms of one implicit stage F = P - Z - s [L(kappa) Y - Y/Wi + G k g] = 0 in
+// the parameters, given its adjoint lamr: dJ/dkappa += s (dL/dkappa)^T(lamr, Y) +
+// s G g sym(lamr), dJ/dWi += s/Wi^2 <lamr, Y> - (G/Wi) s g <lamr, k>,
+// dJ/dbeta += -s g <lamr, k>/(Wi Re)  (G = (1 - beta)/(Wi Re), k = kappa + kappa^T).
+template <int DIM>
+__device__ __forceinline__ void stage_param_terms(const double K[3][3], const double* lamr, const double* Y,
+                                                  double sc, double G, double g, double Wi, double Re,
+                                                  double gK[3][3], double& gWi, double& gbeta) {
+    constexpr int NC = Packed<DIM>::NC;
+    double Y3[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+    for (int r = 0; r < NC; ++r) {
+        const int i = Packed<DIM>::I(r), j = Packed<DIM>::J(r);
+        Y3[i][j] = Y[r];
+        Y3[j][i] = Y[r];
+    }
+    double sym_dot = 0.0, y_dot = 0.0;
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) {
+        const int r = Packed<DIM>::I(cc), s2 = Packed<DIM>::J(cc);
+        const double l = lamr[cc];
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) {
+            gK[r][b] += sc * l * Y3[b][s2];
+            gK[s2][b] += sc * l * Y3[r][b];
+        }
+        gK[r][s2] += sc * G * g * l;
+        gK[s2][r] += sc * G * g * l;
+        sym_dot += l * (K[r][s2] + K[s2][r]);
+        y_dot += l * Y[cc];
+    }
+    const double lam_G = sc * g * sym_dot;
+    gWi += sc / (Wi * Wi) * y_dot - G / Wi * lam_G;
+    gbeta += -lam_G / (Wi * Re);
+}
+
+// Adjoint of the SDIRK2 first step in the paper's variable for zero initial
+// modes, one thread per point, FP64.  With phi_j^0 = 0 (iota_j = 1/(1 + gamma
+// mu_j dt), W = sum_j w_j iota_j, S = sum_j w_j mu_j iota_j^2, gd = gamma dt,
+// f1 = (1 - gamma) dt, M = a I - gd W L(kappa)) the forward reads
+//   P1 = M^-1 (P0 + gd G k g0)                          (stage 1: h = 0)
+//   h2 = f1 S P1,  zP = P0 + (f1/gd)(P1 - P0)
+//   P2 = M^-1 (zP - gd (L h2 - h2/Wi) + gd G k g1)     (stage 2)
+//   phi_j^1 = iota_j (f1 iota_j P1 + gd P2),  Phi^1 = P2,  Psi^1 = W P2 - h2
+// Since a P - gd W L P = P + gd (W P/Wi - L W P), each stage is
+// P - Z - gd [L Y - Y/Wi + G k g] = 0 with Y = W P1 (stage 1) and Y = Psi^1
+// (stage 2).  Reverse, z_j the adjoint of phi_j^1:
+//   lamP2 = s1 + W lamPsi + gd sum_j iota_j z_j,  lamr2 = M^-T lamP2
+//   lamh2 = -lamPsi - gd (L^T lamr2 - lamr2/Wi)
+//   lamP1 = f1 sum_j iota_j^2 z_j + f1 S lamh2 + (f1/gd) lamr2,  lamr1 = M^-T lamP1
+//   adjoint of Phi^0 = s0 + lamr1 + (1 - f1/gd) lamr2
+// and the stage terms of stage_param_terms with (lamr1, W P1, g0), (lamr2, Psi^1, g1).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) paper_start_adjoint_kernel(const PaperStartAdjArgs<T> A,
+                                                                       const StartConsts C) {
+    constexpr int NC = Packed<DIM>::NC;
+    const long long N = A.N;
+    const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+    double gWi = 0.0, gbeta = 0.0;
+    if (p < N) {
+        const double gd = C.gam * A.dt, f1 = (1.0 - C.gam) * A.dt;
+        double S = 0.0;
+        for (int jj = 0; jj < A.m; ++jj) S += C.w[jj] * C.mu[jj] * C.inv_den[jj] * C.inv_den[jj];
+        double K[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+        for (int i = 0; i < DIM; ++i)
+#pragma unroll
+            for (int j = 0; j < DIM; ++j) K[i][j] = (double)A.kap0[(long long)(i * DIM + j) * N + p];
+        double M0[NC][NC], M[NC][NC];
+        assemble_M<DIM>(K, A.a, gd * C.W, M0);
+        double P0[NC], src[NC], P1[NC], P2[NC], h2[NC], Y1[NC], Psi1[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int i = Packed<DIM>::I(c), j = Packed<DIM>::J(c);
+            P0[c] = A.sigma0 ? (double)A.sigma0[(long long)c * N + p] : 0.0;
+            src[c] = A.G * (K[i][j] + K[j][i]);
+            P1[c] = P0[c] + gd * src[c] * C.g[0];
+        }
+        // forward, recomputed
+#pragma unroll
+        for (int r = 0; r < NC; ++r)
+#pragma unroll
+            for (int k = 0; k < NC; ++k) M[r][k] = M0[r][k];
+        bool ok = gauss_pp<NC>(M, P1, 1e-300);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) h2[c] = f1 * S * P1[c];
+#pragma unroll
+        for (int r = 0; r < NC; ++r) {
+            double Lh = -h2[r] / A.Wi;
+#pragma unroll
+            for (int k = 0; k < NC; ++k) Lh = fma(uc_entry<DIM>(K, r, k), h2[k], Lh);
+            P2[r] = P0[r] + (f1 / gd) * (P1[r] - P0[r]) - gd * Lh + gd * src[r] * C.g[1];
+        }
+#pragma unroll
+        for (int r = 0; r < NC; ++r)
+#pragma unroll
+            for (int k = 0; k < NC; ++k) M[r][k] = M0[r][k];
+        ok = gauss_pp<NC>(M, P2, 1e-300) && ok;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            Y1[c] = C.W * P1[c];
+            Psi1[c] = C.W * P2[c] - h2[c];
+        }
+        // reverse
+        double lamP2[NC], lamP1[NC], lamPsi[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const long long q = (long long)c * N + p;
+            lamPsi[c] = A.lam_psi ? A.lam_psi[q] : 0.0;
+            double a2 = 0.0, a1 = 0.0;
+            for (int jj = 0; jj < A.m; ++jj) {
+                const long long qm = ((long long)jj * NC + c) * N + p;
+                const double z = kB1 * (double)A.ell_prev[qm] + kB2 * (double)A.ell_prev2[qm];
+                a2 = fma(C.inv_den[jj], z, a2);
+                a1 = fma(C.inv_den[jj] * C.inv_den[jj], z, a1);
+            }
+            lamP2[c] = A.s1[q] + C.W * lamPsi[c] + gd * a2;
+            lamP1[c] = f1 * a1;
+        }
+        double Mt[NC][NC];
+#pragma unroll
+        for (int r = 0; r < NC; ++r)
+#pragma unroll
+            for (int k = 0; k < NC; ++k) Mt[r][k] = M0[k][r];
+        ok = gauss_pp<NC>(Mt, lamP2, 1e-300) && ok;          // lamP2 = lamr2
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            double lt = -lamP2[k] / A.Wi;
+#pragma unroll
+            for (int r = 0; r < NC; ++r) lt = fma(uc_entry<DIM>(K, r, k), lamP2[r], lt);
+            const double lamh2 = -lamPsi[k] - gd * lt;
+            lamP1[k] += f1 * S * lamh2 + (f1 / gd) * lamP2[k];
+        }
+#pragma unroll
+        for (int r = 0; r < NC; ++r)
+#pragma unroll
+            for (int k = 0; k < NC; ++k) Mt[r][k] = M0[k][r];
+        ok = gauss_pp<NC>(Mt, lamP1, 1e-300) && ok;          // lamP1 = lamr1
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const long long q = (long long)c * N + p;
+            A.s1_out[q] = A.s0[q] + lamP1[c] + (1.0 - f1 / gd) * lamP2[c];
+            A.s0_out[q] = 0.0;
+        }
+        double gK[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        stage_param_terms<DIM>(K, lamP1, Y1, gd, A.G, C.g[0], A.Wi, A.Re, gK, gWi, gbeta);
+        stage_param_terms<DIM>(K, lamP2, Psi1, gd, A.G, C.g[1], A.Wi, A.Re, gK, gWi, gbeta);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a)
+#pragma unroll
+            for (int b = 0; b < DIM; ++b) A.g_kap[(long long)(a * DIM + b) * N + p] += gK[a][b];
+        if (!ok) atomicOr(A.flags, 2u);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        gWi += __shfl_xor_sync(0xffffffffu, gWi, off);
+        gbeta += __shfl_xor_sync(0xffffffffu, gbeta, off);
+    }
+    const long long grp = p >> 5;
+    if ((threadIdx.x & 31) == 0 && grp * 32 < N) {
+        A.partials[2 * grp + 0] += gWi;
+        A.partials[2 * grp + 1] += gbeta;
+    }
+}
+
+template <typename T>
+cudaError_t launch_start(const PaperStartAdjArgs<T>& a, const StartConsts& c, int dim, cudaStream_t s) {
+    const long long blocks = (a.N + kThreads - 1) / kThreads;
+    if (blocks < 1 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (a.m < 0 || a.m > kMaxModes) return cudaErrorInvalidValue;
+    if (dim == 2) paper_start_adjoint_kernel<T, 2><<<(unsigned)blocks, kThreads, 0, s>>>(a, c);
+    else paper_start_adjoint_kernel<T, 3><<<(unsigned)blocks, kThreads, 0, s>>>(a, c);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch(const PaperAdjArgs<T>& a, int dim, cudaStream_t s) {
     const long long blocks = (a.N + kThreads - 1) / kThreads;
@@ -251,6 +426,16 @@ cudaError_t launch(const PaperAdjArgs<T>& a, int dim, cudaStream_t s) {
 }
 
 }  // namespace
+
+cudaError_t launch_paper_start_adjoint_f64(const PaperStartAdjArgs<double>& a, const StartConsts& c, int dim,
+                                           cudaStream_t s) {
+    return launch_start(a, c, dim, s);
+}
+
+cudaError_t launch_paper_start_adjoint_f32(const PaperStartAdjArgs<float>& a, const StartConsts& c, int dim,
+                                           cudaStream_t s) {
+    return launch_start(a, c, dim, s);
+}
 
 cudaError_t launch_paper_adjoint_f64(const PaperAdjArgs<double>& a, int dim, cudaStream_t s) {
     return launch(a, dim, s);

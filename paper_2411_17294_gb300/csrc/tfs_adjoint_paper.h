@@ -42,6 +42,34 @@ struct PaperAdjArgs {
     ModeConstsD mc;
     ModeConstsF mcf;
 };
+// Adjoint of the SDIRK2 first step in the paper's variable (pointwise law, zero
+// initial modes): sigma0 is Phi(0) (nullptr: 0), lam_psi the adjoint of Psi^1
+// when the run has one step (else nullptr), s1 / s0 the adjoints of Phi^1 and
+// (partial) of Phi^0, ell_prev / ell_prev2 the two later levels of the mode
+// adjoint ring; s1_out receives the whole adjoint of Phi^0 and s0_out 0.
+// a = 1 + gamma dt W/Wi.
+template <typename T>
+struct PaperStartAdjArgs {
+    const T* kap0;
+    const T* sigma0;
+    const double* lam_psi;
+    const double* s1;
+    const double* s0;
+    const T* ell_prev;
+    const T* ell_prev2;
+    double* s1_out;
+    double* s0_out;
+    double* g_kap;
+    double* partials;
+    unsigned* flags;
+    long long N;
+    int m;
+    double dt, a, G, Wi, Re;
+};
+cudaError_t launch_paper_start_adjoint_f64(const PaperStartAdjArgs<double>& a, const StartConsts& c, int dim,
+                                           cudaStream_t s);
+cudaError_t launch_paper_start_adjoint_f32(const PaperStartAdjArgs<float>& a, const StartConsts& c, int dim,
+                                           cudaStream_t s);
 cudaError_t launch_paper_adjoint_f64(const PaperAdjArgs<double>& a, int dim, cudaStream_t s);
 cudaError_t launch_paper_adjoint_f32(const PaperAdjArgs<float>& a, int dim, cudaStream_t s);
 

@@ -1156,13 +1156,20 @@ cudaError_t paper_adjoint_step(const tfs_ctx* h, const AdjLayout& L, int cur, in
     return launch_adjoint_transport(ad, u, sizeof(T) == 8, make_cfg(h), s);
 }
 
-// Psi0^{n+1} of steps 0 .. steps-1 (BDF2 from the start), leaving the host
-// modes of Phi0 as they were.
-std::vector<double> paper_psi0_sequence(tfs_ctx* h, int steps) {
+// Psi0^{n+1} of steps 0 .. steps-1 (with the SDIRK2 start: Psi0 at its two
+// stage times in stage[2], out[0] unused), leaving the host modes of Phi0 as
+// they were.
+std::vector<double> paper_psi0_sequence(tfs_ctx* h, int steps, double stage[2]) {
     const std::vector<double> keep_n = h->phi0_n, keep_nm1 = h->phi0_nm1;
     paper_reset_phi0(h, 0);
     std::vector<double> out((size_t)steps);
+    stage[0] = stage[1] = 0.0;
     for (int k = 0; k < steps; ++k) {
+        if (k == 0 && h->start == TFS_START_SDIRK2) {
+            paper_sdirk2_phi0(h, stage);
+            out[0] = 0.0;
+            continue;
+        }
         out[(size_t)k] = paper_psi0(h);
         paper_advance_phi0(h);
     }
@@ -1195,8 +1202,6 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
     if (valid_handle(h) && h->implicit_transport()) return TFS_ERR_ARG;   // adjoint of the implicit step not built
     // the SDIRK2 first step's adjoint is built for the pointwise law
     if (valid_handle(h) && h->start == TFS_START_SDIRK2 && h->transport != 0) return TFS_ERR_ARG;
-    // the paper's variable: the BDF2 start (implicit transport is refused above)
-    if (valid_handle(h) && h->paper() && h->start == TFS_START_SDIRK2) return TFS_ERR_ARG;
     if (!valid_handle(h) || !dJ_dsigma_T || !checkpoints || !grad_u || !dJ_dsigma0 || !dJ_dgrad_u || !dJ_dWi ||
         !dJ_dbeta)
         return TFS_ERR_ARG;
@@ -1223,7 +1228,8 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
     if (e == cudaSuccess && paper_psi_ring(h)) e = launch_zero(L.t[1], dfield, s);
     if (e == cudaSuccess) e = launch_zero(L.s[1], dfield, s);
     if (e != cudaSuccess) return TFS_ERR_CUDA;
-    const std::vector<double> psi0s = h->paper() ? paper_psi0_sequence(h, steps) : std::vector<double>();
+    double psi0_stage[2] = {0.0, 0.0};
+    const std::vector<double> psi0s = h->paper() ? paper_psi0_sequence(h, steps, psi0_stage) : std::vector<double>();
     int cur = 0;        // s[2*cur] = s1, s[2*cur+1] = s0
     int ell_prev = 0;   // slot of lamQ of the later step; the other slot holds the one before
     const LaunchCfg cfg = make_cfg(h);
@@ -1241,6 +1247,35 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
         for (int n = end - 1; n >= start; --n) {
             const void* sig_np1 = L.seg + (size_t)(n - start) * L.seg_stride;
             const int nxt = 1 - cur;
+            if (h->paper() && n == 0 && h->start == TFS_START_SDIRK2) {
+                // pointwise law (SDIRK2 refuses explicit transport, the adjoint implicit transport)
+                StartConsts c = start_consts(h);
+                c.g[0] = psi0_stage[0];
+                c.g[1] = psi0_stage[1];
+                const double a_p = 1.0 + h->dt * c.gam * c.W / h->Wi;
+                const double G = (1.0 - h->beta) / (h->Wi * h->Re);
+                const double* lam_psi = (steps == 1) ? L.lamR : nullptr;
+                if (h->is_double()) {
+                    PaperStartAdjArgs<double> a{(const double*)grad_u,
+                                                h->sigma0_zero ? nullptr : (const double*)h->sigma0, lam_psi,
+                                                L.s[2 * cur], L.s[2 * cur + 1], (const double*)L.ell[ell_prev],
+                                                (const double*)L.ell[1 - ell_prev], L.s[2 * nxt], L.s[2 * nxt + 1],
+                                                dJ_dgrad_u, L.partials, h->flags, h->N, h->m, h->dt, a_p, G, h->Wi,
+                                                h->Re};
+                    e = launch_paper_start_adjoint_f64(a, c, h->dim, s);
+                } else {
+                    PaperStartAdjArgs<float> a{(const float*)grad_u,
+                                               h->sigma0_zero ? nullptr : (const float*)h->sigma0, lam_psi,
+                                               L.s[2 * cur], L.s[2 * cur + 1], (const float*)L.ell[ell_prev],
+                                               (const float*)L.ell[1 - ell_prev], L.s[2 * nxt], L.s[2 * nxt + 1],
+                                               dJ_dgrad_u, L.partials, h->flags, h->N, h->m, h->dt, a_p, G, h->Wi,
+                                               h->Re};
+                    e = launch_paper_start_adjoint_f32(a, c, h->dim, s);
+                }
+                if (e != cudaSuccess) return TFS_ERR_CUDA;
+                cur = nxt;
+                continue;
+            }
             if (h->paper()) {
                 const double* lam_psi = (n == steps - 1 && !paper_psi_ring(h)) ? L.lamR : nullptr;
                 e = h->is_double() ? paper_adjoint_step<double>(h, L, cur, ell_prev, grad_u, u, sig_np1, lam_psi,

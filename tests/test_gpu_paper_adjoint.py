@@ -1,6 +1,6 @@
 """The adjoint of the paper's own variable (TFS_FORM_PAPER, Section 3.4;
-BDF2 start; pointwise law or explicit transport) through tfs_backward:
-J = <dJ, Psi(T)>.
+BDF2 start with the pointwise law or explicit transport, SDIRK2 start with the
+pointwise law) through tfs_backward: J = <dJ, Psi(T)>.
 
 1. Against FP64 central differences of the oracle's scheme in that variable
    (oracle.paper_form.PaperForm), in random directions of Phi(0) (exact: Psi(T)
@@ -11,7 +11,9 @@ J = <dJ, Psi(T)>.
    differences of the CUDA forward, 1e-6 relative.
 3. A 2D 256^2, m = 32, 200-step run (checkpoint every 50) against central
    differences of the CUDA forward at sampled entries, 1e-6 relative.
-4. Refusals: implicit transport and the SDIRK2 start in this variable.
+4. The SDIRK2 first step (Section 5.1) in this variable: one step alone (the
+   adjoint of Psi^1 enters the start's adjoint) and followed by BDF2 steps.
+5. Refusal: implicit transport in this variable.
 
 Tolerances: FP64 1e-6 relative to the largest entry of each gradient (the
 central differences carry O(h^2) truncation, h = 1e-5); FP32 storage 5e-4
@@ -34,19 +36,20 @@ def _lib():
     ensure_lib()
 
 
-def oracle_J(dim, n, Wi, beta, dt, mu, w, P0, kap, steps, dJ, u=None, eps=0.0, stencil=0):
+def oracle_J(dim, n, Wi, beta, dt, mu, w, P0, kap, steps, dJ, u=None, eps=0.0, stencil=0, start="bdf2"):
     N = int(np.prod(n))
-    pf = PaperForm(dim, N, Wi, beta, dt, mu, w, Phi0=P0, grid=n, eps=eps, stencil=stencil)
+    pf = PaperForm(dim, N, Wi, beta, dt, mu, w, Phi0=P0, grid=n, eps=eps, stencil=stencil, start=start)
     for _ in range(steps):
         psi = pf.step(kap, kap, u)
     return float(np.sum(dJ * psi))
 
 
-def gpu_grads(dim, n, alpha, Wi, beta, dt, mu, w, P0, kap, steps, K, dJ, precision, u=None, eps=0.0, stencil=0):
+def gpu_grads(dim, n, alpha, Wi, beta, dt, mu, w, P0, kap, steps, K, dJ, precision, u=None, eps=0.0, stencil=0,
+              start="bdf2"):
     import torch
     from paper_2411_17294_gb300 import tfs
     s = tfs.Solver(dim, n, alpha, Wi, beta, dt, m=len(mu), precision=precision, mu=mu, w=w,
-                   transport=u is not None, eps=eps, stencil=stencil, form="paper")
+                   transport=u is not None, eps=eps, stencil=stencil, form="paper", start=start)
     kt = torch.as_tensor(kap, dtype=s.dtype, device=s.device).contiguous()
     ut = None if u is None else torch.as_tensor(u, dtype=s.dtype, device=s.device).contiguous()
     s.set_state(torch.as_tensor(P0, dtype=s.dtype, device=s.device))
@@ -75,11 +78,19 @@ CASES = [
     (3, (5, 4, 6), 0.6, 6, 8, 3, True, 1, 0.01),
     (3, (4, 5, 3), 0.35, 16, 7, 7, True, 0, 0.0),
 ]
+SDIRK2_CASES = [
+    (2, (11, 7), 0.5, 8, 1, 1, False, 0, 0.0),
+    (2, (9, 6), 0.3, 12, 8, 3, False, 0, 0.0),
+    (3, (4, 3, 5), 0.7, 6, 6, 6, False, 0, 0.0),
+    (3, (3, 3, 3), 0.45, 32, 2, 1, False, 0, 0.0),
+]
 
 
-@pytest.mark.parametrize("dim,n,alpha,m,steps,K,transport,stencil,eps", CASES)
+@pytest.mark.parametrize("dim,n,alpha,m,steps,K,transport,stencil,eps,start",
+                         [c + ("bdf2",) for c in CASES] + [c + ("sdirk2",) for c in SDIRK2_CASES])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_paper_adjoint_against_oracle_differences(dim, n, alpha, m, steps, K, transport, stencil, eps, precision):
+def test_paper_adjoint_against_oracle_differences(dim, n, alpha, m, steps, K, transport, stencil, eps, start,
+                                                  precision):
     dt, Wi, beta = 4e-3, 1.3, 0.4
     mu, w = soe.soe_nnls(1 - alpha, dt, 50 * dt, m)
     _, kap = inputs.spectral_velocity(dim, n, 2, seed=81)
@@ -93,8 +104,13 @@ def test_paper_adjoint_against_oracle_differences(dim, n, alpha, m, steps, K, tr
         kap, P0, dJ = cast(kap), cast(P0), cast(dJ)
         u = None if u is None else cast(u)
     g_p0, g_k, gWi, gb = gpu_grads(dim, n, alpha, Wi, beta, dt, mu, w, P0, kap, steps, K, dJ, precision, u, eps,
-                                   stencil)
-    J = lambda P, k, Wi_, b_: oracle_J(dim, n, Wi_, b_, dt, mu, w, P, k, steps, dJ, u, eps, stencil)
+                                   stencil, start)
+    J = lambda P, k, Wi_, b_: oracle_J(dim, n, Wi_, b_, dt, mu, w, P, k, steps, dJ, u, eps, stencil, start)
+    if start == "sdirk2":
+        # the start changes the gradient (else the test would not see its adjoint)
+        Jb = lambda P: oracle_J(dim, n, Wi, beta, dt, mu, w, P, kap, steps, dJ)
+        d = np.random.default_rng(6).normal(size=P0.shape)
+        assert abs((Jb(P0 + d) - Jb(P0 - d)) / 2.0 - float(np.sum(g_p0 * d))) > 1e-4 * np.sum(np.abs(g_p0 * d))
     if transport:
         # the transport changes the gradient (else the test would not see its adjoint)
         Jp = lambda P: oracle_J(dim, n, Wi, beta, dt, mu, w, P, kap, steps, dJ)
@@ -228,7 +244,7 @@ def test_paper_adjoint_256_against_central_differences():
         assert close(g_k[c, q].item(), fd), (c, q, g_k[c, q].item(), fd)
 
 
-@pytest.mark.parametrize("transport,start", [("implicit", "bdf2"), (False, "sdirk2")])
+@pytest.mark.parametrize("transport,start", [("implicit", "bdf2"), ("implicit", "sdirk2")])
 def test_paper_adjoint_refusals(transport, start):
     import torch
     from paper_2411_17294_gb300 import tfs
