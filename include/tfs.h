@@ -85,7 +85,8 @@ enum {
                                  solve, the form of the paper's eq. FP_discrete: BiCGStab with a
                                  block-Jacobi preconditioner on FP64 Krylov vectors, no Courant limit;
                                  the workspace grows by ((10 + 2 nc) nc + 4 d) N doubles; tfs_step then synchronises its
-                                 stream; tfs_backward refuses it (TFS_ERR_ARG) */
+                                 stream; tfs_backward solves the transposed system per step with the
+                                 same solver (stress form; the paper's variable: TFS_ERR_ARG) */
     TFS_PARAM_UMAX = 4,       /* declared bound U on |u_a|; checked against tfs_transport_limit */
     TFS_PARAM_KRYLOV_TOL = 5, /* implicit transport: relative residual target, default 1e-13 (FP64)
                                  or 1e-9 (FP32 storage) */

@@ -14,6 +14,7 @@
 #include "../../include/tfs.h"
 #include "tfs_internal.h"
 #include "tfs_adjoint_paper.h"
+#include "tfs_adjoint_implicit.h"
 
 using namespace tfs;
 
@@ -1049,6 +1050,7 @@ namespace {
 struct AdjLayout {
     double* s[4];       // two ping-pong pairs (s1, s0)
     double* t[4];       // the paper's variable with transport: the same for the adjoint of Psi
+    double* cfT;        // implicit transport: the transposed operator's tap coefficients
     double* lamR;
     char* ell[2];
     double* partials;   // 2 per block
@@ -1062,7 +1064,8 @@ bool paper_psi_ring(const tfs_ctx* h) { return h->paper() && h->transport == 1; 
 size_t adj_bytes(const tfs_ctx* h, int seg_steps) {
     const size_t dfield = (size_t)h->nc * (size_t)h->N * 8;
     const long long blocks = (h->N + 31) / 32;
-    return (paper_psi_ring(h) ? 9 : 5) * align_up(dfield) + 2 * align_up(h->modes_bytes()) + align_up((size_t)blocks * 16) + kAlign +
+    const size_t cft = h->implicit_transport() ? align_up(4 * (size_t)h->dim * (size_t)h->N * 8) : 0;
+    return (paper_psi_ring(h) ? 9 : 5) * align_up(dfield) + cft + 2 * align_up(h->modes_bytes()) + align_up((size_t)blocks * 16) + kAlign +
            (size_t)seg_steps * align_up(h->field_bytes());
 }
 
@@ -1083,6 +1086,11 @@ AdjLayout adj_layout(const tfs_ctx* h) {
             L.t[i] = (double*)p;
             p += align_up(dfield);
         }
+    }
+    L.cfT = nullptr;
+    if (h->implicit_transport()) {
+        L.cfT = (double*)p;
+        p += align_up(4 * (size_t)h->dim * (size_t)h->N * 8);
     }
     for (int i = 0; i < 2; ++i) {
         L.ell[i] = p;
@@ -1199,7 +1207,8 @@ int tfs_bind_adjoint_workspace(tfs_handle h, void* dev_ptr, size_t bytes) {
 int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* checkpoints, int K, int steps,
                  const void* grad_u, const void* u, double* dJ_dsigma0, double* dJ_dgrad_u, double* dJ_dWi,
                  double* dJ_dbeta, void* stream) {
-    if (valid_handle(h) && h->implicit_transport()) return TFS_ERR_ARG;   // adjoint of the implicit step not built
+    // the implicit step's adjoint is built for the stress form
+    if (valid_handle(h) && h->implicit_transport() && h->paper()) return TFS_ERR_ARG;
     // the SDIRK2 first step's adjoint is built for the pointwise law
     if (valid_handle(h) && h->start == TFS_START_SDIRK2 && h->transport != 0) return TFS_ERR_ARG;
     if (!valid_handle(h) || !dJ_dsigma_T || !checkpoints || !grad_u || !dJ_dsigma0 || !dJ_dgrad_u || !dJ_dWi ||
@@ -1343,8 +1352,17 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
                 a.Wi = h->Wi;
                 a.Re = h->Re;
                 for (int i = 0; i < 3; ++i) a.inv_h[i] = (double)h->n[i] / h->L[i];
-                e = launch_adjoint_f64(a, cfg, s);
-                if (e == cudaSuccess && h->transport) e = launch_adjoint_transport(a, u, true, cfg, s);
+                if (h->implicit_transport()) {
+                    ImpArgs<double> ia{};
+                    fill_implicit(h, ia, grad_u, grad_u, u, nullptr, h->third_sig(), h->cur_mode, 1 - h->cur_mode);
+                    int it = 0;
+                    double rr = 0.0;
+                    e = run_implicit_adjoint_f64(ia, L.s[2 * cur], a.ell_prev, a.ell_prev2, L.cfT, s, &it, &rr);
+                    h->last_iters = it;
+                    h->last_relres = rr;
+                }
+                if (e == cudaSuccess) e = launch_adjoint_f64(a, cfg, s);
+                if (e == cudaSuccess && h->explicit_transport()) e = launch_adjoint_transport(a, u, true, cfg, s);
             } else {
                 AdjArgs<float> a{};
                 a.kap_n = (const float*)grad_u;
@@ -1379,8 +1397,17 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
                 a.Wi = h->Wi;
                 a.Re = h->Re;
                 for (int i = 0; i < 3; ++i) a.inv_h[i] = (double)h->n[i] / h->L[i];
-                e = launch_adjoint_f32(a, cfg, s);
-                if (e == cudaSuccess && h->transport) {
+                if (h->implicit_transport()) {
+                    ImpArgs<float> ia{};
+                    fill_implicit(h, ia, grad_u, grad_u, u, nullptr, h->third_sig(), h->cur_mode, 1 - h->cur_mode);
+                    int it = 0;
+                    double rr = 0.0;
+                    e = run_implicit_adjoint_f32(ia, L.s[2 * cur], a.ell_prev, a.ell_prev2, L.cfT, s, &it, &rr);
+                    h->last_iters = it;
+                    h->last_relres = rr;
+                }
+                if (e == cudaSuccess) e = launch_adjoint_f32(a, cfg, s);
+                if (e == cudaSuccess && h->explicit_transport()) {
                     AdjArgs<double> ad{};
                     ad.N = a.N;
                     ad.n0 = a.n0;

@@ -26,6 +26,7 @@
 
 #include "tfs_device.cuh"
 #include "tfs_internal.h"
+#include "tfs_adjoint_implicit.h"
 
 namespace tfs {
 namespace {
@@ -613,6 +614,110 @@ __global__ void __launch_bounds__(kThreads) start_push_kernel(const ImpArgs<T> A
     }
 }
 
+// ------------------------------------------------------------------ adjoint
+// Right-hand side of the adjoint's global solve, v = s1 + sum_j rho_j z_j with
+// z_j = b1 lamQ'_j + b2 lamQ''_j (FP64), and the initial guess 0.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) imp_adj_rhs_kernel(const ImpArgs<T> A, const double* s1,
+                                                               const T* ell_prev, const T* ell_prev2, double* b,
+                                                               double* x) {
+    constexpr int NC = Packed<DIM>::NC;
+    const long long N = A.N;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            double acc = 0.0;
+            for (int jj = 0; jj < A.m; ++jj) {
+                const long long q = ((long long)jj * NC + c) * N + p;
+                acc = fma(A.mcd.rho[jj], kB1 * (double)ell_prev[q] + kB2 * (double)ell_prev2[q], acc);
+            }
+            const long long qc = (long long)c * N + p;
+            b[qc] = s1[qc] + acc;
+            x[qc] = 0.0;
+        }
+    }
+}
+
+// Op -> Op^T, part 1: every point block P_p and its inverse transposed in place.
+template <int NC>
+__global__ void __launch_bounds__(kThreads) imp_transpose_blocks_kernel(long long N, double* Mb, double* Pinv) {
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int r = 0; r < NC; ++r)
+#pragma unroll
+            for (int k = r + 1; k < NC; ++k) {
+                const long long i = (long long)(r * NC + k) * N + p, j = (long long)(k * NC + r) * N + p;
+                const double m0 = Mb[i], m1 = Mb[j];
+                Mb[i] = m1;
+                Mb[j] = m0;
+                const double q0 = Pinv[i], q1 = Pinv[j];
+                Pinv[i] = q1;
+                Pinv[j] = q0;
+            }
+    }
+}
+
+// Op -> Op^T, part 2: Op couples p to p + k e_a with Cf_{a,k}(p) (the same on
+// every component), so Op^T couples p to p - k e_a with Cf_{a,k}(p - k e_a):
+// the taps -2, -1, +1, +2 (t = 0..3) map to t' = 3 - t.
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) imp_transpose_taps_kernel(long long N, int n0, int n1, int n2,
+                                                                      const double* __restrict__ Cf,
+                                                                      double* __restrict__ CfT) {
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        GridIdx g;
+        g.n0 = n0;
+        g.n1 = n1;
+        g.n2 = n2;
+        g.x = p % n0;
+        g.y = (p / n0) % n1;
+        g.z = p / ((long long)n0 * n1);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int k = t < 2 ? t - 2 : t - 1;
+                CfT[(long long)(a * 4 + (3 - t)) * N + p] = Cf[(long long)(a * 4 + t) * N + g.at(a, -k)];
+            }
+    }
+}
+
+// s1 <- M_p^T y - sum_j rho_j z_j (M_p = a I - dt L(kappa*), the pointwise part
+// of the operator), so that the pointwise adjoint kernel's own M_p^-T (s1 +
+// sum_j rho_j z_j) is y.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) imp_adj_fix_kernel(const ImpArgs<T> A, const double* y, double* s1,
+                                                               const T* ell_prev, const T* ell_prev2) {
+    constexpr int NC = Packed<DIM>::NC;
+    const long long N = A.N;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        double K[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+        for (int i = 0; i < DIM; ++i)
+#pragma unroll
+            for (int j = 0; j < DIM; ++j) {
+                const long long q = (long long)(i * DIM + j) * N + p;
+                K[i][j] = 2.0 * (double)A.kap_n[q] - (double)A.kap_nm1[q];
+            }
+        double M[NC][NC], yp[NC];
+        assemble_M<DIM>(K, A.a, A.dt, M);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) yp[c] = y[(long long)c * N + p];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            double acc = 0.0;
+            for (int jj = 0; jj < A.m; ++jj) {
+                const long long q = ((long long)jj * NC + c) * N + p;
+                acc = fma(A.mcd.rho[jj], kB1 * (double)ell_prev[q] + kB2 * (double)ell_prev2[q], acc);
+            }
+            double mty = 0.0;
+#pragma unroll
+            for (int r = 0; r < NC; ++r) mty = fma(M[r][c], yp[r], mty);
+            s1[(long long)c * N + p] = mty - acc;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ host side
 // Krylov workspace views (10 vectors of nc N, the point blocks and the
 // preconditioner inverses, partial sums, device scalars)
@@ -879,7 +984,40 @@ cudaError_t run_start_implicit(const ImpArgs<T>& a, const StartConsts& c, cudaSt
     return e;
 }
 
+template <typename T, int DIM>
+cudaError_t run_implicit_adjoint(const ImpArgs<T>& a, double* s1, const T* ell_prev, const T* ell_prev2, double* cfT,
+                                 cudaStream_t st, int* iters, double* relres) {
+    constexpr int NC = Packed<DIM>::NC;
+    KryView<NC> K(a.kry, a.partials, a.N);
+    const unsigned bs = (unsigned)kImpBlocks;
+    imp_setup_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Pinv, K.Cf);
+    imp_transpose_blocks_kernel<NC><<<bs, kThreads, 0, st>>>(a.N, K.Mb, K.Pinv);
+    imp_transpose_taps_kernel<DIM><<<bs, kThreads, 0, st>>>(a.N, a.n0, a.n1, a.n2, K.Cf, cfT);
+    imp_adj_rhs_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, s1, ell_prev, ell_prev2, K.b, K.x);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    K.Cf = cfT;
+    e = krylov_solve<T, DIM>(a, K, st, iters, relres);
+    if (e != cudaSuccess) return e;
+    imp_adj_fix_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.x, s1, ell_prev, ell_prev2);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t run_implicit_adjoint_f64(const ImpArgs<double>& a, double* s1, const double* ell_prev,
+                                     const double* ell_prev2, double* cfT, cudaStream_t s, int* iters,
+                                     double* relres) {
+    return a.dim == 2 ? run_implicit_adjoint<double, 2>(a, s1, ell_prev, ell_prev2, cfT, s, iters, relres)
+                      : run_implicit_adjoint<double, 3>(a, s1, ell_prev, ell_prev2, cfT, s, iters, relres);
+}
+
+cudaError_t run_implicit_adjoint_f32(const ImpArgs<float>& a, double* s1, const float* ell_prev,
+                                     const float* ell_prev2, double* cfT, cudaStream_t s, int* iters,
+                                     double* relres) {
+    return a.dim == 2 ? run_implicit_adjoint<float, 2>(a, s1, ell_prev, ell_prev2, cfT, s, iters, relres)
+                      : run_implicit_adjoint<float, 3>(a, s1, ell_prev, ell_prev2, cfT, s, iters, relres);
+}
 
 cudaError_t run_implicit_f64(const ImpArgs<double>& a, cudaStream_t s, int* iters, double* relres) {
     return a.dim == 2 ? run_implicit<double, 2, false>(a, s, iters, relres)

@@ -96,19 +96,31 @@ def test_implicit_without_velocity_equals_explicit_step():
     assert np.all(rel_err_per_component(outs[0], outs[1]) < 1e-12)
 
 
-def test_implicit_refuses_adjoint_and_reports_its_solve():
+def test_implicit_reports_its_solve_forward_and_backward():
+    # tfs_last_solve reports the forward step's solve, then the adjoint's
+    # transposed solve (its adjoint is checked in test_gpu_implicit_adjoint.py).
+    # Uniform fields under a uniform velocity: the transport of the state and of
+    # the adjoint vanish, so the gradient in sigma0 is the pointwise law's.
     import torch
     from paper_2411_17294_gb300 import tfs
     dim, n, dt = 2, (8, 8), 1e-2
-    s = tfs.Solver(dim, n, 1.0, 1.0, 0.5, dt, m=0, precision=tfs.TFS_FP64, transport="implicit")
-    s.set_state(torch.ones((3, 64), dtype=torch.float64, device=s.device))
-    k = torch.zeros((4, 64), dtype=torch.float64, device=s.device)
-    u = torch.full((2, 64), 3.0, dtype=torch.float64, device=s.device)
-    ck = s.new_checkpoint()
-    s.save(ck)
-    s.step(k, k, u)
-    it, rr = s.last_solve()
-    assert rr <= 1e-13 and it >= 0
-    with pytest.raises(RuntimeError):
-        s.backward(s.stress(), [ck], 1, 1, k, u)
-    s.close()
+    grads = []
+    for transport in ("implicit", False):
+        s = tfs.Solver(dim, n, 1.0, 1.0, 0.5, dt, m=0, precision=tfs.TFS_FP64, transport=transport)
+        s.set_state(torch.ones((3, 64), dtype=torch.float64, device=s.device))
+        k = torch.zeros((4, 64), dtype=torch.float64, device=s.device)
+        u = torch.full((2, 64), 3.0, dtype=torch.float64, device=s.device) if transport else None
+        ck = s.new_checkpoint()
+        s.save(ck)
+        s.step(k, k, u)
+        if transport:
+            it, rr = s.last_solve()
+            assert rr <= 1e-13 and it >= 0
+        g = s.backward(s.stress(), [ck], 1, 1, k, u)
+        if transport:
+            it, rr = s.last_solve()
+            assert rr <= 1e-13 and it >= 0
+            assert not (s.status() & tfs.TFS_FLAG_NOCONV)
+        grads.append(g[0].cpu().numpy())
+        s.close()
+    assert np.allclose(grads[0], grads[1], rtol=1e-12, atol=1e-14)
