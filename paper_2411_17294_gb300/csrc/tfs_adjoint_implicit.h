@@ -19,11 +19,19 @@ namespace tfs {
 // forms M_p^-T (s1 + sum_j rho_j z_j), recovers lamR and does the rest of the
 // step's adjoint unchanged.  `a` is filled as for the forward step (kry,
 // partials, tolerance, iteration limit, grid, stencil, velocity, kappa).
+//
+// The paper's variable (lp_out given): the operator is a I - dt xi L + dt xi T
+// on Phi with -dt T(h) on the right-hand side, v = s1 + xi lamPsi + sum_j dt c_j
+// z_j (lam_psi: the adjoint of Psi, or nullptr), and the adjoint of h gains
+// -dt T^T lamR = -(v - M_p^T lamR)/xi.  s1 is left as it is and lp_out receives
+// lamPsi - (v - M_p^T lamR)/xi: the paper-variable adjoint kernel, given that in
+// place of lamPsi, recovers lamR from M_p^-T (s1 + xi lp_out + sum_j dt c_j z_j)
+// and adds the transport's term to the adjoint of h.
 cudaError_t run_implicit_adjoint_f64(const ImpArgs<double>& a, double* s1, const double* ell_prev,
-                                     const double* ell_prev2, double* cfT, cudaStream_t s, int* iters,
-                                     double* relres);
+                                     const double* ell_prev2, double* cfT, const double* lam_psi, double xi,
+                                     double* lp_out, cudaStream_t s, int* iters, double* relres);
 cudaError_t run_implicit_adjoint_f32(const ImpArgs<float>& a, double* s1, const float* ell_prev,
-                                     const float* ell_prev2, double* cfT, cudaStream_t s, int* iters,
-                                     double* relres);
+                                     const float* ell_prev2, double* cfT, const double* lam_psi, double xi,
+                                     double* lp_out, cudaStream_t s, int* iters, double* relres);
 
 }  // namespace tfs

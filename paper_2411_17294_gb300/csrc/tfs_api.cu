@@ -1051,6 +1051,7 @@ struct AdjLayout {
     double* s[4];       // two ping-pong pairs (s1, s0)
     double* t[4];       // the paper's variable with transport: the same for the adjoint of Psi
     double* cfT;        // implicit transport: the transposed operator's tap coefficients
+    double* lpp;        // implicit transport in the paper's variable: the modified adjoint of Psi
     double* lamR;
     char* ell[2];
     double* partials;   // 2 per block
@@ -1065,7 +1066,8 @@ size_t adj_bytes(const tfs_ctx* h, int seg_steps) {
     const size_t dfield = (size_t)h->nc * (size_t)h->N * 8;
     const long long blocks = (h->N + 31) / 32;
     const size_t cft = h->implicit_transport() ? align_up(4 * (size_t)h->dim * (size_t)h->N * 8) : 0;
-    return (paper_psi_ring(h) ? 9 : 5) * align_up(dfield) + cft + 2 * align_up(h->modes_bytes()) + align_up((size_t)blocks * 16) + kAlign +
+    const size_t lpp = (h->implicit_transport() && h->paper()) ? align_up(dfield) : 0;
+    return (paper_psi_ring(h) ? 9 : 5) * align_up(dfield) + cft + lpp + 2 * align_up(h->modes_bytes()) + align_up((size_t)blocks * 16) + kAlign +
            (size_t)seg_steps * align_up(h->field_bytes());
 }
 
@@ -1091,6 +1093,11 @@ AdjLayout adj_layout(const tfs_ctx* h) {
     if (h->implicit_transport()) {
         L.cfT = (double*)p;
         p += align_up(4 * (size_t)h->dim * (size_t)h->N * 8);
+    }
+    L.lpp = nullptr;
+    if (h->implicit_transport() && h->paper()) {
+        L.lpp = (double*)p;
+        p += align_up(dfield);
     }
     for (int i = 0; i < 2; ++i) {
         L.ell[i] = p;
@@ -1207,8 +1214,6 @@ int tfs_bind_adjoint_workspace(tfs_handle h, void* dev_ptr, size_t bytes) {
 int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* checkpoints, int K, int steps,
                  const void* grad_u, const void* u, double* dJ_dsigma0, double* dJ_dgrad_u, double* dJ_dWi,
                  double* dJ_dbeta, void* stream) {
-    // the implicit step's adjoint is built for the stress form
-    if (valid_handle(h) && h->implicit_transport() && h->paper()) return TFS_ERR_ARG;
     // the SDIRK2 first step's adjoint is built for the pointwise law
     if (valid_handle(h) && h->start == TFS_START_SDIRK2 && h->transport != 0) return TFS_ERR_ARG;
     if (!valid_handle(h) || !dJ_dsigma_T || !checkpoints || !grad_u || !dJ_dsigma0 || !dJ_dgrad_u || !dJ_dWi ||
@@ -1287,6 +1292,30 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
             }
             if (h->paper()) {
                 const double* lam_psi = (n == steps - 1 && !paper_psi_ring(h)) ? L.lamR : nullptr;
+                if (h->implicit_transport()) {
+                    // Op^T solve; the adjoint of Psi handed on carries the transport's term
+                    int it = 0;
+                    double rr = 0.0;
+                    if (h->is_double()) {
+                        ImpArgs<double> ia{};
+                        fill_implicit(h, ia, grad_u, grad_u, u, nullptr, h->third_sig(), h->cur_mode, 1 - h->cur_mode);
+                        fill_implicit_paper(h, ia);
+                        e = run_implicit_adjoint_f64(ia, L.s[2 * cur], (const double*)L.ell[ell_prev],
+                                                     (const double*)L.ell[1 - ell_prev], L.cfT, lam_psi, h->xi_p,
+                                                     L.lpp, s, &it, &rr);
+                    } else {
+                        ImpArgs<float> ia{};
+                        fill_implicit(h, ia, grad_u, grad_u, u, nullptr, h->third_sig(), h->cur_mode, 1 - h->cur_mode);
+                        fill_implicit_paper(h, ia);
+                        e = run_implicit_adjoint_f32(ia, L.s[2 * cur], (const float*)L.ell[ell_prev],
+                                                     (const float*)L.ell[1 - ell_prev], L.cfT, lam_psi, h->xi_p,
+                                                     L.lpp, s, &it, &rr);
+                    }
+                    if (e != cudaSuccess) return TFS_ERR_CUDA;
+                    h->last_iters = it;
+                    h->last_relres = rr;
+                    lam_psi = L.lpp;
+                }
                 e = h->is_double() ? paper_adjoint_step<double>(h, L, cur, ell_prev, grad_u, u, sig_np1, lam_psi,
                                                                 psi0s[(size_t)n], dJ_dgrad_u, s)
                                    : paper_adjoint_step<float>(h, L, cur, ell_prev, grad_u, u, sig_np1, lam_psi,
@@ -1357,7 +1386,8 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
                     fill_implicit(h, ia, grad_u, grad_u, u, nullptr, h->third_sig(), h->cur_mode, 1 - h->cur_mode);
                     int it = 0;
                     double rr = 0.0;
-                    e = run_implicit_adjoint_f64(ia, L.s[2 * cur], a.ell_prev, a.ell_prev2, L.cfT, s, &it, &rr);
+                    e = run_implicit_adjoint_f64(ia, L.s[2 * cur], a.ell_prev, a.ell_prev2, L.cfT, nullptr, 0.0,
+                                                 nullptr, s, &it, &rr);
                     h->last_iters = it;
                     h->last_relres = rr;
                 }
@@ -1402,7 +1432,8 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
                     fill_implicit(h, ia, grad_u, grad_u, u, nullptr, h->third_sig(), h->cur_mode, 1 - h->cur_mode);
                     int it = 0;
                     double rr = 0.0;
-                    e = run_implicit_adjoint_f32(ia, L.s[2 * cur], a.ell_prev, a.ell_prev2, L.cfT, s, &it, &rr);
+                    e = run_implicit_adjoint_f32(ia, L.s[2 * cur], a.ell_prev, a.ell_prev2, L.cfT, nullptr, 0.0,
+                                                 nullptr, s, &it, &rr);
                     h->last_iters = it;
                     h->last_relres = rr;
                 }

@@ -615,11 +615,12 @@ __global__ void __launch_bounds__(kThreads) start_push_kernel(const ImpArgs<T> A
 }
 
 // ------------------------------------------------------------------ adjoint
-// Right-hand side of the adjoint's global solve, v = s1 + sum_j rho_j z_j with
-// z_j = b1 lamQ'_j + b2 lamQ''_j (FP64), and the initial guess 0.
+// Right-hand side of the adjoint's global solve, v = s1 [+ xi lamPsi] + sum_j
+// rho_j z_j with z_j = b1 lamQ'_j + b2 lamQ''_j (FP64), and the initial guess 0.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads) imp_adj_rhs_kernel(const ImpArgs<T> A, const double* s1,
-                                                               const T* ell_prev, const T* ell_prev2, double* b,
+                                                               const T* ell_prev, const T* ell_prev2,
+                                                               const double* lam_psi, double xi, double* b,
                                                                double* x) {
     constexpr int NC = Packed<DIM>::NC;
     const long long N = A.N;
@@ -632,7 +633,7 @@ __global__ void __launch_bounds__(kThreads) imp_adj_rhs_kernel(const ImpArgs<T> 
                 acc = fma(A.mcd.rho[jj], kB1 * (double)ell_prev[q] + kB2 * (double)ell_prev2[q], acc);
             }
             const long long qc = (long long)c * N + p;
-            b[qc] = s1[qc] + acc;
+            b[qc] = s1[qc] + acc + (lam_psi ? xi * lam_psi[qc] : 0.0);
             x[qc] = 0.0;
         }
     }
@@ -714,6 +715,46 @@ __global__ void __launch_bounds__(kThreads) imp_adj_fix_kernel(const ImpArgs<T> 
 #pragma unroll
             for (int r = 0; r < NC; ++r) mty = fma(M[r][c], yp[r], mty);
             s1[(long long)c * N + p] = mty - acc;
+        }
+    }
+}
+
+// The paper's variable: lp = lamPsi - (v - M_p^T y)/xi with v = s1 + xi lamPsi +
+// sum_j dt c_j z_j (y solves Op^T y = v, so v - M_p^T y = dt xi T^T y).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) imp_adj_paper_fix_kernel(const ImpArgs<T> A, const double* y,
+                                                                     const double* s1, const double* lam_psi,
+                                                                     double xi, const T* ell_prev,
+                                                                     const T* ell_prev2, double* lp) {
+    constexpr int NC = Packed<DIM>::NC;
+    const long long N = A.N;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        double K[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+        for (int i = 0; i < DIM; ++i)
+#pragma unroll
+            for (int j = 0; j < DIM; ++j) {
+                const long long q = (long long)(i * DIM + j) * N + p;
+                K[i][j] = 2.0 * (double)A.kap_n[q] - (double)A.kap_nm1[q];
+            }
+        double M[NC][NC], yp[NC];
+        assemble_M<DIM>(K, A.a, A.dt, M);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) yp[c] = y[(long long)c * N + p];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const long long qc = (long long)c * N + p;
+            double acc = 0.0;
+            for (int jj = 0; jj < A.m; ++jj) {
+                const long long q = ((long long)jj * NC + c) * N + p;
+                acc = fma(A.mcd.rho[jj], kB1 * (double)ell_prev[q] + kB2 * (double)ell_prev2[q], acc);
+            }
+            const double lpc = lam_psi ? lam_psi[qc] : 0.0;
+            const double v = s1[qc] + acc + xi * lpc;
+            double mty = 0.0;
+#pragma unroll
+            for (int r = 0; r < NC; ++r) mty = fma(M[r][c], yp[r], mty);
+            lp[qc] = lpc - (v - mty) / xi;
         }
     }
 }
@@ -986,37 +1027,45 @@ cudaError_t run_start_implicit(const ImpArgs<T>& a, const StartConsts& c, cudaSt
 
 template <typename T, int DIM>
 cudaError_t run_implicit_adjoint(const ImpArgs<T>& a, double* s1, const T* ell_prev, const T* ell_prev2, double* cfT,
-                                 cudaStream_t st, int* iters, double* relres) {
+                                 const double* lam_psi, double xi, double* lp_out, cudaStream_t st, int* iters,
+                                 double* relres) {
     constexpr int NC = Packed<DIM>::NC;
     KryView<NC> K(a.kry, a.partials, a.N);
     const unsigned bs = (unsigned)kImpBlocks;
     imp_setup_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Pinv, K.Cf);
     imp_transpose_blocks_kernel<NC><<<bs, kThreads, 0, st>>>(a.N, K.Mb, K.Pinv);
     imp_transpose_taps_kernel<DIM><<<bs, kThreads, 0, st>>>(a.N, a.n0, a.n1, a.n2, K.Cf, cfT);
-    imp_adj_rhs_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, s1, ell_prev, ell_prev2, K.b, K.x);
+    imp_adj_rhs_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, s1, ell_prev, ell_prev2, lp_out ? lam_psi : nullptr, xi,
+                                                        K.b, K.x);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     K.Cf = cfT;
     e = krylov_solve<T, DIM>(a, K, st, iters, relres);
     if (e != cudaSuccess) return e;
-    imp_adj_fix_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.x, s1, ell_prev, ell_prev2);
+    if (lp_out)
+        imp_adj_paper_fix_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.x, s1, lam_psi, xi, ell_prev, ell_prev2,
+                                                                  lp_out);
+    else
+        imp_adj_fix_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.x, s1, ell_prev, ell_prev2);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t run_implicit_adjoint_f64(const ImpArgs<double>& a, double* s1, const double* ell_prev,
-                                     const double* ell_prev2, double* cfT, cudaStream_t s, int* iters,
-                                     double* relres) {
-    return a.dim == 2 ? run_implicit_adjoint<double, 2>(a, s1, ell_prev, ell_prev2, cfT, s, iters, relres)
-                      : run_implicit_adjoint<double, 3>(a, s1, ell_prev, ell_prev2, cfT, s, iters, relres);
+                                     const double* ell_prev2, double* cfT, const double* lam_psi, double xi,
+                                     double* lp_out, cudaStream_t s, int* iters, double* relres) {
+    return a.dim == 2
+               ? run_implicit_adjoint<double, 2>(a, s1, ell_prev, ell_prev2, cfT, lam_psi, xi, lp_out, s, iters, relres)
+               : run_implicit_adjoint<double, 3>(a, s1, ell_prev, ell_prev2, cfT, lam_psi, xi, lp_out, s, iters, relres);
 }
 
 cudaError_t run_implicit_adjoint_f32(const ImpArgs<float>& a, double* s1, const float* ell_prev,
-                                     const float* ell_prev2, double* cfT, cudaStream_t s, int* iters,
-                                     double* relres) {
-    return a.dim == 2 ? run_implicit_adjoint<float, 2>(a, s1, ell_prev, ell_prev2, cfT, s, iters, relres)
-                      : run_implicit_adjoint<float, 3>(a, s1, ell_prev, ell_prev2, cfT, s, iters, relres);
+                                     const float* ell_prev2, double* cfT, const double* lam_psi, double xi,
+                                     double* lp_out, cudaStream_t s, int* iters, double* relres) {
+    return a.dim == 2
+               ? run_implicit_adjoint<float, 2>(a, s1, ell_prev, ell_prev2, cfT, lam_psi, xi, lp_out, s, iters, relres)
+               : run_implicit_adjoint<float, 3>(a, s1, ell_prev, ell_prev2, cfT, lam_psi, xi, lp_out, s, iters, relres);
 }
 
 cudaError_t run_implicit_f64(const ImpArgs<double>& a, cudaStream_t s, int* iters, double* relres) {

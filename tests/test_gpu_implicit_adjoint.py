@@ -10,7 +10,9 @@ the gathered tap coefficients), then the pointwise adjoint.
    alpha < 1 and alpha = 1, 2D and 3D, FP64 and FP32 storage.
 2. torch.autograd through fractional_stress(transport="implicit") against
    central differences of the CUDA forward, 1e-6 relative.
-3. Refusals: the paper's variable and the SDIRK2 start with implicit transport.
+3. Refusal: the SDIRK2 start with implicit transport (either variable); the
+   paper's variable with implicit transport is covered in
+   test_gpu_paper_adjoint.py.
 
 Tolerances: FP64 1e-6 relative (central differences, h = 1e-5; Krylov stopping
 at a relative residual of 1e-13 forward and backward); FP32 storage 5e-4 (its
@@ -161,7 +163,7 @@ def test_implicit_autograd_matches_central_differences():
             assert close(k.grad[c, q].item(), fd(fk, kd[c, q].item()))
 
 
-@pytest.mark.parametrize("form,start", [("paper", "bdf2"), ("stress", "sdirk2")])
+@pytest.mark.parametrize("form,start", [("stress", "sdirk2"), ("paper", "sdirk2")])
 def test_implicit_adjoint_refusals(form, start):
     import torch
     from paper_2411_17294_gb300 import tfs
