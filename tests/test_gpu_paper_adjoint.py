@@ -81,6 +81,7 @@ CASES = [
     (3, (4, 3, 5), 0.3, 12, 9, 4, False, 0, 0.0),
     (2, (40, 1), 0.7, 6, 7, 7, False, 0, 0.0),
     (3, (3, 3, 3), 0.6, 32, 10, 3, False, 0, 0.0),
+    (2, (37, 5), 0.4, 40, 6, 4, False, 0, 0.0),        # more than 32 modes: 16 per FP32 thread
     (2, (12, 10), 0.5, 8, 11, 4, True, 0, 0.0),
     (2, (16, 9), 0.4, 8, 9, 9, True, 1, 0.005),
     (3, (5, 4, 6), 0.6, 6, 8, 3, True, 1, 0.01),
