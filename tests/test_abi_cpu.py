@@ -91,13 +91,13 @@ def test_soe_and_params_validation(lib):
     # with transport off any bound is accepted
     assert lib.tfs_set_param(h, tfs.TFS_PARAM_TRANSPORT, 0.0) == tfs.TFS_OK
     assert lib.tfs_set_param(h, tfs.TFS_PARAM_UMAX, 1e6) == tfs.TFS_OK
-    # first-step method: BDF2 or SDIRK2 only; the adjoint refuses the SDIRK2 start
+    # first-step method: BDF2 or SDIRK2 only; tfs_backward checks its pointers in any mode
     assert lib.tfs_set_param(h, tfs.TFS_PARAM_START, 2.0) == tfs.TFS_ERR_ARG
     assert lib.tfs_set_param(h, tfs.TFS_PARAM_START, 0.5) == tfs.TFS_ERR_ARG
     assert lib.tfs_set_param(h, tfs.TFS_PARAM_START, float(tfs.TFS_START_SDIRK2)) == tfs.TFS_OK
     assert lib.tfs_backward(h, None, None, 1, 1, None, None, None, None, None, None, None) == tfs.TFS_ERR_ARG
     assert lib.tfs_set_param(h, tfs.TFS_PARAM_START, float(tfs.TFS_START_BDF2)) == tfs.TFS_OK
-    # variable carried: stress or the paper's Phi; the adjoint refuses the latter
+    # variable carried: stress or the paper's Phi (null arguments to tfs_backward: TFS_ERR_ARG)
     assert lib.tfs_set_param(h, tfs.TFS_PARAM_FORM, 2.0) == tfs.TFS_ERR_ARG
     assert lib.tfs_set_param(h, tfs.TFS_PARAM_FORM, float(tfs.TFS_FORM_PAPER)) == tfs.TFS_OK
     assert lib.tfs_backward(h, None, None, 1, 1, None, None, None, None, None, None, None) == tfs.TFS_ERR_ARG
