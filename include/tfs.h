@@ -86,7 +86,8 @@ enum {
                                  block-Jacobi preconditioner on FP64 Krylov vectors, no Courant limit;
                                  the workspace grows by ((10 + 2 nc) nc + 4 d) N doubles; tfs_step then synchronises its
                                  stream; tfs_backward solves the transposed system per step with the
-                                 same solver (either form; with the SDIRK2 start: TFS_ERR_ARG) */
+                                 same solver (either form; with the SDIRK2 start the stress form only,
+                                 else TFS_ERR_ARG) */
     TFS_PARAM_UMAX = 4,       /* declared bound U on |u_a|; checked against tfs_transport_limit */
     TFS_PARAM_KRYLOV_TOL = 5, /* implicit transport: relative residual target, default 1e-13 (FP64)
                                  or 1e-9 (FP32 storage) */
@@ -100,9 +101,9 @@ enum {
                                  With transport 2 both stage systems go through the implicit solver
                                  (tfs_last_solve: iterations summed, larger residual).  With
                                  TFS_FORM_PAPER the same method on Phi and its modes.  tfs_backward
-                                 differentiates the start with transport 0 in either form (zero initial
-                                 modes, as tfs_set_state leaves them) and refuses it with transport
-                                 (TFS_ERR_ARG) */
+                                 differentiates the start (zero initial modes, as tfs_set_state leaves
+                                 them) with transport 0 in either form and with transport 2 in the
+                                 stress form, else TFS_ERR_ARG */
     TFS_PARAM_FORM = 8        /* variable carried, TFS_FORM_*: the stress (default), or the paper's own
                                  variable (Section 3.4): Phi with d Phi/dt = (L(kappa) - I/Wi) Psi +
                                  G (kappa + kappa^T) Psi0, Psi = D^{1-alpha} Phi by kernel compression of

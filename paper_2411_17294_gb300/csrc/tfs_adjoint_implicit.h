@@ -34,4 +34,35 @@ cudaError_t run_implicit_adjoint_f32(const ImpArgs<float>& a, double* s1, const 
                                      const float* ell_prev2, double* cfT, const double* lam_psi, double xi,
                                      double* lp_out, cudaStream_t s, int* iters, double* relres);
 
+// Adjoint of the SDIRK2 first step with implicit transport (stress form, zero
+// initial modes): stage 1 solved again for S1 (into S1), then the two
+// transposed stage systems (lamr2 kept in s0_out until the end), then the
+// adjoint of sigma0 into s1_out (s0_out set to 0) and the parameter terms into
+// g_kap and the adjoint's 32-point partials.  s1 / s0in: adjoints of sigma^1
+// and (partial) sigma^0; ell_prev / ell_prev2: the two later mode-ring levels;
+// S2: sigma^1 of the recomputed step; cfT: 4 dim N doubles.  `a` as for the
+// forward start (a = dt W + dt/Wi); iters sums the three solves, relres the
+// largest residual.
+template <typename T>
+struct StartImpAdj {
+    const double* s1;
+    const double* s0in;
+    const T* ell_prev;
+    const T* ell_prev2;
+    const T* S2;
+    double* S1;
+    double* s1_out;
+    double* s0_out;
+    double* g_kap;
+    double* partials;
+    double* cfT;
+    double Wi, Re;
+};
+cudaError_t run_start_implicit_adjoint_f64(const ImpArgs<double>& a, const StartConsts& c,
+                                           const StartImpAdj<double>& j, cudaStream_t s, int* iters,
+                                           double* relres);
+cudaError_t run_start_implicit_adjoint_f32(const ImpArgs<float>& a, const StartConsts& c,
+                                           const StartImpAdj<float>& j, cudaStream_t s, int* iters,
+                                           double* relres);
+
 }  // namespace tfs

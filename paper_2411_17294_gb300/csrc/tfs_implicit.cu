@@ -759,6 +759,164 @@ __global__ void __launch_bounds__(kThreads) imp_adj_paper_fix_kernel(const ImpAr
     }
 }
 
+// Adjoint of the SDIRK2 first step with implicit transport (stress form, zero
+// initial modes).  The forward is the pointwise start's with M replaced by
+// Op = (dt W + dt/Wi) I - dt L(kappa^0) + dt (u.grad - eps Lap):
+//   S1 = Op^-1 dt (W s0 + G k g1),  S2 = Op^-1 dt (W s0 + c1 (S1 - s0) + G k g2),
+//   c1 = sum_j mu_j iota_j dt (1 - gamma) w_j iota_j,  sigma^1 = S2,
+//   sigma_j^1 = dt (1 - gamma) w_j iota_j (S1 - s0)(1 - gamma dt mu_j iota_j) + gamma dt w_j iota_j (S2 - s0),
+// and its reverse the pointwise one with Op^-T in place of M^-T: lamr2 = Op^-T
+// (s1 + a1), lamr1 = Op^-T (zq + dt c1 lamr2), with a1 = sum_j z_j gamma dt w_j
+// iota_j and zq = sum_j z_j (1 - gamma dt mu_j iota_j) dt (1 - gamma) w_j iota_j.
+
+// right-hand side of stage 1 (zero initial modes), initial guess 0
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) sta_r1_kernel(const ImpArgs<T> A, const StartConsts C, double* b,
+                                                          double* x) {
+    constexpr int NC = Packed<DIM>::NC;
+    const long long N = A.N;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const long long qc = (long long)c * N + p;
+            const int i = Packed<DIM>::I(c), j = Packed<DIM>::J(c);
+            const double ks = (double)A.kap_n[(long long)(i * DIM + j) * N + p] +
+                              (double)A.kap_n[(long long)(j * DIM + i) * N + p];
+            const double s0 = A.sigma0 ? (double)A.sigma0[qc] : 0.0;
+            b[qc] = A.dt * (C.W * s0 + A.G * ks * C.g[0]);
+            x[qc] = 0.0;
+        }
+    }
+}
+
+// the two ring sums of the start's adjoint at point p, component c
+template <typename T, int NC>
+__device__ __forceinline__ void sta_ring_sums(const StartConsts& C, int m, double dt, const T* ell_prev,
+                                              const T* ell_prev2, long long N, long long p, int c, double& a1,
+                                              double& zq) {
+    const double f1 = dt * (1.0 - C.gam), f2 = dt * C.gam;
+    a1 = 0.0;
+    zq = 0.0;
+    for (int jj = 0; jj < m; ++jj) {
+        const long long q = ((long long)jj * NC + c) * N + p;
+        const double z = kB1 * (double)ell_prev[q] + kB2 * (double)ell_prev2[q];
+        const double wi = C.w[jj] * C.inv_den[jj];
+        a1 = fma(z, f2 * wi, a1);
+        zq = fma(z * (1.0 - f2 * C.mu[jj] * C.inv_den[jj]), f1 * wi, zq);
+    }
+}
+
+__device__ __forceinline__ double sta_c1(const StartConsts& C, int m, double dt) {
+    const double f1 = dt * (1.0 - C.gam);
+    double c1 = 0.0;
+    for (int jj = 0; jj < m; ++jj) c1 += C.mu[jj] * C.inv_den[jj] * f1 * C.w[jj] * C.inv_den[jj];
+    return c1;
+}
+
+// b = s1 + a1 (stage 2's adjoint system), or b = zq + dt c1 lr2 (stage 1's) when lr2 is given
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) sta_lam_rhs_kernel(const ImpArgs<T> A, const StartConsts C,
+                                                               const double* s1, const double* lr2,
+                                                               const T* ell_prev, const T* ell_prev2, double* b,
+                                                               double* x) {
+    constexpr int NC = Packed<DIM>::NC;
+    const long long N = A.N;
+    const double c1 = sta_c1(C, A.m, A.dt);
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const long long qc = (long long)c * N + p;
+            double a1, zq;
+            sta_ring_sums<T, NC>(C, A.m, A.dt, ell_prev, ell_prev2, N, p, c, a1, zq);
+            b[qc] = lr2 ? zq + A.dt * c1 * lr2[qc] : s1[qc] + a1;
+            x[qc] = 0.0;
+        }
+    }
+}
+
+// adjoint of sigma0 into s1_out (s0_out, which held lamr2, set to 0) and the
+// parameter terms of both stages, as in the pointwise start adjoint
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) sta_final_kernel(const ImpArgs<T> A, const StartConsts C,
+                                                             const double* s0in, const T* ell_prev,
+                                                             const T* ell_prev2, const double* S1, const T* S2,
+                                                             const double* lr1, double* lr2_s0out, double* s1_out,
+                                                             double* g_kap, double* partials, double Wi, double Re) {
+    constexpr int NC = Packed<DIM>::NC;
+    const long long N = A.N;
+    const double c1 = sta_c1(C, A.m, A.dt);
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double gWi = 0.0, gbeta = 0.0;
+    if (p < N) {
+        double K[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+        for (int i = 0; i < DIM; ++i)
+#pragma unroll
+            for (int j = 0; j < DIM; ++j) K[i][j] = (double)A.kap_n[(long long)(i * DIM + j) * N + p];
+        double l1[NC], l2[NC], st1[NC], st2[NC], ks[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const long long qc = (long long)c * N + p;
+            const int i = Packed<DIM>::I(c), j = Packed<DIM>::J(c);
+            ks[c] = K[i][j] + K[j][i];
+            l1[c] = lr1[qc];
+            l2[c] = lr2_s0out[qc];
+            st1[c] = S1[qc];
+            st2[c] = (double)S2[qc];
+            double a1, zq;
+            sta_ring_sums<T, NC>(C, A.m, A.dt, ell_prev, ell_prev2, N, p, c, a1, zq);
+            const double lamS1 = zq + A.dt * c1 * l2[c];
+            s1_out[qc] = s0in[qc] - a1 + A.dt * C.W * (l1[c] + l2[c]) - lamS1;
+            lr2_s0out[qc] = 0.0;
+        }
+        double gK[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int stg = 0; stg < 2; ++stg) {
+            const double* lam = stg == 0 ? l1 : l2;
+            const double* sig = stg == 0 ? st1 : st2;
+            double S3[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+            for (int r = 0; r < NC; ++r) {
+                const int i = Packed<DIM>::I(r), j = Packed<DIM>::J(r);
+                S3[i][j] = sig[r];
+                S3[j][i] = sig[r];
+            }
+            const double src = A.dt * A.G * C.g[stg];
+            double sym_dot = 0.0, sig_dot = 0.0;
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc) {
+                const int r = Packed<DIM>::I(cc), s2 = Packed<DIM>::J(cc);
+                const double l = lam[cc];
+#pragma unroll
+                for (int bb = 0; bb < DIM; ++bb) {
+                    gK[r][bb] += A.dt * l * S3[bb][s2];
+                    gK[s2][bb] += A.dt * l * S3[r][bb];
+                }
+                gK[r][s2] += src * l;
+                gK[s2][r] += src * l;
+                sym_dot += l * ks[cc];
+                sig_dot += l * sig[cc];
+            }
+            const double lam_G = A.dt * C.g[stg] * sym_dot;
+            gWi += A.dt / (Wi * Wi) * sig_dot - A.G / Wi * lam_G;
+            gbeta += -lam_G / (Wi * Re);
+        }
+#pragma unroll
+        for (int a = 0; a < DIM; ++a)
+#pragma unroll
+            for (int bb = 0; bb < DIM; ++bb) g_kap[(long long)(a * DIM + bb) * N + p] += gK[a][bb];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        gWi += __shfl_xor_sync(0xffffffffu, gWi, off);
+        gbeta += __shfl_xor_sync(0xffffffffu, gbeta, off);
+    }
+    const long long grp = p >> 5;     // the 32-point group of this warp
+    if ((threadIdx.x & 31) == 0 && grp * 32 < N) {
+        partials[2 * grp + 0] += gWi;
+        partials[2 * grp + 1] += gbeta;
+    }
+}
+
 // ------------------------------------------------------------------ host side
 // Krylov workspace views (10 vectors of nc N, the point blocks and the
 // preconditioner inverses, partial sums, device scalars)
@@ -1051,6 +1209,68 @@ cudaError_t run_implicit_adjoint(const ImpArgs<T>& a, double* s1, const T* ell_p
 }
 
 }  // namespace
+
+template <typename T, int DIM>
+cudaError_t run_start_implicit_adjoint(const ImpArgs<T>& a, const StartConsts& C, const StartImpAdj<T>& J,
+                                       cudaStream_t st, int* iters, double* relres) {
+    constexpr int NC = Packed<DIM>::NC;
+    KryView<NC> K(a.kry, a.partials, a.N);
+    const unsigned bs = (unsigned)kImpBlocks;
+    const size_t vb = sizeof(double) * (size_t)NC * (size_t)a.N;
+    int it = 0, tot = 0;
+    double rr = 0.0, worst = 0.0;
+    // stage 1 of the forward again: S1
+    imp_setup_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Pinv, K.Cf);
+    sta_r1_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, C, K.b, K.x);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = krylov_solve<T, DIM>(a, K, st, &it, &rr);
+    if (e != cudaSuccess) return e;
+    tot += it;
+    worst = rr > worst ? rr : worst;
+    e = cudaMemcpyAsync(J.S1, K.x, vb, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    // the transposed operator
+    imp_transpose_blocks_kernel<NC><<<bs, kThreads, 0, st>>>(a.N, K.Mb, K.Pinv);
+    imp_transpose_taps_kernel<DIM><<<bs, kThreads, 0, st>>>(a.N, a.n0, a.n1, a.n2, K.Cf, J.cfT);
+    K.Cf = J.cfT;
+    // lamr2 (kept in s0_out until the end)
+    sta_lam_rhs_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, C, J.s1, nullptr, J.ell_prev, J.ell_prev2, K.b, K.x);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = krylov_solve<T, DIM>(a, K, st, &it, &rr);
+    if (e != cudaSuccess) return e;
+    tot += it;
+    worst = rr > worst ? rr : worst;
+    e = cudaMemcpyAsync(J.s0_out, K.x, vb, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    // lamr1
+    sta_lam_rhs_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, C, nullptr, J.s0_out, J.ell_prev, J.ell_prev2, K.b, K.x);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = krylov_solve<T, DIM>(a, K, st, &it, &rr);
+    if (e != cudaSuccess) return e;
+    tot += it;
+    worst = rr > worst ? rr : worst;
+    const long long blocks = (a.N + kThreads - 1) / kThreads;
+    sta_final_kernel<T, DIM><<<(unsigned)blocks, kThreads, 0, st>>>(a, C, J.s0in, J.ell_prev, J.ell_prev2, J.S1,
+                                                                   J.S2, K.x, J.s0_out, J.s1_out, J.g_kap,
+                                                                   J.partials, J.Wi, J.Re);
+    *iters = tot;
+    *relres = worst;
+    return cudaGetLastError();
+}
+
+cudaError_t run_start_implicit_adjoint_f64(const ImpArgs<double>& a, const StartConsts& c,
+                                           const StartImpAdj<double>& j, cudaStream_t s, int* iters,
+                                           double* relres) {
+    return a.dim == 2 ? run_start_implicit_adjoint<double, 2>(a, c, j, s, iters, relres)
+                      : run_start_implicit_adjoint<double, 3>(a, c, j, s, iters, relres);
+}
+
+cudaError_t run_start_implicit_adjoint_f32(const ImpArgs<float>& a, const StartConsts& c,
+                                           const StartImpAdj<float>& j, cudaStream_t s, int* iters,
+                                           double* relres) {
+    return a.dim == 2 ? run_start_implicit_adjoint<float, 2>(a, c, j, s, iters, relres)
+                      : run_start_implicit_adjoint<float, 3>(a, c, j, s, iters, relres);
+}
 
 cudaError_t run_implicit_adjoint_f64(const ImpArgs<double>& a, double* s1, const double* ell_prev,
                                      const double* ell_prev2, double* cfT, const double* lam_psi, double xi,

@@ -1,7 +1,9 @@
 """The adjoint of the implicit-transport step (TFS_PARAM_TRANSPORT = 2, stress
-form, BDF2 start) through tfs_backward: the global solve with the transposed
-operator (the step's block-Jacobi BiCGStab on the transposed point blocks and
-the gathered tap coefficients), then the pointwise adjoint.
+form; BDF2 start, and the SDIRK2 start of Section 5.1) through tfs_backward:
+the global solve with the transposed operator (the step's block-Jacobi
+BiCGStab on the transposed point blocks and the gathered tap coefficients),
+then the pointwise adjoint; for the SDIRK2 start, stage 1 solved again and
+both stage systems transposed.
 
 1. Against FP64 central differences of the oracle's implicit scheme (its dense
    global solve, oracle/orc.c), with velocities above the explicit Courant
@@ -10,9 +12,8 @@ the gathered tap coefficients), then the pointwise adjoint.
    alpha < 1 and alpha = 1, 2D and 3D, FP64 and FP32 storage.
 2. torch.autograd through fractional_stress(transport="implicit") against
    central differences of the CUDA forward, 1e-6 relative.
-3. Refusal: the SDIRK2 start with implicit transport (either variable); the
-   paper's variable with implicit transport is covered in
-   test_gpu_paper_adjoint.py.
+3. Refusal: the SDIRK2 start with implicit transport in the paper's variable
+   (the BDF2 start there is covered in test_gpu_paper_adjoint.py).
 
 Tolerances: FP64 1e-6 relative (central differences, h = 1e-5; Krylov stopping
 at a relative residual of 1e-13 forward and backward); FP32 storage 5e-4 (its
@@ -43,9 +44,18 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("dim,n,alpha,m,steps,K,stencil,eps,speed", CASES)
+SDIRK2_CASES = [
+    (2, (12, 10), 0.5, 8, 8, 3, 0, 0.0, 3.0),
+    (2, (9, 7), 0.4, 6, 1, 1, 1, 0.0, 2.0),
+    (3, (5, 4, 6), 0.6, 6, 6, 2, 1, 0.01, 2.0),
+]
+
+
+@pytest.mark.parametrize("dim,n,alpha,m,steps,K,stencil,eps,speed,start",
+                         [c + ("bdf2",) for c in CASES] + [c + ("sdirk2",) for c in SDIRK2_CASES])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_implicit_adjoint_against_oracle_differences(dim, n, alpha, m, steps, K, stencil, eps, speed, precision):
+def test_implicit_adjoint_against_oracle_differences(dim, n, alpha, m, steps, K, stencil, eps, speed, start,
+                                                     precision):
     import torch
     from paper_2411_17294_gb300 import tfs
     dt, Wi, beta = 2e-3, 1.3, 0.4
@@ -63,7 +73,7 @@ def test_implicit_adjoint_against_oracle_differences(dim, n, alpha, m, steps, K,
         u, kap, s0, dJ = cast(u), cast(kap), cast(s0), cast(dJ)
     # GPU gradients
     s = tfs.Solver(dim, n, alpha, Wi, beta, dt, m=m, precision=precision, mu=mu, w=w, eps=eps, stencil=stencil,
-                   transport="implicit")
+                   transport="implicit", start=start)
     dev, tdt = s.device, s.dtype
     kt = torch.as_tensor(kap, dtype=tdt, device=dev).contiguous()
     ut = torch.as_tensor(u, dtype=tdt, device=dev).contiguous()
@@ -84,7 +94,7 @@ def test_implicit_adjoint_against_oracle_differences(dim, n, alpha, m, steps, K,
     def J(sig0, k, Wi_, b_):
         p = orc.Problem(dim=dim, n=n, alpha=alpha, Wi=Wi_, beta=b_, dt=dt,
                         mu=mu if mu is not None else np.zeros(0), w=w if w is not None else np.zeros(0),
-                        eps=eps, stencil=stencil, transport=True, implicit=True)
+                        eps=eps, stencil=stencil, transport=True, implicit=True, start=start)
         return float(np.sum(dJ * orc.forward(p, sig0, k, u, steps)))
 
     tol = 1e-6 if precision == 0 else 5e-4
@@ -163,7 +173,7 @@ def test_implicit_autograd_matches_central_differences():
             assert close(k.grad[c, q].item(), fd(fk, kd[c, q].item()))
 
 
-@pytest.mark.parametrize("form,start", [("stress", "sdirk2"), ("paper", "sdirk2")])
+@pytest.mark.parametrize("form,start", [("paper", "sdirk2")])
 def test_implicit_adjoint_refusals(form, start):
     import torch
     from paper_2411_17294_gb300 import tfs
