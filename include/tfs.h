@@ -86,8 +86,7 @@ enum {
                                  block-Jacobi preconditioner on FP64 Krylov vectors, no Courant limit;
                                  the workspace grows by ((10 + 2 nc) nc + 4 d) N doubles; tfs_step then synchronises its
                                  stream; tfs_backward solves the transposed system per step with the
-                                 same solver (either form; with the SDIRK2 start the stress form only,
-                                 else TFS_ERR_ARG) */
+                                 same solver (either form, either start) */
     TFS_PARAM_UMAX = 4,       /* declared bound U on |u_a|; checked against tfs_transport_limit */
     TFS_PARAM_KRYLOV_TOL = 5, /* implicit transport: relative residual target, default 1e-13 (FP64)
                                  or 1e-9 (FP32 storage) */
@@ -102,8 +101,7 @@ enum {
                                  (tfs_last_solve: iterations summed, larger residual).  With
                                  TFS_FORM_PAPER the same method on Phi and its modes.  tfs_backward
                                  differentiates the start (zero initial modes, as tfs_set_state leaves
-                                 them) with transport 0 in either form and with transport 2 in the
-                                 stress form, else TFS_ERR_ARG */
+                                 them) with transport 0 or 2 in either form */
     TFS_PARAM_FORM = 8        /* variable carried, TFS_FORM_*: the stress (default), or the paper's own
                                  variable (Section 3.4): Phi with d Phi/dt = (L(kappa) - I/Wi) Psi +
                                  G (kappa + kappa^T) Psi0, Psi = D^{1-alpha} Phi by kernel compression of
@@ -123,7 +121,7 @@ enum {
                                  through the same Krylov solver, and one more nc N FP64 vector.  Needs
                                  alpha < 1 (else TFS_ERR_ARG here); either start (SDIRK2 with transport
                                  0 or 2, else tfs_step returns TFS_ERR_ARG); tfs_backward takes it
-                                 with transport 0 (either start), 1 or 2 (BDF2 start), else TFS_ERR_ARG.  The workspace grows by 2 nc N elements (Psi^n, Psi^{n-1});
+                                 with every transport mode and start the step takes.  The workspace grows by 2 nc N elements (Psi^n, Psi^{n-1});
                                  with a workspace bound, a form it does not fit returns TFS_ERR_NOWORKSPACE.
                                  Changing the form discards the state (call tfs_set_state again) */
 };

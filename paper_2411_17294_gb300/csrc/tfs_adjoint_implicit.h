@@ -34,8 +34,8 @@ cudaError_t run_implicit_adjoint_f32(const ImpArgs<float>& a, double* s1, const 
                                      const float* ell_prev2, double* cfT, const double* lam_psi, double xi,
                                      double* lp_out, cudaStream_t s, int* iters, double* relres);
 
-// Adjoint of the SDIRK2 first step with implicit transport (stress form, zero
-// initial modes): stage 1 solved again for S1 (into S1), then the two
+// Adjoint of the SDIRK2 first step with implicit transport (zero initial
+// modes): stage 1 solved again for S1 (into S1), then the two
 // transposed stage systems (lamr2 kept in s0_out until the end), then the
 // adjoint of sigma0 into s1_out (s0_out set to 0) and the parameter terms into
 // g_kap and the adjoint's 32-point partials.  s1 / s0in: adjoints of sigma^1
@@ -57,6 +57,13 @@ struct StartImpAdj {
     double* partials;
     double* cfT;
     double Wi, Re;
+    // the paper's variable (paper = 1): lam_psi the adjoint of Psi^1 (one-step
+    // run, else nullptr), phi0 = Phi(0) (nullptr: 0), dt the time step (a.dt is
+    // gamma dt W there); S2 is then Psi^1 and S1 receives Phi^(1)
+    int paper;
+    const double* lam_psi;
+    const T* phi0;
+    double dt;
 };
 cudaError_t run_start_implicit_adjoint_f64(const ImpArgs<double>& a, const StartConsts& c,
                                            const StartImpAdj<double>& j, cudaStream_t s, int* iters,

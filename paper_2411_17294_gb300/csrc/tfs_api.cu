@@ -1214,10 +1214,9 @@ int tfs_bind_adjoint_workspace(tfs_handle h, void* dev_ptr, size_t bytes) {
 int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* checkpoints, int K, int steps,
                  const void* grad_u, const void* u, double* dJ_dsigma0, double* dJ_dgrad_u, double* dJ_dWi,
                  double* dJ_dbeta, void* stream) {
-    // the SDIRK2 first step's adjoint: pointwise law, or implicit transport in the stress form
-    if (valid_handle(h) && h->start == TFS_START_SDIRK2 &&
-        (h->explicit_transport() || (h->implicit_transport() && h->paper())))
-        return TFS_ERR_ARG;
+    // the SDIRK2 first step's adjoint: pointwise law or implicit transport (the
+    // forward refuses explicit transport with it)
+    if (valid_handle(h) && h->start == TFS_START_SDIRK2 && h->explicit_transport()) return TFS_ERR_ARG;
     if (!valid_handle(h) || !dJ_dsigma_T || !checkpoints || !grad_u || !dJ_dsigma0 || !dJ_dgrad_u || !dJ_dWi ||
         !dJ_dbeta)
         return TFS_ERR_ARG;
@@ -1271,6 +1270,39 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
                 const double a_p = 1.0 + h->dt * c.gam * c.W / h->Wi;
                 const double G = (1.0 - h->beta) / (h->Wi * h->Re);
                 const double* lam_psi = (steps == 1) ? L.lamR : nullptr;
+                if (h->implicit_transport()) {
+                    // both stage systems global; Phi^(1) of stage 1 kept in lpp
+                    int it = 0;
+                    double rr = 0.0;
+                    if (h->is_double()) {
+                        ImpArgs<double> ia{};
+                        fill_implicit(h, ia, grad_u, grad_u, u, nullptr, h->third_sig(), h->cur_mode, 1 - h->cur_mode);
+                        ia.a = a_p;
+                        ia.dt = c.gam * h->dt * c.W;
+                        StartImpAdj<double> j{L.s[2 * cur], L.s[2 * cur + 1], (const double*)L.ell[ell_prev],
+                                              (const double*)L.ell[1 - ell_prev], (const double*)sig_np1, L.lpp,
+                                              L.s[2 * nxt], L.s[2 * nxt + 1], dJ_dgrad_u, L.partials, L.cfT,
+                                              h->Wi, h->Re, 1, lam_psi,
+                                              h->sigma0_zero ? nullptr : (const double*)h->sigma0, h->dt};
+                        e = run_start_implicit_adjoint_f64(ia, c, j, s, &it, &rr);
+                    } else {
+                        ImpArgs<float> ia{};
+                        fill_implicit(h, ia, grad_u, grad_u, u, nullptr, h->third_sig(), h->cur_mode, 1 - h->cur_mode);
+                        ia.a = a_p;
+                        ia.dt = c.gam * h->dt * c.W;
+                        StartImpAdj<float> j{L.s[2 * cur], L.s[2 * cur + 1], (const float*)L.ell[ell_prev],
+                                             (const float*)L.ell[1 - ell_prev], (const float*)sig_np1, L.lpp,
+                                             L.s[2 * nxt], L.s[2 * nxt + 1], dJ_dgrad_u, L.partials, L.cfT,
+                                             h->Wi, h->Re, 1, lam_psi,
+                                             h->sigma0_zero ? nullptr : (const float*)h->sigma0, h->dt};
+                        e = run_start_implicit_adjoint_f32(ia, c, j, s, &it, &rr);
+                    }
+                    if (e != cudaSuccess) return TFS_ERR_CUDA;
+                    h->last_iters = it;
+                    h->last_relres = rr;
+                    cur = nxt;
+                    continue;
+                }
                 if (h->is_double()) {
                     PaperStartAdjArgs<double> a{(const double*)grad_u,
                                                 h->sigma0_zero ? nullptr : (const double*)h->sigma0, lam_psi,
@@ -1342,7 +1374,7 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
                         StartImpAdj<double> j{L.s[2 * cur], L.s[2 * cur + 1], (const double*)L.ell[ell_prev],
                                               (const double*)L.ell[1 - ell_prev], (const double*)sig_np1, L.lamR,
                                               L.s[2 * nxt], L.s[2 * nxt + 1], dJ_dgrad_u, L.partials, L.cfT,
-                                              h->Wi, h->Re};
+                                              h->Wi, h->Re, 0, nullptr, nullptr, h->dt};
                         e = run_start_implicit_adjoint_f64(ia, c, j, s, &it, &rr);
                     } else {
                         ImpArgs<float> ia{};
@@ -1351,7 +1383,7 @@ int tfs_backward(tfs_handle h, const void* dJ_dsigma_T, const void* const* check
                         StartImpAdj<float> j{L.s[2 * cur], L.s[2 * cur + 1], (const float*)L.ell[ell_prev],
                                              (const float*)L.ell[1 - ell_prev], (const float*)sig_np1, L.lamR,
                                              L.s[2 * nxt], L.s[2 * nxt + 1], dJ_dgrad_u, L.partials, L.cfT,
-                                             h->Wi, h->Re};
+                                             h->Wi, h->Re, 0, nullptr, nullptr, h->dt};
                         e = run_start_implicit_adjoint_f32(ia, c, j, s, &it, &rr);
                     }
                     if (e != cudaSuccess) return TFS_ERR_CUDA;

@@ -917,6 +917,180 @@ __global__ void __launch_bounds__(kThreads) sta_final_kernel(const ImpArgs<T> A,
     }
 }
 
+// The same in the paper's variable (zero initial modes).  With gd = gamma dt,
+// f1 = (1 - gamma) dt, S = sum_j w_j mu_j iota_j^2, Op = a I - gd W L(kappa^0) +
+// gd W T (a = 1 + gd W/Wi) and M_p its pointwise part, the forward is
+//   P1 = Op^-1 (P0 + gd G k g0),  h2 = f1 S P1,  zP = P0 + (f1/gd)(P1 - P0),
+//   P2 = Op^-1 (zP - gd (L h2 - h2/Wi) + gd G k g1 + gd T h2),  Psi^1 = W P2 - h2,
+// and the reverse the pointwise one (paper_start_adjoint_kernel) with Op^-T and
+// one more term in the adjoint of h2, + gd T^T lamr2 = (lamP2 - M_p^T lamr2)/W.
+
+// stage 1 of the forward: b = P0 + gd G k g0, x = 0
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) stp_r1_kernel(const ImpArgs<T> A, const StartConsts C, const T* phi0,
+                                                          double dt, double* b, double* x) {
+    constexpr int NC = Packed<DIM>::NC;
+    const long long N = A.N;
+    const double gd = C.gam * dt;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const long long qc = (long long)c * N + p;
+            const int i = Packed<DIM>::I(c), j = Packed<DIM>::J(c);
+            const double ks = (double)A.kap_n[(long long)(i * DIM + j) * N + p] +
+                              (double)A.kap_n[(long long)(j * DIM + i) * N + p];
+            b[qc] = (phi0 ? (double)phi0[qc] : 0.0) + gd * A.G * ks * C.g[0];
+            x[qc] = 0.0;
+        }
+    }
+}
+
+// lamP2 = s1 + W lamPsi + gd sum_j iota_j z_j at (p, c), and sum_j iota_j^2 z_j
+template <typename T, int NC>
+__device__ __forceinline__ double stp_lamP2(const StartConsts& C, int m, double gd, const double* s1,
+                                            const double* lam_psi, const T* ell_prev, const T* ell_prev2, long long N,
+                                            long long p, int c, double& a1) {
+    double a2 = 0.0;
+    a1 = 0.0;
+    for (int jj = 0; jj < m; ++jj) {
+        const long long q = ((long long)jj * NC + c) * N + p;
+        const double z = kB1 * (double)ell_prev[q] + kB2 * (double)ell_prev2[q];
+        a2 = fma(C.inv_den[jj], z, a2);
+        a1 = fma(C.inv_den[jj] * C.inv_den[jj], z, a1);
+    }
+    const long long qc = (long long)c * N + p;
+    return s1[qc] + C.W * (lam_psi ? lam_psi[qc] : 0.0) + gd * a2;
+}
+
+// b = lamP2 (lr2 == nullptr), else b = lamP1 = f1 sum_j iota_j^2 z_j + f1 S lamh2 + (f1/gd) lr2
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) stp_lam_rhs_kernel(const ImpArgs<T> A, const StartConsts C,
+                                                               const double* s1, const double* lam_psi,
+                                                               const double* lr2, const T* ell_prev,
+                                                               const T* ell_prev2, double dt, double Wi, double* b,
+                                                               double* x) {
+    constexpr int NC = Packed<DIM>::NC;
+    const long long N = A.N;
+    const double gd = C.gam * dt, f1 = (1.0 - C.gam) * dt;
+    double S = 0.0;
+    for (int jj = 0; jj < A.m; ++jj) S += C.w[jj] * C.mu[jj] * C.inv_den[jj] * C.inv_den[jj];
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        double lamP2[NC], a1[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) lamP2[c] = stp_lamP2<T, NC>(C, A.m, gd, s1, lam_psi, ell_prev, ell_prev2, N, p, c, a1[c]);
+        if (!lr2) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                b[(long long)c * N + p] = lamP2[c];
+                x[(long long)c * N + p] = 0.0;
+            }
+            continue;
+        }
+        double K[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+        for (int i = 0; i < DIM; ++i)
+#pragma unroll
+            for (int j = 0; j < DIM; ++j) K[i][j] = (double)A.kap_n[(long long)(i * DIM + j) * N + p];
+        double M[NC][NC], l2[NC];
+        assemble_M<DIM>(K, A.a, A.dt, M);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) l2[c] = lr2[(long long)c * N + p];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            double mty = 0.0, lt = -l2[k] / Wi;
+#pragma unroll
+            for (int r = 0; r < NC; ++r) {
+                mty = fma(M[r][k], l2[r], mty);
+                lt = fma(uc_entry<DIM>(K, r, k), l2[r], lt);
+            }
+            const long long qc = (long long)k * N + p;
+            const double lamh2 = -(lam_psi ? lam_psi[qc] : 0.0) - gd * lt + (lamP2[k] - mty) / C.W;
+            b[qc] = f1 * a1[k] + f1 * S * lamh2 + (f1 / gd) * l2[k];
+            x[qc] = 0.0;
+        }
+    }
+}
+
+// adjoint of Phi(0) into s1_out (s0_out, which held lamr2, set to 0) and the
+// parameter terms of both stages (Y1 = W P1, Y2 = Psi^1; scale gd)
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) stp_final_kernel(const ImpArgs<T> A, const StartConsts C,
+                                                             const double* s0in, const double* P1, const T* Psi1,
+                                                             const double* lr1, double* lr2_s0out, double* s1_out,
+                                                             double* g_kap, double* partials, double dt, double Wi,
+                                                             double Re) {
+    constexpr int NC = Packed<DIM>::NC;
+    const long long N = A.N;
+    const double gd = C.gam * dt, f1 = (1.0 - C.gam) * dt;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double gWi = 0.0, gbeta = 0.0;
+    if (p < N) {
+        double K[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+        for (int i = 0; i < DIM; ++i)
+#pragma unroll
+            for (int j = 0; j < DIM; ++j) K[i][j] = (double)A.kap_n[(long long)(i * DIM + j) * N + p];
+        double l1[NC], l2[NC], Y1[NC], Y2[NC], ks[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const long long qc = (long long)c * N + p;
+            const int i = Packed<DIM>::I(c), j = Packed<DIM>::J(c);
+            ks[c] = K[i][j] + K[j][i];
+            l1[c] = lr1[qc];
+            l2[c] = lr2_s0out[qc];
+            Y1[c] = C.W * P1[qc];
+            Y2[c] = (double)Psi1[qc];
+            s1_out[qc] = s0in[qc] + l1[c] + (1.0 - f1 / gd) * l2[c];
+            lr2_s0out[qc] = 0.0;
+        }
+        double gK[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int stg = 0; stg < 2; ++stg) {
+            const double* lam = stg == 0 ? l1 : l2;
+            const double* Y = stg == 0 ? Y1 : Y2;
+            double Y3[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+            for (int r = 0; r < NC; ++r) {
+                const int i = Packed<DIM>::I(r), j = Packed<DIM>::J(r);
+                Y3[i][j] = Y[r];
+                Y3[j][i] = Y[r];
+            }
+            const double src = gd * A.G * C.g[stg];
+            double sym_dot = 0.0, y_dot = 0.0;
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc) {
+                const int r = Packed<DIM>::I(cc), s2 = Packed<DIM>::J(cc);
+                const double l = lam[cc];
+#pragma unroll
+                for (int bb = 0; bb < DIM; ++bb) {
+                    gK[r][bb] += gd * l * Y3[bb][s2];
+                    gK[s2][bb] += gd * l * Y3[r][bb];
+                }
+                gK[r][s2] += src * l;
+                gK[s2][r] += src * l;
+                sym_dot += l * ks[cc];
+                y_dot += l * Y[cc];
+            }
+            const double lam_G = gd * C.g[stg] * sym_dot;
+            gWi += gd / (Wi * Wi) * y_dot - A.G / Wi * lam_G;
+            gbeta += -lam_G / (Wi * Re);
+        }
+#pragma unroll
+        for (int a = 0; a < DIM; ++a)
+#pragma unroll
+            for (int bb = 0; bb < DIM; ++bb) g_kap[(long long)(a * DIM + bb) * N + p] += gK[a][bb];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        gWi += __shfl_xor_sync(0xffffffffu, gWi, off);
+        gbeta += __shfl_xor_sync(0xffffffffu, gbeta, off);
+    }
+    const long long grp = p >> 5;
+    if ((threadIdx.x & 31) == 0 && grp * 32 < N) {
+        partials[2 * grp + 0] += gWi;
+        partials[2 * grp + 1] += gbeta;
+    }
+}
+
 // ------------------------------------------------------------------ host side
 // Krylov workspace views (10 vectors of nc N, the point blocks and the
 // preconditioner inverses, partial sums, device scalars)
@@ -1221,7 +1395,8 @@ cudaError_t run_start_implicit_adjoint(const ImpArgs<T>& a, const StartConsts& C
     double rr = 0.0, worst = 0.0;
     // stage 1 of the forward again: S1
     imp_setup_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Pinv, K.Cf);
-    sta_r1_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, C, K.b, K.x);
+    if (J.paper) stp_r1_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, C, J.phi0, J.dt, K.b, K.x);
+    else sta_r1_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, C, K.b, K.x);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = krylov_solve<T, DIM>(a, K, st, &it, &rr);
     if (e != cudaSuccess) return e;
@@ -1234,7 +1409,11 @@ cudaError_t run_start_implicit_adjoint(const ImpArgs<T>& a, const StartConsts& C
     imp_transpose_taps_kernel<DIM><<<bs, kThreads, 0, st>>>(a.N, a.n0, a.n1, a.n2, K.Cf, J.cfT);
     K.Cf = J.cfT;
     // lamr2 (kept in s0_out until the end)
-    sta_lam_rhs_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, C, J.s1, nullptr, J.ell_prev, J.ell_prev2, K.b, K.x);
+    if (J.paper)
+        stp_lam_rhs_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, C, J.s1, J.lam_psi, nullptr, J.ell_prev, J.ell_prev2,
+                                                            J.dt, J.Wi, K.b, K.x);
+    else
+        sta_lam_rhs_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, C, J.s1, nullptr, J.ell_prev, J.ell_prev2, K.b, K.x);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = krylov_solve<T, DIM>(a, K, st, &it, &rr);
     if (e != cudaSuccess) return e;
@@ -1243,16 +1422,26 @@ cudaError_t run_start_implicit_adjoint(const ImpArgs<T>& a, const StartConsts& C
     e = cudaMemcpyAsync(J.s0_out, K.x, vb, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
     // lamr1
-    sta_lam_rhs_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, C, nullptr, J.s0_out, J.ell_prev, J.ell_prev2, K.b, K.x);
+    if (J.paper)
+        stp_lam_rhs_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, C, J.s1, J.lam_psi, J.s0_out, J.ell_prev,
+                                                            J.ell_prev2, J.dt, J.Wi, K.b, K.x);
+    else
+        sta_lam_rhs_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, C, nullptr, J.s0_out, J.ell_prev, J.ell_prev2, K.b,
+                                                            K.x);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = krylov_solve<T, DIM>(a, K, st, &it, &rr);
     if (e != cudaSuccess) return e;
     tot += it;
     worst = rr > worst ? rr : worst;
     const long long blocks = (a.N + kThreads - 1) / kThreads;
-    sta_final_kernel<T, DIM><<<(unsigned)blocks, kThreads, 0, st>>>(a, C, J.s0in, J.ell_prev, J.ell_prev2, J.S1,
-                                                                   J.S2, K.x, J.s0_out, J.s1_out, J.g_kap,
-                                                                   J.partials, J.Wi, J.Re);
+    if (J.paper)
+        stp_final_kernel<T, DIM><<<(unsigned)blocks, kThreads, 0, st>>>(a, C, J.s0in, J.S1, J.S2, K.x, J.s0_out,
+                                                                       J.s1_out, J.g_kap, J.partials, J.dt, J.Wi,
+                                                                       J.Re);
+    else
+        sta_final_kernel<T, DIM><<<(unsigned)blocks, kThreads, 0, st>>>(a, C, J.s0in, J.ell_prev, J.ell_prev2, J.S1,
+                                                                       J.S2, K.x, J.s0_out, J.s1_out, J.g_kap,
+                                                                       J.partials, J.Wi, J.Re);
     *iters = tot;
     *relres = worst;
     return cudaGetLastError();

@@ -12,8 +12,8 @@ both stage systems transposed.
    alpha < 1 and alpha = 1, 2D and 3D, FP64 and FP32 storage.
 2. torch.autograd through fractional_stress(transport="implicit") against
    central differences of the CUDA forward, 1e-6 relative.
-3. Refusal: the SDIRK2 start with implicit transport in the paper's variable
-   (the BDF2 start there is covered in test_gpu_paper_adjoint.py).
+(The paper's variable with implicit transport, either start, is covered in
+test_gpu_paper_adjoint.py.)
 
 Tolerances: FP64 1e-6 relative (central differences, h = 1e-5; Krylov stopping
 at a relative residual of 1e-13 forward and backward); FP32 storage 5e-4 (its
@@ -171,22 +171,3 @@ def test_implicit_autograd_matches_central_differences():
                 a[c, q] = x
                 return J(s0d, a, Wi.detach(), beta.detach()).item()
             assert close(k.grad[c, q].item(), fd(fk, kd[c, q].item()))
-
-
-@pytest.mark.parametrize("form,start", [("paper", "sdirk2")])
-def test_implicit_adjoint_refusals(form, start):
-    import torch
-    from paper_2411_17294_gb300 import tfs
-    n, dt, m = (8, 8), 2e-3, 4
-    mu, w = soe.soe_nnls(0.5 if form == "stress" else 0.5, dt, 1.0, m)
-    s = tfs.Solver(2, n, 0.5, 1.0, 0.5, dt, m=m, precision=tfs.TFS_FP64, mu=mu, w=w, transport="implicit",
-                   start=start, form=form)
-    s.set_state(None)
-    k = torch.zeros((4, 64), dtype=torch.float64, device=s.device)
-    u = torch.zeros((2, 64), dtype=torch.float64, device=s.device)
-    c = s.new_checkpoint()
-    s.save(c)
-    s.step(k, k, u)
-    with pytest.raises(tfs.TfsError):
-        s.backward(torch.ones((3, 64), dtype=torch.float64, device=s.device), [c], 1, 1, k, u)
-    s.close()

@@ -1,6 +1,7 @@
 """The adjoint of the paper's own variable (TFS_FORM_PAPER, Section 3.4;
 BDF2 start with the pointwise law, explicit or implicit transport; SDIRK2
-start with the pointwise law) through tfs_backward: J = <dJ, Psi(T)>.
+start with the pointwise law or implicit transport) through tfs_backward:
+J = <dJ, Psi(T)>.
 
 1. Against FP64 central differences of the oracle's scheme in that variable
    (oracle.paper_form.PaperForm), in random directions of Phi(0) (exact: Psi(T)
@@ -13,10 +14,9 @@ start with the pointwise law) through tfs_backward: J = <dJ, Psi(T)>.
    differences of the CUDA forward at sampled entries, 1e-6 relative.
 4. The SDIRK2 first step (Section 5.1) in this variable: one step alone (the
    adjoint of Psi^1 enters the start's adjoint) and followed by BDF2 steps.
-5. Implicit transport (eq. FP_discrete) in this variable: the transposed
-   global solve, against central differences of the oracle's dense implicit
-   scheme, above the explicit limit.
-6. Refusal: implicit transport with the SDIRK2 start.
+5. Implicit transport (eq. FP_discrete) in this variable, with either start:
+   the transposed global solves, against central differences of the oracle's
+   dense implicit scheme, above the explicit limit.
 
 Tolerances: FP64 1e-6 relative to the largest entry of each gradient (the
 central differences carry O(h^2) truncation, h = 1e-5); FP32 storage 5e-4
@@ -154,9 +154,17 @@ IMPLICIT_CASES = [
 ]
 
 
-@pytest.mark.parametrize("dim,n,alpha,m,steps,K,stencil,eps,speed", IMPLICIT_CASES)
+IMPLICIT_SDIRK2_CASES = [
+    (2, (12, 10), 0.5, 8, 6, 3, 0, 0.0, 0.5),
+    (2, (9, 7), 0.4, 6, 1, 1, 1, 0.01, 0.08),      # central stencil: block Jacobi needs a milder flow
+    (3, (5, 4, 6), 0.6, 6, 5, 2, 0, 0.01, 0.4),
+]
+
+
+@pytest.mark.parametrize("dim,n,alpha,m,steps,K,stencil,eps,speed,start",
+                         [c + ("bdf2",) for c in IMPLICIT_CASES] + [c + ("sdirk2",) for c in IMPLICIT_SDIRK2_CASES])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_paper_implicit_adjoint_against_oracle_differences(dim, n, alpha, m, steps, K, stencil, eps, speed,
+def test_paper_implicit_adjoint_against_oracle_differences(dim, n, alpha, m, steps, K, stencil, eps, speed, start,
                                                            precision):
     dt, Wi, beta = 2e-3, 1.3, 0.4
     mu, w = soe.soe_nnls(1 - alpha, dt, 50 * dt, m)
@@ -171,8 +179,9 @@ def test_paper_implicit_adjoint_against_oracle_differences(dim, n, alpha, m, ste
         cast = lambda a: np.asarray(a, np.float32).astype(np.float64)
         kap, P0, dJ, u = cast(kap), cast(P0), cast(dJ), cast(u)
     g_p0, g_k, gWi, gb = gpu_grads(dim, n, alpha, Wi, beta, dt, mu, w, P0, kap, steps, K, dJ, precision, u, eps,
-                                   stencil, implicit=True)
-    J = lambda P, k, Wi_, b_: oracle_J(dim, n, Wi_, b_, dt, mu, w, P, k, steps, dJ, u, eps, stencil, implicit=True)
+                                   stencil, start=start, implicit=True)
+    J = lambda P, k, Wi_, b_: oracle_J(dim, n, Wi_, b_, dt, mu, w, P, k, steps, dJ, u, eps, stencil, start=start,
+                                       implicit=True)
     tol = 1e-6 if precision == 0 else 5e-4
     h = 1e-5
 
@@ -302,22 +311,3 @@ def test_paper_adjoint_256_against_central_differences():
         km[c, q] -= h
         fd = dJ(run(Wi, beta, P0, kp), run(Wi, beta, P0, km)) / (2 * h)
         assert close(g_k[c, q].item(), fd), (c, q, g_k[c, q].item(), fd)
-
-
-@pytest.mark.parametrize("transport,start", [("implicit", "sdirk2")])
-def test_paper_adjoint_refusals(transport, start):
-    import torch
-    from paper_2411_17294_gb300 import tfs
-    n, dt, m = (8, 8), 2e-3, 4
-    mu, w = soe.soe_nnls(0.5, dt, 1.0, m)
-    s = tfs.Solver(2, n, 0.5, 1.0, 0.5, dt, m=m, precision=tfs.TFS_FP64, mu=mu, w=w, transport=transport,
-                   start=start, form="paper")
-    s.set_state(None)
-    k = torch.zeros((4, 64), dtype=torch.float64, device=s.device)
-    u = torch.zeros((2, 64), dtype=torch.float64, device=s.device) if transport else None
-    c = s.new_checkpoint()
-    s.save(c)
-    s.step(k, k, u)
-    with pytest.raises(tfs.TfsError):
-        s.backward(torch.ones((3, 64), dtype=torch.float64, device=s.device), [c], 1, 1, k, u)
-    s.close()
