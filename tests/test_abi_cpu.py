@@ -160,3 +160,51 @@ def test_form_and_transport_resize_checks(lib):
     assert lib.tfs_set_param(h, tfs.TFS_PARAM_TRANSPORT, 2.0) == tfs.TFS_OK
     assert lib.tfs_checkpoint_bytes(h) == 256 + 5 * field + 2 * 4 * field
     lib.tfs_destroy(h)
+
+
+def test_adjoint_workspace_sizing(lib):
+    # tfs_adjoint_workspace_bytes: two ping-pong pairs of FP64 adjoint fields and
+    # lamR (5 fields), two mode-ring levels, the 32-point partials, the scalar
+    # output slot and K segment levels; explicit transport in the paper's
+    # variable adds the Psi ring (4 fields), implicit transport the transposed
+    # tap coefficients (4 d N doubles), both together one more field.  A
+    # workspace bound before a change of form is refused by tfs_backward before
+    # any device access.  Host logic only.
+    from paper_2411_17294_gb300 import tfs
+    rc, h = make(lib, dim=2, n=(16, 16), m=4, precision=0)
+    assert rc == tfs.TFS_OK
+    N, nc, m, d = 256, 3, 4, 2
+    up = lambda b: (b + 255) // 256 * 256
+    dfield = nc * N * 8
+    fixed = 2 * up(m * dfield) + up((N + 31) // 32 * 16) + 256
+    cft = up(4 * d * N * 8)
+
+    def expect(extra_fields, extra_bytes, K):
+        return (5 + extra_fields) * up(dfield) + extra_bytes + fixed + K * up(dfield)
+
+    cases = [
+        (tfs.TFS_FORM_STRESS, 0, 0, 0), (tfs.TFS_FORM_STRESS, 1, 0, 0), (tfs.TFS_FORM_STRESS, 2, 0, cft),
+        (tfs.TFS_FORM_PAPER, 0, 0, 0), (tfs.TFS_FORM_PAPER, 1, 4, 0), (tfs.TFS_FORM_PAPER, 2, 1, cft),
+    ]
+    for form, transport, fields, extra in cases:
+        assert lib.tfs_set_param(h, tfs.TFS_PARAM_FORM, float(form)) == tfs.TFS_OK
+        assert lib.tfs_set_param(h, tfs.TFS_PARAM_TRANSPORT, float(transport)) == tfs.TFS_OK
+        for K in (1, 7):
+            assert lib.tfs_adjoint_workspace_bytes(h, K) == expect(fields, extra, K), (form, transport, K)
+    assert lib.tfs_adjoint_workspace_bytes(h, 0) == 0
+    # bind for the stress form with explicit transport, then carry the paper's variable
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_FORM, float(tfs.TFS_FORM_STRESS)) == tfs.TFS_OK
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_TRANSPORT, 1.0) == tfs.TFS_OK
+    big = 1 << 24
+    assert lib.tfs_bind_workspace(h, ctypes.c_void_p(256 * 1000), big) == tfs.TFS_OK
+    small = lib.tfs_adjoint_workspace_bytes(h, 1)
+    assert lib.tfs_bind_adjoint_workspace(h, ctypes.c_void_p(256 * 4000), small - 1) == tfs.TFS_ERR_NOWORKSPACE
+    assert lib.tfs_bind_adjoint_workspace(h, ctypes.c_void_p(256 * 4000 + 8), small) == tfs.TFS_ERR_ARG
+    assert lib.tfs_bind_adjoint_workspace(h, ctypes.c_void_p(256 * 4000), small) == tfs.TFS_OK
+    assert lib.tfs_set_param(h, tfs.TFS_PARAM_FORM, float(tfs.TFS_FORM_PAPER)) == tfs.TFS_OK
+    p = ctypes.c_void_p(256)
+    arr = (ctypes.c_void_p * 1)(p)
+    gWi, gb = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    rc = lib.tfs_backward(h, p, arr, 1, 1, p, p, p, p, ctypes.byref(gWi), ctypes.byref(gb), None)
+    assert rc == tfs.TFS_ERR_NOWORKSPACE
+    lib.tfs_destroy(h)
