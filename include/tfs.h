@@ -225,8 +225,10 @@ long tfs_step_index(tfs_handle h);
 int tfs_check_wait_bound(unsigned* flags, double* seconds, void* stream);
 
 /* Iterations and final relative residual |b - Op x| / |b| of the last
-   implicit-transport solve (TFS_PARAM_TRANSPORT = 2); either pointer may be
-   NULL.  Host-side, no synchronisation. */
+   implicit-transport solve (TFS_PARAM_TRANSPORT = 2): a step's (the SDIRK2
+   start: its two stages summed, the larger residual), or after tfs_backward
+   its last reverse step's transposed solve(s); either pointer may be NULL.
+   Host-side, no synchronisation. */
 int tfs_last_solve(tfs_handle h, int* iterations, double* relative_residual);
 
 /* Checkpoints: a device buffer holding the full state (header, stress at

@@ -249,7 +249,8 @@ class Solver:
         check(self.lib.tfs_set_step_events(self.h, b, a), "tfs_set_step_events")
 
     def last_solve(self):
-        """(iterations, relative residual) of the last implicit-transport solve."""
+        """(iterations, relative residual) of the last implicit-transport solve:
+        a step's, or after backward() the last reverse step's transposed solve."""
         it = ctypes.c_int(0)
         rr = ctypes.c_double(0.0)
         check(self.lib.tfs_last_solve(self.h, ctypes.byref(it), ctypes.byref(rr)), "tfs_last_solve")
