@@ -115,7 +115,7 @@ def test_library_limit_matches_eigenvalue_scan(alpha, m, stencil):
 
 def test_fractional_courant_scaling():
     # with a fixed SOE accuracy the boundary scales like (b0/dt)^alpha dt, i.e.
-    # C = (dt/b0)^alpha |u|/h is dt-independent (the survey's T1 estimate)
+    # C = (dt/b0)^alpha |u|/h is dt-independent
     Cs = []
     for dt in (1e-3, 1e-4):
         tab = soe.soe_nnls(0.5, dt, 200 * dt, 16)
