@@ -255,3 +255,104 @@ class PaperForm:
         self.kap_prev = kap_n
         self.n += 1
         return self.Psi.copy()
+
+
+def paper_gradients(dim, N, Wi, beta, dt, mu, w, Phi0, kap, steps, dJ, Re=1.0):
+    """Reverse-mode derivatives of J = <dJ, Psi^steps> for the pointwise law,
+    BDF2 start, frozen velocity gradient kap [d*d][N] (kappa* = kappa): returns
+    dict(Psi_T, Phi0, kappa, Wi, beta).  Plain reverse sweep of the step above,
+    one linear operation at a time (no combination of terms):
+
+        h      = sum_j w_j mu_j c_j (b1 phi_j^n + b2 phi_j^{n-1})
+        rhs    = -b1 Phi^n - b2 Phi^{n-1} + dt (L h - h/Wi) + dt G k Psi0^{n+1}
+        Phi^{n+1} = M^-1 rhs,  M = b0 I - dt xi (L - I/Wi)
+        phi_j^{n+1} = c_j (-b1 phi_j^n - b2 phi_j^{n-1} + dt Phi^{n+1})
+        Psi^{n+1} = xi Phi^{n+1} + h
+
+    (k = kappa + kappa^T, G = (1 - beta)/(Wi Re)); Phi^{-1} = Phi^0 = Phi0 and
+    the modes start at zero.  The kappa derivative of L(kappa) X is taken by
+    unit perturbations of kappa, one entry at a time."""
+    d = dim
+    nc = 3 if d == 2 else 6
+    mu = np.asarray(mu, float)
+    w = np.asarray(w, float)
+    c = 1.0 / (B0 + mu * dt)
+    xi = B0 * np.sum(w * c)
+    G = (1.0 - beta) / (Wi * Re)
+    kap = np.asarray(kap, float).reshape(d * d, N)
+    K = kap.T.reshape(N, d, d)
+    P = _packed(d)
+    KS = K + np.swapaxes(K, 1, 2)
+    ks = np.stack([KS[:, i, j] for (i, j) in P])
+    # forward, keeping what the reverse sweep reads
+    pf = PaperForm(dim, N, Wi, beta, dt, mu, w, Phi0=Phi0, Re=Re)
+    hist = []
+    for _ in range(steps):
+        h0 = float(np.sum(w * mu * c * (B1 * pf.phi0_n + B2 * pf.phi0_nm1)))
+        psi0 = xi + h0
+        h = np.tensordot(w * mu * c, B1 * pf.phi_n + B2 * pf.phi_nm1, axes=(0, 0))
+        psi = pf.step(kap, kap)
+        hist.append((pf.Phi_n.copy(), h, psi0))
+    # per-point matrix M and its transpose
+    M = np.zeros((N, nc, nc))
+    for k in range(nc):
+        e = np.zeros((nc, N))
+        e[k] = 1.0
+        M[:, :, k] = (B0 * e - dt * xi * (_upper_convected(d, K, e) - e / Wi)).T
+    Mt = np.swapaxes(M, 1, 2)
+
+    def L_T(v):
+        """L(kappa)^T v per point: column k of L is L(kappa) e_k."""
+        out = np.zeros((nc, N))
+        for k in range(nc):
+            e = np.zeros((nc, N))
+            e[k] = 1.0
+            out[k] = np.sum(_upper_convected(d, K, e) * v, axis=0)
+        return out
+
+    def dL_dot(v, X):
+        """[d*d][N]: entry (a, b) = v . (d/dkappa_ab) L(kappa) X = v . L(E_ab) X."""
+        out = np.zeros((d * d, N))
+        for a in range(d):
+            for b in range(d):
+                E = np.zeros((N, d, d))
+                E[:, a, b] = 1.0
+                out[a * d + b] = np.sum(v * _upper_convected(d, E, X), axis=0)
+        return out
+
+    m = len(mu)
+    aPhi1 = np.zeros((nc, N))          # adjoint of Phi^{n+1}
+    aPhi0 = np.zeros((nc, N))          # partial adjoint of Phi^n (from step n+1)
+    aphi1 = np.zeros((m, nc, N))       # adjoint of phi_j^{n+1}
+    aphi0 = np.zeros((m, nc, N))       # partial adjoint of phi_j^n
+    g_kap = np.zeros((d * d, N))
+    gWi = gbeta = 0.0
+    for n in range(steps - 1, -1, -1):
+        Phi_new, h, psi0 = hist[n]
+        aPsi = np.asarray(dJ, float).reshape(nc, N) if n == steps - 1 else np.zeros((nc, N))
+        # Psi^{n+1} = xi Phi^{n+1} + h;  phi_j^{n+1} = c_j (... + dt Phi^{n+1})
+        aPhi_new = aPhi1 + xi * aPsi + dt * np.tensordot(c, aphi1, axes=(0, 0))
+        ah = aPsi.copy()
+        # Phi^{n+1} = M^-1 rhs
+        arhs = np.linalg.solve(Mt, aPhi_new.T[..., None])[..., 0].T
+        # rhs = -b1 Phi^n - b2 Phi^{n-1} + dt (L h - h/Wi) + dt G k psi0
+        ah += dt * (L_T(arhs) - arhs / Wi)
+        new_aPhi1 = aPhi0 - B1 * arhs
+        new_aPhi0 = -B2 * arhs
+        # h = sum_j w_j mu_j c_j (b1 phi_j^n + b2 phi_j^{n-1}); phi_j^{n+1} = c_j (-b1 phi_j^n - b2 phi_j^{n-1} + ...)
+        wmc = (w * mu * c)[:, None, None]
+        new_aphi1 = aphi0 + B1 * wmc * ah[None] - B1 * c[:, None, None] * aphi1
+        new_aphi0 = B2 * wmc * ah[None] - B2 * c[:, None, None] * aphi1
+        # parameters: M (through kappa and Wi), L h, G and k
+        g_kap += dt * dL_dot(arhs, h) + dt * xi * dL_dot(arhs, Phi_new)
+        for a in range(d):
+            for b in range(d):
+                dks = np.zeros((nc, N))
+                for cc, (i, j) in enumerate(P):
+                    dks[cc] = (1.0 if (i, j) == (a, b) else 0.0) + (1.0 if (j, i) == (a, b) else 0.0)
+                g_kap[a * d + b] += dt * G * psi0 * np.sum(arhs * dks, axis=0)
+        gWi += dt * xi / Wi ** 2 * np.sum(arhs * Phi_new) + dt / Wi ** 2 * np.sum(arhs * h) \
+            - dt * (G / Wi) * psi0 * np.sum(arhs * ks)
+        gbeta += -dt * psi0 * np.sum(arhs * ks) / (Wi * Re)
+        aPhi1, aPhi0, aphi1, aphi0 = new_aPhi1, new_aPhi0, new_aphi1, new_aphi0
+    return dict(Psi_T=psi, Phi0=aPhi1 + aPhi0, kappa=g_kap, Wi=gWi, beta=gbeta)

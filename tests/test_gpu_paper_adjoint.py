@@ -17,6 +17,10 @@ J = <dJ, Psi(T)>.
 5. Implicit transport (eq. FP_discrete) in this variable, with either start:
    the transposed global solves, against central differences of the oracle's
    dense implicit scheme, above the explicit limit.
+6. Element by element against the oracle's reference adjoint
+   (oracle.paper_form.paper_gradients, itself pinned to central differences in
+   tests/test_oracle_paper_adjoint.py), FP64 storage, to 1e-9 of each field's
+   largest entry.
 
 Tolerances: FP64 1e-6 relative to the largest entry of each gradient (the
 central differences carry O(h^2) truncation, h = 1e-5); FP32 storage 5e-4
@@ -28,7 +32,7 @@ import pytest
 
 from helpers import ensure_lib
 from oracle import soe
-from oracle.paper_form import PaperForm
+from oracle.paper_form import PaperForm, paper_gradients
 from paper_2411_17294_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -204,6 +208,23 @@ def test_paper_implicit_adjoint_against_oracle_differences(dim, n, alpha, m, ste
     Jp = lambda P: oracle_J(dim, n, Wi, beta, dt, mu, w, P, kap, steps, dJ)
     d = np.random.default_rng(5).normal(size=P0.shape)
     assert abs((Jp(P0 + d) - Jp(P0 - d)) / 2.0 - float(np.sum(g_p0 * d))) > 1e-3 * np.sum(np.abs(g_p0 * d))
+
+
+@pytest.mark.parametrize("dim,n,alpha,m,steps,K", [(2, (37, 5), 0.5, 8, 9, 4), (3, (4, 3, 5), 0.35, 12, 7, 3)])
+def test_paper_adjoint_fields_match_oracle_adjoint(dim, n, alpha, m, steps, K):
+    dt, Wi, beta = 4e-3, 1.3, 0.4
+    N = int(np.prod(n))
+    mu, w = soe.soe_nnls(1 - alpha, dt, 50 * dt, m)
+    _, kap = inputs.spectral_velocity(dim, n, 2, seed=95)
+    kap = 0.6 * np.asarray(kap)
+    P0 = inputs.random_stress(dim, n, 96)
+    dJ = np.random.default_rng(97).normal(size=P0.shape)
+    g_p0, g_k, gWi, gb = gpu_grads(dim, n, alpha, Wi, beta, dt, mu, w, P0, kap, steps, K, dJ, 0)
+    ref = paper_gradients(dim, N, Wi, beta, dt, mu, w, P0, kap, steps, dJ)
+    for got, exp in ((g_p0, ref["Phi0"]), (g_k, ref["kappa"])):
+        assert np.max(np.abs(got - exp)) <= 1e-9 * np.max(np.abs(exp))
+    assert abs(gWi - ref["Wi"]) <= 1e-9 * abs(ref["Wi"])
+    assert abs(gb - ref["beta"]) <= 1e-9 * abs(ref["beta"])
 
 
 def test_paper_autograd_matches_central_differences():
