@@ -257,11 +257,13 @@ class PaperForm:
         return self.Psi.copy()
 
 
-def paper_gradients(dim, N, Wi, beta, dt, mu, w, Phi0, kap, steps, dJ, Re=1.0):
-    """Reverse-mode derivatives of J = <dJ, Psi^steps> for the pointwise law,
-    BDF2 start, frozen velocity gradient kap [d*d][N] (kappa* = kappa): returns
-    dict(Psi_T, Phi0, kappa, Wi, beta).  Plain reverse sweep of the step above,
-    one linear operation at a time (no combination of terms):
+def paper_gradients(dim, N, Wi, beta, dt, mu, w, Phi0, kap, steps, dJ, Re=1.0, u=None, grid=None, L=None, eps=0.0,
+                    stencil=0, implicit=False):
+    """Reverse-mode derivatives of J = <dJ, Psi^steps> for the BDF2 start and a
+    frozen velocity gradient kap [d*d][N] (kappa* = kappa), pointwise or with
+    transport (u, grid as for PaperForm; explicit on 2 Psi^n - Psi^{n-1}, or
+    implicit): returns dict(Psi_T, Phi0, kappa, Wi, beta).  Plain reverse sweep
+    of the step above, one linear operation at a time (no combination of terms):
 
         h      = sum_j w_j mu_j c_j (b1 phi_j^n + b2 phi_j^{n-1})
         rhs    = -b1 Phi^n - b2 Phi^{n-1} + dt (L h - h/Wi) + dt G k Psi0^{n+1}
@@ -270,7 +272,10 @@ def paper_gradients(dim, N, Wi, beta, dt, mu, w, Phi0, kap, steps, dJ, Re=1.0):
         Psi^{n+1} = xi Phi^{n+1} + h
 
     (k = kappa + kappa^T, G = (1 - beta)/(Wi Re)); Phi^{-1} = Phi^0 = Phi0 and
-    the modes start at zero.  The kappa derivative of L(kappa) X is taken by
+    the modes start at zero.  Explicit transport subtracts dt T(2 Psi^n -
+    Psi^{n-1}) from rhs; implicit transport adds dt xi T to M and subtracts
+    dt T(h) from rhs (T = u.grad - eps Lap, assembled densely from unit
+    vectors: small grids only).  The kappa derivative of L(kappa) X is taken by
     unit perturbations of kappa, one entry at a time."""
     d = dim
     nc = 3 if d == 2 else 6
@@ -285,14 +290,24 @@ def paper_gradients(dim, N, Wi, beta, dt, mu, w, Phi0, kap, steps, dJ, Re=1.0):
     KS = K + np.swapaxes(K, 1, 2)
     ks = np.stack([KS[:, i, j] for (i, j) in P])
     # forward, keeping what the reverse sweep reads
-    pf = PaperForm(dim, N, Wi, beta, dt, mu, w, Phi0=Phi0, Re=Re)
+    pf = PaperForm(dim, N, Wi, beta, dt, mu, w, Phi0=Phi0, Re=Re, grid=grid, L=L, eps=eps, stencil=stencil,
+                   implicit=implicit)
     hist = []
     for _ in range(steps):
         h0 = float(np.sum(w * mu * c * (B1 * pf.phi0_n + B2 * pf.phi0_nm1)))
         psi0 = xi + h0
         h = np.tensordot(w * mu * c, B1 * pf.phi_n + B2 * pf.phi_nm1, axes=(0, 0))
-        psi = pf.step(kap, kap)
+        psi = pf.step(kap, kap, u)
         hist.append((pf.Phi_n.copy(), h, psi0))
+    nn = nc * N
+    Tm = None
+    if u is not None:
+        Tm = np.zeros((nn, nn))        # column k = T applied to unit vector k
+        for k in range(nn):
+            e = np.zeros((nc, N))
+            e.flat[k] = 1.0
+            Tm[:, k] = pf._transport_op(e, u).ravel()
+    TT = lambda v: (Tm.T @ v.ravel()).reshape(nc, N)
     # per-point matrix M and its transpose
     M = np.zeros((N, nc, nc))
     for k in range(nc):
@@ -300,6 +315,15 @@ def paper_gradients(dim, N, Wi, beta, dt, mu, w, Phi0, kap, steps, dJ, Re=1.0):
         e[k] = 1.0
         M[:, :, k] = (B0 * e - dt * xi * (_upper_convected(d, K, e) - e / Wi)).T
     Mt = np.swapaxes(M, 1, 2)
+    AT = None
+    if u is not None and implicit:
+        A = np.zeros((nn, nn))
+        for k in range(nn):
+            e = np.zeros((nc, N))
+            e.flat[k] = 1.0
+            A[:, k] = (B0 * e - dt * xi * (_upper_convected(d, K, e) - e / Wi)).ravel()
+        A += dt * xi * Tm
+        AT = A.T
 
     def L_T(v):
         """L(kappa)^T v per point: column k of L is L(kappa) e_k."""
@@ -325,18 +349,27 @@ def paper_gradients(dim, N, Wi, beta, dt, mu, w, Phi0, kap, steps, dJ, Re=1.0):
     aPhi0 = np.zeros((nc, N))          # partial adjoint of Phi^n (from step n+1)
     aphi1 = np.zeros((m, nc, N))       # adjoint of phi_j^{n+1}
     aphi0 = np.zeros((m, nc, N))       # partial adjoint of phi_j^n
+    aPsi1 = np.zeros((nc, N))          # explicit transport: adjoint of Psi^{n+1} from later steps
+    aPsi0 = np.zeros((nc, N))          # and the partial one of Psi^n
     g_kap = np.zeros((d * d, N))
     gWi = gbeta = 0.0
     for n in range(steps - 1, -1, -1):
         Phi_new, h, psi0 = hist[n]
-        aPsi = np.asarray(dJ, float).reshape(nc, N) if n == steps - 1 else np.zeros((nc, N))
+        aPsi = aPsi1 + (np.asarray(dJ, float).reshape(nc, N) if n == steps - 1 else 0.0)
         # Psi^{n+1} = xi Phi^{n+1} + h;  phi_j^{n+1} = c_j (... + dt Phi^{n+1})
         aPhi_new = aPhi1 + xi * aPsi + dt * np.tensordot(c, aphi1, axes=(0, 0))
         ah = aPsi.copy()
-        # Phi^{n+1} = M^-1 rhs
-        arhs = np.linalg.solve(Mt, aPhi_new.T[..., None])[..., 0].T
-        # rhs = -b1 Phi^n - b2 Phi^{n-1} + dt (L h - h/Wi) + dt G k psi0
+        # Phi^{n+1} = M^-1 rhs (implicit transport: the dense operator)
+        if AT is not None:
+            arhs = np.linalg.solve(AT, aPhi_new.ravel()).reshape(nc, N)
+        else:
+            arhs = np.linalg.solve(Mt, aPhi_new.T[..., None])[..., 0].T
+        # rhs = -b1 Phi^n - b2 Phi^{n-1} + dt (L h - h/Wi) + dt G k psi0 [- dt T(h) | - dt T(2 Psi^n - Psi^{n-1})]
         ah += dt * (L_T(arhs) - arhs / Wi)
+        if AT is not None:
+            ah -= dt * TT(arhs)
+        if u is not None and not implicit:
+            aPsi1, aPsi0 = aPsi0 - 2.0 * dt * TT(arhs), dt * TT(arhs)
         new_aPhi1 = aPhi0 - B1 * arhs
         new_aPhi0 = -B2 * arhs
         # h = sum_j w_j mu_j c_j (b1 phi_j^n + b2 phi_j^{n-1}); phi_j^{n+1} = c_j (-b1 phi_j^n - b2 phi_j^{n-1} + ...)

@@ -1,6 +1,7 @@
 """The oracle's reference adjoint in the paper's variable
 (oracle.paper_form.paper_gradients: a plain reverse sweep of the step of
-Section 3.4, pointwise law, BDF2 start, frozen velocity gradient) pinned to
+Section 3.4, BDF2 start, frozen velocity gradient; pointwise, explicit or
+implicit transport) pinned to
 central differences of the oracle's own forward, every entry of every
 gradient field: exactly along Phi(0) (Psi(T) is affine in it), to the
 differences' O(h^2) truncation in kappa, Wi and beta."""
@@ -12,22 +13,35 @@ from oracle.paper_form import PaperForm, paper_gradients
 from paper_2411_17294_gb300 import inputs
 
 
-@pytest.mark.parametrize("dim,n,alpha,m,steps", [(2, (4, 3), 0.5, 5, 6), (3, (2, 2, 3), 0.3, 4, 5),
-                                                 (2, (3, 3), 0.7, 8, 1)])
-def test_paper_gradients_against_central_differences(dim, n, alpha, m, steps):
+CASES = [
+    # dim, n, alpha, m, steps, transport (None, "explicit", "implicit"), stencil, eps, velocity scale
+    (2, (4, 3), 0.5, 5, 6, None, 0, 0.0, 0.0),
+    (3, (2, 2, 3), 0.3, 4, 5, None, 0, 0.0, 0.0),
+    (2, (3, 3), 0.7, 8, 1, None, 0, 0.0, 0.0),
+    (2, (4, 3), 0.5, 5, 5, "explicit", 0, 0.0, 0.3),
+    (3, (2, 3, 2), 0.5, 5, 5, "explicit", 1, 0.01, 0.3),
+    (2, (4, 3), 0.5, 5, 5, "implicit", 1, 0.01, 2.0),
+    (3, (2, 3, 2), 0.4, 4, 4, "implicit", 0, 0.0, 3.0),
+]
+
+
+@pytest.mark.parametrize("dim,n,alpha,m,steps,transport,stencil,eps,speed", CASES)
+def test_paper_gradients_against_central_differences(dim, n, alpha, m, steps, transport, stencil, eps, speed):
     N = int(np.prod(n))
     dt, Wi, beta, Re = 4e-3, 1.3, 0.4, 1.7
     mu, w = soe.soe_nnls(1 - alpha, dt, 50 * dt, m)
-    _, kap = inputs.spectral_velocity(dim, n, 1, seed=3)
+    u, kap = inputs.spectral_velocity(dim, n, 1, seed=3)
     kap = 0.6 * np.asarray(kap)
+    u = speed * np.asarray(u) if transport else None
     P0 = inputs.random_stress(dim, n, 4)
     dJ = np.random.default_rng(5).normal(size=P0.shape)
-    g = paper_gradients(dim, N, Wi, beta, dt, mu, w, P0, kap, steps, dJ, Re=Re)
+    tk = dict(grid=n, eps=eps, stencil=stencil, implicit=transport == "implicit")
+    g = paper_gradients(dim, N, Wi, beta, dt, mu, w, P0, kap, steps, dJ, Re=Re, u=u, **tk)
 
     def J(P, k, Wi_, b_):
-        pf = PaperForm(dim, N, Wi_, b_, dt, mu, w, Phi0=P, Re=Re)
+        pf = PaperForm(dim, N, Wi_, b_, dt, mu, w, Phi0=P, Re=Re, **tk)
         for _ in range(steps):
-            psi = pf.step(k, k)
+            psi = pf.step(k, k, u)
         return float(np.sum(dJ * psi))
 
     assert np.isclose(J(P0, kap, Wi, beta), float(np.sum(dJ * g["Psi_T"])), rtol=1e-14)
@@ -48,4 +62,8 @@ def test_paper_gradients_against_central_differences(dim, n, alpha, m, steps):
     fdB = (J(P0, kap, Wi, beta + h) - J(P0, kap, Wi, beta - h)) / (2 * h)
     assert abs(g["Wi"] - fdW) <= 1e-7 * abs(fdW)
     assert abs(g["beta"] - fdB) <= 1e-7 * abs(fdB)
+    if transport:
+        # the transport changes the gradient, so its adjoint is what the pins see
+        g0 = paper_gradients(dim, N, Wi, beta, dt, mu, w, P0, kap, steps, dJ, Re=Re)
+        assert np.max(np.abs(g0["Phi0"] - g["Phi0"])) > 1e-3 * np.max(np.abs(g["Phi0"]))
 
