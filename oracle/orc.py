@@ -263,3 +263,103 @@ def gradients(prob: Problem, sigma0, kap, u, steps: int, dJ_dsigma_T) -> dict:
 if __name__ == "__main__":   # pragma: no cover
     build(force=True)
     print(_LIB, file=sys.stderr)
+
+
+def gradients_implicit(prob: Problem, sigma0, kap, u, steps: int, dJ_dsigma_T) -> dict:
+    """Reverse-mode derivatives of J with dJ/dsigma(T) = dJ_dsigma_T for the
+    implicit-transport step (orc_step_implicit, BDF2 start, frozen kap [d*d][N]),
+    small grids.  Plain reverse sweep of the step, in numpy:
+
+        R   = eta sigma0 - H + dt G k g,   H = sum_j eta_j (b1 sigma_j^n + b2 sigma_j^{n-1})
+              (alpha = 1: H = b1 sigma^n + b2 sigma^{n-1} + b0 sigma0)
+        A sigma^{n+1} = R,   A = a I - dt L(kappa) + dt (u.grad - eps Lap)   (dense, over the grid)
+        sigma_j^{n+1} = c_j (-b1 sigma_j^n - b2 sigma_j^{n-1}) + rho_j (sigma^{n+1} - sigma0)
+
+    (a = eta + dt/Wi, k = kappa + kappa^T, G = (1 - beta)/(Wi Re), g = g_alpha(t_{n+1})),
+    with the transport matrix assembled from unit vectors by the stencils of
+    oracle.paper_form.transport_op.  Returns dict(sigma_T, sigma0, kappa, Wi, beta)."""
+    from .paper_form import _packed, _upper_convected, transport_op
+    from scipy.special import gamma as Gamma
+    d, N, nc, m = prob.dim, prob.N, prob.nc, prob.m
+    dt, Wi, Re = prob.dt, prob.Wi, prob.Re
+    B0, B1, B2 = 1.5, -2.0, 0.5
+    classic = prob.alpha == 1.0
+    mu = np.asarray(prob.mu, float)[:m]
+    w = np.asarray(prob.w, float)[:m]
+    c = 1.0 / (B0 + mu * dt)
+    eta_j = mu * dt * c
+    rho = w * dt * c
+    eta = B0 if classic else float(np.sum(B0 * w * dt * c))
+    a = eta + dt / Wi
+    G = (1.0 - prob.beta) / (Wi * Re)
+    kap = np.asarray(kap, float).reshape(d * d, N)
+    K = kap.T.reshape(N, d, d)
+    P = _packed(d)
+    KS = K + np.swapaxes(K, 1, 2)
+    ks = np.stack([KS[:, i, j] for (i, j) in P])
+    s0 = np.zeros((nc, N)) if sigma0 is None else np.asarray(sigma0, float).reshape(nc, N)
+    # forward, keeping sigma^{n+1}
+    o = Oracle(prob, sigma0)
+    hist = []
+    for _ in range(steps):
+        o.step(kap, kap, u)
+        hist.append(o.sig_n.copy())
+    # the dense operator and its transpose
+    L = prob.L if prob.L is not None else (2 * np.pi,) * d
+    nn = nc * N
+    A = np.zeros((nn, nn))
+    for k in range(nn):
+        e = np.zeros((nc, N))
+        e.flat[k] = 1.0
+        img = a * e - dt * _upper_convected(d, K, e) + dt * transport_op(d, prob.n, L, prob.eps, prob.stencil, e, u)
+        A[:, k] = img.ravel()
+    AT = A.T
+
+    def dL_dot(v, X):
+        out = np.zeros((d * d, N))
+        for ia in range(d):
+            for ib in range(d):
+                E = np.zeros((N, d, d))
+                E[:, ia, ib] = 1.0
+                out[ia * d + ib] = np.sum(v * _upper_convected(d, E, X), axis=0)
+        return out
+
+    a1 = np.asarray(dJ_dsigma_T, float).reshape(nc, N).copy()   # adjoint of sigma^{n+1} (full)
+    a0 = np.zeros((nc, N))                                     # partial adjoint of sigma^n
+    z1 = np.zeros((m, nc, N))                                  # adjoint of sigma_j^{n+1}
+    z0 = np.zeros((m, nc, N))                                  # partial adjoint of sigma_j^n
+    g_s0 = np.zeros((nc, N))
+    g_kap = np.zeros((d * d, N))
+    gWi = gbeta = 0.0
+    for n in range(steps - 1, -1, -1):
+        sig_new = hist[n]
+        g = 1.0 if classic else (n + 1) ** (prob.alpha - 1.0) * dt ** (prob.alpha - 1.0) / Gamma(prob.alpha)
+        # sigma_j^{n+1} = c_j (...) + rho_j (sigma^{n+1} - sigma0)
+        a_sig = a1 + np.tensordot(rho, z1, axes=(0, 0))
+        g_s0 -= np.tensordot(rho, z1, axes=(0, 0))
+        # A sigma^{n+1} = R
+        ar = np.linalg.solve(AT, a_sig.ravel()).reshape(nc, N)
+        # R = eta sigma0 - H + dt G k g
+        g_s0 += eta * ar
+        if classic:
+            new_a1 = a0 - B1 * ar
+            new_a0 = -B2 * ar
+            g_s0 -= B0 * ar
+        else:
+            new_a1 = a0.copy()
+            new_a0 = np.zeros((nc, N))
+        new_z1 = z0 - B1 * eta_j[:, None, None] * ar[None] - B1 * c[:, None, None] * z1
+        new_z0 = -B2 * eta_j[:, None, None] * ar[None] - B2 * c[:, None, None] * z1
+        # parameters: A through kappa and Wi (a), R through G and k
+        g_kap += dt * dL_dot(ar, sig_new)
+        for ia in range(d):
+            for ib in range(d):
+                dks = np.zeros((nc, N))
+                for cc, (i, j) in enumerate(P):
+                    dks[cc] = (1.0 if (i, j) == (ia, ib) else 0.0) + (1.0 if (j, i) == (ia, ib) else 0.0)
+                g_kap[ia * d + ib] += dt * G * g * np.sum(ar * dks, axis=0)
+        gWi += dt / Wi ** 2 * np.sum(ar * sig_new) - dt * (G / Wi) * g * np.sum(ar * ks)
+        gbeta += -dt * g * np.sum(ar * ks) / (Wi * Re)
+        a1, a0, z1, z0 = new_a1, new_a0, new_z1, new_z0
+    g_s0 += a1 + a0            # sigma^0 = sigma^{-1} = sigma0
+    return dict(sigma_T=hist[-1], sigma0=g_s0, kappa=g_kap, Wi=gWi, beta=gbeta)

@@ -69,6 +69,34 @@ def _upper_convected(dim, K, s):
     return np.stack([T[:, i, j] for (i, j) in P])
 
 
+def transport_op(dim, grid, L, eps, stencil, E, u):
+    """sum_a u_a D_a E - eps Lap E for E [nc][N], u [d][N] on the periodic grid
+    (x fastest), box lengths L: D_a upwind-biased third order (radius 2, biased
+    by the sign of u_a at the point; stencil 0) or central second order
+    (stencil 1), Lap the three-point Laplacian per axis (numpy.roll)."""
+    d = dim
+    nc = E.shape[0]
+    shp = (nc,) + tuple(reversed(grid))                          # [nc][(z)][y][x]
+    F = E.reshape(shp)
+    U = np.asarray(u, float).reshape((d,) + tuple(reversed(grid)))
+    out = np.zeros(shp)
+    for a in range(d):
+        ax = F.ndim - 1 - a                                      # x is the last array axis
+        h = L[a] / grid[a]
+        at = lambda k: np.roll(F, -k, axis=ax)                   # F at offset k along axis a
+        ua = U[a][None]
+        if stencil == 1:
+            D = (at(1) - at(-1)) / (2 * h)
+        else:
+            fw = (at(-2) - 6 * at(-1) + 3 * F + 2 * at(1)) / (6 * h)
+            bw = (-2 * at(-1) - 3 * F + 6 * at(1) - at(2)) / (6 * h)
+            D = np.where(ua >= 0, fw, bw)
+        out += ua * D
+        if eps != 0.0:
+            out -= eps * (at(-1) - 2 * F + at(1)) / h ** 2
+    return out.reshape(nc, -1)
+
+
 class PaperForm:
     """State of the paper-variable scheme on a set of independent points."""
 
@@ -161,26 +189,7 @@ class PaperForm:
 
     def _transport_op(self, E, u):
         """sum_a u_a D_a E - eps Lap E for E [nc][N], u [d][N], periodic."""
-        d = self.dim
-        shp = (self.nc,) + tuple(reversed(self.grid))          # [nc][(z)][y][x]
-        F = E.reshape(shp)
-        U = np.asarray(u, float).reshape((d,) + tuple(reversed(self.grid)))
-        out = np.zeros(shp)
-        for a in range(d):
-            ax = F.ndim - 1 - a                                  # x is the last array axis
-            h = self.L[a] / self.grid[a]
-            at = lambda k: np.roll(F, -k, axis=ax)               # F at offset k along axis a
-            ua = U[a][None]
-            if self.stencil == 1:
-                D = (at(1) - at(-1)) / (2 * h)
-            else:
-                fw = (at(-2) - 6 * at(-1) + 3 * F + 2 * at(1)) / (6 * h)
-                bw = (-2 * at(-1) - 3 * F + 6 * at(1) - at(2)) / (6 * h)
-                D = np.where(ua >= 0, fw, bw)
-            out += ua * D
-            if self.eps != 0.0:
-                out -= self.eps * (at(-1) - 2 * F + at(1)) / h ** 2
-        return out.reshape(self.nc, self.N)
+        return transport_op(self.dim, self.grid, self.L, self.eps, self.stencil, E, u)
 
     def _solve_implicit(self, K, rhs, u, diag=B0, scale=None):
         """Solve (diag I - scale (L(K) - I/Wi)) Phi + scale T(Phi) = rhs over the grid (dense);
