@@ -408,6 +408,57 @@ def paper_form_record(dev, steps: int, warmup: int, grid: int | None = None):
             "frac": achieved / peak, "device_flags": flags}
 
 
+def fp64_record(dev, steps: int, warmup: int, grid: int | None = None):
+    """The main workload in the FP64 storage form (everything in double): time
+    per step and the HBM roofline fraction of its step kernel against the FP64
+    byte count, beside the FP32 headline (the FP32 form is the faster one)."""
+    import torch
+
+    from paper_2411_17294_gb300 import inputs, soe, tfs
+    W = dict(WORKLOAD)
+    if grid:
+        W["n"] = (grid,) * 3
+    dt = W["dt"]
+    mu, w = soe.build(W["alpha"], dt, W["horizon_steps"] * dt, W["m"])
+    u, kap = inputs.spectral_velocity(3, W["n"], W["kmax"], W["seed"], device=dev)
+    s = tfs.Solver(3, W["n"], W["alpha"], W["Wi"], W["beta"], dt, m=W["m"], precision=tfs.TFS_FP64, mu=mu, w=w,
+                   transport=True, device=dev)
+    kn = torch.as_tensor(kap, dtype=torch.float64, device=dev).contiguous()
+    km = kn.clone()
+    ut = torch.as_tensor(u, dtype=torch.float64, device=dev).contiguous()
+    del kap, u
+    stream = torch.cuda.Stream(device=dev)
+    kb = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ka = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        s.set_state(None, stream=stream)
+        for _ in range(warmup):
+            s.step(kn, km, ut, stream=stream)
+        for e in kb + ka:
+            e.record(stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(steps):
+            s.set_step_events(kb[k], ka[k])
+            s.step(kn, km, ut, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    s.set_step_events(None, None)
+    N = s.N
+    s.close()
+    launch_ms = statistics.mean(kb[k].elapsed_time(ka[k]) for k in range(steps))
+    ms = e0.elapsed_time(e1) / steps
+    bpp = step_kernel_bytes_per_point(3, W["m"], 8, transport=True)
+    peak, peak_kind = read_peaks()
+    achieved = bpp * N / (launch_ms * 1e-3) / 1e9
+    return {"workload": W["name"].replace("FP32 modes + compensated sum", "FP64 storage and arithmetic"),
+            "ms_per_step": ms, "avg_launch_ms": launch_ms,
+            "G_point_mode_updates_per_s": N * W["m"] / (ms * 1e-3) / 1e9,
+            "algorithmic_bytes_per_point": bpp, "achieved_gbs": achieved, "peak": peak, "peak_kind": peak_kind,
+            "frac": achieved / peak, "bound": "fp64 pipe (1/64 of the FP32 rate on this GPU)"}
+
+
 def max_over_ranks(local_ms: float, dist, device) -> float:
     """The slowest rank's time (all ranks get it); local_ms itself on one process."""
     if dist is None:
@@ -453,6 +504,8 @@ def main():
                     help="time only the step in the paper's variable and print its record (profiling)")
     ap.add_argument("--implicit-only", action="store_true",
                     help="time only the implicit-transport step and print its record (profiling)")
+    ap.add_argument("--fp64-only", action="store_true",
+                    help="time only the FP64 storage form of the step and print its record (profiling)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32plain"])
     ap.add_argument("--grid", type=int, default=WORKLOAD["n"][0],
                     help="cube side of the step workload (default 256; smaller sides are for profiling)")
@@ -483,6 +536,14 @@ def main():
         tbuild.build()
         torch.cuda.set_device(0)
         print(json.dumps(implicit_transport_record(torch.device("cuda", 0))), flush=True)
+        return
+    if args.fp64_only:
+        import torch
+        from paper_2411_17294_gb300 import build as tbuild
+        tbuild.build()
+        torch.cuda.set_device(0)
+        print(json.dumps(fp64_record(torch.device("cuda", 0), steps=args.steps, warmup=args.warmup,
+                                     grid=args.grid)), flush=True)
         return
     if args.paper_only:
         import torch
@@ -527,6 +588,8 @@ def main():
     kap_nm1 = kap_n.clone()          # frozen velocity, but a distinct buffer: both levels are read
     u = torch.as_tensor(u64, dtype=tdt, device=dev).contiguous()
     del u64, kap64
+    U_lim = s.transport_limit()
+    courant = float(u.double().abs().sum(dim=0).max()) / (3 * U_lim) if U_lim > 0 else float("inf")
     stream = torch.cuda.Stream(device=dev)
     N = s.N
     elem = 8 if prec == tfs.TFS_FP64 else 4
@@ -611,6 +674,13 @@ def main():
         except Exception as exc:  # pragma: no cover - reported, not fatal
             paper = {"error": str(exc)}
 
+    fp64 = None
+    if not args.no_adjoint and prec != tfs.TFS_FP64:
+        try:
+            fp64 = fp64_record(dev, steps=5, warmup=3, grid=args.grid)
+        except Exception as exc:  # pragma: no cover - reported, not fatal
+            fp64 = {"error": str(exc)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         try:
@@ -632,17 +702,27 @@ def main():
                        "points_per_gpu": N},
             "roofline": {"bound": "hbm", "kernel": "fwd_kernel<float,3> (step kernel)", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "traffic_source": "ncu dram__bytes of the committed capture, used only while the "
+                                           "step kernel's sources hash to the captured ones (else null)",
                          "peak_kind": peak_kind, "algorithmic_bytes_per_point": bytes_pp,
                          "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": avg_launch_s * 1e3,
                          "step_share": sum(launch_ms) / total_ms,
                          "whole_step_gbs": algorithmic_bytes_per_point(3, W["m"], elem) * N / (ms_per_step * 1e-3) / 1e9},
             "gpu_launches": launches_per_step * args.steps,
             "device_flags": flags,
+            "stability": {
+                "explicit_courant_fraction": courant,
+                "note": ("inside the explicit transport's stability region" if courant <= 1.0 else
+                         "the velocity exceeds the explicit transport's stability limit (TFS_FLAG_COURANT, "
+                         "device_flags & 4): bytes and work per step do not depend on it, but a long run of "
+                         "this workload needs the implicit transport (transport=2); the test-suite checks the "
+                         "200-step workload pointwise and at a velocity inside the limit")},
             "clocks": clocks,
             "e2e": e2e,
             "adjoint_forward": adj,
             "implicit_transport": imp,
             "paper_form": paper,
+            "fp64_form": fp64,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

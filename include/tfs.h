@@ -151,7 +151,13 @@ typedef struct {
     double L[3];    /* box lengths > 0 */
 } tfs_grid;
 
-/* Create a handle.  alpha in (0, 1]; Wi > 0; beta in [0, 1); dt > 0;
+/* Create a handle for the problem of Section 4.1 on the periodic grid:
+   fractional order alpha and Weissenberg number Wi of the time-fractional
+   Fokker-Planck equation (eq. timefractionalFokkerPlanck; Wi the relaxation
+   time, the paper's 2 De), solvent fraction beta of the momentum equation
+   (eq. Navier_Stokes: G = (1 - beta)/(Wi Re) scales the stress source), m
+   kernel-compression modes (Section 2.2) and the step dt of eq.
+   BDF_and_extrapolation.  alpha in (0, 1]; Wi > 0; beta in [0, 1); dt > 0;
    0 <= m <= 64 (m = 0 required when alpha == 1, m >= 1 otherwise);
    precision one of TFS_FP64, TFS_FP32, TFS_FP32_PLAIN.  No device memory is
    allocated.  On error *h is set to NULL. */
@@ -163,7 +169,8 @@ int tfs_create(tfs_handle* h, const tfs_grid* grid, double alpha, double Wi, dou
    limit of tfs_transport_limit returns TFS_ERR_UNSTABLE (and is not set). */
 int tfs_set_param(tfs_handle h, int key, double value);
 
-/* Copy the SOE table: exponents mu_j >= 0 and weights w_j >= 0 (finite),
+/* Kernel compression of Section 2.2 (eq. tf_approximate_kernel).
+   Copy the SOE table: exponents mu_j >= 0 and weights w_j >= 0 (finite),
    j < m, approximating t^-alpha/Gamma(1-alpha) by sum_j w_j exp(-mu_j t)
    (Section 2.2).  Host arrays, copied; m must equal the handle's m.
    Precomputes c_j = 1/(b0 + mu_j dt), rho_j = w_j dt c_j, eta_j = mu_j dt c_j
@@ -189,18 +196,31 @@ size_t tfs_workspace_bytes(tfs_handle h);
    256-byte aligned.  The library never frees it. */
 int tfs_bind_workspace(tfs_handle h, void* dev_ptr, size_t bytes);
 
-/* Start from rest: sigma^0 = sigma^{-1} = sigma0 (NULL = zero stress), all
-   modes zero, step counter 0, status flags cleared. */
+/* Initial conditions of eq. amnsfp_initial_conditions: the stress (or Phi
+   with TFS_FORM_PAPER) starts at sigma0 [nc][N] (device, element type of the
+   handle; NULL = zero stress, the paper's start from rest) and every
+   fractional mode at zero; sigma^{-1} = sigma^0 (the empty past of the BDF2
+   start), step counter 0, status flags cleared.  TFS_ERR_NOWORKSPACE without
+   a workspace; enqueues on `stream`. */
 int tfs_set_state(tfs_handle h, const void* sigma0, void* stream);
 
-/* One step t_n -> t_{n+1}.  grad_u_n = kappa^n, grad_u_nm1 = kappa^{n-1}
-   (NULL = same as grad_u_n); u = velocity [d][N] (NULL allowed when transport
-   is off).  Enqueues the step kernel, preceded by the transport pre-pass when
-   transport is on. */
+/* One step t_n -> t_{n+1} of eq. FP_discrete with the mode push-forward of
+   eq. BDF_Phi_k_n+1 and the extrapolated gradient kappa* = 2 kappa^n -
+   kappa^{n-1} of eq. BDF_and_extrapolation.  grad_u_n = kappa^n, grad_u_nm1
+   = kappa^{n-1} [d*d][N] (NULL = same as grad_u_n); u = velocity [d][N]
+   (NULL allowed when transport is off); device pointers of the handle's
+   element type, read only.  Enqueues the step kernel, preceded by the
+   transport pre-pass when transport is explicit (transport 2: the Krylov
+   solve, which synchronises `stream`).  TFS_ERR_STATE before tfs_set_state,
+   TFS_ERR_NOSOE without a table, TFS_ERR_UNSTABLE when a declared velocity
+   bound exceeds the explicit limit, TFS_ERR_CUDA on a failed launch. */
 int tfs_step(tfs_handle h, const void* grad_u_n, const void* grad_u_nm1, const void* u, void* stream);
 
-/* Copy the current stress sigma^n to out [nc][N] (device); with TFS_FORM_PAPER
-   the stress Psi^n. */
+/* Copy the current polymer stress to out [nc][N] (device, caller-owned,
+   element type of the handle): sigma^n, the degree-2 part of Psi of eq.
+   mm_ExtraStress in the packed units of eq. mm_coupling_order2; with
+   TFS_FORM_PAPER the stress Psi^n = D^{1-alpha} Phi^n.  Enqueues a copy on
+   `stream`; TFS_ERR_STATE before tfs_set_state. */
 int tfs_get_stress(tfs_handle h, void* out, void* stream);
 
 /* Measurement hook (no counterpart in the paper): with two cudaEvent_t
@@ -245,7 +265,10 @@ int tfs_load(tfs_handle h, const void* src, void* stream);
 size_t tfs_adjoint_workspace_bytes(tfs_handle h, int segment_steps);
 int tfs_bind_adjoint_workspace(tfs_handle h, void* dev_ptr, size_t bytes);
 
-/* Reverse-mode derivative of J(sigma^T) for a run of `steps` steps from the
+/* Adjoint of the scheme of eq. FP_discrete / eq. BDF_Phi_k_n+1 (the paper
+   computes no gradients: this is the exact reverse of the discrete steps that
+   tfs_step takes).
+   Reverse-mode derivative of J(sigma^T) for a run of `steps` steps from the
    state set by tfs_set_state, with a frozen velocity gradient grad_u [d*d][N]
    (and velocity u when transport is on), given dJ/dsigma(T) [nc][N] (element
    type of the handle).  checkpoints[k] must hold tfs_save of step k*K for
@@ -281,17 +304,29 @@ int tfs_destroy(tfs_handle h);
    s = element size, up256 = round up to 256) return TFS_ERR_TOOBIG before any
    device work.  Arguments as tfs_create / tfs_set_soe (mu, w: host, m
    entries, NULL when alpha == 1); Re = 1, eps = 0, upwind3 stencil, transport
-   on iff u != NULL, no Courant check; sigma0 [nc][N] (NULL = zero), grad_u
+   on iff u != NULL (points beyond the velocity limit of tfs_transport_limit
+   latch TFS_FLAG_COURANT; nothing is refused); sigma0 [nc][N] (NULL = zero), grad_u
    [d*d][N] frozen for all steps, sigma_out [nc][N]: device pointers of the
    precision's element type.  Enqueues on `stream` and returns; the result is
    in sigma_out once the stream reaches it.  The array's device address is
    looked up on the first call on each device (with that device current): make
    that first call before any stream capture.  Every call shares the array and
    clears it at its start, so calls whose GPU work overlaps (other streams or
-   host threads) race and must not be issued.  Allocates nothing. */
+   host threads) race and must not be issued.  The device flags its kernels
+   latch (TFS_FLAG_*) stay in the array: read them with tfs_static_status.
+   Allocates nothing. */
 int tfs_run_static(const tfs_grid* grid, double alpha, double Wi, double beta, int m, double dt,
                    int precision, const double* mu, const double* w, const void* sigma0,
                    const void* grad_u, const void* u, int steps, void* sigma_out, void* stream);
+
+/* Device flags (TFS_FLAG_*) latched by the most recent tfs_run_static on the
+   current device, which has no handle to ask through tfs_status: a non-finite
+   result, a near-singular point system, the Courant limit exceeded, or a
+   bounded wait that gave up.  Synchronises `stream` (pass the stream of that
+   run) and copies the word from the library's fixed array into
+   *device_flags; allocates nothing.  The paper has no counterpart.
+   TFS_ERR_ARG for NULL, TFS_ERR_CUDA if the copy fails. */
+int tfs_static_status(unsigned* device_flags, void* stream);
 
 #ifdef __cplusplus
 }

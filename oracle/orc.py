@@ -17,6 +17,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+from .paper_form import packed_pairs, transport_op, upper_convected
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tfs_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
@@ -260,11 +262,6 @@ def gradients(prob: Problem, sigma0, kap, u, steps: int, dJ_dsigma_T) -> dict:
                 Wi=g_Wi.value, beta=g_beta.value)
 
 
-if __name__ == "__main__":   # pragma: no cover
-    build(force=True)
-    print(_LIB, file=sys.stderr)
-
-
 def gradients_implicit(prob: Problem, sigma0, kap, u, steps: int, dJ_dsigma_T) -> dict:
     """Reverse-mode derivatives of J with dJ/dsigma(T) = dJ_dsigma_T for the
     implicit-transport step (orc_step_implicit, BDF2 start, frozen kap [d*d][N]),
@@ -278,7 +275,6 @@ def gradients_implicit(prob: Problem, sigma0, kap, u, steps: int, dJ_dsigma_T) -
     (a = eta + dt/Wi, k = kappa + kappa^T, G = (1 - beta)/(Wi Re), g = g_alpha(t_{n+1})),
     with the transport matrix assembled from unit vectors by the stencils of
     oracle.paper_form.transport_op.  Returns dict(sigma_T, sigma0, kappa, Wi, beta)."""
-    from .paper_form import _packed, _upper_convected, transport_op
     from scipy.special import gamma as Gamma
     d, N, nc, m = prob.dim, prob.N, prob.nc, prob.m
     dt, Wi, Re = prob.dt, prob.Wi, prob.Re
@@ -294,7 +290,7 @@ def gradients_implicit(prob: Problem, sigma0, kap, u, steps: int, dJ_dsigma_T) -
     G = (1.0 - prob.beta) / (Wi * Re)
     kap = np.asarray(kap, float).reshape(d * d, N)
     K = kap.T.reshape(N, d, d)
-    P = _packed(d)
+    P = packed_pairs(d)
     KS = K + np.swapaxes(K, 1, 2)
     ks = np.stack([KS[:, i, j] for (i, j) in P])
     s0 = np.zeros((nc, N)) if sigma0 is None else np.asarray(sigma0, float).reshape(nc, N)
@@ -311,7 +307,7 @@ def gradients_implicit(prob: Problem, sigma0, kap, u, steps: int, dJ_dsigma_T) -
     for k in range(nn):
         e = np.zeros((nc, N))
         e.flat[k] = 1.0
-        img = a * e - dt * _upper_convected(d, K, e) + dt * transport_op(d, prob.n, L, prob.eps, prob.stencil, e, u)
+        img = a * e - dt * upper_convected(d, K, e) + dt * transport_op(d, prob.n, L, prob.eps, prob.stencil, e, u)
         A[:, k] = img.ravel()
     AT = A.T
 
@@ -321,7 +317,7 @@ def gradients_implicit(prob: Problem, sigma0, kap, u, steps: int, dJ_dsigma_T) -
             for ib in range(d):
                 E = np.zeros((N, d, d))
                 E[:, ia, ib] = 1.0
-                out[ia * d + ib] = np.sum(v * _upper_convected(d, E, X), axis=0)
+                out[ia * d + ib] = np.sum(v * upper_convected(d, E, X), axis=0)
         return out
 
     a1 = np.asarray(dJ_dsigma_T, float).reshape(nc, N).copy()   # adjoint of sigma^{n+1} (full)
@@ -363,3 +359,8 @@ def gradients_implicit(prob: Problem, sigma0, kap, u, steps: int, dJ_dsigma_T) -
         a1, a0, z1, z0 = new_a1, new_a0, new_z1, new_z0
     g_s0 += a1 + a0            # sigma^0 = sigma^{-1} = sigma0
     return dict(sigma_T=hist[-1], sigma0=g_s0, kappa=g_kap, Wi=gWi, beta=gbeta)
+
+
+if __name__ == "__main__":   # pragma: no cover
+    build(force=True)
+    print(_LIB, file=sys.stderr)

@@ -9,7 +9,10 @@ Phi with a time derivative on Phi and the fractional operator on the right:
 
 D^{1-alpha} f = d/dt (g_alpha * f) with g_alpha(t) = t^(alpha-1)/Gamma(alpha)
 (Section 1).  For the degree-2 block, in the stress units of the oracle's
-stress form (reading G1-G3),
+stress form (the coupling of eq. mm_coupling_order2 with relaxation rate 1/Wi,
+Wi the relaxation time, and the Oldroyd-B source sqrt2 kappa_ii on the
+diagonal entries of eq. conf_op_tested, which is kappa + kappa^T in stress
+units),
 
     d Phi2/dt = L(kappa) Psi2 - Psi2/Wi + G (kappa + kappa^T) Psi0,   L(k) s = k s + s k^T,
 
@@ -53,13 +56,13 @@ import numpy as np
 B0, B1, B2 = 1.5, -2.0, 0.5
 
 
-def _packed(dim):
+def packed_pairs(dim):
     return [(0, 0), (0, 1), (1, 1)] if dim == 2 else [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
 
 
-def _upper_convected(dim, K, s):
+def upper_convected(dim, K, s):
     """L(K) s for packed symmetric s, K [N, d, d], s [nc, N] -> [nc, N]."""
-    P = _packed(dim)
+    P = packed_pairs(dim)
     N = s.shape[1]
     S = np.zeros((N, dim, dim))
     for c, (i, j) in enumerate(P):
@@ -142,7 +145,7 @@ class PaperForm:
         for k in range(nc):
             e = np.zeros((nc, N))
             e[k] = 1.0
-            M[:, :, k] = (e - scale * (_upper_convected(d, K, e) - e / self.Wi)).T
+            M[:, :, k] = (e - scale * (upper_convected(d, K, e) - e / self.Wi)).T
         return np.linalg.solve(M, rhs.T[..., None])[..., 0].T
 
     def _sdirk2_first_step(self, K, u=None):
@@ -158,14 +161,14 @@ class PaperForm:
         g = 1.0 - np.sqrt(0.5)
         den = 1.0 + g * self.mu * dt
         xi1 = np.sum(self.w / den)
-        P = _packed(d)
+        P = packed_pairs(d)
         KS = K + np.swapaxes(K, 1, 2)
         src = np.stack([KS[:, i, j] for (i, j) in P])
         ZPhi, Zphi, Zphi0 = self.Phi_n.copy(), self.phi_n.copy(), self.phi0_n.copy()
         for stage in (1, 2):
             h1 = np.tensordot(self.w * self.mu / den, Zphi, axes=(0, 0))
             psi0 = xi1 - float(np.sum(self.w * self.mu * Zphi0 / den))
-            Lh = _upper_convected(d, K, h1) - h1 / self.Wi
+            Lh = upper_convected(d, K, h1) - h1 / self.Wi
             rhs = ZPhi - g * dt * Lh + g * dt * self.G * src * psi0
             if u is not None:
                 Phi = self._solve_implicit(K, rhs + g * dt * self._transport_op(h1, u), u, 1.0, g * dt * xi1)
@@ -202,7 +205,7 @@ class PaperForm:
         for k in range(n):
             e = np.zeros((nc, N))
             e.flat[k] = 1.0
-            img = diag * e - scale * (_upper_convected(d, K, e) - e / self.Wi)
+            img = diag * e - scale * (upper_convected(d, K, e) - e / self.Wi)
             img = img + scale * self._transport_op(e, u)
             A[:, k] = img.ravel()
         return np.linalg.solve(A, rhs.ravel()).reshape(nc, N)
@@ -236,8 +239,8 @@ class PaperForm:
         psi0 = self.xi * 1.0 + h0
         # degree 2
         h = self._h(self.phi_n, self.phi_nm1)
-        Lh = _upper_convected(d, K, h) - h / self.Wi
-        P = _packed(d)
+        Lh = upper_convected(d, K, h) - h / self.Wi
+        P = packed_pairs(d)
         KS = K + np.swapaxes(K, 1, 2)
         src = np.stack([KS[:, i, j] for (i, j) in P])
         rhs = -B1 * self.Phi_n - B2 * self.Phi_nm1 + dt * Lh + dt * self.G * src * psi0
@@ -251,7 +254,7 @@ class PaperForm:
             for k in range(nc):
                 e = np.zeros((nc, N))
                 e[k] = 1.0
-                img = B0 * e - dt * self.xi * (_upper_convected(d, K, e) - e / self.Wi)
+                img = B0 * e - dt * self.xi * (upper_convected(d, K, e) - e / self.Wi)
                 M[:, :, k] = img.T
             Phi = np.linalg.solve(M, rhs.T[..., None])[..., 0].T
         phi_new = self.c[:, None, None] * (-B1 * self.phi_n - B2 * self.phi_nm1 + dt * Phi[None])
@@ -295,7 +298,7 @@ def paper_gradients(dim, N, Wi, beta, dt, mu, w, Phi0, kap, steps, dJ, Re=1.0, u
     G = (1.0 - beta) / (Wi * Re)
     kap = np.asarray(kap, float).reshape(d * d, N)
     K = kap.T.reshape(N, d, d)
-    P = _packed(d)
+    P = packed_pairs(d)
     KS = K + np.swapaxes(K, 1, 2)
     ks = np.stack([KS[:, i, j] for (i, j) in P])
     # forward, keeping what the reverse sweep reads
@@ -322,7 +325,7 @@ def paper_gradients(dim, N, Wi, beta, dt, mu, w, Phi0, kap, steps, dJ, Re=1.0, u
     for k in range(nc):
         e = np.zeros((nc, N))
         e[k] = 1.0
-        M[:, :, k] = (B0 * e - dt * xi * (_upper_convected(d, K, e) - e / Wi)).T
+        M[:, :, k] = (B0 * e - dt * xi * (upper_convected(d, K, e) - e / Wi)).T
     Mt = np.swapaxes(M, 1, 2)
     AT = None
     if u is not None and implicit:
@@ -330,7 +333,7 @@ def paper_gradients(dim, N, Wi, beta, dt, mu, w, Phi0, kap, steps, dJ, Re=1.0, u
         for k in range(nn):
             e = np.zeros((nc, N))
             e.flat[k] = 1.0
-            A[:, k] = (B0 * e - dt * xi * (_upper_convected(d, K, e) - e / Wi)).ravel()
+            A[:, k] = (B0 * e - dt * xi * (upper_convected(d, K, e) - e / Wi)).ravel()
         A += dt * xi * Tm
         AT = A.T
 
@@ -340,7 +343,7 @@ def paper_gradients(dim, N, Wi, beta, dt, mu, w, Phi0, kap, steps, dJ, Re=1.0, u
         for k in range(nc):
             e = np.zeros((nc, N))
             e[k] = 1.0
-            out[k] = np.sum(_upper_convected(d, K, e) * v, axis=0)
+            out[k] = np.sum(upper_convected(d, K, e) * v, axis=0)
         return out
 
     def dL_dot(v, X):
@@ -350,7 +353,7 @@ def paper_gradients(dim, N, Wi, beta, dt, mu, w, Phi0, kap, steps, dJ, Re=1.0, u
             for b in range(d):
                 E = np.zeros((N, d, d))
                 E[:, a, b] = 1.0
-                out[a * d + b] = np.sum(v * _upper_convected(d, E, X), axis=0)
+                out[a * d + b] = np.sum(v * upper_convected(d, E, X), axis=0)
         return out
 
     m = len(mu)

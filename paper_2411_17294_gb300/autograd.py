@@ -62,11 +62,15 @@ def fractional_stress(sigma0, grad_u, Wi, beta, *, dim, n, alpha, dt, steps, K=5
                       Re=1.0, start="bdf2", form="stress"):
     """sigma(T) after `steps` steps from sigma0 [nc, N] with the frozen velocity
     gradient grad_u [d*d, N] (and velocity u [d, N] when transport is on);
-    differentiable in sigma0, grad_u, Wi and beta (0-d tensors).  start:
-    "bdf2" (empty past) or "sdirk2" (the paper's first step; pointwise law).
-    form="paper": the paper's variable (Section 3.4; sigma0 is Phi(0), the
-    result Psi(T), mu/w the SOE of the kernel of order 1 - alpha; explicit
-    transport with the BDF2 start, either start without transport)."""
+    differentiable in sigma0, grad_u, Wi and beta (0-d tensors).
+    transport: False (pointwise law), True or "explicit", or "implicit" (u.grad
+    and eps Lap inside the global solve; the reverse sweep solves the
+    transposed system).  start: "bdf2" (empty past) or "sdirk2" (the paper's
+    first step), which takes the pointwise law or implicit transport (the
+    library refuses it with explicit transport).  form="paper": the paper's
+    variable (Section 3.4; sigma0 is Phi(0), the result Psi(T), mu/w the SOE of
+    the kernel of order 1 - alpha), with every transport mode and start that
+    the stress form takes."""
     cfg = dict(dim=dim, n=tuple(n), alpha=alpha, dt=dt, steps=int(steps), K=int(K), mu=mu, w=w,
                precision=precision, transport=(u is not None) if transport is None else transport, eps=eps,
                stencil=stencil, L=L, Re=Re, start=start, form=form)

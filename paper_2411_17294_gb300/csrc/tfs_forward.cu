@@ -8,24 +8,27 @@
 //   solve (eta + dt/Wi) s - dt (kappa* s + s kappa*^T) = R   -> sigma^{n+1}
 //   sigma_j^{n+1} = -c_j (b1 sigma_j^n + b2 sigma_j^{n-1}) + rho_j (sigma^{n+1} - sigma0)
 //
-// Structure.  When transport is on, a small pre-pass (transport_kernel)
-// evaluates the stencil term A at every point (one thread per point, all
-// components) and the step kernel reads it like any other per-point input.
-// The step kernel is persistent: each block loops over tiles of 32 consecutive
-// points, and everything a tile reads -- the m x nc (mode, component) planes of
-// both levels, kappa^n, kappa^{n-1}, A, sigma0, and for alpha = 1 the stress
-// levels -- is copied global -> shared with cp.async (16-byte chunks,
-// zero-filled past the end of the grid) while the previous tile is computed.
-// The mode stream (94% of the bytes) and every per-point input are therefore
-// in flight without holding registers, and the compute phase makes no global
-// loads.  Inside a tile, warp c handles stress component c (lane = point): it
-// forms Q_j = b1 x + b2 y from shared memory (stored back in place of the
-// older level), the history sum H (FP32 storage: Kahan summation of terms
-// formed exactly by FMA, eta_j split hi + lo) and its component of the
-// right-hand side.  Warp 0 then solves
-// the 32 point systems with lane = point; all warps write the new mode level
-// from the Q_j kept in shared memory.  Every mode value is read once and
-// written once.
+// Structure.  When transport is on, a pre-pass evaluates the stencil term A
+// at every point (transport_tiled: a 32 x 8 tile of E = 2 sigma^n - sigma^{n-1}
+// with a 2-cell halo in shared memory, marching over z with the z taps in
+// registers; transport_kernel, one thread per point, for grids that do not
+// tile) and the step kernel reads it like any other per-point input.  The
+// step kernel is persistent: each block of 3 warps loops over tiles of 32
+// consecutive points, and everything a tile reads -- the m x nc (mode,
+// component) planes of both levels, kappa^n, kappa^{n-1}, A, sigma0, and for
+// alpha = 1 (or the paper's variable) the two levels of the carried field --
+// is staged global -> shared by TMA (cp.async.bulk.tensor.2d, one thread
+// issues, completion on mbarriers with bounded waits) or, on grids whose plane
+// length is not a multiple of 16 bytes, by cp.async.  The mode stream (94% of
+// the bytes) and every per-point input are in flight without holding
+// registers, and the compute phase makes no global loads.  Inside a tile,
+// warp w handles stress components w and w + 3 in 3D (w in 2D), lane = point:
+// it forms Q_j = b1 x + b2 y from shared memory, the history sum H (FP32
+// storage: Kahan summation of terms formed exactly by FMA, eta_j split
+// hi + lo) and its components of the right-hand side.  Warp 0 then solves the
+// 32 point systems with lane = point; all warps write the new mode level from
+// the Q_j with streaming stores.  Every mode value is read once and written
+// once.
 //
 // Point solve.  FP64 storage: FP64 Gaussian elimination with partial
 // pivoting.  FP32 storage: FP32 LU with partial pivoting, one refinement step

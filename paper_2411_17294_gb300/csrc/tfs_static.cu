@@ -12,16 +12,22 @@
 // The array is part of the library image: every GPU that loads libtfs.so holds
 // it until the process exits.  In host code its name only stands for the
 // array; the device address is looked up with cudaGetSymbolAddress once per
-// device (on the first call with that device current) and cached.  That first
-// call on a device must therefore come before any stream capture.  All calls
-// share the one array and each call starts by clearing what must start at zero
-// (modes, flags) and writing the initial stress, so calls that overlap on the
-// GPU (different streams, or host threads) race and must not be issued.
+// device and context (on the first call with that device current, and again
+// when the current context is a different one, e.g. after cudaDeviceReset)
+// and cached.  That first call on a device must therefore come before any
+// stream capture.  All calls share the one array and each call starts by
+// clearing what must start at zero (modes, flags) and writing the initial
+// stress, so calls that overlap on the GPU (different streams, or host
+// threads) race and must not be issued.  The status word the step kernels
+// latch (non-finite result, singular point system, Courant limit, a bounded
+// wait that gave up) stays in the array after the call; tfs_static_status
+// reads it.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <cmath>
 #include <mutex>
+#include <utility>
 
 #include "../../include/tfs.h"
 #include "tfs_internal.h"
@@ -37,22 +43,53 @@ __device__ __align__(256) unsigned char g_static_state[kStaticBytes];
 
 constexpr int kMaxDevices = 64;
 void* g_static_addr[kMaxDevices] = {};
+unsigned long long g_static_ctx[kMaxDevices] = {};   // context the cached address belongs to
 std::mutex g_static_mutex;
 
 size_t up256(size_t v) { return (v + kAlignS - 1) / kAlignS * kAlignS; }
 
-// Device address of g_static_state for the current device (looked up once).
+// Unique id of the calling thread's current CUDA context (0: none current, or
+// the driver does not offer the query).  Context ids are never reused, so a
+// cached address whose id differs from the current one belongs to a context
+// that no longer exists (cudaDeviceReset) or to another one.
+unsigned long long current_context_id() {
+    using CtxCur = CUresult (*)(CUcontext*);
+    using CtxId = CUresult (*)(CUcontext, unsigned long long*);
+    static const std::pair<CtxCur, CtxId> fns = [] {
+        void* a = nullptr;
+        void* b = nullptr;
+        cudaDriverEntryPointQueryResult qa = cudaDriverEntryPointSymbolNotFound, qb = qa;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) != cudaSuccess ||
+            qa != cudaDriverEntryPointSuccess)
+            a = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) != cudaSuccess ||
+            qb != cudaDriverEntryPointSuccess)
+            b = nullptr;
+        return std::pair<CtxCur, CtxId>(reinterpret_cast<CtxCur>(a), reinterpret_cast<CtxId>(b));
+    }();
+    if (!fns.first || !fns.second) return 0;
+    CUcontext c = nullptr;
+    if (fns.first(&c) != CUDA_SUCCESS || !c) return 0;
+    unsigned long long id = 0;
+    if (fns.second(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of g_static_state for the current device, looked up once per
+// device and context.
 cudaError_t static_base(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_static_mutex);
-    if (!g_static_addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_static_addr[dev] || ctx == 0 || ctx != g_static_ctx[dev]) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_state);
+        e = cudaGetSymbolAddress(&p, g_static_state);   // makes the device's primary context current
         if (e != cudaSuccess) return e;
         g_static_addr[dev] = p;
+        g_static_ctx[dev] = current_context_id();
     }
     *out = g_static_addr[dev];
     return cudaSuccess;
@@ -73,8 +110,6 @@ void fill_step_args(FwdArgs<T>& a, long long N, const long long n[3], const doub
     a.eps = 0.0;
     for (int i = 0; i < 3; ++i) a.inv_h[i] = (double)n[i] / L[i];
     a.g = alpha == 1.0 ? 1.0 : std::pow((double)(step + 1) * dt, alpha - 1.0) / std::tgamma(alpha);
-    a.courant_coef = 0.0;               // no stability check in this entry point
-    a.courant_limit = 1e300;
     auto split = [](double v) {
         F2c r;
         r.hi = (float)v;
@@ -160,6 +195,23 @@ extern "C" int tfs_run_static(const tfs_grid* grid, double alpha, double Wi, dou
         md[i] = p;
         p += up256(modes);
     }
+    // Courant flag of the explicit transport: a point is flagged when
+    // sum_a |u_a|/h_a exceeds U sum_a 1/h_a, U the velocity limit of
+    // tfs_transport_limit for this table (host computation, no device memory)
+    double ccoef = 0.0;
+    if (u) {
+        tfs_handle hh = nullptr;
+        double U = 0.0;
+        int rc = tfs_create(&hh, grid, alpha, Wi, beta, m, dt, precision);
+        if (rc == TFS_OK && alpha < 1.0) rc = tfs_set_soe(hh, mu, w, m);
+        if (rc == TFS_OK) rc = tfs_transport_limit(hh, &U);
+        if (hh) tfs_destroy(hh);
+        if (rc != TFS_OK) return rc;
+        double sih = 0.0;
+        for (int ax = 0; ax < grid->dim; ++ax) sih += (double)n[ax] / L[ax];
+        ccoef = U > 0.0 ? 1.0 / (U * sih) : 1e300;
+    }
+
     cudaStream_t s = (cudaStream_t)stream;
     const bool dbl = precision == TFS_FP64;
     cudaError_t e = launch_fill_levels(sig[0], sig[1], s0copy, sigma0, (long long)nc * N, dbl, s);
@@ -181,6 +233,8 @@ extern "C" int tfs_run_static(const tfs_grid* grid, double alpha, double Wi, dou
         if (dbl) {
             FwdArgs<double> a{};
             fill_step_args(a, N, n, L, mm, dt, eta, Wi, beta, alpha, step);
+            a.courant_coef = ccoef;
+            a.courant_limit = 1.0;
             a.kap_n = (const double*)grad_u;
             a.kap_nm1 = (const double*)grad_u;
             a.u = (const double*)u;
@@ -198,6 +252,8 @@ extern "C" int tfs_run_static(const tfs_grid* grid, double alpha, double Wi, dou
         } else {
             FwdArgs<float> a{};
             fill_step_args(a, N, n, L, mm, dt, eta, Wi, beta, alpha, step);
+            a.courant_coef = ccoef;
+            a.courant_limit = 1.0;
             a.kap_n = (const float*)grad_u;
             a.kap_nm1 = (const float*)grad_u;
             a.u = (const float*)u;
@@ -220,4 +276,17 @@ extern "C" int tfs_run_static(const tfs_grid* grid, double alpha, double Wi, dou
     }
     e = cudaMemcpyAsync(sigma_out, sig[cur], field, cudaMemcpyDeviceToDevice, s);
     return e == cudaSuccess ? TFS_OK : TFS_ERR_CUDA;
+}
+
+extern "C" int tfs_static_status(unsigned* device_flags, void* stream) {
+    if (!device_flags) return TFS_ERR_ARG;
+    void* base_v = nullptr;
+    if (static_base(&base_v) != cudaSuccess) return TFS_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned f = 0u;
+    cudaError_t e = cudaMemcpyAsync(&f, base_v, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return TFS_ERR_CUDA;
+    *device_flags = f;
+    return TFS_OK;
 }

@@ -30,7 +30,7 @@ EXPORTS = [
     "tfs_create", "tfs_set_param", "tfs_set_soe", "tfs_transport_limit", "tfs_workspace_bytes", "tfs_bind_workspace",
     "tfs_set_state", "tfs_step", "tfs_get_stress", "tfs_set_step_events", "tfs_step_index", "tfs_last_solve", "tfs_checkpoint_bytes", "tfs_save",
     "tfs_load", "tfs_adjoint_workspace_bytes", "tfs_bind_adjoint_workspace", "tfs_backward", "tfs_status",
-    "tfs_strerror", "tfs_destroy", "tfs_run_static", "tfs_check_wait_bound",
+    "tfs_strerror", "tfs_destroy", "tfs_run_static", "tfs_static_status", "tfs_check_wait_bound",
 ]
 
 
@@ -86,6 +86,7 @@ def load_library(path: str | None = None):
         "tfs_run_static": (ctypes.c_int, [ctypes.POINTER(TfsGrid), ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, dp, vp, vp, vp,
                                           ctypes.c_int, vp, vp]),
+        "tfs_static_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -4,7 +4,7 @@ checked against FP64 central finite differences of the CUDA forward itself
 import numpy as np
 import pytest
 
-from helpers import ensure_lib, stable_velocity
+from helpers import courant_fraction, ensure_lib, stable_velocity
 from oracle import soe
 from paper_2411_17294_gb300 import inputs
 
@@ -16,19 +16,29 @@ def _lib():
     ensure_lib()
 
 
-@pytest.mark.parametrize("transport,start", [(False, "bdf2"), (True, "bdf2"), (False, "sdirk2")])
-def test_autograd_matches_central_differences(transport, start):
+@pytest.mark.parametrize("transport,start,form", [
+    (False, "bdf2", "stress"), (True, "bdf2", "stress"), (False, "sdirk2", "stress"),
+    # implicit transport with the paper's first step, and in the paper's variable
+    ("implicit", "sdirk2", "stress"), ("implicit", "bdf2", "paper"), ("implicit", "sdirk2", "paper")])
+def test_autograd_matches_central_differences(transport, start, form):
     import torch
     from paper_2411_17294_gb300.autograd import fractional_stress
     dim, n, alpha, dt, steps, K, m = 2, (8, 8), 0.5, 2e-3, 30, 7, 8
-    mu, w = soe.soe_nnls(alpha, dt, steps * dt, m)
+    mu, w = soe.soe_nnls(1 - alpha if form == "paper" else alpha, dt, steps * dt, m)
     dev = torch.device("cuda", 0)
     u_np, k_np = inputs.spectral_velocity(dim, n, 2, seed=31)
-    u_np = stable_velocity(dict(dim=dim, n=n, alpha=alpha, dt=dt, mu=mu, w=w), u_np)
+    case = dict(dim=dim, n=n, alpha=alpha, dt=dt, mu=mu, w=w, transport=True)
+    if transport == "implicit":
+        # twice the explicit stress-form limit (the explicit step would be unstable)
+        mu_s, w_s = soe.soe_nnls(alpha, dt, steps * dt, m)
+        u_np = np.asarray(u_np) * (2.0 / courant_fraction(dict(case, mu=mu_s, w=w_s), u_np))
+    else:
+        u_np = stable_velocity(case, u_np)
     s0_np = inputs.random_stress(dim, n, 32)
     target = torch.as_tensor(np.random.default_rng(33).normal(size=s0_np.shape), device=dev)
     kw = dict(dim=dim, n=n, alpha=alpha, dt=dt, steps=steps, K=K, mu=mu, w=w,
-              u=torch.as_tensor(u_np, device=dev) if transport else None, start=start)
+              u=torch.as_tensor(u_np, device=dev) if transport else None, start=start, form=form,
+              transport=transport if transport == "implicit" else None)
 
     def J(s0, k, Wi, beta):
         sT = fractional_stress(s0, k, Wi, beta, **kw)

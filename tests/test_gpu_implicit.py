@@ -124,3 +124,29 @@ def test_implicit_reports_its_solve_forward_and_backward():
         grads.append(g[0].cpu().numpy())
         s.close()
     assert np.allclose(grads[0], grads[1], rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_implicit_at_thirty_times_the_explicit_limit(precision):
+    # The 2D 1024^2 implicit-transport workload runs at about 31 times the
+    # explicit Courant limit (the spectral velocity at unit RMS).  The same
+    # velocity recipe on a grid within reach of the oracle's dense solve (24^2,
+    # 1728 unknowns), with the velocity scaled to 30 times the limit: the Krylov
+    # solve still meets its tolerance and the result matches the dense solve.
+    from paper_2411_17294_gb300 import tfs
+    n, alpha, m, Wi, beta, dt, steps = (24, 24), 0.5, 16, 1.0, 0.5, 5e-4, 4
+    mu, w = soe.soe_nnls(alpha, dt, 200 * dt, m)
+    case = dict(dim=2, n=n, alpha=alpha, Wi=Wi, beta=beta, dt=dt, mu=mu, w=w, eps=0.0, stencil=0)
+    u, kap = inputs.spectral_velocity(2, n, 8, seed=2)
+    u = np.asarray(u) * (30.0 / courant_fraction(dict(case, transport=True), u))
+    assert 29.0 < courant_fraction(dict(case, transport=True), u) < 31.0
+    sigma0 = inputs.random_stress(2, n, 18)
+    if precision == 1:
+        kap, u, sigma0 = (np.asarray(a, np.float32).astype(np.float64) for a in (kap, u, sigma0))
+    prob = orc.Problem(dim=2, n=n, alpha=alpha, Wi=Wi, beta=beta, dt=dt, mu=mu, w=w, eps=0.0, stencil=0,
+                       transport=True, implicit=True)
+    ref = orc.forward(prob, sigma0, kap, u, steps)
+    got, iters, flags = gpu_run(case, sigma0, kap, u, steps, precision)
+    assert not (flags & (tfs.TFS_FLAG_NOCONV | tfs.TFS_FLAG_NONFINITE))
+    assert all(it > 0 for it, _ in iters)
+    assert np.all(rel_err_per_component(got, ref) < (1e-10 if precision == 0 else 2e-5))

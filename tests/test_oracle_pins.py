@@ -7,7 +7,8 @@ P3  (i) the mode recursion equals the full-history convolution with the exact
     below dt the scheme equals BDF2 convolution quadrature of the exact symbol
 P4  alpha = 1: Oldroyd-B relaxation exp(-t/Wi) at second order; the steady
     stress of the Lemma of Section 3.3 (Gaussian with C = I/2 - Wi D) for
-    symmetric trace-free D; the Lyapunov steady state for a general kappa
+    symmetric trace-free D; the Lyapunov steady state for a general kappa;
+    alpha = 1 - 10^-k converges to the alpha = 1 path, linearly in 1 - alpha
 P5  the full d x d tensor form stays symmetric and equals the packed form
 P6  uniform kappa and constant u give the same stress at every point
 P7  smooth start from rest: second order in dt for every alpha
@@ -171,6 +172,41 @@ def test_alpha1_lyapunov_steady_state_general_kappa():
     o = orc.Oracle(point_problem(2, 1.0, Wi, beta, 0.05))
     sT = o.run(4000, k.reshape(4, 1))
     assert np.allclose(sT[:, 0], pack(ss), rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("flow", [False, True])
+def test_alpha_to_one_limit_recovers_oldroyd_b(flow):
+    # alpha -> 1: the Caputo kernel t^-alpha/Gamma(1-alpha) tends to the Dirac
+    # delta (its mass on [0, T], T^(1-alpha)/Gamma(2-alpha), tends to 1 while its
+    # part on [dt, T] vanishes with 1/Gamma(1-alpha)), so the law becomes the
+    # Oldroyd-B equation of the paper's alpha = 1 case (eq.
+    # macroscopic_fokker_planck with D^{1-alpha} = identity; Section 5.1's
+    # classical runs).  With tables that carry the kernel's whole mass (the
+    # completing Dirac term of soe_build) the SOE scheme at alpha = 1 - 10^-k
+    # converges to the alpha = 1 scheme (plain BDF2, itself pinned above by
+    # exp(-t/Wi) and the steady states), linearly in 1 - alpha: the error drops
+    # by a factor 10 per decade.  Zero flow from sigma0 != 0 (the relaxation
+    # exp(-t/Wi) in the limit) and a constant kappa from rest (the approach to
+    # the Lyapunov steady state).
+    dim, Wi, beta, dt, steps, m = 2, 0.8, 0.6, 0.01, 200, 32
+    T = dt * steps
+    if flow:
+        kap, sig0 = np.array([[0.1, 0.4], [-0.3, -0.2]]).reshape(4, 1), None
+    else:
+        kap, sig0 = np.zeros((4, 1)), np.array([[1.0], [0.3], [0.5]])
+    ref = orc.Oracle(point_problem(dim, 1.0, Wi, beta, dt), sig0).run(steps, kap)[:, 0]
+    if not flow:
+        # the alpha = 1 path is the BDF2 relaxation (first order from sigma0 != 0, P4)
+        assert np.max(np.abs(ref - sig0[:, 0] * math.exp(-T / Wi))) < 5e-3 * np.max(np.abs(sig0))
+    errs = []
+    for k in range(1, 6):
+        alpha = 1.0 - 10.0 ** (-k)
+        mu, w = soe.soe_build(alpha, dt, T, m)
+        out = orc.Oracle(point_problem(dim, alpha, Wi, beta, dt, mu, w), sig0).run(steps, kap)[:, 0]
+        errs.append(np.max(np.abs(out - ref)) / np.max(np.abs(ref)))
+    ratios = [a / b for a, b in zip(errs, errs[1:])]
+    assert all(8.0 < r < 12.0 for r in ratios[1:]), (errs, ratios)
+    assert errs[3] < 1e-3 and errs[4] < 1e-4, errs
 
 
 # ------------------------------------------------------------------ P5
@@ -357,8 +393,9 @@ DTS_PAPER_CASE = [1 / 20, 1 / 40, 1 / 80, 1 / 160]
 
 def test_paper_first_convergence_case_bochner_norm():
     # The paper's convergence case (Section 5.1): no flow, unit square, initial
-    # stress cos(2 pi x) cos(4 pi y), eps = 1e-2, De = 0.5 (Wi = 2 De, reading
-    # G2), alpha = 0.5, T = 1, error in the weighted Bochner norm of eq.
+    # stress cos(2 pi x) cos(4 pi y), eps = 1e-2, De = 0.5 (Wi = 2 De: eq.
+    # conf_op_tested gives degree-2 modes the relaxation rate 1/De where the
+    # printed matrix has 1/(2 De)), alpha = 0.5, T = 1, error in the weighted Bochner norm of eq.
     # weighted_Bochner_space_norm, diffusion implicit as in the paper.  On the
     # periodic grid the solution is the initial field times E_alpha(-lambda_h
     # t^alpha), lambda_h = 1/Wi + eps x (discrete Laplacian symbol) -> 1/Wi +

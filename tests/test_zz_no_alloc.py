@@ -11,7 +11,7 @@ import math
 import numpy as np
 import pytest
 
-from helpers import ensure_lib, stable_velocity
+from helpers import courant_fraction, ensure_lib, stable_velocity
 from oracle import soe
 from paper_2411_17294_gb300 import inputs
 
@@ -28,6 +28,16 @@ def grid_struct(dim, n):
         g.n[a] = n[a] if a < dim else 1
         g.L[a] = 2 * math.pi if a < dim else 1.0
     return g
+
+
+def static_flags():
+    import torch
+    from paper_2411_17294_gb300 import tfs
+    lib = tfs.load_library()
+    f = ctypes.c_uint(12345)
+    rc = lib.tfs_static_status(ctypes.byref(f), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == tfs.TFS_OK, tfs.strerror(rc)
+    return f.value
 
 
 def run_static(dim, n, alpha, Wi, beta, m, dt, precision, mu, w, sigma0, kap, u, steps):
@@ -90,11 +100,37 @@ def test_static_entry_matches_regular_entry_twice(precision):
     ref_a = run_regular(dim, n, alpha, Wi, beta, m, dt, precision, mu, w, sig_a, kap, u, steps)
     got_a = run_static(dim, n, alpha, Wi, beta, m, dt, precision, mu, w, sig_a, kap, u, steps)
     assert np.all(rel(got_a, ref_a) < TOL[precision])
+    assert static_flags() == 0
     # second call in a row on the same array: zero initial stress and fewer steps
     ref_b = run_regular(dim, n, alpha, Wi, beta, m, dt, precision, mu, w, None, kap, u, steps - 5)
     got_b = run_static(dim, n, alpha, Wi, beta, m, dt, precision, mu, w, None, kap, u, steps - 5)
     assert np.all(rel(got_b, ref_b) < TOL[precision])
     assert np.max(np.abs(ref_b)) > 0
+    assert static_flags() == 0
+
+
+def test_static_entry_reports_its_device_flags():
+    # tfs_run_static has no handle: the flags its kernels latch are read with
+    # tfs_static_status.  A non-finite initial stress latches
+    # TFS_FLAG_NONFINITE; a velocity beyond the explicit transport's limit
+    # latches TFS_FLAG_COURANT; the next clean call clears them.
+    ensure_lib()
+    from paper_2411_17294_gb300 import tfs
+    dim, n, alpha, Wi, beta, m, dt, steps = 2, (16, 12), 0.5, 1.0, 0.5, 6, 1e-3, 4
+    mu, w = soe.soe_nnls(alpha, dt, 10 * dt, m)
+    u, kap = inputs.spectral_velocity(dim, n, 3, seed=44)
+    case = dict(dim=dim, n=n, alpha=alpha, dt=dt, mu=mu, w=w)
+    u_ok = stable_velocity(case, u)
+    sig = inputs.random_stress(dim, n, 45)
+    sig[1, 7] = np.nan
+    out = run_static(dim, n, alpha, Wi, beta, m, dt, 1, mu, w, sig, kap, u_ok, steps)
+    assert np.isnan(out).any()
+    assert static_flags() & tfs.TFS_FLAG_NONFINITE
+    u_bad = np.asarray(u_ok) * (2.0 / courant_fraction(case, u_ok))
+    run_static(dim, n, alpha, Wi, beta, m, dt, 1, mu, w, None, kap, u_bad, steps)
+    assert static_flags() & tfs.TFS_FLAG_COURANT
+    run_static(dim, n, alpha, Wi, beta, m, dt, 1, mu, w, None, kap, u_ok, steps)
+    assert static_flags() == 0
 
 
 def test_static_entry_classic_path_and_size_limit():
