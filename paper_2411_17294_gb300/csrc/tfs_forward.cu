@@ -490,13 +490,25 @@ struct StepShape {
     static constexpr int CPW = NC / W;
 };
 
-template <typename T, int DIM, bool TRANSPORT, bool COMP, bool PAPER, typename Hook>
+// Modes whose Q_j a thread keeps in registers when the stage buffer is to be
+// refilled right after the history sums (QR variant of the step kernel).
+constexpr int kQR = 32;
+
+// One tile.  QR (FP32 storage, stress form, alpha < 1, m <= kQR): the Q_j of a
+// thread's components stay in registers and the solving warp copies its
+// kappa and sigma0 values out of the stage before the hook, so the hook may
+// refill the whole stage buffer with the next tile while this one is solved
+// and pushed forward; otherwise Q_j is stored over level n-1 in the stage and
+// the hook may refill only the level-n mode planes.
+template <typename T, int DIM, bool TRANSPORT, bool COMP, bool PAPER, bool QR, typename Hook>
 __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap& S, T* buf, long long t0,
                                              int classic, void* sR_raw, float* sD, Hook after_pass1) {
     constexpr int NC = Packed<DIM>::NC;
     constexpr int W = StepShape<DIM>::W;
     constexpr int CPW = StepShape<DIM>::CPW;
     constexpr bool F32 = sizeof(T) == 4;
+    static_assert(!QR || (F32 && !PAPER), "the register variant serves the FP32 stress form");
+    float qr[QR ? CPW : 1][QR ? kQR : 1];   // Q_j in registers (QR)
     const int lane = threadIdx.x;
     const int w = threadIdx.y;
     const long long N = A.N;
@@ -542,20 +554,37 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
             float hs[CPW], comp[CPW];
 #pragma unroll
             for (int cc = 0; cc < CPW; ++cc) hs[cc] = comp[cc] = 0.0f;
-#pragma unroll 4
-            for (int j = 0; j < m; ++j) {
-                const float eh = A.mc.eta_hi[j], el = A.mc.eta_lo[j];
+            auto kahan_term = [&](int j, int cc, float qj) {
+                const float yv = __fmaf_rn(A.mc.eta_hi[j], qj, __fmaf_rn(A.mc.eta_lo[j], qj, -comp[cc]));
+                const float t = __fadd_rn(hs[cc], yv);
+                comp[cc] = __fsub_rn(__fsub_rn(t, hs[cc]), yv);
+                hs[cc] = t;
+            };
+            if constexpr (QR) {
 #pragma unroll
-                for (int cc = 0; cc < CPW; ++cc) {
-                    const int o = (j * NC + cc * W) * kTile;
-                    const float x = lv0[o];
-                    const float y = lv1[o];
-                    const float qj = __fmaf_rn(0.5f, y, -2.0f * x);
-                    lv1[o] = qj;
-                    const float yv = __fmaf_rn(eh, qj, __fmaf_rn(el, qj, -comp[cc]));
-                    const float t = __fadd_rn(hs[cc], yv);
-                    comp[cc] = __fsub_rn(__fsub_rn(t, hs[cc]), yv);
-                    hs[cc] = t;
+                for (int j = 0; j < kQR; ++j) {
+                    if (j < m) {
+#pragma unroll
+                        for (int cc = 0; cc < CPW; ++cc) {
+                            const int o = (j * NC + cc * W) * kTile;
+                            const float qj = __fmaf_rn(0.5f, (float)lv1[o], -2.0f * (float)lv0[o]);
+                            qr[cc][j] = qj;
+                            kahan_term(j, cc, qj);
+                        }
+                    }
+                }
+            } else {
+#pragma unroll 4
+                for (int j = 0; j < m; ++j) {
+#pragma unroll
+                    for (int cc = 0; cc < CPW; ++cc) {
+                        const int o = (j * NC + cc * W) * kTile;
+                        const float x = lv0[o];
+                        const float y = lv1[o];
+                        const float qj = __fmaf_rn(0.5f, y, -2.0f * x);
+                        lv1[o] = qj;
+                        kahan_term(j, cc, qj);
+                    }
                 }
             }
 #pragma unroll
@@ -564,14 +593,29 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
             float hs[CPW];
 #pragma unroll
             for (int cc = 0; cc < CPW; ++cc) hs[cc] = 0.0f;
-#pragma unroll 4
-            for (int j = 0; j < m; ++j) {
+            if constexpr (QR) {
 #pragma unroll
-                for (int cc = 0; cc < CPW; ++cc) {
-                    const int o = (j * NC + cc * W) * kTile;
-                    const float qj = __fmaf_rn(0.5f, lv1[o], -2.0f * lv0[o]);
-                    lv1[o] = qj;
-                    hs[cc] = __fmaf_rn(A.mc.eta_hi[j], qj, hs[cc]);
+                for (int j = 0; j < kQR; ++j) {
+                    if (j < m) {
+#pragma unroll
+                        for (int cc = 0; cc < CPW; ++cc) {
+                            const int o = (j * NC + cc * W) * kTile;
+                            const float qj = __fmaf_rn(0.5f, (float)lv1[o], -2.0f * (float)lv0[o]);
+                            qr[cc][j] = qj;
+                            hs[cc] = __fmaf_rn(A.mc.eta_hi[j], qj, hs[cc]);
+                        }
+                    }
+                }
+            } else {
+#pragma unroll 4
+                for (int j = 0; j < m; ++j) {
+#pragma unroll
+                    for (int cc = 0; cc < CPW; ++cc) {
+                        const int o = (j * NC + cc * W) * kTile;
+                        const float qj = __fmaf_rn(0.5f, lv1[o], -2.0f * lv0[o]);
+                        lv1[o] = qj;
+                        hs[cc] = __fmaf_rn(A.mc.eta_hi[j], qj, hs[cc]);
+                    }
                 }
             }
 #pragma unroll
@@ -623,8 +667,30 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
             reinterpret_cast<double*>(sR_raw)[c * kTile + lane] = R;
         }
     }
+    // QR: the solving warp's stage inputs in registers, so that the hook may
+    // refill the whole stage
+    float kn_r[QR ? DIM * DIM : 1], km_r[QR ? DIM * DIM : 1], s0_r[QR ? NC : 1];
+    if constexpr (QR) {
+        if (w == 0) {
+#pragma unroll
+            for (int i = 0; i < DIM * DIM; ++i) {
+                kn_r[i] = (float)buf[(S.kn + i) * kTile + lane];
+                km_r[i] = (float)buf[(S.km + i) * kTile + lane];
+            }
+#pragma unroll
+            for (int r = 0; r < NC; ++r) s0_r[r] = has_s0 ? (float)buf[(S.s0 + r) * kTile + lane] : 0.0f;
+        }
+    }
+    auto kn_at = [&](int i) -> float {
+        if constexpr (QR) return kn_r[i];
+        else return (float)buf[(S.kn + i) * kTile + lane];
+    };
+    auto km_at = [&](int i) -> float {
+        if constexpr (QR) return km_r[i];
+        else return (float)buf[(S.km + i) * kTile + lane];
+    };
     __syncthreads();
-    // level n of the mode planes is no longer read in this tile
+    // level n of the mode planes (QR: the whole stage) is no longer read in this tile
     after_pass1();
 
     // ---- (a2) + (a5) point solve by warp 0
@@ -723,8 +789,7 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
             for (int a = 0; a < DIM; ++a)
 #pragma unroll
                 for (int b = 0; b < DIM; ++b)
-                    K[a][b] = two_sum_f2(2.0f * (float)buf[(S.kn + a * DIM + b) * kTile + lane],
-                                         -(float)buf[(S.km + a * DIM + b) * kTile + lane]);
+                    K[a][b] = two_sum_f2(2.0f * kn_at(a * DIM + b), -km_at(a * DIM + b));
             const f2* sR = reinterpret_cast<const f2*>(sR_raw);
             f2 R[NC], x[NC];
 #pragma unroll
@@ -754,7 +819,9 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
 #pragma unroll
         for (int r = 0; r < NC; ++r) {
             finite = finite && isfinite((double)out[r]);
-            const T s0r = has_s0 ? buf[(S.s0 + r) * kTile + lane] : (T)0;
+            T s0r;
+            if constexpr (QR) s0r = (T)s0_r[r];
+            else s0r = has_s0 ? buf[(S.s0 + r) * kTile + lane] : (T)0;
             // the push-forward uses the stored value of sigma^{n+1}
             if constexpr (F32) sD[r * kTile + lane] = __fsub_rn((float)out[r], (float)s0r);
             else reinterpret_cast<double*>(sD)[r * kTile + lane] = (double)out[r] - (double)s0r;
@@ -782,7 +849,20 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
         const T* qv = buf + ((m * NC + w) * kTile + lane);
         T* out = A.modes_nm1 + (long long)w * N + p;
         const long long stride = (long long)NC * N;
-        if constexpr (F32) {
+        if constexpr (QR) {
+            float d[CPW];
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc) d[cc] = sD[(w + cc * W) * kTile + lane];
+#pragma unroll
+            for (int j = 0; j < kQR; ++j) {
+                if (j < m) {
+                    const float rho = A.mc.rho[j], cj = A.mc.c[j];
+#pragma unroll
+                    for (int cc = 0; cc < CPW; ++cc)
+                        __stcs(out + j * stride + (long long)cc * W * N, __fmaf_rn(rho, d[cc], -cj * qr[cc][j]));
+                }
+            }
+        } else if constexpr (F32) {
             float d[CPW];
 #pragma unroll
             for (int cc = 0; cc < CPW; ++cc) d[cc] = sD[(w + cc * W) * kTile + lane];
@@ -815,7 +895,7 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
 // level-n mode planes are fetched as soon as the current tile has read its
 // own (after its history sums) and the rest after its push-forward.  One loop
 // serves every variant, so that the tile code is instantiated once.
-template <typename T, int DIM, bool TRANSPORT, bool COMP, bool PAPER>
+template <typename T, int DIM, bool TRANSPORT, bool COMP, bool PAPER, bool QR>
 __global__ void __launch_bounds__(32 * StepShape<DIM>::W, 4)
 fwd_kernel(const FwdArgs<T> A, const __grid_constant__ TmaPlan tp, const int classic, const long long num_tiles,
            const int stages, const int vec16) {
@@ -888,13 +968,15 @@ fwd_kernel(const FwdArgs<T> A, const __grid_constant__ TmaPlan tp, const int cla
             else cp_async_wait<0>();
             __syncthreads();
         }
+        // one buffer: the next tile's level-n mode planes as soon as the history
+        // sums have read them (QR: the whole next tile), the rest after the push
         auto early = [&] {
-            if (!two && next < num_tiles) issue(0, next, true, false);
+            if (!two && next < num_tiles) issue(0, next, true, QR);
         };
-        compute_tile<T, DIM, TRANSPORT, COMP, PAPER>(A, S, b ? buf1 : buf0, tile * kTile, classic, sR_store, sD,
-                                                     early);
+        compute_tile<T, DIM, TRANSPORT, COMP, PAPER, QR>(A, S, b ? buf1 : buf0, tile * kTile, classic, sR_store,
+                                                         sD, early);
         __syncthreads();
-        if (!two && next < num_tiles) issue(0, next, false, true);
+        if (!QR && !two && next < num_tiles) issue(0, next, false, true);
     }
     if (!use_tma) cp_async_wait<0>();
 }
@@ -902,8 +984,9 @@ fwd_kernel(const FwdArgs<T> A, const __grid_constant__ TmaPlan tp, const int cla
 template <typename T, int DIM, bool TRANSPORT, bool COMP, bool PAPER>
 cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s) {
     constexpr int NC = Packed<DIM>::NC;
+    constexpr bool kQRok = sizeof(T) == 4 && !PAPER;
     cudaError_t e;
-    auto kern = fwd_kernel<T, DIM, TRANSPORT, COMP, PAPER>;
+    auto kern = fwd_kernel<T, DIM, TRANSPORT, COMP, PAPER, false>;
     const long long num_tiles = (a.N + kTile - 1) / kTile;
     const bool levels = cfg.classic || PAPER;
     if (PAPER && (cfg.classic || !a.psi)) return cudaErrorInvalidValue;
@@ -936,6 +1019,21 @@ cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+    }
+    // one stage buffer per block: the variant that keeps Q_j in registers
+    // refills the whole buffer right after the history sums
+    bool qr = false;
+    if constexpr (kQRok) {
+        if (!cfg.classic && a.m <= kQR && plan.stages == 1) {
+            PersistPlan qp;
+            e = persistent_plan(reinterpret_cast<const void*>(fwd_kernel<T, DIM, TRANSPORT, COMP, PAPER, true>),
+                                32 * StepShape<DIM>::W, stage_bytes, static_bytes, 1, &qp);
+            if (e != cudaSuccess) return e;
+            if (qp.stages * qp.per_sm >= plan.stages * plan.per_sm) {
+                qr = true;
+                plan = qp;
+            }
+        }
     }
     const int stages = plan.stages;
     const size_t dyn = plan.dyn;
@@ -971,8 +1069,12 @@ cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s
         e = cudaEventRecord(cfg.ev_before, s);
         if (e != cudaSuccess) return e;
     }
-    kern<<<dim3((unsigned)grid), dim3(32, StepShape<DIM>::W), dyn, s>>>(a, tp, cfg.classic ? 1 : 0, num_tiles,
-                                                                       stages, vec16);
+    if (qr)
+        fwd_kernel<T, DIM, TRANSPORT, COMP, PAPER, kQRok><<<dim3((unsigned)grid), dim3(32, StepShape<DIM>::W), dyn, s>>>(
+            a, tp, 0, num_tiles, stages, vec16);
+    else
+        kern<<<dim3((unsigned)grid), dim3(32, StepShape<DIM>::W), dyn, s>>>(a, tp, cfg.classic ? 1 : 0, num_tiles,
+                                                                           stages, vec16);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (cfg.ev_after) e = cudaEventRecord(cfg.ev_after, s);
