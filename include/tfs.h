@@ -189,7 +189,10 @@ int tfs_transport_limit(tfs_handle h, double* umax_out);
 
 /* Bytes of device workspace the handle needs: 256 (status) + 5 fields of
    nc N elements (sigma0 copy, stress ring of 3, transport term) + 2 mode levels
-   of m nc N elements, each rounded up to 256 bytes. */
+   of m nc ceil(N/32)*32 elements (stored tile by tile: the m nc values of 32
+   consecutive points are contiguous), each rounded up to 256 bytes; more with
+   the paper's variable or implicit transport (see TFS_PARAM_FORM and
+   TFS_PARAM_TRANSPORT). */
 size_t tfs_workspace_bytes(tfs_handle h);
 
 /* Bind caller-owned device memory of at least tfs_workspace_bytes bytes,
@@ -300,7 +303,7 @@ int tfs_destroy(tfs_handle h);
    The whole state (stress ring, sigma0 copy, transport term, status word, both mode levels)
    lives in one fixed device array of 64 MiB compiled into the library, which
    every GPU that loads the library holds until the process exits; problems
-   whose state needs more (256 + 5 up256(nc N s) + 2 up256(m nc N s) bytes,
+   whose state needs more (256 + 5 up256(nc N s) + 2 up256(m nc ceil(N/32)*32 s) bytes,
    s = element size, up256 = round up to 256) return TFS_ERR_TOOBIG before any
    device work.  Arguments as tfs_create / tfs_set_soe (mu, w: host, m
    entries, NULL when alpha == 1); Re = 1, eps = 0, upwind3 stencil, transport

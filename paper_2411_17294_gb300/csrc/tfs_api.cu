@@ -21,7 +21,7 @@ using namespace tfs;
 namespace {
 
 constexpr uint64_t kMagic = 0x3153464154434b50ull;   // checkpoint tag
-constexpr uint64_t kVersion = 2;
+constexpr uint64_t kVersion = 3;   // 3: tile-major mode levels
 constexpr size_t kAlign = 256;
 constexpr size_t kHeaderBytes = 256;
 
@@ -93,7 +93,8 @@ struct tfs_ctx {
     bool is_double() const { return precision == TFS_FP64; }
     bool classic() const { return alpha == 1.0; }
     size_t field_bytes() const { return (size_t)nc * (size_t)N * es(); }
-    size_t modes_bytes() const { return (size_t)m * field_bytes(); }
+    // forward mode levels: tile-major over ceil(N / 32) whole tiles (mode_index)
+    size_t modes_bytes() const { return (size_t)m * (size_t)nc * (size_t)mode_points(N) * es(); }
     int third_sig() const { return 3 - cur_sig - prev_sig; }
     bool explicit_transport() const { return transport == 1; }
     // explicit transport: the Courant bound of the form carried applies

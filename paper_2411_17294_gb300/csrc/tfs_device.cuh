@@ -368,6 +368,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
 // Tiled 2D copy of the tensor map's box at (x, y) into shared memory; the
 // transferred bytes are counted on `bar`.  The map must live in kernel
 // parameter (__grid_constant__), constant or global memory.
+// Untiled bulk copy global -> shared (cp.async.bulk): both addresses 16-byte
+// aligned and `bytes` a multiple of 16; completion counted on the mbarrier.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int x, int y, uint64_t* bar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(

@@ -72,103 +72,101 @@ __host__ __device__ __forceinline__ StageMap stage_map(int m, bool transport, bo
     return S;
 }
 
-// Global source of stage plane `plane` (the segment of 32 points starts at t0).
+// Global source of stage plane `plane` for the tile starting at point t0: the
+// first of its 32 elements.  Mode rows come from the tile-major levels (always
+// 32 stored elements, padding past N included); every other plane is a field
+// [.][N] read at t0 (elements past N are zero-filled by the caller).
 template <typename T, int DIM>
-__device__ __forceinline__ const T* plane_src(const FwdArgs<T>& A, const StageMap& S, int plane) {
+__device__ __forceinline__ const T* row_src(const FwdArgs<T>& A, const StageMap& S, int plane, long long t0) {
     constexpr int NC = DIM == 2 ? 3 : 6;
     const long long N = A.N;
     if (plane < S.kn) {
         const int mnc = A.m * NC;
-        return plane < mnc ? A.modes_n + (long long)plane * N : A.modes_nm1 + (long long)(plane - mnc) * N;
+        const T* lv = plane < mnc ? A.modes_n : A.modes_nm1;
+        const int row = plane < mnc ? plane : plane - mnc;
+        return lv + mode_index(t0, row, mnc);
     }
-    if (plane < S.km) return A.kap_n + (long long)(plane - S.kn) * N;
-    if (plane < S.tr) return A.kap_nm1 + (long long)(plane - S.km) * N;
-    if (plane < S.s0) return A.trans + (long long)(plane - S.tr) * N;
-    if (plane < S.sig) return A.sigma0 + (long long)(plane - S.s0) * N;
+    if (plane < S.km) return A.kap_n + (long long)(plane - S.kn) * N + t0;
+    if (plane < S.tr) return A.kap_nm1 + (long long)(plane - S.km) * N + t0;
+    if (plane < S.s0) return A.trans + (long long)(plane - S.tr) * N + t0;
+    if (plane < S.sig) return A.sigma0 + (long long)(plane - S.s0) * N + t0;
     const int k = plane - S.sig;
-    return k < NC ? A.sig_n + (long long)k * N : A.sig_nm1 + (long long)(k - NC) * N;
+    return (k < NC ? A.sig_n + (long long)k * N : A.sig_nm1 + (long long)(k - NC) * N) + t0;
 }
 
-// Copy the stage planes [pb, pe) of the tile starting at point t0.
+// Copy the stage planes [pb, pe) of the tile starting at point t0 (cp.async).
 template <typename T, int DIM>
 __device__ __forceinline__ void issue_planes(const FwdArgs<T>& A, const StageMap& S, T* buf, long long t0, int tid,
                                              int nthr, bool vec16, int pb, int pe) {
     const long long N = A.N;
-    if (vec16 && t0 + kTile <= N) {
-        // full tile, 16-byte chunks: thread tid always copies chunk k = tid % CPP of
-        // planes pb + tid / CPP, + nthr / CPP, ...; the mode planes of each level
-        // are equally spaced (N apart), so their sources advance by a fixed stride
-        constexpr int EPC = 16 / sizeof(T);
-        constexpr int CPP = kTile / EPC;
-        const int k = tid % CPP;
-        const int step = nthr / CPP;            // planes per round (nthr is a multiple of CPP)
-        const int mnc = A.m * (DIM == 2 ? 3 : 6);
-        const long long off = t0 + (long long)k * EPC;
-        const long long stride = (long long)step * N;
-        int plane = pb + tid / CPP;
-        if (plane < min(pe, mnc)) {
-            const T* src = A.modes_n + (long long)plane * N + off;
-            for (; plane < min(pe, mnc); plane += step, src += stride) cp_async16(buf + plane * kTile + k * EPC, src, 16);
+    const int mnc = A.m * (DIM == 2 ? 3 : 6);
+    const int mend = 2 * mnc;   // mode planes [0, 2 mnc): whole rows, always 16-byte chunks
+    constexpr int EPC = 16 / sizeof(T);    // elements per chunk
+    constexpr int CPP = kTile / EPC;       // chunks per plane row
+    {
+        const int lo = pb, hi = min(pe, mend);
+        for (int q = tid; q < (hi - lo) * CPP; q += nthr) {
+            const int plane = lo + q / CPP;
+            const int k = q % CPP;
+            cp_async16(buf + plane * kTile + k * EPC, row_src<T, DIM>(A, S, plane, t0) + k * EPC, 16);
         }
-        if (plane >= mnc && plane < min(pe, 2 * mnc)) {
-            const T* src = A.modes_nm1 + (long long)(plane - mnc) * N + off;
-            for (; plane < min(pe, 2 * mnc); plane += step, src += stride)
-                cp_async16(buf + plane * kTile + k * EPC, src, 16);
-        }
-        for (; plane < pe; plane += step)
-            cp_async16(buf + plane * kTile + k * EPC, plane_src<T, DIM>(A, S, plane) + off, 16);
-        return;
     }
+    const int b0 = max(pb, mend);
+    if (b0 >= pe) return;
     if (vec16) {
-        constexpr int EPC = 16 / sizeof(T);    // elements per chunk
-        constexpr int CPP = kTile / EPC;       // chunks per plane segment
-        const int total = (pe - pb) * CPP;
+        const int total = (pe - b0) * CPP;
         for (int q = tid; q < total; q += nthr) {
-            const int plane = pb + q / CPP;
+            const int plane = b0 + q / CPP;
             const int k = q % CPP;
             const long long p0 = t0 + (long long)k * EPC;
             long long valid = N - p0;
             valid = valid < 0 ? 0 : (valid > EPC ? EPC : valid);
-            const T* base = plane_src<T, DIM>(A, S, plane);
+            const T* base = row_src<T, DIM>(A, S, plane, 0);
             cp_async16(buf + plane * kTile + k * EPC, base + (valid > 0 ? p0 : 0), (int)(valid * sizeof(T)));
         }
     } else {
-        const int total = (pe - pb) * kTile;
+        const int total = (pe - b0) * kTile;
         for (int q = tid; q < total; q += nthr) {
-            const int plane = pb + q / kTile;
+            const int plane = b0 + q / kTile;
             const int l = q % kTile;
             const long long p = t0 + l;
-            const T* base = plane_src<T, DIM>(A, S, plane);
+            const T* base = row_src<T, DIM>(A, S, plane, 0);
             cp_async_small<sizeof(T)>(buf + plane * kTile + l, base + (p < N ? p : 0), p < N ? (int)sizeof(T) : 0);
         }
     }
 }
 
-template <typename T, int DIM>
-__device__ __forceinline__ void issue_tile(const FwdArgs<T>& A, const StageMap& S, T* buf, long long t0, int tid,
-                                           int nthr, bool vec16) {
-    issue_planes<T, DIM>(A, S, buf, t0, tid, nthr, vec16, 0, S.planes);
+// TMA staging (one thread issues): the level-n mode rows complete on bar_e,
+// everything else (level n-1, kappa levels, A, sigma0, stress levels) on bar_l.
+// Each mode level of a tile is one contiguous block (tile-major storage),
+// fetched by untiled bulk copies of at most 32 KB; the per-point fields by
+// tensor-map tiles of 32 points.
+constexpr unsigned kBulkChunk = 32768;
+
+template <typename T>
+__device__ __forceinline__ void bulk_level(T* dst, const T* src, unsigned bytes, uint64_t* bar) {
+    for (unsigned off = 0; off < bytes; off += kBulkChunk) {
+        const unsigned b = bytes - off < kBulkChunk ? bytes - off : kBulkChunk;
+        bulk_load(reinterpret_cast<char*>(dst) + off, reinterpret_cast<const char*>(src) + off, b, bar);
+    }
 }
 
-// TMA staging (one thread issues): the level-n mode planes complete on bar_e,
-// everything else (level n-1, kappa levels, A, sigma0, stress levels) on bar_l.
 template <typename T, int DIM, bool TRANSPORT>
-__device__ __forceinline__ void tma_issue(const TmaPlan& tp, const StageMap& S, T* buf, long long t0, int mnc,
-                                          bool has_s0, bool levels, bool early, bool late, uint64_t* bar_e,
-                                          uint64_t* bar_l) {
+__device__ __forceinline__ void tma_issue(const FwdArgs<T>& A, const TmaPlan& tp, const StageMap& S, T* buf,
+                                          long long t0, int mnc, bool has_s0, bool levels, bool early, bool late,
+                                          uint64_t* bar_e, uint64_t* bar_l) {
     constexpr int NC = Packed<DIM>::NC;
     constexpr unsigned kPlaneBytes = kTile * sizeof(T);
     const int x = (int)t0;
+    const unsigned level_bytes = (unsigned)mnc * kPlaneBytes;
     fence_proxy_async_smem();
     if (early && mnc > 0) {
-        mbar_arrive_expect_tx(bar_e, (unsigned)mnc * kPlaneBytes);
-        for (int b = 0; b < tp.mode_boxes; ++b)
-            tma_load_2d(buf + (size_t)b * tp.mode_box * kTile, &tp.lv_n, x, b * tp.mode_box, bar_e);
+        mbar_arrive_expect_tx(bar_e, level_bytes);
+        bulk_level(buf, A.modes_n + mode_index(t0, 0, mnc), level_bytes, bar_e);
     }
     if (late) {
         mbar_arrive_expect_tx(bar_l, (unsigned)(S.planes - mnc) * kPlaneBytes);
-        for (int b = 0; b < tp.mode_boxes && mnc > 0; ++b)
-            tma_load_2d(buf + (size_t)(mnc + b * tp.mode_box) * kTile, &tp.lv_nm1, x, b * tp.mode_box, bar_l);
+        if (mnc > 0) bulk_level(buf + (size_t)mnc * kTile, A.modes_nm1 + mode_index(t0, 0, mnc), level_bytes, bar_l);
         tma_load_2d(buf + (size_t)S.kn * kTile, &tp.kn, x, 0, bar_l);
         tma_load_2d(buf + (size_t)S.km * kTile, &tp.km, x, 0, bar_l);
         if (TRANSPORT) tma_load_2d(buf + (size_t)S.tr * kTile, &tp.tr, x, 0, bar_l);
@@ -847,8 +845,9 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
     // ---- (a6) push-forward of the modes over the oldest level
     if (!classic && active) {
         const T* qv = buf + ((m * NC + w) * kTile + lane);
-        T* out = A.modes_nm1 + (long long)w * N + p;
-        const long long stride = (long long)NC * N;
+        // row j NC + c of this tile's block in the tile-major level
+        T* out = A.modes_nm1 + mode_index(p, w, m * NC);
+        constexpr long long stride = (long long)NC * kTile;
         if constexpr (QR) {
             float d[CPW];
 #pragma unroll
@@ -859,7 +858,7 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
                     const float rho = A.mc.rho[j], cj = A.mc.c[j];
 #pragma unroll
                     for (int cc = 0; cc < CPW; ++cc)
-                        __stcs(out + j * stride + (long long)cc * W * N, __fmaf_rn(rho, d[cc], -cj * qr[cc][j]));
+                        __stcs(out + j * stride + (long long)cc * W * kTile, __fmaf_rn(rho, d[cc], -cj * qr[cc][j]));
                 }
             }
         } else if constexpr (F32) {
@@ -871,7 +870,7 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
                 const float rho = A.mc.rho[j], cj = A.mc.c[j];
 #pragma unroll
                 for (int cc = 0; cc < CPW; ++cc)
-                    __stcs(out + j * stride + (long long)cc * W * N,
+                    __stcs(out + j * stride + (long long)cc * W * kTile,
                            __fmaf_rn(rho, d[cc], -cj * qv[(j * NC + cc * W) * kTile]));
             }
         } else {
@@ -882,7 +881,7 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
             for (int j = 0; j < m; ++j)
 #pragma unroll
                 for (int cc = 0; cc < CPW; ++cc)
-                    __stcs(out + j * stride + (long long)cc * W * N,
+                    __stcs(out + j * stride + (long long)cc * W * kTile,
                            (T)fma(A.mc.rho[j], d[cc], -A.mc.c[j] * (double)qv[(j * NC + cc * W) * kTile]));
         }
     }
@@ -933,8 +932,8 @@ fwd_kernel(const FwdArgs<T> A, const __grid_constant__ TmaPlan tp, const int cla
         T* dst = b ? buf1 : buf0;
         if (use_tma) {
             if (tid == 0)
-                tma_issue<T, DIM, TRANSPORT>(tp, S, dst, t * kTile, mnc, has_s0, classic != 0 || PAPER, early, late, &bars[b][0],
-                                             &bars[b][1]);
+                tma_issue<T, DIM, TRANSPORT>(A, tp, S, dst, t * kTile, mnc, has_s0, classic != 0 || PAPER, early, late,
+                                             &bars[b][0], &bars[b][1]);
         } else {
             issue_planes<T, DIM>(A, S, dst, t * kTile, tid, nthr, v16, early ? 0 : mnc, late ? S.planes : mnc);
             cp_async_commit();
@@ -1046,16 +1045,7 @@ cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s
     memset(&tp, 0, sizeof(tp));
     {
         const bool dbl = sizeof(T) == 8;
-        const int mnc = (cfg.classic ? 0 : a.m) * NC;
-        int boxes = (mnc + 255) / 256;
-        while (boxes > 0 && boxes <= mnc && mnc % boxes != 0) ++boxes;
-        tp.mode_boxes = mnc > 0 ? boxes : 0;
-        tp.mode_box = mnc > 0 ? mnc / boxes : 0;
         bool ok = a.N < (1ll << 31);
-        if (ok && mnc > 0) {
-            ok = encode_plane_map(&tp.lv_n, a.modes_n, a.N, mnc, tp.mode_box, dbl) &&
-                 encode_plane_map(&tp.lv_nm1, a.modes_nm1, a.N, mnc, tp.mode_box, dbl);
-        }
         ok = ok && encode_plane_map(&tp.kn, a.kap_n, a.N, DIM * DIM, DIM * DIM, dbl) &&
              encode_plane_map(&tp.km, a.kap_nm1, a.N, DIM * DIM, DIM * DIM, dbl);
         if (ok && TRANSPORT) ok = encode_plane_map(&tp.tr, a.trans, a.N, NC, NC, dbl);

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kThreads) imp_rhs_kernel(const ImpArgs<T> A, d
                 // compensated sum as in the default step, then one rounding to double
                 float hs = 0.0f, comp = 0.0f;
                 for (int jj = 0; jj < A.m; ++jj) {
-                    const long long q = ((long long)jj * NC + c) * N + p;
+                    const long long q = mode_index(p, jj * NC + c, A.m * NC);
                     const float qj = __fmaf_rn(0.5f, (float)A.modes_nm1[q], -2.0f * (float)A.modes_n[q]);
                     A.modes_nm1[q] = (T)qj;
                     if (COMP) {
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kThreads) imp_rhs_kernel(const ImpArgs<T> A, d
             } else {
                 double H = 0.0;
                 for (int jj = 0; jj < A.m; ++jj) {
-                    const long long q = ((long long)jj * NC + c) * N + p;
+                    const long long q = mode_index(p, jj * NC + c, A.m * NC);
                     const double qj = kB1 * (double)A.modes_n[q] + kB2 * (double)A.modes_nm1[q];
                     A.modes_nm1[q] = (T)qj;
                     H = fma(A.mcd.eta[jj], qj, H);
@@ -404,13 +404,13 @@ __global__ void __launch_bounds__(kThreads) imp_push_kernel(const ImpArgs<T> A, 
             if constexpr (F32) {
                 const float d = __fsub_rn((float)out, (float)s0);
                 for (int j = 0; j < A.m; ++j) {
-                    const long long q = ((long long)j * NC + c) * N + p;
+                    const long long q = mode_index(p, j * NC + c, A.m * NC);
                     A.modes_nm1[q] = __fmaf_rn(A.mc.rho[j], d, -A.mc.c[j] * (float)A.modes_nm1[q]);
                 }
             } else {
                 const double d = (double)out - (double)s0;
                 for (int j = 0; j < A.m; ++j) {
-                    const long long q = ((long long)j * NC + c) * N + p;
+                    const long long q = mode_index(p, j * NC + c, A.m * NC);
                     A.modes_nm1[q] = (T)fma(A.mcd.rho[j], d, -A.mcd.c[j] * (double)A.modes_nm1[q]);
                 }
             }
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(kThreads) imp_rhs_paper_kernel(const ImpArgs<T
             if constexpr (F32) {
                 float hs = 0.0f, comp = 0.0f;
                 for (int jj = 0; jj < A.m; ++jj) {
-                    const long long q = ((long long)jj * NC + c) * N + p;
+                    const long long q = mode_index(p, jj * NC + c, A.m * NC);
                     const float qj = __fmaf_rn(0.5f, (float)A.modes_nm1[q], -2.0f * (float)A.modes_n[q]);
                     A.modes_nm1[q] = (T)qj;
                     if (COMP) {
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(kThreads) imp_rhs_paper_kernel(const ImpArgs<T
             } else {
                 double hs = 0.0;
                 for (int jj = 0; jj < A.m; ++jj) {
-                    const long long q = ((long long)jj * NC + c) * N + p;
+                    const long long q = mode_index(p, jj * NC + c, A.m * NC);
                     const double qj = kB1 * (double)A.modes_n[q] + kB2 * (double)A.modes_nm1[q];
                     A.modes_nm1[q] = (T)qj;
                     hs = fma(A.mcd.eta[jj], qj, hs);
@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(kThreads) start_rhs_kernel(const ImpArgs<T> A,
             const double s0 = A.sigma0 ? (double)A.sigma0[qc] : 0.0;
             double zs = 0.0;
             for (int jj = 0; jj < A.m; ++jj)
-                zs = fma(C.mu[jj] * C.inv_den[jj], (double)Z[((long long)jj * NC + c) * N + p], zs);
+                zs = fma(C.mu[jj] * C.inv_den[jj], (double)Z[mode_index(p, jj * NC + c, A.m * NC)], zs);
             b[qc] = A.dt * (C.W * s0 + zs + A.G * ks * gs);
             if (x0) x0[qc] = (double)A.sig_n[qc];
         }
@@ -598,7 +598,7 @@ __global__ void __launch_bounds__(kThreads) start_push_kernel(const ImpArgs<T> A
             const double s0 = A.sigma0 ? (double)A.sigma0[qc] : 0.0;
             const double d = x[qc] - s0;
             for (int jj = 0; jj < A.m; ++jj) {
-                const long long q = ((long long)jj * NC + c) * N + p;
+                const long long q = mode_index(p, jj * NC + c, A.m * NC);
                 const double z = stage == 1 ? (double)A.modes_n[q] : (double)A.modes_nm1[q];
                 const double kj = (-C.mu[jj] * z + C.w[jj] * d) * C.inv_den[jj];
                 A.modes_nm1[q] = (T)fma(f, kj, z);
@@ -1259,7 +1259,7 @@ __global__ void __launch_bounds__(kThreads) start_rhs_paper_kernel(const ImpArgs
             zP[c] = stage == 1 ? P0 : P0 + f1 * (P1 - P0) / gd;
             double hs = 0.0;
             for (int jj = 0; jj < A.m; ++jj) {
-                const double z0 = (double)A.modes_n[((long long)jj * NC + c) * N + p];
+                const double z0 = (double)A.modes_n[mode_index(p, jj * NC + c, A.m * NC)];
                 double z = z0;
                 if (stage == 2) z = fma(f1, P1 - C.mu[jj] * (fma(gd, P1, z0) * C.inv_den[jj]), z0);
                 hs = fma(C.w[jj] * C.mu[jj] * C.inv_den[jj], z, hs);
@@ -1306,7 +1306,7 @@ __global__ void __launch_bounds__(kThreads) start_push_paper_kernel(const ImpArg
             }
             const double P1 = (double)A.psi[qc], P2 = x[qc];
             for (int jj = 0; jj < A.m; ++jj) {
-                const long long q = ((long long)jj * NC + c) * N + p;
+                const long long q = mode_index(p, jj * NC + c, A.m * NC);
                 const double z0 = (double)A.modes_n[q];
                 const double z = fma(f1, P1 - C.mu[jj] * (fma(gd, P1, z0) * C.inv_den[jj]), z0);
                 A.modes_nm1[q] = (T)(fma(gd, P2, z) * C.inv_den[jj]);

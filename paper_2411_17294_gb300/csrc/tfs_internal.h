@@ -11,6 +11,19 @@ namespace tfs {
 constexpr int kMaxModes = 64;
 constexpr double kB0 = 1.5, kB1 = -2.0, kB2 = 0.5;   // BDF2 (Section 4.1)
 
+// Storage of the forward mode levels, tile-major: the m nc rows (row j nc + c
+// for mode j, component c) of the 32 consecutive points of tile p / 32 are
+// contiguous, so that one tile's level is one contiguous block of m nc 32
+// elements (a single bulk copy, and one DRAM stream instead of m nc of them);
+// a level spans ceil(N / 32) whole tiles, the points past N being padding.
+constexpr int kModeTile = 32;
+__host__ __device__ __forceinline__ long long mode_index(long long p, int row, int rows) {
+    return ((p >> 5) * rows + row) * kModeTile + (p & 31);
+}
+__host__ __device__ __forceinline__ long long mode_points(long long N) {
+    return (N + kModeTile - 1) / kModeTile * kModeTile;
+}
+
 // Per-mode constants of the BDF2 push-forward (eq. BDF_Phi_k_n+1):
 // c_j = 1/(b0 + mu_j dt), rho_j = w_j dt c_j, eta_j = mu_j dt c_j.
 // The float copies carry a hi/lo split of eta_j for the compensated mode sum.
@@ -31,7 +44,7 @@ struct F2c {
 };
 
 // Arguments of one forward step launch.  Field pointers follow the layouts of
-// include/tfs.h; the mode arrays are [m][nc][N].
+// include/tfs.h; the mode levels are tile-major (mode_index).
 template <typename T>
 struct FwdArgs {
     const T* kap_n;        // [d*d][N]
@@ -43,8 +56,8 @@ struct FwdArgs {
     T* sig_np1;            // [nc][N]
     T* sig_copy;           // optional second destination of sigma^{n+1}
     T* trans;              // [nc][N] transport term A: written by the pre-pass, read by the step
-    const T* modes_n;      // [m][nc][N]
-    T* modes_nm1;          // [m][nc][N]  read as level n-1, overwritten with level n+1
+    const T* modes_n;      // tile-major mode level n (mode_index)
+    T* modes_nm1;          // level n-1, overwritten with level n+1
     unsigned* flags;       // latched device status
     long long N;
     int n0, n1, n2;
@@ -66,17 +79,16 @@ struct FwdArgs {
     F2c xi_f2, dtxi_f2;    // xi, dt xi
 };
 
-// Tensor maps of the plane groups a tile stages, each a 2D view [planes][N]
-// (x = point, y = plane) with a box of 32 points; `on` = 0 selects the
-// cp.async path (grids whose N * element size is not a multiple of 16 bytes,
-// or unaligned fields).
+// Tensor maps of the per-point plane groups a tile stages, each a 2D view
+// [planes][N] (x = point, y = plane) with a box of 32 points; `on` = 0 selects
+// the cp.async path (grids whose N * element size is not a multiple of 16
+// bytes, or unaligned fields).  The tile-major mode levels need no map: each
+// tile's level is one contiguous block, fetched by untiled bulk copies.
 struct TmaPlan {
-    CUtensorMap lv_n, lv_nm1;   // mode levels n and n-1: box height mode_box, mode_boxes boxes per level
     CUtensorMap kn, km;         // velocity gradient levels [d*d]
     CUtensorMap tr, s0;         // transport term, initial stress [nc]
     CUtensorMap sn, sm;         // stress levels n, n-1 [nc] (alpha = 1)
     int on;
-    int mode_box, mode_boxes;
 };
 
 // Host: encode a [planes][N] tensor map with a box of 32 x box_h (false if the
@@ -105,7 +117,7 @@ struct ImpArgs {
     const T* sig_nm1;
     T* sig_np1;
     T* sig_copy;           // optional second destination of sigma^{n+1}
-    const T* modes_n;      // [m][nc][N]
+    const T* modes_n;      // tile-major mode level n (mode_index)
     T* modes_nm1;          // level n-1 in; Q_j after the right-hand side; level n+1 out
     unsigned* flags;
     long long N;
@@ -154,8 +166,8 @@ template <typename T>
 struct StartArgs {
     const T* kap0;         // [d*d][N]
     const T* sigma0;       // [nc][N] or nullptr for zero
-    const T* modes0;       // [m][nc][N] level 0
-    T* modes1;             // [m][nc][N] level 1 (out)
+    const T* modes0;       // tile-major mode level 0 (mode_index)
+    T* modes1;             // level 1 (out)
     T* sig1;               // [nc][N] (out)
     T* sig_copy;           // optional second destination of sigma^1
     unsigned* flags;

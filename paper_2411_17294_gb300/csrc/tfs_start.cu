@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(kThreads) start_point_kernel(const StartArgs<T
         for (int c = 0; c < NC; ++c) {
             double zs = 0.0;
             for (int jj = 0; jj < A.m; ++jj)
-                zs = fma(C.mu[jj] * C.inv_den[jj], (double)A.modes0[((long long)jj * NC + c) * N + p], zs);
+                zs = fma(C.mu[jj] * C.inv_den[jj], (double)A.modes0[mode_index(p, jj * NC + c, A.m * NC)], zs);
             S1[c] = A.dt * (C.W * s0[c] + zs + src[c] * C.g[0]);
         }
         {
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kThreads) start_point_kernel(const StartArgs<T
             const double d = S1[c] - s0[c];
             double zs = 0.0;
             for (int jj = 0; jj < A.m; ++jj) {
-                const double z0 = (double)A.modes0[((long long)jj * NC + c) * N + p];
+                const double z0 = (double)A.modes0[mode_index(p, jj * NC + c, A.m * NC)];
                 const double z = fma(f1, (-C.mu[jj] * z0 + C.w[jj] * d) * C.inv_den[jj], z0);
                 zs = fma(C.mu[jj] * C.inv_den[jj], z, zs);
             }
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kThreads) start_point_kernel(const StartArgs<T
         for (int c = 0; c < NC; ++c) {
             const double d1 = S1[c] - s0[c], d2 = S2[c] - s0[c];
             for (int jj = 0; jj < A.m; ++jj) {
-                const long long q = ((long long)jj * NC + c) * N + p;
+                const long long q = mode_index(p, jj * NC + c, A.m * NC);
                 const double z0 = (double)A.modes0[q];
                 const double z = fma(f1, (-C.mu[jj] * z0 + C.w[jj] * d1) * C.inv_den[jj], z0);
                 A.modes1[q] = (T)fma(f2, (-C.mu[jj] * z + C.w[jj] * d2) * C.inv_den[jj], z);
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kThreads) start_paper_kernel(const StartArgs<T
         for (int c = 0; c < NC; ++c) {
             double hs = 0.0;
             for (int jj = 0; jj < A.m; ++jj)
-                hs = fma(C.w[jj] * C.mu[jj] * C.inv_den[jj], (double)A.modes0[((long long)jj * NC + c) * N + p], hs);
+                hs = fma(C.w[jj] * C.mu[jj] * C.inv_den[jj], (double)A.modes0[mode_index(p, jj * NC + c, A.m * NC)], hs);
             h[c] = hs;
         }
         upper_convected_minus<DIM>(K, h, A.inv_wi, Lh);
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kThreads) start_paper_kernel(const StartArgs<T
         for (int c = 0; c < NC; ++c) {
             double hs = 0.0;
             for (int jj = 0; jj < A.m; ++jj) {
-                const double z0 = (double)A.modes0[((long long)jj * NC + c) * N + p];
+                const double z0 = (double)A.modes0[mode_index(p, jj * NC + c, A.m * NC)];
                 const double ph = fma(gd, P1[c], z0) * C.inv_den[jj];
                 const double z = fma(f1, P1[c] - C.mu[jj] * ph, z0);
                 hs = fma(C.w[jj] * C.mu[jj] * C.inv_den[jj], z, hs);
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kThreads) start_paper_kernel(const StartArgs<T
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             for (int jj = 0; jj < A.m; ++jj) {
-                const long long q = ((long long)jj * NC + c) * N + p;
+                const long long q = mode_index(p, jj * NC + c, A.m * NC);
                 const double z0 = (double)A.modes0[q];
                 const double ph = fma(gd, P1[c], z0) * C.inv_den[jj];
                 const double z = fma(f1, P1[c] - C.mu[jj] * ph, z0);

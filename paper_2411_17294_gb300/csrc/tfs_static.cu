@@ -148,7 +148,7 @@ extern "C" int tfs_run_static(const tfs_grid* grid, double alpha, double Wi, dou
     const int nc = grid->dim == 2 ? 3 : 6;
     const size_t es = precision == TFS_FP64 ? 8 : 4;
     const size_t field = (size_t)nc * (size_t)N * es;
-    const size_t modes = (size_t)m * field;
+    const size_t modes = (size_t)m * (size_t)nc * (size_t)mode_points(N) * es;   // tile-major levels
     const size_t need = kAlignS + 5 * up256(field) + 2 * up256(modes);
     if (need > kStaticBytes) return TFS_ERR_TOOBIG;
 
