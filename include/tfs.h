@@ -82,15 +82,19 @@ enum {
     TFS_PARAM_STENCIL = 2,    /* TFS_STENCIL_*, default upwind3 */
     TFS_PARAM_TRANSPORT = 3,  /* 0: pointwise law (u ignored); 1: explicit transport (default);
                                  2: implicit transport -- u.grad and eps Lap at t_{n+1} inside a global
-                                 solve, the form of the paper's eq. FP_discrete: BiCGStab with a
-                                 block-Jacobi preconditioner on FP64 Krylov vectors, no Courant limit;
-                                 the workspace grows by ((10 + 2 nc) nc + 4 d) N doubles; tfs_step then synchronises its
+                                 solve, the form of the paper's eq. FP_discrete: block-Jacobi
+                                 preconditioned BiCGStab on a float copy of the system inside an FP64
+                                 defect correction (the result meets the FP64 residual target; FP64
+                                 BiCGStab finishes if the float passes stall), no Courant limit;
+                                 the workspace grows by ((10 + 2 nc) nc + 4 d) N doubles plus
+                                 (2 nc^2 + 4 d + 9 nc) N floats; tfs_step then synchronises its
                                  stream; tfs_backward solves the transposed system per step with the
                                  same solver (either form, either start) */
     TFS_PARAM_UMAX = 4,       /* declared bound U on |u_a|; checked against tfs_transport_limit */
     TFS_PARAM_KRYLOV_TOL = 5, /* implicit transport: relative residual target, default 1e-13 (FP64)
                                  or 1e-9 (FP32 storage) */
-    TFS_PARAM_KRYLOV_MAXIT = 6, /* implicit transport: iteration limit, default 500 */
+    TFS_PARAM_KRYLOV_MAXIT = 6, /* implicit transport: iteration limit of each Krylov run (each float
+                                   pass of the defect correction, the FP64 finish), default 500 */
     TFS_PARAM_START = 7,      /* first step from the initial state, TFS_START_*: BDF2 with an empty
                                  past (default), or the two-stage SDIRK2 the paper takes for
                                  non-trivial initial data (Section 5.1; gamma = 1 - 1/sqrt2, stiffly

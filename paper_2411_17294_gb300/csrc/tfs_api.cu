@@ -271,9 +271,11 @@ bool limits_violated(tfs_ctx* h) {
 // preconditioner inverses [nc*nc][N], all FP64
 size_t krylov_bytes_for(const tfs_ctx* h, int form) {
     // 10 vectors, the point blocks and their inverses, 4 stencil coefficients per
-    // axis, and (the paper's variable) h
-    return ((10 + 2 * (size_t)h->nc + (form == TFS_FORM_PAPER ? 1 : 0)) * (size_t)h->nc + 4 * (size_t)h->dim) *
-           (size_t)h->N * sizeof(double);
+    // axis, the FP32 section of the inner solve, and (the paper's variable) h
+    return (((10 + 2 * (size_t)h->nc + (form == TFS_FORM_PAPER ? 1 : 0)) * (size_t)h->nc + 4 * (size_t)h->dim) *
+                (size_t)h->N +
+            (size_t)kry_float_doubles(h->nc, h->dim, h->N)) *
+           sizeof(double);
 }
 size_t krylov_bytes(const tfs_ctx* h) { return krylov_bytes_for(h, h->form); }
 size_t forward_bytes_for(const tfs_ctx* h, int transport, int form);

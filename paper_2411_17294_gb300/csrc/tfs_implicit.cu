@@ -9,9 +9,10 @@
 //
 // with the stencils of the explicit form (D_a upwinded on the sign of u_a(p))
 // acting on every stress component.  It is solved by BiCGStab (van der Vorst,
-// 1992) preconditioned on the right by block Jacobi: the nc x nc block of each
-// point, M_p plus the diagonal of the transport stencil.  Krylov vectors are
-// FP64 in both storage modes.
+// 1992) preconditioned on the right by block Jacobi (the nc x nc block of
+// each point, M_p plus the diagonal of the transport stencil), inside a
+// mixed-precision defect correction: FP64 residuals of the FP64 system, the
+// BiCGStab iterations on a float copy of it for the corrections.
 //
 // Kernels: rhs (history sum H over the modes, Q_j = b1 x + b2 y written over
 // the oldest mode level, R, initial guess E = 2 sigma^n - sigma^{n-1}), apply
@@ -204,11 +205,10 @@ __device__ __forceinline__ void block_partials(double a0, double a1, int nsets, 
 // w0 / w1 are given (w1 may be y itself: the (t, t) product).  The periodic
 // neighbour offsets are 32-bit (an implicit-transport workspace for 2^31 points
 // would not fit any device).
-template <typename T, int DIM>
-__global__ void __launch_bounds__(kThreads) imp_apply_kernel(const ImpArgs<T> A, const double* __restrict__ Mb,
-                                                             const double* __restrict__ Cf,
-                                                             const double* __restrict__ x, double* y,
-                                                             const double* w0, const double* w1, double* partials,
+template <typename T, int DIM, typename V>
+__global__ void __launch_bounds__(kThreads) imp_apply_kernel(const ImpArgs<T> A, const V* __restrict__ Mb,
+                                                             const V* __restrict__ Cf, const V* __restrict__ x, V* y,
+                                                             const V* w0, const V* w1, double* partials,
                                                              const double* sc) {
     constexpr int NC = Packed<DIM>::NC;
     if (done(sc)) return;
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kThreads) imp_apply_kernel(const ImpArgs<T> A,
         const int len[3] = {n0, n1, n2};
         const int str[3] = {1, n0, n0 * n1};
         int off[3][4];
-        double cf[3][4];
+        V cf[3][4];
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
 #pragma unroll
@@ -237,24 +237,24 @@ __global__ void __launch_bounds__(kThreads) imp_apply_kernel(const ImpArgs<T> A,
                 cf[a][t] = Cf[(long long)(a * 4 + t) * N + p];
             }
         }
-        double xp[NC];
+        V xp[NC];
 #pragma unroll
         for (int k = 0; k < NC; ++k) xp[k] = x[(long long)k * N + p];
 #pragma unroll
         for (int r = 0; r < NC; ++r) {
-            double acc = 0.0;
+            V acc = (V)0;
 #pragma unroll
             for (int k = 0; k < NC; ++k) acc = fma(Mb[(long long)(r * NC + k) * N + p], xp[k], acc);
-            const double* f = x + (long long)r * N + p;
+            const V* f = x + (long long)r * N + p;
 #pragma unroll
             for (int a = 0; a < DIM; ++a)
 #pragma unroll
                 for (int t = 0; t < 4; ++t)
-                    if (cf[a][t] != 0.0) acc = fma(cf[a][t], f[off[a][t]], acc);
+                    if (cf[a][t] != (V)0) acc = fma(cf[a][t], f[off[a][t]], acc);
             const long long q = (long long)r * N + p;
             y[q] = acc;
-            if (w0) a0 = fma(w0[q], acc, a0);
-            if (w1) a1 = fma(w1[q], acc, a1);
+            if (w0) a0 = fma((double)w0[q], (double)acc, a0);
+            if (w1) a1 = fma((double)w1[q], (double)acc, a1);
         }
     }
     if (w0) block_partials(a0, a1, w1 ? 2 : 1, partials);
@@ -262,25 +262,24 @@ __global__ void __launch_bounds__(kThreads) imp_apply_kernel(const ImpArgs<T> A,
 
 // z = P^-1 v with v = a x + b y (+ c w): forms the combination, stores it in
 // `comb` (when given) and its preconditioned image in z
-template <int NC>
-__global__ void __launch_bounds__(kThreads) imp_comb_precond_kernel(long long N, const double* Pinv, int mode,
-                                                                    double* p, const double* r, const double* v,
-                                                                    double* z, const double* sc) {
+template <int NC, typename V>
+__global__ void __launch_bounds__(kThreads) imp_comb_precond_kernel(long long N, const V* Pinv, int mode, V* p,
+                                                                    const V* r, const V* v, V* z, const double* sc) {
     if (done(sc)) return;
     // mode 0: p = r + beta (p - omega v);  mode 1: p (as s) = r - alpha v
-    const double beta = sc[S_BETA], omega = sc[S_OMEGA], alpha = sc[S_ALPHA];
+    const V beta = (V)sc[S_BETA], omega = (V)sc[S_OMEGA], alpha = (V)sc[S_ALPHA];
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        double w[NC];
+        V w[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             const long long q = (long long)c * N + i;
-            const double nv = mode == 0 ? fma(beta, p[q] - omega * v[q], r[q]) : fma(-alpha, v[q], r[q]);
+            const V nv = mode == 0 ? fma(beta, p[q] - omega * v[q], r[q]) : fma(-alpha, v[q], r[q]);
             p[q] = nv;
             w[c] = nv;
         }
 #pragma unroll
         for (int rr = 0; rr < NC; ++rr) {
-            double acc = 0.0;
+            V acc = (V)0;
 #pragma unroll
             for (int k = 0; k < NC; ++k) acc = fma(Pinv[(long long)(rr * NC + k) * N + i], w[k], acc);
             z[(long long)rr * N + i] = acc;
@@ -289,29 +288,31 @@ __global__ void __launch_bounds__(kThreads) imp_comb_precond_kernel(long long N,
 }
 
 // x += alpha ph + omega sh;  r = s - omega t;  partial sums of (r, r) and (rh, r)
-__global__ void __launch_bounds__(kThreads) imp_xr_kernel(long long n, double* x, const double* ph, const double* sh,
-                                                          double* r, const double* s, const double* t, const double* rh,
-                                                          double* partials, const double* sc) {
+template <typename V>
+__global__ void __launch_bounds__(kThreads) imp_xr_kernel(long long n, V* x, const V* ph, const V* sh, V* r,
+                                                          const V* s, const V* t, const V* rh, double* partials,
+                                                          const double* sc) {
     if (done(sc)) return;
-    const double alpha = sc[S_ALPHA], omega = sc[S_OMEGA];
+    const V alpha = (V)sc[S_ALPHA], omega = (V)sc[S_OMEGA];
     double a0 = 0.0, a1 = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         x[i] = fma(alpha, ph[i], fma(omega, sh[i], x[i]));
-        const double rv = fma(-omega, t[i], s[i]);
+        const V rv = fma(-omega, t[i], s[i]);
         r[i] = rv;
-        a0 = fma(rv, rv, a0);
-        a1 = fma(rh[i], rv, a1);
+        a0 = fma((double)rv, (double)rv, a0);
+        a1 = fma((double)rh[i], (double)rv, a1);
     }
     block_partials(a0, a1, 2, partials);
 }
 
 // per-block partial sums of x.y and x.z (z may be null), for the start of the iteration
-__global__ void __launch_bounds__(kThreads) imp_dot2_kernel(const double* x, const double* y, const double* z,
-                                                            long long n, double* partials) {
+template <typename V>
+__global__ void __launch_bounds__(kThreads) imp_dot2_kernel(const V* x, const V* y, const V* z, long long n,
+                                                            double* partials) {
     double a0 = 0.0, a1 = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        a0 = fma(x[i], y[i], a0);
-        if (z) a1 = fma(x[i], z[i], a1);
+        a0 = fma((double)x[i], (double)y[i], a0);
+        if (z) a1 = fma((double)x[i], (double)z[i], a1);
     }
     block_partials(a0, a1, z ? 2 : 1, partials);
 }
@@ -419,16 +420,45 @@ __global__ void __launch_bounds__(kThreads) imp_push_kernel(const ImpArgs<T> A, 
     }
 }
 
-// r = b - r (r holds Op(x0)); rh = r; p = v = 0
-__global__ void __launch_bounds__(kThreads) imp_init_kernel(long long n, const double* b, double* r, double* rh,
-                                                            double* p, double* v) {
+// r = b - r (r holds Op(x0)), or r = b when x0 = 0 (zero: x set to 0 too);
+// rh = r; p = v = 0
+template <typename V>
+__global__ void __launch_bounds__(kThreads) imp_init_kernel(long long n, const V* b, V* r, V* rh, V* p, V* v,
+                                                            V* x, int zero) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const double rv = b[i] - r[i];
+        const V rv = zero ? b[i] : b[i] - r[i];
         r[i] = rv;
         rh[i] = rv;
-        p[i] = 0.0;
-        v[i] = 0.0;
+        p[i] = (V)0;
+        v[i] = (V)0;
+        if (zero) x[i] = (V)0;
     }
+}
+
+// Outer step of the mixed-precision solve: r64 = b - r64 (r64 holds Op(x) in
+// FP64), its float copy rf, and the partial sums of (r64, r64)
+__global__ void __launch_bounds__(kThreads) imp_resid_kernel(long long n, const double* b, double* r64, float* rf,
+                                                             double* partials) {
+    double a0 = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double rv = b[i] - r64[i];
+        r64[i] = rv;
+        rf[i] = (float)rv;
+        a0 = fma(rv, rv, a0);
+    }
+    block_partials(a0, 0.0, 1, partials);
+}
+
+// x += d (the FP32 correction of the inner solve)
+__global__ void __launch_bounds__(kThreads) imp_correct_kernel(long long n, double* x, const float* d) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] += (double)d[i];
+}
+
+// float copies of the step's operator blocks, preconditioner and tap coefficients
+__global__ void __launch_bounds__(kThreads) imp_to_float_kernel(long long n, const double* src, float* dst) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
 }
 
 // ------------------------------------------------------------------ the paper's variable
@@ -1093,26 +1123,127 @@ __global__ void __launch_bounds__(kThreads) stp_final_kernel(const ImpArgs<T> A,
 
 // ------------------------------------------------------------------ host side
 // Krylov workspace views (10 vectors of nc N, the point blocks and the
-// preconditioner inverses, partial sums, device scalars)
+// preconditioner inverses, the tap coefficients, the FP32 section of the inner
+// solve, the paper's variable's h, partial sums, device scalars)
 template <int NC>
 struct KryView {
     double *b, *x, *r, *rh, *p, *v, *sv, *t, *ph, *sh, *Mb, *Pinv, *Cf, *H, *partials, *sc;
+    float *Mbf, *Pinvf, *Cff;                           // float copies of Mb, Pinv, Cf
+    float *xf, *rf, *rhf, *pf, *vf, *svf, *tf, *phf, *shf;   // inner-solve vectors
     KryView(double* w, double* parts, long long N) {
+        constexpr int D = NC == 3 ? 2 : 3;
         const long long n = (long long)NC * N;
         b = w; x = w + n; r = w + 2 * n; rh = w + 3 * n; p = w + 4 * n; v = w + 5 * n; sv = w + 6 * n;
         t = w + 7 * n; ph = w + 8 * n; sh = w + 9 * n;
         Mb = w + 10 * n;
         Pinv = Mb + (long long)NC * NC * N;
         Cf = Pinv + (long long)NC * NC * N;                  // 4 taps x dim axes
-        H = Cf + 4LL * (NC == 3 ? 2 : 3) * N;                 // the paper's variable only
+        float* f = reinterpret_cast<float*>(Cf + 4LL * D * N);
+        Mbf = f; Pinvf = Mbf + (long long)NC * NC * N; Cff = Pinvf + (long long)NC * NC * N;
+        float* fv = Cff + 4LL * D * N;
+        xf = fv; rf = fv + n; rhf = fv + 2 * n; pf = fv + 3 * n; vf = fv + 4 * n; svf = fv + 5 * n;
+        tf = fv + 6 * n; phf = fv + 7 * n; shf = fv + 8 * n;
+        H = Cf + 4LL * D * N + kry_float_doubles(NC, D, N);   // the paper's variable only
         partials = parts;
         sc = parts + kPartialSets * kImpBlocks;
     }
 };
 
-// BiCGStab on Op x = b from the initial guess in x (b and x filled, Mb and Pinv
-// set up, all on stream st).  Leaves the last iterate in x, latches
-// TFS_FLAG_NOCONV when the tolerance was not reached; synchronises st.
+// One BiCGStab run (right block-Jacobi preconditioning) on Op x = b with
+// vectors and coefficients of type V (FP64: the step's operator; FP32: its
+// float copy in the inner solve), from x (x_zero: from 0), to the relative
+// residual tol (|r| <= tol |b|) or maxit iterations.  The iteration runs on the
+// device scalars sc; the host looks at them every kCheck passes.  Returns the
+// iterations, the last recursive (r, r) and (b, b); synchronises st.
+template <typename V>
+struct BiVecs {
+    const V* b;
+    V *x, *r, *rh, *p, *v, *sv, *t, *ph, *sh;
+    const V *Mb, *Pinv, *Cf;
+};
+
+template <typename T, int DIM, typename V>
+cudaError_t bicgstab(const ImpArgs<T>& a, const BiVecs<V>& K, double* partials, double* sc, double tol, int maxit,
+                     bool x_zero, cudaStream_t st, int* iters, double* rr_out, double* bnorm2_out) {
+    constexpr int NC = Packed<DIM>::NC;
+    const long long N = a.N;
+    const long long n = (long long)NC * N;
+    const unsigned bs = (unsigned)kImpBlocks;
+    cudaError_t e = cudaSuccess;
+    auto ok = [&]() {
+        if (e == cudaSuccess) e = cudaGetLastError();
+        return e == cudaSuccess;
+    };
+    double hs[S_COUNT] = {};
+    hs[S_RHO] = hs[S_ALPHA] = hs[S_OMEGA] = 1.0;
+    hs[S_TOL2] = tol * tol;
+    e = cudaMemcpyAsync(sc, hs, sizeof(hs), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    imp_dot2_kernel<V><<<bs, kThreads, 0, st>>>(K.b, K.b, nullptr, n, partials);
+    if (!ok()) return e;
+    imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 3);
+    if (!ok()) return e;
+    e = cudaMemcpyAsync(hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    *bnorm2_out = hs[S_BNORM2];
+    if (hs[S_BNORM2] == 0.0) {
+        e = cudaMemsetAsync(K.x, 0, sizeof(V) * (size_t)n, st);   // b = 0: x = 0
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        *iters = 0;
+        *rr_out = 0.0;
+        return e;
+    }
+    if (!x_zero) {
+        imp_apply_kernel<T, DIM, V><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Cf, K.x, K.r, nullptr, nullptr, partials, sc);
+        if (!ok()) return e;
+    }
+    imp_init_kernel<V><<<bs, kThreads, 0, st>>>(n, K.b, K.r, K.rh, K.p, K.v, K.x, x_zero ? 1 : 0);
+    if (!ok()) return e;
+    imp_dot2_kernel<V><<<bs, kThreads, 0, st>>>(K.r, K.r, K.rh, n, partials);
+    if (!ok()) return e;
+    imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 4);
+    if (!ok()) return e;
+    constexpr int kCheck = 8;
+    for (int it = 0; it < maxit; ++it) {
+        imp_beta_kernel<<<1, 1, 0, st>>>(sc);
+        imp_comb_precond_kernel<NC, V><<<bs, kThreads, 0, st>>>(N, K.Pinv, 0, K.p, K.r, K.v, K.ph, sc);
+        imp_apply_kernel<T, DIM, V><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Cf, K.ph, K.v, K.rh, nullptr, partials, sc);
+        imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 1);
+        imp_comb_precond_kernel<NC, V><<<bs, kThreads, 0, st>>>(N, K.Pinv, 1, K.sv, K.r, K.v, K.sh, sc);
+        imp_apply_kernel<T, DIM, V><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Cf, K.sh, K.t, K.sv, K.t, partials, sc);
+        imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 2);
+        imp_xr_kernel<V><<<bs, kThreads, 0, st>>>(n, K.x, K.ph, K.sh, K.r, K.sv, K.t, K.rh, partials, sc);
+        imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 0);
+        if (!ok()) return e;
+        if ((it + 1) % kCheck == 0 || it + 1 == maxit) {
+            e = cudaMemcpyAsync(hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return e;
+            if (hs[S_DONE] != 0.0) break;
+        }
+    }
+    e = cudaMemcpyAsync(hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    *iters = (int)hs[S_ITERS];
+    *rr_out = hs[S_RR];
+    return e;
+}
+
+// Op x = b to the relative residual a.tol (|b - Op x| <= tol |b|, Op in FP64)
+// from the initial guess in x (b, x filled; Mb, Pinv, Cf set up, all on st),
+// by mixed-precision defect correction: the FP64 residual r = b - Op x, an
+// inner BiCGStab on the float copy of the operator for the correction d
+// (Op d = r to the relative residual the outer target asks for, at most 1e-6
+// below |r|: float arithmetic ends there), x += d, until the FP64 residual
+// meets the target.  The inner iterations then run on float vectors and float
+// coefficients (FP32 arithmetic and half the bytes; on this GPU FP64 runs at
+// 1/64 of the FP32 rate); the FP64 residual keeps the accuracy of the result
+// that of the FP64 system.  If an outer pass gains less than a factor 16, the
+// FP64 BiCGStab finishes from the current x.  Leaves the result in x,
+// latches TFS_FLAG_NOCONV when the tolerance was not reached; synchronises st.
+// Returns the iterations (inner and FP64 ones) and the final FP64 relative
+// residual.
 template <typename T, int DIM>
 cudaError_t krylov_solve(const ImpArgs<T>& a, const KryView<Packed<DIM>::NC>& K, cudaStream_t st, int* iters,
                          double* relres) {
@@ -1127,58 +1258,84 @@ cudaError_t krylov_solve(const ImpArgs<T>& a, const KryView<Packed<DIM>::NC>& K,
         if (e == cudaSuccess) e = cudaGetLastError();
         return e == cudaSuccess;
     };
+    // float copies of the operator (the blocks and their inverses are
+    // contiguous; the taps may be the transposed ones of an adjoint solve,
+    // kept elsewhere)
+    imp_to_float_kernel<<<bs, kThreads, 0, st>>>(2LL * NC * NC * N, K.Mb, K.Mbf);
+    imp_to_float_kernel<<<bs, kThreads, 0, st>>>(4LL * DIM * N, K.Cf, K.Cff);
+    if (!ok()) return e;
+    // device scalars of the outer FP64 residual (never "done": the FP64 operator
+    // kernel skips its work once the scalars it is given say so)
+    double* sco = sc + 16;
+    {
+        double z[S_COUNT] = {};
+        e = cudaMemcpyAsync(sco, z, sizeof(z), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
+    // inner solve: right-hand side rf (overwritten by the residual: b is read
+    // only before the init kernel sets r = b), correction xf
+    const BiVecs<float> Fv{K.rf, K.xf, K.rf, K.rhf, K.pf, K.vf, K.svf, K.tf, K.phf, K.shf, K.Mbf, K.Pinvf, K.Cff};
     double hs[S_COUNT] = {};
-    hs[S_RHO] = hs[S_ALPHA] = hs[S_OMEGA] = 1.0;
-    hs[S_TOL2] = a.tol * a.tol;
-    e = cudaMemcpyAsync(sc, hs, sizeof(hs), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return e;
-    imp_dot2_kernel<<<bs, kThreads, 0, st>>>(K.b, K.b, nullptr, n, partials);
+    double bnorm2 = 0.0, rr = 0.0;
+    int total = 0;
+    bool converged = false;
+    // (b, b)
+    imp_dot2_kernel<double><<<bs, kThreads, 0, st>>>(K.b, K.b, nullptr, n, partials);
     if (!ok()) return e;
     imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 3);
     if (!ok()) return e;
     e = cudaMemcpyAsync(hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
-    const double bnorm2 = hs[S_BNORM2];
-    bool converged = false;
+    bnorm2 = hs[S_BNORM2];
     if (bnorm2 == 0.0) {
         e = cudaMemsetAsync(K.x, 0, sizeof(double) * (size_t)n, st);   // b = 0: x = 0
-        converged = true;
-        hs[S_RR] = 0.0;
-        hs[S_ITERS] = 0.0;
-    } else {
-        imp_apply_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Cf, K.x, K.r, nullptr, nullptr, partials, sc);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        *iters = 0;
+        *relres = 0.0;
+        return e;
+    }
+    const double tol2 = a.tol * a.tol * bnorm2;
+    double prev_rr = -1.0;
+    constexpr int kOuterMax = 12;
+    for (int outer = 0; outer < kOuterMax; ++outer) {
+        // r = b - Op x in FP64, its float copy, (r, r)
+        imp_apply_kernel<T, DIM, double><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Cf, K.x, K.r, nullptr, nullptr,
+                                                                   partials, sco);
+        imp_resid_kernel<<<bs, kThreads, 0, st>>>(n, K.b, K.r, K.rf, partials);
+        imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sco, 3);
         if (!ok()) return e;
-        imp_init_kernel<<<bs, kThreads, 0, st>>>(n, K.b, K.r, K.rh, K.p, K.v);
-        if (!ok()) return e;
-        imp_dot2_kernel<<<bs, kThreads, 0, st>>>(K.r, K.r, K.rh, n, partials);
-        if (!ok()) return e;
-        imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 4);
-        if (!ok()) return e;
-        // the iteration runs on device scalars; the host looks at them every kCheck passes
-        constexpr int kCheck = 8;
-        for (int it = 0; it < a.maxit; ++it) {
-            imp_beta_kernel<<<1, 1, 0, st>>>(sc);
-            imp_comb_precond_kernel<NC><<<bs, kThreads, 0, st>>>(N, K.Pinv, 0, K.p, K.r, K.v, K.ph, sc);
-            imp_apply_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Cf, K.ph, K.v, K.rh, nullptr, partials, sc);
-            imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 1);
-            imp_comb_precond_kernel<NC><<<bs, kThreads, 0, st>>>(N, K.Pinv, 1, K.sv, K.r, K.v, K.sh, sc);
-            imp_apply_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Cf, K.sh, K.t, K.sv, K.t, partials, sc);
-            imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 2);
-            imp_xr_kernel<<<bs, kThreads, 0, st>>>(n, K.x, K.ph, K.sh, K.r, K.sv, K.t, K.rh, partials, sc);
-            imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 0);
-            if (!ok()) return e;
-            if ((it + 1) % kCheck == 0 || it + 1 == a.maxit) {
-                e = cudaMemcpyAsync(hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, st);
-                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-                if (e != cudaSuccess) return e;
-                if (hs[S_DONE] != 0.0) break;
-            }
-        }
-        e = cudaMemcpyAsync(hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(hs, sco, sizeof(hs), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return e;
-        converged = hs[S_RR] <= hs[S_TOL2] * bnorm2;
+        rr = hs[S_BNORM2];
+        if (rr <= tol2) {
+            converged = true;
+            break;
+        }
+        if (prev_rr >= 0.0 && rr > prev_rr / 16.0) break;   // the float inner solve no longer gains: FP64 below
+        prev_rr = rr;
+        // inner: Op d = r in float, to the target relative to |r| (not below 1e-6),
+        // at most maxit iterations per pass
+        double inner_tol = std::sqrt(tol2 / rr) * 0.5;
+        if (inner_tol < 1e-6) inner_tol = 1e-6;
+        int it = 0;
+        double irr = 0.0, ib2 = 0.0;
+        e = bicgstab<T, DIM, float>(a, Fv, partials, sc, inner_tol, a.maxit, true, st, &it, &irr, &ib2);
+        if (e != cudaSuccess) return e;
+        total += it;
+        imp_correct_kernel<<<bs, kThreads, 0, st>>>(n, K.x, K.xf);
+        if (!ok()) return e;
+    }
+    if (!converged) {
+        // FP64 BiCGStab from the current iterate
+        const BiVecs<double> D{K.b, K.x, K.r, K.rh, K.p, K.v, K.sv, K.t, K.ph, K.sh, K.Mb, K.Pinv, K.Cf};
+        int it = 0;
+        double b2 = 0.0;
+        e = bicgstab<T, DIM, double>(a, D, partials, sc, a.tol, a.maxit, false, st, &it, &rr, &b2);
+        if (e != cudaSuccess) return e;
+        total += it;
+        converged = rr <= tol2;
     }
     if (!converged) {
         unsigned f = 0u;
@@ -1189,8 +1346,8 @@ cudaError_t krylov_solve(const ImpArgs<T>& a, const KryView<Packed<DIM>::NC>& K,
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return e;
     }
-    *iters = (int)hs[S_ITERS];
-    *relres = bnorm2 > 0.0 ? std::sqrt(hs[S_RR] / bnorm2) : 0.0;
+    *iters = total;
+    *relres = std::sqrt(rr / bnorm2);
     return e;
 }
 

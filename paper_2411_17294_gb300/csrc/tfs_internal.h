@@ -142,6 +142,14 @@ struct ImpArgs {
 };
 constexpr int kImpBlocks = 1024;   // blocks of the implicit-step kernels (and reduction partials)
 
+// FP32 section of the implicit-transport workspace (the inner solve of the
+// mixed-precision Krylov scheme): float copies of the point blocks and their
+// inverses (2 nc^2 N), of the tap coefficients (4 d N) and nine Krylov vectors
+// (9 nc N), counted in doubles (rounded up).
+__host__ __device__ __forceinline__ long long kry_float_doubles(int nc, int dim, long long N) {
+    return ((2LL * nc * nc + 4LL * dim + 9LL * nc) * N + 1) / 2;
+}
+
 // host driver of one implicit step (BiCGStab, block-Jacobi preconditioned);
 // synchronises `s`; returns the iterations used and the final relative residual
 cudaError_t run_implicit_f64(const ImpArgs<double>& a, cudaStream_t s, int* iters, double* relres);
