@@ -230,6 +230,40 @@ int tfs_step(tfs_handle h, const void* grad_u_n, const void* grad_u_nm1, const v
    `stream`; TFS_ERR_STATE before tfs_set_state. */
 int tfs_get_stress(tfs_handle h, void* out, void* stream);
 
+/* Slab decomposition (for running one periodic domain on several GPUs).  The
+   paper's runtime partitions its meshes over MPI ranks (Section 5, the
+   experimental setup); this is the library's counterpart for the periodic
+   grid: the domain is cut along its slowest axis (z in 3D, y in 2D) into
+   slabs, one handle per slab created with the slab's own grid (n[d-1] its
+   plane count, L[d-1] its length, the other axes those of the whole domain).
+   Every point's update is local except the transport stencil, which reaches
+   R = 2 planes into the neighbouring slabs; each step therefore takes the
+   neighbours' boundary planes of sigma^n and sigma^{n-1} (both enter E =
+   2 sigma^n - sigma^{n-1}).  A slab step of the stress form with explicit
+   transport (or none) gives, at every point, the same result as the step of
+   the whole domain.
+   A halo buffer is [2 levels][nc][R][plane] elements of the handle's type
+   (level 0 sigma^n, level 1 sigma^{n-1}; plane = n[0] points in 2D, n[0] n[1]
+   in 3D, x fastest), device memory owned by the caller; tfs_halo_bytes gives
+   its size (0 for an invalid handle). */
+size_t tfs_halo_bytes(tfs_handle h);
+
+/* The slab's own boundary planes as its neighbours need them, after the last
+   step (or tfs_set_state): lo <- its first R planes (the lower neighbour's
+   halo_hi), hi <- its last R planes (the upper neighbour's halo_lo); either
+   may be NULL.  Enqueues device copies on `stream`.  TFS_ERR_ARG for the
+   paper's variable or a slab thinner than R planes. */
+int tfs_get_halo(tfs_handle h, void* lo, void* hi, void* stream);
+
+/* One step of a slab: tfs_step with the planes beyond the slab's ends read
+   from halo_lo (the lower neighbour's last R planes: slab coordinates -R ..
+   -1) and halo_hi (the upper neighbour's first R planes: n[d-1] .. n[d-1] + R
+   - 1) instead of wrapping around the slab.  Stress form with transport 0 or
+   1 (TFS_ERR_ARG otherwise, and for NULL halos); other errors as tfs_step.
+   The halos are read by the transport pre-pass, on `stream`. */
+int tfs_step_slab(tfs_handle h, const void* grad_u_n, const void* grad_u_nm1, const void* u, const void* halo_lo,
+                  const void* halo_hi, void* stream);
+
 /* Measurement hook (no counterpart in the paper): with two cudaEvent_t
    (passed as void*, both or neither), every later tfs_step records ev_before
    on its stream just before the step kernel and ev_after just after it (the

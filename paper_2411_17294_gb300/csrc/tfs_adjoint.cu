@@ -66,8 +66,6 @@ __host__ __device__ __forceinline__ size_t adj_stage_bytes(const AdjStageMap& S)
 template <typename T, int DIM>
 __device__ __forceinline__ const T* adj_tsrc(const AdjArgs<T>& A, const AdjStageMap& S, int plane) {
     const long long N = A.N;
-    if (plane < S.e2) return A.ell_prev + (long long)plane * N;
-    if (plane < S.kn) return A.ell_prev2 + (long long)(plane - S.e2) * N;
     if (plane < S.km) return A.kap_n + (long long)(plane - S.kn) * N;
     if (plane < S.sig) return A.kap_nm1 + (long long)(plane - S.km) * N;
     return A.sig_np1 + (long long)(plane - S.sig) * N;
@@ -120,8 +118,24 @@ __device__ __forceinline__ void adj_issue(const AdjArgs<T>& A, const AdjStageMap
                                           int tid, int nthr, bool vec16, int tb_begin, int tb_end, bool doubles) {
     T* tb = reinterpret_cast<T*>(buf);
     double* db = reinterpret_cast<double*>(buf + (size_t)S.tplanes * kTileA * sizeof(T));
-    stage_planes<T>(tb, tb_begin, tb_end, [&](int pl) { return adj_tsrc<T, DIM>(A, S, pl); }, t0, A.N, tid, nthr,
-                    vec16);
+    // the adjoint mode ring is tile-major (mode_index): each of its rows is 32
+    // stored elements (padding past N included), copied in 16-byte chunks
+    {
+        constexpr int EPC = 16 / sizeof(T);
+        constexpr int CPP = kTileA / EPC;
+        const int mnc = S.e2;
+        const int lo = tb_begin, hi = min(tb_end, S.kn);
+        for (int q = tid; q < (hi - lo) * CPP; q += nthr) {
+            const int plane = lo + q / CPP;
+            const int k = q % CPP;
+            const T* row = plane < mnc ? A.ell_prev + mode_index(t0, plane, mnc)
+                                       : A.ell_prev2 + mode_index(t0, plane - mnc, mnc);
+            cp_async16(tb + plane * kTileA + k * EPC, row + k * EPC, 16);
+        }
+    }
+    if (max(tb_begin, S.kn) < tb_end)
+        stage_planes<T>(tb, max(tb_begin, S.kn), tb_end, [&](int pl) { return adj_tsrc<T, DIM>(A, S, pl); }, t0,
+                        A.N, tid, nthr, vec16);
     if (doubles)
         stage_planes<double>(db, 0, S.dplanes, [&](int pl) { return adj_dsrc<T, DIM>(A, S, pl); }, t0, A.N, tid,
                              nthr, vec16);
@@ -329,8 +343,8 @@ __device__ __forceinline__ void adj_tile(const AdjArgs<T>& A, const AdjStageMap&
     // ---- new adjoint mode level: lamQ_j = -c_j z_j - eta_j lamR, over the oldest slot
     if (!classic && active) {
         const T* zv = tb + (S.e2 + w) * kTileA + lane;
-        T* out = A.ell_prev2 + (long long)w * N + p;
-        const long long stride = (long long)NC * N;
+        T* out = A.ell_prev2 + mode_index(p, w, m * NC);   // tile-major ring, row j NC + c
+        constexpr long long stride = (long long)NC * kTileA;
         if constexpr (F32) {
             float l[CPW];
 #pragma unroll
@@ -340,7 +354,7 @@ __device__ __forceinline__ void adj_tile(const AdjArgs<T>& A, const AdjStageMap&
                 const float ej = A.mcf.eta_hi[j], cjf = A.mcf.c[j];
 #pragma unroll
                 for (int cc = 0; cc < CPW; ++cc)
-                    __stcs(out + j * stride + (long long)cc * W * N,
+                    __stcs(out + j * stride + (long long)cc * W * kTileA,
                            __fmaf_rn(-ej, l[cc], -cjf * zv[(j * NC + cc * W) * kTileA]));
             }
         } else {
@@ -351,7 +365,7 @@ __device__ __forceinline__ void adj_tile(const AdjArgs<T>& A, const AdjStageMap&
             for (int j = 0; j < m; ++j)
 #pragma unroll
                 for (int cc = 0; cc < CPW; ++cc)
-                    __stcs(out + j * stride + (long long)cc * W * N,
+                    __stcs(out + j * stride + (long long)cc * W * kTileA,
                            (T)fma(-A.mc.eta[j], l[cc], -A.mc.c[j] * (double)zv[(j * NC + cc * W) * kTileA]));
         }
     }

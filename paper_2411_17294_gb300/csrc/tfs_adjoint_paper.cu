@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kThreads) paper_adjoint_kernel(const PaperAdjA
                 const float rh = A.mcf.rho[jj];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    const long long q = ((long long)jj * NC + c) * N + p;
+                    const long long q = mode_index(p, jj * NC + c, A.m * NC);
                     const float z = __fmaf_rn(0.5f, (float)A.ell_prev2[q], -2.0f * (float)A.ell_prev[q]);
                     zs[(jj * NC + c) * kThreads + tid] = z;
                     const float yv = __fmaf_rn(rh, z, -comp[c]);
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kThreads) paper_adjoint_kernel(const PaperAdjA
             for (int jj = 0; jj < A.m; ++jj) {
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    const long long q = ((long long)jj * NC + c) * N + p;
+                    const long long q = mode_index(p, jj * NC + c, A.m * NC);
                     const double zj = kB1 * (double)A.ell_prev[q] + kB2 * (double)A.ell_prev2[q];
                     ss[c] = fma(A.mc.rho[jj], zj, ss[c]);        // rho_j = dt c_j in this variable
                 }
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kThreads) paper_adjoint_kernel(const PaperAdjA
                 const float eh = A.mcf.eta_hi[jj], el = A.mcf.eta_lo[jj], cj = A.mcf.c[jj];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    const long long q = ((long long)jj * NC + c) * N + p;
+                    const long long q = mode_index(p, jj * NC + c, A.m * NC);
                     const float z = zs[(jj * NC + c) * kThreads + tid];
                     A.ell_prev2[q] = (T)__fmaf_rn(eh, lh[c], __fmaf_rn(el, lh[c], -cj * z));
                 }
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kThreads) paper_adjoint_kernel(const PaperAdjA
             for (int jj = 0; jj < A.m; ++jj) {
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    const long long q = ((long long)jj * NC + c) * N + p;
+                    const long long q = mode_index(p, jj * NC + c, A.m * NC);
                     const double zj = kB1 * (double)A.ell_prev[q] + kB2 * (double)A.ell_prev2[q];
                     A.ell_prev2[q] = (T)(A.mc.eta[jj] * (double)lh[c] - A.mc.c[jj] * zj);
                 }
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kThreads) paper_start_adjoint_kernel(const Pap
             lamPsi[c] = A.lam_psi ? A.lam_psi[q] : 0.0;
             double a2 = 0.0, a1 = 0.0;
             for (int jj = 0; jj < A.m; ++jj) {
-                const long long qm = ((long long)jj * NC + c) * N + p;
+                const long long qm = mode_index(p, jj * NC + c, A.m * NC);
                 const double z = kB1 * (double)A.ell_prev[qm] + kB2 * (double)A.ell_prev2[qm];
                 a2 = fma(C.inv_den[jj], z, a2);
                 a1 = fma(C.inv_den[jj] * C.inv_den[jj], z, a1);

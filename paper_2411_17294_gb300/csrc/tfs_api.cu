@@ -26,6 +26,7 @@ constexpr size_t kAlign = 256;
 constexpr size_t kHeaderBytes = 256;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+constexpr int kHaloPlanes = 2;   // radius of the upwind3 stencil: the planes a slab's neighbours need
 
 }  // namespace
 
@@ -73,6 +74,9 @@ struct tfs_ctx {
     cudaStream_t last_stream = nullptr;
     // optional events recorded around the step kernel of every tfs_step
     cudaEvent_t ev_before = nullptr, ev_after = nullptr;
+    // neighbours' boundary planes of a slab step (tfs_step_slab; null otherwise)
+    const void* halo_lo = nullptr;
+    const void* halo_hi = nullptr;
     // cached stability bounds of the explicit transport (invalidated by SOE and stencil changes)
     bool lim_valid = false;
     double lam_star = 0.0;   // advection: largest stable dt |u| / h (1D)
@@ -101,6 +105,10 @@ struct tfs_ctx {
     bool checked_transport() const { return transport == 1; }
     bool implicit_transport() const { return transport == 2; }
     bool paper() const { return form == TFS_FORM_PAPER; }
+    // slab decomposition along the slowest axis: points per plane of that axis
+    // and its length
+    long long slab_plane() const { return dim == 3 ? n[0] * n[1] : n[0]; }
+    long long slab_len() const { return n[dim - 1]; }
 };
 
 namespace {
@@ -683,6 +691,9 @@ int do_step(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* s
         a.trans = (double*)h->trans;
         a.modes_n = (const double*)h->modes[cm];
         a.modes_nm1 = (double*)h->modes[pm];
+        a.halo_lo = (const double*)h->halo_lo;
+        a.halo_hi = (const double*)h->halo_hi;
+        a.halo_r = kHaloPlanes;
         a.g = g_alpha(h, h->step);
         a.mc = h->mcd;
         if (h->paper()) {
@@ -704,6 +715,9 @@ int do_step(tfs_ctx* h, const void* kn, const void* knm1, const void* u, void* s
         a.trans = (float*)h->trans;
         a.modes_n = (const float*)h->modes[cm];
         a.modes_nm1 = (float*)h->modes[pm];
+        a.halo_lo = (const float*)h->halo_lo;
+        a.halo_hi = (const float*)h->halo_hi;
+        a.halo_r = kHaloPlanes;
         a.g = g_alpha(h, h->step);
         a.src_f2 = split_f2(a.dt * a.G * a.g);
         a.mc = h->mcf;
@@ -937,6 +951,45 @@ int tfs_set_state(tfs_handle h, const void* sigma0, void* stream) {
 int tfs_step(tfs_handle h, const void* grad_u_n, const void* grad_u_nm1, const void* u, void* stream) {
     if (!valid_handle(h)) return TFS_ERR_ARG;
     return do_step(h, grad_u_n, grad_u_nm1, u, nullptr, (cudaStream_t)stream);
+}
+
+size_t tfs_halo_bytes(tfs_handle h) {
+    if (!valid_handle(h)) return 0;
+    return 2 * (size_t)h->nc * kHaloPlanes * (size_t)h->slab_plane() * h->es();
+}
+
+int tfs_get_halo(tfs_handle h, void* lo, void* hi, void* stream) {
+    if (!valid_handle(h) || (!lo && !hi)) return TFS_ERR_ARG;
+    if (!h->ws) return TFS_ERR_NOWORKSPACE;
+    if (!h->state_set) return TFS_ERR_STATE;
+    if (h->paper() || h->slab_len() < kHaloPlanes) return TFS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    const size_t es = h->es();
+    const size_t width = (size_t)kHaloPlanes * (size_t)h->slab_plane() * es;   // R planes of one component
+    const char* lv[2] = {h->sig[h->cur_sig], h->sig[h->prev_sig]};
+    for (int side = 0; side < 2; ++side) {
+        char* dst = (char*)(side == 0 ? lo : hi);
+        if (!dst) continue;
+        const size_t first = side == 0 ? 0 : (size_t)(h->slab_len() - kHaloPlanes) * (size_t)h->slab_plane() * es;
+        for (int l = 0; l < 2; ++l) {
+            cudaError_t e = cudaMemcpy2DAsync(dst + (size_t)l * h->nc * width, width, lv[l] + first,
+                                              (size_t)h->N * es, width, (size_t)h->nc, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return TFS_ERR_CUDA;
+        }
+    }
+    return TFS_OK;
+}
+
+int tfs_step_slab(tfs_handle h, const void* grad_u_n, const void* grad_u_nm1, const void* u, const void* halo_lo,
+                  const void* halo_hi, void* stream) {
+    if (!valid_handle(h) || !halo_lo || !halo_hi) return TFS_ERR_ARG;
+    if (h->paper() || h->implicit_transport() || h->slab_len() < kHaloPlanes) return TFS_ERR_ARG;
+    h->halo_lo = halo_lo;
+    h->halo_hi = halo_hi;
+    const int rc = do_step(h, grad_u_n, grad_u_nm1, u, nullptr, (cudaStream_t)stream);
+    h->halo_lo = h->halo_hi = nullptr;
+    return rc;
 }
 
 int tfs_get_stress(tfs_handle h, void* out, void* stream) {

@@ -209,28 +209,35 @@ __device__ __forceinline__ void load_stencil(const FwdArgs<T>& A, int c, int ste
     L.m0 = __ldg(sm + p);
 #pragma unroll
     for (int ax = 0; ax < DIM; ++ax) {
-        // neighbour indices with periodic wrap (|offset| <= 2, any n >= 1)
-        auto nb = [&](int off) -> long long {
+        // both levels at offset off (|off| <= 2) along ax: periodic wrap, or on a
+        // slab the slowest axis beyond the grid from the halo planes
+        auto load2 = [&](int off, T& vn, T& vm) {
             int v = (int)co[ax] + off;
             const int nax = (int)nn[ax];
+            if ((v < 0 || v >= nax) && ax == DIM - 1 && A.halo_lo) {
+                const long long pl = ax == 2 ? (long long)nn[0] * nn[1] : (long long)nn[0];
+                const long long in_plane = p - (long long)co[ax] * pl;
+                const T* hb = v < 0 ? A.halo_lo : A.halo_hi;
+                const int k = v < 0 ? v + A.halo_r : v - nax;
+                const long long q = ((long long)c * A.halo_r + k) * pl + in_plane;
+                vn = __ldg(hb + q);
+                vm = __ldg(hb + (long long)(DIM == 2 ? 3 : 6) * A.halo_r * pl + q);
+                return;
+            }
             if (v < 0) v += nax;
             if (v < 0) v += nax;
             if (v >= nax) v -= nax;
             if (v >= nax) v -= nax;
-            return p + ((long long)v - (long long)co[ax]) * strides[ax];
+            const long long q = p + ((long long)v - (long long)co[ax]) * strides[ax];
+            vn = __ldg(sn + q);
+            vm = __ldg(sm + q);
         };
         L.u[ax] = __ldg(A.u + (long long)ax * A.N + p);
-        const long long q1 = nb(-1), q2 = nb(1);
-        L.n[ax][1] = __ldg(sn + q1);
-        L.m[ax][1] = __ldg(sm + q1);
-        L.n[ax][2] = __ldg(sn + q2);
-        L.m[ax][2] = __ldg(sm + q2);
+        load2(-1, L.n[ax][1], L.m[ax][1]);
+        load2(1, L.n[ax][2], L.m[ax][2]);
         if (stencil == 0) {
-            const long long q0 = nb(-2), q3 = nb(2);
-            L.n[ax][0] = __ldg(sn + q0);
-            L.m[ax][0] = __ldg(sm + q0);
-            L.n[ax][3] = __ldg(sn + q3);
-            L.m[ax][3] = __ldg(sm + q3);
+            load2(-2, L.n[ax][0], L.m[ax][0]);
+            load2(2, L.n[ax][3], L.m[ax][3]);
         } else {
             L.n[ax][0] = L.m[ax][0] = L.n[ax][3] = L.m[ax][3] = (T)0;
         }
@@ -399,7 +406,24 @@ __global__ void __launch_bounds__(kTX * kTY) transport_tiled(const FwdArgs<T> A,
     const bool lap = A.eps != 0.0;
     const float ccoef = (float)A.courant_coef, climit = (float)A.courant_limit;
     const float ihf[3] = {(float)A.inv_h[0], (float)A.inv_h[1], (float)A.inv_h[2]};
+    // E at (gx, gy, gz); the slowest coordinate (gz in 3D, gy in 2D) may lie up
+    // to kHalo outside the grid: it wraps, or on a slab comes from the halo planes
     auto Eat = [&](int c, int gx, int gy, int gz) -> T {
+        int sl = DIM == 3 ? gz : gy;
+        const int ns = DIM == 3 ? n2 : n1;
+        if (sl < 0 || sl >= ns) {
+            if (A.halo_lo) {
+                const long long pl = DIM == 3 ? plane : (long long)n0;
+                const long long in_plane = DIM == 3 ? gx + (long long)n0 * gy : (long long)gx;
+                const T* hb = sl < 0 ? A.halo_lo : A.halo_hi;
+                const int k = sl < 0 ? sl + A.halo_r : sl - ns;
+                const long long q = ((long long)c * A.halo_r + k) * pl + in_plane;
+                return (T)2 * __ldg(hb + q) - __ldg(hb + (long long)NC * A.halo_r * pl + q);
+            }
+            sl = wrapi<T>(sl, ns);
+        }
+        if (DIM == 3) gz = sl;
+        else gy = sl;
         const long long q = (long long)c * N + gx + (long long)n0 * gy + plane * gz;
         return (T)2 * __ldg(A.sig_n + q) - __ldg(A.sig_nm1 + q);
     };
@@ -410,13 +434,12 @@ __global__ void __launch_bounds__(kTX * kTY) transport_tiled(const FwdArgs<T> A,
 #pragma unroll
         for (int c = 0; c < NC; ++c)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) qz[c][k] = Eat(c, x, y, wrapi<T>(zbeg - 2 + k, n2));
+            for (int k = 0; k < 4; ++k) qz[c][k] = Eat(c, x, y, zbeg - 2 + k);
     }
     for (int z = zbeg; z < zend; ++z) {
         if (DIM == 3) {
-            const int zz = wrapi<T>(z + 2, n2);
 #pragma unroll
-            for (int c = 0; c < NC; ++c) qz[c][4] = Eat(c, x, y, zz);
+            for (int c = 0; c < NC; ++c) qz[c][4] = Eat(c, x, y, z + 2);
         }
         // own cell and halo cells of the shared tile at plane z
 #pragma unroll
@@ -425,7 +448,9 @@ __global__ void __launch_bounds__(kTX * kTY) transport_tiled(const FwdArgs<T> A,
             const int hy = h / kSX, hx = h - hy * kSX;
             const bool inner = hx >= kHalo && hx < kHalo + kTX && hy >= kHalo && hy < kHalo + kTY;
             if (!inner) {
-                const int gx = wrapi<T>(x0 + hx - kHalo, n0), gy = wrapi<T>(y0 + hy - kHalo, n1);
+                // y wraps here in 3D; in 2D it is the slowest axis (wrapped, or a halo row, by Eat)
+                const int gx = wrapi<T>(x0 + hx - kHalo, n0);
+                const int gy = DIM == 3 ? wrapi<T>(y0 + hy - kHalo, n1) : y0 + hy - kHalo;
 #pragma unroll
                 for (int c = 0; c < NC; ++c) Es[c][hy][hx] = Eat(c, gx, gy, DIM == 3 ? z : 0);
             }

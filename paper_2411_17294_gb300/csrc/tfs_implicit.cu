@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kThreads) imp_apply_kernel(const ImpArgs<T> A,
     if (done(sc)) return;
     const long long N = A.N;
     const int n0 = A.n0, n1 = A.n1, n2 = A.n2;
-    double a0 = 0.0, a1 = 0.0;
+    V a0 = (V)0, a1 = (V)0;   // per-thread dot products (a few points each), then double per block
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
         const unsigned pp = (unsigned)p;
         const unsigned q1 = pp / (unsigned)n0;
@@ -253,11 +253,11 @@ __global__ void __launch_bounds__(kThreads) imp_apply_kernel(const ImpArgs<T> A,
                     if (cf[a][t] != (V)0) acc = fma(cf[a][t], f[off[a][t]], acc);
             const long long q = (long long)r * N + p;
             y[q] = acc;
-            if (w0) a0 = fma((double)w0[q], (double)acc, a0);
-            if (w1) a1 = fma((double)w1[q], (double)acc, a1);
+            if (w0) a0 = fma(w0[q], acc, a0);
+            if (w1) a1 = fma(w1[q], acc, a1);
         }
     }
-    if (w0) block_partials(a0, a1, w1 ? 2 : 1, partials);
+    if (w0) block_partials((double)a0, (double)a1, w1 ? 2 : 1, partials);
 }
 
 // z = P^-1 v with v = a x + b y (+ c w): forms the combination, stores it in
@@ -294,36 +294,36 @@ __global__ void __launch_bounds__(kThreads) imp_xr_kernel(long long n, V* x, con
                                                           const double* sc) {
     if (done(sc)) return;
     const V alpha = (V)sc[S_ALPHA], omega = (V)sc[S_OMEGA];
-    double a0 = 0.0, a1 = 0.0;
+    V a0 = (V)0, a1 = (V)0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         x[i] = fma(alpha, ph[i], fma(omega, sh[i], x[i]));
         const V rv = fma(-omega, t[i], s[i]);
         r[i] = rv;
-        a0 = fma((double)rv, (double)rv, a0);
-        a1 = fma((double)rh[i], (double)rv, a1);
+        a0 = fma(rv, rv, a0);
+        a1 = fma(rh[i], rv, a1);
     }
-    block_partials(a0, a1, 2, partials);
+    block_partials((double)a0, (double)a1, 2, partials);
 }
 
 // per-block partial sums of x.y and x.z (z may be null), for the start of the iteration
 template <typename V>
 __global__ void __launch_bounds__(kThreads) imp_dot2_kernel(const V* x, const V* y, const V* z, long long n,
                                                             double* partials) {
-    double a0 = 0.0, a1 = 0.0;
+    V a0 = (V)0, a1 = (V)0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        a0 = fma((double)x[i], (double)y[i], a0);
-        if (z) a1 = fma((double)x[i], (double)z[i], a1);
+        a0 = fma(x[i], y[i], a0);
+        if (z) a1 = fma(x[i], z[i], a1);
     }
-    block_partials(a0, a1, z ? 2 : 1, partials);
+    block_partials((double)a0, (double)a1, z ? 2 : 1, partials);
 }
 
 // One block: add the partial sums in a fixed order into scalar slots, then the
 // scalar step of the iteration.
-//   op 0: RR, RHO_NEW <- (r, r), (rh, r); convergence test; beta for the next pass
+//   op 0: RR, RHO_NEW <- (r, r), (rh, r); convergence test; beta and rho of the next direction
 //   op 1: RHV <- (rh, v); alpha
 //   op 2: TS, TT <- (t, s), (t, t); omega
 //   op 3: BNORM2 <- (b, b)
-//   op 4: RR, RHO_NEW <- (r, r), (rh, r) at the start (no beta)
+//   op 4: RR, RHO_NEW <- (r, r), (rh, r) at the start; beta and rho of the first direction
 __global__ void __launch_bounds__(kThreads) imp_scalar_kernel(const double* partials, double* sc, int op) {
     __shared__ double sh[2][kThreads];
     double a0 = 0.0, a1 = 0.0;
@@ -347,10 +347,17 @@ __global__ void __launch_bounds__(kThreads) imp_scalar_kernel(const double* part
         sc[S_BNORM2] = v0;
         return;
     }
+    // beta and rho of the next direction, once (r, r) and (rh, r) are known
+    auto next_direction = [&]() {
+        if (done(sc)) return;
+        sc[S_BETA] = (sc[S_RHO_NEW] / sc[S_RHO]) * (sc[S_ALPHA] / sc[S_OMEGA]);
+        sc[S_RHO] = sc[S_RHO_NEW];
+    };
     if (op == 4) {
         sc[S_RR] = v0;
         sc[S_RHO_NEW] = v1;
         if (v0 <= sc[S_TOL2] * sc[S_BNORM2]) sc[S_DONE] = 1.0;
+        next_direction();
         return;
     }
     if (done(sc)) return;
@@ -376,15 +383,8 @@ __global__ void __launch_bounds__(kThreads) imp_scalar_kernel(const double* part
             sc[S_BREAK] = 1.0;
             sc[S_DONE] = 1.0;
         }
+        next_direction();
     }
-    if (op == 0 || op == 4) return;
-}
-
-// beta and rho for the next direction (after op 0 / op 4)
-__global__ void imp_beta_kernel(double* sc) {
-    if (done(sc)) return;
-    sc[S_BETA] = (sc[S_RHO_NEW] / sc[S_RHO]) * (sc[S_ALPHA] / sc[S_OMEGA]);
-    sc[S_RHO] = sc[S_RHO_NEW];
 }
 
 template <typename T, int DIM>
@@ -659,7 +659,7 @@ __global__ void __launch_bounds__(kThreads) imp_adj_rhs_kernel(const ImpArgs<T> 
         for (int c = 0; c < NC; ++c) {
             double acc = 0.0;
             for (int jj = 0; jj < A.m; ++jj) {
-                const long long q = ((long long)jj * NC + c) * N + p;
+                const long long q = mode_index(p, jj * NC + c, A.m * NC);
                 acc = fma(A.mcd.rho[jj], kB1 * (double)ell_prev[q] + kB2 * (double)ell_prev2[q], acc);
             }
             const long long qc = (long long)c * N + p;
@@ -738,7 +738,7 @@ __global__ void __launch_bounds__(kThreads) imp_adj_fix_kernel(const ImpArgs<T> 
         for (int c = 0; c < NC; ++c) {
             double acc = 0.0;
             for (int jj = 0; jj < A.m; ++jj) {
-                const long long q = ((long long)jj * NC + c) * N + p;
+                const long long q = mode_index(p, jj * NC + c, A.m * NC);
                 acc = fma(A.mcd.rho[jj], kB1 * (double)ell_prev[q] + kB2 * (double)ell_prev2[q], acc);
             }
             double mty = 0.0;
@@ -776,7 +776,7 @@ __global__ void __launch_bounds__(kThreads) imp_adj_paper_fix_kernel(const ImpAr
             const long long qc = (long long)c * N + p;
             double acc = 0.0;
             for (int jj = 0; jj < A.m; ++jj) {
-                const long long q = ((long long)jj * NC + c) * N + p;
+                const long long q = mode_index(p, jj * NC + c, A.m * NC);
                 acc = fma(A.mcd.rho[jj], kB1 * (double)ell_prev[q] + kB2 * (double)ell_prev2[q], acc);
             }
             const double lpc = lam_psi ? lam_psi[qc] : 0.0;
@@ -828,7 +828,7 @@ __device__ __forceinline__ void sta_ring_sums(const StartConsts& C, int m, doubl
     a1 = 0.0;
     zq = 0.0;
     for (int jj = 0; jj < m; ++jj) {
-        const long long q = ((long long)jj * NC + c) * N + p;
+        const long long q = mode_index(p, jj * NC + c, m * NC);
         const double z = kB1 * (double)ell_prev[q] + kB2 * (double)ell_prev2[q];
         const double wi = C.w[jj] * C.inv_den[jj];
         a1 = fma(z, f2 * wi, a1);
@@ -983,7 +983,7 @@ __device__ __forceinline__ double stp_lamP2(const StartConsts& C, int m, double 
     double a2 = 0.0;
     a1 = 0.0;
     for (int jj = 0; jj < m; ++jj) {
-        const long long q = ((long long)jj * NC + c) * N + p;
+        const long long q = mode_index(p, jj * NC + c, m * NC);
         const double z = kB1 * (double)ell_prev[q] + kB2 * (double)ell_prev2[q];
         a2 = fma(C.inv_den[jj], z, a2);
         a1 = fma(C.inv_den[jj] * C.inv_den[jj], z, a1);
@@ -1206,7 +1206,6 @@ cudaError_t bicgstab(const ImpArgs<T>& a, const BiVecs<V>& K, double* partials, 
     if (!ok()) return e;
     constexpr int kCheck = 8;
     for (int it = 0; it < maxit; ++it) {
-        imp_beta_kernel<<<1, 1, 0, st>>>(sc);
         imp_comb_precond_kernel<NC, V><<<bs, kThreads, 0, st>>>(N, K.Pinv, 0, K.p, K.r, K.v, K.ph, sc);
         imp_apply_kernel<T, DIM, V><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Cf, K.ph, K.v, K.rh, nullptr, partials, sc);
         imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 1);
@@ -1234,8 +1233,8 @@ cudaError_t bicgstab(const ImpArgs<T>& a, const BiVecs<V>& K, double* partials, 
 // from the initial guess in x (b, x filled; Mb, Pinv, Cf set up, all on st),
 // by mixed-precision defect correction: the FP64 residual r = b - Op x, an
 // inner BiCGStab on the float copy of the operator for the correction d
-// (Op d = r to the relative residual the outer target asks for, at most 1e-6
-// below |r|: float arithmetic ends there), x += d, until the FP64 residual
+// (Op d = r to the relative residual the outer target asks for, at most 1e-4
+// below |r| per pass), x += d, until the FP64 residual
 // meets the target.  The inner iterations then run on float vectors and float
 // coefficients (FP32 arithmetic and half the bytes; on this GPU FP64 runs at
 // 1/64 of the FP32 rate); the FP64 residual keeps the accuracy of the result
@@ -1296,6 +1295,11 @@ cudaError_t krylov_solve(const ImpArgs<T>& a, const KryView<Packed<DIM>::NC>& K,
         return e;
     }
     const double tol2 = a.tol * a.tol * bnorm2;
+    // each float pass reduces the residual by 1e-4: in float arithmetic
+    // BiCGStab's convergence turns erratic well before 1e-6 (measured on the
+    // 2D 1024^2 workload: passes to 1e-4 took 230-500 iterations, to 1e-6 often
+    // ran into the iteration limit), so more passes of fewer iterations win
+    constexpr double kInnerFloor = 1e-4;
     double prev_rr = -1.0;
     constexpr int kOuterMax = 12;
     for (int outer = 0; outer < kOuterMax; ++outer) {
@@ -1318,7 +1322,7 @@ cudaError_t krylov_solve(const ImpArgs<T>& a, const KryView<Packed<DIM>::NC>& K,
         // inner: Op d = r in float, to the target relative to |r| (not below 1e-6),
         // at most maxit iterations per pass
         double inner_tol = std::sqrt(tol2 / rr) * 0.5;
-        if (inner_tol < 1e-6) inner_tol = 1e-6;
+        if (inner_tol < kInnerFloor) inner_tol = kInnerFloor;
         int it = 0;
         double irr = 0.0, ib2 = 0.0;
         e = bicgstab<T, DIM, float>(a, Fv, partials, sc, inner_tol, a.maxit, true, st, &it, &irr, &ib2);

@@ -77,6 +77,15 @@ struct FwdArgs {
     const T* psi_nm1;
     double xi, inv_wi;
     F2c xi_f2, dtxi_f2;    // xi, dt xi
+    // slab of a larger periodic domain along the slowest axis (z in 3D, y in
+    // 2D): the stencil's neighbours beyond the slab come from the neighbouring
+    // slabs' boundary planes, [2 levels][nc][R][plane] (level 0 sigma^n, 1
+    // sigma^{n-1}; R = halo_r planes of n0 (2D) or n0 n1 (3D) points; halo_lo
+    // plane k is slab coordinate k - R, halo_hi plane k is n_s + k); both
+    // nullptr: the slowest axis wraps periodically within the grid
+    const T* halo_lo;
+    const T* halo_hi;
+    int halo_r;
 };
 
 // Tensor maps of the per-point plane groups a tile stages, each a 2D view

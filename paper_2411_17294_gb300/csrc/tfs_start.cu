@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(32) start_adjoint_kernel(const StartAdjArgs<T>
         for (int c = 0; c < NC; ++c) {
             double a1 = 0.0, a2 = 0.0;
             for (int jj = 0; jj < A.m; ++jj) {
-                const long long q = ((long long)jj * NC + c) * N + p;
+                const long long q = mode_index(p, jj * NC + c, A.m * NC);
                 const double z = kB1 * (double)A.ell_prev[q] + kB2 * (double)A.ell_prev2[q];
                 const double wi = C.w[jj] * C.inv_den[jj];
                 a1 = fma(z, f2 * wi, a1);

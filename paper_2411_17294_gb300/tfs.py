@@ -31,6 +31,7 @@ EXPORTS = [
     "tfs_set_state", "tfs_step", "tfs_get_stress", "tfs_set_step_events", "tfs_step_index", "tfs_last_solve", "tfs_checkpoint_bytes", "tfs_save",
     "tfs_load", "tfs_adjoint_workspace_bytes", "tfs_bind_adjoint_workspace", "tfs_backward", "tfs_status",
     "tfs_strerror", "tfs_destroy", "tfs_run_static", "tfs_static_status", "tfs_check_wait_bound",
+    "tfs_halo_bytes", "tfs_get_halo", "tfs_step_slab",
 ]
 
 
@@ -87,6 +88,9 @@ def load_library(path: str | None = None):
                                           ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, dp, vp, vp, vp,
                                           ctypes.c_int, vp, vp]),
         "tfs_static_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint), vp]),
+        "tfs_halo_bytes": (sz, [H]),
+        "tfs_get_halo": (ctypes.c_int, [H, vp, vp, vp]),
+        "tfs_step_slab": (ctypes.c_int, [H, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -227,6 +231,29 @@ class Solver:
         up = u.data_ptr() if u is not None else 0
         check(self.lib.tfs_step(self.h, ctypes.c_void_p(kn), ctypes.c_void_p(knm1), ctypes.c_void_p(up),
                                 ctypes.c_void_p(_stream_ptr(stream))), "tfs_step")
+
+    def halo_buffers(self):
+        """Two halo buffers (lo, hi) for a slab of this handle's grid:
+        [2 levels][nc][2 planes][plane points] tensors of the handle's dtype."""
+        torch = _torch()
+        count = self.lib.tfs_halo_bytes(self.h) // (8 if self.dtype == torch.float64 else 4)
+        return (torch.empty(count, dtype=self.dtype, device=self.device),
+                torch.empty(count, dtype=self.dtype, device=self.device))
+
+    def get_halo(self, lo, hi, stream=None):
+        """The slab's own boundary planes as its neighbours need them (tfs_get_halo)."""
+        check(self.lib.tfs_get_halo(self.h, ctypes.c_void_p(lo.data_ptr() if lo is not None else 0),
+                                    ctypes.c_void_p(hi.data_ptr() if hi is not None else 0),
+                                    ctypes.c_void_p(_stream_ptr(stream))), "tfs_get_halo")
+
+    def step_slab(self, grad_u_n, grad_u_nm1, u, halo_lo, halo_hi, stream=None):
+        """One step of a slab with the neighbours' boundary planes (tfs_step_slab)."""
+        knm1 = grad_u_nm1.data_ptr() if grad_u_nm1 is not None else 0
+        up = u.data_ptr() if u is not None else 0
+        check(self.lib.tfs_step_slab(self.h, ctypes.c_void_p(grad_u_n.data_ptr()), ctypes.c_void_p(knm1),
+                                     ctypes.c_void_p(up), ctypes.c_void_p(halo_lo.data_ptr()),
+                                     ctypes.c_void_p(halo_hi.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
+              "tfs_step_slab")
 
     def stress(self, stream=None):
         torch = _torch()

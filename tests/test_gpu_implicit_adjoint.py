@@ -151,12 +151,17 @@ def test_implicit_autograd_matches_central_differences():
     def fd(fun, x0):
         return (fun(x0 + h) - fun(x0 - h)) / (2 * h)
 
-    def close(a, b):
-        return abs(a - b) <= 1e-6 * max(abs(a), abs(b))
+    def close(a, b, scale=0.0):
+        # relative 1e-6; field entries normwise (against the largest entry of
+        # their gradient field): the forward's and the adjoint's Krylov solves
+        # stop at a relative residual of 1e-13, which leaves an absolute error
+        # of ~1e-8 on entries that are small against the field
+        return abs(a - b) <= 1e-6 * max(abs(a), abs(b), scale)
 
     t = lambda x: torch.tensor(x, dtype=torch.float64, device=dev)
     with torch.no_grad():
         s0d, kd = s0.detach(), k.detach()
+        gs0, gk = float(s0.grad.abs().max()), float(k.grad.abs().max())
         assert close(Wi.grad.item(), fd(lambda x: J(s0d, kd, t(x), beta.detach()).item(), 1.4))
         assert close(beta.grad.item(), fd(lambda x: J(s0d, kd, Wi.detach(), t(x)).item(), 0.3))
         for (c, q) in [(0, 0), (2, 63), (1, 17)]:
@@ -164,10 +169,10 @@ def test_implicit_autograd_matches_central_differences():
                 a = s0d.clone()
                 a[c, q] = x
                 return J(a, kd, Wi.detach(), beta.detach()).item()
-            assert close(s0.grad[c, q].item(), fd(fs, s0d[c, q].item()))
+            assert close(s0.grad[c, q].item(), fd(fs, s0d[c, q].item()), gs0)
         for (c, q) in [(0, 5), (3, 40)]:
             def fk(x, c=c, q=q):
                 a = kd.clone()
                 a[c, q] = x
                 return J(s0d, a, Wi.detach(), beta.detach()).item()
-            assert close(k.grad[c, q].item(), fd(fk, kd[c, q].item()))
+            assert close(k.grad[c, q].item(), fd(fk, kd[c, q].item()), gk)
