@@ -11,8 +11,12 @@ the HBM roofline of the step kernel.  The per-step working set (~41 GB) is far
 larger than L2, so no L2 flush is needed between steps.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun (N > 1) every rank runs its own 256^3 problem (weak scaling,
-no data-path collective); rank 0 prints one JSON line.
+Under torchrun (N > 1) the ranks share one periodic domain of 256 x 256 x
+(256 N) points cut into z-slabs, one 256^3 slab per rank (weak scaling):
+before every step each rank sends its two boundary planes of both stress
+levels to its neighbours on the ring and steps its slab with theirs
+(tfs_get_halo -> NCCL point-to-point -> tfs_step_slab); rank 0 prints one JSON
+line.
 """
 from __future__ import annotations
 
@@ -244,7 +248,24 @@ def cpu_baseline(steps_hint: int = 3, budget_s: float = 15.0):
                       f"FP64 C oracle with OpenMP", "seconds": el}
 
 
-def end_to_end(s, kap, u, steps: int, stream, dev):
+def make_stepper(s, world: int, rank: int, stream):
+    """One step of this rank's problem: tfs_step on one GPU; with several ranks,
+    the slab step of the shared domain (boundary planes exchanged on the ring
+    first, on `stream`'s order)."""
+    if world == 1:
+        return lambda kn, km, u: s.step(kn, km, u, stream=stream)
+    from paper_2411_17294_gb300 import slab
+    lo, hi = s.halo_buffers()
+    rlo, rhi = s.halo_buffers()
+
+    def step(kn, km, u):
+        s.get_halo(lo, hi, stream=stream)
+        slab.exchange(lo, hi, rlo, rhi, rank, world)
+        s.step_slab(kn, km, u, rlo, rhi, stream=stream)
+    return step
+
+
+def end_to_end(s, kap, u, steps: int, stream, dev, stepper=None):
     """Steps fed from pinned host memory as a time-dependent run would be: per
     step the host-to-device copy of that step's velocity gradient kappa^n and
     velocity u, and the device-to-host read of the new stress through
@@ -289,7 +310,8 @@ def end_to_end(s, kap, u, steps: int, stream, dev):
         stream.wait_event(loaded[k])
         if k >= 2:
             stream.wait_event(read[k - 2])           # d_sig[k % 2] was read out after step k - 2
-        s.step(d_k[k % 3], d_k[(k - 1) % 3] if k > 0 else d_k[0], d_u[k % 2], stream=stream)
+        (stepper or (lambda a, b, c: s.step(a, b, c, stream=stream)))(
+            d_k[k % 3], d_k[(k - 1) % 3] if k > 0 else d_k[0], d_u[k % 2])
         if s.lib.tfs_get_stress(s.h, d_sig[k % 2].data_ptr(), stream.cuda_stream) != 0:
             raise RuntimeError("tfs_get_stress failed")
         stepped[k].record(stream)
@@ -596,10 +618,11 @@ def main():
     bytes_pp = step_kernel_bytes_per_point(3, W["m"], elem, transport=True)
     bytes_launch = bytes_pp * N
 
+    stepper = make_stepper(s, world, rank, stream)
     with torch.cuda.stream(stream):
         s.set_state(None, stream=stream)
         for _ in range(args.warmup):
-            s.step(kap_n, kap_nm1, u, stream=stream)
+            stepper(kap_n, kap_nm1, u)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -622,7 +645,7 @@ def main():
         ev[0].record(stream)
         for k in range(args.steps):
             s.set_step_events(kb[k], ka[k])     # recorded on `stream` around the step kernel only
-            s.step(kap_n, kap_nm1, u, stream=stream)
+            stepper(kap_n, kap_nm1, u)
         ev[1].record(stream)
     torch.cuda.synchronize()
     if dist is not None:
@@ -639,14 +662,15 @@ def main():
     achieved = bytes_launch / avg_launch_s / 1e9
     peak, peak_kind = read_peaks()
     traffic = read_traffic() if prec == tfs.TFS_FP32 else None
-    launches_per_step = 2         # transport pre-pass + step kernel
+    launches_per_step = 2         # transport pre-pass + step kernel (slabs: plus the halo copies)
 
     # ---- end to end through the C ABI with host buffers ----------------------
     e2e = None
     if args.e2e_steps > 0:
         if dist is not None:
             dist.barrier()
-        e2e_ms, bi, bo = end_to_end(s, kap_n, u, args.e2e_steps, stream, dev)
+        with torch.cuda.stream(stream):
+            e2e_ms, bi, bo = end_to_end(s, kap_n, u, args.e2e_steps, stream, dev, stepper)
         e2e_ms = max_over_ranks(e2e_ms, dist, dev)
         e2e = {"value": whole_job_rate(N * W["m"] * args.e2e_steps, world, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
@@ -699,7 +723,10 @@ def main():
                        "Wi": W["Wi"], "beta": W["beta"], "dt": W["dt"], "transport": True,
                        "precision": args.precision, "l2": f"per-step working set {algorithmic_bytes_per_point(3, W['m'], elem) * N / 1e9:.1f} GB "
                              f">> 129 MB L2, no flush",
-                       "points_per_gpu": N},
+                       "points_per_gpu": N,
+                       "parallelism": "one GPU" if world == 1 else
+                       f"{world} z-slabs of one periodic 256 x 256 x {256 * world} domain, ring halo exchange "
+                       "(NCCL point-to-point, 2 planes x 2 levels x 6 components per side per step)"},
             "roofline": {"bound": "hbm", "kernel": "fwd_kernel<float,3> (step kernel)", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "traffic_source": "ncu dram__bytes of the committed capture, used only while the "
