@@ -28,7 +28,11 @@
 namespace tfs {
 namespace {
 
-constexpr int kThreads = 128;
+// 64 threads per block: z_j of a block (m nc 64 floats, 24 KB at m = 32 in 2D)
+// lets nine blocks share an SM where 128-thread blocks fit four (measured on
+// the 2D 512^2 m = 32 FP32 adjoint workload: 16.4 ms against 18.6 ms for the
+// 100-step reverse sweep with its recompute)
+constexpr int kThreads = 64;
 
 // Entry (r, k) of the packed matrix of S -> kappa S + S kappa^T (as uc_entry,
 // in the arithmetic type R; r and k fold at compile time under static_for).
