@@ -406,53 +406,75 @@ __global__ void __launch_bounds__(kTX * kTY) transport_tiled(const FwdArgs<T> A,
     const bool lap = A.eps != 0.0;
     const float ccoef = (float)A.courant_coef, climit = (float)A.courant_limit;
     const float ihf[3] = {(float)A.inv_h[0], (float)A.inv_h[1], (float)A.inv_h[2]};
-    // E at (gx, gy, gz); the slowest coordinate (gz in 3D, gy in 2D) may lie up
-    // to kHalo outside the grid: it wraps, or on a slab comes from the halo planes
-    auto Eat = [&](int c, int gx, int gy, int gz) -> T {
-        int sl = DIM == 3 ? gz : gy;
-        const int ns = DIM == 3 ? n2 : n1;
-        if (sl < 0 || sl >= ns) {
-            if (A.halo_lo) {
-                const long long pl = DIM == 3 ? plane : (long long)n0;
-                const long long in_plane = DIM == 3 ? gx + (long long)n0 * gy : (long long)gx;
-                const T* hb = sl < 0 ? A.halo_lo : A.halo_hi;
-                const int k = sl < 0 ? sl + A.halo_r : sl - ns;
-                const long long q = ((long long)c * A.halo_r + k) * pl + in_plane;
-                return (T)2 * __ldg(hb + q) - __ldg(hb + (long long)NC * A.halo_r * pl + q);
-            }
-            sl = wrapi<T>(sl, ns);
+    // Both stress levels of the slowest-axis plane sl (z in 3D, a y row in 2D),
+    // resolved once per plane: sl may lie up to kHalo outside the grid, where
+    // it wraps, or on a slab comes from the halo planes; then E at a point of
+    // that plane is 2 n[c cstride + q] - m[c cstride + q].
+    struct PlanePtr {
+        const T* n;
+        const T* m;
+        long long cstride;
+    };
+    const int ns = DIM == 3 ? n2 : n1;
+    const long long pl = DIM == 3 ? plane : (long long)n0;
+    auto plane_at = [&](int sl) -> PlanePtr {
+        if ((sl < 0 || sl >= ns) && A.halo_lo) {
+            const T* hb = sl < 0 ? A.halo_lo : A.halo_hi;
+            const long long k = sl < 0 ? sl + A.halo_r : sl - ns;
+            return {hb + k * pl, hb + ((long long)NC * A.halo_r + k) * pl, (long long)A.halo_r * pl};
         }
-        if (DIM == 3) gz = sl;
-        else gy = sl;
-        const long long q = (long long)c * N + gx + (long long)n0 * gy + plane * gz;
-        return (T)2 * __ldg(A.sig_n + q) - __ldg(A.sig_nm1 + q);
+        const long long w = wrapi<T>(sl, ns);
+        return {A.sig_n + w * pl, A.sig_nm1 + w * pl, N};
+    };
+    auto E_in = [&](const PlanePtr& P, int c, long long q) -> T {
+        const long long o = (long long)c * P.cstride + q;
+        return (T)2 * __ldg(P.n + o) - __ldg(P.m + o);
     };
     const int zbeg = DIM == 3 ? blockIdx.z * zchunk : 0;
     const int zend = DIM == 3 ? min(zbeg + zchunk, n2) : 1;
+    const long long q_xy = x + (long long)n0 * y;   // this thread's column within a z plane (3D)
     T qz[NC][5];   // E of this column at z-2 .. z+2 (3D)
     if (DIM == 3) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c)
+        for (int k = 0; k < 4; ++k) {
+            const PlanePtr P = plane_at(zbeg - 2 + k);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) qz[c][k] = Eat(c, x, y, zbeg - 2 + k);
+            for (int c = 0; c < NC; ++c) qz[c][k] = E_in(P, c, q_xy);
+        }
     }
     for (int z = zbeg; z < zend; ++z) {
         if (DIM == 3) {
+            const PlanePtr P = plane_at(z + 2);
 #pragma unroll
-            for (int c = 0; c < NC; ++c) qz[c][4] = Eat(c, x, y, z + 2);
+            for (int c = 0; c < NC; ++c) qz[c][4] = E_in(P, c, q_xy);
         }
         // own cell and halo cells of the shared tile at plane z
+        if (DIM == 3) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) Es[c][ty + kHalo][tx + kHalo] = DIM == 3 ? qz[c][2] : Eat(c, x, y, 0);
-        for (int h = tid; h < kSX * kSY; h += kTX * kTY) {
-            const int hy = h / kSX, hx = h - hy * kSX;
-            const bool inner = hx >= kHalo && hx < kHalo + kTX && hy >= kHalo && hy < kHalo + kTY;
-            if (!inner) {
-                // y wraps here in 3D; in 2D it is the slowest axis (wrapped, or a halo row, by Eat)
-                const int gx = wrapi<T>(x0 + hx - kHalo, n0);
-                const int gy = DIM == 3 ? wrapi<T>(y0 + hy - kHalo, n1) : y0 + hy - kHalo;
+            for (int c = 0; c < NC; ++c) Es[c][ty + kHalo][tx + kHalo] = qz[c][2];
+        } else {
+            const PlanePtr P = plane_at(y);
 #pragma unroll
-                for (int c = 0; c < NC; ++c) Es[c][hy][hx] = Eat(c, gx, gy, DIM == 3 ? z : 0);
+            for (int c = 0; c < NC; ++c) Es[c][ty + kHalo][tx + kHalo] = E_in(P, c, x);
+        }
+        {
+            const PlanePtr Pz = plane_at(DIM == 3 ? z : 0);   // 3D: the plane z (inside the grid)
+            for (int h = tid; h < kSX * kSY; h += kTX * kTY) {
+                const int hy = h / kSX, hx = h - hy * kSX;
+                const bool inner = hx >= kHalo && hx < kHalo + kTX && hy >= kHalo && hy < kHalo + kTY;
+                if (!inner) {
+                    const int gx = wrapi<T>(x0 + hx - kHalo, n0);
+                    if (DIM == 3) {
+                        const int gy = wrapi<T>(y0 + hy - kHalo, n1);
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) Es[c][hy][hx] = E_in(Pz, c, gx + (long long)n0 * gy);
+                    } else {
+                        // in 2D the rows are the slowest axis: wrapped, or a halo row on a slab
+                        const PlanePtr P = plane_at(y0 + hy - kHalo);
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) Es[c][hy][hx] = E_in(P, c, gx);
+                    }
+                }
             }
         }
         __syncthreads();
