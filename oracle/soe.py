@@ -15,8 +15,9 @@ kernel that means AAA on s^alpha, then r(s)/s ~ s^(alpha-1).
 
 ``soe_aaa``     the construction above, written from the AAA algorithm of
                 Nakatsukasa, Sete & Trefethen (2018): greedy support points,
-                least-squares weights from the Loewner matrix SVD, poles from
-                the barycentric generalised eigenvalue problem.
+                least-squares weights from the Loewner matrix SVD, removal of
+                spurious pole-zero pairs (Froissart doublets) with a refit,
+                poles from the barycentric generalised eigenvalue problem.
 ``soe_nnls``    a positive construction with exactly m terms for any m:
                 exponents on a geometric grid, weights by non-negative least
                 squares on the relative kernel error over [dt/10, T]; the grid
@@ -106,6 +107,45 @@ def _poles(zj, wj):
     return ev[np.isfinite(ev)]
 
 
+def _residues(zj, fj, wj, poles):
+    """Residues of the barycentric r(s) = N(s)/D(s) at simple poles p: N(p)/D'(p)."""
+    out = []
+    for p in poles:
+        c = 1.0 / (p - zj)
+        out.append((c @ (wj * fj)) / (-(c * c) @ wj))
+    return np.array(out)
+
+
+def _aaa_cleanup(Z, F, zj, fj, wj, tol=1e-13):
+    """Removal of spurious pole-zero pairs (Froissart doublets), the last step
+    of the AAA algorithm of Nakatsukasa, Sete & Trefethen: a pole whose residue
+    is below tol * max|F| (or that sits on a support point, whose weight has
+    vanished) is spurious; the support point nearest to it is dropped and the
+    weights of the remaining support points are refitted by least squares
+    (the smallest right singular vector of the Loewner matrix on the other
+    samples).  Repeated until no such pole is left.  Returns (zj, fj, wj)."""
+    Z = np.asarray(Z, dtype=np.float64)
+    F = np.asarray(F, dtype=np.float64)
+    scale = np.max(np.abs(F))
+    for _ in range(len(zj)):
+        poles = _poles(zj, wj)
+        on_support = np.array([np.min(np.abs(zj - p)) <= 1e-12 * max(abs(p), 1e-300) for p in poles], dtype=bool)
+        res = np.zeros(len(poles), dtype=complex)
+        if (~on_support).any():
+            res[~on_support] = _residues(zj, fj, wj, poles[~on_support])
+        spurious = on_support | (np.abs(res) < tol * scale)
+        if not spurious.any():
+            break
+        drop = {int(np.argmin(np.abs(zj - p))) for p in poles[spurious]}
+        keep = np.array([k for k in range(len(zj)) if k not in drop], dtype=int)
+        zj, fj = zj[keep], fj[keep]
+        rows = ~np.isin(Z, zj)
+        C = 1.0 / (Z[rows, None] - zj[None, :])
+        _, _, Vh = np.linalg.svd((F[rows, None] - fj[None, :]) * C, full_matrices=False)
+        wj = Vh[-1, :].conj()
+    return zj, fj, wj
+
+
 def soe_aaa(alpha: float, dt: float, T: float, m: int, samples: int = 2000, decades: float = 1.0):
     """SOE of t^-alpha/Gamma(1-alpha) on [dt, T] with m terms (Section 2.2).
 
@@ -113,8 +153,12 @@ def soe_aaa(alpha: float, dt: float, T: float, m: int, samples: int = 2000, deca
     `decades` on each side, with m support points (m-1 poles).  The rational
     function divided by s has the m-1 poles plus a pole at s = 0 whose residue
     r(0) gives a term with exponent 0; all m residues become the weights.
-    Returns (mu, w) sorted by mu, or raises ValueError when a pole is not
-    real and negative or a weight is negative."""
+    Spurious pole-zero pairs are removed first (_aaa_cleanup).  Returns (mu, w)
+    sorted by mu, or raises ValueError when the cleanup leaves fewer than m
+    terms, a pole is not real and negative or a weight is negative (in FP64 on
+    these sample ranges the case beyond about m = 20: the extra degrees of
+    freedom give complex or positive poles whose residues are not small
+    enough to count as spurious)."""
     if not (0.0 < alpha < 1.0):
         raise ValueError("alpha must lie in (0, 1)")
     lo = math.log10(1.0 / T) - decades
@@ -122,6 +166,9 @@ def soe_aaa(alpha: float, dt: float, T: float, m: int, samples: int = 2000, deca
     Z = np.logspace(lo, hi, samples)
     F = Z ** alpha
     zj, fj, wj = _aaa(Z, F, m, 0.0)
+    zj, fj, wj = _aaa_cleanup(Z, F, zj, fj, wj)
+    if len(zj) < m:
+        raise ValueError("spurious poles removed: fewer than m terms remain")
     poles = _poles(zj, wj)
     if np.max(np.abs(poles.imag)) > 1e-8 * np.max(np.abs(poles)):
         raise ValueError("complex poles")

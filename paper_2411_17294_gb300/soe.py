@@ -22,8 +22,10 @@ The table is computed once on the host in FP64 and handed to tfs_set_soe.
     Without it the step's local weight misses that mass, and the zero-flow
     relaxation at alpha = 0.8 is several percent off its closed form.
 ``aaa(alpha, dt, T, m)``  the paper's recipe: AAA rational approximation of
-    s^alpha (Laplace variable) divided by s, partial fractions, inverse Laplace
-    transform; valid while the poles stay real and negative (about m <= 20).
+    s^alpha (Laplace variable) divided by s, with the removal of spurious
+    pole-zero pairs, partial fractions, inverse Laplace transform; valid while
+    the poles stay real and negative (about m <= 20: beyond, complex or
+    positive poles remain whose residues are too large to count as spurious).
 """
 from __future__ import annotations
 
@@ -144,11 +146,40 @@ def aaa(alpha: float, dt: float, T: float, m: int, samples: int = 2000):
         approx = f.copy()
         approx[free] = (cauchy @ (bw * fs)) / (cauchy @ bw)
     zs, fs = np.array(sup), np.array(val)
-    k = len(zs)
-    A = np.zeros((k + 1, k + 1)); A[0, 1:] = bw; A[1:, 0] = 1.0; A[1:, 1:] = np.diag(zs)
-    B = np.eye(k + 1); B[0, 0] = 0.0
-    poles = linalg.eigvals(A, B)
-    poles = poles[np.isfinite(poles)]
+
+    def denominator_zeros(zs, bw):
+        k = len(zs)
+        A = np.zeros((k + 1, k + 1)); A[0, 1:] = bw; A[1:, 0] = 1.0; A[1:, 1:] = np.diag(zs)
+        B = np.eye(k + 1); B[0, 0] = 0.0
+        ev = linalg.eigvals(A, B)
+        return ev[np.isfinite(ev)]
+
+    # Froissart doublets (the AAA algorithm's cleanup step): a pole with a
+    # residue below 1e-13 of max|f|, or one on a support point (zero weight),
+    # is spurious; drop the nearest support point, refit the weights by the
+    # Loewner least-squares problem on the remaining samples, repeat
+    fmax = float(np.max(np.abs(f)))
+    while len(zs) > 1:
+        poles = denominator_zeros(zs, bw)
+        bad = []
+        for p in poles:
+            gap = np.abs(p - zs)
+            if gap.min() <= 1e-12 * abs(p):
+                bad.append(int(np.argmin(gap)))
+                continue
+            c = 1.0 / (p - zs)
+            if abs(np.sum(bw * fs * c) / -np.sum(bw * c * c)) < 1e-13 * fmax:
+                bad.append(int(np.argmin(gap)))
+        if not bad:
+            break
+        keep = np.setdiff1d(np.arange(len(zs)), np.unique(bad))
+        zs, fs = zs[keep], fs[keep]
+        rest = ~np.isin(z, zs)
+        cauchy = 1.0 / (z[rest][:, None] - zs[None, :])
+        bw = np.linalg.svd((f[rest][:, None] - fs[None, :]) * cauchy)[2][-1]
+    if len(zs) < m:
+        raise ValueError("AAA: spurious poles removed, fewer than m terms remain")
+    poles = denominator_zeros(zs, bw)
     if np.any(np.abs(poles.imag) > 1e-8 * np.abs(poles)) or np.any(poles.real >= 0):
         raise ValueError("AAA produced complex or non-negative poles")
     poles = poles.real

@@ -234,3 +234,46 @@ def test_completed_table_gives_the_mittag_leffler_relaxation(alpha):
     assert errs[0] < 2e-6, errs
     if alpha >= 0.8:
         assert errs[1] > 1e-2, errs
+
+
+def test_aaa_cleanup_removes_froissart_doublets():
+    # f(s) = 1/(s + 2) + 3/(s + 5) is rational of type (1, 2): three support
+    # points reproduce it exactly, and AAA run to eight support points adds
+    # five spurious poles (pole-zero pairs with negligible residues).  The
+    # cleanup of the AAA algorithm (Nakatsukasa, Sete & Trefethen) removes them
+    # and leaves the poles -2, -5 with residues 1, 3.
+    Z = np.logspace(-1, 2, 400)
+    F = 1.0 / (Z + 2.0) + 3.0 / (Z + 5.0)
+    zj, fj, wj = soe._aaa(Z, F, 8, 0.0)
+    assert len(soe._poles(zj, wj)) == 7
+    zj, fj, wj = soe._aaa_cleanup(Z, F, zj, fj, wj)
+    poles = soe._poles(zj, wj)
+    order = np.argsort(poles.real)
+    assert np.allclose(poles[order], [-5.0, -2.0], rtol=1e-10)
+    assert np.allclose(soe._residues(zj, fj, wj, poles[order]), [3.0, 1.0], rtol=1e-10)
+
+
+def test_product_aaa_matches_oracle_aaa():
+    # the library's builder and the oracle's are written independently; on the
+    # paper's recipe at m = 16 they give the same table
+    from paper_2411_17294_gb300 import soe as psoe
+    mu, w = psoe.aaa(0.5, 1e-3, 1.0, 16)
+    mu2, w2 = soe.soe_aaa(0.5, 1e-3, 1.0, 16)
+    assert np.allclose(mu, mu2, rtol=1e-9, atol=0.0) and np.allclose(w, w2, rtol=1e-9)
+
+
+@pytest.mark.parametrize("alpha,m", [(0.6, 32), (0.5, 48), (0.2, 32), (0.9, 32)])
+def test_aaa_beyond_twenty_terms_is_refused(alpha, m):
+    # Measured reading of the paper's recipe in FP64 at the workloads' sizes
+    # (dt = 2e-4, T = 200 dt): even after the removal of spurious pole-zero
+    # pairs, the m-point AAA approximant of s^alpha keeps complex or positive
+    # poles (residues ~1e-8 of max|s^alpha|, far above the cleanup's 1e-13), so
+    # both builders refuse the table and the NNLS fit serves these m.
+    from paper_2411_17294_gb300 import soe as psoe
+    dt = 2e-4
+    with pytest.raises(ValueError):
+        soe.soe_aaa(alpha, dt, 200 * dt, m)
+    with pytest.raises(ValueError):
+        psoe.aaa(alpha, dt, 200 * dt, m)
+    mu, w = soe.soe_nnls(alpha, dt, 200 * dt, m)
+    assert len(mu) == m and soe.max_rel_error(alpha, mu, w, dt, 200 * dt) < 1e-7
