@@ -369,6 +369,53 @@ int tfs_run_static(const tfs_grid* grid, double alpha, double Wi, double beta, i
    TFS_ERR_ARG for NULL, TFS_ERR_CUDA if the copy fails. */
 int tfs_static_status(unsigned* device_flags, void* stream);
 
+/* ---- The velocity the stress is coupled to: one Navier-Stokes projection
+   step on the periodic square (Section 4.1: BDF2 with the extrapolation of
+   eq. BDF_and_extrapolation, the rotational viscous term of eq.
+   velocity_correction in the pressure equation eq. NS_Poisson, the velocity
+   from the Helmholtz equation eq. NS_Helmholtz, the polymer stress entering as
+   its divergence, eq. Navier_Stokes).  Fourier spectral derivatives (d/dx_a
+   multiplies mode k by i k_a, zero at the Nyquist wavenumber; the Laplacian
+   is its square), so Poisson and Helmholtz are divisions per mode and the
+   velocity stays divergence-free; the transforms are the library's own FFT
+   kernels.  Internal state FP64; the fields exchanged with the caller are of
+   the precision given at creation (double for TFS_FP64, else float), so that
+   they feed the stress handle directly.  A coupled step, in the paper's
+   order: tfs_ns_step(sigma^n) -> u^{n+1}, kappa^{n+1}, then tfs_step(h,
+   kappa^{n+1}, kappa^{n+1}, u^{n+1}) (the stress step with kappa* =
+   kappa^{n+1}, the velocity already known). */
+typedef struct tfs_ns_ctx* tfs_ns_handle;
+
+/* Grid n0 x n1 (powers of two, 2 .. 1024), box L0 x L1, solvent fraction beta
+   in (0, 1] and Reynolds number Re > 0 (viscosity beta/Re), step dt > 0,
+   precision as tfs_create.  No device memory is allocated; on error *h = NULL. */
+int tfs_ns_create(tfs_ns_handle* h, int n0, int n1, double L0, double L1, double beta, double Re, double dt,
+                  int precision);
+
+/* Device workspace of the handle: 21 complex and 8 real FP64 fields of n0 n1
+   values, each rounded up to 256 bytes. */
+size_t tfs_ns_workspace_bytes(tfs_ns_handle h);
+
+/* Bind caller-owned device memory (256-byte aligned) of at least
+   tfs_ns_workspace_bytes bytes; discards the state. */
+int tfs_ns_bind_workspace(tfs_ns_handle h, void* dev_ptr, size_t bytes);
+
+/* Initial velocity u0 [2][N] (device; x fastest, N = n0 n1), projected onto
+   divergence-free fields.  u_prev = the level one step earlier (projected
+   too) or NULL for an empty past (u^{-1} = u^0 and the previous explicit
+   terms equal to the first ones).  Enqueues on `stream`. */
+int tfs_ns_set_state(tfs_ns_handle h, const void* u0, const void* u_prev, void* stream);
+
+/* One step with the polymer stress sigma^n [3][N] (packed xx, xy, yy, as
+   tfs_get_stress returns it; NULL = no stress): writes u^{n+1} [2][N] and the
+   velocity gradient kappa^{n+1} [4][N] (kappa_ij = du_i/dx_j at i*2 + j);
+   either output may be NULL.  Enqueues on `stream`; TFS_ERR_STATE before
+   tfs_ns_set_state, TFS_ERR_NOWORKSPACE without a workspace. */
+int tfs_ns_step(tfs_ns_handle h, const void* sigma, void* u_out, void* grad_u_out, void* stream);
+
+/* Free the handle (host memory only). */
+int tfs_ns_destroy(tfs_ns_handle h);
+
 #ifdef __cplusplus
 }
 #endif

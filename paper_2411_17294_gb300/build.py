@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtfs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["tfs_api.cu", "tfs_forward.cu", "tfs_adjoint.cu", "tfs_util.cu", "tfs_static.cu", "tfs_implicit.cu",
-           "tfs_start.cu", "tfs_selftest.cu", "tfs_adjoint_paper.cu"]
+           "tfs_start.cu", "tfs_selftest.cu", "tfs_adjoint_paper.cu", "tfs_ns.cu"]
 
 
 def nvcc() -> str:

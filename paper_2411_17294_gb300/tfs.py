@@ -32,6 +32,8 @@ EXPORTS = [
     "tfs_load", "tfs_adjoint_workspace_bytes", "tfs_bind_adjoint_workspace", "tfs_backward", "tfs_status",
     "tfs_strerror", "tfs_destroy", "tfs_run_static", "tfs_static_status", "tfs_check_wait_bound",
     "tfs_halo_bytes", "tfs_get_halo", "tfs_step_slab",
+    "tfs_ns_create", "tfs_ns_workspace_bytes", "tfs_ns_bind_workspace", "tfs_ns_set_state", "tfs_ns_step",
+    "tfs_ns_destroy",
 ]
 
 
@@ -91,6 +93,14 @@ def load_library(path: str | None = None):
         "tfs_halo_bytes": (sz, [H]),
         "tfs_get_halo": (ctypes.c_int, [H, vp, vp, vp]),
         "tfs_step_slab": (ctypes.c_int, [H, vp, vp, vp, vp, vp, vp]),
+        "tfs_ns_create": (ctypes.c_int, [ctypes.POINTER(H), ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_int]),
+        "tfs_ns_workspace_bytes": (sz, [H]),
+        "tfs_ns_bind_workspace": (ctypes.c_int, [H, vp, sz]),
+        "tfs_ns_set_state": (ctypes.c_int, [H, vp, vp, vp]),
+        "tfs_ns_step": (ctypes.c_int, [H, vp, vp, vp, vp]),
+        "tfs_ns_destroy": (ctypes.c_int, [H]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -353,3 +363,57 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class NSSolver:
+    """The Navier-Stokes projection step on the periodic square (tfs_ns_*): the
+    velocity the stress is coupled to.  Fields are torch tensors of the
+    precision's dtype: velocity [2, N], gradient [4, N], stress [3, N]."""
+
+    def __init__(self, n, L, beta: float, Re: float, dt: float, precision: int = TFS_FP64, device=None):
+        torch = _torch()
+        lib = load_library()
+        self.lib = lib
+        self.n = (int(n[0]), int(n[1]))
+        self.N = self.n[0] * self.n[1]
+        self.dtype = torch.float64 if precision == TFS_FP64 else torch.float32
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        h = ctypes.c_void_p()
+        check(lib.tfs_ns_create(ctypes.byref(h), self.n[0], self.n[1], float(L[0]), float(L[1]), float(beta),
+                                float(Re), float(dt), int(precision)), "tfs_ns_create")
+        self.h = h
+        nbytes = lib.tfs_ns_workspace_bytes(h)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        check(lib.tfs_ns_bind_workspace(h, ctypes.c_void_p(base + (-base) % 256), nbytes), "tfs_ns_bind_workspace")
+
+    def _dev(self, t, rows):
+        torch = _torch()
+        return torch.as_tensor(t).to(device=self.device, dtype=self.dtype).reshape(rows, self.N).contiguous()
+
+    def set_state(self, u0, u_prev=None, stream=None):
+        u0 = self._dev(u0, 2)
+        up = None if u_prev is None else self._dev(u_prev, 2)
+        check(self.lib.tfs_ns_set_state(self.h, ctypes.c_void_p(u0.data_ptr()),
+                                        ctypes.c_void_p(up.data_ptr() if up is not None else 0),
+                                        ctypes.c_void_p(_stream_ptr(stream))), "tfs_ns_set_state")
+        self._keep = (u0, up)
+
+    def step(self, sigma=None, u_out=None, grad_u_out=None, stream=None):
+        """One step with the stress sigma^n (None: no stress); returns (u, kappa)."""
+        torch = _torch()
+        if u_out is None:
+            u_out = torch.empty((2, self.N), dtype=self.dtype, device=self.device)
+        if grad_u_out is None:
+            grad_u_out = torch.empty((4, self.N), dtype=self.dtype, device=self.device)
+        sp = 0 if sigma is None else sigma.data_ptr()
+        check(self.lib.tfs_ns_step(self.h, ctypes.c_void_p(sp), ctypes.c_void_p(u_out.data_ptr()),
+                                   ctypes.c_void_p(grad_u_out.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
+              "tfs_ns_step")
+        return u_out, grad_u_out
+
+    def close(self):
+        if self.h:
+            self.lib.tfs_ns_destroy(self.h)
+            self.h = None
