@@ -481,6 +481,67 @@ def fp64_record(dev, steps: int, warmup: int, grid: int | None = None):
             "frac": achieved / peak, "bound": "fp64 pipe (1/64 of the FP32 rate on this GPU)"}
 
 
+NS_COUPLED = dict(name="coupled Navier-Stokes projection + stress step, 2D periodic 1024^2, m=32 SOE modes, alpha=0.5, "
+                       "FP32 storage, explicit transport", n=(1024, 1024), alpha=0.5, Wi=1.0, beta=0.5, Re=100.0,
+                  m=32, dt=5e-4, kmax=32, seed=2)
+
+
+def ns_coupled_record(dev, steps: int = 10, warmup: int = 3):
+    """The coupled step in the paper's order (Section 4.1): the velocity from the
+    stress at t_n by the projection step (tfs_ns_step: 11 FFTs of 1024^2 and the
+    per-mode Poisson and Helmholtz solves), then the stress step with that
+    velocity.  The initial velocity is the spectral field scaled to 0.3 of the
+    explicit transport's limit.  Times per step of both parts (CUDA events)."""
+    import torch
+
+    from paper_2411_17294_gb300 import inputs, soe, tfs
+    C = NS_COUPLED
+    n, dt = C["n"], C["dt"]
+    mu, w = soe.build(C["alpha"], dt, 200 * dt, C["m"])
+    L = (2 * math.pi, 2 * math.pi)
+    st = tfs.Solver(2, n, C["alpha"], C["Wi"], C["beta"], dt, m=C["m"], precision=tfs.TFS_FP32, mu=mu, w=w,
+                    transport=True, device=dev, L=L)
+    U = st.transport_limit()
+    u0, _ = inputs.spectral_velocity(2, n, C["kmax"], C["seed"], device=dev)
+    u0 = torch.as_tensor(u0, dtype=torch.float64, device=dev)
+    u0 = u0 * (0.3 * U / float(u0.abs().max()))
+    ns = tfs.NSSolver(n, L, C["beta"], C["Re"], dt, precision=tfs.TFS_FP32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * steps)]
+    with torch.cuda.stream(stream):
+        ns.set_state(u0.float(), stream=stream)
+        st.set_state(None, stream=stream)
+        sig = torch.empty((3, st.N), dtype=torch.float32, device=dev)
+        u_t = torch.empty((2, st.N), dtype=torch.float32, device=dev)
+        k_t = torch.empty((4, st.N), dtype=torch.float32, device=dev)
+
+        def coupled(k=None):
+            if k is not None:
+                ev[3 * k].record(stream)
+            st.lib.tfs_get_stress(st.h, sig.data_ptr(), stream.cuda_stream)
+            ns.step(sig, u_t, k_t, stream=stream)
+            if k is not None:
+                ev[3 * k + 1].record(stream)
+            st.step(k_t, k_t, u_t, stream=stream)
+            if k is not None:
+                ev[3 * k + 2].record(stream)
+        for _ in range(warmup):
+            coupled()
+        torch.cuda.synchronize()
+        for k in range(steps):
+            coupled(k)
+    torch.cuda.synchronize()
+    ns_ms = statistics.mean(ev[3 * k].elapsed_time(ev[3 * k + 1]) for k in range(steps))
+    st_ms = statistics.mean(ev[3 * k + 1].elapsed_time(ev[3 * k + 2]) for k in range(steps))
+    flags = st.status()
+    N = st.N
+    ns.close()
+    st.close()
+    return {"workload": C["name"], "ns_ms_per_step": ns_ms, "stress_ms_per_step": st_ms,
+            "coupled_ms_per_step": ns_ms + st_ms,
+            "G_point_mode_updates_per_s": N * C["m"] / ((ns_ms + st_ms) * 1e-3) / 1e9, "device_flags": flags}
+
+
 def max_over_ranks(local_ms: float, dist, device) -> float:
     """The slowest rank's time (all ranks get it); local_ms itself on one process."""
     if dist is None:
@@ -526,6 +587,8 @@ def main():
                     help="time only the step in the paper's variable and print its record (profiling)")
     ap.add_argument("--implicit-only", action="store_true",
                     help="time only the implicit-transport step and print its record (profiling)")
+    ap.add_argument("--coupled-only", action="store_true",
+                    help="time only the coupled Navier-Stokes + stress step and print its record (profiling)")
     ap.add_argument("--fp64-only", action="store_true",
                     help="time only the FP64 storage form of the step and print its record (profiling)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32plain"])
@@ -558,6 +621,13 @@ def main():
         tbuild.build()
         torch.cuda.set_device(0)
         print(json.dumps(implicit_transport_record(torch.device("cuda", 0))), flush=True)
+        return
+    if args.coupled_only:
+        import torch
+        from paper_2411_17294_gb300 import build as tbuild
+        tbuild.build()
+        torch.cuda.set_device(0)
+        print(json.dumps(ns_coupled_record(torch.device("cuda", 0))), flush=True)
         return
     if args.fp64_only:
         import torch
@@ -698,6 +768,13 @@ def main():
         except Exception as exc:  # pragma: no cover - reported, not fatal
             paper = {"error": str(exc)}
 
+    coupled = None
+    if not args.no_adjoint:
+        try:
+            coupled = ns_coupled_record(dev)
+        except Exception as exc:  # pragma: no cover - reported, not fatal
+            coupled = {"error": str(exc)}
+
     fp64 = None
     if not args.no_adjoint and prec != tfs.TFS_FP64:
         try:
@@ -750,6 +827,7 @@ def main():
             "implicit_transport": imp,
             "paper_form": paper,
             "fp64_form": fp64,
+            "ns_coupled": coupled,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
