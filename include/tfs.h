@@ -393,7 +393,8 @@ int tfs_ns_create(tfs_ns_handle* h, int n0, int n1, double L0, double L1, double
                   int precision);
 
 /* Device workspace of the handle: 21 complex and 8 real FP64 fields of n0 n1
-   values, each rounded up to 256 bytes. */
+   values and the transforms' twiddle tables (n0/2 + n1/2 complex), each
+   rounded up to 256 bytes. */
 size_t tfs_ns_workspace_bytes(tfs_ns_handle h);
 
 /* Bind caller-owned device memory (256-byte aligned) of at least

@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/tfs.h"
 #include "tfs_internal.h"
@@ -42,13 +43,16 @@ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_dou
 __device__ __forceinline__ double2 cimul(double d, double2 a) { return make_double2(-d * a.y, d * a.x); }
 
 // DFT of each row of length n (a power of two, 2 .. kMaxLen) with
-// exp(sign 2 pi i j k / n), times `scale`; one block per row, rows of `in`
-// and `out` n elements apart (in == out allowed: a row is read whole first).
-// Stockham autosort: stage Ns = 1, 2, 4, ... combines butterflies of span Ns
-// from the first and second halves, writing them to expand(j) = (j / Ns) 2 Ns
-// + j % Ns and expand(j) + Ns, ping-ponging between two shared buffers; the
-// result is in natural order.
-__global__ void __launch_bounds__(kNsThreads) fft_rows_kernel(const double2* in, double2* out, int n, double sign,
+// exp(-+ 2 pi i j k / n) (forward / inverse), times `scale`; one block per row,
+// rows of `in` and `out` n elements apart (in == out allowed: a row is read
+// whole first).  tw[t] = exp(-2 pi i t / n), t < n/2 (computed once on the
+// host in FP64).  Stockham autosort: stage Ns = 1, 2, 4, ... combines
+// butterflies of span Ns from the first and second halves, the second operand
+// turned by exp(-+ pi i k / Ns) = tw[k n / (2 Ns)], k = j mod Ns, and writes
+// them to expand(j) = (j / Ns) 2 Ns + j % Ns and expand(j) + Ns, ping-ponging
+// between two shared buffers; the result is in natural order.
+__global__ void __launch_bounds__(kNsThreads) fft_rows_kernel(const double2* in, double2* out, int n,
+                                                              const double2* __restrict__ tw, int inverse,
                                                               double scale) {
     extern __shared__ double2 fft_buf[];
     double2* x = fft_buf;
@@ -58,20 +62,21 @@ __global__ void __launch_bounds__(kNsThreads) fft_rows_kernel(const double2* in,
     __syncthreads();
     const int half = n >> 1;
     for (int ns = 1; ns < n; ns <<= 1) {
+        const int step = half / ns;
         for (int j = threadIdx.x; j < half; j += blockDim.x) {
             const int k = j & (ns - 1);
-            double s, c;
-            sincospi(sign * (double)k / (double)ns, &s, &c);
+            double2 t = __ldg(tw + k * step);
+            if (inverse) t.y = -t.y;
             const double2 a = x[j];
-            const double2 b = cmul(x[j + half], make_double2(c, s));
+            const double2 b = cmul(x[j + half], t);
             const int o = ((j - k) << 1) + k;
             y[o] = cadd(a, b);
             y[o + ns] = csub(a, b);
         }
         __syncthreads();
-        double2* t = x;
+        double2* tmp = x;
         x = y;
-        y = t;
+        y = tmp;
     }
     double2* dst = out + (long long)blockIdx.x * n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = cscale(x[i], scale);
@@ -236,6 +241,9 @@ struct tfs_ns_ctx {
     double* u = nullptr;
     double* kap = nullptr;
     double* conv = nullptr;
+    double2* tw0 = nullptr;       // exp(-2 pi i t / n0), t < n0/2; and for n1
+    double2* tw1 = nullptr;
+    std::vector<double2> tw_host; // both tables, uploaded by tfs_ns_set_state
     int cur = 0;                  // slot of level n (n-1 in the other)
     bool have_prev_terms = false; // f^{n-1} exists (else the empty past: f^{n-1} = f^n)
     bool state_set = false;
@@ -249,7 +257,7 @@ size_t ns_up(size_t v) { return (v + kNsAlign - 1) / kNsAlign * kNsAlign; }
 
 size_t ns_bytes(const tfs_ns_ctx* h) {
     const size_t cplx = ns_up(sizeof(double2) * (size_t)h->N), real = ns_up(sizeof(double) * (size_t)h->N);
-    return 21 * cplx + 8 * real;
+    return 21 * cplx + 8 * real + ns_up(sizeof(double2) * (size_t)(h->n0 / 2 + h->n1 / 2));
 }
 
 void ns_layout(tfs_ns_ctx* h) {
@@ -270,6 +278,9 @@ void ns_layout(tfs_ns_ctx* h) {
     h->kap = (double*)p;
     p += 4 * real;
     h->conv = (double*)p;
+    p += 2 * real;
+    h->tw0 = (double2*)p;
+    h->tw1 = h->tw0 + h->n0 / 2;
 }
 
 unsigned ns_grid(long long n) {
@@ -277,10 +288,11 @@ unsigned ns_grid(long long n) {
     return (unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b));
 }
 
-cudaError_t fft_rows(const tfs_ns_ctx*, const double2* in, double2* out, int n, int rows, double sign, double scale,
-                     cudaStream_t s) {
+cudaError_t fft_rows(const tfs_ns_ctx* h, const double2* in, double2* out, int n, int rows, double sign,
+                     double scale, cudaStream_t s) {
     const int threads = n / 2 < kNsThreads ? (n / 2 > 0 ? n / 2 : 1) : kNsThreads;
-    fft_rows_kernel<<<rows, threads, 2 * n * sizeof(double2), s>>>(in, out, n, sign, scale);
+    const double2* tw = n == h->n0 ? h->tw0 : h->tw1;
+    fft_rows_kernel<<<rows, threads, 2 * n * sizeof(double2), s>>>(in, out, n, tw, sign > 0 ? 1 : 0, scale);
     return cudaGetLastError();
 }
 
@@ -343,7 +355,9 @@ template <typename T>
 int ns_set_state(tfs_ns_ctx* h, const T* u0, const T* uprev, cudaStream_t s) {
     const long long N = h->N;
     const int c = h->cur, o = 1 - c;
-    cudaError_t e = fft2_real<T>(h, u0, h->uh[c][0], s);
+    cudaError_t e = cudaMemcpyAsync(h->tw0, h->tw_host.data(), sizeof(double2) * h->tw_host.size(),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = fft2_real<T>(h, u0, h->uh[c][0], s);
     if (e == cudaSuccess) e = fft2_real<T>(h, u0 + N, h->uh[c][1], s);
     if (e == cudaSuccess) {
         ns_project_kernel<<<ns_grid(N), kNsThreads, 0, s>>>(h->uh[c][0], h->uh[c][1], h->n0, h->n1, h->sx, h->sy);
@@ -433,6 +447,12 @@ int tfs_ns_create(tfs_ns_handle* out, int n0, int n1, double L0, double L1, doub
     h->nu = beta / Re;
     h->dt = dt;
     h->precision = precision;
+    // twiddle tables exp(-2 pi i t / n), t < n/2, of both axes (FP64, host)
+    for (int n : {n0, n1})
+        for (int t = 0; t < n / 2; ++t) {
+            const double a = -2.0 * 3.14159265358979323846 * (double)t / (double)n;
+            h->tw_host.push_back(make_double2(std::cos(a), std::sin(a)));
+        }
     *out = h;
     return TFS_OK;
 }
