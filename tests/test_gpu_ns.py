@@ -109,3 +109,40 @@ def test_coupled_velocity_and_stress_match_oracle(precision):
     assert np.max(np.abs(ref_s)) > 1e-3 and np.max(np.abs(ref_u)) > 1e-3
     assert np.all(rel_err_per_component(got_u, ref_u) < tol)
     assert np.all(rel_err_per_component(got_s, ref_s) < tol)
+
+
+def test_coupled_1024_matches_oracle():
+    # The coupled step at the 2D 1024^2 size of the benchmark record (alpha =
+    # 0.5, m = 32, Wi = 2, beta = 0.9, Re = 100, dt = 5e-4, FP32 storage,
+    # spectral velocity at 0.3 of the explicit transport's limit), six steps,
+    # against the coupled oracle over the whole field.
+    import torch
+    from paper_2411_17294_gb300 import soe as psoe
+    from paper_2411_17294_gb300 import tfs
+    n, L, dt, steps = (1024, 1024), (2 * math.pi, 2 * math.pi), 5e-4, 6
+    alpha, Wi, beta, Re, m = 0.5, 2.0, 0.9, 100.0, 32
+    mu, w = psoe.build(alpha, dt, 200 * dt, m)
+    st = tfs.Solver(2, n, alpha, Wi, beta, dt, m=m, precision=tfs.TFS_FP32, mu=mu, w=w, transport=True, L=L)
+    U = st.transport_limit()
+    u0, _ = inputs.spectral_velocity(2, n, 32, 2)
+    u0 = np.asarray(u0) * (0.3 * U / np.max(np.abs(u0)))
+    u0 = np.asarray(u0, np.float32).astype(np.float64)
+    ns = tfs.NSSolver(n, L, beta, Re, dt, precision=tfs.TFS_FP32)
+    ns.set_state(u0)
+    st.set_state(None)
+    for _ in range(steps):
+        u_t, k_t = ns.step(st.stress())
+        st.step(k_t, k_t, u_t)
+    got_u, got_s, flags = u_t.double().cpu().numpy(), st.stress().double().cpu().numpy(), st.status()
+    ns.close()
+    st.close()
+    ons = NSOracle(n, L, beta, Re, dt)
+    ons.set_state(u0)
+    ost = orc.Oracle(orc.Problem(dim=2, n=n, alpha=alpha, Wi=Wi, beta=beta, dt=dt, mu=mu, w=w, transport=True,
+                                 L=L), None)
+    for _ in range(steps):
+        u, kap = ons.step(ost.sig_n)
+        ost.step(kap, kap, u)
+    assert flags == 0
+    assert np.all(rel_err_per_component(got_u, u) < 2e-5)
+    assert np.all(rel_err_per_component(got_s, ost.sig_n) < 2e-5)
