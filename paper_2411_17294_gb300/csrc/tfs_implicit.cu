@@ -260,6 +260,129 @@ __global__ void __launch_bounds__(kThreads) imp_apply_kernel(const ImpArgs<T> A,
     if (w0) block_partials((double)a0, (double)a1, w1 ? 2 : 1, partials);
 }
 
+// The same operator on grids with n0 % 32 == 0 and n1 % 8 == 0, tiled: a unit
+// is a 32 x 8 (x, y) tile and a chunk of kZc z planes (one plane in 2D); the
+// block stages the tile of x with a 2-cell halo in x and y in shared memory
+// once per plane (every x value loaded once per tile instead of at nine taps),
+// keeps x at z-2 .. z+2 of its own column in registers (3D), and applies the
+// taps without branches (a zero coefficient adds nothing).  Units are handed
+// out grid-stride over exactly kImpBlocks blocks, so that the partial sums are
+// those of fixed blocks, reduced in a fixed order as everywhere else.
+constexpr int kAX = 32, kAY = 8, kAH = 2, kAZc = 8;
+constexpr int kASX = kAX + 2 * kAH, kASY = kAY + 2 * kAH;
+
+template <typename T, int DIM, typename V>
+__global__ void __launch_bounds__(kThreads) imp_apply_tiled_kernel(const ImpArgs<T> A, const V* __restrict__ Mb,
+                                                                    const V* __restrict__ Cf,
+                                                                    const V* __restrict__ x, V* y, const V* w0,
+                                                                    const V* w1, double* partials,
+                                                                    const double* sc) {
+    constexpr int NC = Packed<DIM>::NC;
+    __shared__ V Xs[NC][kASY][kASX];
+    if (done(sc)) return;
+    const long long N = A.N;
+    const int n0 = A.n0, n1 = A.n1, n2 = DIM == 3 ? A.n2 : 1;
+    const long long plane = (long long)n0 * n1;
+    static_assert(kAX * kAY == kThreads, "one thread per tile point (block_partials reduces kThreads values)");
+    const int tid = threadIdx.x, tx = tid % kAX, ty = tid / kAX;
+    const int tiles_x = n0 / kAX, tiles_y = n1 / kAY;
+    const int zchunks = (n2 + kAZc - 1) / kAZc;
+    const long long units = (long long)tiles_x * tiles_y * zchunks;
+    auto wrap = [](int v, int n) { v %= n; return v < 0 ? v + n : v; };
+    V a0 = (V)0, a1 = (V)0;
+    for (long long unit = blockIdx.x; unit < units; unit += gridDim.x) {
+        const int txy = (int)(unit % ((long long)tiles_x * tiles_y));
+        const int zc = (int)(unit / ((long long)tiles_x * tiles_y));
+        const int x0 = (txy % tiles_x) * kAX, y0 = (txy / tiles_x) * kAY;
+        const int gx = x0 + tx, gy = y0 + ty;
+        const long long qxy = gx + (long long)n0 * gy;
+        const int zb = zc * kAZc, ze = min(zb + kAZc, n2);
+        V qz[NC][5];   // x of this column at z-2 .. z+2 (3D)
+        if (DIM == 3) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const long long o = plane * wrap(zb - 2 + k, n2) + qxy;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) qz[c][k] = x[(long long)c * N + o];
+            }
+        }
+        for (int z = zb; z < ze; ++z) {
+            const long long zo = plane * z;
+            if (DIM == 3) {
+                const long long o = plane * wrap(z + 2, n2) + qxy;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) qz[c][4] = x[(long long)c * N + o];
+            }
+            __syncthreads();   // the previous plane's reads of Xs are done
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                Xs[c][ty + kAH][tx + kAH] = DIM == 3 ? qz[c][2] : x[(long long)c * N + zo + qxy];
+            for (int h = tid; h < kASX * kASY; h += kAX * kAY) {
+                const int hy = h / kASX, hx = h - hy * kASX;
+                if (hx >= kAH && hx < kAH + kAX && hy >= kAH && hy < kAH + kAY) continue;
+                const long long o = zo + wrap(x0 + hx - kAH, n0) + (long long)n0 * wrap(y0 + hy - kAH, n1);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) Xs[c][hy][hx] = x[(long long)c * N + o];
+            }
+            __syncthreads();
+            const long long p = zo + qxy;
+            V cf[DIM][4];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) cf[a][t] = Cf[(long long)(a * 4 + t) * N + p];
+            V xp[NC];
+#pragma unroll
+            for (int k = 0; k < NC; ++k) xp[k] = Xs[k][ty + kAH][tx + kAH];
+#pragma unroll
+            for (int r = 0; r < NC; ++r) {
+                V acc = (V)0;
+#pragma unroll
+                for (int k = 0; k < NC; ++k) acc = fma(Mb[(long long)(r * NC + k) * N + p], xp[k], acc);
+                const int sy = ty + kAH, sx = tx + kAH;
+                // taps -2, -1, +1, +2 along x, y (and z from the registers)
+                acc = fma(cf[0][0], Xs[r][sy][sx - 2], acc);
+                acc = fma(cf[0][1], Xs[r][sy][sx - 1], acc);
+                acc = fma(cf[0][2], Xs[r][sy][sx + 1], acc);
+                acc = fma(cf[0][3], Xs[r][sy][sx + 2], acc);
+                acc = fma(cf[1][0], Xs[r][sy - 2][sx], acc);
+                acc = fma(cf[1][1], Xs[r][sy - 1][sx], acc);
+                acc = fma(cf[1][2], Xs[r][sy + 1][sx], acc);
+                acc = fma(cf[1][3], Xs[r][sy + 2][sx], acc);
+                if (DIM == 3) {
+                    acc = fma(cf[DIM - 1][0], qz[r][0], acc);
+                    acc = fma(cf[DIM - 1][1], qz[r][1], acc);
+                    acc = fma(cf[DIM - 1][2], qz[r][3], acc);
+                    acc = fma(cf[DIM - 1][3], qz[r][4], acc);
+                }
+                const long long q = (long long)r * N + p;
+                y[q] = acc;
+                if (w0) a0 = fma(w0[q], acc, a0);
+                if (w1) a1 = fma(w1[q], acc, a1);
+            }
+            if (DIM == 3) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) qz[c][k] = qz[c][k + 1];
+            }
+        }
+    }
+    if (w0) block_partials((double)a0, (double)a1, w1 ? 2 : 1, partials);
+}
+
+// Op x -> y (with the partial dot products): the tiled kernel where the grid
+// tiles, the per-point one elsewhere.  Both compute every entry in the same
+// order, so the result does not depend on which one runs.
+template <typename T, int DIM, typename V>
+void launch_apply(const ImpArgs<T>& a, const V* Mb, const V* Cf, const V* x, V* y, const V* w0, const V* w1,
+                  double* partials, const double* sc, cudaStream_t st) {
+    if (a.n0 % kAX == 0 && a.n1 % kAY == 0)
+        imp_apply_tiled_kernel<T, DIM, V><<<kImpBlocks, kThreads, 0, st>>>(a, Mb, Cf, x, y, w0, w1, partials, sc);
+    else
+        imp_apply_kernel<T, DIM, V><<<kImpBlocks, kThreads, 0, st>>>(a, Mb, Cf, x, y, w0, w1, partials, sc);
+}
+
 // z = P^-1 v with v = a x + b y (+ c w): forms the combination, stores it in
 // `comb` (when given) and its preconditioned image in z
 template <int NC, typename V>
@@ -1195,7 +1318,7 @@ cudaError_t bicgstab(const ImpArgs<T>& a, const BiVecs<V>& K, double* partials, 
         return e;
     }
     if (!x_zero) {
-        imp_apply_kernel<T, DIM, V><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Cf, K.x, K.r, nullptr, nullptr, partials, sc);
+        launch_apply<T, DIM, V>(a, K.Mb, K.Cf, K.x, K.r, nullptr, nullptr, partials, sc, st);
         if (!ok()) return e;
     }
     imp_init_kernel<V><<<bs, kThreads, 0, st>>>(n, K.b, K.r, K.rh, K.p, K.v, K.x, x_zero ? 1 : 0);
@@ -1207,10 +1330,10 @@ cudaError_t bicgstab(const ImpArgs<T>& a, const BiVecs<V>& K, double* partials, 
     constexpr int kCheck = 8;
     for (int it = 0; it < maxit; ++it) {
         imp_comb_precond_kernel<NC, V><<<bs, kThreads, 0, st>>>(N, K.Pinv, 0, K.p, K.r, K.v, K.ph, sc);
-        imp_apply_kernel<T, DIM, V><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Cf, K.ph, K.v, K.rh, nullptr, partials, sc);
+        launch_apply<T, DIM, V>(a, K.Mb, K.Cf, K.ph, K.v, K.rh, nullptr, partials, sc, st);
         imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 1);
         imp_comb_precond_kernel<NC, V><<<bs, kThreads, 0, st>>>(N, K.Pinv, 1, K.sv, K.r, K.v, K.sh, sc);
-        imp_apply_kernel<T, DIM, V><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Cf, K.sh, K.t, K.sv, K.t, partials, sc);
+        launch_apply<T, DIM, V>(a, K.Mb, K.Cf, K.sh, K.t, K.sv, K.t, partials, sc, st);
         imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 2);
         imp_xr_kernel<V><<<bs, kThreads, 0, st>>>(n, K.x, K.ph, K.sh, K.r, K.sv, K.t, K.rh, partials, sc);
         imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 0);
@@ -1304,8 +1427,7 @@ cudaError_t krylov_solve(const ImpArgs<T>& a, const KryView<Packed<DIM>::NC>& K,
     constexpr int kOuterMax = 12;
     for (int outer = 0; outer < kOuterMax; ++outer) {
         // r = b - Op x in FP64, its float copy, (r, r)
-        imp_apply_kernel<T, DIM, double><<<bs, kThreads, 0, st>>>(a, K.Mb, K.Cf, K.x, K.r, nullptr, nullptr,
-                                                                   partials, sco);
+        launch_apply<T, DIM, double>(a, K.Mb, K.Cf, K.x, K.r, nullptr, nullptr, partials, sco, st);
         imp_resid_kernel<<<bs, kThreads, 0, st>>>(n, K.b, K.r, K.rf, partials);
         imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sco, 3);
         if (!ok()) return e;
