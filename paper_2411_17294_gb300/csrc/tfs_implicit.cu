@@ -21,7 +21,9 @@
 // new mode level from Q_j).  One thread per point, grid-stride loops.
 #include <cuda_runtime.h>
 
+#include <array>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <vector>
 
@@ -181,291 +183,83 @@ constexpr int kPartialSets = 2;    // dot products reduced in one pass
 
 __device__ __forceinline__ bool done(const double* sc) { return sc[S_DONE] != 0.0; }
 
+constexpr int kWarps = kThreads / 32;
+
+// sum over the 32 lanes of a warp in a fixed order (lane 0 holds it)
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// sums of two values over the block (every thread calls), in thread 0; the
+// per-warp sums pass through sh
+__device__ __forceinline__ void block_sum2(double& a0, double& a1, double (*sh)[kWarps]) {
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = a0;
+        sh[1][threadIdx.x >> 5] = a1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a0 = a1 = 0.0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            a0 += sh[0][w];
+            a1 += sh[1][w];
+        }
+    }
+}
+
 // block-level reduction of two values into partials[set * kImpBlocks + block]
 __device__ __forceinline__ void block_partials(double a0, double a1, int nsets, double* partials) {
-    __shared__ double sh[2][kThreads];
-    sh[0][threadIdx.x] = a0;
-    sh[1][threadIdx.x] = a1;
-    __syncthreads();
-    for (int st = kThreads / 2; st > 0; st >>= 1) {
-        if ((int)threadIdx.x < st) {
-            sh[0][threadIdx.x] += sh[0][threadIdx.x + st];
-            sh[1][threadIdx.x] += sh[1][threadIdx.x + st];
-        }
-        __syncthreads();
-    }
+    __shared__ double sh[2][kWarps];
+    block_sum2(a0, a1, sh);
     if (threadIdx.x == 0) {
-        partials[blockIdx.x] = sh[0][0];
-        if (nsets > 1) partials[kImpBlocks + blockIdx.x] = sh[1][0];
+        partials[blockIdx.x] = a0;
+        if (nsets > 1) partials[kImpBlocks + blockIdx.x] = a1;
     }
 }
 
-// y = Op(x) = P_p x_p + sum_a sum_t Cf x_{p + tap} with the per-step blocks and
-// coefficients of imp_setup_kernel; partial sums of (w0, y) and (w1, y) when
-// w0 / w1 are given (w1 may be y itself: the (t, t) product).  The periodic
-// neighbour offsets are 32-bit (an implicit-transport workspace for 2^31 points
-// would not fit any device).
-template <typename T, int DIM, typename V>
-__global__ void __launch_bounds__(kThreads) imp_apply_kernel(const ImpArgs<T> A, const V* __restrict__ Mb,
-                                                             const V* __restrict__ Cf, const V* __restrict__ x, V* y,
-                                                             const V* w0, const V* w1, double* partials,
-                                                             const double* sc) {
-    constexpr int NC = Packed<DIM>::NC;
-    if (done(sc)) return;
-    const long long N = A.N;
-    const int n0 = A.n0, n1 = A.n1, n2 = A.n2;
-    V a0 = (V)0, a1 = (V)0;   // per-thread dot products (a few points each), then double per block
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-        const unsigned pp = (unsigned)p;
-        const unsigned q1 = pp / (unsigned)n0;
-        const int c[3] = {(int)(pp - q1 * (unsigned)n0), (int)(q1 % (unsigned)n1), (int)(q1 / (unsigned)n1)};
-        const int len[3] = {n0, n1, n2};
-        const int str[3] = {1, n0, n0 * n1};
-        int off[3][4];
-        V cf[3][4];
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int k = t < 2 ? t - 2 : t - 1;
-                int v = c[a] + k;
-                if (v < 0) v += len[a];
-                if (v < 0) v += len[a];
-                if (v >= len[a]) v -= len[a];
-                if (v >= len[a]) v -= len[a];
-                off[a][t] = (v - c[a]) * str[a];
-                cf[a][t] = Cf[(long long)(a * 4 + t) * N + p];
-            }
-        }
-        V xp[NC];
-#pragma unroll
-        for (int k = 0; k < NC; ++k) xp[k] = x[(long long)k * N + p];
-#pragma unroll
-        for (int r = 0; r < NC; ++r) {
-            V acc = (V)0;
-#pragma unroll
-            for (int k = 0; k < NC; ++k) acc = fma(Mb[(long long)(r * NC + k) * N + p], xp[k], acc);
-            const V* f = x + (long long)r * N + p;
-#pragma unroll
-            for (int a = 0; a < DIM; ++a)
-#pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    if (cf[a][t] != (V)0) acc = fma(cf[a][t], f[off[a][t]], acc);
-            const long long q = (long long)r * N + p;
-            y[q] = acc;
-            if (w0) a0 = fma(w0[q], acc, a0);
-            if (w1) a1 = fma(w1[q], acc, a1);
-        }
+// After block_partials: true in every thread of the block that finishes last
+// (a ticket drawn after a fence that publishes the block's partial sums), which
+// then resets the ticket for the next launch.
+__device__ __forceinline__ bool last_block(unsigned* ticket) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        if (last) *ticket = 0u;
     }
-    if (w0) block_partials((double)a0, (double)a1, w1 ? 2 : 1, partials);
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
 }
 
-// The same operator on grids with n0 % 32 == 0 and n1 % 8 == 0, tiled: a unit
-// is a 32 x 8 (x, y) tile and a chunk of kZc z planes (one plane in 2D); the
-// block stages the tile of x with a 2-cell halo in x and y in shared memory
-// once per plane (every x value loaded once per tile instead of at nine taps),
-// keeps x at z-2 .. z+2 of its own column in registers (3D), and applies the
-// taps without branches (a zero coefficient adds nothing).  Units are handed
-// out grid-stride over exactly kImpBlocks blocks, so that the partial sums are
-// those of fixed blocks, reduced in a fixed order as everywhere else.
-constexpr int kAX = 32, kAY = 8, kAH = 2, kAZc = 8;
-constexpr int kASX = kAX + 2 * kAH, kASY = kAY + 2 * kAH;
-
-template <typename T, int DIM, typename V>
-__global__ void __launch_bounds__(kThreads) imp_apply_tiled_kernel(const ImpArgs<T> A, const V* __restrict__ Mb,
-                                                                    const V* __restrict__ Cf,
-                                                                    const V* __restrict__ x, V* y, const V* w0,
-                                                                    const V* w1, double* partials,
-                                                                    const double* sc) {
-    constexpr int NC = Packed<DIM>::NC;
-    __shared__ V Xs[NC][kASY][kASX];
-    if (done(sc)) return;
-    const long long N = A.N;
-    const int n0 = A.n0, n1 = A.n1, n2 = DIM == 3 ? A.n2 : 1;
-    const long long plane = (long long)n0 * n1;
-    static_assert(kAX * kAY == kThreads, "one thread per tile point (block_partials reduces kThreads values)");
-    const int tid = threadIdx.x, tx = tid % kAX, ty = tid / kAX;
-    const int tiles_x = n0 / kAX, tiles_y = n1 / kAY;
-    const int zchunks = (n2 + kAZc - 1) / kAZc;
-    const long long units = (long long)tiles_x * tiles_y * zchunks;
-    auto wrap = [](int v, int n) { v %= n; return v < 0 ? v + n : v; };
-    V a0 = (V)0, a1 = (V)0;
-    for (long long unit = blockIdx.x; unit < units; unit += gridDim.x) {
-        const int txy = (int)(unit % ((long long)tiles_x * tiles_y));
-        const int zc = (int)(unit / ((long long)tiles_x * tiles_y));
-        const int x0 = (txy % tiles_x) * kAX, y0 = (txy / tiles_x) * kAY;
-        const int gx = x0 + tx, gy = y0 + ty;
-        const long long qxy = gx + (long long)n0 * gy;
-        const int zb = zc * kAZc, ze = min(zb + kAZc, n2);
-        V qz[NC][5];   // x of this column at z-2 .. z+2 (3D)
-        if (DIM == 3) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const long long o = plane * wrap(zb - 2 + k, n2) + qxy;
-#pragma unroll
-                for (int c = 0; c < NC; ++c) qz[c][k] = x[(long long)c * N + o];
-            }
-        }
-        for (int z = zb; z < ze; ++z) {
-            const long long zo = plane * z;
-            if (DIM == 3) {
-                const long long o = plane * wrap(z + 2, n2) + qxy;
-#pragma unroll
-                for (int c = 0; c < NC; ++c) qz[c][4] = x[(long long)c * N + o];
-            }
-            __syncthreads();   // the previous plane's reads of Xs are done
-#pragma unroll
-            for (int c = 0; c < NC; ++c)
-                Xs[c][ty + kAH][tx + kAH] = DIM == 3 ? qz[c][2] : x[(long long)c * N + zo + qxy];
-            for (int h = tid; h < kASX * kASY; h += kAX * kAY) {
-                const int hy = h / kASX, hx = h - hy * kASX;
-                if (hx >= kAH && hx < kAH + kAX && hy >= kAH && hy < kAH + kAY) continue;
-                const long long o = zo + wrap(x0 + hx - kAH, n0) + (long long)n0 * wrap(y0 + hy - kAH, n1);
-#pragma unroll
-                for (int c = 0; c < NC; ++c) Xs[c][hy][hx] = x[(long long)c * N + o];
-            }
-            __syncthreads();
-            const long long p = zo + qxy;
-            V cf[DIM][4];
-#pragma unroll
-            for (int a = 0; a < DIM; ++a)
-#pragma unroll
-                for (int t = 0; t < 4; ++t) cf[a][t] = Cf[(long long)(a * 4 + t) * N + p];
-            V xp[NC];
-#pragma unroll
-            for (int k = 0; k < NC; ++k) xp[k] = Xs[k][ty + kAH][tx + kAH];
-#pragma unroll
-            for (int r = 0; r < NC; ++r) {
-                V acc = (V)0;
-#pragma unroll
-                for (int k = 0; k < NC; ++k) acc = fma(Mb[(long long)(r * NC + k) * N + p], xp[k], acc);
-                const int sy = ty + kAH, sx = tx + kAH;
-                // taps -2, -1, +1, +2 along x, y (and z from the registers)
-                acc = fma(cf[0][0], Xs[r][sy][sx - 2], acc);
-                acc = fma(cf[0][1], Xs[r][sy][sx - 1], acc);
-                acc = fma(cf[0][2], Xs[r][sy][sx + 1], acc);
-                acc = fma(cf[0][3], Xs[r][sy][sx + 2], acc);
-                acc = fma(cf[1][0], Xs[r][sy - 2][sx], acc);
-                acc = fma(cf[1][1], Xs[r][sy - 1][sx], acc);
-                acc = fma(cf[1][2], Xs[r][sy + 1][sx], acc);
-                acc = fma(cf[1][3], Xs[r][sy + 2][sx], acc);
-                if (DIM == 3) {
-                    acc = fma(cf[DIM - 1][0], qz[r][0], acc);
-                    acc = fma(cf[DIM - 1][1], qz[r][1], acc);
-                    acc = fma(cf[DIM - 1][2], qz[r][3], acc);
-                    acc = fma(cf[DIM - 1][3], qz[r][4], acc);
-                }
-                const long long q = (long long)r * N + p;
-                y[q] = acc;
-                if (w0) a0 = fma(w0[q], acc, a0);
-                if (w1) a1 = fma(w1[q], acc, a1);
-            }
-            if (DIM == 3) {
-#pragma unroll
-                for (int c = 0; c < NC; ++c)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) qz[c][k] = qz[c][k + 1];
-            }
-        }
-    }
-    if (w0) block_partials((double)a0, (double)a1, w1 ? 2 : 1, partials);
-}
-
-// Op x -> y (with the partial dot products): the tiled kernel where the grid
-// tiles, the per-point one elsewhere.  Both compute every entry in the same
-// order, so the result does not depend on which one runs.
-template <typename T, int DIM, typename V>
-void launch_apply(const ImpArgs<T>& a, const V* Mb, const V* Cf, const V* x, V* y, const V* w0, const V* w1,
-                  double* partials, const double* sc, cudaStream_t st) {
-    if (a.n0 % kAX == 0 && a.n1 % kAY == 0)
-        imp_apply_tiled_kernel<T, DIM, V><<<kImpBlocks, kThreads, 0, st>>>(a, Mb, Cf, x, y, w0, w1, partials, sc);
-    else
-        imp_apply_kernel<T, DIM, V><<<kImpBlocks, kThreads, 0, st>>>(a, Mb, Cf, x, y, w0, w1, partials, sc);
-}
-
-// z = P^-1 v with v = a x + b y (+ c w): forms the combination, stores it in
-// `comb` (when given) and its preconditioned image in z
-template <int NC, typename V>
-__global__ void __launch_bounds__(kThreads) imp_comb_precond_kernel(long long N, const V* Pinv, int mode, V* p,
-                                                                    const V* r, const V* v, V* z, const double* sc) {
-    if (done(sc)) return;
-    // mode 0: p = r + beta (p - omega v);  mode 1: p (as s) = r - alpha v
-    const V beta = (V)sc[S_BETA], omega = (V)sc[S_OMEGA], alpha = (V)sc[S_ALPHA];
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        V w[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const long long q = (long long)c * N + i;
-            const V nv = mode == 0 ? fma(beta, p[q] - omega * v[q], r[q]) : fma(-alpha, v[q], r[q]);
-            p[q] = nv;
-            w[c] = nv;
-        }
-#pragma unroll
-        for (int rr = 0; rr < NC; ++rr) {
-            V acc = (V)0;
-#pragma unroll
-            for (int k = 0; k < NC; ++k) acc = fma(Pinv[(long long)(rr * NC + k) * N + i], w[k], acc);
-            z[(long long)rr * N + i] = acc;
-        }
-    }
-}
-
-// x += alpha ph + omega sh;  r = s - omega t;  partial sums of (r, r) and (rh, r)
-template <typename V>
-__global__ void __launch_bounds__(kThreads) imp_xr_kernel(long long n, V* x, const V* ph, const V* sh, V* r,
-                                                          const V* s, const V* t, const V* rh, double* partials,
-                                                          const double* sc) {
-    if (done(sc)) return;
-    const V alpha = (V)sc[S_ALPHA], omega = (V)sc[S_OMEGA];
-    V a0 = (V)0, a1 = (V)0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        x[i] = fma(alpha, ph[i], fma(omega, sh[i], x[i]));
-        const V rv = fma(-omega, t[i], s[i]);
-        r[i] = rv;
-        a0 = fma(rv, rv, a0);
-        a1 = fma(rh[i], rv, a1);
-    }
-    block_partials((double)a0, (double)a1, 2, partials);
-}
-
-// per-block partial sums of x.y and x.z (z may be null), for the start of the iteration
-template <typename V>
-__global__ void __launch_bounds__(kThreads) imp_dot2_kernel(const V* x, const V* y, const V* z, long long n,
-                                                            double* partials) {
-    V a0 = (V)0, a1 = (V)0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        a0 = fma(x[i], y[i], a0);
-        if (z) a1 = fma(x[i], z[i], a1);
-    }
-    block_partials((double)a0, (double)a1, z ? 2 : 1, partials);
-}
-
-// One block: add the partial sums in a fixed order into scalar slots, then the
-// scalar step of the iteration.
+// One block: add the partial sums of nparts blocks in a fixed order into scalar
+// slots, then the scalar step of the iteration.
 //   op 0: RR, RHO_NEW <- (r, r), (rh, r); convergence test; beta and rho of the next direction
 //   op 1: RHV <- (rh, v); alpha
 //   op 2: TS, TT <- (t, s), (t, t); omega
 //   op 3: BNORM2 <- (b, b)
 //   op 4: RR, RHO_NEW <- (r, r), (rh, r) at the start; beta and rho of the first direction
-__global__ void __launch_bounds__(kThreads) imp_scalar_kernel(const double* partials, double* sc, int op) {
-    __shared__ double sh[2][kThreads];
-    double a0 = 0.0, a1 = 0.0;
-    for (int i = threadIdx.x; i < kImpBlocks; i += kThreads) {
-        a0 += partials[i];
-        a1 += partials[kImpBlocks + i];
+__device__ void scalar_step(const double* partials, int nparts, double* sc, int op) {
+    __shared__ double sh[2][kWarps];
+    static_assert(kImpBlocks <= 4 * kThreads, "at most four partial sums per thread");
+    // the (at most) four partial sums of a thread are loaded together; written by
+    // other blocks of this launch, they are read from L2
+    double p0[4], p1[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = threadIdx.x + k * kThreads;
+        p0[k] = i < nparts ? __ldcg(partials + i) : 0.0;
+        p1[k] = i < nparts ? __ldcg(partials + kImpBlocks + i) : 0.0;
     }
-    sh[0][threadIdx.x] = a0;
-    sh[1][threadIdx.x] = a1;
-    __syncthreads();
-    for (int st = kThreads / 2; st > 0; st >>= 1) {
-        if ((int)threadIdx.x < st) {
-            sh[0][threadIdx.x] += sh[0][threadIdx.x + st];
-            sh[1][threadIdx.x] += sh[1][threadIdx.x + st];
-        }
-        __syncthreads();
-    }
+    double v0 = (p0[0] + p0[1]) + (p0[2] + p0[3]);
+    double v1 = (p1[0] + p1[1]) + (p1[2] + p1[3]);
+    block_sum2(v0, v1, sh);
     if (threadIdx.x != 0) return;
-    const double v0 = sh[0][0], v1 = sh[1][0];
     if (op == 3) {
         sc[S_BNORM2] = v0;
         return;
@@ -510,6 +304,377 @@ __global__ void __launch_bounds__(kThreads) imp_scalar_kernel(const double* part
     }
 }
 
+// Grid of the operator kernels (all they take of a step's arguments)
+struct ImpGrid {
+    long long N;
+    int n0, n1, n2;
+};
+
+// Index of coefficient k of point p: FP64 coefficients (the step's system) are
+// [k][N]; the float copies of the inner solve are tile-major (mode_index over
+// 32-point tiles, K coefficients per point), so that the K loads of a point share
+// one base address and differ by constants.
+template <typename V, int K>
+__device__ __forceinline__ long long coef_at(long long p, int k, long long N) {
+    if constexpr (sizeof(V) == 4) return mode_index(p, k, K);
+    else return (long long)k * N + p;
+}
+
+// y = Op(x) = P_p x_p + sum_a sum_t Cf x_{p + tap} with the per-step blocks and
+// coefficients of imp_setup_kernel (float: blocks and taps of a point in one
+// tile-major array, Cf = Mb + nc^2 tile rows); partial sums of (w0, y) and (w1, y) when
+// w0 / w1 are given (w1 may be y itself: the (t, t) product), and with op >= 0
+// the scalar step op of scalar_step in the block that finishes last.  The
+// periodic neighbour offsets are 32-bit (an implicit-transport workspace for
+// 2^31 points would not fit any device).
+template <int DIM, typename V>
+__global__ void __launch_bounds__(kThreads) imp_apply_kernel(const ImpGrid A, const V* __restrict__ Mb,
+                                                             const V* __restrict__ Cf, const V* __restrict__ x, V* y,
+                                                             const V* w0, const V* w1, double* partials, double* sc,
+                                                             int op, unsigned* ticket) {
+    constexpr int NC = Packed<DIM>::NC;
+    constexpr int KA = NC * NC + 4 * DIM;   // coefficients per point (float layout)
+    if (done(sc)) return;
+    const long long N = A.N;
+    const int n0 = A.n0, n1 = A.n1, n2 = A.n2;
+    const bool w1y = w1 == y;   // (y, y): from the register, not read back
+    V a0 = (V)0, a1 = (V)0;   // per-thread dot products (a few points each), then double per block
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        const unsigned pp = (unsigned)p;
+        const unsigned q1 = pp / (unsigned)n0;
+        const int c[3] = {(int)(pp - q1 * (unsigned)n0), (int)(q1 % (unsigned)n1), (int)(q1 / (unsigned)n1)};
+        const int len[3] = {n0, n1, n2};
+        const int str[3] = {1, n0, n0 * n1};
+        int off[3][4];
+        V cf[3][4];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int k = t < 2 ? t - 2 : t - 1;
+                int v = c[a] + k;
+                if (v < 0) v += len[a];
+                if (v < 0) v += len[a];
+                if (v >= len[a]) v -= len[a];
+                if (v >= len[a]) v -= len[a];
+                off[a][t] = (v - c[a]) * str[a];
+                cf[a][t] = Cf[coef_at<V, KA>(p, a * 4 + t, N)];
+            }
+        }
+        V xp[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) xp[k] = x[(long long)k * N + p];
+#pragma unroll
+        for (int r = 0; r < NC; ++r) {
+            V acc = (V)0;
+#pragma unroll
+            for (int k = 0; k < NC; ++k) acc = fma(Mb[coef_at<V, KA>(p, r * NC + k, N)], xp[k], acc);
+            const V* f = x + (long long)r * N + p;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a)
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (cf[a][t] != (V)0) acc = fma(cf[a][t], f[off[a][t]], acc);
+            const long long q = (long long)r * N + p;
+            y[q] = acc;
+            if (w0) a0 = fma(w0[q], acc, a0);
+            if (w1) a1 = fma(w1y ? acc : w1[q], acc, a1);
+        }
+    }
+    if (w0) {
+        block_partials((double)a0, (double)a1, w1 ? 2 : 1, partials);
+        if (op >= 0 && last_block(ticket)) scalar_step(partials, gridDim.x, sc, op);
+    }
+}
+
+// The same operator on grids with n0 % 32 == 0 and n1 % 8 == 0, tiled: a unit
+// is a 32 x 8 (x, y) tile and a chunk of kZc z planes (one plane in 2D); the
+// block stages the tile of x with a 2-cell halo in x and y in shared memory
+// once per plane (every x value loaded once per tile instead of at nine taps),
+// keeps x at z-2 .. z+2 of its own column in registers (3D), and applies the
+// taps without branches (a zero coefficient adds nothing).  The point's
+// coefficients (and w0) are loaded before the staging barrier, so that their
+// loads and those of the tile are in flight together.  Units are handed out
+// grid-stride over a fixed grid, so that the partial sums are those of fixed
+// blocks, reduced in a fixed order as everywhere else.
+constexpr int kAX = 32, kAY = 8, kAH = 2, kAZc = 8;
+constexpr int kASX = kAX + 2 * kAH, kASY = kAY + 2 * kAH;
+
+template <int DIM, typename V>
+__global__ void __launch_bounds__(kThreads, DIM == 2 && sizeof(V) == 4 ? 6 : 1)
+    imp_apply_tiled_kernel(const ImpGrid A, const V* __restrict__ Mb, const V* __restrict__ Cf,
+                                                                    const V* __restrict__ x, V* y, const V* w0,
+                                                                    const V* w1, double* partials, double* sc,
+                                                                    int op, unsigned* ticket) {
+    constexpr int NC = Packed<DIM>::NC;
+    constexpr int KA = NC * NC + 4 * DIM;   // coefficients per point (float layout)
+    constexpr bool kPreMb = NC <= 3;   // the 2D blocks in registers across the barrier (3D: too many)
+    __shared__ V Xs[NC][kASY][kASX];
+    if (done(sc)) return;
+    const bool w1y = w1 == y;
+    const long long N = A.N;
+    const int n0 = A.n0, n1 = A.n1, n2 = DIM == 3 ? A.n2 : 1;
+    const long long plane = (long long)n0 * n1;
+    static_assert(kAX * kAY == kThreads, "one thread per tile point (block_partials reduces kThreads values)");
+    const int tid = threadIdx.x, tx = tid % kAX, ty = tid / kAX;
+    const int tiles_x = n0 / kAX, tiles = tiles_x * (n1 / kAY);
+    const int zchunks = (n2 + kAZc - 1) / kAZc;
+    const int units = tiles * zchunks;   // 32-bit: a unit holds at least 256 points
+    auto wrap = [](int v, int n) { v %= n; return v < 0 ? v + n : v; };
+    auto wrap1 = [](int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); };   // -n <= v < 2n
+    // the halo cell this thread stages: the ring of width kAH around the tile
+    // (kAH rows above, kAH rows below, kAH columns left and right), one cell per
+    // thread of the first kHalo
+    constexpr int kHalo = kASX * kASY - kAX * kAY;
+    static_assert(kHalo <= kThreads, "one halo cell per thread");
+    const bool halo = tid < kHalo;
+    int hx, hy;
+    {
+        int t = tid;
+        if (t < kAH * kASX) {
+            hy = t / kASX; hx = t % kASX;
+        } else if ((t -= kAH * kASX) < kAH * kASX) {
+            hy = kAH + kAY + t / kASX; hx = t % kASX;
+        } else if ((t -= kAH * kASX) < kAY * kAH) {
+            hy = kAH + t / kAH; hx = t % kAH;
+        } else {
+            t -= kAY * kAH;
+            hy = kAH + t / kAH; hx = kAH + kAX + t % kAH;
+        }
+    }
+    V a0 = (V)0, a1 = (V)0;
+    for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
+        const int txy = zchunks == 1 ? unit : unit % tiles;
+        const int zc = zchunks == 1 ? 0 : unit / tiles;
+        const int x0 = (txy % tiles_x) * kAX, y0 = (txy / tiles_x) * kAY;
+        const int gx = x0 + tx, gy = y0 + ty;
+        const long long qxy = gx + (long long)n0 * gy;
+        const int zb = zc * kAZc, ze = min(zb + kAZc, n2);
+        V qz[NC][5];   // x of this column at z-2 .. z+2 (3D)
+        if (DIM == 3) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const long long o = plane * wrap(zb - 2 + k, n2) + qxy;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) qz[c][k] = x[(long long)c * N + o];
+            }
+        }
+        for (int z = zb; z < ze; ++z) {
+            const long long zo = plane * z;
+            const long long p = zo + qxy;
+            V cf[DIM][4], mb[kPreMb ? NC : 1][kPreMb ? NC : 1], wv[NC];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) cf[a][t] = Cf[coef_at<V, KA>(p, a * 4 + t, N)];
+            if constexpr (kPreMb) {
+#pragma unroll
+                for (int r = 0; r < NC; ++r)
+#pragma unroll
+                    for (int k = 0; k < NC; ++k) mb[r][k] = Mb[coef_at<V, KA>(p, r * NC + k, N)];
+            }
+#pragma unroll
+            for (int r = 0; r < NC; ++r) wv[r] = w0 ? w0[(long long)r * N + p] : (V)0;
+            V xin[NC], xh[NC];   // this point's x (2D) and the halo cell's, loaded before the barrier
+            if (DIM == 3) {
+                const long long o = plane * wrap(z + 2, n2) + qxy;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) qz[c][4] = x[(long long)c * N + o];
+            } else {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) xin[c] = x[(long long)c * N + p];
+            }
+            if (halo) {
+                const long long o = zo + wrap1(x0 + hx - kAH, n0) + (long long)n0 * wrap1(y0 + hy - kAH, n1);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) xh[c] = x[(long long)c * N + o];
+            }
+            __syncthreads();   // the previous plane's reads of Xs are done
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                Xs[c][ty + kAH][tx + kAH] = DIM == 3 ? qz[c][2] : xin[c];
+                if (halo) Xs[c][hy][hx] = xh[c];
+            }
+            __syncthreads();
+            V xp[NC];
+#pragma unroll
+            for (int k = 0; k < NC; ++k) xp[k] = Xs[k][ty + kAH][tx + kAH];
+#pragma unroll
+            for (int r = 0; r < NC; ++r) {
+                V acc = (V)0;
+#pragma unroll
+                for (int k = 0; k < NC; ++k) {
+                    V m;
+                    if constexpr (kPreMb) m = mb[r][k];
+                    else m = Mb[coef_at<V, KA>(p, r * NC + k, N)];
+                    acc = fma(m, xp[k], acc);
+                }
+                const int sy = ty + kAH, sx = tx + kAH;
+                // taps -2, -1, +1, +2 along x, y (and z from the registers)
+                acc = fma(cf[0][0], Xs[r][sy][sx - 2], acc);
+                acc = fma(cf[0][1], Xs[r][sy][sx - 1], acc);
+                acc = fma(cf[0][2], Xs[r][sy][sx + 1], acc);
+                acc = fma(cf[0][3], Xs[r][sy][sx + 2], acc);
+                acc = fma(cf[1][0], Xs[r][sy - 2][sx], acc);
+                acc = fma(cf[1][1], Xs[r][sy - 1][sx], acc);
+                acc = fma(cf[1][2], Xs[r][sy + 1][sx], acc);
+                acc = fma(cf[1][3], Xs[r][sy + 2][sx], acc);
+                if (DIM == 3) {
+                    acc = fma(cf[DIM - 1][0], qz[r][0], acc);
+                    acc = fma(cf[DIM - 1][1], qz[r][1], acc);
+                    acc = fma(cf[DIM - 1][2], qz[r][3], acc);
+                    acc = fma(cf[DIM - 1][3], qz[r][4], acc);
+                }
+                const long long q = (long long)r * N + p;
+                y[q] = acc;
+                if (w0) a0 = fma(wv[r], acc, a0);
+                if (w1) a1 = fma(w1y ? acc : w1[q], acc, a1);
+            }
+            if (DIM == 3) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) qz[c][k] = qz[c][k + 1];
+            }
+        }
+    }
+    if (w0) {
+        block_partials((double)a0, (double)a1, w1 ? 2 : 1, partials);
+        if (op >= 0 && last_block(ticket)) scalar_step(partials, gridDim.x, sc, op);
+    }
+}
+
+// Blocks of a grid-stride kernel resident at once on this device (one wave), at
+// most kImpBlocks: a partial second wave would stream its share of the vectors
+// with a fraction of the SMs.  The count depends only on the device and the
+// kernel, so the partial sums stay those of fixed blocks.
+template <typename Kern>
+unsigned resident_blocks(Kern kernel) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kThreads, 0) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return (unsigned)kImpBlocks;
+    }
+    const long long g = (long long)sms * per;
+    return (unsigned)(g < 1 ? 1 : (g > kImpBlocks ? kImpBlocks : g));
+}
+
+// Op x -> y (with the partial dot products; with op >= 0 the scalar step op in
+// the last block, ticket its counter): the tiled kernel where the grid tiles,
+// the per-point one elsewhere.  Both compute every entry in the same order, so
+// the result does not depend on which one runs.
+template <int DIM, typename V>
+unsigned apply_blocks(bool tiled) {
+    static const unsigned gt = resident_blocks(imp_apply_tiled_kernel<DIM, V>);
+    static const unsigned gp = resident_blocks(imp_apply_kernel<DIM, V>);
+    return tiled ? gt : gp;
+}
+
+template <typename T, int DIM, typename V>
+void launch_apply(const ImpArgs<T>& a, const V* Mb, const V* Cf, const V* x, V* y, const V* w0, const V* w1,
+                  double* partials, double* sc, int op, unsigned* ticket, cudaStream_t st) {
+    const ImpGrid G{a.N, a.n0, a.n1, a.n2};
+    const bool tiled = a.n0 % kAX == 0 && a.n1 % kAY == 0;
+    const unsigned g = apply_blocks<DIM, V>(tiled);
+    if (tiled)
+        imp_apply_tiled_kernel<DIM, V><<<g, kThreads, 0, st>>>(G, Mb, Cf, x, y, w0, w1, partials, sc, op, ticket);
+    else
+        imp_apply_kernel<DIM, V><<<g, kThreads, 0, st>>>(G, Mb, Cf, x, y, w0, w1, partials, sc, op, ticket);
+}
+
+// z = P^-1 v with v = a x + b y (+ c w): forms the combination, stores it in
+// `comb` (when given) and its preconditioned image in z
+// (every call passes distinct p, r, v, z)
+template <int NC, typename V>
+__global__ void __launch_bounds__(kThreads) imp_comb_precond_kernel(long long N, const V* __restrict__ Pinv, int mode,
+                                                                    V* __restrict__ p, const V* __restrict__ r,
+                                                                    const V* __restrict__ v, V* __restrict__ z,
+                                                                    const double* sc) {
+    if (done(sc)) return;
+    // mode 0: p = r + beta (p - omega v);  mode 1: p (as s) = r - alpha v
+    const V beta = (V)sc[S_BETA], omega = (V)sc[S_OMEGA], alpha = (V)sc[S_ALPHA];
+#pragma unroll 2
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        V w[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const long long q = (long long)c * N + i;
+            const V nv = mode == 0 ? fma(beta, p[q] - omega * v[q], r[q]) : fma(-alpha, v[q], r[q]);
+            p[q] = nv;
+            w[c] = nv;
+        }
+#pragma unroll
+        for (int rr = 0; rr < NC; ++rr) {
+            V acc = (V)0;
+#pragma unroll
+            for (int k = 0; k < NC; ++k) acc = fma(Pinv[coef_at<V, NC * NC>(i, rr * NC + k, N)], w[k], acc);
+            z[(long long)rr * N + i] = acc;
+        }
+    }
+}
+
+// x += alpha ph + omega sh;  r = s - omega t;  partial sums of (r, r) and (rh, r),
+// then scalar step 0 in the block that finishes last
+// (every call passes seven distinct vectors)
+template <typename V>
+__global__ void __launch_bounds__(kThreads) imp_xr_kernel(long long n, V* __restrict__ x, const V* __restrict__ ph,
+                                                          const V* __restrict__ sh, V* __restrict__ r,
+                                                          const V* __restrict__ s, const V* __restrict__ t,
+                                                          const V* __restrict__ rh, double* partials, double* sc,
+                                                          unsigned* ticket) {
+    if (done(sc)) return;
+    const V alpha = (V)sc[S_ALPHA], omega = (V)sc[S_OMEGA];
+    V a0 = (V)0, a1 = (V)0;
+    // kB elements per thread and pass, all their loads issued before the first
+    // store (kB runs of kThreads, each coalesced, at constant offsets)
+    constexpr int kB = 4;
+    const long long stride = (long long)gridDim.x * kThreads * kB;
+    for (long long i0 = (long long)blockIdx.x * kThreads * kB + threadIdx.x; i0 < n; i0 += stride) {
+        const long long lim = n - i0;
+        V xv[kB], pv[kB], hv[kB], sv[kB], tv[kB], qv[kB];
+#pragma unroll
+        for (int k = 0; k < kB; ++k) {
+            const long long i = i0 + k * kThreads;
+            if (k * kThreads < lim) {
+                xv[k] = x[i]; pv[k] = ph[i]; hv[k] = sh[i]; sv[k] = s[i]; tv[k] = t[i]; qv[k] = rh[i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kB; ++k) {
+            const long long i = i0 + k * kThreads;
+            if (k * kThreads < lim) {
+                x[i] = fma(alpha, pv[k], fma(omega, hv[k], xv[k]));
+                const V rv = fma(-omega, tv[k], sv[k]);
+                r[i] = rv;
+                a0 = fma(rv, rv, a0);
+                a1 = fma(qv[k], rv, a1);
+            }
+        }
+    }
+    block_partials((double)a0, (double)a1, 2, partials);
+    if (last_block(ticket)) scalar_step(partials, gridDim.x, sc, 0);
+}
+
+// per-block partial sums of x.y and x.z (z may be null), for the start of the iteration
+template <typename V>
+__global__ void __launch_bounds__(kThreads) imp_dot2_kernel(const V* x, const V* y, const V* z, long long n,
+                                                            double* partials) {
+    V a0 = (V)0, a1 = (V)0;
+#pragma unroll 4
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        a0 = fma(x[i], y[i], a0);
+        if (z) a1 = fma(x[i], z[i], a1);
+    }
+    block_partials((double)a0, (double)a1, z ? 2 : 1, partials);
+}
+
+// The scalar step alone, after a kernel that leaves its kImpBlocks partial sums
+__global__ void __launch_bounds__(kThreads) imp_scalar_kernel(const double* partials, double* sc, int op) {
+    scalar_step(partials, kImpBlocks, sc, op);
+}
+
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads) imp_push_kernel(const ImpArgs<T> A, const double* x) {
     constexpr int NC = Packed<DIM>::NC;
@@ -548,6 +713,7 @@ __global__ void __launch_bounds__(kThreads) imp_push_kernel(const ImpArgs<T> A, 
 template <typename V>
 __global__ void __launch_bounds__(kThreads) imp_init_kernel(long long n, const V* b, V* r, V* rh, V* p, V* v,
                                                             V* x, int zero) {
+#pragma unroll 4
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const V rv = zero ? b[i] : b[i] - r[i];
         r[i] = rv;
@@ -578,10 +744,22 @@ __global__ void __launch_bounds__(kThreads) imp_correct_kernel(long long n, doub
         x[i] += (double)d[i];
 }
 
-// float copies of the step's operator blocks, preconditioner and tap coefficients
-__global__ void __launch_bounds__(kThreads) imp_to_float_kernel(long long n, const double* src, float* dst) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        dst[i] = (float)src[i];
+// float tile-major copies of the step's operator (the point blocks and the tap
+// coefficients, nc^2 + 4 d per point, in Af) and of the block-Jacobi inverses
+// (nc^2 per point, in Pf), from the FP64 [k][N] arrays
+template <int NC, int DIM>
+__global__ void __launch_bounds__(kThreads) imp_float_operator_kernel(long long N, const double* Mb, const double* Cf,
+                                                                      const double* Pinv, float* Af, float* Pf) {
+    constexpr int KA = NC * NC + 4 * DIM, KP = NC * NC;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            Af[mode_index(p, k, KA)] = (float)Mb[(long long)k * N + p];
+            Pf[mode_index(p, k, KP)] = (float)Pinv[(long long)k * N + p];
+        }
+#pragma unroll
+        for (int k = 0; k < 4 * DIM; ++k) Af[mode_index(p, KP + k, KA)] = (float)Cf[(long long)k * N + p];
+    }
 }
 
 // ------------------------------------------------------------------ the paper's variable
@@ -1251,8 +1429,9 @@ __global__ void __launch_bounds__(kThreads) stp_final_kernel(const ImpArgs<T> A,
 template <int NC>
 struct KryView {
     double *b, *x, *r, *rh, *p, *v, *sv, *t, *ph, *sh, *Mb, *Pinv, *Cf, *H, *partials, *sc;
-    float *Mbf, *Pinvf, *Cff;                           // float copies of Mb, Pinv, Cf
+    float *Af, *Pf;   // float tile-major copies: blocks and taps (nc^2 + 4 d per point), inverses (nc^2)
     float *xf, *rf, *rhf, *pf, *vf, *svf, *tf, *phf, *shf;   // inner-solve vectors
+    unsigned* ticket;
     KryView(double* w, double* parts, long long N) {
         constexpr int D = NC == 3 ? 2 : 3;
         const long long n = (long long)NC * N;
@@ -1261,14 +1440,19 @@ struct KryView {
         Mb = w + 10 * n;
         Pinv = Mb + (long long)NC * NC * N;
         Cf = Pinv + (long long)NC * NC * N;                  // 4 taps x dim axes
-        float* f = reinterpret_cast<float*>(Cf + 4LL * D * N);
-        Mbf = f; Pinvf = Mbf + (long long)NC * NC * N; Cff = Pinvf + (long long)NC * NC * N;
-        float* fv = Cff + 4LL * D * N;
+        // the float section starts on a 128-byte boundary (its tile rows are 128 bytes)
+        double* fd = Cf + 4LL * D * N;
+        fd += (16 - (long long)((reinterpret_cast<uintptr_t>(fd) / sizeof(double)) % 16)) % 16;
+        const long long Np = mode_points(N);
+        Af = reinterpret_cast<float*>(fd);
+        Pf = Af + (long long)(NC * NC + 4 * D) * Np;
+        float* fv = Pf + (long long)NC * NC * Np;
         xf = fv; rf = fv + n; rhf = fv + 2 * n; pf = fv + 3 * n; vf = fv + 4 * n; svf = fv + 5 * n;
         tf = fv + 6 * n; phf = fv + 7 * n; shf = fv + 8 * n;
         H = Cf + 4LL * D * N + kry_float_doubles(NC, D, N);   // the paper's variable only
         partials = parts;
         sc = parts + kPartialSets * kImpBlocks;
+        ticket = reinterpret_cast<unsigned*>(sc + 31);   // last-block counter (the outer scalars: sc + 16)
     }
 };
 
@@ -1286,12 +1470,15 @@ struct BiVecs {
 };
 
 template <typename T, int DIM, typename V>
-cudaError_t bicgstab(const ImpArgs<T>& a, const BiVecs<V>& K, double* partials, double* sc, double tol, int maxit,
-                     bool x_zero, cudaStream_t st, int* iters, double* rr_out, double* bnorm2_out) {
+cudaError_t bicgstab(const ImpArgs<T>& a, const BiVecs<V>& K, double* partials, double* sc, unsigned* ticket,
+                     double tol, int maxit, bool x_zero, cudaStream_t st, int* iters, double* rr_out,
+                     double* bnorm2_out) {
     constexpr int NC = Packed<DIM>::NC;
     const long long N = a.N;
     const long long n = (long long)NC * N;
     const unsigned bs = (unsigned)kImpBlocks;
+    static const unsigned g_comb = resident_blocks(imp_comb_precond_kernel<NC, V>);
+    static const unsigned g_xr = resident_blocks(imp_xr_kernel<V>);
     cudaError_t e = cudaSuccess;
     auto ok = [&]() {
         if (e == cudaSuccess) e = cudaGetLastError();
@@ -1301,6 +1488,7 @@ cudaError_t bicgstab(const ImpArgs<T>& a, const BiVecs<V>& K, double* partials, 
     hs[S_RHO] = hs[S_ALPHA] = hs[S_OMEGA] = 1.0;
     hs[S_TOL2] = tol * tol;
     e = cudaMemcpyAsync(sc, hs, sizeof(hs), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     imp_dot2_kernel<V><<<bs, kThreads, 0, st>>>(K.b, K.b, nullptr, n, partials);
     if (!ok()) return e;
@@ -1318,7 +1506,7 @@ cudaError_t bicgstab(const ImpArgs<T>& a, const BiVecs<V>& K, double* partials, 
         return e;
     }
     if (!x_zero) {
-        launch_apply<T, DIM, V>(a, K.Mb, K.Cf, K.x, K.r, nullptr, nullptr, partials, sc, st);
+        launch_apply<T, DIM, V>(a, K.Mb, K.Cf, K.x, K.r, nullptr, nullptr, partials, sc, -1, ticket, st);
         if (!ok()) return e;
     }
     imp_init_kernel<V><<<bs, kThreads, 0, st>>>(n, K.b, K.r, K.rh, K.p, K.v, K.x, x_zero ? 1 : 0);
@@ -1327,23 +1515,67 @@ cudaError_t bicgstab(const ImpArgs<T>& a, const BiVecs<V>& K, double* partials, 
     if (!ok()) return e;
     imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 4);
     if (!ok()) return e;
+    // one iteration, five launches: the scalar steps run in the last block of the
+    // kernel that leaves their partial sums
+    auto iteration = [&](cudaStream_t s) {
+        imp_comb_precond_kernel<NC, V><<<g_comb, kThreads, 0, s>>>(N, K.Pinv, 0, K.p, K.r, K.v, K.ph, sc);
+        launch_apply<T, DIM, V>(a, K.Mb, K.Cf, K.ph, K.v, K.rh, nullptr, partials, sc, 1, ticket, s);
+        imp_comb_precond_kernel<NC, V><<<g_comb, kThreads, 0, s>>>(N, K.Pinv, 1, K.sv, K.r, K.v, K.sh, sc);
+        launch_apply<T, DIM, V>(a, K.Mb, K.Cf, K.sh, K.t, K.sv, K.t, partials, sc, 2, ticket, s);
+        imp_xr_kernel<V><<<g_xr, kThreads, 0, s>>>(n, K.x, K.ph, K.sh, K.r, K.sv, K.t, K.rh, partials, sc, ticket);
+    };
+    // The kCheck iterations between two looks at the scalars run as one CUDA
+    // graph, captured once per device, grid and workspace and kept (per host
+    // thread): the kernels take nothing else, and a finished iteration makes the
+    // remaining launches return at once.
     constexpr int kCheck = 8;
-    for (int it = 0; it < maxit; ++it) {
-        imp_comb_precond_kernel<NC, V><<<bs, kThreads, 0, st>>>(N, K.Pinv, 0, K.p, K.r, K.v, K.ph, sc);
-        launch_apply<T, DIM, V>(a, K.Mb, K.Cf, K.ph, K.v, K.rh, nullptr, partials, sc, st);
-        imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 1);
-        imp_comb_precond_kernel<NC, V><<<bs, kThreads, 0, st>>>(N, K.Pinv, 1, K.sv, K.r, K.v, K.sh, sc);
-        launch_apply<T, DIM, V>(a, K.Mb, K.Cf, K.sh, K.t, K.sv, K.t, partials, sc, st);
-        imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 2);
-        imp_xr_kernel<V><<<bs, kThreads, 0, st>>>(n, K.x, K.ph, K.sh, K.r, K.sv, K.t, K.rh, partials, sc);
-        imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sc, 0);
-        if (!ok()) return e;
-        if ((it + 1) % kCheck == 0 || it + 1 == maxit) {
-            e = cudaMemcpyAsync(hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    using Key = std::array<long long, 24>;
+    static thread_local Key key{};
+    static thread_local cudaGraphExec_t exec = nullptr;
+    if (maxit >= kCheck) {
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        const Key k{dev, N, a.n0, a.n1, a.n2, (long long)g_comb, (long long)g_xr,
+                    (long long)K.x, (long long)K.r, (long long)K.rh, (long long)K.p, (long long)K.v,
+                    (long long)K.sv, (long long)K.t, (long long)K.ph, (long long)K.sh, (long long)K.Mb,
+                    (long long)K.Pinv, (long long)K.Cf, (long long)partials, (long long)sc, (long long)ticket,
+                    0, 0};
+        if (!exec || k != key) {
+            if (exec) (void)cudaGraphExecDestroy(exec);
+            exec = nullptr;
+            (void)apply_blocks<DIM, V>(true);   // the occupancy queries before the capture
+            cudaStream_t cs = nullptr;
+            e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
             if (e != cudaSuccess) return e;
-            if (hs[S_DONE] != 0.0) break;
+            cudaGraph_t gr = nullptr;
+            e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                for (int i = 0; i < kCheck; ++i) iteration(cs);
+                e = cudaStreamEndCapture(cs, &gr);
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, gr, 0);
+            if (gr) (void)cudaGraphDestroy(gr);
+            (void)cudaStreamDestroy(cs);
+            if (e != cudaSuccess) {
+                exec = nullptr;
+                (void)cudaGetLastError();
+                return e;
+            }
+            key = k;
         }
+    }
+    for (int it = 0; it < maxit; it += kCheck) {
+        if (it + kCheck <= maxit) {
+            e = cudaGraphLaunch(exec, st);
+        } else {
+            for (int i = it; i < maxit; ++i) iteration(st);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        if (hs[S_DONE] != 0.0) break;
     }
     e = cudaMemcpyAsync(hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1383,8 +1615,7 @@ cudaError_t krylov_solve(const ImpArgs<T>& a, const KryView<Packed<DIM>::NC>& K,
     // float copies of the operator (the blocks and their inverses are
     // contiguous; the taps may be the transposed ones of an adjoint solve,
     // kept elsewhere)
-    imp_to_float_kernel<<<bs, kThreads, 0, st>>>(2LL * NC * NC * N, K.Mb, K.Mbf);
-    imp_to_float_kernel<<<bs, kThreads, 0, st>>>(4LL * DIM * N, K.Cf, K.Cff);
+    imp_float_operator_kernel<NC, DIM><<<bs, kThreads, 0, st>>>(N, K.Mb, K.Cf, K.Pinv, K.Af, K.Pf);
     if (!ok()) return e;
     // device scalars of the outer FP64 residual (never "done": the FP64 operator
     // kernel skips its work once the scalars it is given say so)
@@ -1396,7 +1627,8 @@ cudaError_t krylov_solve(const ImpArgs<T>& a, const KryView<Packed<DIM>::NC>& K,
     }
     // inner solve: right-hand side rf (overwritten by the residual: b is read
     // only before the init kernel sets r = b), correction xf
-    const BiVecs<float> Fv{K.rf, K.xf, K.rf, K.rhf, K.pf, K.vf, K.svf, K.tf, K.phf, K.shf, K.Mbf, K.Pinvf, K.Cff};
+    const BiVecs<float> Fv{K.rf,  K.xf,  K.rf,  K.rhf, K.pf,  K.vf, K.svf,
+                           K.tf,  K.phf, K.shf, K.Af,  K.Pf,  K.Af + 32LL * NC * NC};   // taps: nc^2 tile rows on
     double hs[S_COUNT] = {};
     double bnorm2 = 0.0, rr = 0.0;
     int total = 0;
@@ -1427,7 +1659,7 @@ cudaError_t krylov_solve(const ImpArgs<T>& a, const KryView<Packed<DIM>::NC>& K,
     constexpr int kOuterMax = 12;
     for (int outer = 0; outer < kOuterMax; ++outer) {
         // r = b - Op x in FP64, its float copy, (r, r)
-        launch_apply<T, DIM, double>(a, K.Mb, K.Cf, K.x, K.r, nullptr, nullptr, partials, sco, st);
+        launch_apply<T, DIM, double>(a, K.Mb, K.Cf, K.x, K.r, nullptr, nullptr, partials, sco, -1, K.ticket, st);
         imp_resid_kernel<<<bs, kThreads, 0, st>>>(n, K.b, K.r, K.rf, partials);
         imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sco, 3);
         if (!ok()) return e;
@@ -1447,7 +1679,7 @@ cudaError_t krylov_solve(const ImpArgs<T>& a, const KryView<Packed<DIM>::NC>& K,
         if (inner_tol < kInnerFloor) inner_tol = kInnerFloor;
         int it = 0;
         double irr = 0.0, ib2 = 0.0;
-        e = bicgstab<T, DIM, float>(a, Fv, partials, sc, inner_tol, a.maxit, true, st, &it, &irr, &ib2);
+        e = bicgstab<T, DIM, float>(a, Fv, partials, sc, K.ticket, inner_tol, a.maxit, true, st, &it, &irr, &ib2);
         if (e != cudaSuccess) return e;
         total += it;
         imp_correct_kernel<<<bs, kThreads, 0, st>>>(n, K.x, K.xf);
@@ -1458,7 +1690,7 @@ cudaError_t krylov_solve(const ImpArgs<T>& a, const KryView<Packed<DIM>::NC>& K,
         const BiVecs<double> D{K.b, K.x, K.r, K.rh, K.p, K.v, K.sv, K.t, K.ph, K.sh, K.Mb, K.Pinv, K.Cf};
         int it = 0;
         double b2 = 0.0;
-        e = bicgstab<T, DIM, double>(a, D, partials, sc, a.tol, a.maxit, false, st, &it, &rr, &b2);
+        e = bicgstab<T, DIM, double>(a, D, partials, sc, K.ticket, a.tol, a.maxit, false, st, &it, &rr, &b2);
         if (e != cudaSuccess) return e;
         total += it;
         converged = rr <= tol2;

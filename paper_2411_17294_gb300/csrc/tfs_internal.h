@@ -152,11 +152,12 @@ struct ImpArgs {
 constexpr int kImpBlocks = 1024;   // blocks of the implicit-step kernels (and reduction partials)
 
 // FP32 section of the implicit-transport workspace (the inner solve of the
-// mixed-precision Krylov scheme): float copies of the point blocks and their
-// inverses (2 nc^2 N), of the tap coefficients (4 d N) and nine Krylov vectors
-// (9 nc N), counted in doubles (rounded up).
+// mixed-precision Krylov scheme): tile-major float copies of the point blocks,
+// the tap coefficients and the block inverses ((2 nc^2 + 4 d) per point over the
+// points padded to whole 32-point tiles) and nine Krylov vectors (9 nc N),
+// counted in doubles (rounded up), plus 16 for the section's 128-byte alignment.
 __host__ __device__ __forceinline__ long long kry_float_doubles(int nc, int dim, long long N) {
-    return ((2LL * nc * nc + 4LL * dim + 9LL * nc) * N + 1) / 2;
+    return ((2LL * nc * nc + 4LL * dim) * mode_points(N) + 9LL * nc * N + 1) / 2 + 16;
 }
 
 // host driver of one implicit step (BiCGStab, block-Jacobi preconditioned);
