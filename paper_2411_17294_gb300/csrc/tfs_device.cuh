@@ -44,11 +44,11 @@ template <> struct Packed<3> {
 // r-th packed component of kappa E_k + E_k kappa^T where E_k is the symmetric
 // unit matrix of packed component k.  All index tests fold at compile time
 // once the loops over r and k are unrolled.
-template <int DIM>
-__device__ __forceinline__ double uc_entry(const double K[3][3], int r, int k) {
+template <int DIM, typename R>
+__device__ __forceinline__ R uc_entry(const R K[3][3], int r, int k) {
     const int ro = Packed<DIM>::I(r), so = Packed<DIM>::J(r);
     const int i = Packed<DIM>::I(k), j = Packed<DIM>::J(k);
-    double v = 0.0;
+    R v = R(0);
     // (kappa E)_{ro,so} = sum_l K[ro][l] E[l][so];  (E kappa^T)_{ro,so} = sum_l E[ro][l] K[so][l]
     // E[l][s] = 1 for (l,s) in {(i,j), (j,i)}
     if (so == j) v += K[ro][i];

@@ -308,6 +308,7 @@ __device__ void scalar_step(const double* partials, int nparts, double* sc, int 
 struct ImpGrid {
     long long N;
     int n0, n1, n2;
+    unsigned* flags;   // TFS_FLAG_TIMEOUT of a copy wait that gave up
 };
 
 // Index of coefficient k of point p: FP64 coefficients (the step's system) are
@@ -544,16 +545,219 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 && sizeof(V) == 4 ? 6 : 1)
     }
 }
 
+// The float operator on 2D grids with n0 % 32 == 0 and n1 % 8 == 0 (16-byte
+// aligned vectors), software-pipelined: a unit is one 32 x 8 tile, staged into
+// one of two shared-memory stages while the previous unit is applied from the
+// other.  The tile's coefficient rows (tile-major: 8 contiguous rows of
+// nc^2 + 8 coefficients x 32 points, 2176 bytes each) arrive by bulk copies
+// (cp.async.bulk, one per row from lanes of warp 0, completing on the stage's
+// mbarrier); its x rows with a margin of 4 cells in x and 2 in y (whole 16-byte
+// chunks, wrapped periodically) and its w0 rows by 16-byte cp.async copies of
+// every thread.  Every entry of y is formed in the order of
+// imp_apply_tiled_kernel, so the two give the same y.  A wait that gives up
+// latches TFS_FLAG_TIMEOUT, lets the copies in flight land (bounded) and ends
+// the block's units; the block still adds its partial sums, so the last-block
+// count stays whole.
+constexpr int kPX = kAX + 8;   // staged x row: x0 - 4 .. x0 + 35
+constexpr int kPipeFull = 9 + 8;   // 2D: nc^2 block entries and 4 taps x 2 axes per point
+constexpr int kPipeCompact = 6;    // 2D: the extrapolated velocity gradient (4) and the velocity (2)
+template <int KC>
+struct PipeStage {
+    float X[3][kASY][kPX];
+    float C[kAY][KC][kAX];
+    float W[3][kAY][kAX];
+};
+template <int KC>
+constexpr size_t pipe_smem() { return 2 * sizeof(PipeStage<KC>); }
+
+// Scalars of the compact float operator: the step's a and dt, and per axis
+// eps/h^2, 1/(6h) and 1/(2h), with the stencil (imp_setup_kernel's formulas).
+struct CompactConsts {
+    float dt, a;
+    float e[2], ih6[2], ih2[2];
+    int stencil;
+};
+
+// The float operator on 2D grids with n0 % 32 == 0 and n1 % 8 == 0 (16-byte
+// aligned vectors), software-pipelined: a unit is one 32 x 8 tile, staged into
+// one of two shared-memory stages while the previous unit is applied from the
+// other.  The tile's coefficient rows (tile-major: 8 contiguous rows of KC
+// values x 32 points) arrive by bulk copies (cp.async.bulk, one per row from
+// lanes of warp 0, completing on the stage's mbarrier); its x rows with a
+// margin of 4 cells in x and 2 in y (whole 16-byte chunks, wrapped periodically)
+// and its w0 rows by 16-byte cp.async copies of every thread.
+//   KC = kPipeFull: the coefficients are the rounded blocks and taps of
+//     imp_setup_kernel, and every entry of y is formed in the order of
+//     imp_apply_tiled_kernel (the two give the same y);
+//   KC = kPipeCompact: per point the extrapolated velocity gradient and the
+//     velocity, from which the block and the taps are formed in float with
+//     imp_setup_kernel's formulas (the step's operator to float rounding, from
+//     35% of the bytes).
+// A wait that gives up latches TFS_FLAG_TIMEOUT, lets the copies in flight land
+// (bounded) and ends the block's units; the block still adds its partial sums,
+// so the last-block count stays whole.
+template <int KC>
+__global__ void __launch_bounds__(kThreads) imp_apply_pipe2d_kernel(const ImpGrid A, const CompactConsts Q,
+                                                                    const float* __restrict__ Af,
+                                                                    const float* __restrict__ x, float* y,
+                                                                    const float* w0, const float* w1,
+                                                                    double* partials, double* sc, int op,
+                                                                    unsigned* ticket) {
+    constexpr int NC = 3;
+    using Stage = PipeStage<KC>;
+    extern __shared__ __align__(128) unsigned char pipe_smem_buf[];
+    __shared__ __align__(8) uint64_t bars[2];
+    Stage* stage = reinterpret_cast<Stage*>(pipe_smem_buf);
+    if (done(sc)) return;
+    const bool w1y = w1 == y;
+    const long long N = A.N;
+    const int n0 = A.n0, n1 = A.n1;
+    const int tid = threadIdx.x, tx = tid % kAX, ty = tid / kAX;
+    const int tiles_x = n0 / kAX, units = tiles_x * (n1 / kAY);
+    auto wrap1 = [](int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); };   // -n <= v < 2n
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // stage unit `unit` into stage sidx (its earlier reads are done: a block barrier precedes)
+    auto issue = [&](int unit, int sidx) {
+        Stage& S = stage[sidx];
+        const int x0 = (unit % tiles_x) * kAX, y0 = (unit / tiles_x) * kAY;
+        if (tid < 32) {
+            // coefficients: the tile's 8 row segments, KC x 32 floats each, contiguous
+            fence_proxy_async_smem();
+            if (tid == 0) mbar_arrive_expect_tx(&bars[sidx], (unsigned)sizeof(S.C));
+            __syncwarp();
+            if (tid < kAY) {
+                const long long p0 = (long long)(y0 + tid) * n0 + x0;
+                bulk_load(&S.C[tid][0][0], Af + (p0 >> 5) * (KC * kAX), KC * kAX * sizeof(float), &bars[sidx]);
+            }
+        }
+        // x: nc x 12 rows x 10 chunks (chunk 0: x0-4 .. x0-1, chunk 9: x0+32 .. x0+35, wrapped)
+        constexpr int kXc = kPX / 4, kXrow = kASY * kXc;
+        for (int i = tid; i < NC * kXrow; i += kThreads) {
+            const int c = i / kXrow, rem = i - c * kXrow, row = rem / kXc, ch = rem - row * kXc;
+            const int gy = wrap1(y0 + row - kAH, n1);
+            const int gx = ch == 0 ? wrap1(x0 - 4, n0) : (ch == kXc - 1 ? wrap1(x0 + kAX, n0) : x0 + 4 * (ch - 1));
+            cp_async16(&S.X[c][row][4 * ch], x + (long long)c * N + (long long)gy * n0 + gx, 16);
+        }
+        if (w0) {
+            constexpr int kWc = kAX / 4, kWrow = kAY * kWc;
+            for (int i = tid; i < NC * kWrow; i += kThreads) {
+                const int c = i / kWrow, rem = i - c * kWrow, row = rem / kWc, ch = rem - row * kWc;
+                cp_async16(&S.W[c][row][4 * ch], w0 + (long long)c * N + (long long)(y0 + row) * n0 + x0 + 4 * ch, 16);
+            }
+        }
+        cp_async_commit();
+    };
+    float a0 = 0.f, a1 = 0.f;
+    int unit = blockIdx.x;
+    if (unit < units) issue(unit, 0);
+    for (int it = 0; unit < units; ++it, unit += gridDim.x) {
+        const int sidx = it & 1;
+        const int next = unit + gridDim.x;
+        if (next < units) {
+            issue(next, sidx ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        const unsigned parity = (unsigned)(it >> 1) & 1u;
+        const bool ok = mbar_wait(&bars[sidx], parity);
+        if (__syncthreads_or(!ok)) {   // (also: this unit's stage is complete for every thread)
+            if (tid == 0) atomicOr(A.flags, 8u);
+            mbar_wait(&bars[sidx], parity);
+            if (next < units) mbar_wait(&bars[sidx ^ 1], (unsigned)((it + 1) >> 1) & 1u);
+            cp_async_wait<0>();
+            break;
+        }
+        const Stage& S = stage[sidx];
+        const int x0 = (unit % tiles_x) * kAX, y0 = (unit / tiles_x) * kAY;
+        const long long p = (long long)(y0 + ty) * n0 + x0 + tx;
+        const int sy = ty + kAH, sx = tx + 4;
+        // the point's block M and taps cf[axis][-2, -1, +1, +2]
+        float M[NC][NC], cf[2][4];
+        if constexpr (KC == kPipeFull) {
+#pragma unroll
+            for (int r = 0; r < NC; ++r)
+#pragma unroll
+                for (int k = 0; k < NC; ++k) M[r][k] = S.C[ty][r * NC + k][tx];
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) cf[a][t] = S.C[ty][NC * NC + 4 * a + t][tx];
+        } else {
+            const float K[3][3] = {{S.C[ty][0][tx], S.C[ty][1][tx], 0.f}, {S.C[ty][2][tx], S.C[ty][3][tx], 0.f},
+                                   {0.f, 0.f, 0.f}};
+            float diag = 0.f;
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const float ua = S.C[ty][4 + a][tx], e = Q.e[a];
+                if (Q.stencil == 0) diag += fabsf(ua) * Q.ih2[a];
+                diag += 2.f * e;
+                float c[4];
+                if (Q.stencil == 1) {
+                    const float h2 = ua * Q.ih2[a];
+                    c[0] = 0.f; c[1] = -h2 - e; c[2] = h2 - e; c[3] = 0.f;
+                } else if (ua >= 0.f) {
+                    const float s6 = ua * Q.ih6[a];
+                    c[0] = s6; c[1] = -6.f * s6 - e; c[2] = 2.f * s6 - e; c[3] = 0.f;
+                } else {
+                    const float s6 = ua * Q.ih6[a];
+                    c[0] = 0.f; c[1] = -2.f * s6 - e; c[2] = 6.f * s6 - e; c[3] = -s6;
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t) cf[a][t] = Q.dt * c[t];
+            }
+#pragma unroll
+            for (int r = 0; r < NC; ++r)
+#pragma unroll
+                for (int k = 0; k < NC; ++k) {
+                    const float l = uc_entry<2>(K, r, k);
+                    M[r][k] = r == k ? fmaf(-Q.dt, l, Q.a) + Q.dt * diag : -Q.dt * l;
+                }
+        }
+        float xp[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) xp[k] = S.X[k][sy][sx];
+#pragma unroll
+        for (int r = 0; r < NC; ++r) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < NC; ++k) acc = fmaf(M[r][k], xp[k], acc);
+            acc = fmaf(cf[0][0], S.X[r][sy][sx - 2], acc);
+            acc = fmaf(cf[0][1], S.X[r][sy][sx - 1], acc);
+            acc = fmaf(cf[0][2], S.X[r][sy][sx + 1], acc);
+            acc = fmaf(cf[0][3], S.X[r][sy][sx + 2], acc);
+            acc = fmaf(cf[1][0], S.X[r][sy - 2][sx], acc);
+            acc = fmaf(cf[1][1], S.X[r][sy - 1][sx], acc);
+            acc = fmaf(cf[1][2], S.X[r][sy + 1][sx], acc);
+            acc = fmaf(cf[1][3], S.X[r][sy + 2][sx], acc);
+            const long long q = (long long)r * N + p;
+            y[q] = acc;
+            if (w0) a0 = fmaf(S.W[r][ty][tx], acc, a0);
+            if (w1) a1 = fmaf(w1y ? acc : w1[q], acc, a1);
+        }
+        __syncthreads();   // every read of this stage is done before it is refilled
+    }
+    if (w0) {
+        block_partials((double)a0, (double)a1, w1 ? 2 : 1, partials);
+        if (op >= 0 && last_block(ticket)) scalar_step(partials, gridDim.x, sc, op);
+    }
+}
+
 // Blocks of a grid-stride kernel resident at once on this device (one wave), at
 // most kImpBlocks: a partial second wave would stream its share of the vectors
 // with a fraction of the SMs.  The count depends only on the device and the
 // kernel, so the partial sums stay those of fixed blocks.
 template <typename Kern>
-unsigned resident_blocks(Kern kernel) {
+unsigned resident_blocks(Kern kernel, size_t dyn = 0) {
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kThreads, 0) != cudaSuccess) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kThreads, dyn) != cudaSuccess) {
         (void)cudaGetLastError();
         return (unsigned)kImpBlocks;
     }
@@ -572,11 +776,48 @@ unsigned apply_blocks(bool tiled) {
     return tiled ? gt : gp;
 }
 
+// blocks of the pipelined 2D kernel (its dynamic shared-memory limit raised
+// once, before the occupancy query; 0 if that fails)
+template <int KC>
+unsigned pipe_blocks() {
+    static const unsigned g = []() {
+        if (cudaFuncSetAttribute(imp_apply_pipe2d_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pipe_smem<KC>()) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return 0u;
+        }
+        return resident_blocks(imp_apply_pipe2d_kernel<KC>, pipe_smem<KC>());
+    }();
+    return g;
+}
+
+// whether the pipelined kernel serves this 2D float operator (whole tiles,
+// 16-byte aligned vectors)
+template <typename T>
+bool pipe_fits(const ImpArgs<T>& a, const void* x, const void* w0, const void* coef) {
+    auto al16 = [](const void* q) { return q == nullptr || reinterpret_cast<uintptr_t>(q) % 16 == 0; };
+    return a.n0 % kAX == 0 && a.n1 % kAY == 0 && al16(x) && al16(w0) && al16(coef);
+}
+
+// cc: the compact float operator (Mb then holds its per-point values), which
+// only the pipelined 2D kernel applies
 template <typename T, int DIM, typename V>
 void launch_apply(const ImpArgs<T>& a, const V* Mb, const V* Cf, const V* x, V* y, const V* w0, const V* w1,
-                  double* partials, double* sc, int op, unsigned* ticket, cudaStream_t st) {
-    const ImpGrid G{a.N, a.n0, a.n1, a.n2};
+                  double* partials, double* sc, int op, unsigned* ticket, const CompactConsts* cc, cudaStream_t st) {
+    const ImpGrid G{a.N, a.n0, a.n1, a.n2, a.flags};
     const bool tiled = a.n0 % kAX == 0 && a.n1 % kAY == 0;
+    if constexpr (DIM == 2 && std::is_same<V, float>::value) {
+        if (cc) {
+            imp_apply_pipe2d_kernel<kPipeCompact><<<pipe_blocks<kPipeCompact>(), kThreads, pipe_smem<kPipeCompact>(),
+                                                    st>>>(G, *cc, Mb, x, y, w0, w1, partials, sc, op, ticket);
+            return;
+        }
+        if (pipe_fits(a, x, w0, Mb) && Cf == Mb + 32 * 9 && pipe_blocks<kPipeFull>() > 0) {
+            imp_apply_pipe2d_kernel<kPipeFull><<<pipe_blocks<kPipeFull>(), kThreads, pipe_smem<kPipeFull>(), st>>>(
+                G, CompactConsts{}, Mb, x, y, w0, w1, partials, sc, op, ticket);
+            return;
+        }
+    }
     const unsigned g = apply_blocks<DIM, V>(tiled);
     if (tiled)
         imp_apply_tiled_kernel<DIM, V><<<g, kThreads, 0, st>>>(G, Mb, Cf, x, y, w0, w1, partials, sc, op, ticket);
@@ -652,6 +893,39 @@ __global__ void __launch_bounds__(kThreads) imp_xr_kernel(long long n, V* __rest
                 a1 = fma(qv[k], rv, a1);
             }
         }
+    }
+    block_partials((double)a0, (double)a1, 2, partials);
+    if (last_block(ticket)) scalar_step(partials, gridDim.x, sc, 0);
+}
+
+// The same update on float vectors of 16-byte aligned storage with n % 4 == 0,
+// four elements per thread and pass in 16-byte loads and stores
+__global__ void __launch_bounds__(kThreads) imp_xr4_kernel(long long n, float4* __restrict__ x,
+                                                           const float4* __restrict__ ph,
+                                                           const float4* __restrict__ sh, float4* __restrict__ r,
+                                                           const float4* __restrict__ s,
+                                                           const float4* __restrict__ t,
+                                                           const float4* __restrict__ rh, double* partials,
+                                                           double* sc, unsigned* ticket) {
+    if (done(sc)) return;
+    const float alpha = (float)sc[S_ALPHA], omega = (float)sc[S_OMEGA];
+    float a0 = 0.f, a1 = 0.f;
+    const long long n4 = n / 4;
+    for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n4; i += (long long)gridDim.x * kThreads) {
+        const float4 xv = x[i], pv = ph[i], hv = sh[i], sv = s[i], tv = t[i], qv = rh[i];
+        float4 xo, ro;
+        xo.x = fmaf(alpha, pv.x, fmaf(omega, hv.x, xv.x));
+        xo.y = fmaf(alpha, pv.y, fmaf(omega, hv.y, xv.y));
+        xo.z = fmaf(alpha, pv.z, fmaf(omega, hv.z, xv.z));
+        xo.w = fmaf(alpha, pv.w, fmaf(omega, hv.w, xv.w));
+        ro.x = fmaf(-omega, tv.x, sv.x);
+        ro.y = fmaf(-omega, tv.y, sv.y);
+        ro.z = fmaf(-omega, tv.z, sv.z);
+        ro.w = fmaf(-omega, tv.w, sv.w);
+        x[i] = xo;
+        r[i] = ro;
+        a0 = fmaf(ro.x, ro.x, a0); a0 = fmaf(ro.y, ro.y, a0); a0 = fmaf(ro.z, ro.z, a0); a0 = fmaf(ro.w, ro.w, a0);
+        a1 = fmaf(qv.x, ro.x, a1); a1 = fmaf(qv.y, ro.y, a1); a1 = fmaf(qv.z, ro.z, a1); a1 = fmaf(qv.w, ro.w, a1);
     }
     block_partials((double)a0, (double)a1, 2, partials);
     if (last_block(ticket)) scalar_step(partials, gridDim.x, sc, 0);
@@ -759,6 +1033,28 @@ __global__ void __launch_bounds__(kThreads) imp_float_operator_kernel(long long 
         }
 #pragma unroll
         for (int k = 0; k < 4 * DIM; ++k) Af[mode_index(p, KP + k, KA)] = (float)Cf[(long long)k * N + p];
+    }
+}
+
+// The compact float operator of a 2D forward solve: per point (tile-major, 6
+// values) the extrapolated velocity gradient 2 kappa^n - kappa^{n-1} and the
+// velocity, as imp_setup_kernel takes them, rounded to float; with the float
+// block-Jacobi inverses (tile-major, nc^2 per point) in Pf
+template <typename T>
+__global__ void __launch_bounds__(kThreads) imp_float_compact_kernel(const ImpArgs<T> A, const double* Pinv,
+                                                                     float* Cc, float* Pf) {
+    constexpr int NC = 3, KP = NC * NC;
+    const long long N = A.N;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int ij = 0; ij < 4; ++ij) {
+            const long long q = (long long)ij * N + p;
+            Cc[mode_index(p, ij, kPipeCompact)] = (float)(2.0 * (double)A.kap_n[q] - (double)A.kap_nm1[q]);
+        }
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax) Cc[mode_index(p, 4 + ax, kPipeCompact)] = (float)A.u[(long long)ax * N + p];
+#pragma unroll
+        for (int k = 0; k < KP; ++k) Pf[mode_index(p, k, KP)] = (float)Pinv[(long long)k * N + p];
     }
 }
 
@@ -1432,6 +1728,7 @@ struct KryView {
     float *Af, *Pf;   // float tile-major copies: blocks and taps (nc^2 + 4 d per point), inverses (nc^2)
     float *xf, *rf, *rhf, *pf, *vf, *svf, *tf, *phf, *shf;   // inner-solve vectors
     unsigned* ticket;
+    bool transposed = false;   // the taps and blocks of an adjoint solve (no compact float operator)
     KryView(double* w, double* parts, long long N) {
         constexpr int D = NC == 3 ? 2 : 3;
         const long long n = (long long)NC * N;
@@ -1467,6 +1764,7 @@ struct BiVecs {
     const V* b;
     V *x, *r, *rh, *p, *v, *sv, *t, *ph, *sh;
     const V *Mb, *Pinv, *Cf;
+    const CompactConsts* cc;   // the compact float operator (Mb holds its values), or null
 };
 
 template <typename T, int DIM, typename V>
@@ -1479,6 +1777,14 @@ cudaError_t bicgstab(const ImpArgs<T>& a, const BiVecs<V>& K, double* partials, 
     const unsigned bs = (unsigned)kImpBlocks;
     static const unsigned g_comb = resident_blocks(imp_comb_precond_kernel<NC, V>);
     static const unsigned g_xr = resident_blocks(imp_xr_kernel<V>);
+    static const unsigned g_xr4 = resident_blocks(imp_xr4_kernel);
+    // the float update in 16-byte accesses where every vector allows it
+    bool xr4 = false;
+    if constexpr (std::is_same<V, float>::value) {
+        auto al16 = [](const void* q) { return reinterpret_cast<uintptr_t>(q) % 16 == 0; };
+        xr4 = n % 4 == 0 && al16(K.x) && al16(K.ph) && al16(K.sh) && al16(K.r) && al16(K.sv) && al16(K.t) &&
+              al16(K.rh);
+    }
     cudaError_t e = cudaSuccess;
     auto ok = [&]() {
         if (e == cudaSuccess) e = cudaGetLastError();
@@ -1506,7 +1812,7 @@ cudaError_t bicgstab(const ImpArgs<T>& a, const BiVecs<V>& K, double* partials, 
         return e;
     }
     if (!x_zero) {
-        launch_apply<T, DIM, V>(a, K.Mb, K.Cf, K.x, K.r, nullptr, nullptr, partials, sc, -1, ticket, st);
+        launch_apply<T, DIM, V>(a, K.Mb, K.Cf, K.x, K.r, nullptr, nullptr, partials, sc, -1, ticket, K.cc, st);
         if (!ok()) return e;
     }
     imp_init_kernel<V><<<bs, kThreads, 0, st>>>(n, K.b, K.r, K.rh, K.p, K.v, K.x, x_zero ? 1 : 0);
@@ -1519,32 +1825,48 @@ cudaError_t bicgstab(const ImpArgs<T>& a, const BiVecs<V>& K, double* partials, 
     // kernel that leaves their partial sums
     auto iteration = [&](cudaStream_t s) {
         imp_comb_precond_kernel<NC, V><<<g_comb, kThreads, 0, s>>>(N, K.Pinv, 0, K.p, K.r, K.v, K.ph, sc);
-        launch_apply<T, DIM, V>(a, K.Mb, K.Cf, K.ph, K.v, K.rh, nullptr, partials, sc, 1, ticket, s);
+        launch_apply<T, DIM, V>(a, K.Mb, K.Cf, K.ph, K.v, K.rh, nullptr, partials, sc, 1, ticket, K.cc, s);
         imp_comb_precond_kernel<NC, V><<<g_comb, kThreads, 0, s>>>(N, K.Pinv, 1, K.sv, K.r, K.v, K.sh, sc);
-        launch_apply<T, DIM, V>(a, K.Mb, K.Cf, K.sh, K.t, K.sv, K.t, partials, sc, 2, ticket, s);
-        imp_xr_kernel<V><<<g_xr, kThreads, 0, s>>>(n, K.x, K.ph, K.sh, K.r, K.sv, K.t, K.rh, partials, sc, ticket);
+        launch_apply<T, DIM, V>(a, K.Mb, K.Cf, K.sh, K.t, K.sv, K.t, partials, sc, 2, ticket, K.cc, s);
+        if (xr4)
+            imp_xr4_kernel<<<g_xr4, kThreads, 0, s>>>(
+                n, reinterpret_cast<float4*>(K.x), reinterpret_cast<const float4*>(K.ph),
+                reinterpret_cast<const float4*>(K.sh), reinterpret_cast<float4*>(K.r),
+                reinterpret_cast<const float4*>(K.sv), reinterpret_cast<const float4*>(K.t),
+                reinterpret_cast<const float4*>(K.rh), partials, sc, ticket);
+        else
+            imp_xr_kernel<V><<<g_xr, kThreads, 0, s>>>(n, K.x, K.ph, K.sh, K.r, K.sv, K.t, K.rh, partials, sc,
+                                                       ticket);
     };
     // The kCheck iterations between two looks at the scalars run as one CUDA
     // graph, captured once per device, grid and workspace and kept (per host
     // thread): the kernels take nothing else, and a finished iteration makes the
     // remaining launches return at once.
     constexpr int kCheck = 8;
-    using Key = std::array<long long, 24>;
+    using Key = std::array<long long, 34>;
     static thread_local Key key{};
     static thread_local cudaGraphExec_t exec = nullptr;
     if (maxit >= kCheck) {
         int dev = 0;
         e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
+        // everything the captured launches take: the grid, the vectors, the
+        // scalars, and the compact operator's constants (by value in the graph)
+        CompactConsts q{};
+        if (K.cc) q = *K.cc;
+        auto bits = [](float f) { long long b = 0; std::memcpy(&b, &f, sizeof(f)); return b; };
         const Key k{dev, N, a.n0, a.n1, a.n2, (long long)g_comb, (long long)g_xr,
                     (long long)K.x, (long long)K.r, (long long)K.rh, (long long)K.p, (long long)K.v,
                     (long long)K.sv, (long long)K.t, (long long)K.ph, (long long)K.sh, (long long)K.Mb,
                     (long long)K.Pinv, (long long)K.Cf, (long long)partials, (long long)sc, (long long)ticket,
-                    0, 0};
+                    (long long)a.flags, K.cc ? 1 : 0, bits(q.dt), bits(q.a), bits(q.e[0]), bits(q.e[1]),
+                    bits(q.ih6[0]), bits(q.ih6[1]), bits(q.ih2[0]), bits(q.ih2[1]), q.stencil, 0};
         if (!exec || k != key) {
             if (exec) (void)cudaGraphExecDestroy(exec);
             exec = nullptr;
             (void)apply_blocks<DIM, V>(true);   // the occupancy queries before the capture
+            (void)pipe_blocks<kPipeFull>();
+            (void)pipe_blocks<kPipeCompact>();
             cudaStream_t cs = nullptr;
             e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
             if (e != cudaSuccess) return e;
@@ -1612,10 +1934,31 @@ cudaError_t krylov_solve(const ImpArgs<T>& a, const KryView<Packed<DIM>::NC>& K,
         if (e == cudaSuccess) e = cudaGetLastError();
         return e == cudaSuccess;
     };
-    // float copies of the operator (the blocks and their inverses are
-    // contiguous; the taps may be the transposed ones of an adjoint solve,
-    // kept elsewhere)
-    imp_float_operator_kernel<NC, DIM><<<bs, kThreads, 0, st>>>(N, K.Mb, K.Cf, K.Pinv, K.Af, K.Pf);
+    // the float operator: on whole 2D tiles of a forward solve the compact one
+    // (velocity gradient and velocity per point, applied by the pipelined
+    // kernel), else float copies of the blocks and taps (the taps may be the
+    // transposed ones of an adjoint solve, kept elsewhere); the block inverses
+    // in both cases
+    CompactConsts q{};
+    bool compact = false;
+    if constexpr (DIM == 2) {
+        compact = !K.transposed && pipe_fits(a, K.xf, K.rhf, K.Af) && pipe_fits(a, K.shf, K.svf, K.phf) &&
+                  pipe_blocks<kPipeCompact>() > 0;
+        if (compact) {
+            q.dt = (float)a.dt;
+            q.a = (float)a.a;
+            for (int ax = 0; ax < 2; ++ax) {
+                q.e[ax] = (float)(a.eps * a.inv_h[ax] * a.inv_h[ax]);
+                q.ih6[ax] = (float)(a.inv_h[ax] / 6.0);
+                q.ih2[ax] = (float)(0.5 * a.inv_h[ax]);
+            }
+            q.stencil = a.stencil;
+        }
+    }
+    if (compact)
+        imp_float_compact_kernel<T><<<bs, kThreads, 0, st>>>(a, K.Pinv, K.Af, K.Pf);
+    else
+        imp_float_operator_kernel<NC, DIM><<<bs, kThreads, 0, st>>>(N, K.Mb, K.Cf, K.Pinv, K.Af, K.Pf);
     if (!ok()) return e;
     // device scalars of the outer FP64 residual (never "done": the FP64 operator
     // kernel skips its work once the scalars it is given say so)
@@ -1627,8 +1970,9 @@ cudaError_t krylov_solve(const ImpArgs<T>& a, const KryView<Packed<DIM>::NC>& K,
     }
     // inner solve: right-hand side rf (overwritten by the residual: b is read
     // only before the init kernel sets r = b), correction xf
-    const BiVecs<float> Fv{K.rf,  K.xf,  K.rf,  K.rhf, K.pf,  K.vf, K.svf,
-                           K.tf,  K.phf, K.shf, K.Af,  K.Pf,  K.Af + 32LL * NC * NC};   // taps: nc^2 tile rows on
+    const BiVecs<float> Fv{K.rf,  K.xf,  K.rf,  K.rhf, K.pf,  K.vf, K.svf, K.tf,
+                           K.phf, K.shf, K.Af,  K.Pf,  K.Af + 32LL * NC * NC,   // taps: nc^2 tile rows on
+                           compact ? &q : nullptr};
     double hs[S_COUNT] = {};
     double bnorm2 = 0.0, rr = 0.0;
     int total = 0;
@@ -1659,7 +2003,8 @@ cudaError_t krylov_solve(const ImpArgs<T>& a, const KryView<Packed<DIM>::NC>& K,
     constexpr int kOuterMax = 12;
     for (int outer = 0; outer < kOuterMax; ++outer) {
         // r = b - Op x in FP64, its float copy, (r, r)
-        launch_apply<T, DIM, double>(a, K.Mb, K.Cf, K.x, K.r, nullptr, nullptr, partials, sco, -1, K.ticket, st);
+        launch_apply<T, DIM, double>(a, K.Mb, K.Cf, K.x, K.r, nullptr, nullptr, partials, sco, -1, K.ticket, nullptr,
+                                     st);
         imp_resid_kernel<<<bs, kThreads, 0, st>>>(n, K.b, K.r, K.rf, partials);
         imp_scalar_kernel<<<1, kThreads, 0, st>>>(partials, sco, 3);
         if (!ok()) return e;
@@ -1687,7 +2032,7 @@ cudaError_t krylov_solve(const ImpArgs<T>& a, const KryView<Packed<DIM>::NC>& K,
     }
     if (!converged) {
         // FP64 BiCGStab from the current iterate
-        const BiVecs<double> D{K.b, K.x, K.r, K.rh, K.p, K.v, K.sv, K.t, K.ph, K.sh, K.Mb, K.Pinv, K.Cf};
+        const BiVecs<double> D{K.b, K.x, K.r, K.rh, K.p, K.v, K.sv, K.t, K.ph, K.sh, K.Mb, K.Pinv, K.Cf, nullptr};
         int it = 0;
         double b2 = 0.0;
         e = bicgstab<T, DIM, double>(a, D, partials, sc, K.ticket, a.tol, a.maxit, false, st, &it, &rr, &b2);
@@ -1887,6 +2232,7 @@ cudaError_t run_implicit_adjoint(const ImpArgs<T>& a, double* s1, const T* ell_p
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     K.Cf = cfT;
+    K.transposed = true;
     e = krylov_solve<T, DIM>(a, K, st, iters, relres);
     if (e != cudaSuccess) return e;
     if (lp_out)
@@ -1923,6 +2269,7 @@ cudaError_t run_start_implicit_adjoint(const ImpArgs<T>& a, const StartConsts& C
     imp_transpose_blocks_kernel<NC><<<bs, kThreads, 0, st>>>(a.N, K.Mb, K.Pinv);
     imp_transpose_taps_kernel<DIM><<<bs, kThreads, 0, st>>>(a.N, a.n0, a.n1, a.n2, K.Cf, J.cfT);
     K.Cf = J.cfT;
+    K.transposed = true;
     // lamr2 (kept in s0_out until the end)
     if (J.paper)
         stp_lam_rhs_kernel<T, DIM><<<bs, kThreads, 0, st>>>(a, C, J.s1, J.lam_psi, nullptr, J.ell_prev, J.ell_prev2,
