@@ -120,6 +120,60 @@ __device__ __forceinline__ bool gauss_pp(double M[NC][NC], double x[NC], double 
     return ok;
 }
 
+// gauss_pp on NR right-hand sides at once (the columns of X): the elimination
+// of M runs once, and every column goes through exactly the operations that
+// gauss_pp applies to a single right-hand side, so each solution is bitwise
+// that of gauss_pp.  Returns false when a pivot is not larger than `tiny`.
+template <int NC, int NR>
+__device__ __forceinline__ bool gauss_pp_multi(double M[NC][NC], double X[NC][NR], double tiny) {
+    bool ok = true;
+    static_for<0, NC>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        static_for<k + 1, NC>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            const bool sw = fabs(M[i][k]) > fabs(M[k][k]);
+            static_for<k, NC>([&](auto jj) {
+                constexpr int j = decltype(jj)::value;
+                const double t0 = M[k][j], t1 = M[i][j];
+                M[k][j] = sw ? t1 : t0;
+                M[i][j] = sw ? t0 : t1;
+            });
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const double t0 = X[k][r], t1 = X[i][r];
+                X[k][r] = sw ? t1 : t0;
+                X[i][r] = sw ? t0 : t1;
+            }
+        });
+        ok = ok && (fabs(M[k][k]) > tiny);
+        const double inv = 1.0 / M[k][k];
+        M[k][k] = inv;
+        static_for<k + 1, NC>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            const double f = M[i][k] * inv;
+            static_for<k + 1, NC>([&](auto jj) {
+                constexpr int j = decltype(jj)::value;
+                M[i][j] = fma(-f, M[k][j], M[i][j]);
+            });
+#pragma unroll
+            for (int r = 0; r < NR; ++r) X[i][r] = fma(-f, X[k][r], X[i][r]);
+        });
+    });
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        static_for<0, NC>([&](auto rr) {
+            constexpr int i = NC - 1 - decltype(rr)::value;
+            double acc = X[i][r];
+            static_for<i + 1, NC>([&](auto jj) {
+                constexpr int j = decltype(jj)::value;
+                acc = fma(-M[i][j], X[j][r], acc);
+            });
+            X[i][r] = acc * M[i][i];
+        });
+    }
+    return ok;
+}
+
 // FP32 LU factorisation with partial pivoting by compare-and-swap on whole
 // rows (the multipliers move with their rows), recording every swap decision so
 // that the factors can be applied to further right-hand sides:  P M = L U.

@@ -35,6 +35,7 @@ namespace tfs {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kMB = 8;   // mode values a thread reads before it writes the first back
 
 template <typename T, int DIM, bool COMP>
 __global__ void __launch_bounds__(kThreads) imp_rhs_kernel(const ImpArgs<T> A, double* b, double* x0) {
@@ -61,30 +62,56 @@ __global__ void __launch_bounds__(kThreads) imp_rhs_kernel(const ImpArgs<T> A, d
                 const double H = kB1 * (double)A.sig_n[qc] + kB2 * (double)A.sig_nm1[qc] + kB0 * s0;
                 R = A.eta * s0 - H + A.dt * A.G * A.g * ks;
             } else if constexpr (F32) {
-                // compensated sum as in the default step, then one rounding to double
+                // compensated sum as in the default step, then one rounding to double;
+                // the modes are read kMB at a time, before the first of them is
+                // written back (the sum keeps its order)
                 float hs = 0.0f, comp = 0.0f;
-                for (int jj = 0; jj < A.m; ++jj) {
-                    const long long q = mode_index(p, jj * NC + c, A.m * NC);
-                    const float qj = __fmaf_rn(0.5f, (float)A.modes_nm1[q], -2.0f * (float)A.modes_n[q]);
-                    A.modes_nm1[q] = (T)qj;
-                    if (COMP) {
-                        const float yv = __fmaf_rn(A.mc.eta_hi[jj], qj, __fmaf_rn(A.mc.eta_lo[jj], qj, -comp));
-                        const float t = __fadd_rn(hs, yv);
-                        comp = __fsub_rn(__fsub_rn(t, hs), yv);
-                        hs = t;
-                    } else {
-                        hs = __fmaf_rn(A.mc.eta_hi[jj], qj, hs);
+                for (int j0 = 0; j0 < A.m; j0 += kMB) {
+                    float vn1[kMB], vn[kMB];
+#pragma unroll
+                    for (int k = 0; k < kMB; ++k)
+                        if (j0 + k < A.m) {
+                            const long long q = mode_index(p, (j0 + k) * NC + c, A.m * NC);
+                            vn1[k] = (float)A.modes_nm1[q];
+                            vn[k] = (float)A.modes_n[q];
+                        }
+#pragma unroll
+                    for (int k = 0; k < kMB; ++k) {
+                        const int jj = j0 + k;
+                        if (jj >= A.m) break;
+                        const float qj = __fmaf_rn(0.5f, vn1[k], -2.0f * vn[k]);
+                        A.modes_nm1[mode_index(p, jj * NC + c, A.m * NC)] = (T)qj;
+                        if (COMP) {
+                            const float yv = __fmaf_rn(A.mc.eta_hi[jj], qj, __fmaf_rn(A.mc.eta_lo[jj], qj, -comp));
+                            const float t = __fadd_rn(hs, yv);
+                            comp = __fsub_rn(__fsub_rn(t, hs), yv);
+                            hs = t;
+                        } else {
+                            hs = __fmaf_rn(A.mc.eta_hi[jj], qj, hs);
+                        }
                     }
                 }
                 const double H = (double)hs - (double)comp;
                 R = A.eta * s0 - H + A.dt * A.G * A.g * ks;
             } else {
                 double H = 0.0;
-                for (int jj = 0; jj < A.m; ++jj) {
-                    const long long q = mode_index(p, jj * NC + c, A.m * NC);
-                    const double qj = kB1 * (double)A.modes_n[q] + kB2 * (double)A.modes_nm1[q];
-                    A.modes_nm1[q] = (T)qj;
-                    H = fma(A.mcd.eta[jj], qj, H);
+                for (int j0 = 0; j0 < A.m; j0 += kMB) {
+                    double vn1[kMB], vn[kMB];
+#pragma unroll
+                    for (int k = 0; k < kMB; ++k)
+                        if (j0 + k < A.m) {
+                            const long long q = mode_index(p, (j0 + k) * NC + c, A.m * NC);
+                            vn1[k] = (double)A.modes_nm1[q];
+                            vn[k] = (double)A.modes_n[q];
+                        }
+#pragma unroll
+                    for (int k = 0; k < kMB; ++k) {
+                        const int jj = j0 + k;
+                        if (jj >= A.m) break;
+                        const double qj = kB1 * vn[k] + kB2 * vn1[k];
+                        A.modes_nm1[mode_index(p, jj * NC + c, A.m * NC)] = (T)qj;
+                        H = fma(A.mcd.eta[jj], qj, H);
+                    }
                 }
                 R = A.eta * s0 - H + A.dt * A.G * A.g * ks;
             }
@@ -143,19 +170,25 @@ __global__ void __launch_bounds__(kThreads) imp_setup_kernel(const ImpArgs<T> A,
         }
 #pragma unroll
         for (int r = 0; r < NC; ++r) M[r][r] += A.dt * diag;
+        // the inverse, column by column of the identity; in 2D one elimination
+        // for all three (3D: the 6 x 6 blocks of both would not fit the registers)
+        constexpr int NR = NC <= 3 ? NC : 1;
         bool ok = true;
 #pragma unroll
-        for (int k = 0; k < NC; ++k) {
-            double P[NC][NC], col[NC];
+        for (int k0 = 0; k0 < NC; k0 += NR) {
+            double P[NC][NC], X[NC][NR];
 #pragma unroll
             for (int r = 0; r < NC; ++r) {
 #pragma unroll
                 for (int c = 0; c < NC; ++c) P[r][c] = M[r][c];
-                col[r] = r == k ? 1.0 : 0.0;
-            }
-            ok = gauss_pp<NC>(P, col, 1e-300) && ok;
 #pragma unroll
-            for (int r = 0; r < NC; ++r) Pinv[(long long)(r * NC + k) * N + p] = col[r];
+                for (int k = 0; k < NR; ++k) X[r][k] = r == k0 + k ? 1.0 : 0.0;
+            }
+            ok = gauss_pp_multi<NC, NR>(P, X, 1e-300) && ok;
+#pragma unroll
+            for (int r = 0; r < NC; ++r)
+#pragma unroll
+                for (int k = 0; k < NR; ++k) Pinv[(long long)(r * NC + k0 + k) * N + p] = X[r][k];
         }
         if (!ok) atomicOr(A.flags, 2u);
 #pragma unroll
@@ -247,6 +280,17 @@ __device__ __forceinline__ bool last_block(unsigned* ticket) {
 __device__ void scalar_step(const double* partials, int nparts, double* sc, int op) {
     __shared__ double sh[2][kWarps];
     static_assert(kImpBlocks <= 4 * kThreads, "at most four partial sums per thread");
+    // thread 0 reads the scalars it needs together with the partial sums (no
+    // other block writes them during the launch): one round trip, not two
+    double s_done = 0.0, s_rho = 0.0, s_alpha = 0.0, s_omega = 0.0, s_lim = 0.0, s_iters = 0.0;
+    if (threadIdx.x == 0 && op != 3) {
+        s_done = sc[S_DONE];
+        s_rho = sc[S_RHO];
+        s_alpha = sc[S_ALPHA];
+        s_omega = sc[S_OMEGA];
+        s_lim = sc[S_TOL2] * sc[S_BNORM2];
+        s_iters = sc[S_ITERS];
+    }
     // the (at most) four partial sums of a thread are loaded together; written by
     // other blocks of this launch, they are read from L2
     double p0[4], p1[4];
@@ -264,27 +308,29 @@ __device__ void scalar_step(const double* partials, int nparts, double* sc, int 
         sc[S_BNORM2] = v0;
         return;
     }
-    // beta and rho of the next direction, once (r, r) and (rh, r) are known
-    auto next_direction = [&]() {
-        if (done(sc)) return;
-        sc[S_BETA] = (sc[S_RHO_NEW] / sc[S_RHO]) * (sc[S_ALPHA] / sc[S_OMEGA]);
-        sc[S_RHO] = sc[S_RHO_NEW];
+    // beta and rho of the next direction, once (r, r) = v0 and (rh, r) = v1 are
+    // known and the iteration goes on
+    auto next_direction = [&](bool done_now) {
+        if (done_now) return;
+        sc[S_BETA] = (v1 / s_rho) * (s_alpha / s_omega);
+        sc[S_RHO] = v1;
     };
     if (op == 4) {
         sc[S_RR] = v0;
         sc[S_RHO_NEW] = v1;
-        if (v0 <= sc[S_TOL2] * sc[S_BNORM2]) sc[S_DONE] = 1.0;
-        next_direction();
+        const bool conv = v0 <= s_lim;
+        if (conv) sc[S_DONE] = 1.0;
+        next_direction(s_done != 0.0 || conv);
         return;
     }
-    if (done(sc)) return;
+    if (s_done != 0.0) return;
     if (op == 1) {
         sc[S_RHV] = v0;
         if (v0 == 0.0) {
             sc[S_BREAK] = 1.0;
             sc[S_DONE] = 1.0;
         } else {
-            sc[S_ALPHA] = sc[S_RHO] / v0;
+            sc[S_ALPHA] = s_rho / v0;
         }
     } else if (op == 2) {
         sc[S_TS] = v0;
@@ -293,14 +339,17 @@ __device__ void scalar_step(const double* partials, int nparts, double* sc, int 
     } else {
         sc[S_RR] = v0;
         sc[S_RHO_NEW] = v1;
-        sc[S_ITERS] += 1.0;
-        if (v0 <= sc[S_TOL2] * sc[S_BNORM2]) {
+        sc[S_ITERS] = s_iters + 1.0;
+        bool stop = false;
+        if (v0 <= s_lim) {
             sc[S_DONE] = 1.0;
-        } else if (v1 == 0.0 || sc[S_OMEGA] == 0.0) {
+            stop = true;
+        } else if (v1 == 0.0 || s_omega == 0.0) {
             sc[S_BREAK] = 1.0;
             sc[S_DONE] = 1.0;
+            stop = true;
         }
-        next_direction();
+        next_direction(stop);
     }
 }
 
@@ -545,19 +594,6 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 && sizeof(V) == 4 ? 6 : 1)
     }
 }
 
-// The float operator on 2D grids with n0 % 32 == 0 and n1 % 8 == 0 (16-byte
-// aligned vectors), software-pipelined: a unit is one 32 x 8 tile, staged into
-// one of two shared-memory stages while the previous unit is applied from the
-// other.  The tile's coefficient rows (tile-major: 8 contiguous rows of
-// nc^2 + 8 coefficients x 32 points, 2176 bytes each) arrive by bulk copies
-// (cp.async.bulk, one per row from lanes of warp 0, completing on the stage's
-// mbarrier); its x rows with a margin of 4 cells in x and 2 in y (whole 16-byte
-// chunks, wrapped periodically) and its w0 rows by 16-byte cp.async copies of
-// every thread.  Every entry of y is formed in the order of
-// imp_apply_tiled_kernel, so the two give the same y.  A wait that gives up
-// latches TFS_FLAG_TIMEOUT, lets the copies in flight land (bounded) and ends
-// the block's units; the block still adds its partial sums, so the last-block
-// count stays whole.
 constexpr int kPX = kAX + 8;   // staged x row: x0 - 4 .. x0 + 35
 constexpr int kPipeFull = 9 + 8;   // 2D: nc^2 block entries and 4 taps x 2 axes per point
 constexpr int kPipeCompact = 6;    // 2D: the extrapolated velocity gradient (4) and the velocity (2)
@@ -578,27 +614,123 @@ struct CompactConsts {
     int stencil;
 };
 
+// The 2D point block M and taps cf[axis][-2, -1, +1, +2] of the compact float
+// operator from the point's values kc (kappa_00, kappa_01, kappa_10, kappa_11 of
+// the extrapolated gradient, u_0, u_1): imp_setup_kernel's formulas in float.
+__device__ __forceinline__ void compact_operator(const float kc[kPipeCompact], const CompactConsts& Q, float M[3][3],
+                                                 float cf[2][4]) {
+    const float K[3][3] = {{kc[0], kc[1], 0.f}, {kc[2], kc[3], 0.f}, {0.f, 0.f, 0.f}};
+    float diag = 0.f;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const float ua = kc[4 + a], e = Q.e[a];
+        if (Q.stencil == 0) diag += fabsf(ua) * Q.ih2[a];
+        diag += 2.f * e;
+        float c[4];
+        if (Q.stencil == 1) {
+            const float h2 = ua * Q.ih2[a];
+            c[0] = 0.f; c[1] = -h2 - e; c[2] = h2 - e; c[3] = 0.f;
+        } else if (ua >= 0.f) {
+            const float s6 = ua * Q.ih6[a];
+            c[0] = s6; c[1] = -6.f * s6 - e; c[2] = 2.f * s6 - e; c[3] = 0.f;
+        } else {
+            const float s6 = ua * Q.ih6[a];
+            c[0] = 0.f; c[1] = -2.f * s6 - e; c[2] = 6.f * s6 - e; c[3] = -s6;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) cf[a][t] = Q.dt * c[t];
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float l = uc_entry<2>(K, r, k);
+            M[r][k] = r == k ? fmaf(-Q.dt, l, Q.a) + Q.dt * diag : -Q.dt * l;
+        }
+}
+
+// The compact float operator on 2D grids with n0 % 32 == 0 and n1 % 8 == 0,
+// without staging: a block applies 32 x 8 tiles (a warp per row segment),
+// grid-stride, every thread loading its point's values, x at the point and at
+// its eight taps (the neighbours' rows are those of the block's other warps or
+// the tile's margin: L1 serves most) and w0, with no barrier between tiles, so
+// that the loads of every resident warp stay in flight together.  (Staging the
+// tile in shared memory by bulk and cp.async copies, as imp_apply_pipe2d_kernel
+// does, measured slower for these 6 values per point: 23.3 against 22.3 us at
+// 1024^2.)
+__global__ void __launch_bounds__(kThreads) imp_apply_l1_kernel(const ImpGrid A, const CompactConsts Q,
+                                                                const float* __restrict__ Cc,
+                                                                const float* __restrict__ x, float* y,
+                                                                const float* w0, const float* w1, double* partials,
+                                                                double* sc, int op, unsigned* ticket) {
+    constexpr int NC = 3;
+    if (done(sc)) return;
+    const bool w1y = w1 == y;
+    const long long N = A.N;
+    const int n0 = A.n0, n1 = A.n1;
+    const int tid = threadIdx.x, tx = tid % kAX, ty = tid / kAX;
+    const int tiles_x = n0 / kAX, units = tiles_x * (n1 / kAY);
+    auto wrap1 = [](int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); };   // -n <= v < 2n
+    float a0 = 0.f, a1 = 0.f;
+    for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
+        const int gx = (unit % tiles_x) * kAX + tx, gy = (unit / tiles_x) * kAY + ty;
+        const long long p = (long long)gy * n0 + gx;
+        float kc[kPipeCompact];
+#pragma unroll
+        for (int k = 0; k < kPipeCompact; ++k) kc[k] = Cc[mode_index(p, k, kPipeCompact)];
+        // offsets of the taps -2, -1, +1, +2 along x, then y
+        const long long row = (long long)gy * n0;
+        long long off[8];
+        off[0] = row + wrap1(gx - 2, n0); off[1] = row + wrap1(gx - 1, n0);
+        off[2] = row + wrap1(gx + 1, n0); off[3] = row + wrap1(gx + 2, n0);
+        off[4] = (long long)wrap1(gy - 2, n1) * n0 + gx; off[5] = (long long)wrap1(gy - 1, n1) * n0 + gx;
+        off[6] = (long long)wrap1(gy + 1, n1) * n0 + gx; off[7] = (long long)wrap1(gy + 2, n1) * n0 + gx;
+        float xp[NC], xt[NC][8], wv[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const float* xc = x + (long long)c * N;
+            xp[c] = xc[p];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) xt[c][t] = xc[off[t]];
+            wv[c] = w0 ? w0[(long long)c * N + p] : 0.f;
+        }
+        float M[NC][NC], cf[2][4];
+        compact_operator(kc, Q, M, cf);
+#pragma unroll
+        for (int r = 0; r < NC; ++r) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < NC; ++k) acc = fmaf(M[r][k], xp[k], acc);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) acc = fmaf(cf[t / 4][t % 4], xt[r][t], acc);
+            const long long q = (long long)r * N + p;
+            y[q] = acc;
+            if (w0) a0 = fmaf(wv[r], acc, a0);
+            if (w1) a1 = fmaf(w1y ? acc : w1[q], acc, a1);
+        }
+    }
+    if (w0) {
+        block_partials((double)a0, (double)a1, w1 ? 2 : 1, partials);
+        if (op >= 0 && last_block(ticket)) scalar_step(partials, gridDim.x, sc, op);
+    }
+}
+
 // The float operator on 2D grids with n0 % 32 == 0 and n1 % 8 == 0 (16-byte
 // aligned vectors), software-pipelined: a unit is one 32 x 8 tile, staged into
 // one of two shared-memory stages while the previous unit is applied from the
 // other.  The tile's coefficient rows (tile-major: 8 contiguous rows of KC
-// values x 32 points) arrive by bulk copies (cp.async.bulk, one per row from
-// lanes of warp 0, completing on the stage's mbarrier); its x rows with a
-// margin of 4 cells in x and 2 in y (whole 16-byte chunks, wrapped periodically)
-// and its w0 rows by 16-byte cp.async copies of every thread.
-//   KC = kPipeFull: the coefficients are the rounded blocks and taps of
-//     imp_setup_kernel, and every entry of y is formed in the order of
-//     imp_apply_tiled_kernel (the two give the same y);
-//   KC = kPipeCompact: per point the extrapolated velocity gradient and the
-//     velocity, from which the block and the taps are formed in float with
-//     imp_setup_kernel's formulas (the step's operator to float rounding, from
-//     35% of the bytes).
+// values x 32 points: the rounded blocks and taps of imp_setup_kernel) arrive by
+// bulk copies (cp.async.bulk, one per row from lanes of warp 0, completing on
+// the stage's mbarrier); its x rows with a margin of 4 cells in x and 2 in y
+// (whole 16-byte chunks, wrapped periodically) and its w0 rows by 16-byte
+// cp.async copies of every thread.  Every entry of y is formed in the order of
+// imp_apply_tiled_kernel (the two give the same y).  It serves the float
+// operators that are not compact (the transposed ones of adjoint solves).
 // A wait that gives up latches TFS_FLAG_TIMEOUT, lets the copies in flight land
 // (bounded) and ends the block's units; the block still adds its partial sums,
 // so the last-block count stays whole.
 template <int KC>
-__global__ void __launch_bounds__(kThreads) imp_apply_pipe2d_kernel(const ImpGrid A, const CompactConsts Q,
-                                                                    const float* __restrict__ Af,
+__global__ void __launch_bounds__(kThreads) imp_apply_pipe2d_kernel(const ImpGrid A, const float* __restrict__ Af,
                                                                     const float* __restrict__ x, float* y,
                                                                     const float* w0, const float* w1,
                                                                     double* partials, double* sc, int op,
@@ -678,47 +810,16 @@ __global__ void __launch_bounds__(kThreads) imp_apply_pipe2d_kernel(const ImpGri
         const long long p = (long long)(y0 + ty) * n0 + x0 + tx;
         const int sy = ty + kAH, sx = tx + 4;
         // the point's block M and taps cf[axis][-2, -1, +1, +2]
+        static_assert(KC == kPipeFull, "nc^2 block entries and 8 taps per point");
         float M[NC][NC], cf[2][4];
-        if constexpr (KC == kPipeFull) {
 #pragma unroll
-            for (int r = 0; r < NC; ++r)
+        for (int r = 0; r < NC; ++r)
 #pragma unroll
-                for (int k = 0; k < NC; ++k) M[r][k] = S.C[ty][r * NC + k][tx];
+            for (int k = 0; k < NC; ++k) M[r][k] = S.C[ty][r * NC + k][tx];
 #pragma unroll
-            for (int a = 0; a < 2; ++a)
+        for (int a = 0; a < 2; ++a)
 #pragma unroll
-                for (int t = 0; t < 4; ++t) cf[a][t] = S.C[ty][NC * NC + 4 * a + t][tx];
-        } else {
-            const float K[3][3] = {{S.C[ty][0][tx], S.C[ty][1][tx], 0.f}, {S.C[ty][2][tx], S.C[ty][3][tx], 0.f},
-                                   {0.f, 0.f, 0.f}};
-            float diag = 0.f;
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                const float ua = S.C[ty][4 + a][tx], e = Q.e[a];
-                if (Q.stencil == 0) diag += fabsf(ua) * Q.ih2[a];
-                diag += 2.f * e;
-                float c[4];
-                if (Q.stencil == 1) {
-                    const float h2 = ua * Q.ih2[a];
-                    c[0] = 0.f; c[1] = -h2 - e; c[2] = h2 - e; c[3] = 0.f;
-                } else if (ua >= 0.f) {
-                    const float s6 = ua * Q.ih6[a];
-                    c[0] = s6; c[1] = -6.f * s6 - e; c[2] = 2.f * s6 - e; c[3] = 0.f;
-                } else {
-                    const float s6 = ua * Q.ih6[a];
-                    c[0] = 0.f; c[1] = -2.f * s6 - e; c[2] = 6.f * s6 - e; c[3] = -s6;
-                }
-#pragma unroll
-                for (int t = 0; t < 4; ++t) cf[a][t] = Q.dt * c[t];
-            }
-#pragma unroll
-            for (int r = 0; r < NC; ++r)
-#pragma unroll
-                for (int k = 0; k < NC; ++k) {
-                    const float l = uc_entry<2>(K, r, k);
-                    M[r][k] = r == k ? fmaf(-Q.dt, l, Q.a) + Q.dt * diag : -Q.dt * l;
-                }
-        }
+            for (int t = 0; t < 4; ++t) cf[a][t] = S.C[ty][NC * NC + 4 * a + t][tx];
         float xp[NC];
 #pragma unroll
         for (int k = 0; k < NC; ++k) xp[k] = S.X[k][sy][sx];
@@ -791,6 +892,11 @@ unsigned pipe_blocks() {
     return g;
 }
 
+inline unsigned l1_blocks() {
+    static const unsigned g = resident_blocks(imp_apply_l1_kernel);
+    return g;
+}
+
 // whether the pipelined kernel serves this 2D float operator (whole tiles,
 // 16-byte aligned vectors)
 template <typename T>
@@ -800,7 +906,7 @@ bool pipe_fits(const ImpArgs<T>& a, const void* x, const void* w0, const void* c
 }
 
 // cc: the compact float operator (Mb then holds its per-point values), which
-// only the pipelined 2D kernel applies
+// only imp_apply_l1_kernel applies
 template <typename T, int DIM, typename V>
 void launch_apply(const ImpArgs<T>& a, const V* Mb, const V* Cf, const V* x, V* y, const V* w0, const V* w1,
                   double* partials, double* sc, int op, unsigned* ticket, const CompactConsts* cc, cudaStream_t st) {
@@ -808,13 +914,12 @@ void launch_apply(const ImpArgs<T>& a, const V* Mb, const V* Cf, const V* x, V* 
     const bool tiled = a.n0 % kAX == 0 && a.n1 % kAY == 0;
     if constexpr (DIM == 2 && std::is_same<V, float>::value) {
         if (cc) {
-            imp_apply_pipe2d_kernel<kPipeCompact><<<pipe_blocks<kPipeCompact>(), kThreads, pipe_smem<kPipeCompact>(),
-                                                    st>>>(G, *cc, Mb, x, y, w0, w1, partials, sc, op, ticket);
+            imp_apply_l1_kernel<<<l1_blocks(), kThreads, 0, st>>>(G, *cc, Mb, x, y, w0, w1, partials, sc, op, ticket);
             return;
         }
         if (pipe_fits(a, x, w0, Mb) && Cf == Mb + 32 * 9 && pipe_blocks<kPipeFull>() > 0) {
             imp_apply_pipe2d_kernel<kPipeFull><<<pipe_blocks<kPipeFull>(), kThreads, pipe_smem<kPipeFull>(), st>>>(
-                G, CompactConsts{}, Mb, x, y, w0, w1, partials, sc, op, ticket);
+                G, Mb, x, y, w0, w1, partials, sc, op, ticket);
             return;
         }
     }
@@ -823,6 +928,47 @@ void launch_apply(const ImpArgs<T>& a, const V* Mb, const V* Cf, const V* x, V* 
         imp_apply_tiled_kernel<DIM, V><<<g, kThreads, 0, st>>>(G, Mb, Cf, x, y, w0, w1, partials, sc, op, ticket);
     else
         imp_apply_kernel<DIM, V><<<g, kThreads, 0, st>>>(G, Mb, Cf, x, y, w0, w1, partials, sc, op, ticket);
+}
+
+// The combination and the block-Jacobi step of imp_comb_precond_kernel with the
+// compact float operator of a 2D forward solve: the point block M (with the
+// centre taps) is formed from the point's 6 values as imp_apply_l1_kernel forms
+// it, and M z = w is solved by cofactors, instead of reading 9 stored inverse
+// entries (the preconditioner is then M^-1 of the float operator itself).
+__global__ void __launch_bounds__(kThreads) imp_comb_compact_kernel(long long N, const float* __restrict__ Cc,
+                                                                    const CompactConsts Q, int mode,
+                                                                    float* __restrict__ p,
+                                                                    const float* __restrict__ r,
+                                                                    const float* __restrict__ v,
+                                                                    float* __restrict__ z, const double* sc) {
+    if (done(sc)) return;
+    // mode 0: p = r + beta (p - omega v);  mode 1: p (as s) = r - alpha v
+    const float beta = (float)sc[S_BETA], omega = (float)sc[S_OMEGA], alpha = (float)sc[S_ALPHA];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        float kc[kPipeCompact], w[3];
+#pragma unroll
+        for (int k = 0; k < kPipeCompact; ++k) kc[k] = Cc[mode_index(i, k, kPipeCompact)];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long q = (long long)c * N + i;
+            const float nv = mode == 0 ? fmaf(beta, p[q] - omega * v[q], r[q]) : fmaf(-alpha, v[q], r[q]);
+            p[q] = nv;
+            w[c] = nv;
+        }
+        float M[3][3], cf[2][4];
+        compact_operator(kc, Q, M, cf);
+        // cofactors C[i][j] of M; z = C^T w / det
+        const float c00 = M[1][1] * M[2][2] - M[1][2] * M[2][1], c01 = M[1][2] * M[2][0] - M[1][0] * M[2][2],
+                    c02 = M[1][0] * M[2][1] - M[1][1] * M[2][0];
+        const float c10 = M[0][2] * M[2][1] - M[0][1] * M[2][2], c11 = M[0][0] * M[2][2] - M[0][2] * M[2][0],
+                    c12 = M[0][1] * M[2][0] - M[0][0] * M[2][1];
+        const float c20 = M[0][1] * M[1][2] - M[0][2] * M[1][1], c21 = M[0][2] * M[1][0] - M[0][0] * M[1][2],
+                    c22 = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+        const float inv = 1.f / (M[0][0] * c00 + M[0][1] * c01 + M[0][2] * c02);
+        z[i] = (c00 * w[0] + c10 * w[1] + c20 * w[2]) * inv;
+        z[N + i] = (c01 * w[0] + c11 * w[1] + c21 * w[2]) * inv;
+        z[2 * N + i] = (c02 * w[0] + c12 * w[1] + c22 * w[2]) * inv;
+    }
 }
 
 // z = P^-1 v with v = a x + b y (+ c w): forms the combination, stores it in
@@ -964,17 +1110,24 @@ __global__ void __launch_bounds__(kThreads) imp_push_kernel(const ImpArgs<T> A, 
             if (A.sig_copy) A.sig_copy[qc] = out;
             const T s0 = A.sigma0 ? A.sigma0[qc] : (T)0;
             if (A.classic) continue;
-            if constexpr (F32) {
-                const float d = __fsub_rn((float)out, (float)s0);
-                for (int j = 0; j < A.m; ++j) {
+            // the modes read kMB at a time before the first is written back
+            for (int j0 = 0; j0 < A.m; j0 += kMB) {
+                T qv[kMB];
+#pragma unroll
+                for (int k = 0; k < kMB; ++k)
+                    if (j0 + k < A.m) qv[k] = A.modes_nm1[mode_index(p, (j0 + k) * NC + c, A.m * NC)];
+#pragma unroll
+                for (int k = 0; k < kMB; ++k) {
+                    const int j = j0 + k;
+                    if (j >= A.m) break;
                     const long long q = mode_index(p, j * NC + c, A.m * NC);
-                    A.modes_nm1[q] = __fmaf_rn(A.mc.rho[j], d, -A.mc.c[j] * (float)A.modes_nm1[q]);
-                }
-            } else {
-                const double d = (double)out - (double)s0;
-                for (int j = 0; j < A.m; ++j) {
-                    const long long q = mode_index(p, j * NC + c, A.m * NC);
-                    A.modes_nm1[q] = (T)fma(A.mcd.rho[j], d, -A.mcd.c[j] * (double)A.modes_nm1[q]);
+                    if constexpr (F32) {
+                        const float d = __fsub_rn((float)out, (float)s0);
+                        A.modes_nm1[q] = __fmaf_rn(A.mc.rho[j], d, -A.mc.c[j] * (float)qv[k]);
+                    } else {
+                        const double d = (double)out - (double)s0;
+                        A.modes_nm1[q] = (T)fma(A.mcd.rho[j], d, -A.mcd.c[j] * (double)qv[k]);
+                    }
                 }
             }
         }
@@ -1038,12 +1191,10 @@ __global__ void __launch_bounds__(kThreads) imp_float_operator_kernel(long long 
 
 // The compact float operator of a 2D forward solve: per point (tile-major, 6
 // values) the extrapolated velocity gradient 2 kappa^n - kappa^{n-1} and the
-// velocity, as imp_setup_kernel takes them, rounded to float; with the float
-// block-Jacobi inverses (tile-major, nc^2 per point) in Pf
+// velocity, as imp_setup_kernel takes them, rounded to float (the operator and
+// its block-Jacobi preconditioner are formed from them where they are applied)
 template <typename T>
-__global__ void __launch_bounds__(kThreads) imp_float_compact_kernel(const ImpArgs<T> A, const double* Pinv,
-                                                                     float* Cc, float* Pf) {
-    constexpr int NC = 3, KP = NC * NC;
+__global__ void __launch_bounds__(kThreads) imp_float_compact_kernel(const ImpArgs<T> A, float* Cc) {
     const long long N = A.N;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
@@ -1053,8 +1204,6 @@ __global__ void __launch_bounds__(kThreads) imp_float_compact_kernel(const ImpAr
         }
 #pragma unroll
         for (int ax = 0; ax < 2; ++ax) Cc[mode_index(p, 4 + ax, kPipeCompact)] = (float)A.u[(long long)ax * N + p];
-#pragma unroll
-        for (int k = 0; k < KP; ++k) Pf[mode_index(p, k, KP)] = (float)Pinv[(long long)k * N + p];
     }
 }
 
@@ -1776,6 +1925,17 @@ cudaError_t bicgstab(const ImpArgs<T>& a, const BiVecs<V>& K, double* partials, 
     const long long n = (long long)NC * N;
     const unsigned bs = (unsigned)kImpBlocks;
     static const unsigned g_comb = resident_blocks(imp_comb_precond_kernel<NC, V>);
+    static const unsigned g_combc = resident_blocks(imp_comb_compact_kernel);
+    // the combination and the preconditioner (compact: from the operator's values)
+    auto comb = [&](int mode, V* pv, V* z, cudaStream_t s) {
+        if constexpr (std::is_same<V, float>::value && DIM == 2) {
+            if (K.cc) {
+                imp_comb_compact_kernel<<<g_combc, kThreads, 0, s>>>(N, K.Mb, *K.cc, mode, pv, K.r, K.v, z, sc);
+                return;
+            }
+        }
+        imp_comb_precond_kernel<NC, V><<<g_comb, kThreads, 0, s>>>(N, K.Pinv, mode, pv, K.r, K.v, z, sc);
+    };
     static const unsigned g_xr = resident_blocks(imp_xr_kernel<V>);
     static const unsigned g_xr4 = resident_blocks(imp_xr4_kernel);
     // the float update in 16-byte accesses where every vector allows it
@@ -1824,9 +1984,9 @@ cudaError_t bicgstab(const ImpArgs<T>& a, const BiVecs<V>& K, double* partials, 
     // one iteration, five launches: the scalar steps run in the last block of the
     // kernel that leaves their partial sums
     auto iteration = [&](cudaStream_t s) {
-        imp_comb_precond_kernel<NC, V><<<g_comb, kThreads, 0, s>>>(N, K.Pinv, 0, K.p, K.r, K.v, K.ph, sc);
+        comb(0, K.p, K.ph, s);
         launch_apply<T, DIM, V>(a, K.Mb, K.Cf, K.ph, K.v, K.rh, nullptr, partials, sc, 1, ticket, K.cc, s);
-        imp_comb_precond_kernel<NC, V><<<g_comb, kThreads, 0, s>>>(N, K.Pinv, 1, K.sv, K.r, K.v, K.sh, sc);
+        comb(1, K.sv, K.sh, s);
         launch_apply<T, DIM, V>(a, K.Mb, K.Cf, K.sh, K.t, K.sv, K.t, partials, sc, 2, ticket, K.cc, s);
         if (xr4)
             imp_xr4_kernel<<<g_xr4, kThreads, 0, s>>>(
@@ -1866,7 +2026,7 @@ cudaError_t bicgstab(const ImpArgs<T>& a, const BiVecs<V>& K, double* partials, 
             exec = nullptr;
             (void)apply_blocks<DIM, V>(true);   // the occupancy queries before the capture
             (void)pipe_blocks<kPipeFull>();
-            (void)pipe_blocks<kPipeCompact>();
+            (void)l1_blocks();
             cudaStream_t cs = nullptr;
             e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
             if (e != cudaSuccess) return e;
@@ -1935,15 +2095,14 @@ cudaError_t krylov_solve(const ImpArgs<T>& a, const KryView<Packed<DIM>::NC>& K,
         return e == cudaSuccess;
     };
     // the float operator: on whole 2D tiles of a forward solve the compact one
-    // (velocity gradient and velocity per point, applied by the pipelined
-    // kernel), else float copies of the blocks and taps (the taps may be the
-    // transposed ones of an adjoint solve, kept elsewhere); the block inverses
-    // in both cases
+    // (velocity gradient and velocity per point, from which imp_apply_l1_kernel
+    // forms the operator and imp_comb_compact_kernel the preconditioner), else
+    // float copies of the blocks, the taps (which may be the transposed ones of
+    // an adjoint solve, kept elsewhere) and the block inverses
     CompactConsts q{};
     bool compact = false;
     if constexpr (DIM == 2) {
-        compact = !K.transposed && pipe_fits(a, K.xf, K.rhf, K.Af) && pipe_fits(a, K.shf, K.svf, K.phf) &&
-                  pipe_blocks<kPipeCompact>() > 0;
+        compact = !K.transposed && a.n0 % kAX == 0 && a.n1 % kAY == 0;
         if (compact) {
             q.dt = (float)a.dt;
             q.a = (float)a.a;
@@ -1956,7 +2115,7 @@ cudaError_t krylov_solve(const ImpArgs<T>& a, const KryView<Packed<DIM>::NC>& K,
         }
     }
     if (compact)
-        imp_float_compact_kernel<T><<<bs, kThreads, 0, st>>>(a, K.Pinv, K.Af, K.Pf);
+        imp_float_compact_kernel<T><<<bs, kThreads, 0, st>>>(a, K.Af);
     else
         imp_float_operator_kernel<NC, DIM><<<bs, kThreads, 0, st>>>(N, K.Mb, K.Cf, K.Pinv, K.Af, K.Pf);
     if (!ok()) return e;
