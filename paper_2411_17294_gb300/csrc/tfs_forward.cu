@@ -14,13 +14,15 @@
 // registers; transport_kernel, one thread per point, for grids that do not
 // tile) and the step kernel reads it like any other per-point input.  The
 // step kernel is persistent: each block of 3 warps loops over tiles of 32
-// consecutive points, and everything a tile reads -- the m x nc (mode,
-// component) planes of both levels, kappa^n, kappa^{n-1}, A, sigma0, and for
-// alpha = 1 (or the paper's variable) the two levels of the carried field --
-// is staged global -> shared by TMA (cp.async.bulk.tensor.2d, one thread
-// issues, completion on mbarriers with bounded waits) or, on grids whose plane
-// length is not a multiple of 16 bytes, by cp.async.  The mode stream (94% of
-// the bytes) and every per-point input are in flight without holding
+// consecutive points, and everything a tile reads is staged global -> shared
+// by one thread before the compute phase: both mode levels by untiled bulk
+// copies (cp.async.bulk; the mode levels are stored tile-major, so a tile's
+// m nc rows of 32 values are one contiguous block per level), and kappa^n,
+// kappa^{n-1}, A, sigma0 and, for alpha = 1 or the paper's variable, the two
+// levels of the carried field by tensor-map tiles (cp.async.bulk.tensor.2d;
+// cp.async on grids whose plane length is not a multiple of 16 bytes), with
+// completion counted on mbarriers whose waits are bounded.  The mode stream
+// (94% of the bytes) and every per-point input are in flight without holding
 // registers, and the compute phase makes no global loads.  Inside a tile,
 // warp w handles stress components w and w + 3 in 3D (w in 2D), lane = point:
 // it forms Q_j = b1 x + b2 y from shared memory, the history sum H (FP32
@@ -354,6 +356,7 @@ __global__ void __launch_bounds__(256) transport_kernel(const FwdArgs<T> A, cons
     constexpr int NC = Packed<DIM>::NC;
     const long long N = A.N;
     const float ccoef = (float)A.courant_coef, climit = (float)A.courant_limit;
+    bool over = false;   // a point above the Courant limit (latched once per block)
     const float ihf[3] = {(float)A.inv_h[0], (float)A.inv_h[1], (float)A.inv_h[2]};
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
         const unsigned pu = (unsigned)p;
@@ -371,9 +374,10 @@ __global__ void __launch_bounds__(256) transport_kernel(const FwdArgs<T> A, cons
             float cr = 0.0f;
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) cr += fabsf((float)A.u[(long long)ax * N + p]) * ihf[ax];
-            if (ccoef * cr > climit) atomicOr(A.flags, 4u);
+            over = over || ccoef * cr > climit;
         }
     }
+    if (__syncthreads_or(over) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(A.flags, 4u);
 }
 
 // Tiled transport pre-pass for grids with n0 % 32 == 0 and n1 % 8 == 0.
@@ -405,6 +409,7 @@ __global__ void __launch_bounds__(kTX * kTY) transport_tiled(const FwdArgs<T> A,
     const T dtT = (T)A.dt, edt = (T)(A.eps * A.dt);
     const bool lap = A.eps != 0.0;
     const float ccoef = (float)A.courant_coef, climit = (float)A.courant_limit;
+    bool over = false;   // a point above the Courant limit (latched once per block)
     const float ihf[3] = {(float)A.inv_h[0], (float)A.inv_h[1], (float)A.inv_h[2]};
     // Both stress levels of the slowest-axis plane sl (z in 3D, a y row in 2D),
     // resolved once per plane: sl may lie up to kHalo outside the grid, where
@@ -514,7 +519,7 @@ __global__ void __launch_bounds__(kTX * kTY) transport_tiled(const FwdArgs<T> A,
             float cr = 0.0f;
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) cr += fabsf((float)u[ax]) * ihf[ax];
-            if (ccoef * cr > climit) atomicOr(A.flags, 4u);
+            over = over || ccoef * cr > climit;
         }
         __syncthreads();
         if (DIM == 3) {
@@ -524,6 +529,260 @@ __global__ void __launch_bounds__(kTX * kTY) transport_tiled(const FwdArgs<T> A,
                 for (int k = 0; k < 4; ++k) qz[c][k] = qz[c][k + 1];
         }
     }
+    if (__syncthreads_or(over) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(A.flags, 4u);
+}
+
+// Staged 3D transport pre-pass (grids with n0 % 32 == 0, n1 % 8 == 0 and
+// n0 n1 < 2^31 whose transported levels, halo planes and velocity start on
+// 16-byte boundaries).  Same tile and z march as transport_tiled, but the
+// values a plane needs are copied global -> shared by cp.async two planes
+// ahead, into one of two stage buffers, so that the loads of planes z+1 and
+// z+2 are in flight while plane z is evaluated and no register holds a load in
+// flight.  For the plane z a stage holds: both stress levels of the block's
+// own 32 x 8 columns at z+2 (the z taps, kept in registers), both levels of the
+// 4 halo rows (y0-2, y0-1, y0+8, y0+9) and of the x halo pairs (x0-2, x0-1 and
+// x0+32, x0+33) at z, and u at z.  Rows move as 16-byte pieces, the x halo as
+// pairs of values.  The copies have fixed roles: warp c < 6 fetches component
+// c's rows (own columns and y halo), warps 6 and 7 the velocity and the x halo,
+// so that every address is a per-thread constant plus a per-plane base.
+// E = 2 sigma^n - sigma^{n-1} is formed once per value into the shared tile.
+// The stencil is applied as 13 per-point coefficients (the upwind3 or central2
+// weights times dt u_a / h_a, with the Laplacian's weights times eps dt / h_a^2)
+// shared by the six components.
+template <typename T>
+struct StagedTile {
+    static constexpr int NC = 6;
+    static constexpr int kPer = 16 / (int)sizeof(T);           // values per 16-byte piece
+    static constexpr int kRowChunks = kTX / kPer;              // pieces of a 32-value row
+    static constexpr int kRowsPerPass = 32 / kRowChunks;       // rows one warp copies per instruction
+    // stage layout (values): col[2][NC][kTY][32], yh[2][NC][4][32], u[3][kTY][32], xh[2][NC][kTY][2][2]
+    static constexpr int kOffYh = 2 * NC * kTY * kTX;
+    static constexpr int kOffU = kOffYh + 2 * NC * 4 * kTX;
+    static constexpr int kOffXh = kOffU + 3 * kTY * kTX;
+    static constexpr int kStageVals = kOffXh + 2 * NC * kTY * 4;
+    static constexpr size_t kStageBytes = (size_t)kStageVals * sizeof(T);
+    static constexpr size_t kTileBytes = (size_t)NC * kSY * kSX * sizeof(T);
+    static constexpr size_t kSmemBytes = 2 * kStageBytes + kTileBytes;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kTX * kTY, sizeof(T) == 4 ? 4 : 2)
+    transport_staged(const FwdArgs<T> A, const int stencil, const int zchunk) {
+    using L = StagedTile<T>;
+    constexpr int NC = L::NC;
+    constexpr int kPer = L::kPer, kRC = L::kRowChunks, kRP = L::kRowsPerPass;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* stage0 = reinterpret_cast<T*>(smem_raw);
+    T (*Es)[kSY][kSX] = reinterpret_cast<T (*)[kSY][kSX]>(smem_raw + 2 * L::kStageBytes);
+    const int tx = threadIdx.x, ty = threadIdx.y;   // ty = warp
+    const int n0 = A.n0, n1 = A.n1, n2 = A.n2;
+    const long long N = A.N;
+    const long long plane = (long long)n0 * n1;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+    const float ccoef = (float)A.courant_coef, climit = (float)A.courant_limit;
+    bool over = false;   // a point above the Courant limit (latched once per block)
+    const float ihf[3] = {(float)A.inv_h[0], (float)A.inv_h[1], (float)A.inv_h[2]};
+    // per-axis stencil scales: g_a = dt u_a (1/h_a)/6 multiplies the derivative
+    // weights, Lw_a = eps dt / h_a^2 the Laplacian's
+    const T ih6[3] = {(T)(A.inv_h[0] / 6.0), (T)(A.inv_h[1] / 6.0), (T)(A.inv_h[2] / 6.0)};
+    const T dtT = (T)A.dt;
+    const T Lw[3] = {(T)(A.eps * A.dt * A.inv_h[0] * A.inv_h[0]), (T)(A.eps * A.dt * A.inv_h[1] * A.inv_h[1]),
+                     (T)(A.eps * A.dt * A.inv_h[2] * A.inv_h[2])};
+    struct PlanePtr {
+        const T* n;
+        const T* m;
+        long long cstride;
+    };
+    // both stress levels of plane sl, -kHalo <= sl < n2 + kHalo: inside the
+    // grid, wrapped, or on a slab the neighbours' planes from the halo buffers
+    auto plane_at = [&](int sl) -> PlanePtr {
+        if ((sl < 0 || sl >= n2) && A.halo_lo) {
+            const T* hb = sl < 0 ? A.halo_lo : A.halo_hi;
+            const long long k = sl < 0 ? sl + A.halo_r : sl - n2;
+            return {hb + k * plane, hb + ((long long)NC * A.halo_r + k) * plane, (long long)A.halo_r * plane};
+        }
+        while (sl < 0) sl += n2;
+        while (sl >= n2) sl -= n2;
+        return {A.sig_n + sl * plane, A.sig_nm1 + sl * plane, N};
+    };
+    // per-thread copy roles (in-plane offsets; fit in 32 bits: n0 n1 < 2^31).
+    // Warps c < NC: offA = own-column row rsub, offB (offB2) = y halo row rsub
+    // (rsub + kRP).  Warps NC, NC + 1 (l = 0..63): offA = u row l / kRC,
+    // offB = x halo pair of row (l >> 1) & 7 on side l & 1, lcb = l >> 4 (the
+    // pair's level * NC + component is lcb + 4 i for its three copies i).
+    const int lane = tx, w = ty;
+    unsigned offA, offB, offB2 = 0;
+    int lcb = 0;
+    if (w < NC) {
+        const int ch = lane % kRC, rsub = lane / kRC;
+        offA = (unsigned)((y0 + rsub) * n0 + x0 + ch * kPer);
+        // y halo rows k: y0-2, y0-1, y0+8, y0+9 wrapped
+        auto gy = [&](int k) {
+            int y = k < 2 ? y0 - 2 + k : y0 + kTY - 2 + k;
+            if (y < 0) y += n1;
+            if (y >= n1) y -= n1;
+            return y;
+        };
+        offB = (unsigned)(gy(rsub) * n0 + x0 + ch * kPer);
+        if (kRP < 4) offB2 = (unsigned)(gy(rsub + kRP) * n0 + x0 + ch * kPer);
+    } else {
+        const int l = lane + 32 * (w - NC);
+        offA = (unsigned)((y0 + l / kRC) * n0 + x0 + (l % kRC) * kPer);
+        const int side = l & 1, r = (l >> 1) & 7;
+        int xs = side ? x0 + kTX : x0 - kHalo;
+        if (xs < 0) xs += n0;
+        if (xs >= n0) xs -= n0;
+        offB = (unsigned)((y0 + r) * n0 + xs);
+        lcb = l >> 4;
+    }
+    auto issue = [&](int st, int z) {
+        T* S = stage0 + (size_t)st * L::kStageVals;
+        if (w < NC) {
+            const int c = w;
+            const int ch = lane % kRC, rsub = lane / kRC;
+            const PlanePtr Pc = plane_at(z + 2);
+            const T* cn = Pc.n + c * Pc.cstride;
+            const T* cm = Pc.m + c * Pc.cstride;
+            // own columns at z + 2: rows rsub + kRP i
+#pragma unroll
+            for (int i = 0; i < kTY / kRP; ++i) {
+                const unsigned o = offA + (unsigned)(i * kRP * n0);
+                const int d = ((c * kTY) + rsub + i * kRP) * kTX + ch * kPer;
+                cp_async16(S + d, cn + o, 16);
+                cp_async16(S + NC * kTY * kTX + d, cm + o, 16);
+            }
+            const T* hn = A.sig_n + (long long)z * plane + c * N;   // plane z is inside the grid
+            const T* hm = A.sig_nm1 + (long long)z * plane + c * N;
+#pragma unroll
+            for (int i = 0; i < (kRP < 4 ? 2 : 1); ++i) {
+                const int k = rsub + i * kRP;
+                if (k < 4) {
+                    const unsigned o = i == 0 ? offB : offB2;
+                    const int d = L::kOffYh + (c * 4 + k) * kTX + ch * kPer;
+                    cp_async16(S + d, hn + o, 16);
+                    cp_async16(S + NC * 4 * kTX + d, hm + o, 16);
+                }
+            }
+        } else {
+            const int l = lane + 32 * (w - NC);
+            const T* ub = A.u + (long long)z * plane;
+            // u rows l / kRC + (64 / kRC) i of the three axes
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+                for (int i = 0; i < kTY * kRC / 64; ++i) {
+                    const unsigned o = offA + (unsigned)(i * (64 / kRC) * n0);
+                    const int d = L::kOffU + (ax * kTY + l / kRC + i * (64 / kRC)) * kTX + (l % kRC) * kPer;
+                    cp_async16(S + d, ub + ax * N + o, 16);
+                }
+            const T* hn = A.sig_n + (long long)z * plane;
+            const T* hm = A.sig_nm1 + (long long)z * plane;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const int lc = lcb + 4 * i;
+                const int lev = lc >= NC, c = lc - (lev ? NC : 0);
+                const T* src = (lev ? hm : hn) + c * N + offB;
+                cp_async_small<2 * sizeof(T)>(S + L::kOffXh + (size_t)(l + 64 * i) * 2, src, 2 * sizeof(T));
+            }
+        }
+    };
+    const int zbeg = blockIdx.z * zchunk;
+    const int zend = min(zbeg + zchunk, n2);
+    const long long q_xy = (tx + x0) + (long long)n0 * (ty + y0);
+    T qz[NC][5];   // E of this column at z-2 .. z+2
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const PlanePtr P = plane_at(zbeg - 2 + k);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const long long o = (long long)c * P.cstride + q_xy;
+            qz[c][k] = (T)2 * __ldg(P.n + o) - __ldg(P.m + o);
+        }
+    }
+    issue(0, zbeg);
+    cp_async_commit();
+    if (zbeg + 1 < zend) issue(1, zbeg + 1);
+    cp_async_commit();
+    for (int z = zbeg, it = 0; z < zend; ++z, ++it) {
+        const T* S = stage0 + (size_t)(it & 1) * L::kStageVals;
+        cp_async_wait<1>();
+        __syncthreads();   // the stage of plane z has landed; the tile is free
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int o = (c * kTY + ty) * kTX + tx;
+            qz[c][4] = (T)2 * S[o] - S[NC * kTY * kTX + o];
+            Es[c][ty + kHalo][tx + kHalo] = qz[c][2];
+        }
+        T u[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) u[ax] = S[L::kOffU + (ax * kTY + ty) * kTX + tx];
+        if (w < NC) {
+            // component w's halo cells: the 4 y rows (lane = x), then the x pairs
+            const int c = w;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int o = L::kOffYh + (c * 4 + k) * kTX + lane;
+                Es[c][k < 2 ? k : kTY + k][lane + kHalo] = (T)2 * S[o] - S[o + NC * 4 * kTX];
+            }
+            const int r = lane >> 2, e = lane & 3;   // e: x0-2, x0-1, x0+32, x0+33
+            const int o = L::kOffXh + ((c * kTY + r) * 2 + (e >> 1)) * 2 + (e & 1);
+            Es[c][r + kHalo][e < 2 ? e : kTX + e] = (T)2 * S[o] - S[o + NC * kTY * 4];
+        }
+        __syncthreads();   // the tile is complete and the stage has been read
+        if (z + 2 < zend) issue(it & 1, z + 2);
+        cp_async_commit();
+        // the 13 stencil coefficients of this point: taps -2, -1, +1, +2 along
+        // each axis and the centre
+        T cf[3][4], c0 = (T)0;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            const T g = dtT * u[ax] * ih6[ax];
+            T wm2, wm1, w0, wp1, wp2;
+            if (stencil == 1) {
+                wm2 = (T)0; wm1 = (T)-3; w0 = (T)0; wp1 = (T)3; wp2 = (T)0;
+            } else if (u[ax] >= (T)0) {
+                wm2 = (T)1; wm1 = (T)-6; w0 = (T)3; wp1 = (T)2; wp2 = (T)0;
+            } else {
+                wm2 = (T)0; wm1 = (T)-2; w0 = (T)-3; wp1 = (T)6; wp2 = (T)-1;
+            }
+            cf[ax][0] = g * wm2;
+            cf[ax][1] = g * wm1 - Lw[ax];
+            cf[ax][2] = g * wp1 - Lw[ax];
+            cf[ax][3] = g * wp2;
+            c0 += g * w0 + (T)2 * Lw[ax];
+        }
+        const long long p = q_xy + plane * z;
+        const int sy = ty + kHalo, sx = tx + kHalo;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            T acc = c0 * qz[c][2];
+            acc += cf[0][0] * Es[c][sy][sx - 2];
+            acc += cf[0][1] * Es[c][sy][sx - 1];
+            acc += cf[0][2] * Es[c][sy][sx + 1];
+            acc += cf[0][3] * Es[c][sy][sx + 2];
+            acc += cf[1][0] * Es[c][sy - 2][sx];
+            acc += cf[1][1] * Es[c][sy - 1][sx];
+            acc += cf[1][2] * Es[c][sy + 1][sx];
+            acc += cf[1][3] * Es[c][sy + 2][sx];
+            acc += cf[2][0] * qz[c][0];
+            acc += cf[2][1] * qz[c][1];
+            acc += cf[2][2] * qz[c][3];
+            acc += cf[2][3] * qz[c][4];
+            A.trans[(long long)c * N + p] = acc;
+        }
+        if (ccoef > 0.0f) {
+            float cr = 0.0f;
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) cr += fabsf((float)u[ax]) * ihf[ax];
+            over = over || ccoef * cr > climit;
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) qz[c][k] = qz[c][k + 1];
+    }
+    cp_async_wait<0>();
+    if (__syncthreads_or(over) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(A.flags, 4u);
 }
 
 // Warps per block of the step kernel: each warp handles NC / kWarps stress
@@ -1027,6 +1286,23 @@ fwd_kernel(const FwdArgs<T> A, const __grid_constant__ TmaPlan tp, const int cla
     if (!use_tma) cp_async_wait<0>();
 }
 
+inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Raises the dynamic shared-memory limit of transport_staged<T> once per
+// device (the attribute belongs to the device's copy of the kernel).
+template <typename T>
+cudaError_t staged_smem_ready() {
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(transport_staged<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)StagedTile<T>::kSmemBytes);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+    return e;
+}
+
 template <typename T, int DIM, bool TRANSPORT, bool COMP, bool PAPER>
 cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s) {
     constexpr int NC = Packed<DIM>::NC;
@@ -1055,8 +1331,19 @@ cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s
         if (a.n0 % kTX == 0 && a.n1 % kTY == 0) {
             const int zchunk = 8;
             const int gz = DIM == 3 ? (a.n2 + zchunk - 1) / zchunk : 1;
-            transport_tiled<T, DIM><<<dim3(a.n0 / kTX, a.n1 / kTY, gz), dim3(kTX, kTY), 0, s>>>(ta, cfg.stencil,
-                                                                                             zchunk);
+            const dim3 grid(a.n0 / kTX, a.n1 / kTY, gz), block(kTX, kTY);
+            bool staged = false;
+            if constexpr (DIM == 3) {
+                staged = (long long)a.n0 * a.n1 < (1ll << 31) && aligned16(ta.sig_n) && aligned16(ta.sig_nm1) &&
+                         aligned16(ta.u) &&
+                         (!ta.halo_lo || (aligned16(ta.halo_lo) && aligned16(ta.halo_hi)));
+                if (staged) {
+                    e = staged_smem_ready<T>();
+                    if (e != cudaSuccess) return e;
+                    transport_staged<T><<<grid, block, StagedTile<T>::kSmemBytes, s>>>(ta, cfg.stencil, zchunk);
+                }
+            }
+            if (!staged) transport_tiled<T, DIM><<<grid, block, 0, s>>>(ta, cfg.stencil, zchunk);
         } else {
             const int threads = 256;
             long long blocks = (a.N + threads - 1) / threads;

@@ -75,6 +75,7 @@ RAGGED = [
     # sizes with n0 % 32 == 0 and n1 % 8 == 0 take the tiled transport pre-pass
     (3, (32, 16, 10), 0.6, 8, True, 0.01, 0),
     (3, (64, 8, 3), 0.4, 6, True, 0.0, 1),
+    (3, (32, 8, 1), 0.5, 4, True, 0.0, 1),
     (2, (64, 24), 0.5, 8, True, 0.02, 0),
 ]
 

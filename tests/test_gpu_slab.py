@@ -98,6 +98,76 @@ def test_slabs_equal_whole_domain(dim, n, slabs, eps, stencil, precision):
     assert all(f == flags_whole for f in flags)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_unaligned_velocity_and_halo_planes(precision):
+    """The 3D tiled pre-pass stages whole rows in 16-byte pieces; a velocity or
+    halo buffer that does not start on a 16-byte boundary is served by the
+    pre-pass that loads value by value, with the same arithmetic.  Both paths,
+    whole domain and two slabs, give the stress of the aligned whole-domain
+    run."""
+    import torch
+    from paper_2411_17294_gb300 import slab, tfs
+    dim, n, slabs = 3, (64, 16, 12), (6, 6)
+    alpha, Wi, beta, dt, m, steps = 0.6, 1.3, 0.4, 2e-3, 8, 5
+    L = [0.25 * k for k in n]
+    mu, w = soe.soe_nnls(alpha, dt, steps * dt, m)
+    u, kap = inputs.spectral_velocity(dim, n, 4, seed=53)
+    case = dict(dim=dim, n=n, alpha=alpha, dt=dt, mu=mu, w=w, eps=0.01, stencil=0, L=L)
+    u = stable_velocity(case, u)
+    sig0 = inputs.random_stress(dim, n, 54)
+    dev = torch.device("cuda", 0)
+    dtype = torch.float64 if precision == 0 else torch.float32
+    t = lambda a: torch.as_tensor(np.asarray(a), dtype=dtype, device=dev).contiguous()
+
+    def shifted(x):
+        """x in a buffer that starts one element past a 16-byte boundary"""
+        buf = torch.zeros(x.numel() + 1, dtype=x.dtype, device=x.device)
+        v = buf[1:].view(x.shape)
+        v.copy_(x)
+        assert v.data_ptr() % 16 != 0
+        return v
+
+    def solver(grid, lengths):
+        return tfs.Solver(dim, grid, alpha, Wi, beta, dt, m=m, precision=precision, mu=mu, w=w, eps=0.01,
+                          stencil=0, transport=True, L=lengths)
+
+    def whole_run(ut):
+        s = solver(n, L)
+        s.set_state(t(sig0))
+        kt = t(kap)
+        for _ in range(steps):
+            s.step(kt, kt, ut)
+        out = s.stress().cpu().numpy()
+        s.close()
+        return out
+
+    ref = whole_run(t(u))
+    got_u = whole_run(shifted(t(u)))
+    parts, k0 = [], 0
+    for ns in slabs:
+        s = solver(tuple(n[:-1]) + (ns,), L[:-1] + [0.25 * ns])
+        s.set_state(t(_slice(sig0, dim, n, k0, k0 + ns)))
+        parts.append((s, t(_slice(kap, dim, n, k0, k0 + ns)), t(_slice(u, dim, n, k0, k0 + ns))))
+        k0 += ns
+    for _ in range(steps):
+        sends = []
+        for s, _, _ in parts:
+            lo, hi = s.halo_buffers()
+            s.get_halo(lo, hi)
+            sends.append((lo, hi))
+        recvs = slab.exchange_local(sends)
+        for (s, ks, us), (rlo, rhi) in zip(parts, recvs):
+            s.step_slab(ks, ks, us, shifted(rlo), shifted(rhi))
+    got_slab = np.concatenate([s.stress().cpu().numpy() for s, _, _ in parts], axis=1)
+    for s, _, _ in parts:
+        s.close()
+    scale = np.max(np.abs(ref))
+    assert scale > 0
+    tol = 1e-13 if precision == 0 else 1e-6
+    for got in (got_u, got_slab):
+        assert np.max(np.abs(got - ref)) <= tol * scale
+
+
 def test_slab_entry_points_refuse_what_they_do_not_serve():
     import torch
     from paper_2411_17294_gb300 import tfs
