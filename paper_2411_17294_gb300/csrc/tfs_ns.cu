@@ -12,11 +12,13 @@
 // multiplies mode k by i k_a (zero at the Nyquist wavenumber of the axis), the
 // Laplacian is the square of that, so Poisson and Helmholtz are divisions per
 // mode and the result is divergence-free to rounding.  Products are formed on
-// the grid.  The transforms are this file's own: a radix-2 Stockham autosort
-// FFT of each row in shared memory (the formulation of Govindaraju et al.,
+// the grid.  The transforms are this file's own: a Stockham autosort FFT of
+// each row in shared memory (the formulation of Govindaraju et al.,
 // "High performance discrete Fourier transforms on graphics processors",
-// SC 2008), FP64 complex, and a tiled transpose between the two axes; spectral
-// arrays are kept transposed, [kx][ky].
+// SC 2008) in radix 4, FP64 complex, and a tiled transpose between the two axes; spectral
+// arrays are kept transposed, [kx][ky].  Real fields go two to a complex
+// transform (f + i g forward, split by the Hermitian symmetry of real spectra;
+// A + i B inverse), so a step takes 6 two-dimensional transforms, not 11.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -45,12 +47,13 @@ __device__ __forceinline__ double2 cimul(double d, double2 a) { return make_doub
 // DFT of each row of length n (a power of two, 2 .. kMaxLen) with
 // exp(-+ 2 pi i j k / n) (forward / inverse), times `scale`; one block per row,
 // rows of `in` and `out` n elements apart (in == out allowed: a row is read
-// whole first).  tw[t] = exp(-2 pi i t / n), t < n/2 (computed once on the
-// host in FP64).  Stockham autosort: stage Ns = 1, 2, 4, ... combines
-// butterflies of span Ns from the first and second halves, the second operand
-// turned by exp(-+ pi i k / Ns) = tw[k n / (2 Ns)], k = j mod Ns, and writes
-// them to expand(j) = (j / Ns) 2 Ns + j % Ns and expand(j) + Ns, ping-ponging
-// between two shared buffers; the result is in natural order.
+// whole first).  tw[t] = exp(-2 pi i t / n), t < n (computed once on the host
+// in FP64).  Stockham autosort, radix 4: stage Ns = 1, 4, 16, ... takes the
+// four operands j + r n/4 (r = 0..3) of butterfly j, turns operand r by
+// exp(-+ 2 pi i r k / (4 Ns)) = tw[r k n / (4 Ns)], k = j mod Ns, applies the
+// 4-point DFT and writes output r to (j / Ns) 4 Ns + k + r Ns; a length that is
+// not a power of four ends with one radix-2 stage (Ns = n/2).  The buffers
+// ping-pong in shared memory; the result is in natural order.
 __global__ void __launch_bounds__(kNsThreads) fft_rows_kernel(const double2* in, double2* out, int n,
                                                               const double2* __restrict__ tw, int inverse,
                                                               double scale) {
@@ -60,8 +63,41 @@ __global__ void __launch_bounds__(kNsThreads) fft_rows_kernel(const double2* in,
     const double2* src = in + (long long)blockIdx.x * n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = src[i];
     __syncthreads();
-    const int half = n >> 1;
-    for (int ns = 1; ns < n; ns <<= 1) {
+    const int quarter = n >> 2;
+    int ns = 1;
+    for (; 4 * ns <= n; ns <<= 2) {
+        const int step = n / (4 * ns);
+        for (int j = threadIdx.x; j < quarter; j += blockDim.x) {
+            const int k = j & (ns - 1);
+            const double2 v0 = x[j];
+            double2 v1 = x[j + quarter], v2 = x[j + 2 * quarter], v3 = x[j + 3 * quarter];
+            if (ns > 1) {   // the first stage's twiddles are all 1
+                double2 t1 = __ldg(tw + k * step), t2 = __ldg(tw + 2 * k * step), t3 = __ldg(tw + 3 * k * step);
+                if (inverse) {
+                    t1.y = -t1.y;
+                    t2.y = -t2.y;
+                    t3.y = -t3.y;
+                }
+                v1 = cmul(v1, t1);
+                v2 = cmul(v2, t2);
+                v3 = cmul(v3, t3);
+            }
+            const double2 a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3), d = csub(v1, v3);
+            // (v1 - v3) times -i (forward) or +i (inverse)
+            const double2 a3 = inverse ? make_double2(-d.y, d.x) : make_double2(d.y, -d.x);
+            const int o = ((j - k) << 2) + k;
+            y[o] = cadd(a0, a2);
+            y[o + ns] = cadd(a1, a3);
+            y[o + 2 * ns] = csub(a0, a2);
+            y[o + 3 * ns] = csub(a1, a3);
+        }
+        __syncthreads();
+        double2* tmp = x;
+        x = y;
+        y = tmp;
+    }
+    if (ns < n) {   // radix-2 stage, Ns = n/2
+        const int half = n >> 1;
         const int step = half / ns;
         for (int j = threadIdx.x; j < half; j += blockDim.x) {
             const int k = j & (ns - 1);
@@ -79,7 +115,10 @@ __global__ void __launch_bounds__(kNsThreads) fft_rows_kernel(const double2* in,
         y = tmp;
     }
     double2* dst = out + (long long)blockIdx.x * n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = cscale(x[i], scale);
+    if (scale == 1.0)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = x[i];
+    else
+        for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = cscale(x[i], scale);
 }
 
 // out[c][r] = in[r][c] for a rows x cols complex matrix (32 x 32 tiles)
@@ -97,19 +136,46 @@ __global__ void transpose_kernel(const double2* in, double2* out, int rows, int 
     }
 }
 
+// Two real fields per complex transform: z = f + i g on the grid (g absent: 0).
 template <typename T>
-__global__ void real_to_complex_kernel(const T* f, double2* z, long long n) {
+__global__ void pack_pair_kernel(const T* f, const T* g, double2* z, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        z[i] = make_double2((double)f[i], 0.0);
+        z[i] = make_double2((double)f[i], g ? (double)g[i] : 0.0);
 }
 
-// real part of z into the FP64 field d (when given) and the caller's field t (when given)
+// Spectra of the two real fields of Z = DFT(f + i g) ([kx][ky], row kx of n1
+// entries): with W = conj(Z(-k)), F = (Z + W)/2 and G = (Z - W)/(2i), the
+// Hermitian and anti-Hermitian parts (G not written when absent).
+__global__ void unpack_pair_kernel(const double2* Z, double2* F, double2* G, int n0, int n1) {
+    const long long n = (long long)n0 * n1;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q / n1), j = (int)(q - (long long)i * n1);
+        const long long qm = (long long)(i == 0 ? 0 : n0 - i) * n1 + (j == 0 ? 0 : n1 - j);
+        const double2 z = Z[q], zm = Z[qm];
+        F[q] = make_double2(0.5 * (z.x + zm.x), 0.5 * (z.y - zm.y));
+        if (G) G[q] = make_double2(0.5 * (z.y + zm.y), -0.5 * (z.x - zm.x));
+    }
+}
+
+// Z = A + i B in spectral space (B absent: 0), for one inverse transform of two
+// real fields: the real part of the result is a, the imaginary part b
+__global__ void pack_spectra_kernel(const double2* A, const double2* B, double2* Z, long long n) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const double2 a = A[q];
+        Z[q] = B ? make_double2(a.x - B[q].y, a.y + B[q].x) : a;
+    }
+}
+
+// real and imaginary parts of z into the FP64 fields da, db and the caller's
+// fields ta, tb (each when given)
 template <typename T>
-__global__ void complex_to_real_kernel(const double2* z, double* d, T* t, long long n) {
+__global__ void unpack_grid_kernel(const double2* z, double* da, T* ta, double* db, T* tb, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const double v = z[i].x;
-        if (d) d[i] = v;
-        if (t) t[i] = (T)v;
+        const double2 v = z[i];
+        if (da) da[i] = v.x;
+        if (ta) ta[i] = (T)v.x;
+        if (db) db[i] = v.y;
+        if (tb) tb[i] = (T)v.y;
     }
 }
 
@@ -118,7 +184,8 @@ __global__ void complex_to_real_kernel(const double2* z, double* d, T* t, long l
 // zero at the Nyquist index of each axis.
 __device__ __forceinline__ void wavenumbers(long long idx, int n0, int n1, double sx, double sy, double& dx,
                                             double& dy) {
-    const int i = (int)(idx / n1), j = (int)(idx - (long long)(idx / n1) * n1);
+    const int qi = (int)idx;   // n0 n1 <= kMaxLen^2
+    const int i = qi / n1, j = qi - i * n1;
     dx = i == n0 / 2 ? 0.0 : (double)(i < n0 / 2 ? i : i - n0) * sx;
     dy = j == n1 / 2 ? 0.0 : (double)(j < n1 / 2 ? j : j - n1) * sy;
 }
@@ -182,37 +249,38 @@ struct NsModes {
     double2 *ox, *oy;
 };
 
+// Per mode, with h = (b1 u^n + b2 u^{n-1})/dt and w = h + E(conv - div sigma):
+// Xi = h + E(nu curl curl u + conv - div sigma), p = i k.Xi / k^2 (Lap p =
+// -div Xi), (b0/dt + nu k^2) u^{n+1} = -i k p - w.  In Fourier space
+// k.(curl curl u) = k.(k^2 u - k (k.u)) = 0 for every k, so k.Xi = k.w and
+//   u^{n+1} = -(w - k (k.w)/k^2) / (b0/dt + nu k^2),
+// the projection of -w onto divergence-free fields, which the kernel forms
+// directly (the rotational term changes the pressure of the scheme only on a
+// bounded domain).  Mode 0: u^{n+1} = -w dt/b0.
 __global__ void ns_update_kernel(const NsModes M, int n0, int n1, double sx, double sy, double nu, double dt) {
+    const double idt = 1.0 / dt, b0dt = kB0 / dt;
     NS_LOOP(q, (long long)n0 * n1) {
         double dx, dy;
         wavenumbers(q, n0, n1, sx, sy, dx, dy);
         const double k2 = dx * dx + dy * dy;
-        // curl curl u = grad div u - Lap u at both levels
-        const double2 diva = cadd(cimul(dx, M.ax[q]), cimul(dy, M.ay[q]));
-        const double2 divb = cadd(cimul(dx, M.bx[q]), cimul(dy, M.by[q]));
-        const double2 cax = cadd(cimul(dx, diva), cscale(M.ax[q], k2));
-        const double2 cay = cadd(cimul(dy, diva), cscale(M.ay[q], k2));
-        const double2 cbx = cadd(cimul(dx, divb), cscale(M.bx[q], k2));
-        const double2 cby = cadd(cimul(dy, divb), cscale(M.by[q], k2));
-        const double2 hx = cscale(cadd(cscale(M.ax[q], kB1), cscale(M.bx[q], kB2)), 1.0 / dt);
-        const double2 hy = cscale(cadd(cscale(M.ay[q], kB1), cscale(M.by[q], kB2)), 1.0 / dt);
-        auto ext = [](double2 f0, double2 f1) { return csub(cscale(f0, 2.0), f1); };
-        // Xi = hist + E(nu curl curl u + conv - div sigma)
-        const double2 xix = cadd(hx, ext(csub(cadd(cscale(cax, nu), M.c0x[q]), M.d0x[q]),
-                                         csub(cadd(cscale(cbx, nu), M.c1x[q]), M.d1x[q])));
-        const double2 xiy = cadd(hy, ext(csub(cadd(cscale(cay, nu), M.c0y[q]), M.d0y[q]),
-                                         csub(cadd(cscale(cby, nu), M.c1y[q]), M.d1y[q])));
-        // Lap p = -div Xi (mean zero)
-        double2 p = make_double2(0.0, 0.0);
-        if (k2 > 0.0) p = cscale(cadd(cimul(dx, xix), cimul(dy, xiy)), 1.0 / k2);
-        // (b0/dt + nu k2) u^{n+1} = -grad p - hist + E(-conv + div sigma)
-        const double inv = 1.0 / (kB0 / dt + nu * k2);
-        const double2 rx = cadd(csub(csub(make_double2(0.0, 0.0), cimul(dx, p)), hx),
-                                ext(csub(M.d0x[q], M.c0x[q]), csub(M.d1x[q], M.c1x[q])));
-        const double2 ry = cadd(csub(csub(make_double2(0.0, 0.0), cimul(dy, p)), hy),
-                                ext(csub(M.d0y[q], M.c0y[q]), csub(M.d1y[q], M.c1y[q])));
-        M.ox[q] = cscale(rx, inv);
-        M.oy[q] = cscale(ry, inv);
+        auto wcomp = [&](double2 a, double2 b, double2 c0, double2 c1, double2 d0, double2 d1) {
+            const double2 h = cscale(cadd(cscale(a, kB1), cscale(b, kB2)), idt);
+            return cadd(h, csub(cscale(csub(c0, d0), 2.0), csub(c1, d1)));
+        };
+        double2 wx = wcomp(M.ax[q], M.bx[q], M.c0x[q], M.c1x[q], M.d0x[q], M.d1x[q]);
+        double2 wy = wcomp(M.ay[q], M.by[q], M.c0y[q], M.c1y[q], M.d0y[q], M.d1y[q]);
+        double inv = dt / kB0;
+        if (k2 > 0.0) {
+            // one division gives both 1/k^2 and 1/(b0/dt + nu k^2)
+            const double den = b0dt + nu * k2;
+            const double r = 1.0 / (k2 * den);
+            const double2 s = cscale(cadd(cscale(wx, dx), cscale(wy, dy)), den * r);   // (k.w)/k^2
+            wx = csub(wx, cscale(s, dx));
+            wy = csub(wy, cscale(s, dy));
+            inv = k2 * r;
+        }
+        M.ox[q] = cscale(wx, -inv);
+        M.oy[q] = cscale(wy, -inv);
     }
 }
 
@@ -241,7 +309,7 @@ struct tfs_ns_ctx {
     double* u = nullptr;
     double* kap = nullptr;
     double* conv = nullptr;
-    double2* tw0 = nullptr;       // exp(-2 pi i t / n0), t < n0/2; and for n1
+    double2* tw0 = nullptr;       // exp(-2 pi i t / n0), t < n0; and for n1
     double2* tw1 = nullptr;
     std::vector<double2> tw_host; // both tables, uploaded by tfs_ns_set_state
     int cur = 0;                  // slot of level n (n-1 in the other)
@@ -257,7 +325,7 @@ size_t ns_up(size_t v) { return (v + kNsAlign - 1) / kNsAlign * kNsAlign; }
 
 size_t ns_bytes(const tfs_ns_ctx* h) {
     const size_t cplx = ns_up(sizeof(double2) * (size_t)h->N), real = ns_up(sizeof(double) * (size_t)h->N);
-    return 21 * cplx + 8 * real + ns_up(sizeof(double2) * (size_t)(h->n0 / 2 + h->n1 / 2));
+    return 21 * cplx + 8 * real + ns_up(sizeof(double2) * (size_t)(h->n0 + h->n1));
 }
 
 void ns_layout(tfs_ns_ctx* h) {
@@ -280,7 +348,7 @@ void ns_layout(tfs_ns_ctx* h) {
     h->conv = (double*)p;
     p += 2 * real;
     h->tw0 = (double2*)p;
-    h->tw1 = h->tw0 + h->n0 / 2;
+    h->tw1 = h->tw0 + h->n0;
 }
 
 unsigned ns_grid(long long n) {
@@ -301,25 +369,35 @@ cudaError_t transpose(const double2* in, double2* out, int rows, int cols, cudaS
     return cudaGetLastError();
 }
 
-// spectral [kx][ky] of a real grid field [y][x]
+// spectra [kx][ky] of two real grid fields [y][x] (g absent: G not formed),
+// by one complex transform of f + i g
 template <typename T>
-cudaError_t fft2_real(tfs_ns_ctx* h, const T* f, double2* out, cudaStream_t s) {
-    real_to_complex_kernel<T><<<ns_grid(h->N), kNsThreads, 0, s>>>(f, h->tmp[0], h->N);
+cudaError_t fft2_pair(tfs_ns_ctx* h, const T* f, const T* g, double2* F, double2* G, cudaStream_t s) {
+    pack_pair_kernel<T><<<ns_grid(h->N), kNsThreads, 0, s>>>(f, g, h->tmp[0], h->N);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = fft_rows(h, h->tmp[0], h->tmp[0], h->n0, h->n1, -1.0, 1.0, s);
-    if (e == cudaSuccess) e = transpose(h->tmp[0], out, h->n1, h->n0, s);
-    if (e == cudaSuccess) e = fft_rows(h, out, out, h->n1, h->n0, -1.0, 1.0, s);
+    if (e == cudaSuccess) e = transpose(h->tmp[0], h->tmp[1], h->n1, h->n0, s);
+    if (e == cudaSuccess) e = fft_rows(h, h->tmp[1], h->tmp[1], h->n1, h->n0, -1.0, 1.0, s);
+    if (e == cudaSuccess) {
+        unpack_pair_kernel<<<ns_grid(h->N), kNsThreads, 0, s>>>(h->tmp[1], F, G, h->n0, h->n1);
+        e = cudaGetLastError();
+    }
     return e;
 }
 
-// real grid field [y][x] of the spectral [kx][ky] (into d and/or t)
+// real grid fields [y][x] of the spectra A and B ([kx][ky], both Hermitian; B
+// may be absent), by one inverse transform of A + i B: a into da and/or ta, b
+// into db and/or tb
 template <typename T>
-cudaError_t ifft2_real(tfs_ns_ctx* h, const double2* in, double* d, T* t, cudaStream_t s) {
-    cudaError_t e = fft_rows(h, in, h->tmp[0], h->n1, h->n0, 1.0, 1.0, s);
+cudaError_t ifft2_pair(tfs_ns_ctx* h, const double2* A, const double2* B, double* da, T* ta, double* db, T* tb,
+                       cudaStream_t s) {
+    pack_spectra_kernel<<<ns_grid(h->N), kNsThreads, 0, s>>>(A, B, h->tmp[0], h->N);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = fft_rows(h, h->tmp[0], h->tmp[0], h->n1, h->n0, 1.0, 1.0, s);
     if (e == cudaSuccess) e = transpose(h->tmp[0], h->tmp[1], h->n0, h->n1, s);
     if (e == cudaSuccess) e = fft_rows(h, h->tmp[1], h->tmp[1], h->n0, h->n1, 1.0, 1.0 / (double)h->N, s);
     if (e == cudaSuccess) {
-        complex_to_real_kernel<T><<<ns_grid(h->N), kNsThreads, 0, s>>>(h->tmp[1], d, t, h->N);
+        unpack_grid_kernel<T><<<ns_grid(h->N), kNsThreads, 0, s>>>(h->tmp[1], da, ta, db, tb, h->N);
         e = cudaGetLastError();
     }
     return e;
@@ -331,14 +409,14 @@ template <typename T>
 cudaError_t grid_fields(tfs_ns_ctx* h, double2* ux, double2* uy, double* u, double* kap, T* uo, T* ko,
                         cudaStream_t s) {
     const long long N = h->N;
-    cudaError_t e = ifft2_real<T>(h, ux, u, uo, s);
-    if (e == cudaSuccess) e = ifft2_real<T>(h, uy, u + N, uo ? uo + N : nullptr, s);
+    cudaError_t e = ifft2_pair<T>(h, ux, uy, u, uo, u + N, uo ? uo + N : nullptr, s);
     if (e != cudaSuccess) return e;
     ns_gradient_kernel<<<ns_grid(N), kNsThreads, 0, s>>>(ux, uy, h->gh[0], h->gh[1], h->gh[2], h->gh[3], h->n0, h->n1,
                                                          h->sx, h->sy);
     e = cudaGetLastError();
-    for (int c = 0; c < 4 && e == cudaSuccess; ++c)
-        e = ifft2_real<T>(h, h->gh[c], kap + c * N, ko ? ko + c * N : nullptr, s);
+    for (int c = 0; c < 4 && e == cudaSuccess; c += 2)
+        e = ifft2_pair<T>(h, h->gh[c], h->gh[c + 1], kap + c * N, ko ? ko + c * N : nullptr, kap + (c + 1) * N,
+                          ko ? ko + (c + 1) * N : nullptr, s);
     return e;
 }
 
@@ -346,8 +424,7 @@ cudaError_t grid_fields(tfs_ns_ctx* h, double2* ux, double2* uy, double* u, doub
 cudaError_t convection(tfs_ns_ctx* h, const double* u, const double* kap, double2* cx, double2* cy, cudaStream_t s) {
     ns_convection_kernel<<<ns_grid(h->N), kNsThreads, 0, s>>>(u, kap, h->conv, h->conv + h->N, h->N);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = fft2_real<double>(h, h->conv, cx, s);
-    if (e == cudaSuccess) e = fft2_real<double>(h, h->conv + h->N, cy, s);
+    if (e == cudaSuccess) e = fft2_pair<double>(h, h->conv, h->conv + h->N, cx, cy, s);
     return e;
 }
 
@@ -357,16 +434,14 @@ int ns_set_state(tfs_ns_ctx* h, const T* u0, const T* uprev, cudaStream_t s) {
     const int c = h->cur, o = 1 - c;
     cudaError_t e = cudaMemcpyAsync(h->tw0, h->tw_host.data(), sizeof(double2) * h->tw_host.size(),
                                     cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = fft2_real<T>(h, u0, h->uh[c][0], s);
-    if (e == cudaSuccess) e = fft2_real<T>(h, u0 + N, h->uh[c][1], s);
+    if (e == cudaSuccess) e = fft2_pair<T>(h, u0, u0 + N, h->uh[c][0], h->uh[c][1], s);
     if (e == cudaSuccess) {
         ns_project_kernel<<<ns_grid(N), kNsThreads, 0, s>>>(h->uh[c][0], h->uh[c][1], h->n0, h->n1, h->sx, h->sy);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && uprev) {
         // the given level n-1 and its explicit terms (no stress)
-        e = fft2_real<T>(h, uprev, h->uh[o][0], s);
-        if (e == cudaSuccess) e = fft2_real<T>(h, uprev + N, h->uh[o][1], s);
+        e = fft2_pair<T>(h, uprev, uprev + N, h->uh[o][0], h->uh[o][1], s);
         if (e == cudaSuccess) {
             ns_project_kernel<<<ns_grid(N), kNsThreads, 0, s>>>(h->uh[o][0], h->uh[o][1], h->n0, h->n1, h->sx, h->sy);
             e = cudaGetLastError();
@@ -394,7 +469,8 @@ int ns_step(tfs_ns_ctx* h, const T* sigma, T* u_out, T* kap_out, cudaStream_t s)
     // explicit terms of level n: convection from the stored grid fields, stress divergence
     cudaError_t e = convection(h, h->u, h->kap, h->ch[c][0], h->ch[c][1], s);
     if (e == cudaSuccess && sigma) {
-        for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = fft2_real<T>(h, sigma + k * N, h->sh[k], s);
+        e = fft2_pair<T>(h, sigma, sigma + N, h->sh[0], h->sh[1], s);
+        if (e == cudaSuccess) e = fft2_pair<T>(h, sigma + 2 * N, (const T*)nullptr, h->sh[2], nullptr, s);
         if (e == cudaSuccess) {
             ns_divstress_kernel<<<ns_grid(N), kNsThreads, 0, s>>>(h->sh[0], h->sh[1], h->sh[2], h->dh[c][0],
                                                                   h->dh[c][1], h->n0, h->n1, h->sx, h->sy);
@@ -447,9 +523,9 @@ int tfs_ns_create(tfs_ns_handle* out, int n0, int n1, double L0, double L1, doub
     h->nu = beta / Re;
     h->dt = dt;
     h->precision = precision;
-    // twiddle tables exp(-2 pi i t / n), t < n/2, of both axes (FP64, host)
+    // twiddle tables exp(-2 pi i t / n), t < n, of both axes (FP64, host)
     for (int n : {n0, n1})
-        for (int t = 0; t < n / 2; ++t) {
+        for (int t = 0; t < n; ++t) {
             const double a = -2.0 * 3.14159265358979323846 * (double)t / (double)n;
             h->tw_host.push_back(make_double2(std::cos(a), std::sin(a)));
         }
