@@ -798,12 +798,48 @@ struct StepShape {
 // refilled right after the history sums (QR variant of the step kernel).
 constexpr int kQR = 32;
 
-// One tile.  QR (FP32 storage, stress form, alpha < 1, m <= kQR): the Q_j of a
-// thread's components stay in registers and the solving warp copies its
-// kappa and sigma0 values out of the stage before the hook, so the hook may
-// refill the whole stage buffer with the next tile while this one is solved
-// and pushed forward; otherwise Q_j is stored over level n-1 in the stage and
-// the hook may refill only the level-n mode planes.
+// Packed index of the symmetric pair (a, b) (inverse of Packed<DIM>::I, J)
+template <int DIM>
+__device__ __forceinline__ int packed_index(int a, int b) {
+    if (a == b) return DIM == 2 ? 2 * a : a;
+    if (DIM == 2) return 1;
+    return a + b == 3 ? 3 : (a + b == 2 ? 4 : 5);   // yz, xz, xy
+}
+
+// Right-hand side component r of the paper's variable in FP32 storage (the
+// solving warp's system):
+//   -b1 Phi^n - b2 Phi^{n-1} + dt G (kappa* + kappa*^T) Psi0 [- A] + dt (L(kappa*) h - h/Wi)
+// Kat(a, b): kappa*_ab in double-float; Hat(a, b): the leading part of the
+// history sum h_ab.  One definition for the solving warp (all r, values in
+// registers) and for the per-warp form of the register variant (its own r,
+// values read from shared memory), so both give the same bits.
+template <int DIM, bool TRANSPORT, typename KA, typename HA>
+__device__ __forceinline__ f2 paper_rhs_f32(const FwdArgs<float>& A, const StageMap& S, const float* buf, int lane,
+                                            KA Kat, HA Hat, int r) {
+    constexpr int NC = Packed<DIM>::NC;
+    const int i = Packed<DIM>::I(r), j = Packed<DIM>::J(r);
+    const f2 src{A.src_f2.hi, A.src_f2.lo};
+    const float dtf = A.dt_f2.hi, iwi = (float)A.inv_wi;
+    const float pn = buf[(S.sig + r) * kTile + lane];
+    const float pm = buf[(S.sig + NC + r) * kTile + lane];
+    f2 v = two_sum_f2(2.0f * pn, -0.5f * pm);
+    v = f2_add(v, f2_mul(src, f2_add(Kat(i, j), Kat(j, i))));
+    if constexpr (TRANSPORT) v = f2_add_f(v, -buf[(S.tr + r) * kTile + lane]);
+    // the operator on h enters scaled by dt: float accuracy suffices
+    float lh = -iwi * Hat(i, j);
+#pragma unroll
+    for (int l = 0; l < DIM; ++l) lh = __fmaf_rn(Kat(i, l).hi, Hat(l, j), __fmaf_rn(Hat(i, l), Kat(j, l).hi, lh));
+    return f2_add_f(v, dtf * lh);
+}
+
+// One tile.  QR (FP32 storage, alpha < 1, m <= kQR): the Q_j of a thread's
+// components stay in registers and the solving warp copies its kappa and
+// sigma0 values out of the stage before the hook (in the paper's variable every
+// warp first forms its components' right-hand side from the stage, kept in
+// sD until the solve), so the hook may refill the whole stage buffer with the
+// next tile while this one is solved and pushed forward; otherwise Q_j is
+// stored over level n-1 in the stage and the hook may refill only the level-n
+// mode planes.
 template <typename T, int DIM, bool TRANSPORT, bool COMP, bool PAPER, bool QR, typename Hook>
 __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap& S, T* buf, long long t0,
                                              int classic, void* sR_raw, float* sD, Hook after_pass1) {
@@ -811,7 +847,7 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
     constexpr int W = StepShape<DIM>::W;
     constexpr int CPW = StepShape<DIM>::CPW;
     constexpr bool F32 = sizeof(T) == 4;
-    static_assert(!QR || (F32 && !PAPER), "the register variant serves the FP32 stress form");
+    static_assert(!QR || F32, "the register variant serves FP32 storage");
     float qr[QR ? CPW : 1][QR ? kQR : 1];   // Q_j in registers (QR)
     const int lane = threadIdx.x;
     const int w = threadIdx.y;
@@ -993,6 +1029,23 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
         if constexpr (QR) return km_r[i];
         else return (float)buf[(S.km + i) * kTile + lane];
     };
+    if constexpr (PAPER && QR) {
+        // every h is in sR: each warp forms its components' right-hand side
+        // from the stage (into sD, which the solving warp reads before it
+        // writes its own values there)
+        __syncthreads();
+        const f2* sH = reinterpret_cast<const f2*>(sR_raw);
+        const float* fb = reinterpret_cast<const float*>(buf);
+        auto Kat = [&](int a, int b) {
+            return two_sum_f2(2.0f * fb[(S.kn + a * DIM + b) * kTile + lane], -fb[(S.km + a * DIM + b) * kTile + lane]);
+        };
+        auto Hat = [&](int a, int b) { return sH[packed_index<DIM>(a, b) * kTile + lane].hi; };
+#pragma unroll
+        for (int cc = 0; cc < CPW; ++cc) {
+            const int c = w + cc * W;
+            reinterpret_cast<f2*>(sD)[c * kTile + lane] = paper_rhs_f32<DIM, TRANSPORT>(A, S, fb, lane, Kat, Hat, c);
+        }
+    }
     __syncthreads();
     // level n of the mode planes (QR: the whole stage) is no longer read in this tile
     after_pass1();
@@ -1014,39 +1067,35 @@ __device__ __forceinline__ void compute_tile(const FwdArgs<T>& A, const StageMap
                 for (int a = 0; a < DIM; ++a)
 #pragma unroll
                     for (int b = 0; b < DIM; ++b) {
-                        K[a][b] = two_sum_f2(2.0f * (float)buf[(S.kn + a * DIM + b) * kTile + lane],
-                                             -(float)buf[(S.km + a * DIM + b) * kTile + lane]);
+                        K[a][b] = two_sum_f2(2.0f * kn_at(a * DIM + b), -km_at(a * DIM + b));
                         Kf[a][b] = K[a][b].hi;
                     }
                 const f2* sH = reinterpret_cast<const f2*>(sR_raw);
                 f2 h[NC], R[NC], x[NC];
-                float Hs[3][3];
+                if constexpr (QR) {
+                    // h is read after the solve (fewer live registers during it)
 #pragma unroll
-                for (int r = 0; r < NC; ++r) {
-                    h[r] = sH[r * kTile + lane];
-                    Hs[Packed<DIM>::I(r)][Packed<DIM>::J(r)] = h[r].hi;
-                    Hs[Packed<DIM>::J(r)][Packed<DIM>::I(r)] = h[r].hi;
-                }
-                const f2 src{A.src_f2.hi, A.src_f2.lo};
-                const float dtf = A.dt_f2.hi, iwi = (float)A.inv_wi;
+                    for (int r = 0; r < NC; ++r) R[r] = reinterpret_cast<const f2*>(sD)[r * kTile + lane];
+                } else {
+                    float Hs[3][3];
 #pragma unroll
-                for (int r = 0; r < NC; ++r) {
-                    const int i = Packed<DIM>::I(r), j = Packed<DIM>::J(r);
-                    const float pn = (float)buf[(S.sig + r) * kTile + lane];
-                    const float pm = (float)buf[(S.sig + NC + r) * kTile + lane];
-                    f2 v = two_sum_f2(2.0f * pn, -0.5f * pm);
-                    v = f2_add(v, f2_mul(src, f2_add(K[i][j], K[j][i])));
-                    if constexpr (TRANSPORT) v = f2_add_f(v, -(float)buf[(S.tr + r) * kTile + lane]);
-                    // the operator on h enters scaled by dt: float accuracy suffices
-                    float lh = -iwi * Hs[i][j];
+                    for (int r = 0; r < NC; ++r) {
+                        h[r] = sH[r * kTile + lane];
+                        Hs[Packed<DIM>::I(r)][Packed<DIM>::J(r)] = h[r].hi;
+                        Hs[Packed<DIM>::J(r)][Packed<DIM>::I(r)] = h[r].hi;
+                    }
+                    auto Kat = [&](int a, int b) { return K[a][b]; };
+                    auto Hat = [&](int a, int b) { return Hs[a][b]; };
 #pragma unroll
-                    for (int l = 0; l < DIM; ++l) lh = __fmaf_rn(Kf[i][l], Hs[l][j], __fmaf_rn(Hs[i][l], Kf[j][l], lh));
-                    R[r] = f2_add_f(v, dtf * lh);
+                    for (int r = 0; r < NC; ++r)
+                        R[r] = paper_rhs_f32<DIM, TRANSPORT>(A, S, reinterpret_cast<const float*>(buf), lane, Kat, Hat,
+                                                             r);
                 }
                 if (!solve_point_f32<DIM>(K, A.a_f2, A.dtxi_f2, R, x)) fl |= 2u;
                 const f2 xi{A.xi_f2.hi, A.xi_f2.lo};
 #pragma unroll
                 for (int r = 0; r < NC; ++r) {
+                    if constexpr (QR) h[r] = sH[r * kTile + lane];
                     out[r] = (T)(x[r].hi + x[r].lo);
                     const f2 ps = f2_add(f2_mul(xi, x[r]), h[r]);
                     psi[r] = (T)(ps.hi + ps.lo);
@@ -1306,7 +1355,7 @@ cudaError_t staged_smem_ready() {
 template <typename T, int DIM, bool TRANSPORT, bool COMP, bool PAPER>
 cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s) {
     constexpr int NC = Packed<DIM>::NC;
-    constexpr bool kQRok = sizeof(T) == 4 && !PAPER;
+    constexpr bool kQRok = sizeof(T) == 4;
     cudaError_t e;
     auto kern = fwd_kernel<T, DIM, TRANSPORT, COMP, PAPER, false>;
     const long long num_tiles = (a.N + kTile - 1) / kTile;
