@@ -68,11 +68,15 @@ STEP_KERNEL_SOURCES = [os.path.join(ROOT, "paper_2411_17294_gb300", "csrc", f)
 
 
 def step_kernel_source_hash() -> str:
+    """SHA-256 of the step kernel's sources without their whole-line comments
+    (an edit of a comment does not change the kernel)."""
     import hashlib
     h = hashlib.sha256()
     for f in STEP_KERNEL_SOURCES:
         with open(f, "rb") as fh:
-            h.update(fh.read())
+            for ln in fh:
+                if not ln.lstrip().startswith(b"//"):
+                    h.update(ln)
     return h.hexdigest()
 
 

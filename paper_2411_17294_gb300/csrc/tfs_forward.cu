@@ -9,10 +9,12 @@
 //   sigma_j^{n+1} = -c_j (b1 sigma_j^n + b2 sigma_j^{n-1}) + rho_j (sigma^{n+1} - sigma0)
 //
 // Structure.  When transport is on, a pre-pass evaluates the stencil term A
-// at every point (transport_tiled: a 32 x 8 tile of E = 2 sigma^n - sigma^{n-1}
-// with a 2-cell halo in shared memory, marching over z with the z taps in
-// registers; transport_kernel, one thread per point, for grids that do not
-// tile) and the step kernel reads it like any other per-point input.  The
+// at every point (a 32 x 8 tile of E = 2 sigma^n - sigma^{n-1} with a 2-cell
+// halo in shared memory, marching over z with the z taps in registers:
+// transport_staged in 3D, its planes copied by cp.async two planes ahead,
+// transport_tiled in 2D or for buffers off 16-byte boundaries; transport_kernel,
+// one thread per point, for grids that do not tile) and the step kernel reads
+// it like any other per-point input.  The
 // step kernel is persistent: each block of 3 warps loops over tiles of 32
 // consecutive points, and everything a tile reads is staged global -> shared
 // by one thread before the compute phase: both mode levels by untiled bulk
