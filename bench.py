@@ -551,10 +551,12 @@ def ns_coupled_record(dev, steps: int = 10, warmup: int = 3):
 
 
 def prepass_record(total_ms: float, launch_ms, steps: int, N: int, elem: int, peak: float) -> dict:
-    """The transport pre-pass of the 3D step: its time per step is the step's
-    time less the step kernel's (the two kernels are the only launches of a
-    step and run back to back on one stream); algorithmic bytes per point: two
-    stress levels and u read, the transport term written, 84 B in FP32."""
+    """The transport pre-pass of the 3D step on one GPU: its time per step is
+    the step's time less the step kernel's (the two kernels are the only
+    launches of a step and run back to back on one stream; with slabs the step
+    also exchanges halos, so no figure is given there); algorithmic bytes per
+    point: two stress levels and u read, the transport term written, 84 B in
+    FP32."""
     ms = max(total_ms - sum(launch_ms), 0.0) / steps
     bpp = (2 * 6 + 3 + 6) * elem
     gbs = bpp * N / (ms * 1e-3) / 1e9 if ms > 0 else None
@@ -833,7 +835,8 @@ def main():
                          "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": avg_launch_s * 1e3,
                          "step_share": sum(launch_ms) / total_ms,
                          "whole_step_gbs": algorithmic_bytes_per_point(3, W["m"], elem) * N / (ms_per_step * 1e-3) / 1e9,
-                         "prepass": prepass_record(total_ms, launch_ms, args.steps, N, elem, peak)},
+                         "prepass": prepass_record(total_ms, launch_ms, args.steps, N, elem, peak) if world == 1
+                         else None},
             "gpu_launches": launches_per_step * args.steps,
             "device_flags": flags,
             "stability": {
