@@ -568,7 +568,7 @@ struct StagedTile {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kTX * kTY, sizeof(T) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(kTX * kTY, sizeof(T) == 4 ? 3 : 2)
     transport_staged(const FwdArgs<T> A, const int stencil, const int zchunk) {
     using L = StagedTile<T>;
     constexpr int NC = L::NC;
@@ -1380,9 +1380,10 @@ cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s
             ta.sig_nm1 = a.psi_nm1;
         }
         if (a.n0 % kTX == 0 && a.n1 % kTY == 0) {
-            const int zchunk = 8;
-            const int gz = DIM == 3 ? (a.n2 + zchunk - 1) / zchunk : 1;
-            const dim3 grid(a.n0 / kTX, a.n1 / kTY, gz), block(kTX, kTY);
+            // z planes per block: 16 for the staged kernel (measured at 256^3 with 3 blocks per SM:
+            // 0.39 ms against 0.45 with 8), 8 for the plain one
+            const int zs = 16, zt = 8;
+            const dim3 block(kTX, kTY);
             bool staged = false;
             if constexpr (DIM == 3) {
                 staged = (long long)a.n0 * a.n1 < (1ll << 31) && aligned16(ta.sig_n) && aligned16(ta.sig_nm1) &&
@@ -1391,10 +1392,14 @@ cudaError_t launch_one(const FwdArgs<T>& a, const LaunchCfg& cfg, cudaStream_t s
                 if (staged) {
                     e = staged_smem_ready<T>();
                     if (e != cudaSuccess) return e;
-                    transport_staged<T><<<grid, block, StagedTile<T>::kSmemBytes, s>>>(ta, cfg.stencil, zchunk);
+                    const dim3 grid(a.n0 / kTX, a.n1 / kTY, (a.n2 + zs - 1) / zs);
+                    transport_staged<T><<<grid, block, StagedTile<T>::kSmemBytes, s>>>(ta, cfg.stencil, zs);
                 }
             }
-            if (!staged) transport_tiled<T, DIM><<<grid, block, 0, s>>>(ta, cfg.stencil, zchunk);
+            if (!staged) {
+                const dim3 grid(a.n0 / kTX, a.n1 / kTY, DIM == 3 ? (a.n2 + zt - 1) / zt : 1);
+                transport_tiled<T, DIM><<<grid, block, 0, s>>>(ta, cfg.stencil, zt);
+            }
         } else {
             const int threads = 256;
             long long blocks = (a.N + threads - 1) / threads;
